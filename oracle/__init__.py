@@ -1,0 +1,216 @@
+"""ORACLE -- test infrastructure only.
+
+A plain, slow FP64 CPU restatement of the ABCMB hot path (arXiv 2602.15104)
+used to check the CUDA library.  Only tests/, __graft_entry__.smoke() and
+bench.py's cpu_baseline / reference legs may import it; the library in
+paper_2602_15104_gb300/ never does.  The C sources next to this file cite the
+paper passage each step follows.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+HOOK_FREEZE_METRIC = 1
+HOOK_NO_THOMSON = 2
+HOOK_EDS_CDM = 4
+
+BG_FIELDS = ("a", "Hc", "dHc", "fc", "fb", "fg", "fnu", "tau", "xe", "dxe",
+             "nuT", "Rinv", "cs2", "kappa", "g", "dg")
+SCALAR_FIELDS = ("H0", "Om_b", "Om_c", "Om_g", "Om_nu", "Om_L", "R_nu", "f_He",
+                 "nH0", "A_s", "z_reion", "lna_tc", "lna_sw", "tau0", "lna_He3", "n_s")
+
+_D = ctypes.POINTER(ctypes.c_double)
+_L = ctypes.POINTER(ctypes.c_long)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        L.orc_scalars.argtypes = [_D, ctypes.c_int, _D]
+        L.orc_background.argtypes = [_D, ctypes.c_int, _D, ctypes.c_int, _D]
+        L.orc_nodes.argtypes = [_D, ctypes.c_int, _D]
+        L.orc_nstate_of.argtypes = [_D]
+        L.orc_lna_start_of.argtypes = [_D, ctypes.c_double]
+        L.orc_lna_start_of.restype = ctypes.c_double
+        L.orc_trajectory.argtypes = [_D, _D, ctypes.c_double, _D, ctypes.c_int, _D, _D,
+                                     ctypes.c_double, _L]
+        L.orc_rhs_at.argtypes = [_D, _D, ctypes.c_double, ctypes.c_double, _D, _D]
+        L.orc_bessel.argtypes = [ctypes.c_int, ctypes.c_double, _D]
+        L.orc_project.argtypes = [ctypes.c_int, _D, _D, ctypes.c_double, _D, ctypes.c_int, _D,
+                                  ctypes.c_int, ctypes.c_double, _D, ctypes.c_int]
+        L.orc_cl.argtypes = [_D, ctypes.c_int, _D, ctypes.c_int, ctypes.c_double,
+                             ctypes.c_double, ctypes.c_double, _D]
+        L.orc_run.argtypes = [_D, ctypes.c_int, _D, _D, ctypes.c_int, ctypes.c_int, _D, _D, _D,
+                              _L, ctypes.c_int]
+        L.orc_radau_tableau.argtypes = [_D]
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(_D) if a is not None else None
+
+
+def _arr(x):
+    return np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+
+
+def opts(lmax=12, lmax_g=None, lmax_pol=None, lmax_nu=None, scale_sw=1.0, scale_isw=1.0,
+         scale_dop=1.0, scale_pol=1.0, step_c=0.05, step_cap=0.05, hooks=0):
+    """Options vector: hierarchy truncations, source switches (App. A.1), the
+    step schedule of the oracle's integrator and test hooks."""
+    lg = lmax if lmax_g is None else lmax_g
+    lp = lmax if lmax_pol is None else lmax_pol
+    ln = lmax if lmax_nu is None else lmax_nu
+    return np.array([lg, lp, ln, scale_sw, scale_isw, scale_dop, scale_pol, step_c, step_cap,
+                     hooks], dtype=np.float64)
+
+
+def nstate(o):
+    return lib().orc_nstate_of(_p(_arr(o)))
+
+
+def scalars(params, hooks=0):
+    out = np.zeros(16)
+    rc = lib().orc_scalars(_p(_arr(params)), hooks, _p(out))
+    if rc:
+        raise RuntimeError("oracle background failed")
+    return dict(zip(SCALAR_FIELDS, out))
+
+
+def background(params, lna, hooks=0):
+    lna = _arr(np.atleast_1d(lna))
+    out = np.zeros((lna.size, 16))
+    rc = lib().orc_background(_p(_arr(params)), hooks, _p(lna), lna.size, _p(out))
+    if rc:
+        raise RuntimeError("oracle background failed")
+    return {f: out[:, i] for i, f in enumerate(BG_FIELDS)}
+
+
+def nodes(params, n_tau):
+    out = np.zeros((3, n_tau))
+    if lib().orc_nodes(_p(_arr(params)), n_tau, _p(out)):
+        raise RuntimeError("oracle nodes failed")
+    return out[0], out[1], out[2]
+
+
+def lna_start(params, k):
+    return lib().orc_lna_start_of(_p(_arr(params)), float(k))
+
+
+def trajectory(params, o, k, lna_out, y_init=None, lna_init=0.0):
+    o = _arr(o)
+    lna_out = _arr(lna_out)
+    n = nstate(o)
+    y = np.zeros((lna_out.size, n))
+    steps = ctypes.c_long(0)
+    yi = _arr(y_init) if y_init is not None else None
+    rc = lib().orc_trajectory(_p(_arr(params)), _p(o), float(k), _p(lna_out), lna_out.size,
+                              _p(y), _p(yi), float(lna_init), ctypes.byref(steps))
+    if rc:
+        raise RuntimeError("oracle trajectory failed")
+    return y, steps.value
+
+
+def rhs(params, o, k, lna, y):
+    o = _arr(o)
+    dy = np.zeros(nstate(o))
+    lib().orc_rhs_at(_p(_arr(params)), _p(o), float(k), float(lna), _p(_arr(y)), _p(dy))
+    return dy
+
+
+def bessel(lmax, x):
+    out = np.zeros(lmax + 1)
+    lib().orc_bessel(int(lmax), float(x), _p(out))
+    return out
+
+
+def project(tau, w, tau0, k, S, lmax, scale_pol=1.0, nthreads=0):
+    tau, w, k, S = _arr(tau), _arr(w), _arr(k), _arr(S)
+    D = np.zeros((k.size, lmax - 1, 2))
+    lib().orc_project(tau.size, _p(tau), _p(w), float(tau0), _p(k), k.size, _p(S), int(lmax),
+                      float(scale_pol), _p(D), int(nthreads))
+    return D
+
+
+def cl(k, Delta, lmax, A_s, n_s, k_pivot=0.05):
+    k, Delta = _arr(k), _arr(Delta)
+    out = np.zeros((3, lmax - 1))
+    lib().orc_cl(_p(k), k.size, _p(Delta), int(lmax), float(A_s), float(n_s), float(k_pivot),
+                 _p(out))
+    return out
+
+
+def radau_tableau():
+    out = np.zeros(12)
+    lib().orc_radau_tableau(_p(out))
+    return out[:9].reshape(3, 3), out[9:]
+
+
+def run(params, k, n_tau, lmax_cl, o, want=("S", "Delta", "Cl"), nthreads=0):
+    """Whole path for one cosmology; returns a dict with the requested arrays
+    plus per-mode step counts."""
+    k = _arr(k)
+    o = _arr(o)
+    nk = k.size
+    S = np.zeros((nk, n_tau, 3)) if "S" in want else None
+    D = np.zeros((nk, lmax_cl - 1, 2)) if "Delta" in want else None
+    C = np.zeros((3, lmax_cl - 1)) if "Cl" in want else None
+    steps = np.zeros(nk, dtype=np.int64)
+    rc = lib().orc_run(_p(_arr(params)), int(n_tau), _p(o), _p(k), nk, int(lmax_cl), _p(S),
+                       _p(D), _p(C), steps.ctypes.data_as(_L), int(nthreads))
+    if rc:
+        raise RuntimeError(f"oracle run failed ({rc})")
+    return {"S": S, "Delta": D, "Cl": C, "steps": steps}
+
+
+class Cosmo:
+    """Handle on one oracle cosmology (background built once)."""
+
+    def __init__(self, params, n_tau=0, hooks=0):
+        L = lib()
+        L.orc_create.restype = ctypes.c_void_p
+        L.orc_create.argtypes = [_D, ctypes.c_int, ctypes.c_int]
+        L.orc_destroy.argtypes = [ctypes.c_void_p]
+        L.orc_h_rhs.argtypes = [ctypes.c_void_p, _D, ctypes.c_double, ctypes.c_double, _D, _D]
+        L.orc_h_matrix.argtypes = [ctypes.c_void_p, _D, ctypes.c_double, ctypes.c_double, _D]
+        self._h = L.orc_create(_p(_arr(params)), int(n_tau), int(hooks))
+        if not self._h:
+            raise RuntimeError("oracle background failed")
+
+    def rhs(self, o, k, lna, y):
+        o = _arr(o)
+        dy = np.zeros(nstate(o))
+        lib().orc_h_rhs(self._h, _p(o), float(k), float(lna), _p(_arr(y)), _p(dy))
+        return dy
+
+    def matrix(self, o, k, lna):
+        o = _arr(o)
+        n = nstate(o)
+        A = np.zeros((n, n))
+        lib().orc_h_matrix(self._h, _p(o), float(k), float(lna), _p(A))
+        return A
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().orc_destroy(self._h)
+            self._h = None
+
+
+def dense_solve(A, b):
+    A = _arr(A).copy()
+    b = _arr(b).copy()
+    L = lib()
+    L.orc_dense_solve.argtypes = [_D, ctypes.c_int, _D]
+    if L.orc_dense_solve(_p(A), b.size, _p(b)):
+        raise RuntimeError("singular")
+    return b

@@ -1,0 +1,662 @@
+/*
+ * ORACLE (test infrastructure only; see orc.h).
+ *
+ * Background, thermal history and tau nodes of one flat-LCDM cosmology.
+ *
+ *  - densities: photons rho = pi^2/15 T^4 (App. C.4), massless neutrinos
+ *    N 7 pi^2/120 T_nu^4 (App. C.5, Sec. 2.4 "Neutrino parameters"), baryons
+ *    and CDM ~ a^-3 (App. C.2-C.3), Lambda fixed by flatness (App. A.2,
+ *    derived omega_Lambda);
+ *  - conformal time tau = int dln a / (a H), written as the exact
+ *    radiation+matter closed form plus a quadrature of the Lambda correction;
+ *  - helium: Saha HeIII/HeII until x_HeIII < 1e-9, then Saha HeII/HeI
+ *    (App. B.1.1; the post-Saha correction and the helium ODE are not taken,
+ *    a reading);
+ *  - hydrogen: Saha (App. B.1.2, eq. SahaH) while x_p > 0.99, then a Peebles
+ *    three-level atom (the TLA the paper cites in App. B.1.2).  Its rates are
+ *    not printed in the paper and are taken from the literature: case-B
+ *    recombination fit of Pequignot, Petitjean & Boisson (1991),
+ *    photo-ionisation by detailed balance at the radiation temperature,
+ *    Lambda_2s1s = 8.2245809 /s, Lyman-alpha escape through
+ *    K = lambda_alpha^3 / (8 pi H).  PARITY UNPINNED against an external
+ *    recombination code (none is available here); pinned only by its Saha
+ *    limit and its freeze-out range;
+ *  - matter temperature: T_m = T_CMB (1 - H/Gamma_C) for z > 700, then
+ *    dT_m/dln a = (-2 H T_m + Gamma_C (T_CMB - T_m)) / H (App. B.1.2);
+ *  - reionization: tanh steps (App. B.2, eqs. h_reion, y_reio, he_reion),
+ *    patched as x_e = x_rec + (1 + f_He - x_rec) S_H + f_He S_He (a reading);
+ *    z_reion from tau_reion by bisection (App. A.2, eq. tau_reion: only the
+ *    reionization electrons count);
+ *  - 1/tau_c = a n_e sigma_T, kappa, g, g' (App. B.4), baryon sound speed and
+ *    mean mass (App. C.3);
+ *  - start of tight coupling a_tc: H tau_c = R_tc (App. A.1, eq.
+ *    k_start_small); start of each mode a_i(k) = min(a_tc, a_k) with
+ *    k / H(a_k) = R_large (eq. k_start_large);
+ *  - tau nodes: 1/4 uniform in ln a on [ln a_tc, ln a(z=1300)), 1/2 uniform in
+ *    z on [1300, 900), 1/4 uniform in tau on [tau(z=900), tau_0); trapezoid
+ *    weights in tau (App. B.6: trapezoid rules, no time cut).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "orc.h"
+
+/* ---- physical constants (CODATA 2018 / PDG) ---- */
+#define O_PI 3.14159265358979323846
+#define O_C_CMS 2.99792458e10
+#define O_MPC_CM 3.0856775814913673e24
+#define O_SIGMA_T 6.6524587321e-25     /* cm^2                              */
+#define O_HC 1.239841984e-4            /* h c [eV cm]                       */
+#define O_HBARC 1.973269804e-5         /* hbar c [eV cm]                    */
+#define O_KB 8.617333262e-5            /* eV / K                            */
+#define O_ME 510998.95                 /* m_e c^2 [eV]                      */
+#define O_MH 938783073.6               /* m_H c^2 [eV]                      */
+#define O_MHE_MH 3.971480              /* m(4He atom) / m(H atom)           */
+#define O_EH 13.598434005              /* H ionization energy [eV]          */
+#define O_EHE1 24.587387               /* He I ionization energy [eV]       */
+#define O_EHE2 54.417760               /* He II ionization energy [eV]      */
+#define O_L2S1S 8.2245809              /* 2s -> 1s two-photon rate [1/s]    */
+#define O_G 6.67430e-8                 /* cm^3 / (g s^2)                    */
+#define O_EV_ERG 1.602176634e-12
+
+#define TH_PER_UNIT 2048  /* TLA table nodes per unit ln a */
+#define KP_PER_UNIT 1024  /* kappa table nodes per unit ln a */
+#define CT_PER_UNIT 128   /* conformal-time correction table */
+#define LNA_MIN (-20.0)
+
+/* ------------------------------------------------------------------ */
+/* Gauss-Legendre nodes on [-1,1] by Newton iteration on P_n.          */
+static void gauss_legendre(int n, double *x, double *w)
+{
+    for (int i = 0; i < (n + 1) / 2; i++) {
+        double z = cos(O_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; it++) {
+            double p0 = 1.0, p1 = 0.0;
+            for (int j = 1; j <= n; j++) {
+                double p2 = p1;
+                p1 = p0;
+                p0 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p2) / j;
+            }
+            dp = n * (z * p0 - p1) / (z * z - 1.0);
+            double dz = p0 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        x[i] = -z; x[n - 1 - i] = z;
+        w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+#define GL_N 8
+typedef struct { double x[GL_N], w[GL_N]; } gl_rule;
+static gl_rule gl_make(void)
+{
+    gl_rule r;
+    gauss_legendre(GL_N, r.x, r.w);
+    return r;
+}
+
+static void hermite_basis(double u, double *h00, double *h10, double *h01, double *h11)
+{
+    *h00 = (1 + 2 * u) * (1 - u) * (1 - u);
+    *h10 = u * (1 - u) * (1 - u);
+    *h01 = u * u * (3 - 2 * u);
+    *h11 = u * u * (u - 1);
+}
+
+/* ------------------------------------------------------------------ */
+/* background                                                          */
+static double E2(const orc_cosmo *c, double a)
+{
+    return c->Om_r / (a * a * a * a) + c->Om_m / (a * a * a) + c->Om_L;
+}
+
+double orc_Hconf(const orc_cosmo *c, double lna)
+{
+    double a = exp(lna);
+    return a * c->H0 * sqrt(E2(c, a));
+}
+
+/* radiation+matter conformal time, exact: 2a / (H0 (sqrt(Om_r+Om_m a)+sqrt(Om_r))) */
+static double tau_rm(const orc_cosmo *c, double a)
+{
+    return 2.0 * a / (c->H0 * (sqrt(c->Om_r + c->Om_m * a) + sqrt(c->Om_r)));
+}
+
+static double tau_corr_integrand(const orc_cosmo *c, double lna)
+{
+    double a = exp(lna);
+    double hc = a * c->H0 * sqrt(E2(c, a));
+    double hrm = c->H0 * sqrt(c->Om_r / (a * a) + c->Om_m / a);
+    return 1.0 / hc - 1.0 / hrm;
+}
+
+double orc_tau_of_lna(const orc_cosmo *c, double lna)
+{
+    double a = exp(lna);
+    double t = (lna - c->ct_lna0) / c->ct_dlna;
+    int i = (int)floor(t);
+    if (i < 0) return tau_rm(c, a);
+    if (i > c->n_ct - 2) i = c->n_ct - 2;
+    double u = t - i, h = c->ct_dlna, l0 = c->ct_lna0 + i * h;
+    double d0 = tau_corr_integrand(c, l0), d1 = tau_corr_integrand(c, l0 + h);
+    double h00, h10, h01, h11;
+    hermite_basis(u, &h00, &h10, &h01, &h11);
+    double corr = h00 * c->ct_tau[i] + h10 * h * d0 + h01 * c->ct_tau[i + 1] + h11 * h * d1;
+    return tau_rm(c, a) + corr;
+}
+
+/* ------------------------------------------------------------------ */
+/* recombination pieces                                                */
+static double saha_pref(double T, double mu) /* (2 pi mu T / (hc)^2)^{3/2} [cm^-3] */
+{
+    double v = 2.0 * O_PI * mu * T / (O_HC * O_HC);
+    return v * sqrt(v);
+}
+
+static double nH_of(const orc_cosmo *c, double a) { return c->nH0 / (a * a * a); }
+static double Tg_of(const orc_cosmo *c, double a) { return c->TCMB0 / a; }
+static double mu_eHe(void) { return O_ME * (O_MHE_MH * O_MH) / (O_ME + O_MHE_MH * O_MH); }
+static double mu_eH(void) { return O_ME * O_MH / (O_ME + O_MH); }
+
+static double x_heIII_saha(const orc_cosmo *c, double a)
+{
+    double T = Tg_of(c, a), f = c->f_He;
+    double s = saha_pref(T, mu_eHe()) * exp(-O_EHE2 / T) / nH_of(c, a);
+    double b = 1.0 + f + s;
+    return 2.0 * s * f / (b + sqrt(b * b + 4.0 * s * f));
+}
+
+static double x_heII_saha(const orc_cosmo *c, double a)
+{
+    double T = Tg_of(c, a), f = c->f_He;
+    double s = 4.0 * saha_pref(T, mu_eHe()) * exp(-O_EHE1 / T) / nH_of(c, a);
+    double b = 1.0 + s;
+    return 2.0 * s * f / (b + sqrt(b * b + 4.0 * s * f));
+}
+
+static double x_he(const orc_cosmo *c, double lna)
+{
+    double a = exp(lna);
+    if (lna < c->lna_He3) return c->f_He + x_heIII_saha(c, a);
+    return x_heII_saha(c, a);
+}
+
+static double xp_saha(const orc_cosmo *c, double a)
+{
+    double T = Tg_of(c, a);
+    double s = saha_pref(T, mu_eH()) * exp(-O_EH / T) / nH_of(c, a);
+    return 2.0 / (1.0 + sqrt(1.0 + 4.0 / s));
+}
+
+static double alpha_B(double T_eV) /* cm^3/s, Pequignot et al. (1991) case-B fit */
+{
+    double t = T_eV / O_KB / 1.0e4;
+    return 1.0e-13 * 4.309 * pow(t, -0.6166) / (1.0 + 0.6703 * pow(t, 0.5300));
+}
+
+static double H_sec(const orc_cosmo *c, double a) /* H [1/s] */
+{
+    return c->H0 * sqrt(E2(c, a)) * O_C_CMS / O_MPC_CM;
+}
+
+/* Compton rate Gamma_C [1/s] (App. B.1.2) for recombination x_e */
+static double gamma_C(const orc_cosmo *c, double a, double xe)
+{
+    double rho_g = c->rho_g0 / (a * a * a * a);
+    return 8.0 * O_SIGMA_T * O_C_CMS * rho_g / (3.0 * O_ME) * xe / (1.0 + c->f_He + xe);
+}
+
+static double Tm_quasistatic(const orc_cosmo *c, double a, double xe)
+{
+    return Tg_of(c, a) * (1.0 - H_sec(c, a) / gamma_C(c, a, xe));
+}
+
+/* Peebles TLA (+ T_m ODE when with_Tm) right-hand side in ln a. */
+static void tla_rhs(const orc_cosmo *c, double lna, const double *y, int with_Tm, double *dy)
+{
+    double a = exp(lna);
+    double xp = y[0];
+    double xe = xp + x_he(c, lna);
+    double Tg = Tg_of(c, a);
+    double Tm = with_Tm ? y[1] : Tm_quasistatic(c, a, xe);
+    double nH = nH_of(c, a), H = H_sec(c, a);
+    double alpha = alpha_B(Tm);
+    double beta = alpha_B(Tg) * saha_pref(Tg, mu_eH()) * exp(-0.25 * O_EH / Tg);
+    double lam = O_HC / (0.75 * O_EH);
+    double K = lam * lam * lam / (8.0 * O_PI * H);
+    double n1s = nH * (1.0 - xp);
+    double C = (1.0 + K * O_L2S1S * n1s) / (1.0 + K * (O_L2S1S + beta) * n1s);
+    double dxdt = -C * (alpha * nH * xe * xp - beta * (1.0 - xp) * exp(-0.75 * O_EH / Tg));
+    dy[0] = dxdt / H;
+    if (with_Tm) dy[1] = -2.0 * Tm + gamma_C(c, a, xe) / H * (Tg - Tm);
+}
+
+/* 3-stage Radau IIA coefficients (Hairer & Wanner, order 5). */
+static void radau_tableau(double A[3][3], double cc[3])
+{
+    double s6 = sqrt(6.0);
+    A[0][0] = (88.0 - 7.0 * s6) / 360.0;
+    A[0][1] = (296.0 - 169.0 * s6) / 1800.0;
+    A[0][2] = (-2.0 + 3.0 * s6) / 225.0;
+    A[1][0] = (296.0 + 169.0 * s6) / 1800.0;
+    A[1][1] = (88.0 + 7.0 * s6) / 360.0;
+    A[1][2] = (-2.0 - 3.0 * s6) / 225.0;
+    A[2][0] = (16.0 - s6) / 36.0;
+    A[2][1] = (16.0 + s6) / 36.0;
+    A[2][2] = 1.0 / 9.0;
+    cc[0] = (4.0 - s6) / 10.0;
+    cc[1] = (4.0 + s6) / 10.0;
+    cc[2] = 1.0;
+}
+
+/* Exposed for the order-condition pin. */
+void orc_radau_tableau(double *out12)
+{
+    double A[3][3], cc[3];
+    radau_tableau(A, cc);
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) out12[3 * i + j] = A[i][j];
+    for (int i = 0; i < 3; i++) out12[9 + i] = cc[i];
+}
+
+/* One Radau IIA step of the (n <= 2)-dimensional TLA system; simplified
+   Newton with a finite-difference Jacobian, iterated to convergence. */
+static int tla_radau_step(const orc_cosmo *c, double x, double h, double *y, int n)
+{
+    double A[3][3], cc[3];
+    radau_tableau(A, cc);
+    double J[2][2], f0[2], f1[2], yp[2];
+    tla_rhs(c, x, y, n == 2, f0);
+    for (int j = 0; j < n; j++) {
+        double d = 1e-7 * (fabs(y[j]) + 1e-12);
+        memcpy(yp, y, sizeof(double) * n);
+        yp[j] += d;
+        tla_rhs(c, x, yp, n == 2, f1);
+        memcpy(yp, y, sizeof(double) * n);
+        yp[j] -= d;
+        double fm[2];
+        tla_rhs(c, x, yp, n == 2, fm);
+        for (int i = 0; i < n; i++) J[i][j] = (f1[i] - fm[i]) / (2.0 * d);
+    }
+    int m = 3 * n;
+    double M[36], Z[6] = {0}, R[6];
+    int piv[6];
+    for (int si = 0; si < 3; si++)
+        for (int sj = 0; sj < 3; sj++)
+            for (int i = 0; i < n; i++)
+                for (int j = 0; j < n; j++)
+                    M[(si * n + i) * m + sj * n + j] = (si == sj && i == j ? 1.0 : 0.0) - h * A[si][sj] * J[i][j];
+    if (orc_lu_factor(M, m, piv)) return -1;
+    for (int it = 0; it < 60; it++) {
+        double F[3][2];
+        for (int s = 0; s < 3; s++) {
+            double ys[2];
+            for (int i = 0; i < n; i++) ys[i] = y[i] + Z[s * n + i];
+            tla_rhs(c, x + cc[s] * h, ys, n == 2, F[s]);
+        }
+        for (int s = 0; s < 3; s++)
+            for (int i = 0; i < n; i++) {
+                double acc = 0.0;
+                for (int t = 0; t < 3; t++) acc += A[s][t] * F[t][i];
+                R[s * n + i] = -(Z[s * n + i] - h * acc);
+            }
+        orc_lu_solve(M, m, piv, R);
+        double dmax = 0.0;
+        for (int i = 0; i < m; i++) {
+            Z[i] += R[i];
+            double sc = fabs(R[i]) / (fabs(y[i % n]) + 1e-300);
+            if (sc > dmax) dmax = sc;
+        }
+        if (dmax < 1e-15) break;
+    }
+    for (int i = 0; i < n; i++) y[i] += Z[2 * n + i];
+    return 0;
+}
+
+/* locate ln a in the two-segment TLA table: returns interval index, u in [0,1] */
+static int th_locate(const orc_cosmo *c, double lna, double *u, double *h)
+{
+    int n1 = c->n_th1, n = c->n_th1 + c->n_th2;
+    int i;
+    if (lna <= c->lna_700) {
+        double dl = (c->lna_700 - c->lna_sw) / n1;
+        i = (int)floor((lna - c->lna_sw) / dl);
+        if (i < 0) i = 0;
+        if (i > n1 - 1) i = n1 - 1;
+    } else {
+        double dl = (0.0 - c->lna_700) / c->n_th2;
+        i = n1 + (int)floor((lna - c->lna_700) / dl);
+        if (i < n1) i = n1;
+        if (i > n - 1) i = n - 1;
+    }
+    *h = c->th_lna[i + 1] - c->th_lna[i];
+    *u = (lna - c->th_lna[i]) / *h;
+    return i;
+}
+
+static double th_interp(const orc_cosmo *c, const double *v, const double *dv, double lna)
+{
+    double u, h, h00, h10, h01, h11;
+    int i = th_locate(c, lna, &u, &h);
+    hermite_basis(u, &h00, &h10, &h01, &h11);
+    return h00 * v[i] + h10 * h * dv[i] + h01 * v[i + 1] + h11 * h * dv[i + 1];
+}
+
+/* recombination-only electron fraction (no reionization) */
+static double xe_rec(const orc_cosmo *c, double lna)
+{
+    double xp;
+    if (lna < c->lna_sw) xp = xp_saha(c, exp(lna));
+    else xp = th_interp(c, c->th_xp, c->th_dxp, lna);
+    return xp + x_he(c, lna);
+}
+
+static double tanh_step(double u) { return 0.5 * (1.0 + tanh(u)); }
+
+double orc_xe_of_lna(const orc_cosmo *c, double lna, double *dxe)
+{
+    if (c->hooks & ORC_HOOK_EDS_CDM) { if (dxe) *dxe = 0.0; return 0.0; }
+    double z = exp(-lna) - 1.0;
+    double beta = c->beta_re;
+    double y = pow(1.0 + z, beta), yre = pow(1.0 + c->z_reion, beta);
+    double dy = beta * c->dz_re * pow(1.0 + c->z_reion, beta - 1.0);
+    double u1 = (yre - y) / dy, u2 = (c->z_re_He - z) / c->dz_re_He;
+    double S1 = tanh_step(u1), S2 = tanh_step(u2);
+    double xr = xe_rec(c, lna);
+    double xe = xr + (1.0 + c->f_He - xr) * S1 + c->f_He * S2;
+    if (dxe) {
+        const double d = 1e-5;
+        double dxr = (xe_rec(c, lna + d) - xe_rec(c, lna - d)) / (2.0 * d);
+        double t1 = tanh(u1), t2 = tanh(u2);
+        double dS1 = 0.5 * (1.0 - t1 * t1) * beta * y / dy;      /* dy/dlna = -beta y */
+        double dS2 = 0.5 * (1.0 - t2 * t2) * (1.0 + z) / c->dz_re_He;
+        *dxe = dxr * (1.0 - S1) + (1.0 + c->f_He - xr) * dS1 + c->f_He * dS2;
+    }
+    return xe;
+}
+
+/* matter temperature [eV] and its logarithmic derivative */
+double orc_Tm_of_lna(const orc_cosmo *c, double lna, double *dlnTm)
+{
+    double a = exp(lna);
+    if (lna < c->lna_700) {
+        double Tm = Tm_quasistatic(c, a, xe_rec(c, lna));
+        if (dlnTm) {
+            const double d = 1e-5;
+            double tp = Tm_quasistatic(c, exp(lna + d), xe_rec(c, lna + d));
+            double tm = Tm_quasistatic(c, exp(lna - d), xe_rec(c, lna - d));
+            *dlnTm = (log(tp) - log(tm)) / (2.0 * d);
+        }
+        return Tm;
+    }
+    double Tm = th_interp(c, c->th_Tm, c->th_dTm, lna);
+    if (dlnTm) {
+        double y[2] = {th_interp(c, c->th_xp, c->th_dxp, lna), Tm}, dy[2];
+        tla_rhs(c, lna, y, 1, dy);
+        *dlnTm = dy[1] / Tm;
+    }
+    return Tm;
+}
+
+static double nuT_of(const orc_cosmo *c, double lna, double xe)
+{
+    double a = exp(lna);
+    return xe * c->nH0 * O_SIGMA_T * O_MPC_CM / (a * a * orc_Hconf(c, lna));
+}
+
+static double kappa_of(const orc_cosmo *c, double lna)
+{
+    double t = (lna - c->kp_lna0) / c->kp_dlna;
+    int i = (int)floor(t);
+    if (i < 0) i = 0;
+    if (i > c->n_kp - 2) i = c->n_kp - 2;
+    double u = t - i, h = c->kp_dlna, l0 = c->kp_lna0 + i * h;
+    double d0 = -nuT_of(c, l0, orc_xe_of_lna(c, l0, NULL));
+    double d1 = -nuT_of(c, l0 + h, orc_xe_of_lna(c, l0 + h, NULL));
+    double h00, h10, h01, h11;
+    hermite_basis(u, &h00, &h10, &h01, &h11);
+    return h00 * c->kp_kappa[i] + h10 * h * d0 + h01 * c->kp_kappa[i + 1] + h11 * h * d1;
+}
+
+void orc_bg_eval(const orc_cosmo *c, double lna, orc_bg *o, int with_thermo)
+{
+    double a = exp(lna);
+    double e2 = E2(c, a);
+    o->a = a;
+    o->Hc = a * c->H0 * sqrt(e2);
+    double rg = c->Om_g / (a * a * a * a), rn = c->Om_nu / (a * a * a * a);
+    double rb = c->Om_b / (a * a * a), rc = c->Om_c / (a * a * a);
+    o->fc = rc / e2; o->fb = rb / e2; o->fg = rg / e2; o->fnu = rn / e2;
+    /* d ln H_conf / d ln a = 1 + (1/2) d ln E^2 / d ln a */
+    o->dHc = o->Hc * (1.0 + 0.5 * (-4.0 * (rg + rn) - 3.0 * (rb + rc)) / e2);
+    o->tau = orc_tau_of_lna(c, lna);
+    o->Rinv = c->Om_b > 0.0 ? (4.0 / 3.0) * c->Om_g / (c->Om_b * a) : 0.0;
+    if (!with_thermo || (c->hooks & ORC_HOOK_EDS_CDM)) {
+        o->xe = o->dxe = o->nuT = o->cs2 = 0.0;
+        o->kappa = 0.0; o->expmk = 1.0; o->g = o->dg = 0.0;
+        return;
+    }
+    double dxe = 0.0;
+    o->xe = orc_xe_of_lna(c, lna, with_thermo >= 2 ? &dxe : NULL);
+    o->dxe = dxe;
+    o->nuT = nuT_of(c, lna, o->xe);
+    double dlnTm;
+    double Tm = orc_Tm_of_lna(c, lna, &dlnTm);
+    double mub = O_MH / ((1.0 + o->xe) * (1.0 - c->YHe) + c->YHe / O_MHE_MH);
+    o->cs2 = Tm / mub * (1.0 - dlnTm / 3.0);
+    if (with_thermo < 2) {
+        o->kappa = 0.0; o->expmk = 1.0; o->g = o->dg = 0.0;
+        return;
+    }
+    o->kappa = kappa_of(c, lna);
+    o->expmk = exp(-o->kappa);
+    o->g = o->Hc * o->nuT * o->expmk;
+    o->dg = o->g * (dxe / o->xe - 2.0 + o->nuT);
+}
+
+/* ------------------------------------------------------------------ */
+static double bisect(double (*f)(const orc_cosmo *, double, double), const orc_cosmo *c,
+                     double arg, double lo, double hi)
+{
+    double flo = f(c, lo, arg);
+    for (int it = 0; it < 200; it++) {
+        double mid = 0.5 * (lo + hi);
+        if (mid == lo || mid == hi) break;
+        double fm = f(c, mid, arg);
+        if ((fm < 0.0) == (flo < 0.0)) { lo = mid; flo = fm; }
+        else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+static double f_he3(const orc_cosmo *c, double lna, double arg)
+{ return x_heIII_saha(c, exp(lna)) - arg; }
+static double f_hsw(const orc_cosmo *c, double lna, double arg)
+{ return xp_saha(c, exp(lna)) - arg; }
+static double f_tc(const orc_cosmo *c, double lna, double arg)
+{ return nuT_of(c, lna, orc_xe_of_lna(c, lna, NULL)) - arg; }
+static double f_Hk(const orc_cosmo *c, double lna, double arg)
+{ return orc_Hconf(c, lna) - arg; }
+static double f_tau(const orc_cosmo *c, double lna, double arg)
+{ return orc_tau_of_lna(c, lna) - arg; }
+
+/* optical depth from the reionization electrons alone, for a trial z_reion */
+static double tau_reion_of(const orc_cosmo *c, double zre, gl_rule *gl)
+{
+    double beta = c->beta_re;
+    double dy = beta * c->dz_re * pow(1.0 + zre, beta - 1.0);
+    double ymax = pow(1.0 + zre, beta) + 25.0 * dy;
+    double zmax = pow(ymax, 1.0 / beta) - 1.0;
+    double zhe = c->z_re_He + 25.0 * c->dz_re_He;
+    if (zhe > zmax) zmax = zhe;
+    double lo = -log(1.0 + zmax);
+    int np = 400;
+    double hp = (0.0 - lo) / np, acc = 0.0;
+    for (int p = 0; p < np; p++) {
+        for (int q = 0; q < GL_N; q++) {
+            double lna = lo + hp * (p + 0.5 * (1.0 + gl->x[q]));
+            double a = exp(lna), z = 1.0 / a - 1.0;
+            double S1 = tanh_step((pow(1.0 + zre, beta) - pow(1.0 + z, beta)) / dy);
+            double S2 = tanh_step((c->z_re_He - z) / c->dz_re_He);
+            double xre = (1.0 + c->f_He) * S1 + c->f_He * S2;
+            acc += 0.5 * hp * gl->w[q] * xre * nuT_of(c, lna, 1.0);
+        }
+    }
+    return acc;
+}
+
+int orc_cosmo_init(orc_cosmo *c, const double p[6], int n_tau, int hooks)
+{
+    memset(c, 0, sizeof(*c));
+    gl_rule gl = gl_make();
+    c->omega_b = p[0]; c->omega_cdm = p[1]; c->h = p[2];
+    c->n_s = p[3]; c->ln10As = p[4]; c->tau_reio = p[5];
+    c->hooks = hooks;
+    c->YHe = 0.245; c->TCMB0 = 2.34865418e-4; c->Tnu_ratio = 0.71636856; c->N_nu = 3.0;
+    c->z_re_He = 3.5; c->dz_re_He = 0.5; c->dz_re = 0.5; c->beta_re = 1.5;
+    c->R_tc = 1.5e-3; c->R_large = 7e-2; c->k_pivot = 0.05;
+    c->A_s = exp(c->ln10As) * 1e-10;
+    c->H0 = c->h * 1.0e7 / O_C_CMS; /* 100 h km/s/Mpc divided by c, in 1/Mpc */
+    double H100 = 1.0e7 / O_MPC_CM;  /* s^-1 */
+    double rho_crit100 = 3.0 * H100 * H100 / (8.0 * O_PI * O_G) * O_C_CMS * O_C_CMS / O_EV_ERG; /* eV/cm^3 */
+    double T = c->TCMB0;
+    c->rho_g0 = O_PI * O_PI / 15.0 * T * T * T * T / (O_HBARC * O_HBARC * O_HBARC);
+    double Tn = c->Tnu_ratio * T;
+    double rho_nu0 = c->N_nu * 7.0 * O_PI * O_PI / 120.0 * Tn * Tn * Tn * Tn / (O_HBARC * O_HBARC * O_HBARC);
+    double h2 = c->h * c->h;
+    if (hooks & ORC_HOOK_EDS_CDM) {
+        c->Om_c = 1.0; c->Om_m = 1.0;
+    } else {
+        c->Om_b = c->omega_b / h2;
+        c->Om_c = c->omega_cdm / h2;
+        c->Om_g = c->rho_g0 / (rho_crit100 * h2);
+        c->Om_nu = rho_nu0 / (rho_crit100 * h2);
+        c->Om_r = c->Om_g + c->Om_nu;
+        c->Om_m = c->Om_b + c->Om_c;
+        c->Om_L = 1.0 - c->Om_m - c->Om_r;
+        c->R_nu = c->Om_nu / c->Om_r;
+    }
+    c->f_He = c->YHe / (O_MHE_MH * (1.0 - c->YHe));
+    c->nH0 = (1.0 - c->YHe) * c->omega_b * rho_crit100 / O_MH;
+
+    /* conformal-time correction table */
+    c->ct_lna0 = LNA_MIN;
+    c->ct_dlna = 1.0 / CT_PER_UNIT;
+    c->n_ct = (int)(-LNA_MIN * CT_PER_UNIT) + 1;
+    c->ct_tau = (double *)calloc(c->n_ct, sizeof(double));
+    for (int i = 1; i < c->n_ct; i++) {
+        double l0 = c->ct_lna0 + (i - 1) * c->ct_dlna, acc = 0.0;
+        for (int q = 0; q < GL_N; q++)
+            acc += 0.5 * c->ct_dlna * gl.w[q] * tau_corr_integrand(c, l0 + 0.5 * c->ct_dlna * (1.0 + gl.x[q]));
+        c->ct_tau[i] = c->ct_tau[i - 1] + acc;
+    }
+    c->tau0 = orc_tau_of_lna(c, 0.0);
+    if (hooks & ORC_HOOK_EDS_CDM) return 0;
+
+    /* helium HeIII -> HeII switch, hydrogen Saha -> TLA switch */
+    c->lna_He3 = bisect(f_he3, c, 1e-9, -12.0, -5.0);
+    c->lna_sw = bisect(f_hsw, c, 0.99, -9.0, -6.0);
+    c->lna_700 = -log(701.0);
+
+    /* TLA table */
+    c->n_th1 = (int)ceil((c->lna_700 - c->lna_sw) * TH_PER_UNIT);
+    c->n_th2 = (int)ceil((0.0 - c->lna_700) * TH_PER_UNIT);
+    int nth = c->n_th1 + c->n_th2 + 1;
+    c->th_lna = (double *)malloc(sizeof(double) * nth);
+    c->th_xp = (double *)malloc(sizeof(double) * nth);
+    c->th_dxp = (double *)malloc(sizeof(double) * nth);
+    c->th_Tm = (double *)malloc(sizeof(double) * nth);
+    c->th_dTm = (double *)malloc(sizeof(double) * nth);
+    for (int i = 0; i <= c->n_th1; i++)
+        c->th_lna[i] = c->lna_sw + (c->lna_700 - c->lna_sw) * i / c->n_th1;
+    for (int i = 1; i <= c->n_th2; i++)
+        c->th_lna[c->n_th1 + i] = c->lna_700 + (0.0 - c->lna_700) * i / c->n_th2;
+    c->th_lna[nth - 1] = 0.0;
+    double y[2] = {xp_saha(c, exp(c->lna_sw)), 0.0}, dy[2];
+    for (int i = 0; i < nth; i++) {
+        double lna = c->th_lna[i];
+        int two = (i >= c->n_th1);
+        if (i == c->n_th1)
+            y[1] = Tm_quasistatic(c, exp(lna), y[0] + x_he(c, lna));
+        tla_rhs(c, lna, y, two, dy);
+        c->th_xp[i] = y[0];
+        c->th_dxp[i] = dy[0];
+        if (two) { c->th_Tm[i] = y[1]; c->th_dTm[i] = dy[1]; }
+        else { c->th_Tm[i] = Tm_quasistatic(c, exp(lna), y[0] + x_he(c, lna)); c->th_dTm[i] = 0.0; }
+        if (i + 1 < nth) {
+            double h = c->th_lna[i + 1] - lna;
+            if (tla_radau_step(c, lna, h, y, two ? 2 : 1)) return -1;
+        }
+    }
+
+    /* reionization redshift from tau_reion */
+    {
+        double lo = 0.0, hi = 60.0;
+        for (int it = 0; it < 200; it++) {
+            double mid = 0.5 * (lo + hi);
+            if (mid == lo || mid == hi) break;
+            if (tau_reion_of(c, mid, &gl) < c->tau_reio) lo = mid; else hi = mid;
+        }
+        c->z_reion = 0.5 * (lo + hi);
+    }
+
+    /* optical depth table, integrated from today backwards */
+    c->kp_lna0 = LNA_MIN;
+    c->kp_dlna = 1.0 / KP_PER_UNIT;
+    c->n_kp = (int)(-LNA_MIN * KP_PER_UNIT) + 1;
+    c->kp_kappa = (double *)calloc(c->n_kp, sizeof(double));
+    for (int i = c->n_kp - 2; i >= 0; i--) {
+        double l0 = c->kp_lna0 + i * c->kp_dlna, acc = 0.0;
+        for (int q = 0; q < GL_N; q++) {
+            double lna = l0 + 0.5 * c->kp_dlna * (1.0 + gl.x[q]);
+            acc += 0.5 * c->kp_dlna * gl.w[q] * nuT_of(c, lna, orc_xe_of_lna(c, lna, NULL));
+        }
+        c->kp_kappa[i] = c->kp_kappa[i + 1] + acc;
+    }
+
+    /* tight-coupling start */
+    c->lna_tc = bisect(f_tc, c, 1.0 / c->R_tc, LNA_MIN + 1.0, -3.0);
+
+    /* tau nodes */
+    if (n_tau >= 4) {
+        int nA = n_tau / 4, nB = n_tau / 2, nC = n_tau - nA - nB;
+        c->n_tau = n_tau;
+        c->node_lna = (double *)malloc(sizeof(double) * n_tau);
+        c->node_tau = (double *)malloc(sizeof(double) * n_tau);
+        c->node_w = (double *)malloc(sizeof(double) * n_tau);
+        double l1300 = -log(1301.0), l900 = -log(901.0);
+        for (int j = 0; j < nA; j++)
+            c->node_lna[j] = c->lna_tc + (l1300 - c->lna_tc) * j / nA;
+        for (int j = 0; j < nB; j++)
+            c->node_lna[nA + j] = -log(1.0 + 1300.0 - 400.0 * j / nB);
+        double t900 = orc_tau_of_lna(c, l900);
+        for (int j = 0; j < nC; j++) {
+            double tt = t900 + (c->tau0 - t900) * j / nC;
+            c->node_lna[nA + nB + j] = j == 0 ? l900 : bisect(f_tau, c, tt, l900, 0.0);
+        }
+        for (int j = 0; j < n_tau; j++) c->node_tau[j] = orc_tau_of_lna(c, c->node_lna[j]);
+        for (int j = 0; j < n_tau; j++) {
+            double lo = j > 0 ? c->node_tau[j - 1] : c->node_tau[j];
+            double hi = j < n_tau - 1 ? c->node_tau[j + 1] : c->node_tau[j];
+            c->node_w[j] = 0.5 * (hi - lo);
+        }
+    }
+    return 0;
+}
+
+void orc_cosmo_free(orc_cosmo *c)
+{
+    free(c->ct_tau); free(c->th_lna); free(c->th_xp); free(c->th_dxp);
+    free(c->th_Tm); free(c->th_dTm); free(c->kp_kappa);
+    free(c->node_lna); free(c->node_tau); free(c->node_w);
+    memset(c, 0, sizeof(*c));
+}
+
+double orc_lna_start(const orc_cosmo *c, double k)
+{
+    double target = k / c->R_large;
+    if (orc_Hconf(c, c->lna_tc) >= target) return c->lna_tc;
+    return bisect(f_Hk, c, target, LNA_MIN, c->lna_tc);
+}

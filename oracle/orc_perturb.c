@@ -1,0 +1,320 @@
+/*
+ * ORACLE (test infrastructure only; see orc.h).
+ *
+ * Synchronous-gauge linear perturbations of one k mode in x = ln a, and the
+ * CMB sources at the tau nodes.
+ *
+ * State vector (fixed order):
+ *   [eta, delta_c, delta_b, theta_b,
+ *    delta_g, theta_g, sigma_g, F_g3 .. F_gL,     (photon temperature, L = lmax_g)
+ *    G_0 .. G_Lp,                                  (photon polarization)
+ *    delta_nu, theta_nu, sigma_nu, F_nu3 .. F_nuLn] (massless neutrinos)
+ * with F_1 = 4 theta / (3k) and F_2 = 2 sigma (App. C.4).
+ *
+ * Equations (derivatives in ln a):
+ *   metric       h' = 2 k^2 eta / H^2 + 3 sum_i f_i delta_i          (eq. hprime)
+ *                eta' = 3 H / (2 k^2) sum_i f_i (1 + w_i) theta_i   (eq. etaprime)
+ *                with 8 pi G a^2 rho_i = 3 H^2 f_i, f_i = rho_i / rho_tot;
+ *   CDM          App. C.2;  baryons App. C.3;
+ *   photons      App. C.4, with two readings: the -(9/10) term of sigma_g'
+ *                multiplies sigma_g, and the polarization source is
+ *                (1/2)(1/(H tau_c)) Pi (delta_l0 + delta_l2 / 5), Pi = 2 sigma_g
+ *                + G_0 + G_2 (both follow from the Thomson collision term of
+ *                the cited Ma & Bertschinger hierarchy, which also gives the
+ *                (1/20)(G_0+G_2) of sigma_g');
+ *                truncation (l_max+1)/(H tau) uses conformal time tau;
+ *   neutrinos    App. C.5.
+ * No tight-coupling, ultra-relativistic-fluid or radiation-streaming switch
+ * (App. B.6).
+ *
+ * Initial conditions (not printed in the paper; the cited Ma & Bertschinger
+ * 1995 adiabatic growing mode at leading order in k tau, normalised to
+ * curvature R = 1, i.e. C = 1/2):
+ *   delta_g = delta_nu = -(2/3) C (k tau)^2,  delta_b = delta_c = 3/4 delta_g,
+ *   theta_g = theta_b = -C k^4 tau^3 / 18,
+ *   theta_nu = theta_g (23 + 4 R_nu) / (15 + 4 R_nu),
+ *   sigma_nu = 2 C (k tau)^2 / (3 (15 + 4 R_nu)),
+ *   eta = 2C - C (k tau)^2 (5 + 4 R_nu) / (6 (15 + 4 R_nu)), all others 0.
+ *
+ * Integrator: 3-stage Radau IIA collocation (order 5, L-stable).  The system
+ * is linear, dy/dx = A(x) y, so each step solves the 3N x 3N collocation
+ * system (I - h a_ij A(x_n + c_j h)) Y = (y_n, y_n, y_n) by dense LU; A(x) is
+ * built column by column from the right-hand side.  Steps follow a fixed
+ * schedule h <= step_c / (1 + k/H) (the fastest oscillation of the hierarchy
+ * has phase rate k/H per unit ln a) and land on every tau node; convergence
+ * of this schedule is pinned by a step-halving test.
+ *
+ * Sources (App. B.4, eq. source_functions) with
+ *   alpha = H (h' + 6 eta') / (2 k^2),
+ *   H alpha' = -2 H alpha + eta - (9/2) (H/k)^2 sum_i f_i (1 + w_i) sigma_i
+ * (the traceless Einstein equation of the cited formalism, not printed in
+ * the paper).  The switches group as: SW = g (delta_g/4 + H alpha');
+ * ISW = g (eta - H alpha' - 2 H alpha) + 2 H e^-kappa (eta' - H' alpha - H alpha')
+ * and all of S_T1; Doppler = the H [ ... ] bracket.  Stored per node:
+ * (S_T0, S_T1, S_P) with S_P = g Pi / 8 unscaled; scale_pol is applied to
+ * the temperature use of S_P in the projection and S_E = sqrt(6) S_P.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "orc.h"
+
+#define I_ETA 0
+#define I_DC 1
+#define I_DB 2
+#define I_TB 3
+#define I_G0 4
+
+static int i_pol(const orc_opts *o) { return I_G0 + o->lmax_g + 1; }
+static int i_nu(const orc_opts *o) { return i_pol(o) + o->lmax_pol + 1; }
+int orc_nstate(const orc_opts *o) { return i_nu(o) + o->lmax_nu + 1; }
+
+static void metric(const orc_opts *o, const orc_bg *b, double k, const double *y,
+                   double *hp, double *etap)
+{
+    const int P = i_pol(o), Nn = i_nu(o);
+    (void)P;
+    double kH = k / b->Hc;
+    *hp = 2.0 * kH * kH * y[I_ETA]
+        + 3.0 * (b->fc * y[I_DC] + b->fb * y[I_DB] + b->fg * y[I_G0] + b->fnu * y[Nn]);
+    *etap = 1.5 * b->Hc / (k * k)
+        * (b->fb * y[I_TB] + (4.0 / 3.0) * b->fg * y[I_G0 + 1] + (4.0 / 3.0) * b->fnu * y[Nn + 1]);
+    if (o->hooks & ORC_HOOK_FREEZE_METRIC) { *hp = 0.0; *etap = 0.0; }
+}
+
+/* free-streaming hierarchy part of one chain starting at y[s] (l = 0..L),
+   with first three entries (delta, theta, sigma); adds scattering -nu F_l
+   for l >= 3 (nu = 0 for neutrinos) */
+static void chain_tail(double kH, double Hc, double tau, double nu, int L,
+                       const double *yc, double *dyc)
+{
+    for (int l = 3; l <= L; l++) {
+        double Flm1 = (l == 3) ? 2.0 * yc[2] : yc[l - 1];
+        if (l < L)
+            dyc[l] = kH / (2.0 * l + 1.0) * (l * Flm1 - (l + 1.0) * yc[l + 1]) - nu * yc[l];
+        else
+            dyc[l] = kH * Flm1 - (L + 1.0) / (Hc * tau) * yc[l] - nu * yc[l];
+    }
+}
+
+void orc_rhs_bg(const orc_opts *o, const orc_bg *b, double k, const double *y, double *dy)
+{
+    const int P = i_pol(o), Nn = i_nu(o);
+    const int Lg = o->lmax_g, Lp = o->lmax_pol, Ln = o->lmax_nu;
+    double hp, etap;
+    metric(o, b, k, y, &hp, &etap);
+    double Hc = b->Hc, kH = k / Hc;
+    double nu = (o->hooks & ORC_HOOK_NO_THOMSON) ? 0.0 : b->nuT;
+
+    dy[I_ETA] = etap;
+    dy[I_DC] = -0.5 * hp;
+    dy[I_DB] = -y[I_TB] / Hc - 0.5 * hp;
+    dy[I_TB] = -y[I_TB] + b->cs2 * k * k * y[I_DB] / Hc + b->Rinv * nu * (y[I_G0 + 1] - y[I_TB]);
+
+    /* photon temperature */
+    const double *F = y + I_G0;
+    double *dF = dy + I_G0;
+    const double *G = y + P;
+    double *dG = dy + P;
+    dF[0] = -(4.0 / 3.0) * F[1] / Hc - (2.0 / 3.0) * hp;
+    dF[1] = k * k / Hc * (0.25 * F[0] - F[2]) + nu * (y[I_TB] - F[1]);
+    dF[2] = (4.0 / 15.0) * F[1] / Hc - 0.3 * kH * F[3] + (2.0 / 15.0) * hp + 0.8 * etap
+          - 0.9 * nu * F[2] + 0.05 * nu * (G[0] + G[2]);
+    chain_tail(kH, Hc, b->tau, nu, Lg, F, dF);
+
+    /* photon polarization */
+    double Pi = 2.0 * F[2] + G[0] + G[2];
+    for (int l = 0; l <= Lp; l++) {
+        double Glm1 = l > 0 ? G[l - 1] : 0.0;
+        if (l < Lp)
+            dG[l] = kH / (2.0 * l + 1.0) * (l * Glm1 - (l + 1.0) * G[l + 1]) - nu * G[l];
+        else
+            dG[l] = kH * Glm1 - (Lp + 1.0) / (Hc * b->tau) * G[l] - nu * G[l];
+        if (l == 0) dG[l] += 0.5 * nu * Pi;
+        if (l == 2) dG[l] += 0.1 * nu * Pi;
+    }
+
+    /* massless neutrinos */
+    const double *Fn = y + Nn;
+    double *dFn = dy + Nn;
+    dFn[0] = -(4.0 / 3.0) * Fn[1] / Hc - (2.0 / 3.0) * hp;
+    dFn[1] = k * k / Hc * (0.25 * Fn[0] - Fn[2]);
+    dFn[2] = (4.0 / 15.0) * Fn[1] / Hc - 0.3 * kH * Fn[3] + (2.0 / 15.0) * hp + 0.8 * etap;
+    chain_tail(kH, Hc, b->tau, 0.0, Ln, Fn, dFn);
+}
+
+void orc_rhs(const orc_cosmo *c, const orc_opts *o, double k, double lna,
+             const double *y, double *dy)
+{
+    orc_bg b;
+    orc_bg_eval(c, lna, &b, 1);
+    orc_rhs_bg(o, &b, k, y, dy);
+}
+
+void orc_initial(const orc_cosmo *c, const orc_opts *o, double k, double lna_i, double *y)
+{
+    int N = orc_nstate(o), Nn = i_nu(o);
+    memset(y, 0, sizeof(double) * N);
+    double tau = orc_tau_of_lna(c, lna_i), C = 0.5, Rn = c->R_nu;
+    double kt = k * tau;
+    double dg = -(2.0 / 3.0) * C * kt * kt;
+    double tg = -C * k * kt * kt * kt / 18.0;
+    y[I_ETA] = 2.0 * C - C * kt * kt * (5.0 + 4.0 * Rn) / (6.0 * (15.0 + 4.0 * Rn));
+    y[I_DC] = 0.75 * dg;
+    y[I_DB] = 0.75 * dg;
+    y[I_TB] = tg;
+    y[I_G0] = dg;
+    y[I_G0 + 1] = tg;
+    y[Nn] = dg;
+    y[Nn + 1] = tg * (23.0 + 4.0 * Rn) / (15.0 + 4.0 * Rn);
+    y[Nn + 2] = 2.0 * C * kt * kt / (3.0 * (15.0 + 4.0 * Rn));
+}
+
+/* dense A(x): column j = rhs(e_j) */
+static void build_A(const orc_opts *o, const orc_bg *b, double k, int N, double *A, double *e, double *col)
+{
+    memset(e, 0, sizeof(double) * N);
+    for (int j = 0; j < N; j++) {
+        e[j] = 1.0;
+        orc_rhs_bg(o, b, k, e, col);
+        for (int i = 0; i < N; i++) A[i * N + j] = col[i];
+        e[j] = 0.0;
+    }
+}
+
+typedef struct {
+    int N;
+    double *M, *A, *rhs, *e, *col;
+    int *piv;
+} radau_ws;
+
+static void ws_alloc(radau_ws *w, int N)
+{
+    w->N = N;
+    w->M = (double *)malloc(sizeof(double) * 9 * N * N);
+    w->A = (double *)malloc(sizeof(double) * 3 * N * N);
+    w->rhs = (double *)malloc(sizeof(double) * 3 * N);
+    w->e = (double *)malloc(sizeof(double) * N);
+    w->col = (double *)malloc(sizeof(double) * N);
+    w->piv = (int *)malloc(sizeof(int) * 3 * N);
+}
+static void ws_free(radau_ws *w)
+{
+    free(w->M); free(w->A); free(w->rhs); free(w->e); free(w->col); free(w->piv);
+}
+
+void orc_radau_tableau(double *out12);
+
+static int radau_linear_step(const orc_cosmo *c, const orc_opts *o, double k,
+                             double x, double h, double *y, radau_ws *w)
+{
+    int N = w->N, M3 = 3 * N;
+    double t[12];
+    orc_radau_tableau(t);
+    for (int s = 0; s < 3; s++) {
+        orc_bg b;
+        orc_bg_eval(c, x + t[9 + s] * h, &b, 1);
+        build_A(o, &b, k, N, w->A + (size_t)s * N * N, w->e, w->col);
+    }
+    for (int si = 0; si < 3; si++)
+        for (int i = 0; i < N; i++) {
+            double *row = w->M + (size_t)(si * N + i) * M3;
+            for (int sj = 0; sj < 3; sj++) {
+                double coef = h * t[3 * si + sj];
+                const double *Aj = w->A + (size_t)sj * N * N + (size_t)i * N;
+                for (int j = 0; j < N; j++) row[sj * N + j] = -coef * Aj[j];
+            }
+            row[si * N + i] += 1.0;
+        }
+    if (orc_lu_factor(w->M, M3, w->piv)) return -1;
+    for (int s = 0; s < 3; s++) memcpy(w->rhs + s * N, y, sizeof(double) * N);
+    orc_lu_solve(w->M, M3, w->piv, w->rhs);
+    memcpy(y, w->rhs + 2 * N, sizeof(double) * N);
+    return 0;
+}
+
+static double hmax_at(const orc_cosmo *c, const orc_opts *o, double k, double lna)
+{
+    double h = o->step_c / (1.0 + k / orc_Hconf(c, lna));
+    return h < o->step_cap ? h : o->step_cap;
+}
+
+/* Integrate from (lna_init, y_init) -- or from the adiabatic initial
+   condition at a_i(k) when y_init is NULL -- through the ascending output
+   points, writing y at each into y_out[n_out][N]. */
+int orc_solve_mode(const orc_cosmo *c, const orc_opts *o, double k,
+                   const double *lna_out, int n_out, double *y_out,
+                   const double *y_init, double lna_init, long *n_steps)
+{
+    int N = orc_nstate(o);
+    double *y = (double *)malloc(sizeof(double) * N);
+    double x;
+    if (y_init) { memcpy(y, y_init, sizeof(double) * N); x = lna_init; }
+    else { x = orc_lna_start(c, k); orc_initial(c, o, k, x, y); }
+    radau_ws w;
+    ws_alloc(&w, N);
+    long steps = 0;
+    int rc = 0;
+    for (int n = 0; n < n_out && rc == 0; n++) {
+        double x1 = lna_out[n];
+        if (x1 > x) {
+            double h0 = hmax_at(c, o, k, x), h1 = hmax_at(c, o, k, x1);
+            double hm = h0 < h1 ? h0 : h1;
+            int m = (int)ceil((x1 - x) / hm);
+            if (m < 1) m = 1;
+            double h = (x1 - x) / m;
+            for (int s = 0; s < m && rc == 0; s++) {
+                double xs = x + s * h;
+                double hs = (s == m - 1) ? (x1 - xs) : h;
+                rc = radau_linear_step(c, o, k, xs, hs, y, &w);
+                steps++;
+            }
+            x = x1;
+        }
+        memcpy(y_out + (size_t)n * N, y, sizeof(double) * N);
+    }
+    ws_free(&w);
+    free(y);
+    if (n_steps) *n_steps = steps;
+    return rc;
+}
+
+static void sources_at(const orc_cosmo *c, const orc_opts *o, double k, double lna,
+                       const double *y, double *S, double *scratch)
+{
+    orc_bg b;
+    orc_bg_eval(c, lna, &b, 2);
+    const int Nn = i_nu(o), P = i_pol(o);
+    double hp, etap;
+    metric(o, &b, k, y, &hp, &etap);
+    double *dy = scratch;
+    orc_rhs_bg(o, &b, k, y, dy);
+    double Hc = b.Hc, k2 = k * k;
+    double alpha = Hc * (hp + 6.0 * etap) / (2.0 * k2);
+    double shear = (4.0 / 3.0) * (b.fg * y[I_G0 + 2] + b.fnu * y[Nn + 2]);
+    double Ha_p = -2.0 * Hc * alpha + y[I_ETA] - 4.5 * Hc * Hc / k2 * shear; /* H alpha' */
+    double alpha_p = Ha_p / Hc;
+    double thb = y[I_TB], thb_p = dy[I_TB];
+    double eta = y[I_ETA];
+    double sw = b.g * (0.25 * y[I_G0] + Ha_p);
+    double isw = b.g * (eta - Ha_p - 2.0 * Hc * alpha)
+               + 2.0 * Hc * b.expmk * (etap - b.dHc * alpha - Ha_p);
+    double dop = Hc * (b.g * (thb_p / k2 + alpha_p) + b.dg * (thb / k2 + alpha));
+    S[0] = o->scale_sw * sw + o->scale_isw * isw + o->scale_dop * dop;
+    S[1] = o->scale_isw * b.expmk * k * (Ha_p + 2.0 * Hc * alpha - eta);
+    S[2] = b.g * (2.0 * y[I_G0 + 2] + y[P] + y[P + 2]) / 8.0;
+}
+
+int orc_sources_mode(const orc_cosmo *c, const orc_opts *o, double k, double *S, long *n_steps)
+{
+    int N = orc_nstate(o), nt = c->n_tau;
+    double *Y = (double *)malloc(sizeof(double) * (size_t)nt * N);
+    double *scratch = (double *)malloc(sizeof(double) * N);
+    int rc = orc_solve_mode(c, o, k, c->node_lna, nt, Y, NULL, 0.0, n_steps);
+    for (int i = 0; i < nt && rc == 0; i++)
+        sources_at(c, o, k, c->node_lna[i], Y + (size_t)i * N, S + 3 * i, scratch);
+    free(Y);
+    free(scratch);
+    return rc;
+}

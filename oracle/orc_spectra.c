@@ -1,0 +1,366 @@
+/*
+ * ORACLE (test infrastructure only; see orc.h).
+ *
+ * Spherical Bessel functions, line-of-sight projection and C_ell, plus the
+ * flat C entry points the Python test wrapper calls.
+ *
+ * j_l(x), exact to rounding (the paper's tabulated/Debye scheme of App. B.4 is
+ * an approximation of this): for x > l_max, upward recurrence from
+ * j_0 = sin x / x, j_1 = sin x / x^2 - cos x / x (stable while l < x); else
+ * Miller's downward recurrence started where j_l is below 1e-40 of its peak
+ * and normalised to j_0 (or j_1 near a zero of j_0), with series for j_1 at
+ * small x.  Derivatives from the recurrence and the Bessel equation:
+ *   j_l' = j_{l-1} - (l+1) j_l / x,
+ *   j_l'' = -(2/x) j_l' - (1 - l(l+1)/x^2) j_l.
+ *
+ * Projection (App. B.4): Delta_T = sum_i w_i [S_T0 j + S_T1 j' +
+ * scale_pol S_P (3 j'' + j)/2], Delta_E = sum_i w_i sqrt(6) S_P
+ * sqrt(3 (l+2)! / (8 (l-2)!)) j / x^2, x = k (tau_0 - tau_i), w_i the
+ * trapezoid weights in tau; sums compensated (Neumaier).
+ *
+ * C_ell (eq. c_ell_def, eq. PK_pivot): 4 pi sum_k w_k A_s (k/k_pivot)^(n_s-1)
+ * Delta_X Delta_Y, w_k the trapezoid weights in ln k; C_ell, not D_ell.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#include "orc.h"
+
+#define S_PI 3.14159265358979323846
+
+static double j1_of(double x)
+{
+    if (x < 0.5) { /* Taylor series; term ratio -x^2 / ((2n+2)(2n+5)) */
+        double x2 = x * x;
+        return x / 3.0 * (1.0 - x2 / 10.0 * (1.0 - x2 / 28.0 * (1.0 - x2 / 54.0 * (1.0 - x2 / 88.0 * (1.0 - x2 / 130.0 * (1.0 - x2 / 180.0))))));
+    }
+    return sin(x) / (x * x) - cos(x) / x;
+}
+
+static double j0_of(double x)
+{
+    if (x < 1e-4) return 1.0 - x * x / 6.0;
+    return sin(x) / x;
+}
+
+void orc_bessel_all(int lmax, double x, double *j)
+{
+    memset(j, 0, sizeof(double) * (lmax + 1));
+    if (x == 0.0) { j[0] = 1.0; return; }
+    double j0 = j0_of(x), j1 = j1_of(x);
+    if (x > lmax) {
+        j[0] = j0;
+        if (lmax >= 1) j[1] = j1;
+        for (int l = 1; l < lmax; l++) j[l + 1] = (2.0 * l + 1.0) / x * j[l] - j[l - 1];
+        return;
+    }
+    int ls = (int)ceil(x + 20.0 + 15.0 * cbrt(x));
+    int lcap = lmax + 30 + (int)sqrt(40.0 * lmax);
+    if (ls > lcap) ls = lcap;
+    double jp = 0.0, jc = 1e-250;
+    for (int l = ls; l >= 1; l--) {
+        /* jc = j_l (unnormalised), jp = j_{l+1} */
+        if (l <= lmax) j[l] = jc;
+        double jm = (2.0 * l + 1.0) / x * jc - jp;
+        jp = jc;
+        jc = jm;
+        if (fabs(jc) > 1e200) {
+            jc *= 1e-200; jp *= 1e-200;
+            int top = ls < lmax ? ls : lmax;
+            for (int m = l; m <= top; m++) j[m] *= 1e-200;
+        }
+    }
+    j[0] = jc;
+    double scale = (fabs(j0) >= fabs(j1)) ? j0 / j[0] : j1 / j[1];
+    for (int l = 0; l <= lmax; l++) j[l] *= scale;
+}
+
+/* ------------------------------------------------------------------ */
+static void neumaier_add(double *sum, double *comp, double v)
+{
+    double t = *sum + v;
+    if (fabs(*sum) >= fabs(v)) *comp += (*sum - t) + v;
+    else *comp += (v - t) + *sum;
+    *sum = t;
+}
+
+/* Project one k mode: S [n_tau][3] -> Delta [lmax-1][2] (l = 2..lmax). */
+static void project_mode(int n_tau, const double *tau, const double *w, double tau0,
+                         double k, const double *S, int lmax, double scale_pol,
+                         double *Delta, double *jbuf, double *acc)
+{
+    int nl = lmax - 1;
+    memset(acc, 0, sizeof(double) * 4 * nl);
+    for (int i = 0; i < n_tau; i++) {
+        double x = k * (tau0 - tau[i]);
+        orc_bessel_all(lmax, x, jbuf);
+        double s0 = S[3 * i], s1 = S[3 * i + 1], sp = S[3 * i + 2];
+        for (int l = 2; l <= lmax; l++) {
+            double jl = jbuf[l];
+            double jp = jbuf[l - 1] - (l + 1.0) * jl / x;
+            double jpp = -2.0 / x * jp - (1.0 - l * (l + 1.0) / (x * x)) * jl;
+            double dT = w[i] * (s0 * jl + s1 * jp + scale_pol * sp * 0.5 * (3.0 * jpp + jl));
+            double cE = sqrt(3.0 * (l + 2.0) * (l + 1.0) * l * (l - 1.0) / 8.0);
+            double dE = w[i] * sqrt(6.0) * sp * cE * jl / (x * x);
+            int q = l - 2;
+            neumaier_add(&acc[4 * q], &acc[4 * q + 1], dT);
+            neumaier_add(&acc[4 * q + 2], &acc[4 * q + 3], dE);
+        }
+    }
+    for (int q = 0; q < nl; q++) {
+        Delta[2 * q] = acc[4 * q] + acc[4 * q + 1];
+        Delta[2 * q + 1] = acc[4 * q + 2] + acc[4 * q + 3];
+    }
+}
+
+static void opts_from(const double *oa, orc_opts *o)
+{
+    o->lmax_g = (int)oa[0]; o->lmax_pol = (int)oa[1]; o->lmax_nu = (int)oa[2];
+    o->scale_sw = oa[3]; o->scale_isw = oa[4]; o->scale_dop = oa[5]; o->scale_pol = oa[6];
+    o->step_c = oa[7]; o->step_cap = oa[8]; o->hooks = (int)oa[9];
+}
+
+static void set_threads(int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+}
+
+/* ---------------- C entry points for the Python test wrapper ---------------- */
+
+/* Scalars: [H0, Om_b, Om_c, Om_g, Om_nu, Om_L, R_nu, f_He, nH0, A_s, z_reion,
+             lna_tc, lna_sw, tau0, lna_He3, n_s] */
+int orc_scalars(const double *p, int hooks, double *out)
+{
+    orc_cosmo c;
+    if (orc_cosmo_init(&c, p, 0, hooks)) return -1;
+    double v[16] = {c.H0, c.Om_b, c.Om_c, c.Om_g, c.Om_nu, c.Om_L, c.R_nu, c.f_He,
+                    c.nH0, c.A_s, c.z_reion, c.lna_tc, c.lna_sw, c.tau0, c.lna_He3, c.n_s};
+    memcpy(out, v, sizeof(v));
+    orc_cosmo_free(&c);
+    return 0;
+}
+
+/* Background at points: out[n][16] = [a, Hc, dHc, fc, fb, fg, fnu, tau, xe,
+   dxe, nuT, Rinv, cs2, kappa, g, dg] */
+int orc_background(const double *p, int hooks, const double *lna, int n, double *out)
+{
+    orc_cosmo c;
+    if (orc_cosmo_init(&c, p, 0, hooks)) return -1;
+    for (int i = 0; i < n; i++) {
+        orc_bg b;
+        orc_bg_eval(&c, lna[i], &b, 2);
+        double v[16] = {b.a, b.Hc, b.dHc, b.fc, b.fb, b.fg, b.fnu, b.tau, b.xe, b.dxe,
+                        b.nuT, b.Rinv, b.cs2, b.kappa, b.g, b.dg};
+        memcpy(out + 16 * i, v, sizeof(v));
+    }
+    orc_cosmo_free(&c);
+    return 0;
+}
+
+/* tau nodes: out[3][n_tau] = lna, tau, w */
+int orc_nodes(const double *p, int n_tau, double *out)
+{
+    orc_cosmo c;
+    if (orc_cosmo_init(&c, p, n_tau, 0)) return -1;
+    memcpy(out, c.node_lna, sizeof(double) * n_tau);
+    memcpy(out + n_tau, c.node_tau, sizeof(double) * n_tau);
+    memcpy(out + 2 * n_tau, c.node_w, sizeof(double) * n_tau);
+    orc_cosmo_free(&c);
+    return 0;
+}
+
+int orc_nstate_of(const double *oa)
+{
+    orc_opts o;
+    opts_from(oa, &o);
+    return orc_nstate(&o);
+}
+
+double orc_lna_start_of(const double *p, double k)
+{
+    orc_cosmo c;
+    if (orc_cosmo_init(&c, p, 0, 0)) return NAN;
+    double v = orc_lna_start(&c, k);
+    orc_cosmo_free(&c);
+    return v;
+}
+
+/* Trajectory of one mode at ascending ln a points (y_init may be NULL). */
+int orc_trajectory(const double *p, const double *oa, double k, const double *lna_out,
+                   int n, double *y_out, const double *y_init, double lna_init, long *steps)
+{
+    orc_cosmo c;
+    orc_opts o;
+    opts_from(oa, &o);
+    if (orc_cosmo_init(&c, p, 0, o.hooks & ORC_HOOK_EDS_CDM)) return -1;
+    int rc = orc_solve_mode(&c, &o, k, lna_out, n, y_out, y_init, lna_init, steps);
+    orc_cosmo_free(&c);
+    return rc;
+}
+
+/* Right-hand side at one point (for consistency pins). */
+int orc_rhs_at(const double *p, const double *oa, double k, double lna, const double *y, double *dy)
+{
+    orc_cosmo c;
+    orc_opts o;
+    opts_from(oa, &o);
+    if (orc_cosmo_init(&c, p, 0, o.hooks & ORC_HOOK_EDS_CDM)) return -1;
+    orc_rhs(&c, &o, k, lna, y, dy);
+    orc_cosmo_free(&c);
+    return 0;
+}
+
+void orc_bessel(int lmax, double x, double *out) { orc_bessel_all(lmax, x, out); }
+
+/* Project given sources (synthetic ones in the pins) on given nodes. */
+int orc_project(int n_tau, const double *tau, const double *w, double tau0,
+                const double *k, int nk, const double *S, int lmax, double scale_pol,
+                double *Delta, int nthreads)
+{
+    set_threads(nthreads);
+    int nl = lmax - 1;
+#pragma omp parallel
+    {
+        double *jbuf = (double *)malloc(sizeof(double) * (lmax + 1));
+        double *acc = (double *)malloc(sizeof(double) * 4 * nl);
+#pragma omp for schedule(dynamic, 1)
+        for (int ik = 0; ik < nk; ik++)
+            project_mode(n_tau, tau, w, tau0, k[ik], S + (size_t)ik * n_tau * 3, lmax,
+                         scale_pol, Delta + (size_t)ik * nl * 2, jbuf, acc);
+        free(jbuf);
+        free(acc);
+    }
+    return 0;
+}
+
+/* C_ell from Delta[nk][lmax-1][2]: Cl[3][lmax-1] = TT, TE, EE */
+int orc_cl(const double *k, int nk, const double *Delta, int lmax, double A_s, double n_s,
+           double k_pivot, double *Cl)
+{
+    int nl = lmax - 1;
+    double *wk = (double *)malloc(sizeof(double) * nk);
+    for (int i = 0; i < nk; i++) {
+        double lo = i > 0 ? log(k[i - 1]) : log(k[i]);
+        double hi = i < nk - 1 ? log(k[i + 1]) : log(k[i]);
+        wk[i] = 0.5 * (hi - lo);
+    }
+    for (int q = 0; q < nl; q++) {
+        double s[3] = {0, 0, 0}, cmp[3] = {0, 0, 0};
+        for (int i = 0; i < nk; i++) {
+            double P = A_s * pow(k[i] / k_pivot, n_s - 1.0);
+            double dT = Delta[((size_t)i * nl + q) * 2], dE = Delta[((size_t)i * nl + q) * 2 + 1];
+            double f = 4.0 * S_PI * wk[i] * P;
+            neumaier_add(&s[0], &cmp[0], f * dT * dT);
+            neumaier_add(&s[1], &cmp[1], f * dT * dE);
+            neumaier_add(&s[2], &cmp[2], f * dE * dE);
+        }
+        for (int t = 0; t < 3; t++) Cl[t * nl + q] = s[t] + cmp[t];
+    }
+    free(wk);
+    return 0;
+}
+
+/* Whole path for one cosmology. Any output pointer may be NULL.
+   S_out [nk][n_tau][3], Delta_out [nk][lmax-1][2], Cl_out [3][lmax-1],
+   steps_out [nk]. */
+int orc_run(const double *p, int n_tau, const double *oa, const double *k, int nk,
+            int lmax_cl, double *S_out, double *Delta_out, double *Cl_out,
+            long *steps_out, int nthreads)
+{
+    orc_cosmo c;
+    orc_opts o;
+    opts_from(oa, &o);
+    if (orc_cosmo_init(&c, p, n_tau, o.hooks & ORC_HOOK_EDS_CDM)) return -1;
+    set_threads(nthreads);
+    double *S = S_out ? S_out : (double *)malloc(sizeof(double) * (size_t)nk * n_tau * 3);
+    int rc = 0;
+    /* highest k first: the most expensive modes start earliest */
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : rc)
+    for (int t = 0; t < nk; t++) {
+        int ik = nk - 1 - t;
+        long st = 0;
+        rc |= orc_sources_mode(&c, &o, k[ik], S + (size_t)ik * n_tau * 3, &st);
+        if (steps_out) steps_out[ik] = st;
+    }
+    if (rc == 0 && (Delta_out || Cl_out)) {
+        int nl = lmax_cl - 1;
+        double *D = Delta_out ? Delta_out : (double *)malloc(sizeof(double) * (size_t)nk * nl * 2);
+        orc_project(n_tau, c.node_tau, c.node_w, c.tau0, k, nk, S, lmax_cl, o.scale_pol, D, nthreads);
+        if (Cl_out) orc_cl(k, nk, D, lmax_cl, c.A_s, c.n_s, c.k_pivot, Cl_out);
+        if (!Delta_out) free(D);
+    }
+    if (!S_out) free(S);
+    orc_cosmo_free(&c);
+    return rc;
+}
+
+/* Handle-based access for tests that call the right-hand side many times. */
+void *orc_create(const double *p, int n_tau, int hooks)
+{
+    orc_cosmo *c = (orc_cosmo *)malloc(sizeof(orc_cosmo));
+    if (orc_cosmo_init(c, p, n_tau, hooks)) { orc_cosmo_free(c); free(c); return NULL; }
+    return c;
+}
+
+void orc_destroy(void *h)
+{
+    if (h) { orc_cosmo_free((orc_cosmo *)h); free(h); }
+}
+
+int orc_h_rhs(void *h, const double *oa, double k, double lna, const double *y, double *dy)
+{
+    orc_opts o;
+    opts_from(oa, &o);
+    orc_rhs((orc_cosmo *)h, &o, k, lna, y, dy);
+    return 0;
+}
+
+/* dense A(ln a) [N][N] */
+int orc_h_matrix(void *h, const double *oa, double k, double lna, double *A)
+{
+    orc_opts o;
+    opts_from(oa, &o);
+    int N = orc_nstate(&o);
+    orc_bg b;
+    orc_bg_eval((orc_cosmo *)h, lna, &b, 1);
+    double *e = (double *)calloc(N, sizeof(double)), *col = (double *)malloc(sizeof(double) * N);
+    for (int j = 0; j < N; j++) {
+        e[j] = 1.0;
+        orc_rhs_bg(&o, &b, k, e, col);
+        for (int i = 0; i < N; i++) A[i * N + j] = col[i];
+        e[j] = 0.0;
+    }
+    free(e);
+    free(col);
+    return 0;
+}
+
+/* LU solve of a dense system (pins the factorisation against a library solve) */
+int orc_dense_solve(double *A, int n, double *b)
+{
+    int *piv = (int *)malloc(sizeof(int) * n);
+    int rc = orc_lu_factor(A, n, piv);
+    if (!rc) orc_lu_solve(A, n, piv, b);
+    free(piv);
+    return rc;
+}
+
+/* Adiabatic initial state of the oracle at a given ln a. */
+int orc_initial_at(const double *p, const double *oa, double k, double lna, double *y)
+{
+    orc_cosmo c;
+    orc_opts o;
+    opts_from(oa, &o);
+    if (orc_cosmo_init(&c, p, 0, 0)) return -1;
+    orc_initial(&c, &o, k, lna, y);
+    orc_cosmo_free(&c);
+    return 0;
+}
