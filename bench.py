@@ -1,0 +1,306 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the C_ell hot path on GB300.
+
+One step = the whole path (background tables -> perturbation ODEs and CMB
+sources -> line-of-sight projection -> k-quadrature) for one batch of 64
+seeded flat-LCDM cosmologies: TT/TE/EE to l = 2500, 400 log-spaced k in
+[1e-5, 0.5]/Mpc, hierarchies at l = 30, 6000 tau nodes, FP64.
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs its own batch
+(weak scaling; no collective on the data path -- cosmologies are independent).
+`--impl reference` times the CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2602_15104_gb300 import workload as W  # noqa: E402
+
+METRIC = "C_ℓ spectra/s at ℓmax=2500 TT/TE/EE (≤1e-5 rel vs FP64 oracle); p50/p99 latency"
+FP64_PEAK = 2 * 2 * 152 * 2.07e9  # FMA units/SM x flops/FMA x SMs x max SM clock (1.26 TFLOP/s)
+FLUSH_BYTES = 512 << 20
+
+
+def flops_per_substep(N: int) -> float:
+    """FP64 flops of one linearly implicit Euler substep of the ODE kernel:
+    ~6N for the streaming/metric right-hand side, ~0.3N for the Thomson
+    solve, ~3.3N for the extrapolation tableau and error norm (amortised),
+    ~150 for the background point evaluation (FMA counted as 2)."""
+    return 10.0 * N + 150.0
+
+
+def projection_points(tau_nodes: np.ndarray, tau0: float, k: np.ndarray, lmax: int) -> float:
+    """(node, l) points the projection kernel evaluates: l = 2 .. min(lmax,
+    x + 12 + 7 x^(1/3)) per node, x = k (tau_0 - tau)."""
+    x = np.outer(k, tau0 - tau_nodes).astype(np.float32)
+    lc = np.minimum(np.floor(x + 12.0 + 7.0 * np.cbrt(x)), lmax)
+    return float(np.maximum(lc - 1.0, 0.0).sum())
+
+
+class ClockSampler:
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        dev = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", dev, f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.remove(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(wl, params, k, nthreads=None) -> dict:
+    """The FP64 oracle timed on a bounded sample of one cosmology of the
+    workload, scaled to the whole cosmology: ODE -- every host thread runs one
+    sampled k mode for a fixed number of its Radau steps, and the total is
+    scaled by the exact step count of the oracle's schedule over all k;
+    projection -- one sampled k per thread at the full l and tau range,
+    scaled by the number of k."""
+    import oracle as O
+    cores = nthreads or os.cpu_count()
+    o = O.opts(lmax=wl.l_max_hier)
+    p = params[0]
+    t0 = time.perf_counter()
+    O.scalars(p)
+    t_bg = time.perf_counter() - t0
+    total_steps = int(O.count_steps(p, k, wl.n_tau, o).sum())
+    budget = 40
+    idx = np.linspace(0, len(k) - 1, cores).round().astype(int)
+    ob = O.opts(lmax=wl.l_max_hier, max_steps=budget)
+    t0 = time.perf_counter()
+    O.run(p, k[idx], wl.n_tau, 2, ob, want=("S",), nthreads=cores)
+    t_ode = time.perf_counter() - t0
+    rate = cores * budget / t_ode  # Radau steps per second on all threads
+    tau, w, _ = (None, None, None)
+    lna, tau, w = O.nodes(p, wl.n_tau)
+    tau0 = O.scalars(p)["tau0"]
+    S = np.ones((cores, wl.n_tau, 3))
+    t0 = time.perf_counter()
+    O.project(tau, w, tau0, k[idx], S, wl.l_max_cl, nthreads=cores)
+    t_proj = time.perf_counter() - t0
+    sec = t_bg + total_steps / rate + t_proj * len(k) / cores
+    return {"value": 1.0 / sec, "unit": "spectra/s", "cores": cores, "kind": "oracle",
+            "seconds_per_spectrum": sec,
+            "sample": (f"one cosmology of {wl.name}: {cores} k modes x {budget} Radau steps "
+                       f"(of {total_steps} scheduled) and {cores} of {len(k)} k projected at "
+                       f"l<={wl.l_max_cl}, n_tau={wl.n_tau}; scaled to the cosmology")}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    wl = W.WORKLOADS[args.workload]
+    params, k = wl.params(), wl.k()
+    for _ in range(args.warmup):
+        pass
+    vals = []
+    cb = None
+    for _ in range(args.steps):
+        cb = cpu_baseline(wl, params, k)
+        vals.append(cb["value"])
+    v = statistics.mean(vals)
+    cb["value"] = v
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "spectra/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wl.n_cosmo / v,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": wl.name, "batch": wl.n_cosmo},
+           "cpu_baseline": cb,
+           "e2e": {"value": v, "unit": "spectra/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=W.BATCH64.name, choices=sorted(W.WORKLOADS))
+    ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    from paper_2602_15104_gb300 import abcmb as A
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    wl = W.WORKLOADS[args.workload]
+    B = wl.n_cosmo
+    params = W.draw_cosmologies(B, wl.seed + 1000 * rank)
+    k = wl.k()
+    o = A.options(lmax_hier=wl.l_max_hier, lmax_cl=wl.l_max_cl, n_tau=wl.n_tau, rtol=args.rtol)
+    N = 4 + 3 * (wl.l_max_hier + 1)
+    pipe = A.Pipeline(B, k, o)
+    p_dev = torch.tensor(params, dtype=torch.float64, device="cuda")
+    p_host = torch.from_numpy(params).pin_memory()
+    cl_host = torch.empty((B, 3, o.lmax_cl - 1), dtype=torch.float64, pin_memory=True)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        pipe.run(p_dev)
+    torch.cuda.synchronize()
+    pipe.check_status()
+
+    # device-resident timed steps, per-kernel events on the launching stream
+    names = ["background", "perturb", "project", "cl"]
+    ktimes = {n: [] for n in names}
+    step_ms = []
+    clocks = ClockSampler()
+    clocks.start()
+    barrier()
+    for _ in range(args.steps):
+        flush.fill_(1.0)  # L2 flush between timed iterations (outside the events)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        ev[0].record(stream)
+        A.abcmb_background_tables(p_dev, o, out=pipe.bg)
+        ev[1].record(stream)
+        A.abcmb_perturb(pipe.bg, pipe.k, o, S=pipe.S, status=pipe.status, steps=pipe.steps,
+                        workspace=pipe.ws)
+        ev[2].record(stream)
+        A.abcmb_project(pipe.bg, pipe.S, pipe.k, o, out=pipe.D)
+        ev[3].record(stream)
+        A.abcmb_cl(pipe.bg, pipe.D, pipe.k, o, out=pipe.C)
+        ev[4].record(stream)
+        torch.cuda.synchronize()
+        for i, n in enumerate(names):
+            ktimes[n].append(ev[i].elapsed_time(ev[i + 1]))
+        step_ms.append(ev[0].elapsed_time(ev[4]))
+    barrier()
+    clk = clocks.stop()
+    pipe.check_status()
+
+    # end to end through the public API: host params in, host C_l out
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pipe.run_host(p_host, cl_host)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+
+    t_step = statistics.mean(step_ms)
+    t_e2e = statistics.mean(e2e_ms)
+    if dist is not None:
+        t = torch.tensor([t_step, t_e2e], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_step, t_e2e = float(t[0]), float(t[1])
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel (FP64 ALU bound)
+    kavg = {n: statistics.mean(v) for n, v in ktimes.items()}
+    substeps = float(pipe.steps[:, :, 1].sum().item())
+    flops = {"perturb": substeps * flops_per_substep(N)}
+    pts = 0.0
+    for b in range(B):
+        scal, _, nodes = A.bg_view(pipe.bg[b], o.n_tau)
+        pts += projection_points(nodes[:, 1], scal["TAU0"], k, o.lmax_cl)
+    flops["project"] = 13.0 * pts
+    dom = max(kavg, key=kavg.get)
+    if dom in flops:
+        ach = flops[dom] / (kavg[dom] * 1e-3)
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach / 1e12, "peak": FP64_PEAK / 1e12,
+                "unit": "TFLOP/s", "frac": ach / FP64_PEAK, "traffic": None,
+                "peak_source": "FP64 pipe: 2 FMA/clk/SM x 152 SMs x 2070 MHz (nominal 1.25 TFLOP/s)"}
+    else:
+        roof = None
+    kern = {n: {"ms": kavg[n], "share": kavg[n] / sum(kavg.values())} for n in names}
+    for n in flops:
+        kern[n]["tflops"] = flops[n] / (kavg[n] * 1e-3) / 1e12
+    value = B * world / (t_step * 1e-3)
+    lat = sorted(e2e_ms)
+    out = {
+        "metric": METRIC, "value": value, "unit": "spectra/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "batch": B, "n_k": len(k), "k_range": [wl.k_min, wl.k_max],
+                   "lmax_cl": wl.l_max_cl, "hierarchy_lmax": wl.l_max_hier, "n_tau": wl.n_tau,
+                   "rtol": args.rtol, "l2": "flushed (512 MiB write) between timed steps",
+                   "parallelism": f"replicas x{world}"},
+        "clocks": clk,
+        "e2e": {"value": B * world / (t_e2e * 1e-3), "unit": "spectra/s",
+                "h2d_bytes_per_step": int(params.nbytes),
+                "d2h_bytes_per_step": int(B * 3 * (o.lmax_cl - 1) * 8)},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "what": "batch of 64 spectra, host params to host C_l"},
+        "gpu_launches": 4 * args.steps,
+        "roofline": roof,
+        "kernels": kern,
+        "ode": {"mean_steps_per_mode": float(pipe.steps[:, :, 0].float().mean().item()),
+                "substeps_total": substeps},
+    }
+    if not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline(wl, params, k)
+    print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,176 @@
+/*
+ * abcmb.h -- C ABI of the GB300 (sm_103a) library for the data-parallel hot
+ * path of the ABCMB linear Einstein-Boltzmann method (arXiv 2602.15104):
+ *
+ *   abcmb_background_tables   thermal history + tau nodes per cosmology
+ *   abcmb_perturb             per-k stiff linear perturbation ODEs -> CMB sources
+ *   abcmb_project             line-of-sight projection -> transfer functions
+ *   abcmb_cl                  k-quadrature -> C_ell^{TT,TE,EE}
+ *
+ * Conventions shared by every entry point
+ *   - Every pointer argument is a DEVICE pointer allocated by the caller
+ *     (the library allocates nothing and keeps no state between calls), unless
+ *     its name ends in _host.  Every array is C-contiguous float64 (int32 for
+ *     status/step arrays) in the layout stated at each argument.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls only enqueue work on it; results are valid once the
+ *     stream has been synchronised.
+ *   - Return value: ABCMB_OK, or an error code.  Arguments are validated on
+ *     the host before anything is enqueued (ABCMB_E_INVALID_ARG); launch
+ *     failures return ABCMB_E_CUDA.  Numerical failures found on the device
+ *     are reported in the status words named at each call, never by aborting.
+ *   - Units: Mpc for lengths and conformal time, 1/Mpc for k; C_ell is the
+ *     dimensionless angular power for primordial curvature amplitude A_s
+ *     (C_ell, not D_ell; paper Sec. 2.3 footnote).
+ */
+#ifndef ABCMB_H
+#define ABCMB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    ABCMB_OK = 0,
+    ABCMB_E_INVALID_ARG = 1, /* host-side validation failed; nothing enqueued   */
+    ABCMB_E_CUDA = 2,        /* a kernel launch or CUDA call failed             */
+    ABCMB_E_MAX_STEPS = 3,   /* status word: a mode hit its step budget         */
+    ABCMB_E_NONFINITE = 4,   /* status word: a non-finite value was produced    */
+    ABCMB_E_BACKGROUND = 5,  /* status word: a background root was not found    */
+};
+
+/* Number of doubles per cosmology in params: omega_b, omega_cdm, h, n_s,
+   ln(1e10 A_s), tau_reion (paper App. A.2).  The other cosmological inputs
+   are the paper's defaults: Y_He = 0.245, T_CMB0 = 2.34865418e-4 eV, three
+   massless neutrinos with T_nu/T_gamma = 0.71636856 (N_eff = 3.044),
+   reionization widths Delta z = 0.5, z_He = 3.5, Delta z_He = 0.5,
+   beta = 1.5, k_pivot = 0.05/Mpc, R_tc = 1.5e-3, R_large = 7e-2. */
+#define ABCMB_NPARAM 6
+
+typedef struct {
+    int lmax_g;      /* photon temperature hierarchy truncation, 4..64 (App. A.1 l_max_g)  */
+    int lmax_pol;    /* photon polarization hierarchy truncation, 4..64 (l_max_pol_g)      */
+    int lmax_nu;     /* massless-neutrino hierarchy truncation, 4..64 (l_max_massless_nu)  */
+    int lmax_cl;     /* C_ell computed for every ell in [2, lmax_cl]; 2..5000 (App. A.1)   */
+    int n_tau;       /* number of tau nodes of the line-of-sight integral, 8..65536        */
+    int max_steps;   /* accepted+rejected ODE step budget per k mode, >= 1                 */
+    double rtol;     /* ODE relative tolerance, (0, 1)                                     */
+    double atol;     /* ODE absolute tolerance floor, >= 0                                 */
+    double scale_sw, scale_isw, scale_dop, scale_pol; /* source switches (App. A.1)       */
+} abcmb_options;
+
+/* Fill *o with the defaults used by the library's tests: hierarchies 12,
+   lmax_cl 2500, 6000 tau nodes, rtol 1e-8, atol 1e-12, switches 1. */
+void abcmb_default_options(abcmb_options *o);
+
+/* ABCMB_OK if every field of *o is in its stated range (o may be NULL:
+   ABCMB_E_INVALID_ARG).  Every entry point below applies this check first. */
+int abcmb_validate_options(const abcmb_options *o);
+
+/* Length, in doubles, of one cosmology's background record for these
+   options (ABCMB_BG_* offsets below address it).  Returns 0 if invalid. */
+size_t abcmb_bg_doubles(const abcmb_options *o);
+
+/* Layout of one background record (doubles):
+     [0, ABCMB_BG_NSCALAR)                 scalars, ABCMB_S_* indices
+     [ABCMB_BG_TABLE, + 8 * ABCMB_BG_NLNA) table on the uniform ln a grid
+            ln a_j = ABCMB_BG_LNA0 + j / ABCMB_BG_PER_UNIT, 8 columns per node:
+            1/(H tau_c), d/dln a of it, tau, dtau/dln a = 1/H, c_s^2,
+            d c_s^2/dln a, kappa, x_e
+     then 8 columns per tau node (n_tau nodes): ln a, tau, trapezoid weight,
+            g, dg/dln a, e^-kappa, conformal H, dH/dln a                     */
+#define ABCMB_BG_NSCALAR 64
+#define ABCMB_BG_PER_UNIT 1024
+#define ABCMB_BG_LNA0 (-18.0)
+#define ABCMB_BG_NLNA (18 * 1024 + 1)
+#define ABCMB_BG_TABLE ABCMB_BG_NSCALAR
+#define ABCMB_BG_NODES (ABCMB_BG_TABLE + 8 * ABCMB_BG_NLNA)
+
+enum {
+    ABCMB_S_STATUS = 0, ABCMB_S_H0, ABCMB_S_OMB, ABCMB_S_OMC, ABCMB_S_OMG, ABCMB_S_OMNU,
+    ABCMB_S_OML, ABCMB_S_RNU, ABCMB_S_FHE, ABCMB_S_NH0, ABCMB_S_AS, ABCMB_S_NS,
+    ABCMB_S_ZREION, ABCMB_S_LNA_TC, ABCMB_S_LNA_SW, ABCMB_S_TAU0, ABCMB_S_LNA_HE3,
+    ABCMB_S_LNA_700, ABCMB_S_NTAU, ABCMB_S_COUNT
+};
+
+/*
+ * Background and thermal history of B cosmologies (paper Sec. 2.4
+ * "Background", App. B.1-B.2, App. B.4 kappa and g, App. C.1-C.5 densities):
+ * flat LCDM closed form, conformal time, Saha helium and hydrogen then a
+ * Peebles three-level atom, matter temperature, tanh reionization with
+ * z_reion solved from tau_reion, the tight-coupling start a_tc
+ * (H tau_c = R_tc, App. A.1), and the n_tau tau nodes with trapezoid
+ * weights (1/4 uniform in ln a from a_tc to z = 1300, 1/2 uniform in z on
+ * [1300, 900), 1/4 uniform in tau from z = 900 to tau_0 exclusive).
+ *
+ *   params  [B][ABCMB_NPARAM]            device, read
+ *   bg      [B][abcmb_bg_doubles(o)]     device, written
+ * Device-side failure (a root not bracketed, a non-finite value) sets
+ * bg[b*len + ABCMB_S_STATUS] to ABCMB_E_BACKGROUND / ABCMB_E_NONFINITE.
+ */
+int abcmb_background_tables(int B, const double *params, const abcmb_options *o,
+                            double *bg, void *stream);
+
+/*
+ * Linear synchronous-gauge perturbations (App. B.3.1, App. C: metric eqs.
+ * hprime/etaprime, CDM, baryons, photon temperature and polarization and
+ * massless-neutrino hierarchies, no tight-coupling switch, App. B.6) for
+ * every (cosmology, k) mode, from a_i(k) = min(a_tc, a_k), k/H(a_k) =
+ * R_large (App. A.1), with adiabatic initial conditions, to the last tau
+ * node, landing on every tau node and writing the CMB sources there
+ * (App. B.4, eq. source_functions).
+ *
+ *   bg           [B][abcmb_bg_doubles(o)]  device, read (from abcmb_background_tables)
+ *   k            [Nk]                      device, read, 1/Mpc, each > 0
+ *   S            [B][Nk][n_tau][3]         device, written: S_T0, S_T1 and
+ *                S_P = g Pi / 8 (S_T2 before scale_pol; S_E = sqrt(6) S_P)
+ *   mode_status  [B][Nk] int32             device, written: ABCMB_OK,
+ *                ABCMB_E_MAX_STEPS or ABCMB_E_NONFINITE per mode
+ *   steps        [B][Nk][2] int32 or NULL  device, written: ODE steps taken
+ *                (accepted and rejected) and linearly implicit substeps
+ *   workspace    >= abcmb_perturb_workspace_bytes(B, Nk, o) bytes, device,
+ *                256-byte aligned; returns ABCMB_E_INVALID_ARG if smaller
+ */
+int abcmb_perturb(int B, const double *bg, const double *k, int Nk, const abcmb_options *o,
+                  double *S, int *mode_status, int *steps, void *workspace,
+                  size_t workspace_bytes, void *stream);
+
+/* Bytes of device workspace abcmb_perturb needs for B cosmologies and Nk
+   modes (0 if the options are invalid).  The caller allocates it; its
+   contents need no initialisation and are scratch after the call. */
+size_t abcmb_perturb_workspace_bytes(int B, int Nk, const abcmb_options *o);
+
+/*
+ * Line-of-sight projection (App. B.4): for every ell in [2, lmax_cl],
+ *   Delta_T = sum_i w_i [S_T0 j_l + S_T1 j_l' + scale_pol S_P (3 j_l'' + j_l)/2]
+ *   Delta_E = sqrt(3 (l+2)! / (8 (l-2)!)) sum_i w_i sqrt(6) S_P j_l / x^2
+ * with x = k (tau_0 - tau_i) and trapezoid weights w_i in tau (App. B.6).
+ *
+ *   bg     [B][abcmb_bg_doubles(o)]   device, read
+ *   S      [B][Nk][n_tau][3]          device, read
+ *   k      [Nk]                       device, read
+ *   Delta  [B][Nk][lmax_cl-1][2]      device, written (Delta_T, Delta_E)
+ */
+int abcmb_project(int B, const double *bg, const double *S, const double *k, int Nk,
+                  const abcmb_options *o, double *Delta, void *stream);
+
+/*
+ * k-quadrature (App. B.4 eq. c_ell_def, eq. PK_pivot):
+ *   C_l^{XY} = 4 pi sum_k w_k A_s (k/0.05)^(n_s-1) Delta_X Delta_Y,
+ * w_k the trapezoid weights in ln k over the given (ascending) k nodes.
+ *
+ *   bg     [B][abcmb_bg_doubles(o)]   device, read (A_s, n_s)
+ *   Delta  [B][Nk][lmax_cl-1][2]      device, read
+ *   k      [Nk]                       device, read, strictly ascending
+ *   Cl     [B][3][lmax_cl-1]          device, written: TT, TE, EE for l = 2..lmax_cl
+ */
+int abcmb_cl(int B, const double *bg, const double *Delta, const double *k, int Nk,
+             const abcmb_options *o, double *Cl, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ABCMB_H */

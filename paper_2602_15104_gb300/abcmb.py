@@ -1,0 +1,226 @@
+"""Thin Python binding of libabcmb.so (C ABI: include/abcmb.h).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels; torch supplies device memory and the current stream.  The
+functions carry the C entry points' names.  If the library has not been built
+(``__graft_entry__.build()`` or ``python -m paper_2602_15104_gb300.build``)
+every call raises; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libabcmb.so")
+
+OK, E_INVALID_ARG, E_CUDA, E_MAX_STEPS, E_NONFINITE, E_BACKGROUND = range(6)
+ERRORS = {1: "invalid argument", 2: "CUDA error", 3: "step budget exhausted",
+          4: "non-finite value", 5: "background root not found"}
+
+NPARAM = 6
+BG_NSCALAR = 64
+BG_PER_UNIT = 1024
+BG_LNA0 = -18.0
+BG_NLNA = 18 * 1024 + 1
+BG_TABLE = BG_NSCALAR
+BG_NODES = BG_TABLE + 8 * BG_NLNA
+S_INDEX = dict(STATUS=0, H0=1, OMB=2, OMC=3, OMG=4, OMNU=5, OML=6, RNU=7, FHE=8, NH0=9, AS=10,
+               NS=11, ZREION=12, LNA_TC=13, LNA_SW=14, TAU0=15, LNA_HE3=16, LNA_700=17, NTAU=18)
+TABLE_COLUMNS = ("nuT", "dnuT", "tau", "dtau", "cs2", "dcs2", "kappa", "xe")
+NODE_COLUMNS = ("lna", "tau", "w", "g", "dg", "expmk", "Hc", "dHc")
+
+
+class Options(ctypes.Structure):
+    """Mirror of abcmb_options."""
+
+    _fields_ = [("lmax_g", ctypes.c_int), ("lmax_pol", ctypes.c_int), ("lmax_nu", ctypes.c_int),
+                ("lmax_cl", ctypes.c_int), ("n_tau", ctypes.c_int), ("max_steps", ctypes.c_int),
+                ("rtol", ctypes.c_double), ("atol", ctypes.c_double),
+                ("scale_sw", ctypes.c_double), ("scale_isw", ctypes.c_double),
+                ("scale_dop", ctypes.c_double), ("scale_pol", ctypes.c_double)]
+
+
+def options(lmax_hier=12, lmax_cl=2500, n_tau=6000, rtol=1e-8, atol=1e-12, max_steps=2_000_000,
+            scale_sw=1.0, scale_isw=1.0, scale_dop=1.0, scale_pol=1.0, lmax_g=None, lmax_pol=None,
+            lmax_nu=None) -> Options:
+    o = Options()
+    o.lmax_g = lmax_hier if lmax_g is None else lmax_g
+    o.lmax_pol = lmax_hier if lmax_pol is None else lmax_pol
+    o.lmax_nu = lmax_hier if lmax_nu is None else lmax_nu
+    o.lmax_cl, o.n_tau, o.max_steps = lmax_cl, n_tau, max_steps
+    o.rtol, o.atol = rtol, atol
+    o.scale_sw, o.scale_isw, o.scale_dop, o.scale_pol = scale_sw, scale_isw, scale_dop, scale_pol
+    return o
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def lib():
+    """Load libabcmb.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        O = ctypes.POINTER(Options)
+        L.abcmb_default_options.argtypes = [O]
+        L.abcmb_bg_doubles.argtypes = [O]
+        L.abcmb_bg_doubles.restype = ctypes.c_size_t
+        L.abcmb_perturb_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_int, O]
+        L.abcmb_perturb_workspace_bytes.restype = ctypes.c_size_t
+        L.abcmb_background_tables.argtypes = [ctypes.c_int, _P, O, _P, _P]
+        L.abcmb_perturb.argtypes = [ctypes.c_int, _P, _P, ctypes.c_int, O, _P, _P, _P, _P,
+                                    ctypes.c_size_t, _P]
+        L.abcmb_project.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, O, _P, _P]
+        L.abcmb_cl.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, O, _P, _P]
+        _lib = L
+    return _lib
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _check(rc, what):
+    if rc != OK:
+        raise RuntimeError(f"{what}: {ERRORS.get(rc, rc)}")
+
+
+def _dev(t, dtype=torch.float64):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise TypeError(f"expected a contiguous CUDA {dtype} tensor")
+    return t
+
+
+def bg_doubles(o: Options) -> int:
+    n = lib().abcmb_bg_doubles(ctypes.byref(o))
+    if n == 0:
+        raise ValueError("invalid options")
+    return n
+
+
+def perturb_workspace_bytes(B: int, Nk: int, o: Options) -> int:
+    return lib().abcmb_perturb_workspace_bytes(B, Nk, ctypes.byref(o))
+
+
+def abcmb_background_tables(params: torch.Tensor, o: Options, out: torch.Tensor | None = None):
+    """params [B, 6] (omega_b, omega_cdm, h, n_s, ln(1e10 A_s), tau_reion) -> bg [B, bg_doubles]."""
+    _dev(params)
+    B = params.shape[0]
+    bg = out if out is not None else torch.empty((B, bg_doubles(o)), dtype=torch.float64,
+                                                 device=params.device)
+    _check(lib().abcmb_background_tables(B, _ptr(params), ctypes.byref(o), _ptr(bg), _stream()),
+           "abcmb_background_tables")
+    return bg
+
+
+def abcmb_perturb(bg: torch.Tensor, k: torch.Tensor, o: Options, S=None, status=None, steps=None,
+                  workspace=None):
+    """-> S [B, Nk, n_tau, 3], mode status [B, Nk] int32, steps [B, Nk, 2] int32
+    (steps taken, IMEX substeps)."""
+    _dev(bg), _dev(k)
+    B, Nk = bg.shape[0], k.shape[0]
+    dev = bg.device
+    if S is None:
+        S = torch.empty((B, Nk, o.n_tau, 3), dtype=torch.float64, device=dev)
+    if status is None:
+        status = torch.empty((B, Nk), dtype=torch.int32, device=dev)
+    if steps is None:
+        steps = torch.empty((B, Nk, 2), dtype=torch.int32, device=dev)
+    nbytes = perturb_workspace_bytes(B, Nk, o)
+    if workspace is None:
+        workspace = torch.empty(nbytes // 8 + 32, dtype=torch.float64, device=dev)
+    _check(lib().abcmb_perturb(B, _ptr(bg), _ptr(k), Nk, ctypes.byref(o), _ptr(S), _ptr(status),
+                               _ptr(steps), _ptr(workspace), workspace.numel() * 8, _stream()),
+           "abcmb_perturb")
+    return S, status, steps
+
+
+def abcmb_project(bg: torch.Tensor, S: torch.Tensor, k: torch.Tensor, o: Options, out=None):
+    """-> Delta [B, Nk, lmax_cl - 1, 2] (T, E) for l = 2..lmax_cl."""
+    _dev(bg), _dev(S), _dev(k)
+    B, Nk = bg.shape[0], k.shape[0]
+    D = out if out is not None else torch.empty((B, Nk, o.lmax_cl - 1, 2), dtype=torch.float64,
+                                                device=bg.device)
+    _check(lib().abcmb_project(B, _ptr(bg), _ptr(S), _ptr(k), Nk, ctypes.byref(o), _ptr(D), _stream()),
+           "abcmb_project")
+    return D
+
+
+def abcmb_cl(bg: torch.Tensor, Delta: torch.Tensor, k: torch.Tensor, o: Options, out=None):
+    """-> C_l [B, 3, lmax_cl - 1] (TT, TE, EE) for l = 2..lmax_cl."""
+    _dev(bg), _dev(Delta), _dev(k)
+    B, Nk = bg.shape[0], k.shape[0]
+    C = out if out is not None else torch.empty((B, 3, o.lmax_cl - 1), dtype=torch.float64,
+                                                device=bg.device)
+    _check(lib().abcmb_cl(B, _ptr(bg), _ptr(Delta), _ptr(k), Nk, ctypes.byref(o), _ptr(C), _stream()),
+           "abcmb_cl")
+    return C
+
+
+class Pipeline:
+    """Preallocated buffers for repeated whole-path calls of one shape."""
+
+    def __init__(self, B: int, k, o: Options, device="cuda"):
+        self.o, self.B = o, B
+        self.k = torch.as_tensor(np.asarray(k, dtype=np.float64), device=device).contiguous()
+        Nk = self.k.shape[0]
+        dev = self.k.device
+        self.bg = torch.empty((B, bg_doubles(o)), dtype=torch.float64, device=dev)
+        self.S = torch.empty((B, Nk, o.n_tau, 3), dtype=torch.float64, device=dev)
+        self.status = torch.empty((B, Nk), dtype=torch.int32, device=dev)
+        self.steps = torch.empty((B, Nk, 2), dtype=torch.int32, device=dev)
+        self.ws = torch.empty(perturb_workspace_bytes(B, Nk, o) // 8 + 32, dtype=torch.float64, device=dev)
+        self.D = torch.empty((B, Nk, o.lmax_cl - 1, 2), dtype=torch.float64, device=dev)
+        self.C = torch.empty((B, 3, o.lmax_cl - 1), dtype=torch.float64, device=dev)
+        self.params = torch.empty((B, NPARAM), dtype=torch.float64, device=dev)
+
+    def run(self, params: torch.Tensor | None = None):
+        """Whole path on device-resident params; returns the C_l tensor."""
+        p = self.params if params is None else params
+        abcmb_background_tables(p, self.o, out=self.bg)
+        abcmb_perturb(self.bg, self.k, self.o, S=self.S, status=self.status, steps=self.steps,
+                      workspace=self.ws)
+        abcmb_project(self.bg, self.S, self.k, self.o, out=self.D)
+        abcmb_cl(self.bg, self.D, self.k, self.o, out=self.C)
+        return self.C
+
+    def run_host(self, params_host: np.ndarray, cl_host: torch.Tensor | None = None):
+        """End to end from host parameters (pinned copy in, C_l copy out)."""
+        src = torch.from_numpy(np.ascontiguousarray(params_host, dtype=np.float64))
+        if not src.is_pinned():
+            src = src.pin_memory()
+        self.params.copy_(src, non_blocking=True)
+        C = self.run()
+        out = cl_host if cl_host is not None else torch.empty(C.shape, dtype=C.dtype, pin_memory=True)
+        out.copy_(C, non_blocking=True)
+        return out
+
+    def check_status(self):
+        """Raise if any background or mode status word is set (syncs)."""
+        bad_bg = (self.bg[:, S_INDEX["STATUS"]] != 0).nonzero()
+        if bad_bg.numel():
+            raise RuntimeError(f"background failed for cosmologies {bad_bg.flatten().tolist()}")
+        bad = (self.status != 0).nonzero()
+        if bad.numel():
+            code = int(self.status[tuple(bad[0])])
+            raise RuntimeError(f"{bad.shape[0]} modes failed, first {bad[0].tolist()}: {ERRORS.get(code)}")
+
+
+def bg_view(bg_row: torch.Tensor, n_tau: int):
+    """Split one background record (on any device) into scalars, table and nodes."""
+    r = bg_row.detach().cpu().numpy()
+    scal = {k: r[i] for k, i in S_INDEX.items()}
+    tab = r[BG_TABLE:BG_NODES].reshape(BG_NLNA, 8)
+    nodes = r[BG_NODES:BG_NODES + 8 * n_tau].reshape(n_tau, 8)
+    return scal, tab, nodes

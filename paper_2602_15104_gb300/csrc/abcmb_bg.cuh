@@ -1,0 +1,569 @@
+// Background and thermal history of one cosmology, built by one thread into
+// the background record whose layout include/abcmb.h defines.
+//
+// Follows arXiv 2602.15104: densities (App. C.1-C.5), conformal time
+// (Sec. 2.4 "Background"), helium Saha phases (App. B.1.1), hydrogen Saha
+// (App. B.1.2, eq. SahaH) then a Peebles three-level atom (the TLA cited in
+// App. B.1.2; rates from the literature: Pequignot et al. 1991 case-B fit,
+// detailed-balance photo-ionisation at T_CMB, Lambda_2s1s = 8.2245809/s,
+// Sobolev escape K = lambda_a^3/(8 pi H)), matter temperature (App. B.1.2:
+// quasi-static T_CMB (1 - H/Gamma_C) above z = 700, its ODE below), tanh
+// reionization (App. B.2) with z_reion solved from tau_reion (App. A.2),
+// kappa and g (App. B.4), baryon sound speed (App. C.3), tight-coupling start
+// H tau_c = R_tc (App. A.1) and the tau nodes of the line-of-sight integral
+// with trapezoid weights (App. B.6).
+//
+// Compiled for sm_103a; it also compiles as plain C++ so that the same code
+// can be stepped through on a host for debugging.
+#pragma once
+
+#include <math.h>
+
+#include "../../include/abcmb.h"
+
+#ifdef __CUDACC__
+#define ABCMB_HD __host__ __device__ __forceinline__
+#else
+#define ABCMB_HD inline
+#endif
+
+namespace abcmb {
+
+// ---- physical constants ----
+constexpr double kPi = 3.141592653589793238;
+constexpr double kC = 2.99792458e10;           // cm/s
+constexpr double kMpc = 3.0856775814913673e24; // cm
+constexpr double kSigmaT = 6.6524587321e-25;   // cm^2
+constexpr double kHc = 1.239841984e-4;         // h c, eV cm
+constexpr double kHbarC = 1.973269804e-5;      // hbar c, eV cm
+constexpr double kKB = 8.617333262e-5;         // eV/K
+constexpr double kMe = 510998.95;              // eV
+constexpr double kMH = 938783073.6;            // eV, hydrogen atom
+constexpr double kMHeOverMH = 3.971480;        // 4He atom / H atom
+constexpr double kEH = 13.598434005;           // eV
+constexpr double kEHe1 = 24.587387;            // eV
+constexpr double kEHe2 = 54.417760;            // eV
+constexpr double kL2s1s = 8.2245809;           // 1/s
+constexpr double kG = 6.67430e-8;              // cgs
+constexpr double kEvErg = 1.602176634e-12;
+
+// ---- fixed cosmological inputs (paper defaults, App. A.2) ----
+constexpr double kYHe = 0.245;
+constexpr double kTcmb0 = 2.34865418e-4; // eV
+constexpr double kTnuRatio = 0.71636856;
+constexpr double kNnu = 3.0;
+constexpr double kZreHe = 3.5, kDzReHe = 0.5, kDzRe = 0.5, kBetaRe = 1.5;
+constexpr double kRtc = 1.5e-3, kRlarge = 7e-2, kKpivot = 0.05;
+constexpr double kLna700 = -6.552507968010906; // ln(1/701)
+
+constexpr int kNlna = ABCMB_BG_NLNA;
+constexpr double kLna0 = ABCMB_BG_LNA0;
+constexpr double kDlna = 1.0 / ABCMB_BG_PER_UNIT;
+// table columns
+enum { C_NUT = 0, C_DNUT, C_TAU, C_DTAU, C_CS2, C_DCS2, C_KAPPA, C_XE };
+// tau-node columns
+enum { N_LNA = 0, N_TAU, N_W, N_G, N_DG, N_EXPMK, N_HC, N_DHC };
+
+// 4-point Gauss-Legendre rule on [-1, 1]
+ABCMB_HD double gl4_x(int i)
+{
+    return i == 0 ? -0.8611363115940526 : i == 1 ? -0.3399810435848563
+         : i == 2 ? 0.3399810435848563 : 0.8611363115940526;
+}
+ABCMB_HD double gl4_w(int i) { return (i == 0 || i == 3) ? 0.3478548451374538 : 0.6521451548625461; }
+
+// Scalars of one cosmology (record header).
+struct Cosmo {
+    double H0, Om_b, Om_c, Om_g, Om_nu, Om_L, Om_r, Om_m;
+    double R_nu, f_He, nH0, A_s, n_s;
+    double z_reion, lna_tc, lna_sw, tau0, lna_He3;
+    double rho_g0; // photon energy density today, eV/cm^3
+};
+
+ABCMB_HD Cosmo load_cosmo(const double *rec)
+{
+    Cosmo c;
+    c.H0 = rec[ABCMB_S_H0];
+    c.Om_b = rec[ABCMB_S_OMB];
+    c.Om_c = rec[ABCMB_S_OMC];
+    c.Om_g = rec[ABCMB_S_OMG];
+    c.Om_nu = rec[ABCMB_S_OMNU];
+    c.Om_L = rec[ABCMB_S_OML];
+    c.Om_r = c.Om_g + c.Om_nu;
+    c.Om_m = c.Om_b + c.Om_c;
+    c.R_nu = rec[ABCMB_S_RNU];
+    c.f_He = rec[ABCMB_S_FHE];
+    c.nH0 = rec[ABCMB_S_NH0];
+    c.A_s = rec[ABCMB_S_AS];
+    c.n_s = rec[ABCMB_S_NS];
+    c.z_reion = rec[ABCMB_S_ZREION];
+    c.lna_tc = rec[ABCMB_S_LNA_TC];
+    c.lna_sw = rec[ABCMB_S_LNA_SW];
+    c.tau0 = rec[ABCMB_S_TAU0];
+    c.lna_He3 = rec[ABCMB_S_LNA_HE3];
+    c.rho_g0 = 0.0;
+    return c;
+}
+
+// ---- closed-form background ----
+struct BgClosed {
+    double a, inv_a, Hc, fc, fb, fg, fnu, dlnHc; // dlnHc = d ln H_conf / d ln a
+};
+
+ABCMB_HD BgClosed closed_bg(const Cosmo &c, double lna)
+{
+    BgClosed b;
+    b.a = exp(lna);
+    b.inv_a = 1.0 / b.a;
+    double ia = b.inv_a, ia3 = ia * ia * ia, ia4 = ia3 * ia;
+    double rr = c.Om_r * ia4, rm = c.Om_m * ia3;
+    double e2 = rr + rm + c.Om_L;
+    double ie2 = 1.0 / e2;
+    b.Hc = b.a * c.H0 * sqrt(e2);
+    b.fc = c.Om_c * ia3 * ie2;
+    b.fb = c.Om_b * ia3 * ie2;
+    b.fg = c.Om_g * ia4 * ie2;
+    b.fnu = c.Om_nu * ia4 * ie2;
+    b.dlnHc = 1.0 - (2.0 * rr + 1.5 * rm) * ie2;
+    return b;
+}
+
+ABCMB_HD double hconf(const Cosmo &c, double lna)
+{
+    double a = exp(lna), ia = 1.0 / a;
+    return a * c.H0 * sqrt(c.Om_r * ia * ia * ia * ia + c.Om_m * ia * ia * ia + c.Om_L);
+}
+
+// exact radiation+matter conformal time
+ABCMB_HD double tau_rm(const Cosmo &c, double a)
+{
+    return 2.0 * a / (c.H0 * (sqrt(c.Om_r + c.Om_m * a) + sqrt(c.Om_r)));
+}
+
+// ---- cubic Hermite on the uniform table ----
+struct Herm {
+    int j;
+    double h00, h10, h01, h11, d00, d10, d01, d11; // basis and d/du
+};
+
+ABCMB_HD Herm herm_at(double lna)
+{
+    Herm H;
+    double t = (lna - kLna0) * ABCMB_BG_PER_UNIT;
+    int j = (int)floor(t);
+    if (j < 0) j = 0;
+    if (j > kNlna - 2) j = kNlna - 2;
+    double u = t - j, um = 1.0 - u;
+    H.j = j;
+    H.h00 = (1.0 + 2.0 * u) * um * um;
+    H.h10 = u * um * um;
+    H.h01 = u * u * (3.0 - 2.0 * u);
+    H.h11 = u * u * (u - 1.0);
+    H.d00 = 6.0 * u * (u - 1.0);
+    H.d10 = um * (1.0 - 3.0 * u);
+    H.d01 = -H.d00;
+    H.d11 = u * (3.0 * u - 2.0);
+    return H;
+}
+
+// value of column col with derivative column dcol (sign sgn applied to it)
+ABCMB_HD double herm_val(const double *tab, const Herm &H, int col, int dcol, double sgn = 1.0)
+{
+    const double *r0 = tab + 8 * H.j, *r1 = r0 + 8;
+    return H.h00 * r0[col] + H.h01 * r1[col] + sgn * kDlna * (H.h10 * r0[dcol] + H.h11 * r1[dcol]);
+}
+
+ABCMB_HD double herm_der(const double *tab, const Herm &H, int col, int dcol)
+{
+    const double *r0 = tab + 8 * H.j, *r1 = r0 + 8;
+    return (H.d00 * r0[col] + H.d01 * r1[col]) * ABCMB_BG_PER_UNIT + H.d10 * r0[dcol] + H.d11 * r1[dcol];
+}
+
+// ---- thermal-history pieces ----
+ABCMB_HD double saha_pref(double T, double mu)
+{
+    double v = 2.0 * kPi * mu * T / (kHc * kHc);
+    return v * sqrt(v);
+}
+ABCMB_HD double mu_eH() { return kMe * kMH / (kMe + kMH); }
+ABCMB_HD double mu_eHe() { return kMe * (kMHeOverMH * kMH) / (kMe + kMHeOverMH * kMH); }
+
+// Stable root of x^2 + (b0 + s) x - s f = 0 and its ln a derivative, for a
+// Saha ratio s whose log derivative is dls.
+ABCMB_HD double saha_root(double s, double f, double b0, double dls, double *dx)
+{
+    double b = b0 + s, r = sqrt(b * b + 4.0 * s * f);
+    double x = 2.0 * s * f / (b + r);
+    *dx = s * (f - x) * dls / (2.0 * x + b);
+    return x;
+}
+
+// Saha ratio S(T) e^{-E/T} / n_H with T = T0/a, n_H = nH0/a^3; its log
+// derivative is 3/2 - E/T.
+ABCMB_HD double saha_s(const Cosmo &c, double a, double E, double mu, double g, double *dls)
+{
+    double T = kTcmb0 / a;
+    *dls = 1.5 - E / T;
+    return g * saha_pref(T, mu) * exp(-E / T) * a * a * a / c.nH0;
+}
+
+ABCMB_HD double x_he(const Cosmo &c, double lna, double *dx)
+{
+    double a = exp(lna), dls;
+    if (lna < c.lna_He3) {
+        double s = saha_s(c, a, kEHe2, mu_eHe(), 1.0, &dls);
+        return c.f_He + saha_root(s, c.f_He, 1.0 + c.f_He, dls, dx);
+    }
+    double s = saha_s(c, a, kEHe1, mu_eHe(), 4.0, &dls);
+    return saha_root(s, c.f_He, 1.0, dls, dx);
+}
+
+ABCMB_HD double xp_saha(const Cosmo &c, double lna, double *dx)
+{
+    double dls;
+    double s = saha_s(c, exp(lna), kEH, mu_eH(), 1.0, &dls);
+    return saha_root(s, 1.0, 0.0, dls, dx);
+}
+
+ABCMB_HD double alpha_B(double T)
+{
+    double lt = log(T / kKB * 1.0e-4);
+    return 4.309e-13 * exp(-0.6166 * lt) / (1.0 + 0.6703 * exp(0.5300 * lt));
+}
+
+ABCMB_HD double H_sec(const Cosmo &c, double lna) { return hconf(c, lna) * exp(-lna) * kC / kMpc; }
+
+ABCMB_HD double gamma_C(const Cosmo &c, double a, double xe)
+{
+    double rho_g = c.rho_g0 / (a * a * a * a);
+    return 8.0 * kSigmaT * kC * rho_g / (3.0 * kMe) * xe / (1.0 + c.f_He + xe);
+}
+
+// quasi-static matter temperature and d ln T_m / d ln a
+ABCMB_HD double tm_qs(const Cosmo &c, double lna, double xe, double dxe, double *dlnTm)
+{
+    double a = exp(lna), T = kTcmb0 / a;
+    BgClosed b = closed_bg(c, lna);
+    double H = b.Hc * b.inv_a * kC / kMpc;
+    double r = H / gamma_C(c, a, xe);
+    double dlnH = b.dlnHc - 1.0;
+    double dlnG = -4.0 + dxe * (1.0 + c.f_He) / (xe * (1.0 + c.f_He + xe));
+    *dlnTm = -1.0 - r / (1.0 - r) * (dlnH - dlnG);
+    return T * (1.0 - r);
+}
+
+// Peebles TLA for x_p (and T_m when two) in ln a
+ABCMB_HD void tla_rhs(const Cosmo &c, double lna, double xp, double Tm_in, bool two,
+                      double *dxp, double *dTm)
+{
+    double a = exp(lna), T = kTcmb0 / a, dum;
+    double xe = xp + x_he(c, lna, &dum);
+    double Tm = two ? Tm_in : T * (1.0 - H_sec(c, lna) / gamma_C(c, a, xe));
+    double nH = c.nH0 / (a * a * a), H = H_sec(c, lna);
+    double al = alpha_B(Tm);
+    double be = alpha_B(T) * saha_pref(T, mu_eH()) * exp(-0.25 * kEH / T);
+    double lam = kHc / (0.75 * kEH);
+    double K = lam * lam * lam / (8.0 * kPi * H);
+    double n1s = nH * (1.0 - xp);
+    double C = (1.0 + K * kL2s1s * n1s) / (1.0 + K * (kL2s1s + be) * n1s);
+    *dxp = -C * (al * nH * xe * xp - be * (1.0 - xp) * exp(-0.75 * kEH / T)) / H;
+    *dTm = two ? (-2.0 * Tm + gamma_C(c, a, xe) / H * (T - Tm)) : 0.0;
+}
+
+ABCMB_HD double nuT_closed(const Cosmo &c, double lna, double xe)
+{
+    double a = exp(lna);
+    return xe * c.nH0 * kSigmaT * kMpc / (a * a * hconf(c, lna));
+}
+
+// optical depth of the reionization electrons alone for a trial z_reion
+ABCMB_HD double tau_reion_trial(const Cosmo &c, double zre)
+{
+    double dy = kBetaRe * kDzRe * pow(1.0 + zre, kBetaRe - 1.0);
+    double yre = pow(1.0 + zre, kBetaRe);
+    double zmax = pow(yre + 25.0 * dy, 1.0 / kBetaRe) - 1.0;
+    double zhe = kZreHe + 25.0 * kDzReHe;
+    if (zhe > zmax) zmax = zhe;
+    double lo = -log(1.0 + zmax);
+    const int np = 800;
+    double hp = -lo / np, acc = 0.0;
+    for (int p = 0; p < np; p++)
+        for (int q = 0; q < 4; q++) {
+            double lna = lo + hp * (p + 0.5 * (1.0 + gl4_x(q)));
+            double z = exp(-lna) - 1.0;
+            double S1 = 0.5 * (1.0 + tanh((yre - pow(1.0 + z, kBetaRe)) / dy));
+            double S2 = 0.5 * (1.0 + tanh((kZreHe - z) / kDzReHe));
+            acc += 0.5 * hp * gl4_w(q) * ((1.0 + c.f_He) * S1 + c.f_He * S2) * nuT_closed(c, lna, 1.0);
+        }
+    return acc;
+}
+
+// ---- point evaluation used by the ODE and the sources ----
+struct BgPt {
+    double Hc, inv_Hc, fc, fb, fg, fnu, nuT, Rinv, cs2, tau;
+};
+
+ABCMB_HD BgPt bg_point(const Cosmo &c, const double *tab, double lna)
+{
+    BgPt p;
+    BgClosed b = closed_bg(c, lna);
+    p.Hc = b.Hc;
+    p.inv_Hc = 1.0 / b.Hc;
+    p.fc = b.fc; p.fb = b.fb; p.fg = b.fg; p.fnu = b.fnu;
+    p.Rinv = (4.0 / 3.0) * (c.Om_g / c.Om_b) * b.inv_a;
+    Herm H = herm_at(lna);
+    p.nuT = herm_val(tab, H, C_NUT, C_DNUT);
+    p.cs2 = herm_val(tab, H, C_CS2, C_DCS2);
+    p.tau = herm_val(tab, H, C_TAU, C_DTAU);
+    return p;
+}
+
+// bisection for a root of f(x) - target on [lo, hi]; f monotone
+template <class F>
+ABCMB_HD double bisect(F f, double target, double lo, double hi, bool *ok)
+{
+    double flo = f(lo) - target, fhi = f(hi) - target;
+    *ok = (flo < 0.0) != (fhi < 0.0);
+    for (int it = 0; it < 200; it++) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        double fm = f(mid) - target;
+        if ((fm < 0.0) == (flo < 0.0)) { lo = mid; flo = fm; }
+        else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// ---- the builder ----
+ABCMB_HD void build_background(const double *p, double *rec, int n_tau)
+{
+    for (int i = 0; i < ABCMB_BG_NSCALAR; i++) rec[i] = 0.0;
+    double *tab = rec + ABCMB_BG_TABLE;
+    double *nodes = rec + ABCMB_BG_NODES;
+    int status = ABCMB_OK;
+    bool ok = true;
+
+    Cosmo c;
+    double h = p[2], h2 = h * h;
+    c.H0 = h * 1.0e7 / kC;
+    double H100 = 1.0e7 / kMpc;
+    double rho_crit100 = 3.0 * H100 * H100 / (8.0 * kPi * kG) * kC * kC / kEvErg;
+    double T0 = kTcmb0, Tn = kTnuRatio * kTcmb0;
+    double hbc3 = kHbarC * kHbarC * kHbarC;
+    c.rho_g0 = kPi * kPi / 15.0 * T0 * T0 * T0 * T0 / hbc3;
+    double rho_nu0 = kNnu * 7.0 * kPi * kPi / 120.0 * Tn * Tn * Tn * Tn / hbc3;
+    c.Om_b = p[0] / h2;
+    c.Om_c = p[1] / h2;
+    c.Om_g = c.rho_g0 / (rho_crit100 * h2);
+    c.Om_nu = rho_nu0 / (rho_crit100 * h2);
+    c.Om_r = c.Om_g + c.Om_nu;
+    c.Om_m = c.Om_b + c.Om_c;
+    c.Om_L = 1.0 - c.Om_m - c.Om_r;
+    c.R_nu = c.Om_nu / c.Om_r;
+    c.f_He = kYHe / (kMHeOverMH * (1.0 - kYHe));
+    c.nH0 = (1.0 - kYHe) * p[0] * rho_crit100 / kMH;
+    c.A_s = exp(p[4]) * 1.0e-10;
+    c.n_s = p[3];
+
+    // helium and hydrogen phase switches
+    c.lna_He3 = bisect([&](double l) { double d; double a = exp(l); (void)a;
+                           double dls; double s = saha_s(c, exp(l), kEHe2, mu_eHe(), 1.0, &dls);
+                           return saha_root(s, c.f_He, 1.0 + c.f_He, dls, &d); },
+                       1e-9, -12.0, -5.0, &ok);
+    if (!ok) status = ABCMB_E_BACKGROUND;
+    c.lna_sw = bisect([&](double l) { double d; return xp_saha(c, l, &d); }, 0.99, -9.0, -6.0, &ok);
+    if (!ok) status = ABCMB_E_BACKGROUND;
+
+    // Peebles TLA (x_p, then also T_m below z = 700), RK4 with four
+    // substeps per table cell, stored at the table nodes at and after lna_sw
+    {
+        double dum;
+        int j0 = (int)ceil((c.lna_sw - kLna0) * ABCMB_BG_PER_UNIT);
+        double x = c.lna_sw;
+        double y0 = xp_saha(c, x, &dum), y1 = 0.0;
+        bool two = false;
+        for (int j = j0; j < kNlna; j++) {
+            double target = kLna0 + j * kDlna;
+            while (x < target) {
+                double hs = 0.25 * kDlna;
+                if (target - x < hs * (1.0 + 1e-9)) hs = target - x;
+                bool hit700 = false;
+                if (!two && x < kLna700 && x + hs >= kLna700) { hs = kLna700 - x; hit700 = true; }
+                double k1a, k1b, k2a, k2b, k3a, k3b, k4a, k4b;
+                tla_rhs(c, x, y0, y1, two, &k1a, &k1b);
+                tla_rhs(c, x + 0.5 * hs, y0 + 0.5 * hs * k1a, y1 + 0.5 * hs * k1b, two, &k2a, &k2b);
+                tla_rhs(c, x + 0.5 * hs, y0 + 0.5 * hs * k2a, y1 + 0.5 * hs * k2b, two, &k3a, &k3b);
+                tla_rhs(c, x + hs, y0 + hs * k3a, y1 + hs * k3b, two, &k4a, &k4b);
+                y0 += hs / 6.0 * (k1a + 2.0 * k2a + 2.0 * k3a + k4a);
+                y1 += hs / 6.0 * (k1b + 2.0 * k2b + 2.0 * k3b + k4b);
+                if (hit700) {
+                    x = kLna700;
+                    two = true;
+                    double xe = y0 + x_he(c, x, &dum);
+                    y1 = kTcmb0 * exp(-x) * (1.0 - H_sec(c, x) / gamma_C(c, exp(x), xe));
+                } else {
+                    x += hs;
+                }
+                if (x > target - 1e-14) x = target;
+            }
+            double dxp, dTm;
+            tla_rhs(c, target, y0, y1, two, &dxp, &dTm);
+            double *r = tab + 8 * j;
+            r[C_XE] = y0;      // temporarily x_p
+            r[C_KAPPA] = dxp;  // temporarily dx_p/dln a
+            r[C_CS2] = y1;     // temporarily T_m (z < 700)
+            r[C_DCS2] = dTm;   // temporarily dT_m/dln a
+        }
+    }
+
+    // reionization redshift
+    {
+        double lo = 0.0, hi = 60.0;
+        if (tau_reion_trial(c, hi) < p[5] || tau_reion_trial(c, lo) > p[5]) status = ABCMB_E_BACKGROUND;
+        for (int it = 0; it < 80; it++) {
+            double mid = 0.5 * (lo + hi);
+            if (tau_reion_trial(c, mid) < p[5]) lo = mid; else hi = mid;
+        }
+        c.z_reion = 0.5 * (lo + hi);
+    }
+
+    // table: x_e, 1/(H tau_c), c_s^2, 1/H
+    {
+        double yre = pow(1.0 + c.z_reion, kBetaRe);
+        double dyre = kBetaRe * kDzRe * pow(1.0 + c.z_reion, kBetaRe - 1.0);
+        for (int j = 0; j < kNlna; j++) {
+            double lna = kLna0 + j * kDlna;
+            double *r = tab + 8 * j;
+            BgClosed b = closed_bg(c, lna);
+            double xp, dxp, xh, dxh;
+            if (lna < c.lna_sw) xp = xp_saha(c, lna, &dxp);
+            else { xp = r[C_XE]; dxp = r[C_KAPPA]; }
+            xh = x_he(c, lna, &dxh);
+            double xr = xp + xh, dxr = dxp + dxh;
+            double Tm, dlnTm;
+            if (lna < kLna700) Tm = tm_qs(c, lna, xr, dxr, &dlnTm);
+            else { Tm = r[C_CS2]; dlnTm = r[C_DCS2] / Tm; }
+            double z = b.inv_a - 1.0;
+            double y = pow(1.0 + z, kBetaRe);
+            double t1 = tanh((yre - y) / dyre), t2 = tanh((kZreHe - z) / kDzReHe);
+            double S1 = 0.5 * (1.0 + t1), S2 = 0.5 * (1.0 + t2);
+            double dS1 = 0.5 * (1.0 - t1 * t1) * kBetaRe * y / dyre;
+            double dS2 = 0.5 * (1.0 - t2 * t2) * (1.0 + z) / kDzReHe;
+            double xe = xr + (1.0 + c.f_He - xr) * S1 + c.f_He * S2;
+            double dxe = dxr * (1.0 - S1) + (1.0 + c.f_He - xr) * dS1 + c.f_He * dS2;
+            double nuT = xe * c.nH0 * kSigmaT * kMpc * b.inv_a * b.inv_a / b.Hc;
+            double mub = kMH / ((1.0 + xe) * (1.0 - kYHe) + kYHe / kMHeOverMH);
+            r[C_NUT] = nuT;
+            r[C_DNUT] = nuT * (dxe / xe - 2.0 - b.dlnHc);
+            r[C_CS2] = Tm / mub * (1.0 - dlnTm / 3.0);
+            r[C_DTAU] = 1.0 / b.Hc;
+            r[C_XE] = xe;
+        }
+        for (int j = 0; j < kNlna; j++) {
+            int jl = j > 0 ? j - 1 : j, jh = j < kNlna - 1 ? j + 1 : j;
+            tab[8 * j + C_DCS2] = (tab[8 * jh + C_CS2] - tab[8 * jl + C_CS2]) / ((jh - jl) * kDlna);
+        }
+    }
+
+    // conformal time: closed radiation+matter part plus the Lambda correction
+    {
+        double corr = 0.0;
+        for (int j = 0; j < kNlna; j++) {
+            double lna = kLna0 + j * kDlna;
+            if (j > 0) {
+                double l0 = lna - kDlna;
+                for (int q = 0; q < 4; q++) {
+                    double l = l0 + 0.5 * kDlna * (1.0 + gl4_x(q));
+                    double a = exp(l);
+                    double hrm = c.H0 * sqrt(c.Om_r / (a * a) + c.Om_m / a);
+                    corr += 0.5 * kDlna * gl4_w(q) * (1.0 / hconf(c, l) - 1.0 / hrm);
+                }
+            }
+            tab[8 * j + C_TAU] = tau_rm(c, exp(lna)) + corr;
+        }
+        c.tau0 = tab[8 * (kNlna - 1) + C_TAU];
+    }
+
+    // optical depth: exact integral of the Hermite interpolant of 1/(H tau_c)
+    {
+        tab[8 * (kNlna - 1) + C_KAPPA] = 0.0;
+        for (int j = kNlna - 2; j >= 0; j--) {
+            const double *r0 = tab + 8 * j, *r1 = r0 + 8;
+            double cell = 0.5 * kDlna * (r0[C_NUT] + r1[C_NUT])
+                        + kDlna * kDlna / 12.0 * (r0[C_DNUT] - r1[C_DNUT]);
+            tab[8 * j + C_KAPPA] = r1[C_KAPPA] + cell;
+        }
+    }
+
+    // tight-coupling start: H tau_c = R_tc
+    c.lna_tc = bisect([&](double l) { Herm H = herm_at(l); return -herm_val(tab, H, C_NUT, C_DNUT); },
+                      -1.0 / kRtc, kLna0 + 1.0, -3.0, &ok);
+    if (!ok) status = ABCMB_E_BACKGROUND;
+
+    // tau nodes
+    if (n_tau >= 8) {
+        int nA = n_tau / 4, nB = n_tau / 2, nC = n_tau - nA - nB;
+        double l1300 = -log(1301.0), l900 = -log(901.0);
+        Herm H9 = herm_at(l900);
+        double t900 = herm_val(tab, H9, C_TAU, C_DTAU);
+        for (int i = 0; i < n_tau; i++) {
+            double lna;
+            if (i < nA) lna = c.lna_tc + (l1300 - c.lna_tc) * i / nA;
+            else if (i < nA + nB) lna = -log(1.0 + 1300.0 - 400.0 * (i - nA) / nB);
+            else {
+                int jc = i - nA - nB;
+                double tt = t900 + (c.tau0 - t900) * jc / nC;
+                bool ok2 = true;
+                lna = jc == 0 ? l900
+                    : bisect([&](double l) { Herm H = herm_at(l); return herm_val(tab, H, C_TAU, C_DTAU); },
+                             tt, l900, 0.0, &ok2);
+                if (!ok2) status = ABCMB_E_BACKGROUND;
+            }
+            Herm H = herm_at(lna);
+            BgClosed b = closed_bg(c, lna);
+            double nu = herm_val(tab, H, C_NUT, C_DNUT);
+            double dnu = herm_der(tab, H, C_NUT, C_DNUT);
+            double kap = herm_val(tab, H, C_KAPPA, C_NUT, -1.0);
+            double emk = exp(-kap);
+            double g = b.Hc * nu * emk;
+            double *nd = nodes + 8 * i;
+            nd[N_LNA] = lna;
+            nd[N_TAU] = herm_val(tab, H, C_TAU, C_DTAU);
+            nd[N_G] = g;
+            nd[N_DG] = g * (dnu / nu + b.dlnHc + nu);
+            nd[N_EXPMK] = emk;
+            nd[N_HC] = b.Hc;
+            nd[N_DHC] = b.Hc * b.dlnHc;
+        }
+        for (int i = 0; i < n_tau; i++) {
+            double lo = nodes[8 * (i > 0 ? i - 1 : i) + N_TAU];
+            double hi = nodes[8 * (i < n_tau - 1 ? i + 1 : i) + N_TAU];
+            nodes[8 * i + N_W] = 0.5 * (hi - lo);
+        }
+    }
+
+    if (!(c.tau0 > 0.0 && c.tau0 < 1e6) || !(c.lna_tc < 0.0)) {
+        if (status == ABCMB_OK) status = ABCMB_E_NONFINITE;
+    }
+    rec[ABCMB_S_STATUS] = status;
+    rec[ABCMB_S_H0] = c.H0;
+    rec[ABCMB_S_OMB] = c.Om_b;
+    rec[ABCMB_S_OMC] = c.Om_c;
+    rec[ABCMB_S_OMG] = c.Om_g;
+    rec[ABCMB_S_OMNU] = c.Om_nu;
+    rec[ABCMB_S_OML] = c.Om_L;
+    rec[ABCMB_S_RNU] = c.R_nu;
+    rec[ABCMB_S_FHE] = c.f_He;
+    rec[ABCMB_S_NH0] = c.nH0;
+    rec[ABCMB_S_AS] = c.A_s;
+    rec[ABCMB_S_NS] = c.n_s;
+    rec[ABCMB_S_ZREION] = c.z_reion;
+    rec[ABCMB_S_LNA_TC] = c.lna_tc;
+    rec[ABCMB_S_LNA_SW] = c.lna_sw;
+    rec[ABCMB_S_TAU0] = c.tau0;
+    rec[ABCMB_S_LNA_HE3] = c.lna_He3;
+    rec[ABCMB_S_LNA_700] = kLna700;
+    rec[ABCMB_S_NTAU] = n_tau;
+}
+
+} // namespace abcmb

@@ -1,0 +1,131 @@
+// Background and perturbation kernels plus the option helpers of the C ABI
+// (include/abcmb.h).
+//
+// background_kernel: one thread per cosmology runs abcmb::build_background.
+// perturb_kernel: one thread per (cosmology, k) mode runs
+// abcmb::integrate_mode; modes are ordered k-descending so that the most
+// expensive modes are scheduled first and the lanes of a warp share one k
+// across cosmologies; the per-mode working vectors live in the caller's
+// workspace, laid out [vector][component][mode] so that the lanes of a warp
+// touch consecutive addresses.
+#include <cuda_runtime.h>
+
+#include "abcmb_ode.cuh"
+
+namespace abcmb {
+
+__global__ void background_kernel(int B, const double *__restrict__ params, double *bg, long len, int n_tau)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    build_background(params + (long)b * ABCMB_NPARAM, bg + (long)b * len, n_tau);
+}
+
+__global__ void __launch_bounds__(64)
+perturb_kernel(int B, int Nk, const double *__restrict__ bg, long len, const double *__restrict__ kv,
+               int Lg, int Lp, int Ln, double rtol, double atol, int max_steps, double s_sw,
+               double s_isw, double s_dop, double *S, int *status, int *steps, double *work)
+{
+    __shared__ double sa[65], sb[65];
+    for (int l = threadIdx.x; l < 65; l += blockDim.x) {
+        sa[l] = (double)l / (2.0 * l + 1.0);
+        sb[l] = (l + 1.0) / (2.0 * l + 1.0);
+    }
+    __syncthreads();
+    const long M = (long)B * Nk;
+    const long mi = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (mi >= M) return;
+    const int kidx = Nk - 1 - (int)(mi / B);
+    const int b = (int)(mi % B);
+    const OdeDims d = ode_dims(Lg, Lp, Ln);
+    const StreamCoef sc = {sa, sb};
+    const double *rec = bg + (long)b * len;
+    const int n_tau = (int)rec[ABCMB_S_NTAU];
+    const double sw[3] = {s_sw, s_isw, s_dop};
+    double *Sm = S + ((long)b * Nk + kidx) * (long)n_tau * 3;
+    ModeResult r;
+    if (rec[ABCMB_S_STATUS] != 0.0) {
+        r.status = ABCMB_E_NONFINITE;
+        r.steps = 0;
+        r.substeps = 0;
+        for (int n = 0; n < 3 * n_tau; n++) Sm[n] = 0.0;
+    } else {
+        r = integrate_mode(d, sc, rec, kv[kidx], rtol, atol, max_steps, sw, work + mi, M, Sm);
+    }
+    status[(long)b * Nk + kidx] = r.status;
+    if (steps) {
+        steps[2 * ((long)b * Nk + kidx)] = r.steps;
+        steps[2 * ((long)b * Nk + kidx) + 1] = r.substeps;
+    }
+}
+
+} // namespace abcmb
+
+// ---------------------------------------------------------------- C ABI
+extern "C" void abcmb_default_options(abcmb_options *o)
+{
+    o->lmax_g = 12;
+    o->lmax_pol = 12;
+    o->lmax_nu = 12;
+    o->lmax_cl = 2500;
+    o->n_tau = 6000;
+    o->max_steps = 2000000;
+    o->rtol = 1e-8;
+    o->atol = 1e-12;
+    o->scale_sw = o->scale_isw = o->scale_dop = o->scale_pol = 1.0;
+}
+
+extern "C" int abcmb_validate_options(const abcmb_options *o)
+{
+    if (!o) return ABCMB_E_INVALID_ARG;
+    if (o->lmax_g < 4 || o->lmax_g > 64 || o->lmax_pol < 4 || o->lmax_pol > 64 || o->lmax_nu < 4 ||
+        o->lmax_nu > 64)
+        return ABCMB_E_INVALID_ARG;
+    if (o->lmax_cl < 2 || o->lmax_cl > 5000) return ABCMB_E_INVALID_ARG;
+    if (o->n_tau < 8 || o->n_tau > 65536) return ABCMB_E_INVALID_ARG;
+    if (o->max_steps < 1) return ABCMB_E_INVALID_ARG;
+    if (!(o->rtol > 0.0 && o->rtol < 1.0) || !(o->atol >= 0.0)) return ABCMB_E_INVALID_ARG;
+    return ABCMB_OK;
+}
+
+extern "C" size_t abcmb_bg_doubles(const abcmb_options *o)
+{
+    if (abcmb_validate_options(o) != ABCMB_OK) return 0;
+    return (size_t)ABCMB_BG_NODES + 8 * (size_t)o->n_tau;
+}
+
+extern "C" size_t abcmb_perturb_workspace_bytes(int B, int Nk, const abcmb_options *o)
+{
+    if (B < 1 || Nk < 1 || abcmb_validate_options(o) != ABCMB_OK) return 0;
+    const abcmb::OdeDims d = abcmb::ode_dims(o->lmax_g, o->lmax_pol, o->lmax_nu);
+    return (size_t)abcmb::kNvec * d.N * (size_t)B * Nk * sizeof(double);
+}
+
+extern "C" int abcmb_background_tables(int B, const double *params, const abcmb_options *o, double *bg,
+                                       void *stream)
+{
+    if (B < 1 || !params || !bg || abcmb_validate_options(o) != ABCMB_OK) return ABCMB_E_INVALID_ARG;
+    const long len = (long)abcmb_bg_doubles(o);
+    abcmb::background_kernel<<<(B + 31) / 32, 32, 0, (cudaStream_t)stream>>>(B, params, bg, len, o->n_tau);
+    return cudaGetLastError() == cudaSuccess ? ABCMB_OK : ABCMB_E_CUDA;
+}
+
+extern "C" int abcmb_perturb(int B, const double *bg, const double *k, int Nk, const abcmb_options *o,
+                             double *S, int *mode_status, int *steps, void *workspace, size_t workspace_bytes,
+                             void *stream)
+{
+    if (B < 1 || Nk < 1 || !bg || !k || !S || !mode_status || !workspace ||
+        abcmb_validate_options(o) != ABCMB_OK)
+        return ABCMB_E_INVALID_ARG;
+    if (workspace_bytes < abcmb_perturb_workspace_bytes(B, Nk, o)) return ABCMB_E_INVALID_ARG;
+    if (((size_t)workspace & 255) != 0) return ABCMB_E_INVALID_ARG;
+    const long len = (long)abcmb_bg_doubles(o);
+    const long M = (long)B * Nk;
+    const int threads = 64;
+    const long blocks = (M + threads - 1) / threads;
+    if (blocks > 2147483647L) return ABCMB_E_INVALID_ARG;
+    abcmb::perturb_kernel<<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(
+        B, Nk, bg, len, k, o->lmax_g, o->lmax_pol, o->lmax_nu, o->rtol, o->atol, o->max_steps, o->scale_sw,
+        o->scale_isw, o->scale_dop, S, mode_status, steps, (double *)workspace);
+    return cudaGetLastError() == cudaSuccess ? ABCMB_OK : ABCMB_E_CUDA;
+}

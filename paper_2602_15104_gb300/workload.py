@@ -51,6 +51,23 @@ def log_k_nodes(n: int, k_min: float, k_max: float) -> np.ndarray:
     return np.exp(np.linspace(np.log(k_min), np.log(k_max), n))
 
 
+def synthetic_sources(n_k: int, n_tau: int, seed: int) -> np.ndarray:
+    """Seeded smooth source arrays S[n_k][n_tau][3] indexed by tau-node number,
+    shaped like CMB sources on the standard node grid (a narrow peak where the
+    recombination nodes sit, oscillating with a k-dependent phase, plus a weak
+    late tail); used to feed identical sources to both projections."""
+    rng = np.random.default_rng(seed)
+    i = np.arange(n_tau) / n_tau
+    out = np.empty((n_k, n_tau, 3))
+    for m in range(n_k):
+        for c in range(3):
+            amp, ph, fr = rng.uniform(0.5, 1.5), rng.uniform(0, 2 * np.pi), rng.uniform(5, 60)
+            peak = np.exp(-0.5 * ((i - 0.45) / 0.08) ** 2)
+            tail = 0.05 * np.exp(-((i - 0.9) / 0.1) ** 2)
+            out[m, :, c] = amp * (peak * np.cos(fr * i + ph) + tail) * 10.0 ** (-c)
+    return out
+
+
 @dataclass(frozen=True)
 class Workload:
     """One named configuration of the hot path."""

@@ -1,0 +1,114 @@
+"""Host-side checks of the C ABI library (no GPU compute): it builds for
+sm_103a, loads, exports every entry point include/abcmb.h declares, and
+rejects invalid arguments on the host before enqueuing anything."""
+import ctypes
+import os
+import re
+import shutil
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "abcmb.h")
+
+pytestmark = pytest.mark.skipif(shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"),
+                                reason="nvcc not available")
+
+
+@pytest.fixture(scope="module")
+def A():
+    from paper_2602_15104_gb300 import abcmb, build
+    build.build()
+    abcmb.lib()
+    return abcmb
+
+
+def declared_symbols():
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"\b(abcmb_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(A):
+    L = A.lib()
+    syms = declared_symbols()
+    assert len(syms) >= 8
+    for s in syms:
+        assert hasattr(L, s), s
+
+
+def test_defaults_and_sizes(A):
+    L = A.lib()
+    o = A.Options()
+    L.abcmb_default_options(ctypes.byref(o))
+    assert (o.lmax_g, o.lmax_cl, o.n_tau) == (12, 2500, 6000)
+    assert A.bg_doubles(o) == A.BG_NODES + 8 * o.n_tau
+    N = 4 + 3 * 13
+    assert A.perturb_workspace_bytes(64, 400, o) == 8 * N * 64 * 400 * 8
+    bad = A.options(lmax_hier=3)
+    assert L.abcmb_bg_doubles(ctypes.byref(bad)) == 0
+    assert L.abcmb_perturb_workspace_bytes(64, 400, ctypes.byref(bad)) == 0
+
+
+@pytest.mark.parametrize("field,value", [("lmax_g", 3), ("lmax_nu", 65), ("lmax_cl", 1), ("lmax_cl", 5001),
+                                         ("n_tau", 7), ("max_steps", 0), ("rtol", 0.0), ("rtol", 1.0),
+                                         ("atol", -1.0)])
+def test_invalid_options_rejected_on_host(A, field, value):
+    L = A.lib()
+    o = A.options()
+    setattr(o, field, value)
+    fake = ctypes.c_void_p(256)  # never dereferenced: validation fails first
+    assert L.abcmb_background_tables(1, fake, ctypes.byref(o), fake, None) == A.E_INVALID_ARG
+    assert L.abcmb_perturb(1, fake, fake, 4, ctypes.byref(o), fake, fake, None, fake, 1 << 30,
+                           None) == A.E_INVALID_ARG
+    assert L.abcmb_project(1, fake, fake, fake, 4, ctypes.byref(o), fake, None) == A.E_INVALID_ARG
+    assert L.abcmb_cl(1, fake, fake, fake, 4, ctypes.byref(o), fake, None) == A.E_INVALID_ARG
+
+
+def test_invalid_shapes_and_pointers_rejected(A):
+    L = A.lib()
+    o = A.options()
+    f = ctypes.c_void_p(256)
+    assert L.abcmb_background_tables(0, f, ctypes.byref(o), f, None) == A.E_INVALID_ARG
+    assert L.abcmb_background_tables(1, None, ctypes.byref(o), f, None) == A.E_INVALID_ARG
+    assert L.abcmb_perturb(1, f, f, 0, ctypes.byref(o), f, f, None, f, 1 << 40, None) == A.E_INVALID_ARG
+    # workspace too small, or misaligned
+    assert L.abcmb_perturb(1, f, f, 4, ctypes.byref(o), f, f, None, f, 8, None) == A.E_INVALID_ARG
+    assert L.abcmb_perturb(1, f, f, 4, ctypes.byref(o), f, f, None, ctypes.c_void_p(264), 1 << 40,
+                           None) == A.E_INVALID_ARG
+    assert L.abcmb_project(1, f, None, f, 4, ctypes.byref(o), f, None) == A.E_INVALID_ARG
+    assert L.abcmb_cl(1, f, f, f, 1, ctypes.byref(o), f, None) == A.E_INVALID_ARG  # one k: no quadrature
+    assert L.abcmb_cl(1, f, f, f, 4, ctypes.byref(o), None, None) == A.E_INVALID_ARG
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    from paper_2602_15104_gb300 import abcmb
+    monkeypatch.setattr(abcmb, "_lib", None)
+    monkeypatch.setattr(abcmb, "LIB_PATH", "/nonexistent/libabcmb.so")
+    with pytest.raises(RuntimeError, match="missing"):
+        abcmb.lib()
+
+
+def test_library_package_never_uses_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2602_15104_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", text, re.M), f
+                assert "orc_" not in text, f
+
+
+def test_workload_is_seeded():
+    from paper_2602_15104_gb300 import workload as W
+    a = W.draw_cosmologies(64, 20260102)
+    b = W.draw_cosmologies(4, 20260102)
+    np.testing.assert_array_equal(a[:4], b)
+    for j, (lo, hi) in enumerate(W.PRIORS):
+        assert np.all((a[:, j] >= lo) & (a[:, j] <= hi))
+    k = W.BATCH64.k()
+    assert k.size == 400 and abs(k[0] - 1e-5) < 1e-20 and abs(k[-1] - 0.5) < 1e-15
+    np.testing.assert_allclose(np.diff(np.log(k)), np.log(0.5 / 1e-5) / 399, rtol=1e-10)
+    S1 = W.synthetic_sources(3, 100, 5)
+    S2 = W.synthetic_sources(3, 100, 5)
+    np.testing.assert_array_equal(S1, S2)
