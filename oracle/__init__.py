@@ -65,14 +65,14 @@ def _arr(x):
 
 
 def opts(lmax=12, lmax_g=None, lmax_pol=None, lmax_nu=None, scale_sw=1.0, scale_isw=1.0,
-         scale_dop=1.0, scale_pol=1.0, step_c=0.05, step_cap=0.05, hooks=0):
+         scale_dop=1.0, scale_pol=1.0, step_c=0.05, step_cap=0.05, hooks=0, max_steps=0):
     """Options vector: hierarchy truncations, source switches (App. A.1), the
     step schedule of the oracle's integrator and test hooks."""
     lg = lmax if lmax_g is None else lmax_g
     lp = lmax if lmax_pol is None else lmax_pol
     ln = lmax if lmax_nu is None else lmax_nu
     return np.array([lg, lp, ln, scale_sw, scale_isw, scale_dop, scale_pol, step_c, step_cap,
-                     hooks], dtype=np.float64)
+                     hooks, max_steps], dtype=np.float64)
 
 
 def nstate(o):
@@ -214,3 +214,14 @@ def dense_solve(A, b):
     if L.orc_dense_solve(_p(A), b.size, _p(b)):
         raise RuntimeError("singular")
     return b
+
+
+def count_steps(params, k, n_tau, o):
+    """Radau steps the oracle's fixed schedule takes per k mode (no solve)."""
+    k = _arr(k)
+    out = np.zeros(k.size, dtype=np.int64)
+    L = lib()
+    L.orc_count_steps.argtypes = [_D, ctypes.c_int, _D, _D, ctypes.c_int, _L]
+    if L.orc_count_steps(_p(_arr(params)), int(n_tau), _p(_arr(o)), _p(k), k.size, out.ctypes.data_as(_L)):
+        raise RuntimeError("oracle background failed")
+    return out

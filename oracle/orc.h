@@ -49,6 +49,7 @@ typedef struct {
     double step_c;   /* step schedule: h <= step_c / (1 + k/H)          */
     double step_cap; /* absolute cap on a step in ln a                  */
     int hooks;
+    long max_steps;  /* 0 = unlimited; > 0 stops each mode early (timing samples) */
 } orc_opts;
 
 /* Per-cosmology state: derived parameters, thermal-history tables, tau nodes. */
@@ -112,6 +113,7 @@ void orc_lu_solve(const double *A, int n, const int *piv, double *b);
 
 /* orc_perturb.c */
 int orc_nstate(const orc_opts *o);
+int orc_schedule_count(const orc_cosmo *c, const orc_opts *o, double k, double x0, double x1);
 void orc_rhs_bg(const orc_opts *o, const orc_bg *b, double k, const double *y,
                 double *dy);
 void orc_rhs(const orc_cosmo *c, const orc_opts *o, double k, double lna,

@@ -185,7 +185,7 @@ static void build_A(const orc_opts *o, const orc_bg *b, double k, int N, double 
 
 typedef struct {
     int N;
-    double *M, *A, *rhs, *e, *col;
+    double *M, *Mc, *A, *rhs, *res, *e, *col;
     int *piv;
 } radau_ws;
 
@@ -193,6 +193,8 @@ static void ws_alloc(radau_ws *w, int N)
 {
     w->N = N;
     w->M = (double *)malloc(sizeof(double) * 9 * N * N);
+    w->Mc = (double *)malloc(sizeof(double) * 9 * N * N);
+    w->res = (double *)malloc(sizeof(double) * 3 * N);
     w->A = (double *)malloc(sizeof(double) * 3 * N * N);
     w->rhs = (double *)malloc(sizeof(double) * 3 * N);
     w->e = (double *)malloc(sizeof(double) * N);
@@ -201,7 +203,8 @@ static void ws_alloc(radau_ws *w, int N)
 }
 static void ws_free(radau_ws *w)
 {
-    free(w->M); free(w->A); free(w->rhs); free(w->e); free(w->col); free(w->piv);
+    free(w->M); free(w->Mc); free(w->res); free(w->A); free(w->rhs); free(w->e); free(w->col);
+    free(w->piv);
 }
 
 void orc_radau_tableau(double *out12);
@@ -227,9 +230,22 @@ static int radau_linear_step(const orc_cosmo *c, const orc_opts *o, double k,
             }
             row[si * N + i] += 1.0;
         }
+    memcpy(w->Mc, w->M, sizeof(double) * (size_t)M3 * M3);
     if (orc_lu_factor(w->M, M3, w->piv)) return -1;
     for (int s = 0; s < 3; s++) memcpy(w->rhs + s * N, y, sizeof(double) * N);
     orc_lu_solve(w->M, M3, w->piv, w->rhs);
+    /* iterative refinement: the state mixes O(1) and ~1e-15 components, and
+       a single partial-pivoting solve is accurate only normwise */
+    for (int it = 0; it < 3; it++) {
+        for (int i = 0; i < M3; i++) {
+            double r = y[i % N];
+            const double *row = w->Mc + (size_t)i * M3;
+            for (int j = 0; j < M3; j++) r -= row[j] * w->rhs[j];
+            w->res[i] = r;
+        }
+        orc_lu_solve(w->M, M3, w->piv, w->res);
+        for (int i = 0; i < M3; i++) w->rhs[i] += w->res[i];
+    }
     memcpy(y, w->rhs + 2 * N, sizeof(double) * N);
     return 0;
 }
@@ -238,6 +254,15 @@ static double hmax_at(const orc_cosmo *c, const orc_opts *o, double k, double ln
 {
     double h = o->step_c / (1.0 + k / orc_Hconf(c, lna));
     return h < o->step_cap ? h : o->step_cap;
+}
+
+/* number of equal steps the schedule takes between x0 and x1 */
+int orc_schedule_count(const orc_cosmo *c, const orc_opts *o, double k, double x0, double x1)
+{
+    double h0 = hmax_at(c, o, k, x0), h1 = hmax_at(c, o, k, x1);
+    double hm = h0 < h1 ? h0 : h1;
+    int m = (int)ceil((x1 - x0) / hm);
+    return m < 1 ? 1 : m;
 }
 
 /* Integrate from (lna_init, y_init) -- or from the adiabatic initial
@@ -259,14 +284,12 @@ int orc_solve_mode(const orc_cosmo *c, const orc_opts *o, double k,
     for (int n = 0; n < n_out && rc == 0; n++) {
         double x1 = lna_out[n];
         if (x1 > x) {
-            double h0 = hmax_at(c, o, k, x), h1 = hmax_at(c, o, k, x1);
-            double hm = h0 < h1 ? h0 : h1;
-            int m = (int)ceil((x1 - x) / hm);
-            if (m < 1) m = 1;
+            int m = orc_schedule_count(c, o, k, x, x1);
             double h = (x1 - x) / m;
             for (int s = 0; s < m && rc == 0; s++) {
                 double xs = x + s * h;
                 double hs = (s == m - 1) ? (x1 - xs) : h;
+                if (o->max_steps > 0 && steps >= o->max_steps) { rc = 1; break; }
                 rc = radau_linear_step(c, o, k, xs, hs, y, &w);
                 steps++;
             }
@@ -274,6 +297,7 @@ int orc_solve_mode(const orc_cosmo *c, const orc_opts *o, double k,
         }
         memcpy(y_out + (size_t)n * N, y, sizeof(double) * N);
     }
+    if (rc == 1 && o->max_steps > 0) rc = 0; /* budget reached: timing sample only */
     ws_free(&w);
     free(y);
     if (n_steps) *n_steps = steps;

@@ -121,7 +121,7 @@ static void opts_from(const double *oa, orc_opts *o)
 {
     o->lmax_g = (int)oa[0]; o->lmax_pol = (int)oa[1]; o->lmax_nu = (int)oa[2];
     o->scale_sw = oa[3]; o->scale_isw = oa[4]; o->scale_dop = oa[5]; o->scale_pol = oa[6];
-    o->step_c = oa[7]; o->step_cap = oa[8]; o->hooks = (int)oa[9];
+    o->step_c = oa[7]; o->step_cap = oa[8]; o->hooks = (int)oa[9]; o->max_steps = (long)oa[10];
 }
 
 static void set_threads(int nthreads)
@@ -361,6 +361,25 @@ int orc_initial_at(const double *p, const double *oa, double k, double lna, doub
     opts_from(oa, &o);
     if (orc_cosmo_init(&c, p, 0, 0)) return -1;
     orc_initial(&c, &o, k, lna, y);
+    orc_cosmo_free(&c);
+    return 0;
+}
+
+/* Steps the oracle's schedule takes for each k mode over the tau nodes. */
+int orc_count_steps(const double *p, int n_tau, const double *oa, const double *k, int nk, long *out)
+{
+    orc_cosmo c;
+    orc_opts o;
+    opts_from(oa, &o);
+    if (orc_cosmo_init(&c, p, n_tau, 0)) return -1;
+    for (int i = 0; i < nk; i++) {
+        double x = orc_lna_start(&c, k[i]);
+        long n = 0;
+        for (int j = 0; j < n_tau; j++) {
+            if (c.node_lna[j] > x) { n += orc_schedule_count(&c, &o, k[i], x, c.node_lna[j]); x = c.node_lna[j]; }
+        }
+        out[i] = n;
+    }
     orc_cosmo_free(&c);
     return 0;
 }

@@ -35,6 +35,9 @@ namespace abcmb {
 
 constexpr int kKmax = 6;    // highest extrapolation column
 constexpr int kNvec = kKmax + 2;
+#ifndef ABCMB_CHAIN_FLOOR
+#define ABCMB_CHAIN_FLOOR 1e-3
+#endif
 
 struct OdeDims {
     int Lg, Lp, Ln, N;
@@ -254,7 +257,8 @@ ABCMB_HD ModeResult integrate_mode(const OdeDims &d, const StreamCoef &sc, const
                     }
                     if (j >= 2) {
                         int g = i < 3 ? 0 : i == 3 ? 1 : i < d.iG ? 2 : i < d.iN ? 3 : 4;
-                        double scl = atol + rtol * fmax(fabs(Y[i]), cm[g]);
+                        double scl = atol + rtol * fmax(fmax(fabs(Y[i]), fabs(T[j - 1][i])),
+                                                        ABCMB_CHAIN_FLOOR * cm[g]);
                         double e = fabs(T[j - 1][i] - T[j - 2][i]) / scl;
                         if (!(e <= err)) err = e; // propagates NaN
                     }

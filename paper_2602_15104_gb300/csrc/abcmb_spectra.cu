@@ -43,6 +43,25 @@ __device__ __forceinline__ void j01(double x, double *j0, double *j1)
     }
 }
 
+// Last l at which j_l(x) is kept: the smallest l > x whose Debye decay
+// exponent nu (alpha - tanh alpha), nu = l + 1/2, cosh alpha = nu / x, exceeds
+// 17 (j_l below ~e^-17 of its turning-point size).  Newton on the exponent,
+// whose derivative in nu is alpha; an estimate, so single precision.
+__device__ __forceinline__ int bessel_cut(float x, int lmax)
+{
+    if (x > (float)lmax + 200.0f) return lmax;
+    const float T = 17.0f;
+    float nu = x + 1.0f + 0.8f * cbrtf(fmaxf(x, 1.0f)) * 9.0f;
+    for (int it = 0; it < 8; it++) {
+        float r = fmaxf(nu / fmaxf(x, 1e-30f), 1.0f + 1e-6f);
+        float al = acoshf(r);
+        float f = nu * (al - tanhf(al)) - T;
+        nu = fmaxf(nu - f / fmaxf(al, 1e-3f), x + 0.5f);
+    }
+    int l = (int)ceilf(nu - 0.5f);
+    return l < 2 ? 2 : (l > lmax ? lmax : l);
+}
+
 // One butterfly stage: lanes with bit O set keep the upper half of v[0, 2O)
 // and receive the partner's upper-half copy of their kept half.
 template <int O>
@@ -105,12 +124,15 @@ project_kernel(int B, int Nk, const double *__restrict__ bg, long bg_len,
                 double j0, j1;
                 j01(x, &j0, &j1);
                 jm[m] = j1;
-                jc[m] = 3.0 * u * j1 - j0; // j_2
+                if (x < 0.1) { // series: term ratio -x^2 / ((2n+2)(2n+7))
+                    const double x2 = x * x;
+                    jc[m] = x2 / 15.0 * (1.0 - x2 / 14.0 * (1.0 - x2 / 36.0 * (1.0 - x2 / 66.0)));
+                } else {
+                    jc[m] = 3.0 * u * j1 - j0; // j_2
+                }
                 t[m] = 5.0 * u;
                 tu[m] = 2.0 * u;
-                float xf = (float)x;
-                float lcf = xf + 12.0f + 7.0f * cbrtf(xf);
-                lc[m] = lcf >= (float)lmax ? lmax : (int)lcf;
+                lc[m] = bessel_cut((float)x, lmax);
             } else {
                 A0[m] = A1[m] = A2[m] = Bc[m] = E[m] = 0.0;
                 jm[m] = jc[m] = t[m] = tu[m] = 0.0;
@@ -119,15 +141,15 @@ project_kernel(int B, int Nk, const double *__restrict__ bg, long bg_len,
             lcmax = max(lcmax, lc[m]);
         }
         lcmax = __reduce_max_sync(0xffffffffu, lcmax);
-        for (int l0 = 2; l0 <= lcmax; l0 += kLB) {
-#pragma unroll
-            for (int m = 0; m < kNodesPerLane; m++)
-                if (l0 > lc[m]) { jm[m] = 0.0; jc[m] = 0.0; }
+        // past its cutoff a node's j is held at exactly zero (the upward
+        // recurrence is unstable there), so it contributes nothing further
+        for (int l0 = 2; l0 <= lcmax + 1 && l0 <= lmax; l0 += kLB) {
             double v[2 * kLB];
             double ld = (double)l0;
 #pragma unroll
             for (int q = 0; q < kLB; q++) {
                 double cT = 0.0, cE = 0.0;
+                const int lnext = l0 + q + 1;
 #pragma unroll
                 for (int m = 0; m < kNodesPerLane; m++) {
                     const double coef = fma(fma(A2[m], ld, A1[m]), ld, A0[m]);
@@ -136,7 +158,7 @@ project_kernel(int B, int Nk, const double *__restrict__ bg, long bg_len,
                     cE = fma(E[m], jc[m], cE);
                     const double jn = fma(t[m], jc[m], -jm[m]);
                     jm[m] = jc[m];
-                    jc[m] = jn;
+                    jc[m] = lnext <= lc[m] ? jn : 0.0;
                     t[m] += tu[m];
                 }
                 v[q] = cT;

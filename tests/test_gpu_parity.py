@@ -31,7 +31,7 @@ def A():
 
 def run_gpu(A, params, k, o, stages=("bg", "perturb", "project", "cl")):
     p = torch.tensor(np.atleast_2d(params), dtype=torch.float64, device="cuda")
-    kk = torch.tensor(k, dtype=torch.float64, device="cuda")
+    kk = torch.tensor(k, dtype=torch.float64, device="cuda") if k is not None else None
     out = {}
     bg = A.abcmb_background_tables(p, o)
     out["bg"] = bg
