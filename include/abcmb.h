@@ -79,6 +79,10 @@ size_t abcmb_bg_doubles(const abcmb_options *o);
             ln a_j = ABCMB_BG_LNA0 + j / ABCMB_BG_PER_UNIT, 8 columns per node:
             1/(H tau_c), d/dln a of it, tau, dtau/dln a = 1/H, c_s^2,
             d c_s^2/dln a, kappa, x_e
+     [ABCMB_BG_ODETAB, + 18 * ABCMB_BG_NLNA) on the same grid, 9 (value,
+            d/dln a) pairs per node read by the ODE kernel: 1/H, 1/(H tau),
+            f_c, f_b, f_gamma, f_nu (rho_i / rho_tot), 1/(H tau_c),
+            (4 rho_g / 3 rho_b) / (H tau_c), c_s^2
      then 8 columns per tau node (n_tau nodes): ln a, tau, trapezoid weight,
             g, dg/dln a, e^-kappa, conformal H, dH/dln a                     */
 #define ABCMB_BG_NSCALAR 64
@@ -86,7 +90,8 @@ size_t abcmb_bg_doubles(const abcmb_options *o);
 #define ABCMB_BG_LNA0 (-18.0)
 #define ABCMB_BG_NLNA (18 * 1024 + 1)
 #define ABCMB_BG_TABLE ABCMB_BG_NSCALAR
-#define ABCMB_BG_NODES (ABCMB_BG_TABLE + 8 * ABCMB_BG_NLNA)
+#define ABCMB_BG_ODETAB (ABCMB_BG_TABLE + 8 * ABCMB_BG_NLNA)
+#define ABCMB_BG_NODES (ABCMB_BG_ODETAB + 18 * ABCMB_BG_NLNA)
 
 enum {
     ABCMB_S_STATUS = 0, ABCMB_S_H0, ABCMB_S_OMB, ABCMB_S_OMC, ABCMB_S_OMG, ABCMB_S_OMNU,

@@ -54,7 +54,11 @@ constexpr double kTnuRatio = 0.71636856;
 constexpr double kNnu = 3.0;
 constexpr double kZreHe = 3.5, kDzReHe = 0.5, kDzRe = 0.5, kBetaRe = 1.5;
 constexpr double kRtc = 1.5e-3, kRlarge = 7e-2, kKpivot = 0.05;
-constexpr double kLna700 = -6.552507968010906; // ln(1/701)
+constexpr double kLna700 = -6.55250788703459; // ln(1/701)
+// RK4 steps of the TLA in ln a: fine through the stiff transient after the
+// Saha switch, one table cell afterwards
+constexpr double kTlaFine = 0.125 / ABCMB_BG_PER_UNIT;
+constexpr double kTlaFineSpan = 0.05;
 
 constexpr int kNlna = ABCMB_BG_NLNA;
 constexpr double kLna0 = ABCMB_BG_LNA0;
@@ -334,24 +338,83 @@ ABCMB_HD double bisect(F f, double target, double lo, double hi, bool *ok)
     return 0.5 * (lo + hi);
 }
 
-// ---- the builder ----
-ABCMB_HD void build_background(const double *p, double *rec, int n_tau)
+
+// ---- lane helpers: on the device the builder runs on one warp per cosmology,
+// on a host (debugging) on one thread ----
+ABCMB_HD double lane_sum(double v)
 {
-    for (int i = 0; i < ABCMB_BG_NSCALAR; i++) rec[i] = 0.0;
+#ifdef __CUDA_ARCH__
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+#endif
+    return v;
+}
+
+// sum of v over lanes below (dir > 0) or above (dir < 0) this one, in lane order
+ABCMB_HD double lane_scan_excl(double v, int lane, int dir)
+{
+    double acc = 0.0;
+#ifdef __CUDA_ARCH__
+    for (int s = 0; s < 32; s++) {
+        const int src = dir > 0 ? s : 31 - s;
+        const double t = __shfl_sync(0xffffffffu, v, src);
+        if (dir > 0 ? src < lane : src > lane) acc += t;
+    }
+#else
+    (void)v; (void)lane; (void)dir;
+#endif
+    return acc;
+}
+
+ABCMB_HD void lane_sync()
+{
+#ifdef __CUDA_ARCH__
+    __syncwarp();
+#endif
+}
+
+// optical depth of the reionization electrons alone for a trial z_reion,
+// composite Gauss-Legendre split over the lanes
+ABCMB_HD double tau_reion_par(const Cosmo &c, double zre, int lane, int nl)
+{
+    const double dy = kBetaRe * kDzRe * pow(1.0 + zre, kBetaRe - 1.0);
+    const double yre = pow(1.0 + zre, kBetaRe);
+    double zmax = pow(yre + 25.0 * dy, 1.0 / kBetaRe) - 1.0;
+    const double zhe = kZreHe + 25.0 * kDzReHe;
+    if (zhe > zmax) zmax = zhe;
+    const double lo = -log(1.0 + zmax);
+    const int np = 800;
+    const double hp = -lo / np;
+    double acc = 0.0;
+    for (int pnl = lane; pnl < np; pnl += nl)
+        for (int q = 0; q < 4; q++) {
+            const double lna = lo + hp * (pnl + 0.5 * (1.0 + gl4_x(q)));
+            const double z = exp(-lna) - 1.0;
+            const double S1 = 0.5 * (1.0 + tanh((yre - pow(1.0 + z, kBetaRe)) / dy));
+            const double S2 = 0.5 * (1.0 + tanh((kZreHe - z) / kDzReHe));
+            acc += 0.5 * hp * gl4_w(q) * ((1.0 + c.f_He) * S1 + c.f_He * S2) * nuT_closed(c, lna, 1.0);
+        }
+    return lane_sum(acc);
+}
+
+// ---- the builder (lane = 0..nl-1 of the warp that owns this cosmology) ----
+ABCMB_HD void build_background(const double *p, double *rec, int n_tau, int lane, int nl)
+{
     double *tab = rec + ABCMB_BG_TABLE;
+    double *otab = rec + ABCMB_BG_ODETAB;
     double *nodes = rec + ABCMB_BG_NODES;
     int status = ABCMB_OK;
     bool ok = true;
 
+    // derived parameters (every lane, identically)
     Cosmo c;
-    double h = p[2], h2 = h * h;
+    const double h = p[2], h2 = h * h;
     c.H0 = h * 1.0e7 / kC;
-    double H100 = 1.0e7 / kMpc;
-    double rho_crit100 = 3.0 * H100 * H100 / (8.0 * kPi * kG) * kC * kC / kEvErg;
-    double T0 = kTcmb0, Tn = kTnuRatio * kTcmb0;
-    double hbc3 = kHbarC * kHbarC * kHbarC;
+    const double H100 = 1.0e7 / kMpc;
+    const double rho_crit100 = 3.0 * H100 * H100 / (8.0 * kPi * kG) * kC * kC / kEvErg;
+    const double T0 = kTcmb0, Tn = kTnuRatio * kTcmb0;
+    const double hbc3 = kHbarC * kHbarC * kHbarC;
     c.rho_g0 = kPi * kPi / 15.0 * T0 * T0 * T0 * T0 / hbc3;
-    double rho_nu0 = kNnu * 7.0 * kPi * kPi / 120.0 * Tn * Tn * Tn * Tn / hbc3;
+    const double rho_nu0 = kNnu * 7.0 * kPi * kPi / 120.0 * Tn * Tn * Tn * Tn / hbc3;
     c.Om_b = p[0] / h2;
     c.Om_c = p[1] / h2;
     c.Om_g = c.rho_g0 / (rho_crit100 * h2);
@@ -366,26 +429,39 @@ ABCMB_HD void build_background(const double *p, double *rec, int n_tau)
     c.n_s = p[3];
 
     // helium and hydrogen phase switches
-    c.lna_He3 = bisect([&](double l) { double d; double a = exp(l); (void)a;
-                           double dls; double s = saha_s(c, exp(l), kEHe2, mu_eHe(), 1.0, &dls);
+    c.lna_He3 = bisect([&](double l) { double d, dls;
+                           double s = saha_s(c, exp(l), kEHe2, mu_eHe(), 1.0, &dls);
                            return saha_root(s, c.f_He, 1.0 + c.f_He, dls, &d); },
                        1e-9, -12.0, -5.0, &ok);
     if (!ok) status = ABCMB_E_BACKGROUND;
     c.lna_sw = bisect([&](double l) { double d; return xp_saha(c, l, &d); }, 0.99, -9.0, -6.0, &ok);
     if (!ok) status = ABCMB_E_BACKGROUND;
 
-    // Peebles TLA (x_p, then also T_m below z = 700), RK4 with four
-    // substeps per table cell, stored at the table nodes at and after lna_sw
+    // reionization redshift from tau_reion (lane-parallel quadrature, every
+    // lane takes the same bisection path)
     {
+        double lo = 0.0, hi = 60.0;
+        if (tau_reion_par(c, hi, lane, nl) < p[5] || tau_reion_par(c, lo, lane, nl) > p[5])
+            status = ABCMB_E_BACKGROUND;
+        for (int it = 0; it < 80; it++) {
+            const double mid = 0.5 * (lo + hi);
+            if (tau_reion_par(c, mid, lane, nl) < p[5]) lo = mid; else hi = mid;
+        }
+        c.z_reion = 0.5 * (lo + hi);
+    }
+
+    // Peebles TLA (x_p, then also T_m below z = 700), RK4, stored at the table
+    // nodes at and after lna_sw: sequential, on lane 0
+    if (lane == 0) {
         double dum;
-        int j0 = (int)ceil((c.lna_sw - kLna0) * ABCMB_BG_PER_UNIT);
+        const int j0 = (int)ceil((c.lna_sw - kLna0) * ABCMB_BG_PER_UNIT);
         double x = c.lna_sw;
         double y0 = xp_saha(c, x, &dum), y1 = 0.0;
         bool two = false;
         for (int j = j0; j < kNlna; j++) {
-            double target = kLna0 + j * kDlna;
+            const double target = kLna0 + j * kDlna;
             while (x < target) {
-                double hs = 0.25 * kDlna;
+                double hs = (x - c.lna_sw < kTlaFineSpan) ? kTlaFine : kDlna;
                 if (target - x < hs * (1.0 + 1e-9)) hs = target - x;
                 bool hit700 = false;
                 if (!two && x < kLna700 && x + hs >= kLna700) { hs = kLna700 - x; hit700 = true; }
@@ -399,7 +475,7 @@ ABCMB_HD void build_background(const double *p, double *rec, int n_tau)
                 if (hit700) {
                     x = kLna700;
                     two = true;
-                    double xe = y0 + x_he(c, x, &dum);
+                    const double xe = y0 + x_he(c, x, &dum);
                     y1 = kTcmb0 * exp(-x) * (1.0 - H_sec(c, x) / gamma_C(c, exp(x), xe));
                 } else {
                     x += hs;
@@ -409,123 +485,157 @@ ABCMB_HD void build_background(const double *p, double *rec, int n_tau)
             double dxp, dTm;
             tla_rhs(c, target, y0, y1, two, &dxp, &dTm);
             double *r = tab + 8 * j;
-            r[C_XE] = y0;      // temporarily x_p
-            r[C_KAPPA] = dxp;  // temporarily dx_p/dln a
-            r[C_CS2] = y1;     // temporarily T_m (z < 700)
-            r[C_DCS2] = dTm;   // temporarily dT_m/dln a
+            r[C_XE] = y0;     // temporarily x_p
+            r[C_KAPPA] = dxp; // temporarily dx_p/dln a
+            r[C_CS2] = y1;    // temporarily T_m (z < 700)
+            r[C_DCS2] = dTm;  // temporarily dT_m/dln a
         }
     }
+    lane_sync();
 
-    // reionization redshift
+    // table: x_e, 1/(H tau_c), c_s^2, 1/H (lane-parallel)
     {
-        double lo = 0.0, hi = 60.0;
-        if (tau_reion_trial(c, hi) < p[5] || tau_reion_trial(c, lo) > p[5]) status = ABCMB_E_BACKGROUND;
-        for (int it = 0; it < 80; it++) {
-            double mid = 0.5 * (lo + hi);
-            if (tau_reion_trial(c, mid) < p[5]) lo = mid; else hi = mid;
-        }
-        c.z_reion = 0.5 * (lo + hi);
-    }
-
-    // table: x_e, 1/(H tau_c), c_s^2, 1/H
-    {
-        double yre = pow(1.0 + c.z_reion, kBetaRe);
-        double dyre = kBetaRe * kDzRe * pow(1.0 + c.z_reion, kBetaRe - 1.0);
-        for (int j = 0; j < kNlna; j++) {
-            double lna = kLna0 + j * kDlna;
+        const double yre = pow(1.0 + c.z_reion, kBetaRe);
+        const double dyre = kBetaRe * kDzRe * pow(1.0 + c.z_reion, kBetaRe - 1.0);
+        for (int j = lane; j < kNlna; j += nl) {
+            const double lna = kLna0 + j * kDlna;
             double *r = tab + 8 * j;
-            BgClosed b = closed_bg(c, lna);
-            double xp, dxp, xh, dxh;
+            const BgClosed b = closed_bg(c, lna);
+            double xp, dxp, dxh;
             if (lna < c.lna_sw) xp = xp_saha(c, lna, &dxp);
             else { xp = r[C_XE]; dxp = r[C_KAPPA]; }
-            xh = x_he(c, lna, &dxh);
-            double xr = xp + xh, dxr = dxp + dxh;
+            const double xh = x_he(c, lna, &dxh);
+            const double xr = xp + xh, dxr = dxp + dxh;
             double Tm, dlnTm;
             if (lna < kLna700) Tm = tm_qs(c, lna, xr, dxr, &dlnTm);
             else { Tm = r[C_CS2]; dlnTm = r[C_DCS2] / Tm; }
-            double z = b.inv_a - 1.0;
-            double y = pow(1.0 + z, kBetaRe);
-            double t1 = tanh((yre - y) / dyre), t2 = tanh((kZreHe - z) / kDzReHe);
-            double S1 = 0.5 * (1.0 + t1), S2 = 0.5 * (1.0 + t2);
-            double dS1 = 0.5 * (1.0 - t1 * t1) * kBetaRe * y / dyre;
-            double dS2 = 0.5 * (1.0 - t2 * t2) * (1.0 + z) / kDzReHe;
-            double xe = xr + (1.0 + c.f_He - xr) * S1 + c.f_He * S2;
-            double dxe = dxr * (1.0 - S1) + (1.0 + c.f_He - xr) * dS1 + c.f_He * dS2;
-            double nuT = xe * c.nH0 * kSigmaT * kMpc * b.inv_a * b.inv_a / b.Hc;
-            double mub = kMH / ((1.0 + xe) * (1.0 - kYHe) + kYHe / kMHeOverMH);
+            const double z = b.inv_a - 1.0;
+            const double y = pow(1.0 + z, kBetaRe);
+            const double t1 = tanh((yre - y) / dyre), t2 = tanh((kZreHe - z) / kDzReHe);
+            const double S1 = 0.5 * (1.0 + t1), S2 = 0.5 * (1.0 + t2);
+            const double dS1 = 0.5 * (1.0 - t1 * t1) * kBetaRe * y / dyre;
+            const double dS2 = 0.5 * (1.0 - t2 * t2) * (1.0 + z) / kDzReHe;
+            const double xe = xr + (1.0 + c.f_He - xr) * S1 + c.f_He * S2;
+            const double dxe = dxr * (1.0 - S1) + (1.0 + c.f_He - xr) * dS1 + c.f_He * dS2;
+            const double nuT = xe * c.nH0 * kSigmaT * kMpc * b.inv_a * b.inv_a / b.Hc;
+            const double mub = kMH / ((1.0 + xe) * (1.0 - kYHe) + kYHe / kMHeOverMH);
             r[C_NUT] = nuT;
             r[C_DNUT] = nuT * (dxe / xe - 2.0 - b.dlnHc);
             r[C_CS2] = Tm / mub * (1.0 - dlnTm / 3.0);
             r[C_DTAU] = 1.0 / b.Hc;
             r[C_XE] = xe;
         }
-        for (int j = 0; j < kNlna; j++) {
-            int jl = j > 0 ? j - 1 : j, jh = j < kNlna - 1 ? j + 1 : j;
-            tab[8 * j + C_DCS2] = (tab[8 * jh + C_CS2] - tab[8 * jl + C_CS2]) / ((jh - jl) * kDlna);
-        }
+    }
+    lane_sync();
+    for (int j = lane; j < kNlna; j += nl) {
+        const int jl = j > 0 ? j - 1 : j, jh = j < kNlna - 1 ? j + 1 : j;
+        tab[8 * j + C_DCS2] = (tab[8 * jh + C_CS2] - tab[8 * jl + C_CS2]) / ((jh - jl) * kDlna);
     }
 
-    // conformal time: closed radiation+matter part plus the Lambda correction
+    // conformal time: closed radiation+matter part plus the cumulative Lambda
+    // correction; kappa: suffix sums of the exact cell integrals of the cubic
+    // Hermite interpolant of 1/(H tau_c).  Cells are split into one
+    // contiguous chunk per lane, chunk totals combined in lane order.
     {
-        double corr = 0.0;
-        for (int j = 0; j < kNlna; j++) {
-            double lna = kLna0 + j * kDlna;
-            if (j > 0) {
-                double l0 = lna - kDlna;
-                for (int q = 0; q < 4; q++) {
-                    double l = l0 + 0.5 * kDlna * (1.0 + gl4_x(q));
-                    double a = exp(l);
-                    double hrm = c.H0 * sqrt(c.Om_r / (a * a) + c.Om_m / a);
-                    corr += 0.5 * kDlna * gl4_w(q) * (1.0 / hconf(c, l) - 1.0 / hrm);
-                }
+        const int ncell = kNlna - 1;
+        const int chunk = (ncell + nl - 1) / nl;
+        const int c0 = lane * chunk, c1 = c0 + chunk < ncell ? c0 + chunk : ncell;
+        double run = 0.0;
+        for (int cell = c0; cell < c1; cell++) {
+            const double l0 = kLna0 + cell * kDlna;
+            for (int q = 0; q < 4; q++) {
+                const double l = l0 + 0.5 * kDlna * (1.0 + gl4_x(q));
+                const double a = exp(l);
+                const double hrm = c.H0 * sqrt(c.Om_r / (a * a) + c.Om_m / a);
+                run += 0.5 * kDlna * gl4_w(q) * (1.0 / hconf(c, l) - 1.0 / hrm);
             }
-            tab[8 * j + C_TAU] = tau_rm(c, exp(lna)) + corr;
+            tab[8 * (cell + 1) + C_TAU] = run; // partial, within the chunk
         }
-        c.tau0 = tab[8 * (kNlna - 1) + C_TAU];
+        const double off = lane_scan_excl(run, lane, +1);
+        lane_sync();
+        for (int cell = c0; cell < c1; cell++) {
+            const double lna = kLna0 + (cell + 1) * kDlna;
+            tab[8 * (cell + 1) + C_TAU] += off + tau_rm(c, exp(lna));
+        }
+        if (lane == 0) tab[C_TAU] = tau_rm(c, exp(kLna0));
+        lane_sync();
+        // kappa
+        double srun = 0.0;
+        for (int cell = c1 - 1; cell >= c0; cell--) {
+            const double *r0 = tab + 8 * cell, *r1 = r0 + 8;
+            srun += 0.5 * kDlna * (r0[C_NUT] + r1[C_NUT]) + kDlna * kDlna / 12.0 * (r0[C_DNUT] - r1[C_DNUT]);
+            tab[8 * cell + C_KAPPA] = srun; // partial, within the chunk
+        }
+        const double soff = lane_scan_excl(srun, lane, -1);
+        lane_sync();
+        for (int cell = c0; cell < c1; cell++) tab[8 * cell + C_KAPPA] += soff;
+        if (lane == 0) tab[8 * (kNlna - 1) + C_KAPPA] = 0.0;
+        lane_sync();
+    }
+    c.tau0 = tab[8 * (kNlna - 1) + C_TAU];
+
+    // ODE table: (value, d/dln a) pairs of 1/H, 1/(H tau), f_c, f_b, f_g,
+    // f_nu, 1/(H tau_c), R^-1/(H tau_c), c_s^2
+    for (int j = lane; j < kNlna; j += nl) {
+        const double lna = kLna0 + j * kDlna;
+        const BgClosed b = closed_bg(c, lna);
+        const double *r = tab + 8 * j;
+        double *o = otab + 18 * j;
+        const double ih = 1.0 / b.Hc, iht = ih / r[C_TAU];
+        const double dlnE2 = 2.0 * (b.dlnHc - 1.0);
+        const double Rinv = (4.0 / 3.0) * (c.Om_g / c.Om_b) * b.inv_a;
+        o[0] = ih;
+        o[1] = -ih * b.dlnHc;
+        o[2] = iht;
+        o[3] = iht * (-b.dlnHc - iht);
+        o[4] = b.fc;
+        o[5] = b.fc * (-3.0 - dlnE2);
+        o[6] = b.fb;
+        o[7] = b.fb * (-3.0 - dlnE2);
+        o[8] = b.fg;
+        o[9] = b.fg * (-4.0 - dlnE2);
+        o[10] = b.fnu;
+        o[11] = b.fnu * (-4.0 - dlnE2);
+        o[12] = r[C_NUT];
+        o[13] = r[C_DNUT];
+        o[14] = Rinv * r[C_NUT];
+        o[15] = Rinv * (r[C_DNUT] - r[C_NUT]);
+        o[16] = r[C_CS2];
+        o[17] = r[C_DCS2];
     }
 
-    // optical depth: exact integral of the Hermite interpolant of 1/(H tau_c)
-    {
-        tab[8 * (kNlna - 1) + C_KAPPA] = 0.0;
-        for (int j = kNlna - 2; j >= 0; j--) {
-            const double *r0 = tab + 8 * j, *r1 = r0 + 8;
-            double cell = 0.5 * kDlna * (r0[C_NUT] + r1[C_NUT])
-                        + kDlna * kDlna / 12.0 * (r0[C_DNUT] - r1[C_DNUT]);
-            tab[8 * j + C_KAPPA] = r1[C_KAPPA] + cell;
-        }
-    }
-
-    // tight-coupling start: H tau_c = R_tc
+    // tight-coupling start: H tau_c = R_tc (every lane, identically)
     c.lna_tc = bisect([&](double l) { Herm H = herm_at(l); return -herm_val(tab, H, C_NUT, C_DNUT); },
                       -1.0 / kRtc, kLna0 + 1.0, -3.0, &ok);
     if (!ok) status = ABCMB_E_BACKGROUND;
 
-    // tau nodes
+    // tau nodes (lane-parallel)
+    double node_fail = 0.0;
     if (n_tau >= 8) {
-        int nA = n_tau / 4, nB = n_tau / 2, nC = n_tau - nA - nB;
-        double l1300 = -log(1301.0), l900 = -log(901.0);
-        Herm H9 = herm_at(l900);
-        double t900 = herm_val(tab, H9, C_TAU, C_DTAU);
-        for (int i = 0; i < n_tau; i++) {
+        const int nA = n_tau / 4, nB = n_tau / 2, nC = n_tau - nA - nB;
+        const double l1300 = -log(1301.0), l900 = -log(901.0);
+        const Herm H9 = herm_at(l900);
+        const double t900 = herm_val(tab, H9, C_TAU, C_DTAU);
+        for (int i = lane; i < n_tau; i += nl) {
             double lna;
             if (i < nA) lna = c.lna_tc + (l1300 - c.lna_tc) * i / nA;
             else if (i < nA + nB) lna = -log(1.0 + 1300.0 - 400.0 * (i - nA) / nB);
             else {
-                int jc = i - nA - nB;
-                double tt = t900 + (c.tau0 - t900) * jc / nC;
+                const int jc = i - nA - nB;
+                const double tt = t900 + (c.tau0 - t900) * jc / nC;
                 bool ok2 = true;
                 lna = jc == 0 ? l900
                     : bisect([&](double l) { Herm H = herm_at(l); return herm_val(tab, H, C_TAU, C_DTAU); },
                              tt, l900, 0.0, &ok2);
-                if (!ok2) status = ABCMB_E_BACKGROUND;
+                if (!ok2) node_fail = 1.0;
             }
-            Herm H = herm_at(lna);
-            BgClosed b = closed_bg(c, lna);
-            double nu = herm_val(tab, H, C_NUT, C_DNUT);
-            double dnu = herm_der(tab, H, C_NUT, C_DNUT);
-            double kap = herm_val(tab, H, C_KAPPA, C_NUT, -1.0);
-            double emk = exp(-kap);
-            double g = b.Hc * nu * emk;
+            const Herm H = herm_at(lna);
+            const BgClosed b = closed_bg(c, lna);
+            const double nu = herm_val(tab, H, C_NUT, C_DNUT);
+            const double dnu = herm_der(tab, H, C_NUT, C_DNUT);
+            const double kap = herm_val(tab, H, C_KAPPA, C_NUT, -1.0);
+            const double emk = exp(-kap);
+            const double g = b.Hc * nu * emk;
             double *nd = nodes + 8 * i;
             nd[N_LNA] = lna;
             nd[N_TAU] = herm_val(tab, H, C_TAU, C_DTAU);
@@ -535,35 +645,40 @@ ABCMB_HD void build_background(const double *p, double *rec, int n_tau)
             nd[N_HC] = b.Hc;
             nd[N_DHC] = b.Hc * b.dlnHc;
         }
-        for (int i = 0; i < n_tau; i++) {
-            double lo = nodes[8 * (i > 0 ? i - 1 : i) + N_TAU];
-            double hi = nodes[8 * (i < n_tau - 1 ? i + 1 : i) + N_TAU];
+        lane_sync();
+        for (int i = lane; i < n_tau; i += nl) {
+            const double lo = nodes[8 * (i > 0 ? i - 1 : i) + N_TAU];
+            const double hi = nodes[8 * (i < n_tau - 1 ? i + 1 : i) + N_TAU];
             nodes[8 * i + N_W] = 0.5 * (hi - lo);
         }
     }
+    if (lane_sum(node_fail) > 0.0 && status == ABCMB_OK) status = ABCMB_E_BACKGROUND;
 
     if (!(c.tau0 > 0.0 && c.tau0 < 1e6) || !(c.lna_tc < 0.0)) {
         if (status == ABCMB_OK) status = ABCMB_E_NONFINITE;
     }
-    rec[ABCMB_S_STATUS] = status;
-    rec[ABCMB_S_H0] = c.H0;
-    rec[ABCMB_S_OMB] = c.Om_b;
-    rec[ABCMB_S_OMC] = c.Om_c;
-    rec[ABCMB_S_OMG] = c.Om_g;
-    rec[ABCMB_S_OMNU] = c.Om_nu;
-    rec[ABCMB_S_OML] = c.Om_L;
-    rec[ABCMB_S_RNU] = c.R_nu;
-    rec[ABCMB_S_FHE] = c.f_He;
-    rec[ABCMB_S_NH0] = c.nH0;
-    rec[ABCMB_S_AS] = c.A_s;
-    rec[ABCMB_S_NS] = c.n_s;
-    rec[ABCMB_S_ZREION] = c.z_reion;
-    rec[ABCMB_S_LNA_TC] = c.lna_tc;
-    rec[ABCMB_S_LNA_SW] = c.lna_sw;
-    rec[ABCMB_S_TAU0] = c.tau0;
-    rec[ABCMB_S_LNA_HE3] = c.lna_He3;
-    rec[ABCMB_S_LNA_700] = kLna700;
-    rec[ABCMB_S_NTAU] = n_tau;
+    if (lane == 0) {
+        for (int i = ABCMB_S_COUNT; i < ABCMB_BG_NSCALAR; i++) rec[i] = 0.0;
+        rec[ABCMB_S_STATUS] = status;
+        rec[ABCMB_S_H0] = c.H0;
+        rec[ABCMB_S_OMB] = c.Om_b;
+        rec[ABCMB_S_OMC] = c.Om_c;
+        rec[ABCMB_S_OMG] = c.Om_g;
+        rec[ABCMB_S_OMNU] = c.Om_nu;
+        rec[ABCMB_S_OML] = c.Om_L;
+        rec[ABCMB_S_RNU] = c.R_nu;
+        rec[ABCMB_S_FHE] = c.f_He;
+        rec[ABCMB_S_NH0] = c.nH0;
+        rec[ABCMB_S_AS] = c.A_s;
+        rec[ABCMB_S_NS] = c.n_s;
+        rec[ABCMB_S_ZREION] = c.z_reion;
+        rec[ABCMB_S_LNA_TC] = c.lna_tc;
+        rec[ABCMB_S_LNA_SW] = c.lna_sw;
+        rec[ABCMB_S_TAU0] = c.tau0;
+        rec[ABCMB_S_LNA_HE3] = c.lna_He3;
+        rec[ABCMB_S_LNA_700] = kLna700;
+        rec[ABCMB_S_NTAU] = n_tau;
+    }
 }
 
 } // namespace abcmb

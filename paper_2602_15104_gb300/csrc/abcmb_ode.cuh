@@ -19,14 +19,18 @@
 // (the -(9/10) sigma and (1/20)(G_0 + G_2) of App. C.4 in F_2 form, and the
 // polarization source read as Pi (delta_l0 + delta_l2 / 5) / 2).
 //
-// Integrator: linearly implicit (IMEX) Euler with the Thomson terms implicit
-// -- they are the only stiff terms and form a 2x2 block (theta_b, F_g1), a
-// rank-one-plus-diagonal 3x3 block (F_g2, G_0, G_2) and a diagonal -- and
-// everything else explicit; Aitken-Neville extrapolation over the harmonic
-// substep sequence 1, 2, ..., K raises the order, the difference of the two
-// highest orders is the error estimate, the step is accepted at the first
-// column that meets the tolerance.  Steps land exactly on every tau node,
-// where the sources are evaluated (App. B.4, eq. source_functions).
+// Integrator, two regimes (both extrapolation methods, no tableau constants):
+//  * while 1/(H tau_c) >= 1 (up to recombination): linearly implicit (IMEX)
+//    Euler with the Thomson terms implicit -- they are the only stiff terms
+//    and form a 2x2 block (theta_b, F_g1), a rank-one-plus-diagonal 3x3 block
+//    (F_g2, G_0, G_2) and a diagonal -- and everything else explicit;
+//    Aitken-Neville extrapolation in h over the substep counts 1, 2, ..., K;
+//  * afterwards (free streaming, non-stiff): explicit midpoint rule
+//    (Gragg) with 2, 4, ..., 2K substeps extrapolated in h^2 (GBS).
+// The difference of the two highest orders is the error estimate; a step is
+// accepted at the first column that meets the tolerance.  Steps land exactly
+// on every tau node, where the sources are evaluated (App. B.4, eq.
+// source_functions).
 #pragma once
 
 #include "abcmb_bg.cuh"
@@ -35,9 +39,20 @@ namespace abcmb {
 
 constexpr int kKmax = 6;    // highest extrapolation column
 constexpr int kNvec = kKmax + 2;
+// Error scale of component i: atol + rtol max(|y_i|, kChainFloor * m_g), m_g
+// the largest magnitude in i's group at the step start; groups: {eta, delta_c,
+// delta_b}, {theta_b}, photons {F_g, G} together, neutrinos {F_n}.  Sharing
+// the photon group keeps the tiny tight-coupled polarization moments from
+// dictating the step in the stiff early era.
 #ifndef ABCMB_CHAIN_FLOOR
-#define ABCMB_CHAIN_FLOOR 1e-3
+#define ABCMB_CHAIN_FLOOR 1e-4
 #endif
+// Explicit Gragg-Bulirsch-Stoer steps once 1/(H tau_c) < kNuNonStiff (after
+// recombination); while H 1/(H tau_c) > kSlavedHnu the photon moments l >= 2
+// and the polarization moments are slaved to the slow variables (their local
+// errors are damped by 1/(1 + h nu) every substep) and leave the error norm.
+constexpr double kNuNonStiff = 1.0;
+constexpr double kSlavedHnu = 100.0;
 
 struct OdeDims {
     int Lg, Lp, Ln, N;
@@ -125,6 +140,47 @@ ABCMB_HD void imex_substep(const OdeDims &d, const StreamCoef &sc, double k, dou
     for (int l = 3; l <= d.Lp; l++) y[d.iG + l] *= dmp;
 }
 
+
+// dst += fac * f(x, src), full right-hand side with the Thomson terms explicit
+ABCMB_HD void rhs_axpy(const OdeDims &d, const StreamCoef &sc, double k, const BgPt &b, Vec src, Vec dst,
+                       double fac)
+{
+    const double kH = k * b.inv_Hc;
+    const double eta = src[0], dc = src[1], db = src[2], tb = src[3];
+    const double Fg0 = src[d.iF], Fg1 = src[d.iF + 1], Fn0 = src[d.iN], Fn1 = src[d.iN + 1];
+    const double hp = 2.0 * kH * kH * eta + 3.0 * (b.fc * dc + b.fb * db + b.fg * Fg0 + b.fnu * Fn0);
+    const double ep = 1.5 / kH * (b.fb * tb / k + b.fg * Fg1 + b.fnu * Fn1);
+    const double nu = b.nuT;
+    dst[0] += fac * ep;
+    dst[1] += fac * (-0.5 * hp);
+    dst[2] += fac * (-tb * b.inv_Hc - 0.5 * hp);
+    dst[3] += fac * (-tb + b.cs2 * k * k * db * b.inv_Hc + b.Rinv * nu * (0.75 * k * Fg1 - tb));
+    const double trunc = b.inv_Hc / b.tau;
+    const double Pi = src[d.iF + 2] + src[d.iG] + src[d.iG + 2];
+    for (int ch = 0; ch < 3; ch++) {
+        const int i0 = ch == 0 ? d.iF : ch == 1 ? d.iG : d.iN;
+        const int L = ch == 0 ? d.Lg : ch == 1 ? d.Lp : d.Ln;
+        const double damp = ch == 2 ? 0.0 : nu;
+        double prev = 0.0;
+        for (int l = 0; l < L; l++) {
+            const double cur = src[i0 + l];
+            double v = kH * (sc.a[l] * prev - sc.b[l] * src[i0 + l + 1]) - damp * cur;
+            dst[i0 + l] += fac * v;
+            prev = cur;
+        }
+        const double cur = src[i0 + L];
+        dst[i0 + L] += fac * (kH * prev - (L + 1.0) * trunc * cur - damp * cur);
+    }
+    // corrections: photon F_0 has no damping, F_1 couples to theta_b, Pi sources
+    dst[d.iF] += fac * (nu * Fg0 - (2.0 / 3.0) * hp);
+    dst[d.iF + 1] += fac * nu * (4.0 / 3.0) * tb / k;
+    dst[d.iF + 2] += fac * (0.1 * nu * Pi + (4.0 / 15.0) * hp + 1.6 * ep);
+    dst[d.iG] += fac * 0.5 * nu * Pi;
+    dst[d.iG + 2] += fac * 0.1 * nu * Pi;
+    dst[d.iN] += fac * (-(2.0 / 3.0) * hp);
+    dst[d.iN + 2] += fac * ((4.0 / 15.0) * hp + 1.6 * ep);
+}
+
 ABCMB_HD void initial_state(const OdeDims &d, const Cosmo &c, double k, double tau_i, Vec y)
 {
     for (int i = 0; i < d.N; i++) y[i] = 0.0;
@@ -210,6 +266,17 @@ ABCMB_HD ModeResult integrate_mode(const OdeDims &d, const StreamCoef &sc, const
     }
     double h = 1e-3;
     int node = 0;
+    // non-stiff switch: where 1/(H tau_c) falls below kNuNonStiff after recombination
+    double x_ns = 0.0;
+    {
+        double lo = c.lna_sw, hi = -2.0;
+        for (int it = 0; it < 60; it++) {
+            double mid = 0.5 * (lo + hi);
+            Herm Hm = herm_at(mid);
+            if (herm_val(tab, Hm, C_NUT, C_DNUT) > kNuNonStiff) lo = mid; else hi = mid;
+        }
+        x_ns = hi;
+    }
     while (node < n_tau) {
         const double xn = nodes[8 * node + N_LNA];
         double H = h;
@@ -221,7 +288,7 @@ ABCMB_HD ModeResult integrate_mode(const OdeDims &d, const StreamCoef &sc, const
             // per-chain magnitudes for the error scale
             double cm[5] = {0, 0, 0, 0, 0};
             for (int i = 0; i < d.N; i++) {
-                int g = i < 3 ? 0 : i == 3 ? 1 : i < d.iG ? 2 : i < d.iN ? 3 : 4;
+                int g = i < 3 ? 0 : i == 3 ? 1 : i < d.iN ? 2 : 4;
                 double v = fabs(Y[i]);
                 if (v > cm[g]) cm[g] = v;
             }
@@ -229,7 +296,45 @@ ABCMB_HD ModeResult integrate_mode(const OdeDims &d, const StreamCoef &sc, const
             BgPt bend;
             double err = 0.0;
             int jacc = 0;
+            const bool gbs = x >= x_ns;
+            const bool slaved = H * b0.nuT > kSlavedHnu;
             for (int j = 1; j <= kKmax; j++) {
+              if (gbs) {
+                const int n = 2 * j;
+                const double hs = H / n;
+                res.substeps += n;
+                for (int i = 0; i < d.N; i++) { YS[i] = Y[i]; T[kKmax - 1][i] = Y[i]; }
+                // YS = z0, TK = z1 = z0 + hs f(z0)
+                Vec za = YS, zb = T[kKmax - 1];
+                rhs_axpy(d, sc, k, b0, za, zb, hs);
+                for (int m = 1; m < n; m++) {
+                    BgPt bm = bg_point(c, tab, x + m * hs);
+                    rhs_axpy(d, sc, k, bm, zb, za, 2.0 * hs);
+                    Vec t = za; za = zb; zb = t;
+                }
+                // z_n is in zb
+                err = 0.0;
+                for (int i = 0; i < d.N; i++) {
+                    double cur = zb[i], prev = T[0][i];
+                    T[0][i] = cur;
+                    for (int s2 = 1; s2 < j; s2++) {
+                        double r = (double)j / (double)(j - s2);
+                        double nw = cur + (cur - prev) / (r * r - 1.0);
+                        prev = T[s2][i];
+                        T[s2][i] = nw;
+                        cur = nw;
+                    }
+                    if (j >= 2) {
+                        int g = i < 3 ? 0 : i == 3 ? 1 : i < d.iN ? 2 : 4;
+                        double scl = atol + rtol * fmax(fmax(fabs(Y[i]), fabs(T[j - 1][i])), ABCMB_CHAIN_FLOOR * cm[g]);
+                        double e = fabs(T[j - 1][i] - T[j - 2][i]) / scl;
+                        if (!(e <= err)) err = e;
+                    }
+                }
+                if (!(err == err)) break;
+                if (j >= 2 && err <= 1.0) { jacc = j; break; }
+                continue;
+              }
                 const double hs = H / j;
                 res.substeps += j;
                 for (int i = 0; i < d.N; i++) YS[i] = Y[i];
@@ -255,8 +360,8 @@ ABCMB_HD ModeResult integrate_mode(const OdeDims &d, const StreamCoef &sc, const
                         T[s][i] = nw;
                         cur = nw;
                     }
-                    if (j >= 2) {
-                        int g = i < 3 ? 0 : i == 3 ? 1 : i < d.iG ? 2 : i < d.iN ? 3 : 4;
+                    if (j >= 2 && !(slaved && i >= d.iF + 2 && i < d.iN)) {
+                        int g = i < 3 ? 0 : i == 3 ? 1 : i < d.iN ? 2 : 4;
                         double scl = atol + rtol * fmax(fmax(fabs(Y[i]), fabs(T[j - 1][i])),
                                                         ABCMB_CHAIN_FLOOR * cm[g]);
                         double e = fabs(T[j - 1][i] - T[j - 2][i]) / scl;
@@ -270,7 +375,7 @@ ABCMB_HD ModeResult integrate_mode(const OdeDims &d, const StreamCoef &sc, const
             if (jacc) {
                 for (int i = 0; i < d.N; i++) Y[i] = T[jacc - 1][i];
                 x = land ? xn : x + H;
-                double fac = err > 0.0 ? 0.9 * exp(-log(err) / jacc) : 4.0;
+                double fac = err > 0.0 ? 0.9 * exp(-log(err) / (gbs ? 2 * jacc - 1 : jacc)) : 4.0;
                 if (jacc < kKmax - 1) fac *= 1.5;
                 fac = fmin(4.0, fmax(0.2, fac));
                 double hn = H * fac;
@@ -284,7 +389,7 @@ ABCMB_HD ModeResult integrate_mode(const OdeDims &d, const StreamCoef &sc, const
                     node++;
                 }
             } else {
-                double fac = fmin(0.9, fmax(0.1, 0.9 * exp(-log(err) / kKmax)));
+                double fac = fmin(0.9, fmax(0.1, 0.9 * exp(-log(err) / (gbs ? 2 * kKmax - 1 : kKmax))));
                 h = H * fac;
             }
         } else {

@@ -1,7 +1,7 @@
 // Background and perturbation kernels plus the option helpers of the C ABI
 // (include/abcmb.h).
 //
-// background_kernel: one thread per cosmology runs abcmb::build_background.
+// background_kernel: one warp per cosmology runs abcmb::build_background.
 // perturb_kernel: one thread per (cosmology, k) mode runs
 // abcmb::integrate_mode; modes are ordered k-descending so that the most
 // expensive modes are scheduled first and the lanes of a warp share one k
@@ -14,11 +14,13 @@
 
 namespace abcmb {
 
-__global__ void background_kernel(int B, const double *__restrict__ params, double *bg, long len, int n_tau)
+// one warp (32 threads) per cosmology
+__global__ void __launch_bounds__(32) background_kernel(int B, const double *__restrict__ params, double *bg,
+                                                         long len, int n_tau)
 {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.x;
     if (b >= B) return;
-    build_background(params + (long)b * ABCMB_NPARAM, bg + (long)b * len, n_tau);
+    build_background(params + (long)b * ABCMB_NPARAM, bg + (long)b * len, n_tau, threadIdx.x, 32);
 }
 
 __global__ void __launch_bounds__(64)
@@ -106,7 +108,7 @@ extern "C" int abcmb_background_tables(int B, const double *params, const abcmb_
 {
     if (B < 1 || !params || !bg || abcmb_validate_options(o) != ABCMB_OK) return ABCMB_E_INVALID_ARG;
     const long len = (long)abcmb_bg_doubles(o);
-    abcmb::background_kernel<<<(B + 31) / 32, 32, 0, (cudaStream_t)stream>>>(B, params, bg, len, o->n_tau);
+    abcmb::background_kernel<<<B, 32, 0, (cudaStream_t)stream>>>(B, params, bg, len, o->n_tau);
     return cudaGetLastError() == cudaSuccess ? ABCMB_OK : ABCMB_E_CUDA;
 }
 

@@ -27,6 +27,20 @@ namespace abcmb {
 
 constexpr int kNodesPerLane = 4;
 constexpr int kLB = 16; // l per block (2 * kLB = 32 partial sums per lane)
+// Below x = kSeriesX, j_l comes from its power series
+//   j_l(x) = x^l / (2l+1)!! sum_n (-x^2/2)^n / (n! (2l+3)...(2l+2n+1)),
+// seven terms (error < 1e-13 for x < 1); ser[8 l] = 1/(2l+3) advances the
+// prefactor, ser[8 l + n] = 1 / (2n (2l+2n+1)) is the term ratio.
+constexpr double kSeriesX = 1.0;
+constexpr int kSerL = 32;
+
+__device__ __forceinline__ double series_sum(const double *ser, int l, double z)
+{
+    double s = 1.0;
+#pragma unroll
+    for (int n = 7; n >= 1; n--) s = fma(-z * ser[8 * l + n], s, 1.0);
+    return s;
+}
 
 __device__ __forceinline__ void j01(double x, double *j0, double *j1)
 {
@@ -50,7 +64,9 @@ __device__ __forceinline__ void j01(double x, double *j0, double *j1)
 __device__ __forceinline__ int bessel_cut(float x, int lmax)
 {
     if (x > (float)lmax + 200.0f) return lmax;
-    const float T = 17.0f;
+    // the T2 and E kernels carry j_l / x^2, so at x < 1 the threshold moves
+    // down by x^2
+    const float T = 17.0f + 2.0f * fmaxf(0.0f, -logf(x));
     float nu = x + 1.0f + 0.8f * cbrtf(fmaxf(x, 1.0f)) * 9.0f;
     for (int it = 0; it < 8; it++) {
         float r = fmaxf(nu / fmaxf(x, 1e-30f), 1.0f + 1e-6f);
@@ -92,7 +108,12 @@ project_kernel(int B, int Nk, const double *__restrict__ bg, long bg_len,
     const double *nodes = rec + ABCMB_BG_NODES;
     const double *Sm = S + ((long)b * Nk + kidx) * (long)n_tau * 3;
     const double kk = kv[kidx];
+    __shared__ double ser[8 * kSerL];
     for (int i = threadIdx.x; i < 2 * nl; i += blockDim.x) acc[i] = 0.0;
+    for (int i = threadIdx.x; i < 8 * kSerL; i += blockDim.x) {
+        const int l = i >> 3, n = i & 7;
+        ser[i] = n == 0 ? 1.0 / (2.0 * l + 3.0) : 1.0 / (2.0 * n * (2.0 * l + 2.0 * n + 1.0));
+    }
     __syncthreads();
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
@@ -102,7 +123,9 @@ project_kernel(int B, int Nk, const double *__restrict__ bg, long bg_len,
     for (int g = warp; g < ngroups; g += W) {
         double A0[kNodesPerLane], A1[kNodesPerLane], A2[kNodesPerLane], Bc[kNodesPerLane], E[kNodesPerLane];
         double jm[kNodesPerLane], jc[kNodesPerLane], t[kNodesPerLane], tu[kNodesPerLane];
+        // nodes with x < kSeriesX keep x^l/(2l+1)!! in t[] and x in tu[]
         int lc[kNodesPerLane];
+        bool sm[kNodesPerLane];
         int lcmax = 0;
 #pragma unroll
         for (int m = 0; m < kNodesPerLane; m++) {
@@ -124,46 +147,79 @@ project_kernel(int B, int Nk, const double *__restrict__ bg, long bg_len,
                 double j0, j1;
                 j01(x, &j0, &j1);
                 jm[m] = j1;
-                if (x < 0.1) { // series: term ratio -x^2 / ((2n+2)(2n+7))
-                    const double x2 = x * x;
-                    jc[m] = x2 / 15.0 * (1.0 - x2 / 14.0 * (1.0 - x2 / 36.0 * (1.0 - x2 / 66.0)));
-                } else {
-                    jc[m] = 3.0 * u * j1 - j0; // j_2
-                }
-                t[m] = 5.0 * u;
-                tu[m] = 2.0 * u;
+                sm[m] = x < kSeriesX;
+                jc[m] = sm[m] ? x * x / 15.0 * series_sum(ser, 2, x * x) : 3.0 * u * j1 - j0; // j_2
+                t[m] = sm[m] ? x * x / 15.0 : 5.0 * u;
+                tu[m] = sm[m] ? x : 2.0 * u;
                 lc[m] = bessel_cut((float)x, lmax);
+                if (sm[m] && lc[m] > kSerL - 2) lc[m] = kSerL - 2;
             } else {
                 A0[m] = A1[m] = A2[m] = Bc[m] = E[m] = 0.0;
                 jm[m] = jc[m] = t[m] = tu[m] = 0.0;
+                sm[m] = false;
                 lc[m] = 0;
             }
             lcmax = max(lcmax, lc[m]);
         }
         lcmax = __reduce_max_sync(0xffffffffu, lcmax);
+        bool anysm = false;
+#pragma unroll
+        for (int m = 0; m < kNodesPerLane; m++) anysm |= sm[m];
+        anysm = __any_sync(0xffffffffu, anysm); // warp-uniform
         // past its cutoff a node's j is held at exactly zero (the upward
         // recurrence is unstable there), so it contributes nothing further
         for (int l0 = 2; l0 <= lcmax + 1 && l0 <= lmax; l0 += kLB) {
             double v[2 * kLB];
             double ld = (double)l0;
+            if (!anysm) {
 #pragma unroll
-            for (int q = 0; q < kLB; q++) {
-                double cT = 0.0, cE = 0.0;
-                const int lnext = l0 + q + 1;
+                for (int q = 0; q < kLB; q++) {
+                    double cT = 0.0, cE = 0.0;
+                    const int lnext = l0 + q + 1;
 #pragma unroll
-                for (int m = 0; m < kNodesPerLane; m++) {
-                    const double coef = fma(fma(A2[m], ld, A1[m]), ld, A0[m]);
-                    cT = fma(coef, jc[m], cT);
-                    cT = fma(Bc[m], jm[m], cT);
-                    cE = fma(E[m], jc[m], cE);
-                    const double jn = fma(t[m], jc[m], -jm[m]);
-                    jm[m] = jc[m];
-                    jc[m] = lnext <= lc[m] ? jn : 0.0;
-                    t[m] += tu[m];
+                    for (int m = 0; m < kNodesPerLane; m++) {
+                        const double coef = fma(fma(A2[m], ld, A1[m]), ld, A0[m]);
+                        cT = fma(coef, jc[m], cT);
+                        cT = fma(Bc[m], jm[m], cT);
+                        cE = fma(E[m], jc[m], cE);
+                        const double jn = fma(t[m], jc[m], -jm[m]);
+                        jm[m] = jc[m];
+                        jc[m] = lnext <= lc[m] ? jn : 0.0;
+                        t[m] += tu[m];
+                    }
+                    v[q] = cT;
+                    v[kLB + q] = cE;
+                    ld += 1.0;
                 }
-                v[q] = cT;
-                v[kLB + q] = cE;
-                ld += 1.0;
+            } else {
+                // some node of the group has x < 1: those take j_{l+1} from
+                // its power series instead of the (there unstable) recurrence
+#pragma unroll
+                for (int q = 0; q < kLB; q++) {
+                    double cT = 0.0, cE = 0.0;
+                    const int l = l0 + q, lnext = l + 1;
+                    const int ls = min(lnext, kSerL - 1);
+#pragma unroll
+                    for (int m = 0; m < kNodesPerLane; m++) {
+                        const double coef = fma(fma(A2[m], ld, A1[m]), ld, A0[m]);
+                        cT = fma(coef, jc[m], cT);
+                        cT = fma(Bc[m], jm[m], cT);
+                        cE = fma(E[m], jc[m], cE);
+                        double jn;
+                        if (sm[m]) {
+                            t[m] *= tu[m] * ser[8 * min(l, kSerL - 1)];
+                            jn = t[m] * series_sum(ser, ls, tu[m] * tu[m]);
+                        } else {
+                            jn = fma(t[m], jc[m], -jm[m]);
+                            t[m] += tu[m];
+                        }
+                        jm[m] = jc[m];
+                        jc[m] = lnext <= lc[m] ? jn : 0.0;
+                    }
+                    v[q] = cT;
+                    v[kLB + q] = cE;
+                    ld += 1.0;
+                }
             }
             // reduce-scatter: lane ends with the warp total of v[lane]
             butterfly_stage<16>(v, lane);
