@@ -219,9 +219,10 @@ class Pipeline:
 
 
 def bg_view(bg_row: torch.Tensor, n_tau: int):
-    """Split one background record (on any device) into scalars, table and nodes."""
+    """Split one background record (on any device) into scalars, the 8-column
+    ln a table and the tau nodes (the ODE table between them is skipped)."""
     r = bg_row.detach().cpu().numpy()
     scal = {k: r[i] for k, i in S_INDEX.items()}
-    tab = r[BG_TABLE:BG_NODES].reshape(BG_NLNA, 8)
+    tab = r[BG_TABLE:BG_ODETAB].reshape(BG_NLNA, 8)
     nodes = r[BG_NODES:BG_NODES + 8 * n_tau].reshape(n_tau, 8)
     return scal, tab, nodes
