@@ -39,6 +39,8 @@ enum {
     ABCMB_E_MAX_STEPS = 3,   /* status word: a mode hit its step budget         */
     ABCMB_E_NONFINITE = 4,   /* status word: a non-finite value was produced    */
     ABCMB_E_BACKGROUND = 5,  /* status word: a background root was not found    */
+    ABCMB_E_SCRATCH_TOO_SMALL = 6, /* abcmb_perturb_noalloc: problem needs more
+                                      than ABCMB_NOALLOC_SCRATCH_BYTES     */
 };
 
 /* Number of doubles per cosmology in params: omega_b, omega_cdm, h, n_s,
@@ -146,6 +148,38 @@ int abcmb_perturb(int B, const double *bg, const double *k, int Nk, const abcmb_
    modes (0 if the options are invalid).  The caller allocates it; its
    contents need no initialisation and are scratch after the call. */
 size_t abcmb_perturb_workspace_bytes(int B, int Nk, const abcmb_options *o);
+
+/*
+ * abcmb_perturb for callers that cannot allocate device memory.  The paper has
+ * no counterpart: this is a service of the library, not a step of the method.
+ *
+ * Some callers must not call cudaMalloc at all: an application whose device
+ * memory is entirely owned by another runtime's caching pool (a stray
+ * allocation outside the pool can fail or fragment it), or a latency-bound
+ * loop in which an allocation's implicit device synchronisation is not
+ * acceptable.  This entry point computes exactly what abcmb_perturb computes
+ * (same kernel, same arguments except the workspace) but keeps the working
+ * vectors in a static device array of ABCMB_NOALLOC_SCRATCH_BYTES that the
+ * library owns.  It calls no cudaMalloc, cudaFree or allocating library
+ * routine.
+ *
+ *   - Size limit: abcmb_perturb_workspace_bytes(B, Nk, o) must not exceed
+ *     ABCMB_NOALLOC_SCRATCH_BYTES (64 MiB: e.g. 10 810 modes at hierarchy 30,
+ *     24 385 at hierarchy 12); larger problems return
+ *     ABCMB_E_SCRATCH_TOO_SMALL and enqueue nothing.  Every GPU that loads the
+ *     library reserves the array until the process exits.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture begins.
+ *   - Every call shares the one array, which keeps the last call's contents;
+ *     the kernel overwrites every element it reads, so nothing needs
+ *     clearing.  Calls whose kernels overlap on the GPU (different streams,
+ *     no ordering between them) race on the array: order them.
+ *   - Arguments, outputs and status words as abcmb_perturb.
+ */
+#define ABCMB_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+int abcmb_perturb_noalloc(int B, const double *bg, const double *k, int Nk, const abcmb_options *o,
+                          double *S, int *mode_status, int *steps, void *stream);
 
 /*
  * Line-of-sight projection (App. B.4): for every ell in [2, lmax_cl],

@@ -17,9 +17,11 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libabcmb.so")
 
-OK, E_INVALID_ARG, E_CUDA, E_MAX_STEPS, E_NONFINITE, E_BACKGROUND = range(6)
+OK, E_INVALID_ARG, E_CUDA, E_MAX_STEPS, E_NONFINITE, E_BACKGROUND, E_SCRATCH_TOO_SMALL = range(7)
 ERRORS = {1: "invalid argument", 2: "CUDA error", 3: "step budget exhausted",
-          4: "non-finite value", 5: "background root not found"}
+          4: "non-finite value", 5: "background root not found",
+          6: "problem larger than the library's static scratch"}
+NOALLOC_SCRATCH_BYTES = 64 << 20
 
 NPARAM = 6
 BG_NSCALAR = 64
@@ -78,6 +80,7 @@ def lib():
         L.abcmb_background_tables.argtypes = [ctypes.c_int, _P, O, _P, _P]
         L.abcmb_perturb.argtypes = [ctypes.c_int, _P, _P, ctypes.c_int, O, _P, _P, _P, _P,
                                     ctypes.c_size_t, _P]
+        L.abcmb_perturb_noalloc.argtypes = [ctypes.c_int, _P, _P, ctypes.c_int, O, _P, _P, _P, _P]
         L.abcmb_project.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, O, _P, _P]
         L.abcmb_cl.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, O, _P, _P]
         _lib = L
@@ -145,6 +148,16 @@ def abcmb_perturb(bg: torch.Tensor, k: torch.Tensor, o: Options, S=None, status=
                                _ptr(steps), _ptr(workspace), workspace.numel() * 8, _stream()),
            "abcmb_perturb")
     return S, status, steps
+
+
+def abcmb_perturb_noalloc(bg: torch.Tensor, k: torch.Tensor, o: Options, S, status, steps=None):
+    """abcmb_perturb without a workspace, for callers that cannot allocate
+    device memory: the library's static scratch holds the working vectors.
+    Outputs must be preallocated by the caller; returns the C status code."""
+    _dev(bg), _dev(k), _dev(S)
+    B, Nk = bg.shape[0], k.shape[0]
+    return lib().abcmb_perturb_noalloc(B, _ptr(bg), _ptr(k), Nk, ctypes.byref(o), _ptr(S), _ptr(status),
+                                       _ptr(steps), _stream())
 
 
 def abcmb_project(bg: torch.Tensor, S: torch.Tensor, k: torch.Tensor, o: Options, out=None):

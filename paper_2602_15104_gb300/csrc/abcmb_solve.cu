@@ -10,6 +10,8 @@
 // touch consecutive addresses.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "abcmb_ode.cuh"
 
 namespace abcmb {
@@ -109,6 +111,54 @@ extern "C" int abcmb_background_tables(int B, const double *params, const abcmb_
     if (B < 1 || !params || !bg || abcmb_validate_options(o) != ABCMB_OK) return ABCMB_E_INVALID_ARG;
     const long len = (long)abcmb_bg_doubles(o);
     abcmb::background_kernel<<<B, 32, 0, (cudaStream_t)stream>>>(B, params, bg, len, o->n_tau);
+    return cudaGetLastError() == cudaSuccess ? ABCMB_OK : ABCMB_E_CUDA;
+}
+
+// ---------------------------------------------------------------- no-alloc variant
+// Scratch of abcmb_perturb_noalloc: the perturbation kernel's working vectors
+// live in this file-scope device array instead of a caller-provided
+// workspace.  Every GPU that loads the library holds it until the process
+// exits.  Host code may not pass the symbol itself to a kernel (on the host it
+// names a stand-in, not device memory); the device address is looked up once
+// per device with cudaGetSymbolAddress and cached.
+static __device__ __align__(256) double g_noalloc_scratch[ABCMB_NOALLOC_SCRATCH_BYTES / sizeof(double)];
+
+static std::mutex g_noalloc_mutex;
+static double *g_noalloc_ptr[256];
+
+static int noalloc_scratch(double **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return ABCMB_E_CUDA;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return ABCMB_E_CUDA;
+        g_noalloc_ptr[dev] = (double *)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return ABCMB_OK;
+}
+
+extern "C" int abcmb_perturb_noalloc(int B, const double *bg, const double *k, int Nk, const abcmb_options *o,
+                                     double *S, int *mode_status, int *steps, void *stream)
+{
+    if (B < 1 || Nk < 1 || !bg || !k || !S || !mode_status || abcmb_validate_options(o) != ABCMB_OK)
+        return ABCMB_E_INVALID_ARG;
+    const size_t need = abcmb_perturb_workspace_bytes(B, Nk, o);
+    if (need == 0) return ABCMB_E_INVALID_ARG;
+    if (need > ABCMB_NOALLOC_SCRATCH_BYTES) return ABCMB_E_SCRATCH_TOO_SMALL;
+    double *scratch = nullptr;
+    const int rc = noalloc_scratch(&scratch);
+    if (rc != ABCMB_OK) return rc;
+    // the kernel writes every scratch element it reads, so nothing needs clearing
+    const long len = (long)abcmb_bg_doubles(o);
+    const long M = (long)B * Nk;
+    const int threads = 64;
+    const long blocks = (M + threads - 1) / threads;
+    abcmb::perturb_kernel<<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(
+        B, Nk, bg, len, k, o->lmax_g, o->lmax_pol, o->lmax_nu, o->rtol, o->atol, o->max_steps, o->scale_sw,
+        o->scale_isw, o->scale_dop, S, mode_status, steps, scratch);
     return cudaGetLastError() == cudaSuccess ? ABCMB_OK : ABCMB_E_CUDA;
 }
 
