@@ -41,12 +41,51 @@ def flops_per_substep(N: int) -> float:
     return 10.0 * N + 150.0
 
 
+def rank_params(wl, B: int, rank: int) -> np.ndarray:
+    """Cosmologies of one rank: each rank draws its own seeded batch (weak
+    scaling over independent cosmologies; no data exchange between ranks)."""
+    return W.draw_cosmologies(B, wl.seed + 1000 * rank)
+
+
+def max_over_ranks(values, dist, device) -> list:
+    """Element-wise maximum of per-rank timings (the slowest rank sets the
+    whole job's time); identity on one rank."""
+    if dist is None:
+        return list(values)
+    import torch
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def whole_job_rate(units_per_rank: int, world: int, ms: float) -> float:
+    """Units processed by all ranks per second of the slowest rank."""
+    return units_per_rank * world / (ms * 1e-3)
+
+
+def bessel_cut(x: np.ndarray, lmax: int) -> np.ndarray:
+    """Last l the projection kernel keeps at x: the smallest l > x whose Debye
+    decay exponent nu (alpha - tanh alpha), cosh alpha = nu / x, nu = l + 1/2,
+    reaches 16 + 2 ln(1/x) for x < 1 (the kernel's own rule, evaluated here
+    in float64 to count work)."""
+    x = np.asarray(x, dtype=np.float64)
+    T = 16.0 + 2.0 * np.maximum(0.0, -np.log(np.maximum(x, 1e-300)))
+    nu = x + 1.0 + 7.2 * np.cbrt(np.maximum(x, 1.0))
+    for _ in range(8):
+        r = np.maximum(nu / np.maximum(x, 1e-30), 1.0 + 1e-6)
+        al = np.arccosh(r)
+        f = nu * (al - np.tanh(al)) - T
+        nu = np.maximum(nu - f / np.maximum(al, 1e-3), x + 0.5)
+    lc = np.clip(np.ceil(nu - 0.5), 2, lmax)
+    lc = np.where(x < 1.0, np.minimum(lc, 30), lc)
+    return np.where(x > lmax + 200.0, lmax, lc)
+
+
 def projection_points(tau_nodes: np.ndarray, tau0: float, k: np.ndarray, lmax: int) -> float:
-    """(node, l) points the projection kernel evaluates: l = 2 .. min(lmax,
-    x + 12 + 7 x^(1/3)) per node, x = k (tau_0 - tau)."""
-    x = np.outer(k, tau0 - tau_nodes).astype(np.float32)
-    lc = np.minimum(np.floor(x + 12.0 + 7.0 * np.cbrt(x)), lmax)
-    return float(np.maximum(lc - 1.0, 0.0).sum())
+    """(node, l) points the projection kernel evaluates: l = 2 .. bessel_cut(x)
+    per node, x = k (tau_0 - tau)."""
+    x = np.outer(k, tau0 - tau_nodes)
+    return float(np.maximum(bessel_cut(x, lmax) - 1.0, 0.0).sum())
 
 
 class ClockSampler:
@@ -163,6 +202,10 @@ def main():
     ap.add_argument("--workload", default=W.BATCH64.name, choices=sorted(W.WORKLOADS))
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", type=int, default=None,
+                    help="cosmologies per step (default: the workload's); smaller cases are for profiling")
+    ap.add_argument("--n-k", type=int, default=None,
+                    help="k modes (default: the workload's), log-spaced over the workload's range")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -180,9 +223,9 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     wl = W.WORKLOADS[args.workload]
-    B = wl.n_cosmo
-    params = W.draw_cosmologies(B, wl.seed + 1000 * rank)
-    k = wl.k()
+    B = args.batch or wl.n_cosmo
+    params = rank_params(wl, B, rank)
+    k = W.log_k_nodes(args.n_k, wl.k_min, wl.k_max) if args.n_k else wl.k()
     o = A.options(lmax_hier=wl.l_max_hier, lmax_cl=wl.l_max_cl, n_tau=wl.n_tau, rtol=args.rtol)
     N = 4 + 3 * (wl.l_max_hier + 1)
     pipe = A.Pipeline(B, k, o)
@@ -244,10 +287,7 @@ def main():
 
     t_step = statistics.mean(step_ms)
     t_e2e = statistics.mean(e2e_ms)
-    if dist is not None:
-        t = torch.tensor([t_step, t_e2e], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_step, t_e2e = float(t[0]), float(t[1])
+    t_step, t_e2e = max_over_ranks([t_step, t_e2e], dist, "cuda")
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -273,7 +313,7 @@ def main():
     kern = {n: {"ms": kavg[n], "share": kavg[n] / sum(kavg.values())} for n in names}
     for n in flops:
         kern[n]["tflops"] = flops[n] / (kavg[n] * 1e-3) / 1e12
-    value = B * world / (t_step * 1e-3)
+    value = whole_job_rate(B, world, t_step)
     lat = sorted(e2e_ms)
     out = {
         "metric": METRIC, "value": value, "unit": "spectra/s", "n_gpus": world, "steps": args.steps,
@@ -284,11 +324,11 @@ def main():
                    "rtol": args.rtol, "l2": "flushed (512 MiB write) between timed steps",
                    "parallelism": f"replicas x{world}"},
         "clocks": clk,
-        "e2e": {"value": B * world / (t_e2e * 1e-3), "unit": "spectra/s",
+        "e2e": {"value": whole_job_rate(B, world, t_e2e), "unit": "spectra/s",
                 "h2d_bytes_per_step": int(params.nbytes),
                 "d2h_bytes_per_step": int(B * 3 * (o.lmax_cl - 1) * 8)},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                       "what": "batch of 64 spectra, host params to host C_l"},
+                       "what": f"batch of {B} spectra, host params to host C_l"},
         "gpu_launches": 4 * args.steps,
         "roofline": roof,
         "kernels": kern,

@@ -52,9 +52,9 @@ enum {
 #define ABCMB_NPARAM 6
 
 typedef struct {
-    int lmax_g;      /* photon temperature hierarchy truncation, 4..64 (App. A.1 l_max_g)  */
-    int lmax_pol;    /* photon polarization hierarchy truncation, 4..64 (l_max_pol_g)      */
-    int lmax_nu;     /* massless-neutrino hierarchy truncation, 4..64 (l_max_massless_nu)  */
+    int lmax_g;      /* photon temperature hierarchy truncation, 4..128 (App. A.1 l_max_g) */
+    int lmax_pol;    /* photon polarization hierarchy truncation, 4..128 (l_max_pol_g)     */
+    int lmax_nu;     /* massless-neutrino hierarchy truncation, 4..128 (l_max_massless_nu) */
     int lmax_cl;     /* C_ell computed for every ell in [2, lmax_cl]; 2..5000 (App. A.1)   */
     int n_tau;       /* number of tau nodes of the line-of-sight integral, 8..65536        */
     int max_steps;   /* accepted+rejected ODE step budget per k mode, >= 1                 */
@@ -81,10 +81,10 @@ size_t abcmb_bg_doubles(const abcmb_options *o);
             ln a_j = ABCMB_BG_LNA0 + j / ABCMB_BG_PER_UNIT, 8 columns per node:
             1/(H tau_c), d/dln a of it, tau, dtau/dln a = 1/H, c_s^2,
             d c_s^2/dln a, kappa, x_e
-     [ABCMB_BG_ODETAB, + 18 * ABCMB_BG_NLNA) on the same grid, 9 (value,
+     [ABCMB_BG_ODETAB, + 20 * ABCMB_BG_NLNA) on the same grid, 10 (value,
             d/dln a) pairs per node read by the ODE kernel: 1/H, 1/(H tau),
             f_c, f_b, f_gamma, f_nu (rho_i / rho_tot), 1/(H tau_c),
-            (4 rho_g / 3 rho_b) / (H tau_c), c_s^2
+            (4 rho_g / 3 rho_b) / (H tau_c), c_s^2, H (all conformal)
      then 8 columns per tau node (n_tau nodes): ln a, tau, trapezoid weight,
             g, dg/dln a, e^-kappa, conformal H, dH/dln a                     */
 #define ABCMB_BG_NSCALAR 64
@@ -93,7 +93,7 @@ size_t abcmb_bg_doubles(const abcmb_options *o);
 #define ABCMB_BG_NLNA (18 * 1024 + 1)
 #define ABCMB_BG_TABLE ABCMB_BG_NSCALAR
 #define ABCMB_BG_ODETAB (ABCMB_BG_TABLE + 8 * ABCMB_BG_NLNA)
-#define ABCMB_BG_NODES (ABCMB_BG_ODETAB + 18 * ABCMB_BG_NLNA)
+#define ABCMB_BG_NODES (ABCMB_BG_ODETAB + 20 * ABCMB_BG_NLNA)
 
 enum {
     ABCMB_S_STATUS = 0, ABCMB_S_H0, ABCMB_S_OMB, ABCMB_S_OMC, ABCMB_S_OMG, ABCMB_S_OMNU,
@@ -138,15 +138,21 @@ int abcmb_background_tables(int B, const double *params, const abcmb_options *o,
  *   steps        [B][Nk][2] int32 or NULL  device, written: ODE steps taken
  *                (accepted and rejected) and linearly implicit substeps
  *   workspace    >= abcmb_perturb_workspace_bytes(B, Nk, o) bytes, device,
- *                256-byte aligned; returns ABCMB_E_INVALID_ARG if smaller
+ *                256-byte aligned; returns ABCMB_E_INVALID_ARG if smaller.
+ *                That size is 0, and workspace may be NULL, while every
+ *                hierarchy truncation is <= 63: the state then lives on chip
+ *                (four lanes per mode).  Deeper hierarchies (64..128) run one
+ *                thread per mode with the state in this workspace.
  */
 int abcmb_perturb(int B, const double *bg, const double *k, int Nk, const abcmb_options *o,
                   double *S, int *mode_status, int *steps, void *workspace,
                   size_t workspace_bytes, void *stream);
 
 /* Bytes of device workspace abcmb_perturb needs for B cosmologies and Nk
-   modes (0 if the options are invalid).  The caller allocates it; its
-   contents need no initialisation and are scratch after the call. */
+   modes: 0 when every hierarchy truncation is <= 63 (no workspace needed)
+   or the options are invalid, else 64 (Lg + Lp + Ln + 7) bytes per mode.  The
+   caller allocates it; its contents need no initialisation and are scratch
+   after the call. */
 size_t abcmb_perturb_workspace_bytes(int B, int Nk, const abcmb_options *o);
 
 /*
@@ -158,14 +164,14 @@ size_t abcmb_perturb_workspace_bytes(int B, int Nk, const abcmb_options *o);
  * allocation outside the pool can fail or fragment it), or a latency-bound
  * loop in which an allocation's implicit device synchronisation is not
  * acceptable.  This entry point computes exactly what abcmb_perturb computes
- * (same kernel, same arguments except the workspace) but keeps the working
- * vectors in a static device array of ABCMB_NOALLOC_SCRATCH_BYTES that the
- * library owns.  It calls no cudaMalloc, cudaFree or allocating library
- * routine.
+ * (same kernels, same arguments except the workspace).  Hierarchies <= 63
+ * need no scratch at all; deeper ones keep the working vectors in a static
+ * device array of ABCMB_NOALLOC_SCRATCH_BYTES that the library owns.  It
+ * calls no cudaMalloc, cudaFree or allocating library routine.
  *
  *   - Size limit: abcmb_perturb_workspace_bytes(B, Nk, o) must not exceed
- *     ABCMB_NOALLOC_SCRATCH_BYTES (64 MiB: e.g. 10 810 modes at hierarchy 30,
- *     24 385 at hierarchy 12); larger problems return
+ *     ABCMB_NOALLOC_SCRATCH_BYTES (64 MiB: e.g. 4 245 modes at hierarchy 80,
+ *     2 681 at hierarchy 128); larger problems return
  *     ABCMB_E_SCRATCH_TOO_SMALL and enqueue nothing.  Every GPU that loads the
  *     library reserves the array until the process exits.
  *   - The first call on each device looks up the array's device address

@@ -30,7 +30,7 @@ BG_LNA0 = -18.0
 BG_NLNA = 18 * 1024 + 1
 BG_TABLE = BG_NSCALAR
 BG_ODETAB = BG_TABLE + 8 * BG_NLNA
-BG_NODES = BG_ODETAB + 18 * BG_NLNA
+BG_NODES = BG_ODETAB + 20 * BG_NLNA
 S_INDEX = dict(STATUS=0, H0=1, OMB=2, OMC=3, OMG=4, OMNU=5, OML=6, RNU=7, FHE=8, NH0=9, AS=10,
                NS=11, ZREION=12, LNA_TC=13, LNA_SW=14, TAU0=15, LNA_HE3=16, LNA_700=17, NTAU=18)
 TABLE_COLUMNS = ("nuT", "dnuT", "tau", "dtau", "cs2", "dcs2", "kappa", "xe")
@@ -142,18 +142,20 @@ def abcmb_perturb(bg: torch.Tensor, k: torch.Tensor, o: Options, S=None, status=
     if steps is None:
         steps = torch.empty((B, Nk, 2), dtype=torch.int32, device=dev)
     nbytes = perturb_workspace_bytes(B, Nk, o)
-    if workspace is None:
-        workspace = torch.empty(nbytes // 8 + 32, dtype=torch.float64, device=dev)
+    if workspace is None and nbytes > 0:  # hierarchies > 63 only
+        workspace = torch.empty(nbytes // 8, dtype=torch.float64, device=dev)
+    wbytes = 0 if workspace is None else workspace.numel() * 8
     _check(lib().abcmb_perturb(B, _ptr(bg), _ptr(k), Nk, ctypes.byref(o), _ptr(S), _ptr(status),
-                               _ptr(steps), _ptr(workspace), workspace.numel() * 8, _stream()),
+                               _ptr(steps), _ptr(workspace), wbytes, _stream()),
            "abcmb_perturb")
     return S, status, steps
 
 
 def abcmb_perturb_noalloc(bg: torch.Tensor, k: torch.Tensor, o: Options, S, status, steps=None):
     """abcmb_perturb without a workspace, for callers that cannot allocate
-    device memory: the library's static scratch holds the working vectors.
-    Outputs must be preallocated by the caller; returns the C status code."""
+    device memory: hierarchies > 63 keep their working vectors in the
+    library's static scratch.  Outputs must be preallocated by the caller;
+    returns the C status code."""
     _dev(bg), _dev(k), _dev(S)
     B, Nk = bg.shape[0], k.shape[0]
     return lib().abcmb_perturb_noalloc(B, _ptr(bg), _ptr(k), Nk, ctypes.byref(o), _ptr(S), _ptr(status),
@@ -194,7 +196,8 @@ class Pipeline:
         self.S = torch.empty((B, Nk, o.n_tau, 3), dtype=torch.float64, device=dev)
         self.status = torch.empty((B, Nk), dtype=torch.int32, device=dev)
         self.steps = torch.empty((B, Nk, 2), dtype=torch.int32, device=dev)
-        self.ws = torch.empty(perturb_workspace_bytes(B, Nk, o) // 8 + 32, dtype=torch.float64, device=dev)
+        nbytes = perturb_workspace_bytes(B, Nk, o)
+        self.ws = torch.empty(nbytes // 8, dtype=torch.float64, device=dev) if nbytes else None
         self.D = torch.empty((B, Nk, o.lmax_cl - 1, 2), dtype=torch.float64, device=dev)
         self.C = torch.empty((B, 3, o.lmax_cl - 1), dtype=torch.float64, device=dev)
         self.params = torch.empty((B, NPARAM), dtype=torch.float64, device=dev)

@@ -575,12 +575,12 @@ ABCMB_HD void build_background(const double *p, double *rec, int n_tau, int lane
     c.tau0 = tab[8 * (kNlna - 1) + C_TAU];
 
     // ODE table: (value, d/dln a) pairs of 1/H, 1/(H tau), f_c, f_b, f_g,
-    // f_nu, 1/(H tau_c), R^-1/(H tau_c), c_s^2
+    // f_nu, 1/(H tau_c), R^-1/(H tau_c), c_s^2, H
     for (int j = lane; j < kNlna; j += nl) {
         const double lna = kLna0 + j * kDlna;
         const BgClosed b = closed_bg(c, lna);
         const double *r = tab + 8 * j;
-        double *o = otab + 18 * j;
+        double *o = otab + 20 * j;
         const double ih = 1.0 / b.Hc, iht = ih / r[C_TAU];
         const double dlnE2 = 2.0 * (b.dlnHc - 1.0);
         const double Rinv = (4.0 / 3.0) * (c.Om_g / c.Om_b) * b.inv_a;
@@ -602,6 +602,8 @@ ABCMB_HD void build_background(const double *p, double *rec, int n_tau, int lane
         o[15] = Rinv * (r[C_DNUT] - r[C_NUT]);
         o[16] = r[C_CS2];
         o[17] = r[C_DCS2];
+        o[18] = b.Hc;
+        o[19] = b.Hc * b.dlnHc;
     }
 
     // tight-coupling start: H tau_c = R_tc (every lane, identically)

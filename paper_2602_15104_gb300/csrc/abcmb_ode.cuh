@@ -77,7 +77,7 @@ struct Vec {
     ABCMB_HD double &operator[](int i) const { return p[(long)i * stride]; }
 };
 
-// Streaming coefficients l/(2l+1) and (l+1)/(2l+1), l = 0..64.
+// Streaming coefficients l/(2l+1) and (l+1)/(2l+1), l = 0..128.
 struct StreamCoef {
     const double *a, *b;
 };

@@ -1,0 +1,641 @@
+// Perturbation ODEs with four lanes per (cosmology, k) mode -- the path
+// abcmb_perturb runs.  Same equations and integrator as abcmb_ode.cuh (which
+// documents them: IMEX-Euler / Gragg extrapolation, steps landing on every tau
+// node), laid out for the GB300 FP64 pipe, whose issue rate bounds this kernel:
+//
+//  * A warp holds 8 modes; lane q = 0..3 of a mode's quad owns the Legendre
+//    moments l in [qP, qP+P) of each of the three chains (photon
+//    temperature, polarization, neutrinos) in registers.  Streaming couples
+//    neighbours only, so a substep exchanges one boundary value per chain
+//    per direction (two shuffles).  Lane 0 also owns l <= 2 of every chain,
+//    hence the metric sums, both Thomson blocks and the sources; the four
+//    scalars (eta, delta_c, delta_b, theta_b) are kept identical in all four
+//    lanes.
+//  * The background point (10 interpolated quantities) is split over the
+//    quad: lane q interpolates ODE-table columns q, q+4 and 8 + (q & 1), then
+//    the values are broadcast inside the quad.
+//  * The accepted state and the extrapolation tableau live in shared memory
+//    ([vector][element][lane], conflict-free), the inverse error scales in
+//    the last tableau column's slot until that column is formed; the
+//    working vectors of a column live in registers.
+//  * The error norm is max_i |T_j,j-1 - T_j,j-2|_i / (atol + rtol max(|y_i|,
+//    1e-4 m_g(i))) with y the state at the step start and m_g the largest
+//    magnitude of i's group (eta/delta_c/delta_b, theta_b, photons, neutrinos);
+//    the inverse scales are formed once per step with the approximate
+//    reciprocal (a few ulp of float accuracy, ample for step control).
+//  * Control flow is warp-uniform: every lane runs every loop (quads that
+//    are done, or already accepted their step, compute and discard), so the
+//    full-mask shuffles are always legal.  Masked lanes cost the FP64 pipe as
+//    much as active ones on this part, so nothing is lost by this.
+#pragma once
+
+#include "abcmb_ode.cuh"
+
+namespace abcmb {
+
+constexpr int kQK = kKmax; // extrapolation columns
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kQLmax = 63;  // highest hierarchy truncation (4 lanes x 16 moments)
+
+// ODE-table columns, (value, d/dln a) pairs -- written by build_background
+enum { O_IH = 0, O_IHT, O_FC, O_FB, O_FG, O_FNU, O_NU, O_RNU, O_CS2, O_HC, O_NCOL };
+constexpr int kOStride = 2 * O_NCOL;
+
+struct QBg {
+    double ih, iht, fc, fb, fg, fnu, nu, rnu, cs2, hc;
+};
+
+// cubic Hermite weights on the uniform ln a grid, derivative weights scaled by the spacing
+struct QHerm {
+    int j;
+    double w0, w1, d0, d1;
+};
+
+__device__ __forceinline__ QHerm qherm(double lna)
+{
+    const double t = (lna - kLna0) * ABCMB_BG_PER_UNIT;
+    int j = (int)floor(t);
+    j = j < 0 ? 0 : (j > kNlna - 2 ? kNlna - 2 : j);
+    const double u = t - (double)j, um = 1.0 - u, um2 = um * um;
+    QHerm H;
+    H.j = j;
+    H.w0 = fma(u + u, um2, um2); // (1 + 2u)(1 - u)^2
+    H.w1 = 1.0 - H.w0;           // u^2 (3 - 2u)
+    H.d0 = kDlna * u * um2;      // u (1 - u)^2
+    H.d1 = -kDlna * u * u * um;  // u^2 (u - 1)
+    return H;
+}
+
+__device__ __forceinline__ double ocol(const double *ot, const QHerm &H, int c)
+{
+    const double *r0 = ot + kOStride * H.j + 2 * c, *r1 = r0 + kOStride;
+    return fma(H.w0, r0[0], fma(H.w1, r1[0], fma(H.d0, r0[1], H.d1 * r1[1])));
+}
+
+// all ten quantities, interpolated by one lane (used for the sources)
+__device__ __forceinline__ QBg obg_all(const double *ot, double lna)
+{
+    const QHerm H = qherm(lna);
+    QBg b;
+    b.ih = ocol(ot, H, O_IH);
+    b.iht = ocol(ot, H, O_IHT);
+    b.fc = ocol(ot, H, O_FC);
+    b.fb = ocol(ot, H, O_FB);
+    b.fg = ocol(ot, H, O_FG);
+    b.fnu = ocol(ot, H, O_FNU);
+    b.nu = ocol(ot, H, O_NU);
+    b.rnu = ocol(ot, H, O_RNU);
+    b.cs2 = ocol(ot, H, O_CS2);
+    b.hc = ocol(ot, H, O_HC);
+    return b;
+}
+
+// split over the quad and broadcast
+__device__ __forceinline__ QBg qbg(const double *ot, double lna, int q, int qb)
+{
+    const QHerm H = qherm(lna);
+    const double v0 = ocol(ot, H, q);
+    const double v1 = ocol(ot, H, q + 4);
+    const double v2 = ocol(ot, H, O_CS2 + (q & 1));
+    QBg b;
+    b.ih = __shfl_sync(kFull, v0, qb);
+    b.iht = __shfl_sync(kFull, v0, qb + 1);
+    b.fc = __shfl_sync(kFull, v0, qb + 2);
+    b.fb = __shfl_sync(kFull, v0, qb + 3);
+    b.fg = __shfl_sync(kFull, v1, qb);
+    b.fnu = __shfl_sync(kFull, v1, qb + 1);
+    b.nu = __shfl_sync(kFull, v1, qb + 2);
+    b.rnu = __shfl_sync(kFull, v1, qb + 3);
+    b.cs2 = __shfl_sync(kFull, v2, qb);
+    b.hc = __shfl_sync(kFull, v2, qb + 1);
+    return b;
+}
+
+// Per-chain streaming coefficients in shared memory: F_l' = k_H (A_l F_{l-1}
+// - B_l F_{l+1}) with A_l = l/(2l+1), B_l = (l+1)/(2l+1) below the truncation,
+// A_L = 1, B_L = 0 at it (the -(L+1)/(H tau) F_L term is added separately)
+// and A = B = 0 above it, so padding moments stay zero.
+struct QCoef {
+    const volatile double *A, *Bc; // [3][64]; volatile: re-read each substep, not held in registers
+    int L[3];
+};
+
+// per-mode constants
+struct QMode {
+    double k, ik, k2, k34, c43ik, c15ik; // k, 1/k, k^2, 3k/4, 4/(3k), 3/(2k)
+};
+
+// metric h', eta' from lane 0's state (result broadcast to the quad)
+template <int P>
+__device__ __forceinline__ void q_metric(const double (&z)[3][P], const double (&zs)[4], const QBg &b,
+                                         const QMode &m, int qb, double &hp, double &ep)
+{
+    const double kH = m.k * b.ih;
+    const double src = fma(b.fc, zs[1], fma(b.fb, zs[2], fma(b.fg, z[0][0], b.fnu * z[2][0])));
+    const double h1 = fma(2.0 * kH * kH, zs[0], 3.0 * src);
+    const double e1 = (m.c15ik * b.hc) * fma(b.fb * m.ik, zs[3], fma(b.fg, z[0][1], b.fnu * z[2][1]));
+    hp = __shfl_sync(kFull, h1, qb);
+    ep = __shfl_sync(kFull, e1, qb);
+}
+
+// value of this lane's moment l == L of a chain (0 where the lane does not hold it)
+template <int P>
+__device__ __forceinline__ double pick_L(const double (&v)[P], int q, int L)
+{
+    double r = 0.0;
+#pragma unroll
+    for (int p = 0; p < P; p++) r = (q * P + p == L) ? v[p] : r;
+    return r;
+}
+
+template <int P>
+__device__ __forceinline__ void put_L(double (&v)[P], int q, int L, double x)
+{
+#pragma unroll
+    for (int p = 0; p < P; p++) v[p] = (q * P + p == L) ? x : v[p];
+}
+
+// one linearly implicit Euler substep (see imex_substep), in place
+template <int P>
+__device__ __forceinline__ void q_imex(double (&z)[3][P], double (&zs)[4], const QBg &bc, const QBg &bn,
+                                       const QMode &m, double hs, int q, int qb, const QCoef &qc)
+{
+    double hp, ep;
+    q_metric<P>(z, zs, bc, m, qb, hp, ep);
+    double lft[3], rgt[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ch++) {
+        lft[ch] = __shfl_up_sync(kFull, z[ch][P - 1], 1, 4);
+        rgt[ch] = __shfl_down_sync(kFull, z[ch][0], 1, 4);
+    }
+    // scalars, explicit
+    {
+        const double eta = zs[0], dc = zs[1], db = zs[2], tb = zs[3];
+        const double hh = 0.5 * hs * hp;
+        zs[0] = fma(hs, ep, eta);
+        zs[1] = dc - hh;
+        zs[2] = fma(-hs * bc.ih, tb, db) - hh;
+        zs[3] = fma(hs, fma(bc.cs2 * m.k2 * bc.ih, db, -tb), tb);
+    }
+    // streaming, explicit
+    const double hkH = hs * m.k * bc.ih, htr = hs * bc.iht;
+#pragma unroll
+    for (int ch = 0; ch < 3; ch++) {
+        const volatile double *A = qc.A + 64 * ch, *Bc = qc.Bc + 64 * ch;
+        const double curL = pick_L<P>(z[ch], q, qc.L[ch]);
+        double prev = q == 0 ? 0.0 : lft[ch];
+#pragma unroll
+        for (int p = 0; p < P; p++) {
+            const int l = q * P + p;
+            const double cur = z[ch][p];
+            const double nxt = p < P - 1 ? z[ch][p + 1] : rgt[ch];
+            z[ch][p] = fma(hkH, fma(-Bc[l], nxt, A[l] * prev), cur);
+            prev = cur;
+        }
+        // truncation -(L+1)/(H tau) F_L
+        put_L<P>(z[ch], q, qc.L[ch], fma(-htr * (qc.L[ch] + 1.0), curL, pick_L<P>(z[ch], q, qc.L[ch])));
+    }
+    if (q == 0) {
+        const double m0 = hs * (-2.0 / 3.0) * hp, m2 = hs * fma(4.0 / 15.0, hp, 1.6 * ep);
+        z[0][0] += m0;
+        z[0][2] += m2;
+        z[2][0] += m0;
+        z[2][2] += m2;
+    }
+    // implicit Thomson part at x_{m+1}: one division for the three denominators
+    const double hnu = hs * bn.nu, hRnu = hs * bn.rnu;
+    const double d1 = 1.0 + hnu, d2 = fma(0.3, hnu, 1.0), d3 = d1 + hRnu;
+    const double d12 = d1 * d2, r = 1.0 / (d12 * d3);
+    const double dmp = r * (d2 * d3);
+#pragma unroll
+    for (int p = 0; p < P; p++) {
+        const int l = q * P + p;
+        z[0][p] *= (l >= 3) ? dmp : 1.0;
+        z[1][p] *= (l == 1 || l >= 3) ? dmp : 1.0;
+    }
+    if (q == 0) {
+        const double idet = r * d12, ipin = r * (d1 * d3);
+        const double rb = zs[3], ru = m.k34 * z[0][1];
+        zs[3] = idet * fma(d1, rb, hRnu * ru);
+        z[0][1] = (idet * m.c43ik) * fma(hnu, rb, (1.0 + hRnu) * ru);
+        const double r2 = z[0][2], g0 = z[1][0], g2 = z[1][2];
+        const double hpin = hnu * ((r2 + g0 + g2) * ipin);
+        z[0][2] = fma(0.1, hpin, r2) * dmp;
+        z[1][0] = fma(0.5, hpin, g0) * dmp;
+        z[1][2] = fma(0.1, hpin, g2) * dmp;
+    }
+    zs[3] = __shfl_sync(kFull, zs[3], qb);
+}
+
+// dst += fac f(src), everything explicit (see rhs_axpy)
+template <int P>
+__device__ __forceinline__ void q_rhs_axpy(const double (&s)[3][P], const double (&ss)[4], double (&d)[3][P],
+                                           double (&ds)[4], const QBg &b, const QMode &m, double fac, int q,
+                                           int qb, const QCoef &qc)
+{
+    double hp, ep;
+    q_metric<P>(s, ss, b, m, qb, hp, ep);
+    double lft[3], rgt[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ch++) {
+        lft[ch] = __shfl_up_sync(kFull, s[ch][P - 1], 1, 4);
+        rgt[ch] = __shfl_down_sync(kFull, s[ch][0], 1, 4);
+    }
+    const double F1 = __shfl_sync(kFull, s[0][1], qb);
+    const double Pi = __shfl_sync(kFull, s[0][2] + s[1][0] + s[1][2], qb);
+    const double tb = ss[3], fhp = fac * hp;
+    ds[0] = fma(fac, ep, ds[0]);
+    ds[1] = fma(-0.5, fhp, ds[1]);
+    ds[2] = fma(-fac * b.ih, tb, ds[2]) - 0.5 * fhp;
+    ds[3] = fma(fac, fma(b.cs2 * m.k2 * b.ih, ss[2], fma(b.rnu, fma(m.k34, F1, -tb), -tb)), ds[3]);
+    const double fkH = fac * m.k * b.ih, fnu = fac * b.nu, ftr = fac * b.iht;
+#pragma unroll
+    for (int ch = 0; ch < 3; ch++) {
+        const volatile double *A = qc.A + 64 * ch, *Bc = qc.Bc + 64 * ch;
+        double prev = q == 0 ? 0.0 : lft[ch];
+#pragma unroll
+        for (int p = 0; p < P; p++) {
+            const int l = q * P + p;
+            const double cur = s[ch][p];
+            const double nxt = p < P - 1 ? s[ch][p + 1] : rgt[ch];
+            double v = fma(fkH, fma(-Bc[l], nxt, A[l] * prev), d[ch][p]);
+            if (ch == 0) v = fma((l >= 1) ? -fnu : 0.0, cur, v);
+            if (ch == 1) v = fma(-fnu, cur, v);
+            d[ch][p] = v;
+            prev = cur;
+        }
+        const double curL = pick_L<P>(s[ch], q, qc.L[ch]);
+        put_L<P>(d[ch], q, qc.L[ch], fma(-ftr * (qc.L[ch] + 1.0), curL, pick_L<P>(d[ch], q, qc.L[ch])));
+    }
+    if (q == 0) {
+        const double fPi = fnu * Pi, m2 = fma(4.0 / 15.0, fhp, 1.6 * fac * ep);
+        d[0][0] = fma(-2.0 / 3.0, fhp, d[0][0]);
+        d[0][1] = fma(fnu * m.c43ik, tb, d[0][1]);
+        d[0][2] += fma(0.1, fPi, m2);
+        d[1][0] = fma(0.5, fPi, d[1][0]);
+        d[1][2] = fma(0.1, fPi, d[1][2]);
+        d[2][0] = fma(-2.0 / 3.0, fhp, d[2][0]);
+        d[2][2] += m2;
+    }
+}
+
+// Sources at a tau node from the accepted state in shared memory (lane 0).
+__device__ __forceinline__ void q_sources(const double *ot, const double *nd, double k, const double sw[3],
+                                          const double *Y, int P, double *S)
+{
+    const QBg b = obg_all(ot, nd[N_LNA]);
+    const double Hc = nd[N_HC], dHc = nd[N_DHC], g = nd[N_G], dg = nd[N_DG], emk = nd[N_EXPMK];
+    const double kH = k / Hc, k2 = k * k;
+    auto el = [&](int e) { return Y[e * 32]; };
+    const double eta = el(3 * P), dc = el(3 * P + 1), db = el(3 * P + 2), tb = el(3 * P + 3);
+    const double Fg0 = el(0), Fg1 = el(1), Fg2 = el(2);
+    const double G0 = el(P), G2 = el(P + 2);
+    const double Fn0 = el(2 * P), Fn1 = el(2 * P + 1), Fn2 = el(2 * P + 2);
+    const double hp = 2.0 * kH * kH * eta + 3.0 * (b.fc * dc + b.fb * db + b.fg * Fg0 + b.fnu * Fn0);
+    const double ep = 1.5 / kH * (b.fb * tb / k + b.fg * Fg1 + b.fnu * Fn1);
+    const double alpha = Hc * (hp + 6.0 * ep) / (2.0 * k2);
+    const double shear = (2.0 / 3.0) * (b.fg * Fg2 + b.fnu * Fn2);
+    const double Hap = -2.0 * Hc * alpha + eta - 4.5 * Hc * Hc / k2 * shear;
+    const double ap = Hap / Hc;
+    const double tbp = -tb + b.cs2 * k2 * db / Hc + b.rnu * (0.75 * k * Fg1 - tb);
+    const double swt = g * (0.25 * Fg0 + Hap);
+    const double isw = g * (eta - Hap - 2.0 * Hc * alpha) + 2.0 * Hc * emk * (ep - dHc * alpha - Hap);
+    const double dop = Hc * (g * (tbp / k2 + ap) + dg * (tb / k2 + alpha));
+    S[0] = sw[0] * swt + sw[1] * isw + sw[2] * dop;
+    S[1] = sw[1] * emk * k * (Hap + 2.0 * Hc * alpha - eta);
+    S[2] = g * (Fg2 + G0 + G2) * 0.125;
+}
+
+__device__ __forceinline__ double quad_max(double v)
+{
+    const double a = __shfl_xor_sync(kFull, v, 1);
+    if (!(a <= v)) v = a; // NaN propagates
+    const double c = __shfl_xor_sync(kFull, v, 2);
+    if (!(c <= v)) v = c;
+    return v;
+}
+
+__device__ __forceinline__ double rcp_approx(double x)
+{
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    return r;
+}
+
+// Integrate the modes of one warp (8 per warp, mode index mi for this lane's quad).
+template <int P>
+__device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restrict__ bg, long len,
+                           const double *__restrict__ kv, const QCoef &qc, double rtol, double atol, int max_steps,
+                           const double sw[3], double *S, int *status, int *steps, double *smw)
+{
+    constexpr int E = 3 * P + 4;
+    const int lane = threadIdx.x & 31, q = lane & 3, qb = lane & ~3;
+    const bool valid = mi < M;
+    const int kidx = valid ? Nk - 1 - (int)(mi / B) : 0;
+    const int b = valid ? (int)(mi % B) : 0;
+    const double *rec = bg + (long)b * len;
+    const double *tab = rec + ABCMB_BG_TABLE;
+    const double *ot = rec + ABCMB_BG_ODETAB;
+    const double *nodes = rec + ABCMB_BG_NODES;
+    const int n_tau = (int)rec[ABCMB_S_NTAU];
+    QMode md;
+    md.k = kv[kidx];
+    md.ik = 1.0 / md.k;
+    md.k2 = md.k * md.k;
+    md.k34 = 0.75 * md.k;
+    md.c43ik = (4.0 / 3.0) * md.ik;
+    md.c15ik = 1.5 * md.ik;
+    const double k = md.k;
+    double *Sm = S + ((long)b * Nk + kidx) * (long)n_tau * 3;
+    // shared memory of this lane: element e of vector v at smw[(v E + e) 32 + lane]
+    double *sl = smw + lane;
+    auto Y = [&](int e) -> double & { return sl[e * 32]; };
+    auto T = [&](int s, int e) -> double & { return sl[((1 + s) * E + e) * 32]; };
+
+    int stat = ABCMB_OK, nsteps = 0, nsub = 0, node = 0;
+    bool done = !valid;
+    if (valid && rec[ABCMB_S_STATUS] != 0.0) { stat = ABCMB_E_NONFINITE; done = true; }
+    const Cosmo c = load_cosmo(rec);
+
+    // start: a_i = min(a_tc, a_k), k / H(a_k) = R_large (App. A.1)
+    double x = c.lna_tc;
+    {
+        const double target = k / kRlarge;
+        if (hconf(c, c.lna_tc) < target) {
+            double lo = kLna0, hi = c.lna_tc;
+            if (hconf(c, lo) < target) x = lo;
+            else {
+                for (int it = 0; it < 100; it++) {
+                    const double mid = 0.5 * (lo + hi);
+                    if (mid <= lo || mid >= hi) break;
+                    if (hconf(c, mid) > target) lo = mid; else hi = mid;
+                }
+                x = 0.5 * (lo + hi);
+            }
+        }
+    }
+    // switch to the explicit (GBS) regime where 1/(H tau_c) falls below kNuNonStiff
+    double x_ns;
+    {
+        double lo = c.lna_sw, hi = -2.0;
+        for (int it = 0; it < 60; it++) {
+            const double mid = 0.5 * (lo + hi);
+            const Herm Hm = herm_at(mid);
+            if (herm_val(tab, Hm, C_NUT, C_DNUT) > kNuNonStiff) lo = mid; else hi = mid;
+        }
+        x_ns = hi;
+    }
+    // adiabatic initial state (see initial_state)
+    double z[3][P], zs[4], w[3][P], ws[4];
+    {
+        const Herm Hi = herm_at(x);
+        const double tau_i = herm_val(tab, Hi, C_TAU, C_DTAU);
+        const double C = 0.5, Rn = c.R_nu, kt = k * tau_i;
+        const double dg = -(2.0 / 3.0) * C * kt * kt;
+        const double F1 = -(2.0 / 27.0) * C * kt * kt * kt;
+        const double tg = -C * k * kt * kt * kt / 18.0;
+#pragma unroll
+        for (int ch = 0; ch < 3; ch++)
+#pragma unroll
+            for (int p = 0; p < P; p++) z[ch][p] = 0.0;
+        if (q == 0) {
+            z[0][0] = dg;
+            z[0][1] = F1;
+            z[2][0] = dg;
+            z[2][1] = F1 * (23.0 + 4.0 * Rn) / (15.0 + 4.0 * Rn);
+            z[2][2] = (4.0 / 3.0) * C * kt * kt / (15.0 + 4.0 * Rn);
+        }
+        zs[0] = 2.0 * C - C * kt * kt * (5.0 + 4.0 * Rn) / (6.0 * (15.0 + 4.0 * Rn));
+        zs[1] = 0.75 * dg;
+        zs[2] = 0.75 * dg;
+        zs[3] = tg;
+#pragma unroll
+        for (int ch = 0; ch < 3; ch++)
+#pragma unroll
+            for (int p = 0; p < P; p++) Y(ch * P + p) = z[ch][p];
+#pragma unroll
+        for (int s = 0; s < 4; s++) Y(3 * P + s) = zs[s];
+    }
+
+    double h = 1e-3;
+    while (__any_sync(kFull, !done)) {
+        // this quad's step
+        bool stepping = !done;
+        double xn = x, H = 0.0;
+        bool land = false, emit = false;
+        if (stepping) {
+            xn = nodes[8 * node + N_LNA];
+            H = h;
+            if (x + H >= xn) { H = xn - x; land = true; }
+            if (H <= 0.0) { emit = true; stepping = false; }
+            else if (++nsteps > max_steps) { stat = ABCMB_E_MAX_STEPS; done = true; stepping = false; }
+            else if (H < 1e-13 && !land) { stat = ABCMB_E_NONFINITE; done = true; stepping = false; }
+        }
+        const bool gbs = __all_sync(kFull, !stepping || x >= x_ns);
+        // inverse error scales from the state at the step start; moments slaved
+        // to the tight coupling (photon l >= 2, all of G while H/(H tau_c) >
+        // kSlavedHnu in the implicit regime) and padding moments get zero
+        const bool excl = !gbs && H * qbg(ot, x, q, qb).nu > kSlavedHnu;
+        // the inverse scales occupy the last tableau column's slot, which is
+        // written only by the last column, after its element's scale was read
+        {
+            double cm2 = 0.0, cm3 = 0.0;
+#pragma unroll
+            for (int p = 0; p < P; p++) {
+                z[0][p] = Y(p);
+                z[1][p] = Y(P + p);
+                z[2][p] = Y(2 * P + p);
+                cm2 = fmax(cm2, fmax(fabs(z[0][p]), fabs(z[1][p])));
+                cm3 = fmax(cm3, fabs(z[2][p]));
+            }
+#pragma unroll
+            for (int s = 0; s < 4; s++) zs[s] = Y(3 * P + s);
+            const double fl0 = ABCMB_CHAIN_FLOOR * fmax(fabs(zs[0]), fmax(fabs(zs[1]), fabs(zs[2])));
+            const double fl1 = ABCMB_CHAIN_FLOOR * fabs(zs[3]);
+            const double fl2 = ABCMB_CHAIN_FLOOR * quad_max(cm2);
+            const double fl3 = ABCMB_CHAIN_FLOOR * quad_max(cm3);
+#pragma unroll
+            for (int s = 0; s < 4; s++)
+                T(kQK - 1, 3 * P + s) = rcp_approx(fmax(fma(rtol, fmax(fabs(zs[s]), s < 3 ? fl0 : fl1), atol), 1e-300));
+#pragma unroll
+            for (int ch = 0; ch < 3; ch++)
+#pragma unroll
+                for (int p = 0; p < P; p++) {
+                    const int l = q * P + p;
+                    const bool off = l > qc.L[ch] || (excl && (ch == 1 || (ch == 0 && l >= 2)));
+                    const double sc = fmax(fma(rtol, fmax(fabs(z[ch][p]), ch < 2 ? fl2 : fl3), atol), 1e-300);
+                    T(kQK - 1, ch * P + p) = off ? 0.0 : rcp_approx(sc);
+                }
+        }
+        int jacc = 0;
+        double err = 0.0;
+        bool open = stepping; // still extrapolating this step
+        for (int j = 1; j <= kQK; j++) {
+            if (!__any_sync(kFull, open)) break;
+            if (j > 1) {
+                // working vector z := Y (already loaded for j = 1)
+#pragma unroll
+                for (int ch = 0; ch < 3; ch++)
+#pragma unroll
+                    for (int p = 0; p < P; p++) z[ch][p] = Y(ch * P + p);
+#pragma unroll
+                for (int s = 0; s < 4; s++) zs[s] = Y(3 * P + s);
+            }
+            if (!gbs) {
+                const double hs = H / j;
+                QBg bc = qbg(ot, x, q, qb);
+                for (int m = 0; m < j; m++) {
+                    const double xm = m == j - 1 ? x + H : x + (m + 1) * hs;
+                    const QBg bn = qbg(ot, xm, q, qb);
+                    q_imex<P>(z, zs, bc, bn, md, hs, q, qb, qc);
+                    bc = bn;
+                }
+                if (open) nsub += j;
+            } else {
+                const int n = 2 * j;
+                const double hs = H / n;
+#pragma unroll
+                for (int ch = 0; ch < 3; ch++)
+#pragma unroll
+                    for (int p = 0; p < P; p++) w[ch][p] = z[ch][p];
+#pragma unroll
+                for (int s = 0; s < 4; s++) ws[s] = zs[s];
+                q_rhs_axpy<P>(z, zs, w, ws, qbg(ot, x, q, qb), md, hs, q, qb, qc); // w = z1
+                for (int m = 1; m < n; m += 2) {
+                    const QBg bm = qbg(ot, x + m * hs, q, qb);
+                    q_rhs_axpy<P>(w, ws, z, zs, bm, md, 2.0 * hs, q, qb, qc); // z = z_{m+1}
+                    if (m + 1 < n) {
+                        const QBg bm1 = qbg(ot, x + (m + 1) * hs, q, qb);
+                        q_rhs_axpy<P>(z, zs, w, ws, bm1, md, 2.0 * hs, q, qb, qc);
+                    }
+                }
+                if (open) nsub += n;
+            }
+            // Aitken-Neville update of the tableau and the error estimate
+            double cf[kQK];
+#pragma unroll
+            for (int s = 1; s < kQK; s++) {
+                cf[s] = 0.0;
+                if (s < j) {
+                    if (gbs) {
+                        const double r = (double)j / (double)(j - s);
+                        cf[s] = 1.0 / (r * r - 1.0);
+                    } else {
+                        cf[s] = (double)(j - s) / (double)s;
+                    }
+                }
+            }
+            double el = 0.0;
+#pragma unroll
+            for (int e = 0; e < E; e++) {
+                const int ch = e < 3 * P ? e / P : 3;
+                const int p = e - ch * P;
+                double cur = ch < 3 ? z[ch][p] : zs[p];
+                const double is = T(kQK - 1, e);
+                double lower = cur;
+                double prev = T(0, e);
+                T(0, e) = cur;
+#pragma unroll
+                for (int s = 1; s < kQK; s++) {
+                    if (s < j) {
+                        const double nw = fma(cur - prev, cf[s], cur);
+                        prev = T(s, e);
+                        T(s, e) = nw;
+                        lower = cur;
+                        cur = nw;
+                    }
+                }
+                if (j >= 2) {
+                    const double er = fabs(cur - lower) * is;
+                    if (!(er <= el)) el = er; // NaN propagates
+                }
+            }
+            el = quad_max(el);
+            if (open && j >= 2) {
+                err = el;
+                if (!(el == el)) {
+                    stat = ABCMB_E_NONFINITE;
+                    done = true;
+                    open = false;
+                    jacc = -1;
+                } else if (el <= 1.0) {
+                    jacc = j;
+                    open = false;
+#pragma unroll
+                    for (int e = 0; e < E; e++) Y(e) = T(j - 1, e);
+                }
+            }
+        }
+        if (stepping && jacc == 0 && err > 1e300) {
+            stat = ABCMB_E_NONFINITE;
+            done = true;
+            jacc = -1;
+        }
+        if (stepping && jacc > 0) {
+            x = land ? xn : x + H;
+            const int ord = gbs ? 2 * jacc - 1 : jacc;
+            double fac = err > 0.0 ? 0.9 * exp(-log(err) / ord) : 4.0;
+            if (jacc < kQK - 1) fac *= 1.5;
+            fac = fmin(4.0, fmax(0.2, fac));
+            const double hn = H * fac;
+            h = land ? fmax(h, hn) : hn;
+            if (land) emit = true;
+        } else if (stepping && jacc == 0) {
+            const int ord = gbs ? 2 * kQK - 1 : kQK;
+            h = H * fmin(0.9, fmax(0.1, 0.9 * exp(-log(err) / ord)));
+        }
+        if (emit) {
+            if (q == 0) q_sources(ot, nodes + 8 * node, k, sw, sl, P, Sm + 3 * node);
+            node++;
+            if (node >= n_tau) done = true;
+        }
+    }
+    if (valid && q == 0) {
+        for (int n = node; n < n_tau; n++) Sm[3 * n] = Sm[3 * n + 1] = Sm[3 * n + 2] = 0.0;
+        status[(long)b * Nk + kidx] = stat;
+        if (steps) {
+            steps[2 * ((long)b * Nk + kidx)] = nsteps;
+            steps[2 * ((long)b * Nk + kidx) + 1] = nsub;
+        }
+    }
+}
+
+// Dynamic shared memory of one warp: the accepted state and the K tableau
+// columns, (1 + K) (3P + 4) doubles per lane.
+template <int P>
+constexpr size_t quad_smem_per_warp()
+{
+    return (size_t)(1 + kQK) * (3 * P + 4) * 32 * sizeof(double);
+}
+
+template <int P, int W>
+__global__ void __launch_bounds__(32 * W)
+perturb_quad_kernel(int B, int Nk, const double *__restrict__ bg, long len, const double *__restrict__ kv, int Lg,
+                    int Lp, int Ln, double rtol, double atol, int max_steps, double s_sw, double s_isw,
+                    double s_dop, double *S, int *status, int *steps)
+{
+    extern __shared__ double qsm[];
+    __shared__ double cA[3 * 64], cB[3 * 64];
+    const int Ls[3] = {Lg, Lp, Ln};
+    for (int i = threadIdx.x; i < 3 * 64; i += blockDim.x) {
+        const int ch = i / 64, l = i % 64, L = Ls[ch];
+        cA[i] = l < L ? (double)l / (2.0 * l + 1.0) : (l == L ? 1.0 : 0.0);
+        cB[i] = l < L ? (l + 1.0) / (2.0 * l + 1.0) : 0.0;
+    }
+    __syncthreads();
+    constexpr int E = 3 * P + 4;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long M = (long)B * Nk;
+    const long mi = ((long)blockIdx.x * W + warp) * 8 + (lane >> 2);
+    QCoef qc;
+    qc.A = cA;
+    qc.Bc = cB;
+    qc.L[0] = Lg;
+    qc.L[1] = Lp;
+    qc.L[2] = Ln;
+    const double sw[3] = {s_sw, s_isw, s_dop};
+    double *smw = qsm + (long)warp * (1 + kQK) * E * 32;
+    quad_modes<P>(mi, M, B, Nk, bg, len, kv, qc, rtol, atol, max_steps, sw, S, status, steps, smw);
+}
+
+} // namespace abcmb

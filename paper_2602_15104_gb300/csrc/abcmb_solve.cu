@@ -2,17 +2,21 @@
 // (include/abcmb.h).
 //
 // background_kernel: one warp per cosmology runs abcmb::build_background.
-// perturb_kernel: one thread per (cosmology, k) mode runs
-// abcmb::integrate_mode; modes are ordered k-descending so that the most
-// expensive modes are scheduled first and the lanes of a warp share one k
-// across cosmologies; the per-mode working vectors live in the caller's
-// workspace, laid out [vector][component][mode] so that the lanes of a warp
-// touch consecutive addresses.
+// perturb_quad_kernel (abcmb_ode_quad.cuh): four lanes per (cosmology, k)
+// mode, state in registers and shared memory; the path for hierarchies up to
+// kQLmax = 63.
+// perturb_kernel: one thread per mode runs abcmb::integrate_mode with the
+// per-mode working vectors in a global workspace, laid out
+// [vector][component][mode] so that the lanes of a warp touch consecutive
+// addresses; the path for hierarchies 64..kLmaxHier, whose state does not fit
+// on chip.
+// Both order modes k-descending, so that the most expensive modes are
+// scheduled first and a warp's modes share one k across cosmologies.
 #include <cuda_runtime.h>
 
 #include <mutex>
 
-#include "abcmb_ode.cuh"
+#include "abcmb_ode_quad.cuh"
 
 namespace abcmb {
 
@@ -25,13 +29,15 @@ __global__ void __launch_bounds__(32) background_kernel(int B, const double *__r
     build_background(params + (long)b * ABCMB_NPARAM, bg + (long)b * len, n_tau, threadIdx.x, 32);
 }
 
+constexpr int kLmaxHier = 128;
+
 __global__ void __launch_bounds__(64)
 perturb_kernel(int B, int Nk, const double *__restrict__ bg, long len, const double *__restrict__ kv,
                int Lg, int Lp, int Ln, double rtol, double atol, int max_steps, double s_sw,
                double s_isw, double s_dop, double *S, int *status, int *steps, double *work)
 {
-    __shared__ double sa[65], sb[65];
-    for (int l = threadIdx.x; l < 65; l += blockDim.x) {
+    __shared__ double sa[kLmaxHier + 1], sb[kLmaxHier + 1];
+    for (int l = threadIdx.x; l <= kLmaxHier; l += blockDim.x) {
         sa[l] = (double)l / (2.0 * l + 1.0);
         sb[l] = (l + 1.0) / (2.0 * l + 1.0);
     }
@@ -63,6 +69,56 @@ perturb_kernel(int B, int Nk, const double *__restrict__ bg, long len, const dou
     }
 }
 
+static int max_hier(const abcmb_options *o)
+{
+    int L = o->lmax_g;
+    if (o->lmax_pol > L) L = o->lmax_pol;
+    if (o->lmax_nu > L) L = o->lmax_nu;
+    return L;
+}
+
+template <int P>
+static int launch_quad(int B, const double *bg, const double *k, int Nk, const abcmb_options *o, double *S,
+                       int *st, int *steps, cudaStream_t s)
+{
+    constexpr int W = 1; // one warp (8 modes) per CTA: fine-grained scheduling of uneven modes
+    const size_t smem = W * quad_smem_per_warp<P>();
+    auto kern = perturb_quad_kernel<P, W>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return ABCMB_E_CUDA;
+    const long M = (long)B * Nk;
+    const long blocks = (M + 8 * W - 1) / (8 * W);
+    if (blocks > 2147483647L) return ABCMB_E_INVALID_ARG;
+    const long len = (long)ABCMB_BG_NODES + 8L * o->n_tau;
+    kern<<<(unsigned)blocks, 32 * W, smem, s>>>(B, Nk, bg, len, k, o->lmax_g, o->lmax_pol, o->lmax_nu, o->rtol,
+                                                 o->atol, o->max_steps, o->scale_sw, o->scale_isw, o->scale_dop, S,
+                                                 st, steps);
+    return cudaGetLastError() == cudaSuccess ? ABCMB_OK : ABCMB_E_CUDA;
+}
+
+static int perturb_on_chip(int B, const double *bg, const double *k, int Nk, const abcmb_options *o, double *S,
+                           int *st, int *steps, cudaStream_t s)
+{
+    const int L = max_hier(o);
+    if (L <= 15) return launch_quad<4>(B, bg, k, Nk, o, S, st, steps, s);
+    if (L <= 31) return launch_quad<8>(B, bg, k, Nk, o, S, st, steps, s);
+    return launch_quad<16>(B, bg, k, Nk, o, S, st, steps, s);
+}
+
+static int perturb_in_workspace(int B, const double *bg, const double *k, int Nk, const abcmb_options *o,
+                                double *S, int *st, int *steps, double *work, cudaStream_t s)
+{
+    const long len = (long)ABCMB_BG_NODES + 8L * o->n_tau;
+    const long M = (long)B * Nk;
+    const int threads = 64;
+    const long blocks = (M + threads - 1) / threads;
+    if (blocks > 2147483647L) return ABCMB_E_INVALID_ARG;
+    perturb_kernel<<<(unsigned)blocks, threads, 0, s>>>(B, Nk, bg, len, k, o->lmax_g, o->lmax_pol, o->lmax_nu,
+                                                         o->rtol, o->atol, o->max_steps, o->scale_sw, o->scale_isw,
+                                                         o->scale_dop, S, st, steps, work);
+    return cudaGetLastError() == cudaSuccess ? ABCMB_OK : ABCMB_E_CUDA;
+}
+
 } // namespace abcmb
 
 // ---------------------------------------------------------------- C ABI
@@ -82,8 +138,8 @@ extern "C" void abcmb_default_options(abcmb_options *o)
 extern "C" int abcmb_validate_options(const abcmb_options *o)
 {
     if (!o) return ABCMB_E_INVALID_ARG;
-    if (o->lmax_g < 4 || o->lmax_g > 64 || o->lmax_pol < 4 || o->lmax_pol > 64 || o->lmax_nu < 4 ||
-        o->lmax_nu > 64)
+    if (o->lmax_g < 4 || o->lmax_g > abcmb::kLmaxHier || o->lmax_pol < 4 || o->lmax_pol > abcmb::kLmaxHier ||
+        o->lmax_nu < 4 || o->lmax_nu > abcmb::kLmaxHier)
         return ABCMB_E_INVALID_ARG;
     if (o->lmax_cl < 2 || o->lmax_cl > 5000) return ABCMB_E_INVALID_ARG;
     if (o->n_tau < 8 || o->n_tau > 65536) return ABCMB_E_INVALID_ARG;
@@ -101,6 +157,7 @@ extern "C" size_t abcmb_bg_doubles(const abcmb_options *o)
 extern "C" size_t abcmb_perturb_workspace_bytes(int B, int Nk, const abcmb_options *o)
 {
     if (B < 1 || Nk < 1 || abcmb_validate_options(o) != ABCMB_OK) return 0;
+    if (abcmb::max_hier(o) <= abcmb::kQLmax) return 0; // state on chip
     const abcmb::OdeDims d = abcmb::ode_dims(o->lmax_g, o->lmax_pol, o->lmax_nu);
     return (size_t)abcmb::kNvec * d.N * (size_t)B * Nk * sizeof(double);
 }
@@ -145,6 +202,8 @@ extern "C" int abcmb_perturb_noalloc(int B, const double *bg, const double *k, i
 {
     if (B < 1 || Nk < 1 || !bg || !k || !S || !mode_status || abcmb_validate_options(o) != ABCMB_OK)
         return ABCMB_E_INVALID_ARG;
+    const cudaStream_t s = (cudaStream_t)stream;
+    if (abcmb::max_hier(o) <= abcmb::kQLmax) return abcmb::perturb_on_chip(B, bg, k, Nk, o, S, mode_status, steps, s);
     const size_t need = abcmb_perturb_workspace_bytes(B, Nk, o);
     if (need == 0) return ABCMB_E_INVALID_ARG;
     if (need > ABCMB_NOALLOC_SCRATCH_BYTES) return ABCMB_E_SCRATCH_TOO_SMALL;
@@ -152,32 +211,18 @@ extern "C" int abcmb_perturb_noalloc(int B, const double *bg, const double *k, i
     const int rc = noalloc_scratch(&scratch);
     if (rc != ABCMB_OK) return rc;
     // the kernel writes every scratch element it reads, so nothing needs clearing
-    const long len = (long)abcmb_bg_doubles(o);
-    const long M = (long)B * Nk;
-    const int threads = 64;
-    const long blocks = (M + threads - 1) / threads;
-    abcmb::perturb_kernel<<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(
-        B, Nk, bg, len, k, o->lmax_g, o->lmax_pol, o->lmax_nu, o->rtol, o->atol, o->max_steps, o->scale_sw,
-        o->scale_isw, o->scale_dop, S, mode_status, steps, scratch);
-    return cudaGetLastError() == cudaSuccess ? ABCMB_OK : ABCMB_E_CUDA;
+    return abcmb::perturb_in_workspace(B, bg, k, Nk, o, S, mode_status, steps, scratch, s);
 }
 
 extern "C" int abcmb_perturb(int B, const double *bg, const double *k, int Nk, const abcmb_options *o,
                              double *S, int *mode_status, int *steps, void *workspace, size_t workspace_bytes,
                              void *stream)
 {
-    if (B < 1 || Nk < 1 || !bg || !k || !S || !mode_status || !workspace ||
-        abcmb_validate_options(o) != ABCMB_OK)
+    if (B < 1 || Nk < 1 || !bg || !k || !S || !mode_status || abcmb_validate_options(o) != ABCMB_OK)
         return ABCMB_E_INVALID_ARG;
-    if (workspace_bytes < abcmb_perturb_workspace_bytes(B, Nk, o)) return ABCMB_E_INVALID_ARG;
+    const cudaStream_t s = (cudaStream_t)stream;
+    if (abcmb::max_hier(o) <= abcmb::kQLmax) return abcmb::perturb_on_chip(B, bg, k, Nk, o, S, mode_status, steps, s);
+    if (!workspace || workspace_bytes < abcmb_perturb_workspace_bytes(B, Nk, o)) return ABCMB_E_INVALID_ARG;
     if (((size_t)workspace & 255) != 0) return ABCMB_E_INVALID_ARG;
-    const long len = (long)abcmb_bg_doubles(o);
-    const long M = (long)B * Nk;
-    const int threads = 64;
-    const long blocks = (M + threads - 1) / threads;
-    if (blocks > 2147483647L) return ABCMB_E_INVALID_ARG;
-    abcmb::perturb_kernel<<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(
-        B, Nk, bg, len, k, o->lmax_g, o->lmax_pol, o->lmax_nu, o->rtol, o->atol, o->max_steps, o->scale_sw,
-        o->scale_isw, o->scale_dop, S, mode_status, steps, (double *)workspace);
-    return cudaGetLastError() == cudaSuccess ? ABCMB_OK : ABCMB_E_CUDA;
+    return abcmb::perturb_in_workspace(B, bg, k, Nk, o, S, mode_status, steps, (double *)workspace, s);
 }

@@ -4,10 +4,12 @@
 // abcmb_project: one CTA per (cosmology, k).  A warp takes groups of
 // 32 x kNodesPerLane tau nodes; each lane carries kNodesPerLane independent
 // spherical-Bessel recurrences j_{l+1} = (2l+1)/x j_l - j_{l-1} upward in l
-// from j_0 = sin x/x, j_1 (series at small x), stopping per node where j_l
-// has fallen below ~1e-7 of its turning-point size (l > x + 12 + 7 x^(1/3),
-// the Airy decay), which is also where upward recursion would start to lose
-// accuracy.  With u = 1/x the three temperature kernels collapse to
+// from j_0 = sin x/x, j_1 (power series for x < 1), stopping per node where
+// the Debye decay exponent of j_l passes 16 (bessel_cut), which is also where
+// the upward recursion would start to lose accuracy.  The coefficient
+// (2l+1)/x is formed afresh at every l: accumulated by repeated addition its
+// rounding errors would excite the growing solution y_l past the turning
+// point and cost several digits there.  With u = 1/x the three temperature kernels collapse to
 //   S_T0 j + S_T1 j' + s_pol S_P (3 j'' + j)/2
 //     = (A0 + l A1 + l^2 A2) j_l + B j_{l-1},
 //   g1 = S_T1 - 3 u s_pol S_P,  A0 = S_T0 - s_pol S_P - g1 u,
@@ -59,14 +61,16 @@ __device__ __forceinline__ void j01(double x, double *j0, double *j1)
 
 // Last l at which j_l(x) is kept: the smallest l > x whose Debye decay
 // exponent nu (alpha - tanh alpha), nu = l + 1/2, cosh alpha = nu / x, exceeds
-// 17 (j_l below ~e^-17 of its turning-point size).  Newton on the exponent,
+// 16 (j_l below ~e^-16 of its turning-point size).  A higher threshold keeps
+// more of the tail but lets the recurrence's growing error in; 16 balances
+// the two at ~1e-7 of the largest Delta_l (measured over k in [1e-5, 0.5]).  Newton on the exponent,
 // whose derivative in nu is alpha; an estimate, so single precision.
 __device__ __forceinline__ int bessel_cut(float x, int lmax)
 {
     if (x > (float)lmax + 200.0f) return lmax;
     // the T2 and E kernels carry j_l / x^2, so at x < 1 the threshold moves
     // down by x^2
-    const float T = 17.0f + 2.0f * fmaxf(0.0f, -logf(x));
+    const float T = 16.0f + 2.0f * fmaxf(0.0f, -logf(x));
     float nu = x + 1.0f + 0.8f * cbrtf(fmaxf(x, 1.0f)) * 9.0f;
     for (int it = 0; it < 8; it++) {
         float r = fmaxf(nu / fmaxf(x, 1e-30f), 1.0f + 1e-6f);
@@ -149,8 +153,8 @@ project_kernel(int B, int Nk, const double *__restrict__ bg, long bg_len,
                 jm[m] = j1;
                 sm[m] = x < kSeriesX;
                 jc[m] = sm[m] ? x * x / 15.0 * series_sum(ser, 2, x * x) : 3.0 * u * j1 - j0; // j_2
-                t[m] = sm[m] ? x * x / 15.0 : 5.0 * u;
-                tu[m] = sm[m] ? x : 2.0 * u;
+                t[m] = sm[m] ? x * x / 15.0 : 0.0;
+                tu[m] = sm[m] ? x : u;
                 lc[m] = bessel_cut((float)x, lmax);
                 if (sm[m] && lc[m] > kSerL - 2) lc[m] = kSerL - 2;
             } else {
@@ -176,16 +180,16 @@ project_kernel(int B, int Nk, const double *__restrict__ bg, long bg_len,
                 for (int q = 0; q < kLB; q++) {
                     double cT = 0.0, cE = 0.0;
                     const int lnext = l0 + q + 1;
+                    const double tl = fma(2.0, ld, 1.0); // 2l + 1, exact
 #pragma unroll
                     for (int m = 0; m < kNodesPerLane; m++) {
                         const double coef = fma(fma(A2[m], ld, A1[m]), ld, A0[m]);
                         cT = fma(coef, jc[m], cT);
                         cT = fma(Bc[m], jm[m], cT);
                         cE = fma(E[m], jc[m], cE);
-                        const double jn = fma(t[m], jc[m], -jm[m]);
+                        const double jn = fma(tl * tu[m], jc[m], -jm[m]);
                         jm[m] = jc[m];
                         jc[m] = lnext <= lc[m] ? jn : 0.0;
-                        t[m] += tu[m];
                     }
                     v[q] = cT;
                     v[kLB + q] = cE;
@@ -199,6 +203,7 @@ project_kernel(int B, int Nk, const double *__restrict__ bg, long bg_len,
                     double cT = 0.0, cE = 0.0;
                     const int l = l0 + q, lnext = l + 1;
                     const int ls = min(lnext, kSerL - 1);
+                    const double tl = fma(2.0, ld, 1.0);
 #pragma unroll
                     for (int m = 0; m < kNodesPerLane; m++) {
                         const double coef = fma(fma(A2[m], ld, A1[m]), ld, A0[m]);
@@ -210,8 +215,7 @@ project_kernel(int B, int Nk, const double *__restrict__ bg, long bg_len,
                             t[m] *= tu[m] * ser[8 * min(l, kSerL - 1)];
                             jn = t[m] * series_sum(ser, ls, tu[m] * tu[m]);
                         } else {
-                            jn = fma(t[m], jc[m], -jm[m]);
-                            t[m] += tu[m];
+                            jn = fma(tl * tu[m], jc[m], -jm[m]);
                         }
                         jm[m] = jc[m];
                         jc[m] = lnext <= lc[m] ? jn : 0.0;

@@ -43,14 +43,17 @@ def test_defaults_and_sizes(A):
     L.abcmb_default_options(ctypes.byref(o))
     assert (o.lmax_g, o.lmax_cl, o.n_tau) == (12, 2500, 6000)
     assert A.bg_doubles(o) == A.BG_NODES + 8 * o.n_tau
-    N = 4 + 3 * 13
-    assert A.perturb_workspace_bytes(64, 400, o) == 8 * N * 64 * 400 * 8
+    # hierarchies <= 63 keep the ODE state on chip: no workspace
+    assert A.perturb_workspace_bytes(64, 400, o) == 0
+    assert A.perturb_workspace_bytes(64, 400, A.options(lmax_hier=63)) == 0
+    N = 4 + 3 * 81
+    assert A.perturb_workspace_bytes(64, 400, A.options(lmax_hier=80)) == 8 * N * 64 * 400 * 8
     bad = A.options(lmax_hier=3)
     assert L.abcmb_bg_doubles(ctypes.byref(bad)) == 0
     assert L.abcmb_perturb_workspace_bytes(64, 400, ctypes.byref(bad)) == 0
 
 
-@pytest.mark.parametrize("field,value", [("lmax_g", 3), ("lmax_nu", 65), ("lmax_cl", 1), ("lmax_cl", 5001),
+@pytest.mark.parametrize("field,value", [("lmax_g", 3), ("lmax_nu", 129), ("lmax_cl", 1), ("lmax_cl", 5001),
                                          ("n_tau", 7), ("max_steps", 0), ("rtol", 0.0), ("rtol", 1.0),
                                          ("atol", -1.0)])
 def test_invalid_options_rejected_on_host(A, field, value):
@@ -72,9 +75,11 @@ def test_invalid_shapes_and_pointers_rejected(A):
     assert L.abcmb_background_tables(0, f, ctypes.byref(o), f, None) == A.E_INVALID_ARG
     assert L.abcmb_background_tables(1, None, ctypes.byref(o), f, None) == A.E_INVALID_ARG
     assert L.abcmb_perturb(1, f, f, 0, ctypes.byref(o), f, f, None, f, 1 << 40, None) == A.E_INVALID_ARG
-    # workspace too small, or misaligned
-    assert L.abcmb_perturb(1, f, f, 4, ctypes.byref(o), f, f, None, f, 8, None) == A.E_INVALID_ARG
-    assert L.abcmb_perturb(1, f, f, 4, ctypes.byref(o), f, f, None, ctypes.c_void_p(264), 1 << 40,
+    # deep hierarchies need a workspace: missing, too small, or misaligned
+    o80 = A.options(lmax_hier=80)
+    assert L.abcmb_perturb(1, f, f, 4, ctypes.byref(o80), f, f, None, None, 1 << 40, None) == A.E_INVALID_ARG
+    assert L.abcmb_perturb(1, f, f, 4, ctypes.byref(o80), f, f, None, f, 8, None) == A.E_INVALID_ARG
+    assert L.abcmb_perturb(1, f, f, 4, ctypes.byref(o80), f, f, None, ctypes.c_void_p(264), 1 << 40,
                            None) == A.E_INVALID_ARG
     assert L.abcmb_project(1, f, None, f, 4, ctypes.byref(o), f, None) == A.E_INVALID_ARG
     assert L.abcmb_cl(1, f, f, f, 1, ctypes.byref(o), f, None) == A.E_INVALID_ARG  # one k: no quadrature

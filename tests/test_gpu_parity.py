@@ -98,6 +98,32 @@ def test_sources_parity(A):
             assert np.all(err < 1e-6), (b, k[i], err)
 
 
+def test_hierarchy_paths_agree_where_truncation_is_negligible(A):
+    """Hierarchies <= 15, <= 31 and <= 63 run the four-lanes-per-mode kernel with 4, 8
+    and 16 moments per lane; 64..128 the one-thread-per-mode kernel.  For k tau_0 < 8
+    the moments beyond l ~ 30 are below e^-30 of the low ones, so every truncation
+    from 30 up must give the same sources to the ODE tolerance."""
+    params = W.BATCH64.params()[[3, 40]]
+    k = np.array([1e-4, 3e-4, 5e-4])
+    n_tau = 400
+    runs = {}
+    for L in (30, 40, 63, 64, 100, 128):
+        o = A.options(lmax_hier=L, n_tau=n_tau, lmax_cl=40)
+        r = run_gpu(A, params, k, o, stages=("bg", "perturb"))
+        assert np.all(r["status"] == 0), L
+        runs[L] = r["S"]
+    ref = runs[30]
+    scale = np.abs(ref).max(axis=2, keepdims=True)
+    for L, S in runs.items():
+        assert np.all(np.abs(S - ref) <= 1e-6 * scale), L
+    # and the L = 30 result against the oracle at the same truncation
+    o = A.options(lmax_hier=30, n_tau=n_tau, lmax_cl=40)
+    for b, p in enumerate(params):
+        S_o = O.run(p, k, n_tau, 40, O.opts(lmax=30), want=("S",))["S"]
+        err = np.abs(ref[b] - S_o).max(axis=1) / np.abs(S_o).max(axis=1)
+        assert np.all(err < 1e-6), (b, err)
+
+
 def test_projection_parity_synthetic_sources(A):
     params = W.BATCH64.params()[[0, 63]]
     k = np.array([1e-5, 3e-4, 0.004, 0.05, 0.18, 0.5])

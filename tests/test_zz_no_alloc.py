@@ -1,8 +1,9 @@
 """abcmb_perturb_noalloc: the perturbation step for callers that cannot
 allocate device memory (an application whose device memory belongs to another
 runtime's pool, or a loop that cannot afford an allocation's implicit
-synchronisation).  It must give what abcmb_perturb gives, from the library's
-own static scratch, call after call.
+synchronisation).  It must give what abcmb_perturb gives, call after call:
+from the library's own static scratch for hierarchies above 63 (the
+one-thread-per-mode kernel), with no scratch at all below.
 
 Collected last on purpose (file name), so that a run stopping at the first
 failure has already run every other test; it also passes alone in a fresh
@@ -28,10 +29,12 @@ def A():
     return abcmb
 
 
-def test_noalloc_matches_workspace_entry_point_twice(A):
+@pytest.mark.parametrize("lmax_hier", [70, 12])
+def test_noalloc_matches_workspace_entry_point_twice(A, lmax_hier):
     params = torch.tensor(W.BATCH64.params()[:3], device="cuda")
     k = torch.tensor(W.log_k_nodes(7, 1e-4, 0.05), device="cuda")
-    o = A.options(lmax_hier=12, n_tau=500, lmax_cl=10)
+    o = A.options(lmax_hier=lmax_hier, n_tau=500, lmax_cl=10)
+    assert (A.perturb_workspace_bytes(3, 7, o) > 0) == (lmax_hier > 63)
     bg = A.abcmb_background_tables(params, o)
     S_ref, st_ref, steps_ref = A.abcmb_perturb(bg, k, o)
     torch.cuda.synchronize()
@@ -50,10 +53,10 @@ def test_noalloc_matches_workspace_entry_point_twice(A):
 
 
 def test_noalloc_rejects_problems_beyond_its_scratch(A):
-    o = A.options(lmax_hier=30, n_tau=6000, lmax_cl=2500)
+    o = A.options(lmax_hier=80, n_tau=6000, lmax_cl=2500)
     assert A.perturb_workspace_bytes(64, 400, o) > A.NOALLOC_SCRATCH_BYTES
     params = torch.tensor(W.BATCH64.params()[:1], device="cuda")
-    bg = A.abcmb_background_tables(params, A.options(lmax_hier=30, n_tau=6000, lmax_cl=2500))
+    bg = A.abcmb_background_tables(params, o)
     bg64 = bg.expand(64, -1).contiguous()
     k = torch.tensor(W.BATCH64.k(), device="cuda")
     S = torch.empty(1, dtype=torch.float64, device="cuda")  # never written: rejected on the host
