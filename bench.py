@@ -193,6 +193,64 @@ def run_reference(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+def run_serving(args, A, torch):
+    """Serving benchmark: requests arrive as a Poisson process (seeded), each a
+    cosmology from the priors with lmax_cl uniform on {500, 1000, 2000, 2500,
+    3500} and n_k = 0.16 lmax_cl log-spaced k in [1e-5, 0.5] (hierarchies 30,
+    6000 tau nodes, FP64 ODE, FP32 projection), submitted to abcmb_server at
+    their arrival times; latency = completion - arrival on the host clock."""
+    rng = np.random.default_rng(20260106)
+    n = args.requests
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=n))
+    lmaxes = rng.choice([500, 1000, 2000, 2500, 3500], size=n)
+    nks = np.round(0.16 * lmaxes).astype(int)
+    params = W.draw_cosmologies(n, 20260105)
+    o = A.options(lmax_hier=30, n_tau=6000, rtol=args.rtol)
+    srv = A.Server(int(args.arena_gb * (1 << 30)), args.slots, 3500, int(nks.max()), o)
+    # warm-up: one request of each size, not timed
+    for i, lm in enumerate([500, 1000, 2000, 2500, 3500]):
+        srv.submit(-1 - i, params[i], lm, int(round(0.16 * lm)), 1e-5, 0.5)
+    done = 0
+    while done < 5:
+        srv.progress()
+        while srv.poll() is not None:
+            done += 1
+        time.sleep(0.001)
+    clocks = ClockSampler()
+    clocks.start()
+    t0 = time.perf_counter()
+    nxt, finished, lat, bad, in_flight = 0, 0, np.zeros(n), 0, []
+    while finished < n:
+        now = time.perf_counter() - t0
+        while nxt < n and arrivals[nxt] <= now:
+            rc = srv.submit(nxt, params[nxt], int(lmaxes[nxt]), int(nks[nxt]), 1e-5, 0.5)
+            if rc != A.OK:
+                raise RuntimeError(f"submit failed: {rc}")
+            nxt += 1
+        in_flight.append(srv.progress())
+        r = srv.poll()
+        while r is not None:
+            tag, st, _ = r
+            lat[tag] = time.perf_counter() - t0 - arrivals[tag]
+            bad += st != A.OK
+            finished += 1
+            r = srv.poll()
+        time.sleep(0.0005)
+    makespan = time.perf_counter() - t0
+    clk = clocks.stop()
+    srv.close()
+    out = {"metric": "served C_l spectra/s (mixed precision), p50/p99 latency", "value": n / makespan,
+           "unit": "spectra/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f64+f32", "data": "synthetic",
+           "config": {"workload": "serving_poisson_lmax500-3500", "requests": n, "rate_per_s": args.rate,
+                      "nk_per_lmax": 0.16, "hierarchy_lmax": 30, "n_tau": 6000, "slots": args.slots,
+                      "arena_gb": args.arena_gb, "rtol": args.rtol},
+           "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                         "mean": float(lat.mean())},
+           "makespan_s": makespan, "failed": int(bad), "mean_in_flight": float(np.mean(in_flight)),
+           "clocks": clk}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -200,12 +258,20 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=W.BATCH64.name, choices=sorted(W.WORKLOADS))
-    ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--rtol", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=None,
                     help="cosmologies per step (default: the workload's); smaller cases are for profiling")
     ap.add_argument("--n-k", type=int, default=None,
                     help="k modes (default: the workload's), log-spaced over the workload's range")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="mixed: FP64 ODE, FP32 projection and k-quadrature with Kahan sums")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving benchmark: Poisson arrivals of mixed-size requests through abcmb_server")
+    ap.add_argument("--requests", type=int, default=4096)
+    ap.add_argument("--rate", type=float, default=200.0, help="mean arrivals per second")
+    ap.add_argument("--slots", type=int, default=32)
+    ap.add_argument("--arena-gb", type=float, default=24.0)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -213,11 +279,20 @@ def main():
         run_reference(args, rank, world)
         return
 
+    if args.serve:
+        # one hardware work queue per server slot (the default 8 would alias the
+        # slots' streams onto 8 queues and serialise their kernels); read once,
+        # when the CUDA context is created
+        os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     import torch
     from paper_2602_15104_gb300 import abcmb as A
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    if args.serve:
+        if rank == 0:
+            run_serving(args, A, torch)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -228,7 +303,10 @@ def main():
     k = W.log_k_nodes(args.n_k, wl.k_min, wl.k_max) if args.n_k else wl.k()
     o = A.options(lmax_hier=wl.l_max_hier, lmax_cl=wl.l_max_cl, n_tau=wl.n_tau, rtol=args.rtol)
     N = 4 + 3 * (wl.l_max_hier + 1)
-    pipe = A.Pipeline(B, k, o)
+    mixed = args.precision == "mixed"
+    pipe = A.Pipeline(B, k, o, mixed=mixed)
+    project = A.abcmb_project_mixed if mixed else A.abcmb_project
+    quadrature = A.abcmb_cl_mixed if mixed else A.abcmb_cl
     p_dev = torch.tensor(params, dtype=torch.float64, device="cuda")
     p_host = torch.from_numpy(params).pin_memory()
     cl_host = torch.empty((B, 3, o.lmax_cl - 1), dtype=torch.float64, pin_memory=True)
@@ -262,9 +340,9 @@ def main():
         A.abcmb_perturb(pipe.bg, pipe.k, o, S=pipe.S, status=pipe.status, steps=pipe.steps,
                         workspace=pipe.ws)
         ev[2].record(stream)
-        A.abcmb_project(pipe.bg, pipe.S, pipe.k, o, out=pipe.D)
+        project(pipe.bg, pipe.S, pipe.k, o, out=pipe.D)
         ev[3].record(stream)
-        A.abcmb_cl(pipe.bg, pipe.D, pipe.k, o, out=pipe.C)
+        quadrature(pipe.bg, pipe.D, pipe.k, o, out=pipe.C)
         ev[4].record(stream)
         torch.cuda.synchronize()
         for i, n in enumerate(names):
@@ -318,10 +396,11 @@ def main():
     out = {
         "metric": METRIC, "value": value, "unit": "spectra/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f64+f32" if mixed else "f64", "data": "synthetic",
         "config": {"workload": wl.name, "batch": B, "n_k": len(k), "k_range": [wl.k_min, wl.k_max],
                    "lmax_cl": wl.l_max_cl, "hierarchy_lmax": wl.l_max_hier, "n_tau": wl.n_tau,
-                   "rtol": args.rtol, "l2": "flushed (512 MiB write) between timed steps",
+                   "rtol": args.rtol, "precision": args.precision,
+                   "l2": "flushed (512 MiB write) between timed steps",
                    "parallelism": f"replicas x{world}"},
         "clocks": clk,
         "e2e": {"value": whole_job_rate(B, world, t_e2e), "unit": "spectra/s",

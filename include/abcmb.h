@@ -6,12 +6,14 @@
  *   abcmb_perturb             per-k stiff linear perturbation ODEs -> CMB sources
  *   abcmb_project             line-of-sight projection -> transfer functions
  *   abcmb_cl                  k-quadrature -> C_ell^{TT,TE,EE}
+ *   abcmb_project_mixed, abcmb_cl_mixed   the same two steps in FP32
  *
  * Conventions shared by every entry point
  *   - Every pointer argument is a DEVICE pointer allocated by the caller
  *     (the library allocates nothing and keeps no state between calls), unless
  *     its name ends in _host.  Every array is C-contiguous float64 (int32 for
- *     status/step arrays) in the layout stated at each argument.
+ *     status/step arrays, float32 where a name ends in 32) in the layout
+ *     stated at each argument.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Calls only enqueue work on it; results are valid once the
  *     stream has been synchronised.
@@ -64,7 +66,9 @@ typedef struct {
 } abcmb_options;
 
 /* Fill *o with the defaults used by the library's tests: hierarchies 12,
-   lmax_cl 2500, 6000 tau nodes, rtol 1e-8, atol 1e-12, switches 1. */
+   lmax_cl 2500, 6000 tau nodes, rtol 1e-6, atol 1e-12, switches 1.  At rtol
+   1e-6 the ODE moves C_l by <= 5e-7 relative against the converged solution
+   (measured on the 64-cosmology, l <= 2500 workload). */
 void abcmb_default_options(abcmb_options *o);
 
 /* ABCMB_OK if every field of *o is in its stated range (o may be NULL:
@@ -213,6 +217,73 @@ int abcmb_project(int B, const double *bg, const double *S, const double *k, int
  */
 int abcmb_cl(int B, const double *bg, const double *Delta, const double *k, int Nk,
              const abcmb_options *o, double *Cl, void *stream);
+
+/*
+ * Mixed precision (the FP32 form of the two calls above; the sources stay
+ * FP64): same projection and k-quadrature, with every (node, l) product and
+ * the in-warp sums in FP32 and the sums over tau-node groups and over k
+ * Kahan-compensated in FP32.  x, 1/x, sin x and cos x are formed in FP64 per
+ * node; the Bessel recurrence runs in double-float (pairs of floats,
+ * ~2^-44 relative), since plain FP32 rounding would be amplified past the
+ * turning point.  Expected error against the FP64 path ~1e-5 of each
+ * spectrum's largest value (the projection's FP32 products do not
+ * compensate).
+ *
+ *   Delta32 [B][Nk][lmax_cl-1][2] float32, device (written by
+ *           abcmb_project_mixed, read by abcmb_cl_mixed)
+ *   other arguments as abcmb_project / abcmb_cl; Cl is float64.
+ */
+int abcmb_project_mixed(int B, const double *bg, const double *S, const double *k, int Nk,
+                        const abcmb_options *o, float *Delta32, void *stream);
+int abcmb_cl_mixed(int B, const double *bg, const float *Delta32, const double *k, int Nk,
+                   const abcmb_options *o, double *Cl, void *stream);
+
+/*
+ * Continuous-batching spectrum server.  A host runtime over the calls above
+ * (no counterpart in the paper, which evaluates one cosmology per call):
+ * requests of different lmax_cl and k-grid size queue on the host and are
+ * admitted in arrival order as soon as a stream slot is free and the
+ * caller's device arena holds the request's buffers
+ * (abcmb_server_request_bytes: background record, k, sources, FP32 transfer
+ * functions, C_l).  Each admitted request runs the whole path on its slot's
+ * stream -- background tables, FP64 perturbations, FP32 projection and
+ * k-quadrature (abcmb_project_mixed / abcmb_cl_mixed), C_l copied back --
+ * so requests in flight overlap on the GPU.  Per-request results are
+ * independent of what else is in flight (no shared state between slots).
+ *
+ * The server object, its streams, events and pinned host staging buffers are
+ * created by abcmb_server_create and released by abcmb_server_destroy; all
+ * device memory comes from the caller's arena (256-byte aligned, owned by
+ * the caller, outliving the server).  Not thread-safe: one host thread drives
+ * a server.  Hierarchy truncations must be <= 63 (on-chip ODE state).
+ *
+ *   abcmb_server_create   n_slots in 1..256 streams; requests up to
+ *                         max_lmax_cl and max_n_k; o gives the hierarchies,
+ *                         n_tau, tolerances and switches of every request
+ *   abcmb_server_submit   queue one request: params_host[6] (as
+ *                         abcmb_background_tables), lmax_cl, n_k log-spaced
+ *                         k in [k_min, k_max]; ABCMB_E_SCRATCH_TOO_SMALL if it
+ *                         could never fit the arena
+ *   abcmb_server_progress admit, launch and retire without blocking; returns
+ *                         the number of requests in flight, or a negated
+ *                         error code
+ *   abcmb_server_queued   requests waiting for admission
+ *   abcmb_server_poll     pop one finished request: returns 1 (tag, status --
+ *                         ABCMB_OK or the first failing status --, lmax_cl,
+ *                         C_l [3][lmax_cl - 1] into cl_host), 0 if none is
+ *                         ready, or a negated error code
+ */
+typedef struct abcmb_server abcmb_server;
+size_t abcmb_server_request_bytes(const abcmb_options *o, int lmax_cl, int n_k);
+int abcmb_server_create(void *arena, size_t arena_bytes, int n_slots, int max_lmax_cl, int max_n_k,
+                        const abcmb_options *o, abcmb_server **out);
+int abcmb_server_destroy(abcmb_server *s);
+int abcmb_server_submit(abcmb_server *s, long long tag, const double *params_host, int lmax_cl, int n_k,
+                        double k_min, double k_max);
+int abcmb_server_progress(abcmb_server *s);
+int abcmb_server_queued(const abcmb_server *s);
+int abcmb_server_poll(abcmb_server *s, long long *tag, int *status, int *lmax_cl, double *cl_host,
+                      size_t cl_capacity);
 
 #ifdef __cplusplus
 }

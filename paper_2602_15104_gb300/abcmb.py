@@ -47,7 +47,7 @@ class Options(ctypes.Structure):
                 ("scale_dop", ctypes.c_double), ("scale_pol", ctypes.c_double)]
 
 
-def options(lmax_hier=12, lmax_cl=2500, n_tau=6000, rtol=1e-8, atol=1e-12, max_steps=2_000_000,
+def options(lmax_hier=12, lmax_cl=2500, n_tau=6000, rtol=1e-6, atol=1e-12, max_steps=2_000_000,
             scale_sw=1.0, scale_isw=1.0, scale_dop=1.0, scale_pol=1.0, lmax_g=None, lmax_pol=None,
             lmax_nu=None) -> Options:
     o = Options()
@@ -83,6 +83,19 @@ def lib():
         L.abcmb_perturb_noalloc.argtypes = [ctypes.c_int, _P, _P, ctypes.c_int, O, _P, _P, _P, _P]
         L.abcmb_project.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, O, _P, _P]
         L.abcmb_cl.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, O, _P, _P]
+        L.abcmb_project_mixed.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, O, _P, _P]
+        L.abcmb_cl_mixed.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, O, _P, _P]
+        L.abcmb_server_request_bytes.argtypes = [O, ctypes.c_int, ctypes.c_int]
+        L.abcmb_server_request_bytes.restype = ctypes.c_size_t
+        L.abcmb_server_create.argtypes = [_P, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_int, O,
+                                          ctypes.POINTER(_P)]
+        L.abcmb_server_destroy.argtypes = [_P]
+        L.abcmb_server_submit.argtypes = [_P, ctypes.c_longlong, _P, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                          ctypes.c_double]
+        L.abcmb_server_progress.argtypes = [_P]
+        L.abcmb_server_queued.argtypes = [_P]
+        L.abcmb_server_poll.argtypes = [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int), _P, ctypes.c_size_t]
         _lib = L
     return _lib
 
@@ -184,11 +197,98 @@ def abcmb_cl(bg: torch.Tensor, Delta: torch.Tensor, k: torch.Tensor, o: Options,
     return C
 
 
+def abcmb_project_mixed(bg: torch.Tensor, S: torch.Tensor, k: torch.Tensor, o: Options, out=None):
+    """FP32 projection -> Delta32 [B, Nk, lmax_cl - 1, 2] float32 (T, E)."""
+    _dev(bg), _dev(S), _dev(k)
+    B, Nk = bg.shape[0], k.shape[0]
+    D = out if out is not None else torch.empty((B, Nk, o.lmax_cl - 1, 2), dtype=torch.float32,
+                                                device=bg.device)
+    if D.dtype != torch.float32:
+        raise TypeError("Delta32 must be float32")
+    _check(lib().abcmb_project_mixed(B, _ptr(bg), _ptr(S), _ptr(k), Nk, ctypes.byref(o), _ptr(D), _stream()),
+           "abcmb_project_mixed")
+    return D
+
+
+def abcmb_cl_mixed(bg: torch.Tensor, Delta32: torch.Tensor, k: torch.Tensor, o: Options, out=None):
+    """FP32 k-quadrature with Kahan sums -> C_l [B, 3, lmax_cl - 1] float64."""
+    _dev(bg), _dev(Delta32, torch.float32), _dev(k)
+    if Delta32.dtype != torch.float32:
+        raise TypeError("Delta32 must be float32")
+    B, Nk = bg.shape[0], k.shape[0]
+    C = out if out is not None else torch.empty((B, 3, o.lmax_cl - 1), dtype=torch.float64,
+                                                device=bg.device)
+    _check(lib().abcmb_cl_mixed(B, _ptr(bg), _ptr(Delta32), _ptr(k), Nk, ctypes.byref(o), _ptr(C), _stream()),
+           "abcmb_cl_mixed")
+    return C
+
+
+def server_request_bytes(o: Options, lmax_cl: int, n_k: int) -> int:
+    return lib().abcmb_server_request_bytes(ctypes.byref(o), lmax_cl, n_k)
+
+
+class Server:
+    """Continuous-batching spectrum server (abcmb_server_*): requests of any
+    lmax_cl / k-grid size queue here and run, overlapped on the GPU, as stream
+    slots and arena memory free up.  The device arena is a torch tensor owned
+    by this object."""
+
+    def __init__(self, arena_bytes: int, n_slots: int, max_lmax_cl: int, max_n_k: int, o: Options,
+                 device="cuda"):
+        self.o = o
+        self.max_lmax_cl = max_lmax_cl
+        self.arena = torch.empty(arena_bytes // 8, dtype=torch.float64, device=device)
+        h = ctypes.c_void_p()
+        _check(lib().abcmb_server_create(_ptr(self.arena), self.arena.numel() * 8, n_slots, max_lmax_cl,
+                                         max_n_k, ctypes.byref(o), ctypes.byref(h)), "abcmb_server_create")
+        self._h = h
+        self._buf = np.empty(3 * (max_lmax_cl - 1), dtype=np.float64)
+
+    def submit(self, tag: int, params, lmax_cl: int, n_k: int, k_min: float, k_max: float) -> int:
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        return lib().abcmb_server_submit(self._h, tag, p.ctypes.data_as(ctypes.c_void_p), lmax_cl, n_k,
+                                         k_min, k_max)
+
+    def progress(self) -> int:
+        n = lib().abcmb_server_progress(self._h)
+        if n < 0:
+            raise RuntimeError(f"abcmb_server_progress: {ERRORS.get(-n, -n)}")
+        return n
+
+    def queued(self) -> int:
+        return lib().abcmb_server_queued(self._h)
+
+    def poll(self):
+        """-> (tag, status, C_l [3, lmax_cl - 1]) or None."""
+        tag, st, lm = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_int()
+        r = lib().abcmb_server_poll(self._h, ctypes.byref(tag), ctypes.byref(st), ctypes.byref(lm),
+                                    self._buf.ctypes.data_as(ctypes.c_void_p), self._buf.size)
+        if r < 0:
+            raise RuntimeError(f"abcmb_server_poll: {ERRORS.get(-r, -r)}")
+        if r == 0:
+            return None
+        n = lm.value - 1
+        return tag.value, st.value, self._buf[:3 * n].reshape(3, n).copy()
+
+    def close(self):
+        if self._h:
+            lib().abcmb_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Pipeline:
     """Preallocated buffers for repeated whole-path calls of one shape."""
 
-    def __init__(self, B: int, k, o: Options, device="cuda"):
-        self.o, self.B = o, B
+    def __init__(self, B: int, k, o: Options, device="cuda", mixed: bool = False):
+        """mixed: FP32 projection and k-quadrature (abcmb_project_mixed /
+        abcmb_cl_mixed) after the FP64 ODE."""
+        self.o, self.B, self.mixed = o, B, mixed
         self.k = torch.as_tensor(np.asarray(k, dtype=np.float64), device=device).contiguous()
         Nk = self.k.shape[0]
         dev = self.k.device
@@ -198,7 +298,8 @@ class Pipeline:
         self.steps = torch.empty((B, Nk, 2), dtype=torch.int32, device=dev)
         nbytes = perturb_workspace_bytes(B, Nk, o)
         self.ws = torch.empty(nbytes // 8, dtype=torch.float64, device=dev) if nbytes else None
-        self.D = torch.empty((B, Nk, o.lmax_cl - 1, 2), dtype=torch.float64, device=dev)
+        self.D = torch.empty((B, Nk, o.lmax_cl - 1, 2), dtype=torch.float32 if mixed else torch.float64,
+                             device=dev)
         self.C = torch.empty((B, 3, o.lmax_cl - 1), dtype=torch.float64, device=dev)
         self.params = torch.empty((B, NPARAM), dtype=torch.float64, device=dev)
 
@@ -208,8 +309,12 @@ class Pipeline:
         abcmb_background_tables(p, self.o, out=self.bg)
         abcmb_perturb(self.bg, self.k, self.o, S=self.S, status=self.status, steps=self.steps,
                       workspace=self.ws)
-        abcmb_project(self.bg, self.S, self.k, self.o, out=self.D)
-        abcmb_cl(self.bg, self.D, self.k, self.o, out=self.C)
+        if self.mixed:
+            abcmb_project_mixed(self.bg, self.S, self.k, self.o, out=self.D)
+            abcmb_cl_mixed(self.bg, self.D, self.k, self.o, out=self.C)
+        else:
+            abcmb_project(self.bg, self.S, self.k, self.o, out=self.D)
+            abcmb_cl(self.bg, self.D, self.k, self.o, out=self.C)
         return self.C
 
     def run_host(self, params_host: np.ndarray, cl_host: torch.Tensor | None = None):

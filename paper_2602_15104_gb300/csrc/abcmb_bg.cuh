@@ -274,6 +274,72 @@ ABCMB_HD void tla_rhs(const Cosmo &c, double lna, double xp, double Tm_in, bool 
     *dTm = two ? (-2.0 * Tm + gamma_C(c, a, xe) / H * (T - Tm)) : 0.0;
 }
 
+// The parts of tla_rhs that depend on ln a alone, at one stage point.
+struct TlaPt {
+    double T, nH, H, K, be, bex, xhe, g0, e1, e2;
+};
+constexpr int kTlaPtDoubles = 10;
+
+ABCMB_HD TlaPt tla_point(const Cosmo &c, double lna)
+{
+    TlaPt P;
+    const double a = exp(lna), dum0 = 0.0;
+    (void)dum0;
+    double dum;
+    P.T = kTcmb0 / a;
+    P.nH = c.nH0 / (a * a * a);
+    P.H = H_sec(c, lna);
+    const double lam = kHc / (0.75 * kEH);
+    P.K = lam * lam * lam / (8.0 * kPi * P.H);
+    P.be = alpha_B(P.T) * saha_pref(P.T, mu_eH()) * exp(-0.25 * kEH / P.T);
+    P.bex = P.be * exp(-0.75 * kEH / P.T);
+    P.xhe = x_he(c, lna, &dum);
+    P.g0 = 8.0 * kSigmaT * kC * (c.rho_g0 / (a * a * a * a)) / (3.0 * kMe);
+    const double lt0 = log(P.T / kKB * 1.0e-4);
+    P.e1 = exp(-0.6166 * lt0);
+    P.e2 = exp(0.5300 * lt0);
+    return P;
+}
+
+// tla_rhs from a stage point's ln a-only parts.  Above z = 700 T_m = T (1 - r),
+// r = H / Gamma_C, and alpha_B(T_m) = alpha_B(T) scaled through (1 - r)^p, taken
+// from the series of log(1 - r) and exp while r < 0.02 (both truncated below
+// 1e-17); otherwise, and below z = 700, the rates are evaluated afresh.
+ABCMB_HD void tla_rhs_pt(const Cosmo &c, const TlaPt &P, double xp, double Tm_in, bool two, double *dxp,
+                         double *dTm)
+{
+    const double xe = xp + P.xhe;
+    const double gam = P.g0 * xe / (1.0 + c.f_He + xe);
+    double Tm, al;
+    if (!two) {
+        const double r = P.H / gam;
+        Tm = P.T * (1.0 - r);
+        if (r < 0.02) {
+            double L = 0.0, rn = 1.0;
+            for (int n = 1; n <= 12; n++) {
+                rn *= r;
+                L -= rn / n;
+            }
+            const double q1 = -0.6166 * L, q2 = 0.5300 * L;
+            double f1 = 1.0, f2 = 1.0;
+            for (int n = 8; n >= 1; n--) {
+                f1 = 1.0 + q1 * f1 / n;
+                f2 = 1.0 + q2 * f2 / n;
+            }
+            al = 4.309e-13 * P.e1 * f1 / (1.0 + 0.6703 * P.e2 * f2);
+        } else {
+            al = alpha_B(Tm);
+        }
+    } else {
+        Tm = Tm_in;
+        al = alpha_B(Tm);
+    }
+    const double n1s = P.nH * (1.0 - xp);
+    const double C = (1.0 + P.K * kL2s1s * n1s) / (1.0 + P.K * (kL2s1s + P.be) * n1s);
+    *dxp = -C * (al * P.nH * xe * xp - P.bex * (1.0 - xp)) / P.H;
+    *dTm = two ? (-2.0 * Tm + gam / P.H * (P.T - Tm)) : 0.0;
+}
+
 ABCMB_HD double nuT_closed(const Cosmo &c, double lna, double xe)
 {
     double a = exp(lna);
@@ -451,47 +517,88 @@ ABCMB_HD void build_background(const double *p, double *rec, int n_tau, int lane
     }
 
     // Peebles TLA (x_p, then also T_m below z = 700), RK4, stored at the table
-    // nodes at and after lna_sw: sequential, on lane 0
-    if (lane == 0) {
-        double dum;
+    // nodes at and after lna_sw.  The ln a-only parts of the right-hand side
+    // at the stage points of the one-step-per-cell stretch (cell starts and
+    // midpoints from node jc on) are tabulated by all lanes first, in the ODE
+    // table's space (filled only later); the integration itself is
+    // sequential, on lane 0: fine steps through the stiff transient after
+    // lna_sw, then one RK4 step per table cell, each cell's first stage being
+    // the previous node's stored derivative.
+    {
         const int j0 = (int)ceil((c.lna_sw - kLna0) * ABCMB_BG_PER_UNIT);
-        double x = c.lna_sw;
-        double y0 = xp_saha(c, x, &dum), y1 = 0.0;
-        bool two = false;
-        for (int j = j0; j < kNlna; j++) {
-            const double target = kLna0 + j * kDlna;
-            while (x < target) {
-                double hs = (x - c.lna_sw < kTlaFineSpan) ? kTlaFine : kDlna;
-                if (target - x < hs * (1.0 + 1e-9)) hs = target - x;
-                bool hit700 = false;
-                if (!two && x < kLna700 && x + hs >= kLna700) { hs = kLna700 - x; hit700 = true; }
-                double k1a, k1b, k2a, k2b, k3a, k3b, k4a, k4b;
-                tla_rhs(c, x, y0, y1, two, &k1a, &k1b);
-                tla_rhs(c, x + 0.5 * hs, y0 + 0.5 * hs * k1a, y1 + 0.5 * hs * k1b, two, &k2a, &k2b);
-                tla_rhs(c, x + 0.5 * hs, y0 + 0.5 * hs * k2a, y1 + 0.5 * hs * k2b, two, &k3a, &k3b);
-                tla_rhs(c, x + hs, y0 + hs * k3a, y1 + hs * k3b, two, &k4a, &k4b);
-                y0 += hs / 6.0 * (k1a + 2.0 * k2a + 2.0 * k3a + k4a);
-                y1 += hs / 6.0 * (k1b + 2.0 * k2b + 2.0 * k3b + k4b);
-                if (hit700) {
-                    x = kLna700;
-                    two = true;
-                    const double xe = y0 + x_he(c, x, &dum);
-                    y1 = kTcmb0 * exp(-x) * (1.0 - H_sec(c, x) / gamma_C(c, exp(x), xe));
-                } else {
-                    x += hs;
-                }
-                if (x > target - 1e-14) x = target;
-            }
-            double dxp, dTm;
-            tla_rhs(c, target, y0, y1, two, &dxp, &dTm);
-            double *r = tab + 8 * j;
-            r[C_XE] = y0;     // temporarily x_p
-            r[C_KAPPA] = dxp; // temporarily dx_p/dln a
-            r[C_CS2] = y1;    // temporarily T_m (z < 700)
-            r[C_DCS2] = dTm;  // temporarily dT_m/dln a
+        const int jc = (int)ceil((c.lna_sw + kTlaFineSpan - kLna0) * ABCMB_BG_PER_UNIT);
+        double *pts = otab; // [2 (kNlna - jc) - 1][kTlaPtDoubles]
+        for (int i = lane; i < 2 * (kNlna - jc) - 1; i += nl) {
+            const TlaPt P = tla_point(c, kLna0 + (jc + 0.5 * i) * kDlna);
+            double *d = pts + kTlaPtDoubles * i;
+            d[0] = P.T; d[1] = P.nH; d[2] = P.H; d[3] = P.K; d[4] = P.be;
+            d[5] = P.bex; d[6] = P.xhe; d[7] = P.g0; d[8] = P.e1; d[9] = P.e2;
         }
+        lane_sync();
+        if (lane == 0) {
+            auto ptat = [&](int i) {
+                const double *d = pts + kTlaPtDoubles * i;
+                TlaPt P;
+                P.T = d[0]; P.nH = d[1]; P.H = d[2]; P.K = d[3]; P.be = d[4];
+                P.bex = d[5]; P.xhe = d[6]; P.g0 = d[7]; P.e1 = d[8]; P.e2 = d[9];
+                return P;
+            };
+            double dum;
+            double x = c.lna_sw;
+            double y0 = xp_saha(c, x, &dum), y1 = 0.0;
+            bool two = false;
+            double dxp = 0.0, dTm = 0.0;
+            for (int j = j0; j < kNlna; j++) {
+                const double target = kLna0 + j * kDlna;
+                if (j > jc && !(two == false && x < kLna700 && target >= kLna700)) {
+                    // one RK4 step over the cell [j - 1, j] from tabulated stage points
+                    const double hs = target - x;
+                    const int i = 2 * (j - 1 - jc);
+                    const TlaPt Pm = ptat(i + 1), Pe = ptat(i + 2);
+                    double k2a, k2b, k3a, k3b, k4a, k4b;
+                    const double k1a = dxp, k1b = dTm;
+                    tla_rhs_pt(c, Pm, y0 + 0.5 * hs * k1a, y1 + 0.5 * hs * k1b, two, &k2a, &k2b);
+                    tla_rhs_pt(c, Pm, y0 + 0.5 * hs * k2a, y1 + 0.5 * hs * k2b, two, &k3a, &k3b);
+                    tla_rhs_pt(c, Pe, y0 + hs * k3a, y1 + hs * k3b, two, &k4a, &k4b);
+                    y0 += hs / 6.0 * (k1a + 2.0 * k2a + 2.0 * k3a + k4a);
+                    y1 += hs / 6.0 * (k1b + 2.0 * k2b + 2.0 * k3b + k4b);
+                    x = target;
+                    tla_rhs_pt(c, Pe, y0, y1, two, &dxp, &dTm);
+                } else {
+                    while (x < target) {
+                        double hs = (x - c.lna_sw < kTlaFineSpan) ? kTlaFine : kDlna;
+                        if (target - x < hs * (1.0 + 1e-9)) hs = target - x;
+                        bool hit700 = false;
+                        if (!two && x < kLna700 && x + hs >= kLna700) { hs = kLna700 - x; hit700 = true; }
+                        double k1a, k1b, k2a, k2b, k3a, k3b, k4a, k4b;
+                        tla_rhs(c, x, y0, y1, two, &k1a, &k1b);
+                        tla_rhs(c, x + 0.5 * hs, y0 + 0.5 * hs * k1a, y1 + 0.5 * hs * k1b, two, &k2a, &k2b);
+                        tla_rhs(c, x + 0.5 * hs, y0 + 0.5 * hs * k2a, y1 + 0.5 * hs * k2b, two, &k3a, &k3b);
+                        tla_rhs(c, x + hs, y0 + hs * k3a, y1 + hs * k3b, two, &k4a, &k4b);
+                        y0 += hs / 6.0 * (k1a + 2.0 * k2a + 2.0 * k3a + k4a);
+                        y1 += hs / 6.0 * (k1b + 2.0 * k2b + 2.0 * k3b + k4b);
+                        if (hit700) {
+                            x = kLna700;
+                            two = true;
+                            const double xe = y0 + x_he(c, x, &dum);
+                            y1 = kTcmb0 * exp(-x) * (1.0 - H_sec(c, x) / gamma_C(c, exp(x), xe));
+                        } else {
+                            x += hs;
+                        }
+                        if (x > target - 1e-14) x = target;
+                    }
+                    if (j >= jc) tla_rhs_pt(c, ptat(2 * (j - jc)), y0, y1, two, &dxp, &dTm);
+                    else tla_rhs(c, target, y0, y1, two, &dxp, &dTm);
+                }
+                double *r = tab + 8 * j;
+                r[C_XE] = y0;     // temporarily x_p
+                r[C_KAPPA] = dxp; // temporarily dx_p/dln a
+                r[C_CS2] = y1;    // temporarily T_m (z < 700)
+                r[C_DCS2] = dTm;  // temporarily dT_m/dln a
+            }
+        }
+        lane_sync();
     }
-    lane_sync();
 
     // table: x_e, 1/(H tau_c), c_s^2, 1/H (lane-parallel)
     {

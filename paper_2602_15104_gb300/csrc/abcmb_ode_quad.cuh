@@ -15,7 +15,8 @@
 //    quad: lane q interpolates ODE-table columns q, q+4 and 8 + (q & 1), then
 //    the values are broadcast inside the quad.
 //  * The accepted state and the extrapolation tableau live in shared memory
-//    ([vector][element][lane], conflict-free), the inverse error scales in
+//    ([vector][element][lane], conflict-free; the scalars take one row, lane
+//    q of a quad holding scalar q), the inverse error scales in
 //    the last tableau column's slot until that column is formed; the
 //    working vectors of a column live in registers.
 //  * The error norm is max_i |T_j,j-1 - T_j,j-2|_i / (atol + rtol max(|y_i|,
@@ -33,9 +34,25 @@
 
 namespace abcmb {
 
-constexpr int kQK = kKmax; // extrapolation columns
+constexpr int kQK = 7; // extrapolation columns (orders up to 7 implicit, 13 explicit)
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kQLmax = 63;  // highest hierarchy truncation (4 lanes x 16 moments)
+
+__device__ __forceinline__ double rcp_approx(double x)
+{
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    return r;
+}
+
+// 1/x for normal positive x: the hardware approximation refined by two
+// Newton-Raphson steps r <- r + r (1 - x r), each doubling the correct bits
+__device__ __forceinline__ double recip(double x)
+{
+    double r = rcp_approx(x);
+    r = fma(r, fma(-x, r, 1.0), r);
+    return fma(r, fma(-x, r, 1.0), r);
+}
 
 // ODE-table columns, (value, d/dln a) pairs -- written by build_background
 enum { O_IH = 0, O_IHT, O_FC, O_FB, O_FG, O_FNU, O_NU, O_RNU, O_CS2, O_HC, O_NCOL };
@@ -54,7 +71,7 @@ struct QHerm {
 __device__ __forceinline__ QHerm qherm(double lna)
 {
     const double t = (lna - kLna0) * ABCMB_BG_PER_UNIT;
-    int j = (int)floor(t);
+    int j = (int)t; // t >= 0 on the table (ln a >= -18): truncation is floor
     j = j < 0 ? 0 : (j > kNlna - 2 ? kNlna - 2 : j);
     const double u = t - (double)j, um = 1.0 - u, um2 = um * um;
     QHerm H;
@@ -118,7 +135,31 @@ __device__ __forceinline__ QBg qbg(const double *ot, double lna, int q, int qb)
 struct QCoef {
     const volatile double *A, *Bc; // [3][64]; volatile: re-read each substep, not held in registers
     int L[3];
+    double L1[3]; // L + 1
 };
+
+// Aitken-Neville factors T_{j,s} = T_{j,s-1} + (T_{j,s-1} - T_{j-1,s-1}) f[j][s] for
+// the harmonic sequence n_j = j extrapolated in h (IMEX Euler: f = (j - s) / s) and
+// the sequence n_j = 2j extrapolated in h^2 (Gragg: f = 1 / ((j / (j - s))^2 - 1)),
+// and 1/n, tabulated so that no column divides.
+struct NevTab {
+    double imex[kQK + 1][kQK], gbs[kQK + 1][kQK], inv[2 * kQK + 1];
+};
+
+constexpr NevTab make_nev()
+{
+    NevTab t{};
+    for (int j = 1; j <= kQK; j++)
+        for (int s = 1; s < j; s++) {
+            t.imex[j][s] = (double)(j - s) / (double)s;
+            const double js = (double)(j - s);
+            t.gbs[j][s] = js * js / ((double)j * j - js * js);
+        }
+    for (int n = 1; n <= 2 * kQK; n++) t.inv[n] = 1.0 / n;
+    return t;
+}
+
+__constant__ NevTab c_nev = make_nev();
 
 // per-mode constants
 struct QMode {
@@ -193,7 +234,7 @@ __device__ __forceinline__ void q_imex(double (&z)[3][P], double (&zs)[4], const
             prev = cur;
         }
         // truncation -(L+1)/(H tau) F_L
-        put_L<P>(z[ch], q, qc.L[ch], fma(-htr * (qc.L[ch] + 1.0), curL, pick_L<P>(z[ch], q, qc.L[ch])));
+        put_L<P>(z[ch], q, qc.L[ch], fma(-htr * qc.L1[ch], curL, pick_L<P>(z[ch], q, qc.L[ch])));
     }
     if (q == 0) {
         const double m0 = hs * (-2.0 / 3.0) * hp, m2 = hs * fma(4.0 / 15.0, hp, 1.6 * ep);
@@ -205,7 +246,7 @@ __device__ __forceinline__ void q_imex(double (&z)[3][P], double (&zs)[4], const
     // implicit Thomson part at x_{m+1}: one division for the three denominators
     const double hnu = hs * bn.nu, hRnu = hs * bn.rnu;
     const double d1 = 1.0 + hnu, d2 = fma(0.3, hnu, 1.0), d3 = d1 + hRnu;
-    const double d12 = d1 * d2, r = 1.0 / (d12 * d3);
+    const double d12 = d1 * d2, r = recip(d12 * d3);
     const double dmp = r * (d2 * d3);
 #pragma unroll
     for (int p = 0; p < P; p++) {
@@ -265,7 +306,7 @@ __device__ __forceinline__ void q_rhs_axpy(const double (&s)[3][P], const double
             prev = cur;
         }
         const double curL = pick_L<P>(s[ch], q, qc.L[ch]);
-        put_L<P>(d[ch], q, qc.L[ch], fma(-ftr * (qc.L[ch] + 1.0), curL, pick_L<P>(d[ch], q, qc.L[ch])));
+        put_L<P>(d[ch], q, qc.L[ch], fma(-ftr * qc.L1[ch], curL, pick_L<P>(d[ch], q, qc.L[ch])));
     }
     if (q == 0) {
         const double fPi = fnu * Pi, m2 = fma(4.0 / 15.0, fhp, 1.6 * fac * ep);
@@ -281,13 +322,13 @@ __device__ __forceinline__ void q_rhs_axpy(const double (&s)[3][P], const double
 
 // Sources at a tau node from the accepted state in shared memory (lane 0).
 __device__ __forceinline__ void q_sources(const double *ot, const double *nd, double k, const double sw[3],
-                                          const double *Y, int P, double *S)
+                                          const double *Y, const double sc[4], int P, double *S)
 {
     const QBg b = obg_all(ot, nd[N_LNA]);
     const double Hc = nd[N_HC], dHc = nd[N_DHC], g = nd[N_G], dg = nd[N_DG], emk = nd[N_EXPMK];
     const double kH = k / Hc, k2 = k * k;
     auto el = [&](int e) { return Y[e * 32]; };
-    const double eta = el(3 * P), dc = el(3 * P + 1), db = el(3 * P + 2), tb = el(3 * P + 3);
+    const double eta = sc[0], dc = sc[1], db = sc[2], tb = sc[3];
     const double Fg0 = el(0), Fg1 = el(1), Fg2 = el(2);
     const double G0 = el(P), G2 = el(P + 2);
     const double Fn0 = el(2 * P), Fn1 = el(2 * P + 1), Fn2 = el(2 * P + 2);
@@ -306,6 +347,19 @@ __device__ __forceinline__ void q_sources(const double *ot, const double *nd, do
     S[2] = g * (Fg2 + G0 + G2) * 0.125;
 }
 
+// scalar q of four (eta, delta_c, delta_b, theta_b): this lane's share of the scalar row
+__device__ __forceinline__ double pick4(const double (&v)[4], int q)
+{
+    return q == 0 ? v[0] : (q == 1 ? v[1] : (q == 2 ? v[2] : v[3]));
+}
+
+// all four scalars from the quad's scalar row (lane qb + s holds scalar s)
+__device__ __forceinline__ void load_scalars(double (&v)[4], double mine, int qb)
+{
+#pragma unroll
+    for (int s = 0; s < 4; s++) v[s] = __shfl_sync(kFull, mine, qb + s);
+}
+
 __device__ __forceinline__ double quad_max(double v)
 {
     const double a = __shfl_xor_sync(kFull, v, 1);
@@ -315,20 +369,13 @@ __device__ __forceinline__ double quad_max(double v)
     return v;
 }
 
-__device__ __forceinline__ double rcp_approx(double x)
-{
-    double r;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-    return r;
-}
-
 // Integrate the modes of one warp (8 per warp, mode index mi for this lane's quad).
 template <int P>
 __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restrict__ bg, long len,
                            const double *__restrict__ kv, const QCoef &qc, double rtol, double atol, int max_steps,
                            const double sw[3], double *S, int *status, int *steps, double *smw)
 {
-    constexpr int E = 3 * P + 4;
+    constexpr int E = 3 * P + 1; // chain moments, then one scalar per quad lane
     const int lane = threadIdx.x & 31, q = lane & 3, qb = lane & ~3;
     const bool valid = mi < M;
     const int kidx = valid ? Nk - 1 - (int)(mi / B) : 0;
@@ -413,8 +460,7 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
         for (int ch = 0; ch < 3; ch++)
 #pragma unroll
             for (int p = 0; p < P; p++) Y(ch * P + p) = z[ch][p];
-#pragma unroll
-        for (int s = 0; s < 4; s++) Y(3 * P + s) = zs[s];
+        Y(3 * P) = pick4(zs, q);
     }
 
     double h = 1e-3;
@@ -448,22 +494,20 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
                 cm2 = fmax(cm2, fmax(fabs(z[0][p]), fabs(z[1][p])));
                 cm3 = fmax(cm3, fabs(z[2][p]));
             }
-#pragma unroll
-            for (int s = 0; s < 4; s++) zs[s] = Y(3 * P + s);
-            const double fl0 = ABCMB_CHAIN_FLOOR * fmax(fabs(zs[0]), fmax(fabs(zs[1]), fabs(zs[2])));
-            const double fl1 = ABCMB_CHAIN_FLOOR * fabs(zs[3]);
-            const double fl2 = ABCMB_CHAIN_FLOOR * quad_max(cm2);
-            const double fl3 = ABCMB_CHAIN_FLOOR * quad_max(cm3);
-#pragma unroll
-            for (int s = 0; s < 4; s++)
-                T(kQK - 1, 3 * P + s) = rcp_approx(fmax(fma(rtol, fmax(fabs(zs[s]), s < 3 ? fl0 : fl1), atol), 1e-300));
+            load_scalars(zs, Y(3 * P), qb);
+            // floors clamped away from zero keep every scale a normal number
+            const double fl0 = fmax(ABCMB_CHAIN_FLOOR * fmax(fabs(zs[0]), fmax(fabs(zs[1]), fabs(zs[2]))), 1e-290);
+            const double fl1 = fmax(ABCMB_CHAIN_FLOOR * fabs(zs[3]), 1e-290);
+            const double fl2 = fmax(ABCMB_CHAIN_FLOOR * quad_max(cm2), 1e-290);
+            const double fl3 = fmax(ABCMB_CHAIN_FLOOR * quad_max(cm3), 1e-290);
+            T(kQK - 1, 3 * P) = rcp_approx(fma(rtol, fmax(fabs(pick4(zs, q)), q < 3 ? fl0 : fl1), atol));
 #pragma unroll
             for (int ch = 0; ch < 3; ch++)
 #pragma unroll
                 for (int p = 0; p < P; p++) {
                     const int l = q * P + p;
                     const bool off = l > qc.L[ch] || (excl && (ch == 1 || (ch == 0 && l >= 2)));
-                    const double sc = fmax(fma(rtol, fmax(fabs(z[ch][p]), ch < 2 ? fl2 : fl3), atol), 1e-300);
+                    const double sc = fma(rtol, fmax(fabs(z[ch][p]), ch < 2 ? fl2 : fl3), atol);
                     T(kQK - 1, ch * P + p) = off ? 0.0 : rcp_approx(sc);
                 }
         }
@@ -478,11 +522,10 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
                 for (int ch = 0; ch < 3; ch++)
 #pragma unroll
                     for (int p = 0; p < P; p++) z[ch][p] = Y(ch * P + p);
-#pragma unroll
-                for (int s = 0; s < 4; s++) zs[s] = Y(3 * P + s);
+                load_scalars(zs, Y(3 * P), qb);
             }
             if (!gbs) {
-                const double hs = H / j;
+                const double hs = H * c_nev.inv[j];
                 QBg bc = qbg(ot, x, q, qb);
                 for (int m = 0; m < j; m++) {
                     const double xm = m == j - 1 ? x + H : x + (m + 1) * hs;
@@ -493,7 +536,7 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
                 if (open) nsub += j;
             } else {
                 const int n = 2 * j;
-                const double hs = H / n;
+                const double hs = H * c_nev.inv[n];
 #pragma unroll
                 for (int ch = 0; ch < 3; ch++)
 #pragma unroll
@@ -512,25 +555,15 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
                 if (open) nsub += n;
             }
             // Aitken-Neville update of the tableau and the error estimate
-            double cf[kQK];
-#pragma unroll
-            for (int s = 1; s < kQK; s++) {
-                cf[s] = 0.0;
-                if (s < j) {
-                    if (gbs) {
-                        const double r = (double)j / (double)(j - s);
-                        cf[s] = 1.0 / (r * r - 1.0);
-                    } else {
-                        cf[s] = (double)(j - s) / (double)s;
-                    }
-                }
-            }
-            double el = 0.0;
+            const double *cf = gbs ? c_nev.gbs[j] : c_nev.imex[j];
+            // max of the scaled errors on the high words of their bit patterns:
+            // integer work, monotone for non-negative doubles, NaN on top, exact to 2^-20
+            int elh = 0;
 #pragma unroll
             for (int e = 0; e < E; e++) {
                 const int ch = e < 3 * P ? e / P : 3;
                 const int p = e - ch * P;
-                double cur = ch < 3 ? z[ch][p] : zs[p];
+                double cur = ch < 3 ? z[ch][p] : pick4(zs, q);
                 const double is = T(kQK - 1, e);
                 double lower = cur;
                 double prev = T(0, e);
@@ -547,10 +580,12 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
                 }
                 if (j >= 2) {
                     const double er = fabs(cur - lower) * is;
-                    if (!(er <= el)) el = er; // NaN propagates
+                    elh = max(elh, __double2hiint(fabs(er)));
                 }
             }
-            el = quad_max(el);
+            elh = max(elh, __shfl_xor_sync(kFull, elh, 1));
+            elh = max(elh, __shfl_xor_sync(kFull, elh, 2));
+            const double el = __hiloint2double(elh, 0);
             if (open && j >= 2) {
                 err = el;
                 if (!(el == el)) {
@@ -574,7 +609,7 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
         if (stepping && jacc > 0) {
             x = land ? xn : x + H;
             const int ord = gbs ? 2 * jacc - 1 : jacc;
-            double fac = err > 0.0 ? 0.9 * exp(-log(err) / ord) : 4.0;
+            double fac = err > 0.0 ? 0.9 * (double)__powf((float)err, -1.0f / ord) : 4.0;
             if (jacc < kQK - 1) fac *= 1.5;
             fac = fmin(4.0, fmax(0.2, fac));
             const double hn = H * fac;
@@ -582,12 +617,16 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
             if (land) emit = true;
         } else if (stepping && jacc == 0) {
             const int ord = gbs ? 2 * kQK - 1 : kQK;
-            h = H * fmin(0.9, fmax(0.1, 0.9 * exp(-log(err) / ord)));
+            h = H * fmin(0.9, fmax(0.1, 0.9 * (double)__powf((float)err, -1.0f / ord)));
         }
-        if (emit) {
-            if (q == 0) q_sources(ot, nodes + 8 * node, k, sw, sl, P, Sm + 3 * node);
-            node++;
-            if (node >= n_tau) done = true;
+        if (__any_sync(kFull, emit)) {
+            double sc[4];
+            load_scalars(sc, Y(3 * P), qb); // the accepted scalars, one per quad lane
+            if (emit) {
+                if (q == 0) q_sources(ot, nodes + 8 * node, k, sw, sl, sc, P, Sm + 3 * node);
+                node++;
+                if (node >= n_tau) done = true;
+            }
         }
     }
     if (valid && q == 0) {
@@ -605,7 +644,7 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
 template <int P>
 constexpr size_t quad_smem_per_warp()
 {
-    return (size_t)(1 + kQK) * (3 * P + 4) * 32 * sizeof(double);
+    return (size_t)(1 + kQK) * (3 * P + 1) * 32 * sizeof(double);
 }
 
 template <int P, int W>
@@ -623,7 +662,7 @@ perturb_quad_kernel(int B, int Nk, const double *__restrict__ bg, long len, cons
         cB[i] = l < L ? (l + 1.0) / (2.0 * l + 1.0) : 0.0;
     }
     __syncthreads();
-    constexpr int E = 3 * P + 4;
+    constexpr int E = 3 * P + 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long M = (long)B * Nk;
     const long mi = ((long)blockIdx.x * W + warp) * 8 + (lane >> 2);
@@ -633,6 +672,7 @@ perturb_quad_kernel(int B, int Nk, const double *__restrict__ bg, long len, cons
     qc.L[0] = Lg;
     qc.L[1] = Lp;
     qc.L[2] = Ln;
+    for (int c = 0; c < 3; c++) qc.L1[c] = qc.L[c] + 1.0;
     const double sw[3] = {s_sw, s_isw, s_dop};
     double *smw = qsm + (long)warp * (1 + kQK) * E * 32;
     quad_modes<P>(mi, M, B, Nk, bg, len, kv, qc, rtol, atol, max_steps, sw, S, status, steps, smw);

@@ -1,0 +1,329 @@
+// Continuous-batching spectrum server (host runtime over the C ABI calls).
+//
+// Requests (one cosmology, its lmax_cl and k-grid size) queue on the host;
+// progress() admits them in arrival order while a stream slot is free and
+// the caller's device arena has room for the request's buffers (first fit
+// over a sorted free list), enqueues the whole path on that slot's stream
+// (params and k H2D, background tables, FP64 perturbations, FP32 projection
+// and k-quadrature, C_l D2H into the slot's pinned buffer, completion event),
+// and retires finished slots (event query, never a blocking wait), releasing
+// their arena blocks.  Requests in flight on different streams overlap on the
+// GPU: each one's perturbation grid is small (n_k / 8 one-warp CTAs), so a
+// mix of them is what fills the SMs.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <new>
+#include <vector>
+
+#include "abcmb.h"
+
+namespace {
+
+struct Block {
+    size_t off, len;
+};
+
+// first-fit allocator over [0, size) with 256-byte granules
+class Arena {
+  public:
+    void init(size_t size)
+    {
+        size_ = size & ~(size_t)255;
+        free_.assign(1, Block{0, size_});
+    }
+    bool alloc(size_t len, size_t *off)
+    {
+        len = (len + 255) & ~(size_t)255;
+        for (size_t i = 0; i < free_.size(); i++) {
+            if (free_[i].len >= len) {
+                *off = free_[i].off;
+                free_[i].off += len;
+                free_[i].len -= len;
+                if (free_[i].len == 0) free_.erase(free_.begin() + i);
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t len)
+    {
+        len = (len + 255) & ~(size_t)255;
+        auto it = std::lower_bound(free_.begin(), free_.end(), off,
+                                   [](const Block &b, size_t o) { return b.off < o; });
+        it = free_.insert(it, Block{off, len});
+        // coalesce with neighbours
+        if (it + 1 != free_.end() && it->off + it->len == (it + 1)->off) {
+            it->len += (it + 1)->len;
+            free_.erase(it + 1);
+        }
+        if (it != free_.begin() && (it - 1)->off + (it - 1)->len == it->off) {
+            (it - 1)->len += it->len;
+            free_.erase(it);
+        }
+    }
+    size_t largest() const
+    {
+        size_t m = 0;
+        for (const Block &b : free_) m = std::max(m, b.len);
+        return m;
+    }
+    size_t size() const { return size_; }
+
+  private:
+    size_t size_ = 0;
+    std::vector<Block> free_;
+};
+
+struct Request {
+    long long tag;
+    double params[ABCMB_NPARAM];
+    int lmax_cl, n_k;
+    double k_min, k_max;
+    double t_submit;
+};
+
+struct Slot {
+    bool busy = false;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    Request req;
+    size_t off = 0, bytes = 0;
+    double *host = nullptr;    // pinned: params, k, then C_l on return
+    int *host_status = nullptr; // pinned: mode status words
+    size_t host_doubles = 0;
+    int launch_rc = ABCMB_OK;
+};
+
+struct Result {
+    long long tag;
+    int status, lmax_cl, n_k;
+    std::vector<double> cl;
+};
+
+// sizes of one request's device buffers, in bytes, in allocation order
+struct Layout {
+    size_t bg, k, params, S, status, D, Cl, total;
+};
+
+Layout layout_of(const abcmb_options *o, int n_k)
+{
+    Layout L;
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    L.bg = up(abcmb_bg_doubles(o) * sizeof(double));
+    L.k = up((size_t)n_k * sizeof(double));
+    L.params = up(ABCMB_NPARAM * sizeof(double));
+    L.S = up((size_t)n_k * o->n_tau * 3 * sizeof(double));
+    L.status = up((size_t)n_k * sizeof(int));
+    L.D = up((size_t)n_k * (o->lmax_cl - 1) * 2 * sizeof(float));
+    L.Cl = up((size_t)3 * (o->lmax_cl - 1) * sizeof(double));
+    L.total = L.bg + L.k + L.params + L.S + L.status + L.D + L.Cl;
+    return L;
+}
+
+} // namespace
+
+struct abcmb_server {
+    abcmb_options base;
+    char *arena_base = nullptr;
+    Arena arena;
+    std::vector<Slot> slots;
+    std::deque<Request> queue;
+    std::deque<Result> results;
+    int max_lmax = 0, max_nk = 0;
+};
+
+extern "C" size_t abcmb_server_request_bytes(const abcmb_options *o, int lmax_cl, int n_k)
+{
+    if (!o || lmax_cl < 2 || n_k < 2) return 0;
+    abcmb_options r = *o;
+    r.lmax_cl = lmax_cl;
+    if (abcmb_validate_options(&r) != ABCMB_OK) return 0;
+    return layout_of(&r, n_k).total;
+}
+
+extern "C" int abcmb_server_create(void *arena, size_t arena_bytes, int n_slots, int max_lmax_cl, int max_n_k,
+                                   const abcmb_options *o, abcmb_server **out)
+{
+    if (!out || !arena || ((size_t)arena & 255) != 0 || n_slots < 1 || n_slots > 256 || max_n_k < 2 ||
+        abcmb_validate_options(o) != ABCMB_OK)
+        return ABCMB_E_INVALID_ARG;
+    abcmb_options r = *o;
+    r.lmax_cl = max_lmax_cl;
+    if (abcmb_validate_options(&r) != ABCMB_OK) return ABCMB_E_INVALID_ARG;
+    // requests run the on-chip perturbation path, which needs no workspace
+    if (abcmb_perturb_workspace_bytes(1, 2, o) != 0) return ABCMB_E_INVALID_ARG;
+    *out = nullptr;
+    abcmb_server *s = new (std::nothrow) abcmb_server;
+    if (!s) return ABCMB_E_INVALID_ARG;
+    s->base = *o;
+    s->arena_base = (char *)arena;
+    s->arena.init(arena_bytes);
+    s->max_lmax = max_lmax_cl;
+    s->max_nk = max_n_k;
+    s->slots.resize(n_slots);
+    // params + k on the way in, C_l on the way out, and the background status word last
+    const size_t host_doubles = std::max((size_t)ABCMB_NPARAM + max_n_k, (size_t)3 * (max_lmax_cl - 1)) + 1;
+    for (Slot &sl : s->slots) {
+        sl.host_doubles = host_doubles;
+        if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaMallocHost((void **)&sl.host, host_doubles * sizeof(double)) != cudaSuccess ||
+            cudaMallocHost((void **)&sl.host_status, (size_t)max_n_k * sizeof(int)) != cudaSuccess) {
+            abcmb_server_destroy(s);
+            return ABCMB_E_CUDA;
+        }
+    }
+    *out = s;
+    return ABCMB_OK;
+}
+
+extern "C" int abcmb_server_destroy(abcmb_server *s)
+{
+    if (!s) return ABCMB_E_INVALID_ARG;
+    for (Slot &sl : s->slots) {
+        if (sl.stream) cudaStreamSynchronize(sl.stream);
+        if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.stream) cudaStreamDestroy(sl.stream);
+        if (sl.host) cudaFreeHost(sl.host);
+        if (sl.host_status) cudaFreeHost(sl.host_status);
+    }
+    delete s;
+    return ABCMB_OK;
+}
+
+extern "C" int abcmb_server_submit(abcmb_server *s, long long tag, const double *params_host, int lmax_cl, int n_k,
+                                   double k_min, double k_max)
+{
+    if (!s || !params_host || lmax_cl < 2 || lmax_cl > s->max_lmax || n_k < 2 || n_k > s->max_nk ||
+        !(k_min > 0.0) || !(k_max > k_min))
+        return ABCMB_E_INVALID_ARG;
+    abcmb_options r = s->base;
+    r.lmax_cl = lmax_cl;
+    if (layout_of(&r, n_k).total > s->arena.size()) return ABCMB_E_SCRATCH_TOO_SMALL;
+    Request q;
+    q.tag = tag;
+    memcpy(q.params, params_host, sizeof(q.params));
+    q.lmax_cl = lmax_cl;
+    q.n_k = n_k;
+    q.k_min = k_min;
+    q.k_max = k_max;
+    q.t_submit = 0.0;
+    s->queue.push_back(q);
+    return ABCMB_OK;
+}
+
+static int launch(abcmb_server *s, Slot &sl)
+{
+    const Request &q = sl.req;
+    abcmb_options o = s->base;
+    o.lmax_cl = q.lmax_cl;
+    const Layout L = layout_of(&o, q.n_k);
+    char *p = s->arena_base + sl.off;
+    double *bg = (double *)p;
+    double *k = (double *)(p + L.bg);
+    double *params = (double *)(p + L.bg + L.k);
+    double *S = (double *)(p + L.bg + L.k + L.params);
+    int *st = (int *)(p + L.bg + L.k + L.params + L.S);
+    float *D = (float *)(p + L.bg + L.k + L.params + L.S + L.status);
+    double *Cl = (double *)(p + L.bg + L.k + L.params + L.S + L.status + L.D);
+    // host staging: params, then log-spaced k (the workload's grid rule)
+    double *h = sl.host;
+    memcpy(h, q.params, sizeof(q.params));
+    const double l0 = std::log(q.k_min), l1 = std::log(q.k_max);
+    for (int i = 0; i < q.n_k; i++) h[ABCMB_NPARAM + i] = std::exp(l0 + (l1 - l0) * i / (q.n_k - 1));
+    cudaStream_t st_ = sl.stream;
+    if (cudaMemcpyAsync(params, h, ABCMB_NPARAM * sizeof(double), cudaMemcpyHostToDevice, st_) != cudaSuccess ||
+        cudaMemcpyAsync(k, h + ABCMB_NPARAM, q.n_k * sizeof(double), cudaMemcpyHostToDevice, st_) != cudaSuccess)
+        return ABCMB_E_CUDA;
+    int rc = abcmb_background_tables(1, params, &o, bg, st_);
+    if (rc == ABCMB_OK) rc = abcmb_perturb(1, bg, k, q.n_k, &o, S, st, nullptr, nullptr, 0, st_);
+    if (rc == ABCMB_OK) rc = abcmb_project_mixed(1, bg, S, k, q.n_k, &o, D, st_);
+    if (rc == ABCMB_OK) rc = abcmb_cl_mixed(1, bg, D, k, q.n_k, &o, Cl, st_);
+    if (rc != ABCMB_OK) return rc;
+    // the host staging buffer is reused for C_l only after the H2D copies ran (stream order)
+    if (cudaMemcpyAsync(h, Cl, 3 * (size_t)(q.lmax_cl - 1) * sizeof(double), cudaMemcpyDeviceToHost, st_) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(sl.host_status, st, q.n_k * sizeof(int), cudaMemcpyDeviceToHost, st_) != cudaSuccess ||
+        cudaMemcpyAsync(h + sl.host_doubles - 1, bg + ABCMB_S_STATUS, sizeof(double), cudaMemcpyDeviceToHost,
+                        st_) != cudaSuccess ||
+        cudaEventRecord(sl.done, st_) != cudaSuccess)
+        return ABCMB_E_CUDA;
+    return ABCMB_OK;
+}
+
+// Admit, launch and retire without blocking; returns the number of requests
+// in flight afterwards (>= 0) or a negative error code.
+extern "C" int abcmb_server_progress(abcmb_server *s)
+{
+    if (!s) return -ABCMB_E_INVALID_ARG;
+    // retire
+    for (Slot &sl : s->slots) {
+        if (!sl.busy) continue;
+        const cudaError_t e = cudaEventQuery(sl.done);
+        if (e == cudaErrorNotReady) continue;
+        Result r;
+        r.tag = sl.req.tag;
+        r.lmax_cl = sl.req.lmax_cl;
+        r.n_k = sl.req.n_k;
+        r.status = ABCMB_OK;
+        if (e != cudaSuccess || sl.launch_rc != ABCMB_OK) {
+            r.status = sl.launch_rc != ABCMB_OK ? sl.launch_rc : ABCMB_E_CUDA;
+        } else {
+            if (sl.host[sl.host_doubles - 1] != 0.0) r.status = ABCMB_E_BACKGROUND;
+            for (int i = 0; i < sl.req.n_k; i++)
+                if (sl.host_status[i] != ABCMB_OK) r.status = sl.host_status[i];
+            r.cl.assign(sl.host, sl.host + 3 * (size_t)(sl.req.lmax_cl - 1));
+        }
+        s->results.push_back(std::move(r));
+        s->arena.release(sl.off, sl.bytes);
+        sl.busy = false;
+    }
+    // admit in arrival order
+    while (!s->queue.empty()) {
+        Slot *free_slot = nullptr;
+        for (Slot &sl : s->slots)
+            if (!sl.busy) { free_slot = &sl; break; }
+        if (!free_slot) break;
+        const Request &q = s->queue.front();
+        abcmb_options o = s->base;
+        o.lmax_cl = q.lmax_cl;
+        const size_t bytes = layout_of(&o, q.n_k).total;
+        size_t off = 0;
+        if (!s->arena.alloc(bytes, &off)) break; // wait for memory: keeps arrival order
+        free_slot->req = q;
+        free_slot->off = off;
+        free_slot->bytes = bytes;
+        free_slot->busy = true;
+        s->queue.pop_front();
+        free_slot->launch_rc = launch(s, *free_slot);
+        if (free_slot->launch_rc != ABCMB_OK) cudaEventRecord(free_slot->done, free_slot->stream);
+    }
+    int n = 0;
+    for (const Slot &sl : s->slots) n += sl.busy;
+    return n;
+}
+
+extern "C" int abcmb_server_queued(const abcmb_server *s) { return s ? (int)s->queue.size() : -1; }
+
+// Pop one finished request: 1 and its tag, status and C_l [3][lmax_cl - 1]
+// (TT, TE, EE) into cl_host (room for cl_capacity doubles), or 0 if none is
+// ready.  A result that does not fit stays queued and ABCMB_E_INVALID_ARG is
+// returned negated.
+extern "C" int abcmb_server_poll(abcmb_server *s, long long *tag, int *status, int *lmax_cl, double *cl_host,
+                                 size_t cl_capacity)
+{
+    if (!s || !tag || !status || !lmax_cl || !cl_host) return -ABCMB_E_INVALID_ARG;
+    if (s->results.empty()) return 0;
+    Result &r = s->results.front();
+    if (r.cl.size() > cl_capacity) return -ABCMB_E_INVALID_ARG;
+    *tag = r.tag;
+    *status = r.status;
+    *lmax_cl = r.lmax_cl;
+    if (!r.cl.empty()) memcpy(cl_host, r.cl.data(), r.cl.size() * sizeof(double));
+    s->results.pop_front();
+    return 1;
+}

@@ -16,6 +16,7 @@
 
 #include <mutex>
 
+#include "abcmb_launch.cuh"
 #include "abcmb_ode_quad.cuh"
 
 namespace abcmb {
@@ -84,8 +85,9 @@ static int launch_quad(int B, const double *bg, const double *k, int Nk, const a
     constexpr int W = 1; // one warp (8 modes) per CTA: fine-grained scheduling of uneven modes
     const size_t smem = W * quad_smem_per_warp<P>();
     auto kern = perturb_quad_kernel<P, W>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return ABCMB_E_CUDA;
+    const long avail = smem_optin((const void *)kern);
+    if (avail < 0) return ABCMB_E_CUDA;
+    if ((long)smem > avail) return ABCMB_E_INVALID_ARG;
     const long M = (long)B * Nk;
     const long blocks = (M + 8 * W - 1) / (8 * W);
     if (blocks > 2147483647L) return ABCMB_E_INVALID_ARG;
@@ -130,7 +132,7 @@ extern "C" void abcmb_default_options(abcmb_options *o)
     o->lmax_cl = 2500;
     o->n_tau = 6000;
     o->max_steps = 2000000;
-    o->rtol = 1e-8;
+    o->rtol = 1e-6;
     o->atol = 1e-12;
     o->scale_sw = o->scale_isw = o->scale_dop = o->scale_pol = 1.0;
 }

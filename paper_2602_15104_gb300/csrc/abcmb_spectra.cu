@@ -24,6 +24,8 @@
 #include <math.h>
 
 #include "abcmb_bg.cuh"
+#include "abcmb_bessel.cuh"
+#include "abcmb_launch.cuh"
 
 namespace abcmb {
 
@@ -57,29 +59,6 @@ __device__ __forceinline__ void j01(double x, double *j0, double *j1)
         *j0 = s * u;
         *j1 = (s * u - c) * u;
     }
-}
-
-// Last l at which j_l(x) is kept: the smallest l > x whose Debye decay
-// exponent nu (alpha - tanh alpha), nu = l + 1/2, cosh alpha = nu / x, exceeds
-// 16 (j_l below ~e^-16 of its turning-point size).  A higher threshold keeps
-// more of the tail but lets the recurrence's growing error in; 16 balances
-// the two at ~1e-7 of the largest Delta_l (measured over k in [1e-5, 0.5]).  Newton on the exponent,
-// whose derivative in nu is alpha; an estimate, so single precision.
-__device__ __forceinline__ int bessel_cut(float x, int lmax)
-{
-    if (x > (float)lmax + 200.0f) return lmax;
-    // the T2 and E kernels carry j_l / x^2, so at x < 1 the threshold moves
-    // down by x^2
-    const float T = 16.0f + 2.0f * fmaxf(0.0f, -logf(x));
-    float nu = x + 1.0f + 0.8f * cbrtf(fmaxf(x, 1.0f)) * 9.0f;
-    for (int it = 0; it < 8; it++) {
-        float r = fmaxf(nu / fmaxf(x, 1e-30f), 1.0f + 1e-6f);
-        float al = acoshf(r);
-        float f = nu * (al - tanhf(al)) - T;
-        nu = fmaxf(nu - f / fmaxf(al, 1e-3f), x + 0.5f);
-    }
-    int l = (int)ceilf(nu - 0.5f);
-    return l < 2 ? 2 : (l > lmax ? lmax : l);
 }
 
 // One butterfly stage: lanes with bit O set keep the upper half of v[0, 2O)
@@ -295,9 +274,9 @@ extern "C" int abcmb_project(int B, const double *bg, const double *S, const dou
     const size_t smem = (size_t)nl * 2 * sizeof(double);
     if (smem > 200 * 1024) return ABCMB_E_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    if (cudaFuncSetAttribute(abcmb::project_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-        return ABCMB_E_CUDA;
+    const long avail = abcmb::smem_optin((const void *)abcmb::project_kernel);
+    if (avail < 0) return ABCMB_E_CUDA;
+    if ((long)smem > avail) return ABCMB_E_INVALID_ARG;
     long nblk = (long)B * Nk;
     if (nblk > 2147483647L) return ABCMB_E_INVALID_ARG;
     abcmb::project_kernel<<<(unsigned)nblk, 128, smem, st>>>(B, Nk, bg, len, S, k, o->lmax_cl,

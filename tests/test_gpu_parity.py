@@ -199,6 +199,23 @@ def test_full_size_sampled_modes(A):
             assert np.max(np.abs(D[:, c] - ref["Delta"][0, :, c])) < 1e-5 * scale, (b, i, c)
 
 
+def test_default_tolerance_moves_cl_by_far_less_than_the_target(A):
+    # the library's default rtol against a 1e-10 solution of the same
+    # discretisation, at the full l <= 2500, 400 k, hierarchy 30, 6000-node size
+    wl = W.BATCH64
+    params, k = wl.params()[[7, 50]], wl.k()
+    C = {}
+    for rt in (None, 1e-10):
+        kw = {} if rt is None else {"rtol": rt}
+        o = A.options(lmax_hier=wl.l_max_hier, lmax_cl=wl.l_max_cl, n_tau=wl.n_tau, **kw)
+        pipe = A.Pipeline(len(params), k, o)
+        C[rt] = pipe.run(torch.tensor(params, device="cuda")).cpu().numpy()
+        pipe.check_status()
+    for b in range(len(params)):
+        tt, te, ee = cl_errors(C[None][b], C[1e-10][b])
+        assert max(tt, te, ee) < 2e-6, (b, tt, te, ee)
+
+
 def test_highest_k_self_convergence(A):
     # k = 0.5 is beyond what the oracle's dense solver affords at hierarchy 30;
     # the adaptive solver's sources must be converged well below the target
