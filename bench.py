@@ -251,6 +251,63 @@ def run_serving(args, A, torch):
     print(json.dumps(out), flush=True)
 
 
+def run_gradient(args, A, torch):
+    """Gradient benchmark: Cbar . dC_l/dtheta for the six parameters of each
+    cosmology of a batch (hand-written adjoint through ClWithGradient): one
+    step = taped forward (background, ODE, projection, quadrature) + backward
+    (quadrature, projection and ODE adjoints, the background record's
+    parameter Jacobian by central differences, the contraction)."""
+    wl = W.BATCH16_GRAD
+    B = args.batch or wl.n_cosmo
+    params = W.draw_cosmologies(B, wl.seed)
+    k_np = W.log_k_nodes(args.n_k, wl.k_min, wl.k_max) if args.n_k else wl.k()
+    o = A.options(lmax_hier=wl.l_max_hier, lmax_cl=wl.l_max_cl, n_tau=wl.n_tau, rtol=args.rtol)
+    k = torch.tensor(k_np, device="cuda")
+    rng = np.random.default_rng(3)
+    Cbar = torch.tensor(rng.normal(size=(B, 3, o.lmax_cl - 1)), device="cuda")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step(p_dev):
+        p = p_dev.detach().requires_grad_(True)
+        C = A.cl_with_gradient(p, k, o)
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        (C * Cbar).sum().backward()
+        return p.grad, e
+
+    p_dev = torch.tensor(params, device="cuda")
+    for _ in range(args.warmup):
+        step(p_dev)
+    torch.cuda.synchronize()
+    clocks = ClockSampler()
+    clocks.start()
+    ms, fwd_ms = [], []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g, emid = step(p_dev)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        fwd_ms.append(e0.elapsed_time(emid))
+    clk = clocks.stop()
+    assert bool(torch.isfinite(g).all())
+    t = statistics.mean(ms)
+    out = {"metric": "dC_l/dtheta (6 parameters) per second, hand-written adjoint", "value": B / (t * 1e-3),
+           "unit": "gradients/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t,
+           "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": wl.name, "batch": B, "n_k": len(k_np), "k_range": [wl.k_min, wl.k_max],
+                      "lmax_cl": wl.l_max_cl, "hierarchy_lmax": wl.l_max_hier, "n_tau": wl.n_tau,
+                      "rtol": args.rtol, "checkpoint_every": 64,
+                      "l2": "flushed (512 MiB write) between timed steps"},
+           "forward_ms": statistics.mean(fwd_ms), "backward_ms": t - statistics.mean(fwd_ms),
+           "workspace_gb": A.grad_workspace_bytes(B, len(k_np), o) / 2**30,
+           "gpu_launches": 10 * args.steps, "clocks": clk}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -268,6 +325,8 @@ def main():
                     help="mixed: FP64 ODE, FP32 projection and k-quadrature with Kahan sums")
     ap.add_argument("--serve", action="store_true",
                     help="serving benchmark: Poisson arrivals of mixed-size requests through abcmb_server")
+    ap.add_argument("--grad", action="store_true",
+                    help="gradient benchmark: dC_l/dtheta of a batch through the hand-written adjoint")
     ap.add_argument("--requests", type=int, default=4096)
     ap.add_argument("--rate", type=float, default=200.0, help="mean arrivals per second")
     ap.add_argument("--slots", type=int, default=32)
@@ -292,6 +351,10 @@ def main():
     if args.serve:
         if rank == 0:
             run_serving(args, A, torch)
+        return
+    if args.grad:
+        if rank == 0:
+            run_gradient(args, A, torch)
         return
     dist = None
     if world > 1:

@@ -239,6 +239,89 @@ int abcmb_cl_mixed(int B, const double *bg, const float *Delta32, const double *
                    const abcmb_options *o, double *Cl, void *stream);
 
 /*
+ * Gradients of C_l with respect to the six parameters (sec. "Gradients of
+ * ABCMB outputs", and the gradient timings of sec. 5).  The paper takes them
+ * by automatic differentiation; here the perturbation ODE, the projection and
+ * the k-quadrature have hand-written discrete adjoints (reverse mode, one
+ * contraction Cbar . dC/dtheta per call chain), and the background record's
+ * parameter Jacobian is taken by central differences of
+ * abcmb_background_tables (relative step 1e-4), contracted on the device.
+ * Call order for one vector-Jacobian product:
+ *
+ *   abcmb_perturb_taped   -> S (as abcmb_perturb) and the tape in workspace
+ *   abcmb_project, abcmb_cl  (forward, unchanged)
+ *   abcmb_cl_adjoint      Clbar   -> Deltabar, recbar += d/d(A_s, n_s)
+ *   abcmb_project_adjoint Deltabar -> Sbar, recbar += d/d(node tau, w), d/d tau_0
+ *   abcmb_perturb_adjoint Sbar    -> recbar += d/d(ODE table, conformal-time
+ *                                    table, node data, R_nu)
+ *   abcmb_record_vjp      recbar, records at theta +- h e_j -> grad
+ *
+ * recbar [B][abcmb_bg_doubles(o)] device, float64, zeroed by the caller
+ * before the first adjoint call; the adjoint calls add into it (atomically).
+ * Each mode may take up to 65536 accepted steps; more sets its status to
+ * ABCMB_E_MAX_STEPS.  Errors as abcmb_perturb: ABCMB_E_INVALID_ARG for bad
+ * sizes, pointers or options (nothing launched), ABCMB_E_CUDA for a failed
+ * launch; per-mode status in mode_status.
+ */
+
+/* Bytes of device workspace abcmb_perturb_taped and abcmb_perturb_adjoint
+   need for B cosmologies x Nk modes (tape, checkpoints every 64 accepted
+   steps, replay segment, work vectors); 0 for invalid arguments. */
+size_t abcmb_grad_workspace_bytes(int B, int Nk, const abcmb_options *o);
+
+/*
+ * Forward ODE of abcmb_perturb (one thread per mode), recording each mode's
+ * accepted steps.
+ *   bg, k, S, mode_status   as abcmb_perturb
+ *   workspace  device, >= abcmb_grad_workspace_bytes(B, Nk, o) bytes,
+ *              256-byte aligned, owned by the caller; written here, read by
+ *              abcmb_perturb_adjoint (keep it unchanged in between)
+ */
+int abcmb_perturb_taped(int B, const double *bg, const double *k, int Nk, const abcmb_options *o, double *S,
+                        int *mode_status, void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * Reverse sweep of the ODE: replays each mode's steps from its checkpoints
+ * and pulls Sbar [B][Nk][n_tau][3] (device, read) back to recbar.  Modes
+ * whose forward status was not ABCMB_OK contribute nothing.
+ */
+int abcmb_perturb_adjoint(int B, const double *bg, const double *k, int Nk, const abcmb_options *o,
+                          const double *Sbar, void *workspace, size_t workspace_bytes, double *recbar,
+                          void *stream);
+
+/*
+ * Adjoint of abcmb_cl.
+ *   Delta    [B][Nk][lmax_cl-1][2]  device, read (the forward's)
+ *   Clbar    [B][3][lmax_cl-1]      device, read
+ *   Deltabar [B][Nk][lmax_cl-1][2]  device, written
+ *   recbar   device, entries ABCMB_S_AS and ABCMB_S_NS added to
+ */
+int abcmb_cl_adjoint(int B, const double *bg, const double *Delta, const double *k, int Nk,
+                     const abcmb_options *o, const double *Clbar, double *Deltabar, double *recbar, void *stream);
+
+/*
+ * Adjoint of abcmb_project.
+ *   S        [B][Nk][n_tau][3]      device, read (the forward's)
+ *   Deltabar [B][Nk][lmax_cl-1][2]  device, read
+ *   Sbar     [B][Nk][n_tau][3]      device, written
+ *   recbar   device, node tau and weight entries and ABCMB_S_TAU0 added to
+ */
+int abcmb_project_adjoint(int B, const double *bg, const double *S, const double *k, int Nk,
+                          const abcmb_options *o, const double *Deltabar, double *Sbar, double *recbar,
+                          void *stream);
+
+/*
+ * grad[b][j] = sum_e recbar[b][e] (rec_plus[b][j][e] - rec_minus[b][j][e]) / (2 h[b][j])
+ *   recbar            [B][len]                 device, read
+ *   rec_plus/minus    [B][ABCMB_NPARAM][len]   device, read: background
+ *                     records at params[b] +- h[b][j] e_j
+ *   h                 [B][ABCMB_NPARAM]        device, read, nonzero
+ *   grad              [B][ABCMB_NPARAM]        device, written
+ */
+int abcmb_record_vjp(int B, const abcmb_options *o, const double *recbar, const double *rec_plus,
+                     const double *rec_minus, const double *h, double *grad, void *stream);
+
+/*
  * Continuous-batching spectrum server.  A host runtime over the calls above
  * (no counterpart in the paper, which evaluates one cosmology per call):
  * requests of different lmax_cl and k-grid size queue on the host and are

@@ -85,6 +85,14 @@ def lib():
         L.abcmb_cl.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, O, _P, _P]
         L.abcmb_project_mixed.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, O, _P, _P]
         L.abcmb_cl_mixed.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, O, _P, _P]
+        L.abcmb_grad_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_int, O]
+        L.abcmb_grad_workspace_bytes.restype = ctypes.c_size_t
+        L.abcmb_perturb_taped.argtypes = [ctypes.c_int, _P, _P, ctypes.c_int, O, _P, _P, _P, ctypes.c_size_t, _P]
+        L.abcmb_perturb_adjoint.argtypes = [ctypes.c_int, _P, _P, ctypes.c_int, O, _P, _P, ctypes.c_size_t, _P,
+                                            _P]
+        L.abcmb_cl_adjoint.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, O, _P, _P, _P, _P]
+        L.abcmb_project_adjoint.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, O, _P, _P, _P, _P]
+        L.abcmb_record_vjp.argtypes = [ctypes.c_int, O, _P, _P, _P, _P, _P, _P]
         L.abcmb_server_request_bytes.argtypes = [O, ctypes.c_int, ctypes.c_int]
         L.abcmb_server_request_bytes.restype = ctypes.c_size_t
         L.abcmb_server_create.argtypes = [_P, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_int, O,
@@ -221,6 +229,121 @@ def abcmb_cl_mixed(bg: torch.Tensor, Delta32: torch.Tensor, k: torch.Tensor, o: 
     _check(lib().abcmb_cl_mixed(B, _ptr(bg), _ptr(Delta32), _ptr(k), Nk, ctypes.byref(o), _ptr(C), _stream()),
            "abcmb_cl_mixed")
     return C
+
+
+def grad_workspace_bytes(B: int, Nk: int, o: Options) -> int:
+    n = lib().abcmb_grad_workspace_bytes(B, Nk, ctypes.byref(o))
+    if n == 0:
+        raise ValueError("invalid arguments")
+    return n
+
+
+def abcmb_perturb_taped(bg: torch.Tensor, k: torch.Tensor, o: Options, workspace: torch.Tensor, S=None,
+                        status=None):
+    """Forward ODE recording the tape for abcmb_perturb_adjoint in workspace
+    (a CUDA tensor of >= grad_workspace_bytes bytes).  -> S, mode status."""
+    _dev(bg), _dev(k)
+    B, Nk = bg.shape[0], k.shape[0]
+    dev = bg.device
+    if S is None:
+        S = torch.empty((B, Nk, o.n_tau, 3), dtype=torch.float64, device=dev)
+    if status is None:
+        status = torch.empty((B, Nk), dtype=torch.int32, device=dev)
+    _check(lib().abcmb_perturb_taped(B, _ptr(bg), _ptr(k), Nk, ctypes.byref(o), _ptr(S), _ptr(status),
+                                     _ptr(workspace), workspace.numel() * workspace.element_size(), _stream()),
+           "abcmb_perturb_taped")
+    return S, status
+
+
+def abcmb_perturb_adjoint(bg, k, o: Options, Sbar, workspace, recbar):
+    _dev(bg), _dev(k), _dev(Sbar), _dev(recbar)
+    _check(lib().abcmb_perturb_adjoint(bg.shape[0], _ptr(bg), _ptr(k), k.shape[0], ctypes.byref(o), _ptr(Sbar),
+                                       _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                       _ptr(recbar), _stream()),
+           "abcmb_perturb_adjoint")
+    return recbar
+
+
+def abcmb_cl_adjoint(bg, Delta, k, o: Options, Clbar, recbar, Deltabar=None):
+    _dev(bg), _dev(Delta), _dev(k), _dev(Clbar), _dev(recbar)
+    if Deltabar is None:
+        Deltabar = torch.empty_like(Delta)
+    _check(lib().abcmb_cl_adjoint(bg.shape[0], _ptr(bg), _ptr(Delta), _ptr(k), k.shape[0], ctypes.byref(o),
+                                  _ptr(Clbar), _ptr(Deltabar), _ptr(recbar), _stream()),
+           "abcmb_cl_adjoint")
+    return Deltabar
+
+
+def abcmb_project_adjoint(bg, S, k, o: Options, Deltabar, recbar, Sbar=None):
+    _dev(bg), _dev(S), _dev(k), _dev(Deltabar), _dev(recbar)
+    if Sbar is None:
+        Sbar = torch.empty_like(S)
+    _check(lib().abcmb_project_adjoint(bg.shape[0], _ptr(bg), _ptr(S), _ptr(k), k.shape[0], ctypes.byref(o),
+                                       _ptr(Deltabar), _ptr(Sbar), _ptr(recbar), _stream()),
+           "abcmb_project_adjoint")
+    return Sbar
+
+
+def abcmb_record_vjp(o: Options, recbar, rec_plus, rec_minus, h, grad=None):
+    _dev(recbar), _dev(rec_plus), _dev(rec_minus), _dev(h)
+    B = recbar.shape[0]
+    if grad is None:
+        grad = torch.empty((B, NPARAM), dtype=torch.float64, device=recbar.device)
+    _check(lib().abcmb_record_vjp(B, ctypes.byref(o), _ptr(recbar), _ptr(rec_plus), _ptr(rec_minus), _ptr(h),
+                                  _ptr(grad), _stream()),
+           "abcmb_record_vjp")
+    return grad
+
+
+# relative step of the central differences that give the background record's
+# parameter Jacobian (the record is smooth in the parameters: fixed-step
+# thermal history, converged root finds), floor 1e-3 in absolute terms
+FD_REL_STEP = 1e-4
+
+
+class ClWithGradient(torch.autograd.Function):
+    """C_l [B, 3, lmax_cl - 1] (FP64 path) of params [B, 6], differentiable
+    in params by the library's adjoint calls: backward runs
+    abcmb_cl_adjoint, abcmb_project_adjoint and abcmb_perturb_adjoint (the
+    tape of abcmb_perturb_taped), then contracts the adjoint of the
+    background record with its parameter Jacobian (abcmb_record_vjp)."""
+
+    @staticmethod
+    def forward(ctx, params, k, o):
+        _dev(params), _dev(k)
+        B, Nk = params.shape[0], k.shape[0]
+        bg = abcmb_background_tables(params, o)
+        ws = torch.empty(grad_workspace_bytes(B, Nk, o) // 8 + 1, dtype=torch.float64, device=params.device)
+        S, status = abcmb_perturb_taped(bg, k, o, ws)
+        D = abcmb_project(bg, S, k, o)
+        C = abcmb_cl(bg, D, k, o)
+        if bool((bg[:, S_INDEX["STATUS"]] != 0).any()) or bool((status != 0).any()):
+            raise RuntimeError("forward pass failed (background or mode status set)")
+        ctx.state = (params.detach(), k, o, bg, ws, S, D)
+        return C
+
+    @staticmethod
+    def backward(ctx, Cbar):
+        params, k, o, bg, ws, S, D = ctx.state
+        B = params.shape[0]
+        recbar = torch.zeros_like(bg)
+        Cbar = Cbar.contiguous().to(torch.float64)
+        Dbar = abcmb_cl_adjoint(bg, D, k, o, Cbar, recbar)
+        Sbar = abcmb_project_adjoint(bg, S, k, o, Dbar, recbar)
+        abcmb_perturb_adjoint(bg, k, o, Sbar, ws, recbar)
+        h = FD_REL_STEP * params.abs().clamp_min(1e-3)
+        eye = torch.eye(NPARAM, dtype=torch.float64, device=params.device)
+        pp = (params[:, None, :] + h[:, :, None] * eye).reshape(B * NPARAM, NPARAM).contiguous()
+        pm = (params[:, None, :] - h[:, :, None] * eye).reshape(B * NPARAM, NPARAM).contiguous()
+        rp = abcmb_background_tables(pp, o)
+        rm = abcmb_background_tables(pm, o)
+        grad = abcmb_record_vjp(o, recbar, rp, rm, h.contiguous())
+        return grad, None, None
+
+
+def cl_with_gradient(params: torch.Tensor, k: torch.Tensor, o: Options) -> torch.Tensor:
+    """C_l of params with torch.autograd support (see ClWithGradient)."""
+    return ClWithGradient.apply(params, k, o)
 
 
 def server_request_bytes(o: Options, lmax_cl: int, n_k: int) -> int:

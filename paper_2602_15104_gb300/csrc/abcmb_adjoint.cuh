@@ -1,0 +1,451 @@
+// Discrete adjoint of the perturbation step, one thread per (cosmology, k)
+// mode (host+device; the GPU kernels in abcmb_grad.cu call these per mode).
+//
+// Forward (fwd_taped): the extrapolated IMEX / Gragg integrator of
+// abcmb_ode.cuh on the ODE-table background, landing on every tau node and
+// writing the sources there, which also records each accepted step (start,
+// size, column count, regime, landing) and checkpoints the state every kSeg
+// accepted steps.  Rejected steps do not change the state, so the accepted
+// ones define the discrete map from the initial state to the sources.
+//
+// Backward (bwd): walks the segments last to first; each segment is replayed
+// forward from its checkpoint (the same arithmetic, so the same states), then
+// its steps are reversed: at a landing the sources' transposed Jacobian adds
+// Sbar to ybar; a step's extrapolated value is the Lagrange combination
+// sum_i c_{J,i} Z_i of its column values (Neville's tableau evaluated at
+// h = 0), so its transpose sends c_{J,i} ybar back through column i, whose
+// substeps are recomputed and reversed one by one (abcmb_adjoint_ops.cuh).
+// Every background point met on the way gets the adjoint of its ten
+// quantities, scattered into the adjoint of the ODE-table rows; the sources
+// add adjoints of the node data; the initial state adds the adjoints of the
+// conformal-time table entries at the start and of R_nu.  The start time
+// a_i(k) and the switch to the explicit regime are held fixed (their effect
+// on the sources is of the order of the ODE tolerance).
+#pragma once
+
+#include "abcmb_adjoint_ops.cuh"
+
+namespace abcmb {
+namespace adj {
+
+constexpr int kSeg = 64;        // accepted steps per checkpoint
+constexpr int kAK = kKmax;      // extrapolation columns
+constexpr int kTapeCap = 65536; // accepted steps a mode may take in a gradient run
+
+// work vectors of a mode (each N long, strided)
+enum {
+    V_Y = 0,                   // state
+    V_T = 1,                   // Neville tableau [kAK]
+    V_ZA = V_T + kAK,          // column scratch
+    V_ZB,
+    V_ST,                      // states of one column, [2 kAK + 1]
+    V_AB = V_ST + 2 * kAK + 1, // rolling adjoints [3]
+    V_YB = V_AB + 3,           // ybar
+    V_YN,                      // ybar accumulator over columns
+    V_WT,                      // scratch
+    V_CO,                      // one column's value
+    V_COUNT
+};
+
+struct ModeBufs {
+    double *work; // [V_COUNT][N] strided by M
+    double *seg;  // [kSeg + 1][N] strided by M
+    double *ckpt; // [kTapeCap / kSeg + 1][N] strided by M
+    double *tape; // [kTapeCap][3]: x, H, J | gbs << 8 | land << 9 (per mode, contiguous)
+    long stride;  // M (modes)
+};
+
+ABCMB_HD Vec wv(const ModeBufs &m, const OdeDims &d, int v) { return Vec{m.work + (long)v * d.N * m.stride, m.stride}; }
+ABCMB_HD Vec segv(const ModeBufs &m, const OdeDims &d, int s) { return Vec{m.seg + (long)s * d.N * m.stride, m.stride}; }
+ABCMB_HD Vec ckv(const ModeBufs &m, const OdeDims &d, int c) { return Vec{m.ckpt + (long)c * d.N * m.stride, m.stride}; }
+
+ABCMB_HD void vcopy(const OdeDims &d, Vec a, Vec b)
+{
+    for (int i = 0; i < d.N; i++) b[i] = a[i];
+}
+ABCMB_HD void vzero(const OdeDims &d, Vec a)
+{
+    for (int i = 0; i < d.N; i++) a[i] = 0.0;
+}
+
+// Lagrange weight of column i in T_{J,J-1}: IMEX nodes h ~ 1/i, Gragg nodes h^2 ~ 1/i^2
+ABCMB_HD double lag_w(int J, int i, bool gbs)
+{
+    double w = 1.0;
+    for (int m = 1; m <= J; m++) {
+        if (m == i) continue;
+        w *= gbs ? (double)i * i / ((double)i * i - (double)m * m) : (double)i / (double)(i - m);
+    }
+    return w;
+}
+
+struct ModeCtx {
+    OdeDims d;
+    StreamCoef sc;
+    const double *rec, *tab, *ot, *nodes;
+    double k, sw[3];
+    int n_tau;
+};
+
+ABCMB_HD Bg10 bg_at(const ModeCtx &c, double lna) { return bg_eval(c.ot, hw_at(lna)); }
+
+ABCMB_HD NodeD node_at(const ModeCtx &c, int n)
+{
+    const double *nd = c.nodes + 8 * n;
+    return NodeD{nd[N_HC], nd[N_DHC], nd[N_G], nd[N_DG], nd[N_EXPMK]};
+}
+
+// one column of a step: IMEX with j substeps or Gragg with 2j, from y into out
+// (with keep, ST[m] = state after m substeps, ST[0] = y)
+ABCMB_HD void column(const ModeCtx &c, const ModeBufs &mb, double x, double H, int j, bool gbs, Vec y, Vec out,
+                     bool keep)
+{
+    const OdeDims &d = c.d;
+    if (!gbs) {
+        const double hs = H / j;
+        vcopy(d, y, out);
+        if (keep) vcopy(d, y, wv(mb, d, V_ST));
+        Bg10 bc = bg_at(c, x);
+        for (int m = 0; m < j; m++) {
+            const double xm = m == j - 1 ? x + H : x + (m + 1) * hs;
+            const Bg10 bn = bg_at(c, xm);
+            Vec w = wv(mb, d, V_WT);
+            vcopy(d, out, w);
+            op_E(d, c.sc, c.k, bc, out, w, hs);
+            solve_M(d, c.k, bn, hs, w);
+            vcopy(d, w, out);
+            if (keep) vcopy(d, out, wv(mb, d, V_ST + m + 1));
+            bc = bn;
+        }
+    } else {
+        const int n = 2 * j;
+        const double hs = H / n;
+        Vec za = wv(mb, d, V_ZA), zb = wv(mb, d, V_ZB);
+        vcopy(d, y, za);
+        vcopy(d, y, zb);
+        {
+            const Bg10 b0 = bg_at(c, x);
+            op_E(d, c.sc, c.k, b0, za, zb, hs);
+            op_T(d, c.k, b0, za, zb, hs);
+        }
+        if (keep) {
+            vcopy(d, za, wv(mb, d, V_ST));
+            vcopy(d, zb, wv(mb, d, V_ST + 1));
+        }
+        // za = z_{m-1}, zb = z_m
+        for (int m = 1; m < n; m++) {
+            const Bg10 bm = bg_at(c, x + m * hs);
+            op_E(d, c.sc, c.k, bm, zb, za, 2.0 * hs);
+            op_T(d, c.k, bm, zb, za, 2.0 * hs); // za = z_{m+1}
+            if (keep) vcopy(d, za, wv(mb, d, V_ST + m + 1));
+            Vec t = za;
+            za = zb;
+            zb = t;
+        }
+        vcopy(d, zb, out);
+    }
+}
+
+// Neville update of the tableau V_T with column j's value raw: afterwards
+// V_T[s] = T_{j,s}, s < j (IMEX: nodes h ~ 1/j, Gragg: h^2 ~ 1/j^2)
+ABCMB_HD void neville(const OdeDims &d, const ModeBufs &mb, Vec raw, int j, bool gbs)
+{
+    for (int i = 0; i < d.N; i++) {
+        double cur = raw[i], prev = wv(mb, d, V_T)[i];
+        wv(mb, d, V_T)[i] = cur;
+        for (int s = 1; s < j; s++) {
+            const double f = gbs ? 1.0 / ((double)j * j / ((double)(j - s) * (j - s)) - 1.0)
+                                 : (double)(j - s) / (double)s;
+            const double nw = cur + (cur - prev) * f;
+            prev = wv(mb, d, V_T + s)[i];
+            wv(mb, d, V_T + s)[i] = nw;
+            cur = nw;
+        }
+    }
+}
+
+// the accepted value T_{J,J-1} of a step with J columns, into out
+ABCMB_HD void step_value(const ModeCtx &c, const ModeBufs &mb, double x, double H, int J, bool gbs, Vec y, Vec out)
+{
+    const OdeDims &d = c.d;
+    Vec raw = wv(mb, d, V_CO);
+    for (int j = 1; j <= J; j++) {
+        column(c, mb, x, H, j, gbs, y, raw, false);
+        neville(d, mb, raw, j, gbs);
+    }
+    vcopy(d, wv(mb, d, V_T + J - 1), out);
+}
+
+struct FwdResult {
+    int status, steps, accepted, emit0;
+};
+
+// Forward with the tape.  Error control as the four-lanes kernel (group
+// floors, slaved moments excluded while h / (H tau_c) > kSlavedHnu in the
+// implicit regime).
+ABCMB_HD FwdResult fwd_taped(const ModeCtx &c, const ModeBufs &mb, double rtol, double atol, int max_steps,
+                             double *S)
+{
+    const OdeDims &d = c.d;
+    FwdResult r = {ABCMB_OK, 0, 0, 0};
+    const Cosmo cz = load_cosmo(c.rec);
+    double x = cz.lna_tc;
+    {
+        const double target = c.k / kRlarge;
+        if (hconf(cz, cz.lna_tc) < target) {
+            double lo = kLna0, hi = cz.lna_tc;
+            if (hconf(cz, lo) < target) x = lo;
+            else {
+                for (int it = 0; it < 100; it++) {
+                    const double mid = 0.5 * (lo + hi);
+                    if (mid <= lo || mid >= hi) break;
+                    if (hconf(cz, mid) > target) lo = mid; else hi = mid;
+                }
+                x = 0.5 * (lo + hi);
+            }
+        }
+    }
+    double x_ns;
+    {
+        double lo = cz.lna_sw, hi = -2.0;
+        for (int it = 0; it < 60; it++) {
+            const double mid = 0.5 * (lo + hi);
+            const Herm Hm = herm_at(mid);
+            if (herm_val(c.tab, Hm, C_NUT, C_DNUT) > kNuNonStiff) lo = mid; else hi = mid;
+        }
+        x_ns = hi;
+    }
+    Vec Y = wv(mb, d, V_Y);
+    {
+        const Herm Hi = herm_at(x);
+        initial_fwd(d, c.k, herm_val(c.tab, Hi, C_TAU, C_DTAU), cz.R_nu, Y);
+    }
+    int node = 0;
+    double h = 1e-3;
+    while (node < c.n_tau) {
+        const double xn = c.nodes[8 * node + N_LNA];
+        double H = h;
+        bool land = false;
+        if (x + H >= xn) { H = xn - x; land = true; }
+        if (H <= 0.0) {
+            if (r.accepted == 0) r.emit0++;
+            sources_fwd(d, c.k, bg_at(c, xn), node_at(c, node), c.sw, Y, S + 3 * node);
+            node++;
+            continue;
+        }
+        if (++r.steps > max_steps) { r.status = ABCMB_E_MAX_STEPS; break; }
+        if (H < 1e-13 && !land) { r.status = ABCMB_E_NONFINITE; break; }
+        const bool gbs = x >= x_ns;
+        const Bg10 b0 = bg_at(c, x);
+        const bool excl = !gbs && H * b0.v[B_NU] > kSlavedHnu;
+        double cm[4] = {0, 0, 0, 0};
+        for (int i = 0; i < d.N; i++) {
+            const int g = i < 3 ? 0 : i == 3 ? 1 : i < d.iN ? 2 : 3;
+            cm[g] = fmax(cm[g], fabs(Y[i]));
+        }
+        int jacc = 0;
+        double err = 0.0;
+        Vec raw = wv(mb, d, V_CO);
+        for (int j = 1; j <= kAK; j++) {
+            column(c, mb, x, H, j, gbs, Y, raw, false);
+            neville(d, mb, raw, j, gbs);
+            if (j < 2) continue;
+            err = 0.0;
+            Vec tj = wv(mb, d, V_T + j - 1), tl = wv(mb, d, V_T + j - 2);
+            for (int i = 0; i < d.N; i++) {
+                const int g = i < 3 ? 0 : i == 3 ? 1 : i < d.iN ? 2 : 3;
+                if (excl && i >= d.iF + 2 && i < d.iN) continue;
+                const double scl = atol + rtol * fmax(fabs(Y[i]), fmax(ABCMB_CHAIN_FLOOR * cm[g], 1e-290));
+                const double e = fabs(tj[i] - tl[i]) / scl;
+                if (!(e <= err)) err = e;
+            }
+            if (!(err == err)) break;
+            if (err <= 1.0) { jacc = j; break; }
+        }
+        if (!(err == err) || (jacc == 0 && err > 1e300)) { r.status = ABCMB_E_NONFINITE; break; }
+        if (jacc) {
+            if (r.accepted >= kTapeCap) { r.status = ABCMB_E_MAX_STEPS; break; }
+            if (r.accepted % kSeg == 0) vcopy(d, Y, ckv(mb, d, r.accepted / kSeg));
+            double *tp = mb.tape + 3 * (long)r.accepted;
+            tp[0] = x;
+            tp[1] = H;
+            tp[2] = (double)(jacc | (gbs ? 256 : 0) | (land ? 512 : 0));
+            r.accepted++;
+            vcopy(d, wv(mb, d, V_T + jacc - 1), Y); // as step_value computes it in the replay
+            x = land ? xn : x + H;
+            double fac = err > 0.0 ? 0.9 * exp(-log(err) / (gbs ? 2 * jacc - 1 : jacc)) : 4.0;
+            if (jacc < kAK - 1) fac *= 1.5;
+            fac = fmin(4.0, fmax(0.2, fac));
+            const double hn = H * fac;
+            h = land ? fmax(h, hn) : hn;
+            if (land) {
+                sources_fwd(d, c.k, bg_at(c, xn), node_at(c, node), c.sw, Y, S + 3 * node);
+                node++;
+            }
+        } else {
+            h = H * fmin(0.9, fmax(0.1, 0.9 * exp(-log(err) / (gbs ? 2 * kAK - 1 : kAK))));
+        }
+    }
+    for (int n = node; n < c.n_tau; n++) S[3 * n] = S[3 * n + 1] = S[3 * n + 2] = 0.0;
+    return r;
+}
+
+// Adjoint sink: the adjoint of the background record (same layout as the record).
+struct Sinks {
+    double *recbar;
+};
+
+ABCMB_HD void scatter_bg(const Sinks &sk, double lna, const Bg10 &bb)
+{
+    bg_scatter(sk.recbar + ABCMB_BG_ODETAB, hw_at(lna), bb);
+}
+
+ABCMB_HD void zero_bg(Bg10 &b)
+{
+    for (int q = 0; q < B_N; q++) b.v[q] = 0.0;
+}
+
+// ybar <- Phi^T ybar for one accepted step (y = its start state)
+ABCMB_HD void step_adjoint(const ModeCtx &c, const ModeBufs &mb, const Sinks &sk, double x, double H, int J,
+                           bool gbs, Vec y, Vec yb)
+{
+    const OdeDims &d = c.d;
+    Vec acc = wv(mb, d, V_YN);
+    vzero(d, acc);
+    for (int i = 1; i <= J; i++) {
+        const double w = lag_w(J, i, gbs);
+        column(c, mb, x, H, i, gbs, y, wv(mb, d, V_CO), true); // states in ST[0..]
+        if (!gbs) {
+            const double hs = H / i;
+            Vec v = wv(mb, d, V_AB);
+            for (int e = 0; e < d.N; e++) v[e] = w * yb[e];
+            for (int m = i; m >= 1; m--) {
+                // substep m: z_m = M(bn)^-1 (z_{m-1} + hs E(bc) z_{m-1})
+                const double xa = x + (m - 1) * hs;
+                const double xb = m == i ? x + H : x + m * hs;
+                const Bg10 bc = bg_at(c, xa), bn = bg_at(c, xb);
+                Vec zin = wv(mb, d, V_ST + m - 1), zout = wv(mb, d, V_ST + m);
+                solve_Mt(d, c.k, bn, hs, v); // v = wbar
+                Bg10 bbn, bbc;
+                zero_bg(bbn);
+                zero_bg(bbc);
+                op_T_bgrad(d, c.k, v, zout, hs, bbn);
+                op_E_bgrad(d, c.sc, c.k, bc, v, zin, hs, bbc);
+                scatter_bg(sk, xb, bbn);
+                scatter_bg(sk, xa, bbc);
+                Vec t = wv(mb, d, V_AB + 1);
+                vcopy(d, v, t);
+                op_Et(d, c.sc, c.k, bc, t, v, hs); // v = (I + hs E^T) wbar
+            }
+            for (int e = 0; e < d.N; e++) acc[e] += v[e];
+        } else {
+            const int n = 2 * i;
+            const double hs = H / n;
+            // rolling adjoints: a2 = zbar_{m+1}, a1 = zbar_m, a0 = zbar_{m-1}
+            Vec a2 = wv(mb, d, V_AB), a1 = wv(mb, d, V_AB + 1), a0 = wv(mb, d, V_AB + 2);
+            for (int e = 0; e < d.N; e++) {
+                a2[e] = w * yb[e]; // zbar_n
+                a1[e] = 0.0;       // zbar_{n-1}
+            }
+            for (int m = n - 1; m >= 1; m--) {
+                // z_{m+1} = z_{m-1} + 2 hs f_m(z_m)
+                const Bg10 bm = bg_at(c, x + m * hs);
+                Vec zm = wv(mb, d, V_ST + m);
+                for (int e = 0; e < d.N; e++) a0[e] = a2[e]; // zbar_{m-1} = zbar_{m+1} so far
+                op_Et(d, c.sc, c.k, bm, a2, a1, 2.0 * hs);
+                op_Tt(d, c.k, bm, a2, a1, 2.0 * hs);
+                Bg10 bb;
+                zero_bg(bb);
+                op_E_bgrad(d, c.sc, c.k, bm, a2, zm, 2.0 * hs, bb);
+                op_T_bgrad(d, c.k, a2, zm, 2.0 * hs, bb);
+                scatter_bg(sk, x + m * hs, bb);
+                Vec t = a2;
+                a2 = a1;
+                a1 = a0;
+                a0 = t;
+            }
+            // a2 = zbar_1, a1 = zbar_0 so far; z_1 = z_0 + hs f_0(z_0)
+            const Bg10 b0 = bg_at(c, x);
+            Vec z0 = wv(mb, d, V_ST);
+            for (int e = 0; e < d.N; e++) a1[e] += a2[e];
+            op_Et(d, c.sc, c.k, b0, a2, a1, hs);
+            op_Tt(d, c.k, b0, a2, a1, hs);
+            Bg10 bb;
+            zero_bg(bb);
+            op_E_bgrad(d, c.sc, c.k, b0, a2, z0, hs, bb);
+            op_T_bgrad(d, c.k, a2, z0, hs, bb);
+            scatter_bg(sk, x, bb);
+            for (int e = 0; e < d.N; e++) acc[e] += a1[e];
+        }
+    }
+    vcopy(d, acc, yb);
+}
+
+// sources' adjoint at node n for state y: ybar += ..., the sink gets b and node data
+ABCMB_HD void sources_adjoint(const ModeCtx &c, const Sinks &sk, int n, Vec y, const double *Sb, Vec yb)
+{
+    const double lna = c.nodes[8 * n + N_LNA];
+    Bg10 bb;
+    zero_bg(bb);
+    NodeD nb{0, 0, 0, 0, 0};
+    sources_rev(c.d, c.k, bg_at(c, lna), node_at(c, n), c.sw, y, Sb + 3 * n, yb, bb, nb);
+    scatter_bg(sk, lna, bb);
+    double *nd = sk.recbar + ABCMB_BG_NODES + 8 * n;
+    add_to(nd + N_HC, nb.Hc);
+    add_to(nd + N_DHC, nb.dHc);
+    add_to(nd + N_G, nb.g);
+    add_to(nd + N_DG, nb.dg);
+    add_to(nd + N_EXPMK, nb.emk);
+}
+
+// Backward pass for a mode whose forward (fwd_taped) returned fr; Sb [n_tau][3]
+ABCMB_HD void bwd(const ModeCtx &c, const ModeBufs &mb, const Sinks &sk, const FwdResult &fr, const double *Sb)
+{
+    const OdeDims &d = c.d;
+    if (fr.status != ABCMB_OK) return;
+    Vec yb = wv(mb, d, V_YB);
+    vzero(d, yb);
+    int node = c.n_tau - 1;
+    const int nseg = (fr.accepted + kSeg - 1) / kSeg;
+    for (int sgi = nseg - 1; sgi >= 0; sgi--) {
+        const int s0 = sgi * kSeg, s1 = s0 + kSeg < fr.accepted ? s0 + kSeg : fr.accepted;
+        // replay: seg[s - s0] = state at the start of step s, seg[s1 - s0] = after the last
+        vcopy(d, ckv(mb, d, sgi), segv(mb, d, 0));
+        for (int s = s0; s < s1; s++) {
+            const double *tp = mb.tape + 3 * (long)s;
+            const int fl = (int)tp[2];
+            step_value(c, mb, tp[0], tp[1], fl & 255, (fl & 256) != 0, segv(mb, d, s - s0), segv(mb, d, s - s0 + 1));
+        }
+        for (int s = s1 - 1; s >= s0; s--) {
+            const double *tp = mb.tape + 3 * (long)s;
+            const int fl = (int)tp[2];
+            if (fl & 512) {
+                sources_adjoint(c, sk, node, segv(mb, d, s - s0 + 1), Sb, yb);
+                node--;
+            }
+            step_adjoint(c, mb, sk, tp[0], tp[1], fl & 255, (fl & 256) != 0, segv(mb, d, s - s0), yb);
+        }
+    }
+    // emissions at the start (the start on a node) use the initial state
+    Vec y0 = wv(mb, d, V_Y);
+    const Cosmo cz = load_cosmo(c.rec);
+    if (fr.accepted > 0) vcopy(d, ckv(mb, d, 0), y0);
+    while (node >= 0) {
+        sources_adjoint(c, sk, node, y0, Sb, yb);
+        node--;
+    }
+    // initial state: tau_i from the conformal-time table at the start, and R_nu
+    const double x0 = fr.accepted > 0 ? mb.tape[0] : c.nodes[N_LNA];
+    const Herm Hi = herm_at(x0);
+    const double tau_i = herm_val(c.tab, Hi, C_TAU, C_DTAU);
+    const double taub = initial_dtau(d, c.k, tau_i, cz.R_nu, yb);
+    double *tb = sk.recbar + ABCMB_BG_TABLE;
+    add_to(tb + 8 * Hi.j + C_TAU, Hi.h00 * taub);
+    add_to(tb + 8 * (Hi.j + 1) + C_TAU, Hi.h01 * taub);
+    add_to(tb + 8 * Hi.j + C_DTAU, kDlna * Hi.h10 * taub);
+    add_to(tb + 8 * (Hi.j + 1) + C_DTAU, kDlna * Hi.h11 * taub);
+    add_to(sk.recbar + ABCMB_S_RNU, initial_dRn(d, c.k, tau_i, cz.R_nu, yb));
+}
+
+} // namespace adj
+} // namespace abcmb
