@@ -290,14 +290,50 @@ ABCMB_HD FwdResult fwd_taped(const ModeCtx &c, const ModeBufs &mb, double rtol, 
     return r;
 }
 
-// Adjoint sink: the adjoint of the background record (same layout as the record).
+// Adjoint of the ODE table's two rows j, j + 1 (20 entries each), summed
+// locally: consecutive substeps mostly fall in the same table interval, so
+// their contributions are added to the record (atomically on the device)
+// only when the interval changes.  Added directly, every mode of a cosmology
+// would contend for the same few addresses at every substep.
+struct RowAcc {
+    int j;
+    double v[40];
+};
+
+// Adjoint sink: the adjoint of the background record (same layout as the
+// record) and the row accumulator in front of its ODE table.
 struct Sinks {
     double *recbar;
+    RowAcc *acc;
 };
+
+ABCMB_HD void flush_rows(const Sinks &sk)
+{
+    RowAcc &a = *sk.acc;
+    if (a.j >= 0) {
+        double *r = sk.recbar + ABCMB_BG_ODETAB + 20 * (long)a.j;
+        for (int e = 0; e < 40; e++)
+            if (a.v[e] != 0.0) add_to(r + e, a.v[e]);
+    }
+    a.j = -1;
+}
 
 ABCMB_HD void scatter_bg(const Sinks &sk, double lna, const Bg10 &bb)
 {
-    bg_scatter(sk.recbar + ABCMB_BG_ODETAB, hw_at(lna), bb);
+    const HW h = hw_at(lna);
+    RowAcc &a = *sk.acc;
+    if (h.j != a.j) {
+        flush_rows(sk);
+        a.j = h.j;
+        for (int e = 0; e < 40; e++) a.v[e] = 0.0;
+    }
+    for (int q = 0; q < B_N; q++) {
+        const double g = bb.v[q];
+        a.v[2 * q] += h.w0 * g;
+        a.v[2 * q + 1] += h.d0 * g;
+        a.v[20 + 2 * q] += h.w1 * g;
+        a.v[21 + 2 * q] += h.d1 * g;
+    }
 }
 
 ABCMB_HD void zero_bg(Bg10 &b)
@@ -445,6 +481,7 @@ ABCMB_HD void bwd(const ModeCtx &c, const ModeBufs &mb, const Sinks &sk, const F
     add_to(tb + 8 * Hi.j + C_DTAU, kDlna * Hi.h10 * taub);
     add_to(tb + 8 * (Hi.j + 1) + C_DTAU, kDlna * Hi.h11 * taub);
     add_to(sk.recbar + ABCMB_S_RNU, initial_dRn(d, c.k, tau_i, cz.R_nu, yb));
+    flush_rows(sk);
 }
 
 } // namespace adj

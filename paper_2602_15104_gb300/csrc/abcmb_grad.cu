@@ -138,7 +138,9 @@ adjoint_kernel(int B, int Nk, const double *__restrict__ bg, long len, const dou
     const int *res = (const int *)(ws + g.res) + 4 * mi;
     const FwdResult r = {res[0], res[1], res[2], res[3]};
     const double *Sb = Sbar + ((long)b * Nk + kidx) * (long)c.n_tau * 3;
-    bwd(c, mb, Sinks{recbar + (long)b * len}, r, Sb);
+    RowAcc acc;
+    acc.j = -1;
+    bwd(c, mb, Sinks{recbar + (long)b * len, &acc}, r, Sb);
 }
 
 // ---- k-quadrature adjoint: grid (ceil(nl / 256), B) ----

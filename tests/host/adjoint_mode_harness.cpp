@@ -60,7 +60,9 @@ extern "C" int h_grad(const double *rec, double k, int L, double rtol, const dou
     std::vector<double> S(3 * (size_t)R.c.n_tau);
     const FwdResult fr = fwd_taped(R.c, R.mb, rtol, 1e-14, 10000000, S.data());
     if (fr.status != ABCMB_OK) return fr.status;
-    bwd(R.c, R.mb, Sinks{recbar}, fr, Sb);
+    RowAcc acc;
+    acc.j = -1;
+    bwd(R.c, R.mb, Sinks{recbar, &acc}, fr, Sb);
     return ABCMB_OK;
 }
 
@@ -80,5 +82,9 @@ extern "C" void h_step_adj(const double *rec, double k, int L, double x, double 
     Run R;
     setup(R, rec, k, L);
     std::vector<double> yy(y, y + R.d.N);
-    step_adjoint(R.c, R.mb, Sinks{recbar}, x, H, J, gbs != 0, Vec{yy.data(), 1}, Vec{yb, 1});
+    RowAcc acc;
+    acc.j = -1;
+    const Sinks sk{recbar, &acc};
+    step_adjoint(R.c, R.mb, sk, x, H, J, gbs != 0, Vec{yy.data(), 1}, Vec{yb, 1});
+    flush_rows(sk);
 }
