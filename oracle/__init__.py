@@ -52,6 +52,7 @@ def lib():
         L.orc_run.argtypes = [_D, ctypes.c_int, _D, _D, ctypes.c_int, ctypes.c_int, _D, _D, _D,
                               _L, ctypes.c_int]
         L.orc_radau_tableau.argtypes = [_D]
+        L.orc_pk.argtypes = [_D, _D, _D, ctypes.c_int, ctypes.c_double, _D, ctypes.c_int]
         _lib = L
     return _lib
 
@@ -171,6 +172,16 @@ def run(params, k, n_tau, lmax_cl, o, want=("S", "Delta", "Cl"), nthreads=0):
     if rc:
         raise RuntimeError(f"oracle run failed ({rc})")
     return {"S": S, "Delta": D, "Cl": C, "steps": steps}
+
+
+def pk(params, k, z, o, nthreads=0):
+    """Matter power spectrum P(k, z) [Mpc^3] (App. B.4 eq. PK) of one cosmology."""
+    k = _arr(k)
+    out = np.zeros(k.size)
+    rc = lib().orc_pk(_p(_arr(params)), _p(_arr(o)), _p(k), k.size, float(z), _p(out), int(nthreads))
+    if rc:
+        raise RuntimeError(f"oracle P(k) failed ({rc})")
+    return out
 
 
 class Cosmo:

@@ -383,3 +383,42 @@ int orc_count_steps(const double *p, int n_tau, const double *oa, const double *
     orc_cosmo_free(&c);
     return 0;
 }
+
+/* Matter power spectrum at redshift z (App. B.4, eq. PK):
+     P(k, z) = (2 pi^2 / k^3) A_s (k / k_pivot)^(n_s - 1) delta_m^2,
+     delta_m = (rho_c delta_c + rho_b delta_b) / (rho_c + rho_b),
+   the density-weighted contrast of the non-relativistic species (CDM and
+   baryons here; photons and massless neutrinos are relativistic), with
+   delta_c, delta_b (state entries 1 and 2) from the mode integrated from its
+   adiabatic start to ln a = -ln(1 + z) on the oracle's step schedule. */
+int orc_pk(const double *p, const double *oa, const double *k, int nk, double z, double *Pk, int nthreads)
+{
+    orc_cosmo c;
+    orc_opts o;
+    opts_from(oa, &o);
+    if (orc_cosmo_init(&c, p, 0, o.hooks & ORC_HOOK_EDS_CDM)) return -1;
+    set_threads(nthreads);
+    const double lna = -log1p(z);
+    orc_bg b;
+    orc_bg_eval(&c, lna, &b, 0);
+    const int N = orc_nstate(&o);
+    int rc = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : rc)
+    for (int t = 0; t < nk; t++) {
+        int ik = nk - 1 - t;
+        double *y = (double *)malloc(sizeof(double) * N);
+        long st = 0;
+        if (orc_lna_start(&c, k[ik]) >= lna) {
+            rc |= 2; /* the mode starts after the requested time */
+            Pk[ik] = NAN;
+        } else {
+            rc |= orc_solve_mode(&c, &o, k[ik], &lna, 1, y, NULL, 0.0, &st);
+            const double dm = (b.fc * y[1] + b.fb * y[2]) / (b.fc + b.fb);
+            const double kk = k[ik];
+            Pk[ik] = 2.0 * S_PI * S_PI / (kk * kk * kk) * c.A_s * pow(kk / c.k_pivot, c.n_s - 1.0) * dm * dm;
+        }
+        free(y);
+    }
+    orc_cosmo_free(&c);
+    return rc;
+}

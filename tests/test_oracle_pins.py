@@ -417,3 +417,37 @@ def test_sachs_wolfe_plateau():
     l = np.arange(2, 13)
     Dl = l * (l + 1) * r["Cl"][0] / (2 * np.pi) / 2.1e-9
     assert np.all(Dl[:6] > 1 / 25) and np.all(Dl[:6] < 1.5 / 25), Dl
+
+
+# ---- matter power spectrum (App. B.4 eq. PK) ----
+
+def test_pk_einstein_de_sitter_growth():
+    # EdS, CDM only: delta_m = delta_c grows like a once the decaying mode is
+    # gone, so P(k, z) = P(k, 0) / (1 + z)^2 exactly
+    p = np.array([0.022, 0.12, 0.7, 1.0, 3.0, 0.06])
+    o = O.opts(lmax=8, hooks=O.HOOK_EDS_CDM)
+    k = np.array([1e-3, 1e-2])
+    P0, P1 = O.pk(p, k, 0.0, o), O.pk(p, k, 1.0, o)
+    np.testing.assert_allclose(P1 / P0, 0.25, rtol=1e-6)
+
+
+def test_pk_superhorizon_slope_is_the_tilt(small_params):
+    # k tau_0 << 1: synchronous-gauge delta_m grows like k^2 (up to
+    # (k tau)^2 corrections), so P = (2 pi^2 / k^3) P_R(k) delta_m^2 ~ k^{n_s}
+    o = O.opts(lmax=8)
+    k = np.array([5e-6, 1e-5])
+    P = O.pk(small_params, k, 0.0, o)
+    slope = np.log(P[1] / P[0]) / np.log(2.0)
+    assert abs(slope - small_params[3]) < 2e-4, (slope, small_params[3])
+
+
+def test_pk_primordial_dependence_is_exact(small_params):
+    # the ODE does not see A_s or n_s: P scales with A_s and with (k/k_pivot)^dn_s
+    o = O.opts(lmax=8)
+    k = np.array([2e-4, 1e-3, 4e-3])
+    P = O.pk(small_params, k, 0.0, o)
+    q = small_params.copy()
+    q[3] += 0.02
+    q[4] += 0.1
+    Q = O.pk(q, k, 0.0, o)
+    np.testing.assert_allclose(Q / P, np.exp(0.1) * (k / 0.05) ** 0.02, rtol=1e-11)
