@@ -192,6 +192,23 @@ int abcmb_perturb_noalloc(int B, const double *bg, const double *k, int Nk, cons
                           double *S, int *mode_status, int *steps, void *stream);
 
 /*
+ * Matter power spectrum (App. B.4, eq. PK) at redshift z:
+ *   P(k, z) = (2 pi^2 / k^3) A_s (k/k_pivot)^(n_s-1) delta_m(k, z)^2,
+ *   delta_m = (rho_c delta_c + rho_b delta_b) / (rho_c + rho_b)
+ * (the non-relativistic species), from the same perturbation equations and
+ * integrator as abcmb_perturb, run from a_i(k) to a = 1/(1+z) with no tau
+ * nodes to land on.
+ *
+ *   bg, k        as abcmb_perturb
+ *   z            0 <= z <= 1000
+ *   Pk           [B][Nk]       device, written, Mpc^3 (NaN for a failed mode)
+ *   mode_status  [B][Nk] int32 device, written as abcmb_perturb
+ * Hierarchies up to 63 (ABCMB_E_INVALID_ARG above).
+ */
+int abcmb_matter_pk(int B, const double *bg, const double *k, int Nk, const abcmb_options *o, double z,
+                    double *Pk, int *mode_status, void *stream);
+
+/*
  * Line-of-sight projection (App. B.4): for every ell in [2, lmax_cl],
  *   Delta_T = sum_i w_i [S_T0 j_l + S_T1 j_l' + scale_pol S_P (3 j_l'' + j_l)/2]
  *   Delta_E = sqrt(3 (l+2)! / (8 (l-2)!)) sum_i w_i sqrt(6) S_P j_l / x^2

@@ -81,6 +81,7 @@ def lib():
         L.abcmb_perturb.argtypes = [ctypes.c_int, _P, _P, ctypes.c_int, O, _P, _P, _P, _P,
                                     ctypes.c_size_t, _P]
         L.abcmb_perturb_noalloc.argtypes = [ctypes.c_int, _P, _P, ctypes.c_int, O, _P, _P, _P, _P]
+        L.abcmb_matter_pk.argtypes = [ctypes.c_int, _P, _P, ctypes.c_int, O, ctypes.c_double, _P, _P, _P]
         L.abcmb_project.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, O, _P, _P]
         L.abcmb_cl.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, O, _P, _P]
         L.abcmb_project_mixed.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, O, _P, _P]
@@ -181,6 +182,19 @@ def abcmb_perturb_noalloc(bg: torch.Tensor, k: torch.Tensor, o: Options, S, stat
     B, Nk = bg.shape[0], k.shape[0]
     return lib().abcmb_perturb_noalloc(B, _ptr(bg), _ptr(k), Nk, ctypes.byref(o), _ptr(S), _ptr(status),
                                        _ptr(steps), _stream())
+
+
+def abcmb_matter_pk(bg: torch.Tensor, k: torch.Tensor, o: Options, z: float = 0.0, out=None, status=None):
+    """-> P(k, z) [B, Nk] in Mpc^3, mode status [B, Nk] int32."""
+    _dev(bg), _dev(k)
+    B, Nk = bg.shape[0], k.shape[0]
+    Pk = out if out is not None else torch.empty((B, Nk), dtype=torch.float64, device=bg.device)
+    if status is None:
+        status = torch.empty((B, Nk), dtype=torch.int32, device=bg.device)
+    _check(lib().abcmb_matter_pk(B, _ptr(bg), _ptr(k), Nk, ctypes.byref(o), float(z), _ptr(Pk), _ptr(status),
+                                 _stream()),
+           "abcmb_matter_pk")
+    return Pk, status
 
 
 def abcmb_project(bg: torch.Tensor, S: torch.Tensor, k: torch.Tensor, o: Options, out=None):

@@ -417,16 +417,35 @@ ABCMB_HD void step_adjoint(const ModeCtx &c, const ModeBufs &mb, const Sinks &sk
     vcopy(d, acc, yb);
 }
 
-// sources' adjoint at node n for state y: ybar += ..., the sink gets b and node data
-ABCMB_HD void sources_adjoint(const ModeCtx &c, const Sinks &sk, int n, Vec y, const double *Sb, Vec yb)
+// sources' adjoint at node n for state y: ybar += ..., the sink gets b and
+// node data, and the node's position ln a_n: the state there moves with the
+// ODE flow, dy/dln a_n = f(y), and the table quantities with their
+// interpolant's slope (the steps landing on the node are otherwise frozen)
+ABCMB_HD void sources_adjoint(const ModeCtx &c, const ModeBufs &mb, const Sinks &sk, int n, Vec y,
+                              const double *Sb, Vec yb)
 {
+    const OdeDims &d = c.d;
     const double lna = c.nodes[8 * n + N_LNA];
+    const Bg10 b = bg_at(c, lna);
     Bg10 bb;
     zero_bg(bb);
     NodeD nb{0, 0, 0, 0, 0};
-    sources_rev(c.d, c.k, bg_at(c, lna), node_at(c, n), c.sw, y, Sb + 3 * n, yb, bb, nb);
+    Vec ys = wv(mb, d, V_AB), f = wv(mb, d, V_AB + 1);
+    vzero(d, ys);
+    sources_rev(d, c.k, b, node_at(c, n), c.sw, y, Sb + 3 * n, ys, bb, nb);
+    vzero(d, f);
+    op_E(d, c.sc, c.k, b, y, f, 1.0);
+    op_T(d, c.k, b, y, f, 1.0);
+    double lnab = 0.0;
+    for (int e = 0; e < d.N; e++) {
+        lnab += ys[e] * f[e];
+        yb[e] += ys[e];
+    }
+    const Bg10 db = bg_eval_dlna(c.ot, lna);
+    for (int q = 0; q < B_N; q++) lnab += bb.v[q] * db.v[q];
     scatter_bg(sk, lna, bb);
     double *nd = sk.recbar + ABCMB_BG_NODES + 8 * n;
+    add_to(nd + N_LNA, lnab);
     add_to(nd + N_HC, nb.Hc);
     add_to(nd + N_DHC, nb.dHc);
     add_to(nd + N_G, nb.g);
@@ -456,7 +475,7 @@ ABCMB_HD void bwd(const ModeCtx &c, const ModeBufs &mb, const Sinks &sk, const F
             const double *tp = mb.tape + 3 * (long)s;
             const int fl = (int)tp[2];
             if (fl & 512) {
-                sources_adjoint(c, sk, node, segv(mb, d, s - s0 + 1), Sb, yb);
+                sources_adjoint(c, mb, sk, node, segv(mb, d, s - s0 + 1), Sb, yb);
                 node--;
             }
             step_adjoint(c, mb, sk, tp[0], tp[1], fl & 255, (fl & 256) != 0, segv(mb, d, s - s0), yb);
@@ -467,7 +486,7 @@ ABCMB_HD void bwd(const ModeCtx &c, const ModeBufs &mb, const Sinks &sk, const F
     const Cosmo cz = load_cosmo(c.rec);
     if (fr.accepted > 0) vcopy(d, ckv(mb, d, 0), y0);
     while (node >= 0) {
-        sources_adjoint(c, sk, node, y0, Sb, yb);
+        sources_adjoint(c, mb, sk, node, y0, Sb, yb);
         node--;
     }
     // initial state: tau_i from the conformal-time table at the start, and R_nu

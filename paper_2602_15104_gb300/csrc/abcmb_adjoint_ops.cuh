@@ -55,6 +55,21 @@ ABCMB_HD Bg10 bg_eval(const double *ot, const HW &h)
     return b;
 }
 
+// d/dln a of the ten interpolated quantities (derivative of the cubic Hermite)
+ABCMB_HD Bg10 bg_eval_dlna(const double *ot, double lna)
+{
+    const double t = (lna - kLna0) * ABCMB_BG_PER_UNIT;
+    int j = (int)floor(t);
+    j = j < 0 ? 0 : (j > kNlna - 2 ? kNlna - 2 : j);
+    const double u = t - (double)j, um = 1.0 - u, s = ABCMB_BG_PER_UNIT;
+    const double w0 = -6.0 * u * um * s, w1 = -w0;
+    const double d0 = um * (1.0 - 3.0 * u), d1 = u * (3.0 * u - 2.0); // kDlna * s = 1
+    Bg10 b;
+    const double *r0 = ot + 20 * j, *r1 = r0 + 20;
+    for (int q = 0; q < B_N; q++) b.v[q] = w0 * r0[2 * q] + w1 * r1[2 * q] + d0 * r0[2 * q + 1] + d1 * r1[2 * q + 1];
+    return b;
+}
+
 ABCMB_HD void add_to(double *p, double v)
 {
 #ifdef __CUDA_ARCH__

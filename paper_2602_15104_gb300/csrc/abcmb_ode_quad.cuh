@@ -320,18 +320,21 @@ __device__ __forceinline__ void q_rhs_axpy(const double (&s)[3][P], const double
     }
 }
 
-// Sources at a tau node from the accepted state in shared memory (lane 0).
-__device__ __forceinline__ void q_sources(const double *ot, const double *nd, double k, const double sw[3],
-                                          const double *Y, const double sc[4], int P, double *S)
+// The state components the sources read: photon F_0..F_2, G_0, G_2,
+// neutrino F_0..F_2 (lane 0 of a quad), then the four scalars.
+constexpr int kSrcComp = 12;
+
+// Sources at a tau node from the state components v (kSrcComp values, order above).
+__device__ __forceinline__ void q_sources_v(const double *ot, const double *nd, double k, const double sw[3],
+                                            const double (&v)[kSrcComp], double *S)
 {
     const QBg b = obg_all(ot, nd[N_LNA]);
     const double Hc = nd[N_HC], dHc = nd[N_DHC], g = nd[N_G], dg = nd[N_DG], emk = nd[N_EXPMK];
     const double kH = k / Hc, k2 = k * k;
-    auto el = [&](int e) { return Y[e * 32]; };
-    const double eta = sc[0], dc = sc[1], db = sc[2], tb = sc[3];
-    const double Fg0 = el(0), Fg1 = el(1), Fg2 = el(2);
-    const double G0 = el(P), G2 = el(P + 2);
-    const double Fn0 = el(2 * P), Fn1 = el(2 * P + 1), Fn2 = el(2 * P + 2);
+    const double eta = v[8], dc = v[9], db = v[10], tb = v[11];
+    const double Fg0 = v[0], Fg1 = v[1], Fg2 = v[2];
+    const double G0 = v[3], G2 = v[4];
+    const double Fn0 = v[5], Fn1 = v[6], Fn2 = v[7];
     const double hp = 2.0 * kH * kH * eta + 3.0 * (b.fc * dc + b.fb * db + b.fg * Fg0 + b.fnu * Fn0);
     const double ep = 1.5 / kH * (b.fb * tb / k + b.fg * Fg1 + b.fnu * Fn1);
     const double alpha = Hc * (hp + 6.0 * ep) / (2.0 * k2);
@@ -345,6 +348,26 @@ __device__ __forceinline__ void q_sources(const double *ot, const double *nd, do
     S[0] = sw[0] * swt + sw[1] * isw + sw[2] * dop;
     S[1] = sw[1] * emk * k * (Hap + 2.0 * Hc * alpha - eta);
     S[2] = g * (Fg2 + G0 + G2) * 0.125;
+}
+
+// element index (in a lane's state rows) of source component c < 8, held by lane 0
+template <int P>
+__device__ __forceinline__ int src_elem(int c)
+{
+    return c < 3 ? c : (c == 3 ? P : (c == 4 ? P + 2 : 2 * P + (c - 5)));
+}
+
+// Sources at a tau node from the accepted state in shared memory (lane 0).
+template <int P>
+__device__ __forceinline__ void q_sources(const double *ot, const double *nd, double k, const double sw[3],
+                                          const double *Y, const double sc[4], double *S)
+{
+    double v[kSrcComp];
+#pragma unroll
+    for (int c = 0; c < 8; c++) v[c] = Y[src_elem<P>(c) * 32];
+#pragma unroll
+    for (int s = 0; s < 4; s++) v[8 + s] = sc[s];
+    q_sources_v(ot, nd, k, sw, v, S);
 }
 
 // scalar q of four (eta, delta_c, delta_b, theta_b): this lane's share of the scalar row
@@ -369,11 +392,118 @@ __device__ __forceinline__ double quad_max(double v)
     return v;
 }
 
-// Integrate the modes of one warp (8 per warp, mode index mi for this lane's quad).
+// Matter power spectrum (App. B.4, eq. PK) from the scalars sc (eta, delta_c,
+// delta_b, theta_b) at ln a = lna: P = (2 pi^2 / k^3) A_s (k/k_pivot)^(n_s-1)
+// delta_m^2, delta_m = (rho_c delta_c + rho_b delta_b) / (rho_c + rho_b).
+__device__ __forceinline__ double q_matter_pk(const double *ot, const double *rec, double lna, double k,
+                                              const double sc[4])
+{
+    const QBg b = obg_all(ot, lna);
+    const double dm = (b.fc * sc[1] + b.fb * sc[2]) / (b.fc + b.fb);
+    const double As = rec[ABCMB_S_AS], ns = rec[ABCMB_S_NS];
+    return 2.0 * kPi * kPi / (k * k * k) * As * exp((ns - 1.0) * log(k / kKpivot)) * dm * dm;
+}
+
+// Dense output.  Nodes whose e^-kappa is below kNegligibleWeight (before
+// recombination) enter every source through a factor e^-kappa or g = H nu
+// e^-kappa no larger than ~1e-12 of its peak, so steps pass them freely and
+// their state is interpolated linearly.  Elsewhere a step may pass nodes when
+// the cubic Hermite interpolant on (y, f) at both step ends is accurate to
+// kInterpFrac * rtol: its error is at most (w H)^4 / 384 of a component for
+// solutions varying at rate w, and w is bounded by the streaming frequency
+// k / H_conf plus the rate at which the Thomson coupling changes, |nu'| /
+// max(nu, 1), plus 2 for the background's own evolution, which caps
+// H <= (384 kInterpFrac rtol)^(1/4) / w.  Where the cap is shorter than the
+// distance to the next node, the step lands on that node instead.
+constexpr double kNegligibleWeight = 1e-14;
+constexpr double kInterpFrac = 0.1;
+
+__device__ __forceinline__ double dense_rate(const double *ot, double lna, double nu)
+{
+    int j = (int)((lna - kLna0) * ABCMB_BG_PER_UNIT);
+    j = j < 0 ? 0 : (j > kNlna - 1 ? kNlna - 1 : j);
+    return fabs(ot[kOStride * j + 2 * O_NU + 1]) / fmax(nu, 1.0) + 2.0;
+}
+
 template <int P>
+__device__ __forceinline__ void q_zero(double (&w)[3][P], double (&ws)[4])
+{
+#pragma unroll
+    for (int ch = 0; ch < 3; ch++)
+#pragma unroll
+        for (int p = 0; p < P; p++) w[ch][p] = 0.0;
+#pragma unroll
+    for (int s = 0; s < 4; s++) ws[s] = 0.0;
+}
+
+// the source components of a register vector (lane 0: moments; every lane
+// holds the four scalars) into dst[kSrcComp]
+template <int P>
+__device__ __forceinline__ void q_store_src(double *dst, const double (&v)[3][P], const double (&vs)[4], int q)
+{
+    if (q == 0) {
+        dst[0] = v[0][0];
+        dst[1] = v[0][1];
+        dst[2] = v[0][2];
+        dst[3] = v[1][0];
+        dst[4] = v[1][2];
+        dst[5] = v[2][0];
+        dst[6] = v[2][1];
+        dst[7] = v[2][2];
+#pragma unroll
+        for (int s = 0; s < 4; s++) dst[8 + s] = vs[s];
+    }
+}
+
+__device__ __forceinline__ void q_copy_src(double *dst, const double *src, int q)
+{
+#pragma unroll
+    for (int c = 0; c < 3; c++) dst[q + 4 * c] = src[q + 4 * c];
+}
+
+// the source components of the accepted state (shared memory, quad base
+// column Yq = smw + qb) into dst: lane q copies components q, q + 4, q + 8
+template <int P>
+__device__ __forceinline__ void q_store_y1(double *dst, const double *Yq, int q)
+{
+    dst[q] = Yq[src_elem<P>(q) * 32];
+    dst[q + 4] = Yq[src_elem<P>(q + 4) * 32];
+    dst[8 + q] = Yq[3 * P * 32 + q];
+}
+
+// interpolated source components at fraction th of the step of length H
+template <int P>
+__device__ __forceinline__ void q_dense(double (&v)[kSrcComp], const double *dq, const double *Yq, double th,
+                                        double H, bool hermite)
+{
+    const double um = 1.0 - th;
+    double a0, a1, b0 = 0.0, b1 = 0.0;
+    if (hermite) {
+        a0 = fma(th + th, um * um, um * um); // (1 + 2 th)(1 - th)^2
+        a1 = 1.0 - a0;
+        b0 = H * th * um * um;
+        b1 = -H * th * th * um;
+    } else {
+        a0 = um;
+        a1 = th;
+    }
+#pragma unroll
+    for (int c = 0; c < kSrcComp; c++) {
+        const double y1 = c < 8 ? Yq[src_elem<P>(c) * 32] : Yq[3 * P * 32 + (c - 8)];
+        double r = fma(a0, dq[c], a1 * y1);
+        if (hermite) r = fma(b0, dq[kSrcComp + c], fma(b1, dq[2 * kSrcComp + c], r));
+        v[c] = r;
+    }
+}
+
+// Integrate the modes of one warp (8 per warp, mode index mi for this lane's quad).
+// PK: integrate to ln a = x_out only and write the matter power spectrum
+// there into pk_out[b][k] instead of the sources (S unused).
+template <int P, bool PK = false>
 __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restrict__ bg, long len,
                            const double *__restrict__ kv, const QCoef &qc, double rtol, double atol, int max_steps,
-                           const double sw[3], double *S, int *status, int *steps, double *smw)
+                           const double sw[3], double *S, int *status, int *steps, double *smw, double *dn,
+                           double x_out = 0.0, double *pk_out = nullptr)
 {
     constexpr int E = 3 * P + 1; // chain moments, then one scalar per quad lane
     const int lane = threadIdx.x & 31, q = lane & 3, qb = lane & ~3;
@@ -384,7 +514,7 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
     const double *tab = rec + ABCMB_BG_TABLE;
     const double *ot = rec + ABCMB_BG_ODETAB;
     const double *nodes = rec + ABCMB_BG_NODES;
-    const int n_tau = (int)rec[ABCMB_S_NTAU];
+    const int n_tau = PK ? 1 : (int)rec[ABCMB_S_NTAU];
     QMode md;
     md.k = kv[kidx];
     md.ik = 1.0 / md.k;
@@ -393,7 +523,7 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
     md.c43ik = (4.0 / 3.0) * md.ik;
     md.c15ik = 1.5 * md.ik;
     const double k = md.k;
-    double *Sm = S + ((long)b * Nk + kidx) * (long)n_tau * 3;
+    double *Sm = PK ? nullptr : S + ((long)b * Nk + kidx) * (long)n_tau * 3;
     // shared memory of this lane: element e of vector v at smw[(v E + e) 32 + lane]
     double *sl = smw + lane;
     auto Y = [&](int e) -> double & { return sl[e * 32]; };
@@ -463,25 +593,62 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
         Y(3 * P) = pick4(zs, q);
     }
 
-    double h = 1e-3;
+    // dense output (see kNegligibleWeight): nodes before n_sig carry source weights
+    // below kNegligibleWeight; beyond it a step may pass nodes when the
+    // interpolation cap allows.  This quad's interpolation data in dn:
+    // y0[kSrcComp] f0[kSrcComp] f1[kSrcComp] (lane 0 the chain moments, the
+    // scalars by their owners)
+    double *dq = dn + (lane >> 2) * 3 * kSrcComp;
+    int n_sig = 0;
+    {
+        int lo = 0, hi = n_tau - 1; // first node whose e^-kappa reaches the threshold
+        if (nodes[8 * hi + N_EXPMK] < kNegligibleWeight) lo = hi;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (nodes[8 * mid + N_EXPMK] >= kNegligibleWeight) hi = mid; else lo = mid + 1;
+        }
+        n_sig = lo;
+    }
+    const double x_last = nodes[8 * (n_tau - 1) + N_LNA];
+    const double theta_int = pow(384.0 * kInterpFrac * rtol, 0.25);
+    bool have_y0 = false, have_f0 = false;
+
+    double h = 1e-3, x0 = x;
     while (__any_sync(kFull, !done)) {
         // this quad's step
         bool stepping = !done;
         double xn = x, H = 0.0;
-        bool land = false, emit = false;
+        bool land = false, emit = false, capped = false;
+        int dmode = 0; // 0: none or landing on one node, 1: linear, 2: Hermite dense output
+        const QBg bx = qbg(ot, x, q, qb);
         if (stepping) {
-            xn = nodes[8 * node + N_LNA];
+            xn = PK ? x_out : nodes[8 * node + N_LNA];
             H = h;
-            if (x + H >= xn) { H = xn - x; land = true; }
-            if (H <= 0.0) { emit = true; stepping = false; }
+            if (PK && x + H >= xn) { H = xn - x; land = true; }
+            else if (x + H >= xn) {
+                if (node < n_sig) {
+                    const double xs = nodes[8 * n_sig + N_LNA];
+                    if (x + H >= xs) { H = xs - x; capped = true; }
+                    dmode = 1;
+                } else {
+                    const double cap = theta_int * recip(fma(k, bx.ih, dense_rate(ot, x, bx.nu)));
+                    if (x + cap < xn) { H = xn - x; land = true; }
+                    else {
+                        if (cap < H) { H = cap; capped = true; }
+                        if (x + H > x_last) { H = x_last - x; capped = true; }
+                        dmode = 2;
+                    }
+                }
+            }
+            if (H <= 0.0) { emit = true; stepping = false; dmode = 0; }
             else if (++nsteps > max_steps) { stat = ABCMB_E_MAX_STEPS; done = true; stepping = false; }
-            else if (H < 1e-13 && !land) { stat = ABCMB_E_NONFINITE; done = true; stepping = false; }
+            else if (H < 1e-13 && !land && !capped) { stat = ABCMB_E_NONFINITE; done = true; stepping = false; }
         }
         const bool gbs = __all_sync(kFull, !stepping || x >= x_ns);
         // inverse error scales from the state at the step start; moments slaved
         // to the tight coupling (photon l >= 2, all of G while H/(H tau_c) >
         // kSlavedHnu in the implicit regime) and padding moments get zero
-        const bool excl = !gbs && H * qbg(ot, x, q, qb).nu > kSlavedHnu;
+        const bool excl = !gbs && H * bx.nu > kSlavedHnu;
         // the inverse scales occupy the last tableau column's slot, which is
         // written only by the last column, after its element's scale was read
         {
@@ -510,6 +677,21 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
                     const double sc = fma(rtol, fmax(fabs(z[ch][p]), ch < 2 ? fl2 : fl3), atol);
                     T(kQK - 1, ch * P + p) = off ? 0.0 : rcp_approx(sc);
                 }
+        }
+        // interpolation data at the step start (z, zs hold the state here)
+        {
+            const bool need_f = stepping && dmode == 2 && !have_f0;
+            if (__any_sync(kFull, need_f)) {
+                q_zero<P>(w, ws);
+                q_rhs_axpy<P>(z, zs, w, ws, bx, md, 1.0, q, qb, qc);
+                if (need_f) {
+                    q_store_src<P>(dq + kSrcComp, w, ws, q);
+                    nsub++;
+                }
+            }
+            if (stepping && dmode >= 1 && !have_y0) q_store_src<P>(dq, z, zs, q);
+            have_y0 |= stepping && dmode >= 1;
+            have_f0 |= need_f;
         }
         int jacc = 0;
         double err = 0.0;
@@ -607,30 +789,85 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
             jacc = -1;
         }
         if (stepping && jacc > 0) {
+            x0 = x;
             x = land ? xn : x + H;
             const int ord = gbs ? 2 * jacc - 1 : jacc;
             double fac = err > 0.0 ? 0.9 * (double)__powf((float)err, -1.0f / ord) : 4.0;
             if (jacc < kQK - 1) fac *= 1.5;
             fac = fmin(4.0, fmax(0.2, fac));
             const double hn = H * fac;
-            h = land ? fmax(h, hn) : hn;
+            h = (land || capped) ? fmax(h, hn) : hn;
             if (land) emit = true;
         } else if (stepping && jacc == 0) {
             const int ord = gbs ? 2 * kQK - 1 : kQK;
             h = H * fmin(0.9, fmax(0.1, 0.9 * (double)__powf((float)err, -1.0f / ord)));
         }
+        // dense output of the nodes in (x0, x]
+        bool pend = stepping && jacc > 0 && dmode >= 1;
+        if (__any_sync(kFull, pend && dmode == 2)) {
+            // f1 at the step end
+#pragma unroll
+            for (int ch = 0; ch < 3; ch++)
+#pragma unroll
+                for (int p = 0; p < P; p++) z[ch][p] = Y(ch * P + p);
+            load_scalars(zs, Y(3 * P), qb);
+            q_zero<P>(w, ws);
+            q_rhs_axpy<P>(z, zs, w, ws, qbg(ot, x, q, qb), md, 1.0, q, qb, qc);
+            if (pend && dmode == 2) {
+                q_store_src<P>(dq + 2 * kSrcComp, w, ws, q);
+                nsub++;
+            }
+        }
+        if (__any_sync(kFull, pend)) {
+            __syncwarp();
+            const double iH = pend ? recip(x - x0) : 0.0;
+            while (__any_sync(kFull, pend)) {
+                const int i = node + q;
+                const bool mine = pend && i < n_tau && nodes[8 * i + N_LNA] <= x;
+                if (mine) {
+                    const double th = fmin((nodes[8 * i + N_LNA] - x0) * iH, 1.0);
+                    double v[kSrcComp];
+                    q_dense<P>(v, dq, smw + qb, th, x - x0, dmode == 2);
+                    q_sources_v(ot, nodes + 8 * i, k, sw, v, Sm + 3 * i);
+                }
+                const int cnt = __popc((__ballot_sync(kFull, mine) >> qb) & 0xFu);
+                if (pend) {
+                    node += cnt;
+                    if (node >= n_tau) done = true;
+                    if (cnt < 4 || done) pend = false;
+                }
+            }
+            __syncwarp();
+        }
+        if (stepping && jacc > 0) {
+            // the step end is the next step's start
+            if (dmode >= 1) {
+                if (dmode == 2) q_copy_src(dq + kSrcComp, dq + 2 * kSrcComp, q);
+                q_store_y1<P>(dq, smw + qb, q);
+            }
+            have_y0 = dmode >= 1;
+            have_f0 = dmode == 2;
+        }
+        __syncwarp();
         if (__any_sync(kFull, emit)) {
             double sc[4];
             load_scalars(sc, Y(3 * P), qb); // the accepted scalars, one per quad lane
             if (emit) {
-                if (q == 0) q_sources(ot, nodes + 8 * node, k, sw, sl, sc, P, Sm + 3 * node);
+                if (q == 0) {
+                    if (PK) pk_out[(long)b * Nk + kidx] = q_matter_pk(ot, rec, x_out, k, sc);
+                    else q_sources<P>(ot, nodes + 8 * node, k, sw, sl, sc, Sm + 3 * node);
+                }
                 node++;
                 if (node >= n_tau) done = true;
             }
         }
     }
     if (valid && q == 0) {
-        for (int n = node; n < n_tau; n++) Sm[3 * n] = Sm[3 * n + 1] = Sm[3 * n + 2] = 0.0;
+        if (PK) {
+            if (node < 1) pk_out[(long)b * Nk + kidx] = nan("");
+        } else {
+            for (int n = node; n < n_tau; n++) Sm[3 * n] = Sm[3 * n + 1] = Sm[3 * n + 2] = 0.0;
+        }
         status[(long)b * Nk + kidx] = stat;
         if (steps) {
             steps[2 * ((long)b * Nk + kidx)] = nsteps;
@@ -640,11 +877,12 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
 }
 
 // Dynamic shared memory of one warp: the accepted state and the K tableau
-// columns, (1 + K) (3P + 4) doubles per lane.
+// columns, (1 + K) (3P + 1) doubles per lane, then the 8 quads' dense-output
+// data, 3 kSrcComp doubles each.
 template <int P>
 constexpr size_t quad_smem_per_warp()
 {
-    return (size_t)(1 + kQK) * (3 * P + 1) * 32 * sizeof(double);
+    return ((size_t)(1 + kQK) * (3 * P + 1) * 32 + 8 * 3 * kSrcComp) * sizeof(double);
 }
 
 template <int P, int W>
@@ -674,8 +912,42 @@ perturb_quad_kernel(int B, int Nk, const double *__restrict__ bg, long len, cons
     qc.L[2] = Ln;
     for (int c = 0; c < 3; c++) qc.L1[c] = qc.L[c] + 1.0;
     const double sw[3] = {s_sw, s_isw, s_dop};
-    double *smw = qsm + (long)warp * (1 + kQK) * E * 32;
-    quad_modes<P>(mi, M, B, Nk, bg, len, kv, qc, rtol, atol, max_steps, sw, S, status, steps, smw);
+    double *smw = qsm + (long)warp * ((1 + kQK) * E * 32 + 8 * 3 * kSrcComp);
+    quad_modes<P>(mi, M, B, Nk, bg, len, kv, qc, rtol, atol, max_steps, sw, S, status, steps, smw,
+                  smw + (1 + kQK) * E * 32);
+}
+
+// Matter power spectrum at ln a = x_out for every (cosmology, k) mode: the
+// perturbation ODE alone, with no tau nodes to land on.
+template <int P>
+__global__ void __launch_bounds__(32)
+pk_quad_kernel(int B, int Nk, const double *__restrict__ bg, long len, const double *__restrict__ kv, int Lg,
+               int Lp, int Ln, double rtol, double atol, int max_steps, double x_out, double *Pk, int *status,
+               int *steps)
+{
+    extern __shared__ double qsm[];
+    __shared__ double cA[3 * 64], cB[3 * 64];
+    const int Ls[3] = {Lg, Lp, Ln};
+    for (int i = threadIdx.x; i < 3 * 64; i += blockDim.x) {
+        const int ch = i / 64, l = i % 64, L = Ls[ch];
+        cA[i] = l < L ? (double)l / (2.0 * l + 1.0) : (l == L ? 1.0 : 0.0);
+        cB[i] = l < L ? (l + 1.0) / (2.0 * l + 1.0) : 0.0;
+    }
+    __syncthreads();
+    constexpr int E = 3 * P + 1;
+    const int lane = threadIdx.x & 31;
+    const long M = (long)B * Nk;
+    const long mi = (long)blockIdx.x * 8 + (lane >> 2);
+    QCoef qc;
+    qc.A = cA;
+    qc.Bc = cB;
+    qc.L[0] = Lg;
+    qc.L[1] = Lp;
+    qc.L[2] = Ln;
+    for (int c = 0; c < 3; c++) qc.L1[c] = qc.L[c] + 1.0;
+    const double sw[3] = {0.0, 0.0, 0.0};
+    quad_modes<P, true>(mi, M, B, Nk, bg, len, kv, qc, rtol, atol, max_steps, sw, nullptr, status, steps, qsm,
+                        qsm + (1 + kQK) * E * 32, x_out, Pk);
 }
 
 } // namespace abcmb

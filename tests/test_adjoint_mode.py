@@ -106,3 +106,33 @@ def test_mode_gradient_against_finite_differences(H, rec, k, node):
                     checked += 1
                     break
     assert checked >= 4
+
+
+@pytest.mark.parametrize("k,node", [(0.02, 80), (0.003, 100)])
+def test_node_position_gradient(H, rec, k, node):
+    # a node's ln a moves the sources there with the ODE flow and the
+    # background's slope; later nodes are unaffected up to the integration error
+    n_tau, L, rtol = 120, 8, 1e-9
+    rng = np.random.default_rng(7 + node)
+    Sb = rng.normal(size=(n_tau, 3))
+
+    def phi(r):
+        S, acc = np.zeros((n_tau, 3)), ctypes.c_int()
+        assert H.h_fwd(ptr(r), k, L, rtol, ptr(S), ctypes.byref(acc)) == 0
+        return (Sb * S).sum(), acc.value
+
+    _, acc0 = phi(rec)
+    rb = np.zeros_like(rec)
+    assert H.h_grad(ptr(rec), k, L, rtol, ptr(Sb), ptr(rb)) == 0
+    e = 64 + 28 * 18433 + 8 * node  # the node's ln a
+    for hr in (1e-8, 3e-9, 1e-9):
+        h = hr * abs(rec[e])
+        rp, rm = rec.copy(), rec.copy()
+        rp[e] += h
+        rm[e] -= h
+        (fp, ap), (fm, am) = phi(rp), phi(rm)
+        if ap == am == acc0:
+            fd = (fp - fm) / (2 * h)
+            assert abs(rb[e] - fd) <= 2e-3 * abs(fd), (rb[e], fd)
+            return
+    pytest.fail("no step size kept the accepted steps fixed")
