@@ -184,6 +184,67 @@ def pk(params, k, z, o, nthreads=0):
     return out
 
 
+# Transfer-function k grid (App. A.1, eq. k_transfer_spacing and eq. defkperiod)
+# with the paper's default parameters.
+TRANSFER_GRID = dict(tau0_fid=1.418668e4, tau_rec_fid=281.040565, linstep=0.45, logstep=170.0,
+                     kmin_tau0=0.1, kmax_tau0_over_lmax=1.8)
+
+
+def transfer_k_grid(lmax_cl, tau0_fid=1.418668e4, tau_rec_fid=281.040565, linstep=0.45, logstep=170.0,
+                    kmin_tau0=0.1, kmax_tau0_over_lmax=1.8):
+    """k~ nodes from k_min = kmin_tau0 / tau0_fid up to the last node not above
+    k_max = kmax_tau0_over_lmax * lmax_cl / tau0_fid (reading of eq. kmax_grid:
+    k_max tau0 / lmax = 1.8), each step
+    k_{n+1} = k_n + k_period linstep k_n / (k_n + linstep / logstep),
+    k_period = 2 pi / (tau0_fid - tau_rec_fid)."""
+    kp = 2.0 * np.pi / (tau0_fid - tau_rec_fid)
+    k = kmin_tau0 / tau0_fid
+    kmax = kmax_tau0_over_lmax * lmax_cl / tau0_fid
+    out = []
+    while k <= kmax:
+        out.append(k)
+        k = k + kp * linstep * k / (k + linstep / logstep)
+    return np.array(out)
+
+
+def interp_sources(S, k, kt):
+    """Sources S[..., n_k, n_tau, 3] on the ascending nodes k, interpolated in
+    ln k onto kt (within [k_0, k_last]) by piecewise cubic Hermite
+    polynomials whose slopes at the nodes are the three-point derivatives
+    (centred, one-sided at the ends) -- exact for quadratics in ln k.  The
+    paper interpolates the sources onto its transfer grid without naming the
+    scheme; this is the reading taken."""
+    S = np.asarray(S, dtype=np.float64)
+    x = np.log(np.asarray(k, dtype=np.float64))
+    xt = np.log(np.asarray(kt, dtype=np.float64))
+    n = x.size
+    ax = S.ndim - 3  # the k axis
+    Sk = np.moveaxis(S, ax, 0)
+    slope = np.empty_like(Sk)
+    for i in range(n):
+        if i == 0:
+            a, b, c = 0, 1, 2
+        elif i == n - 1:
+            a, b, c = n - 3, n - 2, n - 1
+        else:
+            a, b, c = i - 1, i, i + 1
+        # derivative at x_i of the parabola through (x_a, x_b, x_c)
+        xa, xb, xc, xi = x[a], x[b], x[c], x[i]
+        la = ((xi - xb) + (xi - xc)) / ((xa - xb) * (xa - xc))
+        lb = ((xi - xa) + (xi - xc)) / ((xb - xa) * (xb - xc))
+        lc = ((xi - xa) + (xi - xb)) / ((xc - xa) * (xc - xb))
+        slope[i] = la * Sk[a] + lb * Sk[b] + lc * Sk[c]
+    out = np.empty((xt.size,) + Sk.shape[1:])
+    for j, xv in enumerate(xt):
+        i = min(max(np.searchsorted(x, xv, side="right") - 1, 0), n - 2)
+        h = x[i + 1] - x[i]
+        t = (xv - x[i]) / h
+        h00, h10 = (1 + 2 * t) * (1 - t) ** 2, t * (1 - t) ** 2
+        h01, h11 = t * t * (3 - 2 * t), t * t * (t - 1)
+        out[j] = h00 * Sk[i] + h10 * h * slope[i] + h01 * Sk[i + 1] + h11 * h * slope[i + 1]
+    return np.moveaxis(out, 0, ax)
+
+
 class Cosmo:
     """Handle on one oracle cosmology (background built once)."""
 

@@ -451,3 +451,45 @@ def test_pk_primordial_dependence_is_exact(small_params):
     q[4] += 0.1
     Q = O.pk(q, k, 0.0, o)
     np.testing.assert_allclose(Q / P, np.exp(0.1) * (k / 0.05) ** 0.02, rtol=1e-11)
+
+
+# ---- transfer k grid and source interpolation (App. A.1 eq. k_transfer_spacing) ----
+
+def test_transfer_grid_limits():
+    # logarithmic steps of 2 pi logstep / (tau0 - tau_rec) at small k, linear
+    # steps of 2 pi linstep / (tau0 - tau_rec) at large k, from 0.1 / tau0 to
+    # the last node below 1.8 l_max / tau0
+    tau0, trec = 1.418668e4, 281.040565
+    k = O.transfer_k_grid(2500)
+    assert abs(k[0] * tau0 - 0.1) < 1e-12
+    assert k[-1] <= 1.8 * 2500 / tau0 < k[-1] + 2.1e-4
+    dlog = np.diff(np.log(k[:3]))
+    # (the step falls short of the limit by k logstep / linstep ~ 3e-3 at k_0)
+    np.testing.assert_allclose(dlog, np.log1p(2 * np.pi * 170 / (tau0 - trec)), rtol=5e-3)
+    np.testing.assert_allclose(np.diff(k[-3:]), 2 * np.pi * 0.45 / (tau0 - trec), rtol=2e-2)
+    assert np.all(np.diff(k) > 0)
+
+
+def test_source_interpolation_exact_for_quadratics_in_lnk():
+    rng = np.random.default_rng(3)
+    k = np.sort(np.exp(rng.uniform(np.log(1e-5), np.log(0.5), 60)))
+    x = np.log(k)
+    coef = rng.normal(size=(3, 7, 3))
+    S = coef[0] + coef[1] * x[:, None, None] + coef[2] * x[:, None, None] ** 2  # [n_k, 7, 3]
+    kt = np.exp(rng.uniform(np.log(k[0]), np.log(k[-1]), 40))
+    xt = np.log(kt)
+    ref = coef[0] + coef[1] * xt[:, None, None] + coef[2] * xt[:, None, None] ** 2
+    np.testing.assert_allclose(O.interp_sources(S, k, kt), ref, rtol=1e-10, atol=1e-10)
+    # and at the nodes it returns the data
+    np.testing.assert_allclose(O.interp_sources(S, k, k), S, rtol=0, atol=1e-13)
+
+
+def test_source_interpolation_converges_at_third_order():
+    # smooth oscillation in k: halving the node spacing cuts the error ~8-16x
+    f = lambda k: np.cos(40.0 * np.log(k))[:, None, None] * np.ones((1, 2, 3))
+    kt = np.exp(np.linspace(np.log(1e-3), np.log(0.3), 333))
+    errs = []
+    for n in (200, 400, 800):
+        k = np.exp(np.linspace(np.log(1e-3), np.log(0.3), n))
+        errs.append(np.abs(O.interp_sources(f(k), k, kt) - f(kt)).max())
+    assert errs[0] / errs[1] > 7 and errs[1] / errs[2] > 7, errs
