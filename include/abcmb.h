@@ -236,6 +236,31 @@ int abcmb_cl(int B, const double *bg, const double *Delta, const double *k, int 
              const abcmb_options *o, double *Cl, void *stream);
 
 /*
+ * Projection onto another k grid (App. A.1 transfer grid, eq.
+ * k_transfer_spacing): abcmb_project at the wavenumbers kt, with each
+ * tau node's sources interpolated from the ODE nodes k by piecewise cubic
+ * Hermite polynomials in ln k whose slopes are three-point derivatives
+ * (centred, one-sided at the ends; exact for quadratics in ln k; outside
+ * [k_0, k_{Nk-1}] the end intervals' cubics extend).
+ *
+ *   S      [B][Nk][n_tau][3]        device, read (sources at k, as from abcmb_perturb)
+ *   k      [Nk], Nk >= 4            device, read, strictly ascending
+ *   kt     [Nkt]                    device, read
+ *   Delta  [B][Nkt][lmax_cl-1][2]   device, written
+ * abcmb_cl on (Delta, kt) then gives C_l on the transfer grid.
+ */
+int abcmb_project_interp(int B, const double *bg, const double *S, const double *k, int Nk, const double *kt,
+                         int Nkt, const abcmb_options *o, double *Delta, void *stream);
+
+/* The transfer grid for lmax_cl (host function; the paper's defaults):
+   from 0.1 / tau0_fid while k tau0_fid <= 1.8 lmax_cl,
+   k_{n+1} = k_n + k_period 0.45 k_n / (k_n + 0.45 / 170),
+   k_period = 2 pi / (tau0_fid - tau_rec_fid), tau0_fid = 14186.68 Mpc,
+   tau_rec_fid = 281.040565 Mpc.  Writes min(count, cap) nodes to k_host (may
+   be NULL) and returns the count; -1 for lmax_cl outside 2..5000. */
+int abcmb_transfer_k_grid(int lmax_cl, double *k_host, int cap);
+
+/*
  * Mixed precision (the FP32 form of the two calls above; the sources stay
  * FP64): same projection and k-quadrature, with every (node, l) product and
  * the in-warp sums in FP32 and the sums over tau-node groups and over k

@@ -83,6 +83,8 @@ def lib():
         L.abcmb_perturb_noalloc.argtypes = [ctypes.c_int, _P, _P, ctypes.c_int, O, _P, _P, _P, _P]
         L.abcmb_matter_pk.argtypes = [ctypes.c_int, _P, _P, ctypes.c_int, O, ctypes.c_double, _P, _P, _P]
         L.abcmb_project.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, O, _P, _P]
+        L.abcmb_project_interp.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, _P, ctypes.c_int, O, _P, _P]
+        L.abcmb_transfer_k_grid.argtypes = [ctypes.c_int, _P, ctypes.c_int]
         L.abcmb_cl.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, O, _P, _P]
         L.abcmb_project_mixed.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, O, _P, _P]
         L.abcmb_cl_mixed.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, O, _P, _P]
@@ -206,6 +208,29 @@ def abcmb_project(bg: torch.Tensor, S: torch.Tensor, k: torch.Tensor, o: Options
     _check(lib().abcmb_project(B, _ptr(bg), _ptr(S), _ptr(k), Nk, ctypes.byref(o), _ptr(D), _stream()),
            "abcmb_project")
     return D
+
+
+def abcmb_project_interp(bg: torch.Tensor, S: torch.Tensor, k: torch.Tensor, kt: torch.Tensor, o: Options,
+                         out=None):
+    """Sources S at the ODE nodes k -> Delta [B, len(kt), lmax_cl - 1, 2] at kt."""
+    _dev(bg), _dev(S), _dev(k), _dev(kt)
+    B, Nk, Nkt = bg.shape[0], k.shape[0], kt.shape[0]
+    D = out if out is not None else torch.empty((B, Nkt, o.lmax_cl - 1, 2), dtype=torch.float64,
+                                                device=bg.device)
+    _check(lib().abcmb_project_interp(B, _ptr(bg), _ptr(S), _ptr(k), Nk, _ptr(kt), Nkt, ctypes.byref(o), _ptr(D),
+                                      _stream()),
+           "abcmb_project_interp")
+    return D
+
+
+def transfer_k_grid(lmax_cl: int) -> np.ndarray:
+    """The transfer-function k grid for lmax_cl (host)."""
+    n = lib().abcmb_transfer_k_grid(int(lmax_cl), None, 0)
+    if n < 0:
+        raise ValueError("lmax_cl out of range")
+    out = np.empty(n)
+    lib().abcmb_transfer_k_grid(int(lmax_cl), out.ctypes.data_as(ctypes.c_void_p), n)
+    return out
 
 
 def abcmb_cl(bg: torch.Tensor, Delta: torch.Tensor, k: torch.Tensor, o: Options, out=None):

@@ -75,10 +75,47 @@ __device__ __forceinline__ void butterfly_stage(double *v, int lane)
     }
 }
 
+// Cubic Hermite interpolation in ln k of the sources at kk from the nodes
+// kn[0..n), n >= 4, slopes from three-point derivatives (centred, one-sided at
+// the ends): S(kk) = sum_m w[m] S(kn[r0 + m]), m < 4.  Outside the nodes the
+// end intervals' cubics extend.
+__device__ void interp_weights(const double *__restrict__ kn, int n, double kk, int *r0_out, double w[4])
+{
+    const double xv = log(kk);
+    int lo = 0, hi = n - 1; // interval i: kn[i] <= kk < kn[i + 1], clamped to [0, n - 2]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (kn[mid] <= kk) lo = mid; else hi = mid;
+    }
+    const int i = lo;
+    const int r0 = i - 1 < 0 ? 0 : (i - 1 > n - 4 ? n - 4 : i - 1);
+    for (int m = 0; m < 4; m++) w[m] = 0.0;
+    const double xi = log(kn[i]), xj = log(kn[i + 1]), h = xj - xi, t = (xv - xi) / h;
+    const double h00 = (1.0 + 2.0 * t) * (1.0 - t) * (1.0 - t), h10 = t * (1.0 - t) * (1.0 - t);
+    const double h01 = t * t * (3.0 - 2.0 * t), h11 = t * t * (t - 1.0);
+    w[i - r0] += h00;
+    w[i + 1 - r0] += h01;
+    // slope at node p: derivative of the parabola through three neighbours
+    for (int side = 0; side < 2; side++) {
+        const int p = i + side;
+        const double c = (side == 0 ? h10 : h11) * h;
+        const int a = p == 0 ? 0 : (p == n - 1 ? n - 3 : p - 1);
+        const double xa = log(kn[a]), xb = log(kn[a + 1]), xc = log(kn[a + 2]), xp = log(kn[p]);
+        w[a - r0] += c * ((xp - xb) + (xp - xc)) / ((xa - xb) * (xa - xc));
+        w[a + 1 - r0] += c * ((xp - xa) + (xp - xc)) / ((xb - xa) * (xb - xc));
+        w[a + 2 - r0] += c * ((xp - xa) + (xp - xb)) / ((xc - xa) * (xc - xb));
+    }
+    *r0_out = r0;
+}
+
+// INTERP: the transfer functions at the wavenumbers kv[0..Nk) from sources
+// given at the ODE nodes kode[0..Nko) (S[B][Nko][n_tau][3]), interpolated per
+// node in ln k (interp_weights); otherwise S is given at kv itself.
+template <bool INTERP>
 __global__ void __launch_bounds__(128)
 project_kernel(int B, int Nk, const double *__restrict__ bg, long bg_len,
                const double *__restrict__ S, const double *__restrict__ kv, int lmax,
-               double scale_pol, double *__restrict__ Delta)
+               double scale_pol, double *__restrict__ Delta, const double *__restrict__ kode, int Nko)
 {
     extern __shared__ double acc[]; // [lmax - 1][2]
     const int nl = lmax - 1;
@@ -89,8 +126,18 @@ project_kernel(int B, int Nk, const double *__restrict__ bg, long bg_len,
     const int n_tau = (int)rec[ABCMB_S_NTAU];
     const double tau0 = rec[ABCMB_S_TAU0];
     const double *nodes = rec + ABCMB_BG_NODES;
-    const double *Sm = S + ((long)b * Nk + kidx) * (long)n_tau * 3;
     const double kk = kv[kidx];
+    const double *Sm;
+    int r0 = 0;
+    double wi[4] = {0.0, 0.0, 0.0, 0.0};
+    long rs = 0; // element stride between consecutive source rows
+    if (INTERP) {
+        interp_weights(kode, Nko, kk, &r0, wi);
+        Sm = S + ((long)b * Nko + r0) * (long)n_tau * 3;
+        rs = (long)n_tau * 3;
+    } else {
+        Sm = S + ((long)b * Nk + kidx) * (long)n_tau * 3;
+    }
     __shared__ double ser[8 * kSerL];
     for (int i = threadIdx.x; i < 2 * nl; i += blockDim.x) acc[i] = 0.0;
     for (int i = threadIdx.x; i < 8 * kSerL; i += blockDim.x) {
@@ -118,7 +165,21 @@ project_kernel(int B, int Nk, const double *__restrict__ bg, long bg_len,
                 const double w = nd[N_W];
                 const double x = kk * (tau0 - nd[N_TAU]);
                 const double u = 1.0 / x;
-                const double s0 = Sm[3 * i], s1 = Sm[3 * i + 1], sp = Sm[3 * i + 2];
+                double s0, s1, sp;
+                if (INTERP) {
+                    s0 = s1 = sp = 0.0;
+#pragma unroll
+                    for (int r = 0; r < 4; r++) {
+                        const double *Sr = Sm + r * rs + 3 * i;
+                        s0 = fma(wi[r], Sr[0], s0);
+                        s1 = fma(wi[r], Sr[1], s1);
+                        sp = fma(wi[r], Sr[2], sp);
+                    }
+                } else {
+                    s0 = Sm[3 * i];
+                    s1 = Sm[3 * i + 1];
+                    sp = Sm[3 * i + 2];
+                }
                 const double s2 = scale_pol * sp;
                 const double g1 = s1 - 3.0 * u * s2;
                 const double u2 = u * u;
@@ -274,14 +335,51 @@ extern "C" int abcmb_project(int B, const double *bg, const double *S, const dou
     const size_t smem = (size_t)nl * 2 * sizeof(double);
     if (smem > 200 * 1024) return ABCMB_E_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    const long avail = abcmb::smem_optin((const void *)abcmb::project_kernel);
+    const long avail = abcmb::smem_optin((const void *)abcmb::project_kernel<false>);
     if (avail < 0) return ABCMB_E_CUDA;
     if ((long)smem > avail) return ABCMB_E_INVALID_ARG;
     long nblk = (long)B * Nk;
     if (nblk > 2147483647L) return ABCMB_E_INVALID_ARG;
-    abcmb::project_kernel<<<(unsigned)nblk, 128, smem, st>>>(B, Nk, bg, len, S, k, o->lmax_cl,
-                                                              o->scale_pol, Delta);
+    abcmb::project_kernel<false><<<(unsigned)nblk, 128, smem, st>>>(B, Nk, bg, len, S, k, o->lmax_cl,
+                                                                     o->scale_pol, Delta, nullptr, 0);
     return cudaGetLastError() == cudaSuccess ? ABCMB_OK : ABCMB_E_CUDA;
+}
+
+extern "C" int abcmb_project_interp(int B, const double *bg, const double *S, const double *k, int Nk,
+                                    const double *kt, int Nkt, const abcmb_options *o, double *Delta, void *stream)
+{
+    if (B < 1 || Nk < 4 || Nkt < 1 || !bg || !S || !k || !kt || !Delta || abcmb_validate_options(o) != ABCMB_OK)
+        return ABCMB_E_INVALID_ARG;
+    const long len = (long)abcmb_bg_doubles(o);
+    const int nl = o->lmax_cl - 1;
+    const size_t smem = (size_t)nl * 2 * sizeof(double);
+    if (smem > 200 * 1024) return ABCMB_E_INVALID_ARG;
+    const long avail = abcmb::smem_optin((const void *)abcmb::project_kernel<true>);
+    if (avail < 0) return ABCMB_E_CUDA;
+    if ((long)smem > avail) return ABCMB_E_INVALID_ARG;
+    const long nblk = (long)B * Nkt;
+    if (nblk > 2147483647L) return ABCMB_E_INVALID_ARG;
+    abcmb::project_kernel<true><<<(unsigned)nblk, 128, smem, (cudaStream_t)stream>>>(
+        B, Nkt, bg, len, S, kt, o->lmax_cl, o->scale_pol, Delta, k, Nk);
+    return cudaGetLastError() == cudaSuccess ? ABCMB_OK : ABCMB_E_CUDA;
+}
+
+// Transfer-function wavenumbers (App. A.1, eq. k_transfer_spacing and eq.
+// defkperiod, the paper's default parameters): from 0.1 / tau0_fid while
+// k tau0_fid <= 1.8 lmax_cl, k_{n+1} = k_n + k_period 0.45 k_n / (k_n + 0.45 / 170),
+// k_period = 2 pi / (tau0_fid - tau_rec_fid).
+extern "C" int abcmb_transfer_k_grid(int lmax_cl, double *k_host, int cap)
+{
+    if (lmax_cl < 2 || lmax_cl > 5000) return -1;
+    const double tau0 = 1.418668e4, trec = 281.040565, lin = 0.45, logs = 170.0;
+    const double kp = 2.0 * 3.141592653589793 / (tau0 - trec);
+    const double kmax = 1.8 * lmax_cl / tau0;
+    int n = 0;
+    for (double kk = 0.1 / tau0; kk <= kmax; kk += kp * lin * kk / (kk + lin / logs)) {
+        if (k_host && n < cap) k_host[n] = kk;
+        n++;
+    }
+    return n;
 }
 
 extern "C" int abcmb_cl(int B, const double *bg, const double *Delta, const double *k, int Nk,

@@ -68,6 +68,23 @@ def synthetic_sources(n_k: int, n_tau: int, seed: int) -> np.ndarray:
     return out
 
 
+def synthetic_sources_smooth(k: np.ndarray, n_tau: int, seed: int) -> np.ndarray:
+    """Seeded source arrays S[len(k)][n_tau][3] that vary smoothly with k
+    (a recombination-like peak in the node index with a phase k r, r drawn per
+    component, plus a weak late tail): inputs for interpolation in k."""
+    rng = np.random.default_rng(seed)
+    i = np.arange(n_tau) / n_tau
+    k = np.asarray(k, dtype=np.float64)
+    out = np.empty((k.size, n_tau, 3))
+    peak = np.exp(-0.5 * ((i - 0.45) / 0.08) ** 2)
+    tail = 0.05 * np.exp(-((i - 0.9) / 0.1) ** 2)
+    for c in range(3):
+        amp, ph, r = rng.uniform(0.5, 1.5), rng.uniform(0, 2 * np.pi), rng.uniform(50.0, 150.0)
+        out[:, :, c] = amp * (peak[None, :] * np.cos(k[:, None] * r * (1.0 + i[None, :]) + ph)
+                              + tail[None, :]) * 10.0 ** (-c)
+    return out
+
+
 @dataclass(frozen=True)
 class Workload:
     """One named configuration of the hot path."""
