@@ -1,5 +1,7 @@
-// Discrete adjoint of the perturbation step, one thread per (cosmology, k)
-// mode (host+device; the GPU kernels in abcmb_grad.cu call these per mode).
+// Discrete adjoint of the perturbation step, one warp per (cosmology, k) mode
+// (host+device; on the host one lane does everything; the GPU kernels in
+// abcmb_grad.cu call these per mode, the 32 lanes sharing the state vectors'
+// elements, see ln_id in abcmb_adjoint_ops.cuh).
 //
 // Forward (fwd_taped): the extrapolated IMEX / Gragg integrator of
 // abcmb_ode.cuh on the ODE-table background, landing on every tau node and
@@ -48,11 +50,11 @@ enum {
 };
 
 struct ModeBufs {
-    double *work; // [V_COUNT][N] strided by M
-    double *seg;  // [kSeg + 1][N] strided by M
-    double *ckpt; // [kTapeCap / kSeg + 1][N] strided by M
-    double *tape; // [kTapeCap][3]: x, H, J | gbs << 8 | land << 9 (per mode, contiguous)
-    long stride;  // M (modes)
+    double *work; // [V_COUNT][N]
+    double *seg;  // [kSeg + 1][N]
+    double *ckpt; // [kTapeCap / kSeg + 1][N]
+    double *tape; // [kTapeCap][3]: x, H, J | gbs << 8 | land << 9
+    long stride;  // element stride of the vectors (1: each mode's vectors contiguous)
 };
 
 ABCMB_HD Vec wv(const ModeBufs &m, const OdeDims &d, int v) { return Vec{m.work + (long)v * d.N * m.stride, m.stride}; }
@@ -61,11 +63,13 @@ ABCMB_HD Vec ckv(const ModeBufs &m, const OdeDims &d, int c) { return Vec{m.ckpt
 
 ABCMB_HD void vcopy(const OdeDims &d, Vec a, Vec b)
 {
-    for (int i = 0; i < d.N; i++) b[i] = a[i];
+    for (int i = ln_id(); i < d.N; i += ln_n()) b[i] = a[i];
+    ln_sync();
 }
 ABCMB_HD void vzero(const OdeDims &d, Vec a)
 {
-    for (int i = 0; i < d.N; i++) a[i] = 0.0;
+    for (int i = ln_id(); i < d.N; i += ln_n()) a[i] = 0.0;
+    ln_sync();
 }
 
 // Lagrange weight of column i in T_{J,J-1}: IMEX nodes h ~ 1/i, Gragg nodes h^2 ~ 1/i^2
@@ -150,7 +154,7 @@ ABCMB_HD void column(const ModeCtx &c, const ModeBufs &mb, double x, double H, i
 // V_T[s] = T_{j,s}, s < j (IMEX: nodes h ~ 1/j, Gragg: h^2 ~ 1/j^2)
 ABCMB_HD void neville(const OdeDims &d, const ModeBufs &mb, Vec raw, int j, bool gbs)
 {
-    for (int i = 0; i < d.N; i++) {
+    for (int i = ln_id(); i < d.N; i += ln_n()) {
         double cur = raw[i], prev = wv(mb, d, V_T)[i];
         wv(mb, d, V_T)[i] = cur;
         for (int s = 1; s < j; s++) {
@@ -162,6 +166,7 @@ ABCMB_HD void neville(const OdeDims &d, const ModeBufs &mb, Vec raw, int j, bool
             cur = nw;
         }
     }
+    ln_sync();
 }
 
 // the accepted value T_{J,J-1} of a step with J columns, into out
@@ -179,6 +184,18 @@ ABCMB_HD void step_value(const ModeCtx &c, const ModeBufs &mb, double x, double 
 struct FwdResult {
     int status, steps, accepted, emit0;
 };
+
+// the sources at node n from state y, written by lane 0 into S[3 n ..]
+ABCMB_HD void emit_sources(const ModeCtx &c, int n, Vec y, double *S)
+{
+    double s3[3];
+    sources_fwd(c.d, c.k, bg_at(c, c.nodes[8 * n + N_LNA]), node_at(c, n), c.sw, y, s3);
+    if (ln_id() == 0) {
+        S[3 * n] = s3[0];
+        S[3 * n + 1] = s3[1];
+        S[3 * n + 2] = s3[2];
+    }
+}
 
 // Forward with the tape.  Error control as the four-lanes kernel (group
 // floors, slaved moments excluded while h / (H tau_c) > kSlavedHnu in the
@@ -229,7 +246,7 @@ ABCMB_HD FwdResult fwd_taped(const ModeCtx &c, const ModeBufs &mb, double rtol, 
         if (x + H >= xn) { H = xn - x; land = true; }
         if (H <= 0.0) {
             if (r.accepted == 0) r.emit0++;
-            sources_fwd(d, c.k, bg_at(c, xn), node_at(c, node), c.sw, Y, S + 3 * node);
+            emit_sources(c, node, Y, S);
             node++;
             continue;
         }
@@ -239,10 +256,11 @@ ABCMB_HD FwdResult fwd_taped(const ModeCtx &c, const ModeBufs &mb, double rtol, 
         const Bg10 b0 = bg_at(c, x);
         const bool excl = !gbs && H * b0.v[B_NU] > kSlavedHnu;
         double cm[4] = {0, 0, 0, 0};
-        for (int i = 0; i < d.N; i++) {
+        for (int i = ln_id(); i < d.N; i += ln_n()) {
             const int g = i < 3 ? 0 : i == 3 ? 1 : i < d.iN ? 2 : 3;
             cm[g] = fmax(cm[g], fabs(Y[i]));
         }
+        for (int g = 0; g < 4; g++) cm[g] = ln_max(cm[g]);
         int jacc = 0;
         double err = 0.0;
         Vec raw = wv(mb, d, V_CO);
@@ -252,13 +270,14 @@ ABCMB_HD FwdResult fwd_taped(const ModeCtx &c, const ModeBufs &mb, double rtol, 
             if (j < 2) continue;
             err = 0.0;
             Vec tj = wv(mb, d, V_T + j - 1), tl = wv(mb, d, V_T + j - 2);
-            for (int i = 0; i < d.N; i++) {
+            for (int i = ln_id(); i < d.N; i += ln_n()) {
                 const int g = i < 3 ? 0 : i == 3 ? 1 : i < d.iN ? 2 : 3;
                 if (excl && i >= d.iF + 2 && i < d.iN) continue;
                 const double scl = atol + rtol * fmax(fabs(Y[i]), fmax(ABCMB_CHAIN_FLOOR * cm[g], 1e-290));
                 const double e = fabs(tj[i] - tl[i]) / scl;
                 if (!(e <= err)) err = e;
             }
+            err = ln_max(err);
             if (!(err == err)) break;
             if (err <= 1.0) { jacc = j; break; }
         }
@@ -266,10 +285,12 @@ ABCMB_HD FwdResult fwd_taped(const ModeCtx &c, const ModeBufs &mb, double rtol, 
         if (jacc) {
             if (r.accepted >= kTapeCap) { r.status = ABCMB_E_MAX_STEPS; break; }
             if (r.accepted % kSeg == 0) vcopy(d, Y, ckv(mb, d, r.accepted / kSeg));
-            double *tp = mb.tape + 3 * (long)r.accepted;
-            tp[0] = x;
-            tp[1] = H;
-            tp[2] = (double)(jacc | (gbs ? 256 : 0) | (land ? 512 : 0));
+            if (ln_id() == 0) {
+                double *tp = mb.tape + 3 * (long)r.accepted;
+                tp[0] = x;
+                tp[1] = H;
+                tp[2] = (double)(jacc | (gbs ? 256 : 0) | (land ? 512 : 0));
+            }
             r.accepted++;
             vcopy(d, wv(mb, d, V_T + jacc - 1), Y); // as step_value computes it in the replay
             x = land ? xn : x + H;
@@ -279,14 +300,16 @@ ABCMB_HD FwdResult fwd_taped(const ModeCtx &c, const ModeBufs &mb, double rtol, 
             const double hn = H * fac;
             h = land ? fmax(h, hn) : hn;
             if (land) {
-                sources_fwd(d, c.k, bg_at(c, xn), node_at(c, node), c.sw, Y, S + 3 * node);
+                emit_sources(c, node, Y, S);
                 node++;
             }
         } else {
             h = H * fmin(0.9, fmax(0.1, 0.9 * exp(-log(err) / (gbs ? 2 * kAK - 1 : kAK))));
         }
     }
-    for (int n = node; n < c.n_tau; n++) S[3 * n] = S[3 * n + 1] = S[3 * n + 2] = 0.0;
+    if (ln_id() == 0)
+        for (int n = node; n < c.n_tau; n++) S[3 * n] = S[3 * n + 1] = S[3 * n + 2] = 0.0;
+    ln_sync();
     return r;
 }
 
@@ -309,6 +332,7 @@ struct Sinks {
 
 ABCMB_HD void flush_rows(const Sinks &sk)
 {
+    if (ln_id() != 0) return;
     RowAcc &a = *sk.acc;
     if (a.j >= 0) {
         double *r = sk.recbar + ABCMB_BG_ODETAB + 20 * (long)a.j;
@@ -320,6 +344,7 @@ ABCMB_HD void flush_rows(const Sinks &sk)
 
 ABCMB_HD void scatter_bg(const Sinks &sk, double lna, const Bg10 &bb)
 {
+    if (ln_id() != 0) return; // every lane holds the same bb
     const HW h = hw_at(lna);
     RowAcc &a = *sk.acc;
     if (h.j != a.j) {
@@ -354,7 +379,8 @@ ABCMB_HD void step_adjoint(const ModeCtx &c, const ModeBufs &mb, const Sinks &sk
         if (!gbs) {
             const double hs = H / i;
             Vec v = wv(mb, d, V_AB);
-            for (int e = 0; e < d.N; e++) v[e] = w * yb[e];
+            for (int e = ln_id(); e < d.N; e += ln_n()) v[e] = w * yb[e];
+            ln_sync();
             for (int m = i; m >= 1; m--) {
                 // substep m: z_m = M(bn)^-1 (z_{m-1} + hs E(bc) z_{m-1})
                 const double xa = x + (m - 1) * hs;
@@ -373,21 +399,24 @@ ABCMB_HD void step_adjoint(const ModeCtx &c, const ModeBufs &mb, const Sinks &sk
                 vcopy(d, v, t);
                 op_Et(d, c.sc, c.k, bc, t, v, hs); // v = (I + hs E^T) wbar
             }
-            for (int e = 0; e < d.N; e++) acc[e] += v[e];
+            for (int e = ln_id(); e < d.N; e += ln_n()) acc[e] += v[e];
+            ln_sync();
         } else {
             const int n = 2 * i;
             const double hs = H / n;
             // rolling adjoints: a2 = zbar_{m+1}, a1 = zbar_m, a0 = zbar_{m-1}
             Vec a2 = wv(mb, d, V_AB), a1 = wv(mb, d, V_AB + 1), a0 = wv(mb, d, V_AB + 2);
-            for (int e = 0; e < d.N; e++) {
+            for (int e = ln_id(); e < d.N; e += ln_n()) {
                 a2[e] = w * yb[e]; // zbar_n
                 a1[e] = 0.0;       // zbar_{n-1}
             }
+            ln_sync();
             for (int m = n - 1; m >= 1; m--) {
                 // z_{m+1} = z_{m-1} + 2 hs f_m(z_m)
                 const Bg10 bm = bg_at(c, x + m * hs);
                 Vec zm = wv(mb, d, V_ST + m);
-                for (int e = 0; e < d.N; e++) a0[e] = a2[e]; // zbar_{m-1} = zbar_{m+1} so far
+                for (int e = ln_id(); e < d.N; e += ln_n()) a0[e] = a2[e]; // zbar_{m-1} = zbar_{m+1} so far
+                ln_sync();
                 op_Et(d, c.sc, c.k, bm, a2, a1, 2.0 * hs);
                 op_Tt(d, c.k, bm, a2, a1, 2.0 * hs);
                 Bg10 bb;
@@ -403,7 +432,8 @@ ABCMB_HD void step_adjoint(const ModeCtx &c, const ModeBufs &mb, const Sinks &sk
             // a2 = zbar_1, a1 = zbar_0 so far; z_1 = z_0 + hs f_0(z_0)
             const Bg10 b0 = bg_at(c, x);
             Vec z0 = wv(mb, d, V_ST);
-            for (int e = 0; e < d.N; e++) a1[e] += a2[e];
+            for (int e = ln_id(); e < d.N; e += ln_n()) a1[e] += a2[e];
+            ln_sync();
             op_Et(d, c.sc, c.k, b0, a2, a1, hs);
             op_Tt(d, c.k, b0, a2, a1, hs);
             Bg10 bb;
@@ -411,7 +441,8 @@ ABCMB_HD void step_adjoint(const ModeCtx &c, const ModeBufs &mb, const Sinks &sk
             op_E_bgrad(d, c.sc, c.k, b0, a2, z0, hs, bb);
             op_T_bgrad(d, c.k, a2, z0, hs, bb);
             scatter_bg(sk, x, bb);
-            for (int e = 0; e < d.N; e++) acc[e] += a1[e];
+            for (int e = ln_id(); e < d.N; e += ln_n()) acc[e] += a1[e];
+            ln_sync();
         }
     }
     vcopy(d, acc, yb);
@@ -432,15 +463,20 @@ ABCMB_HD void sources_adjoint(const ModeCtx &c, const ModeBufs &mb, const Sinks 
     NodeD nb{0, 0, 0, 0, 0};
     Vec ys = wv(mb, d, V_AB), f = wv(mb, d, V_AB + 1);
     vzero(d, ys);
-    sources_rev(d, c.k, b, node_at(c, n), c.sw, y, Sb + 3 * n, ys, bb, nb);
+    // scalar reverse mode, on lane 0 (which alone scatters bb and nb below)
+    if (ln_id() == 0) sources_rev(d, c.k, b, node_at(c, n), c.sw, y, Sb + 3 * n, ys, bb, nb);
+    ln_sync();
     vzero(d, f);
     op_E(d, c.sc, c.k, b, y, f, 1.0);
     op_T(d, c.k, b, y, f, 1.0);
     double lnab = 0.0;
-    for (int e = 0; e < d.N; e++) {
+    for (int e = ln_id(); e < d.N; e += ln_n()) {
         lnab += ys[e] * f[e];
         yb[e] += ys[e];
     }
+    ln_sync();
+    lnab = ln_sum(lnab);
+    if (ln_id() != 0) return;
     const Bg10 db = bg_eval_dlna(c.ot, lna);
     for (int q = 0; q < B_N; q++) lnab += bb.v[q] * db.v[q];
     scatter_bg(sk, lna, bb);
@@ -494,13 +530,15 @@ ABCMB_HD void bwd(const ModeCtx &c, const ModeBufs &mb, const Sinks &sk, const F
     const Herm Hi = herm_at(x0);
     const double tau_i = herm_val(c.tab, Hi, C_TAU, C_DTAU);
     const double taub = initial_dtau(d, c.k, tau_i, cz.R_nu, yb);
+    const double rnub = initial_dRn(d, c.k, tau_i, cz.R_nu, yb);
+    flush_rows(sk);
+    if (ln_id() != 0) return;
     double *tb = sk.recbar + ABCMB_BG_TABLE;
     add_to(tb + 8 * Hi.j + C_TAU, Hi.h00 * taub);
     add_to(tb + 8 * (Hi.j + 1) + C_TAU, Hi.h01 * taub);
     add_to(tb + 8 * Hi.j + C_DTAU, kDlna * Hi.h10 * taub);
     add_to(tb + 8 * (Hi.j + 1) + C_DTAU, kDlna * Hi.h11 * taub);
-    add_to(sk.recbar + ABCMB_S_RNU, initial_dRn(d, c.k, tau_i, cz.R_nu, yb));
-    flush_rows(sk);
+    add_to(sk.recbar + ABCMB_S_RNU, rnub);
 }
 
 } // namespace adj

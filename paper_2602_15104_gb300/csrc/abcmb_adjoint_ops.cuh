@@ -93,11 +93,71 @@ ABCMB_HD void bg_scatter(double *otbar, const HW &h, const Bg10 &bb)
     }
 }
 
+// The lanes that share one mode: on the device the 32 lanes of a warp, lane
+// i taking the state elements i, i + 32, ...; on the host a single lane.
+// Every operator below is called by all lanes of the mode alike, reads its
+// inputs, writes only its own lane's elements of the output, and ends with a
+// lane barrier, so the next operator may read any element.
+ABCMB_HD int ln_id()
+{
+#ifdef __CUDA_ARCH__
+    return threadIdx.x & 31;
+#else
+    return 0;
+#endif
+}
+
+ABCMB_HD int ln_n()
+{
+#ifdef __CUDA_ARCH__
+    return 32;
+#else
+    return 1;
+#endif
+}
+
+ABCMB_HD void ln_sync()
+{
+#ifdef __CUDA_ARCH__
+    __syncwarp();
+#endif
+}
+
+ABCMB_HD double ln_sum(double v)
+{
+#ifdef __CUDA_ARCH__
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+#endif
+    return v;
+}
+
+// maximum over the lanes; a NaN anywhere gives NaN
+ABCMB_HD double ln_max(double v)
+{
+#ifdef __CUDA_ARCH__
+    for (int o = 16; o > 0; o >>= 1) {
+        const double u = __shfl_xor_sync(0xffffffffu, v, o);
+        if (!(u <= v)) v = u;
+    }
+#endif
+    return v;
+}
+
 // streaming coefficients of chain moment l under truncation L
 ABCMB_HD void sc_AB(const StreamCoef &sc, int l, int L, double &A, double &Bc)
 {
     A = l < L ? sc.a[l] : (l == L ? 1.0 : 0.0);
     Bc = l < L ? sc.b[l] : 0.0;
+}
+
+// chain (0 photon temperature, 1 polarization, 2 neutrinos), moment l, its
+// truncation L and first element i0 of state element i >= 4
+ABCMB_HD void chain_of(const OdeDims &d, int i, int &ch, int &l, int &L, int &i0)
+{
+    ch = i < d.iG ? 0 : (i < d.iN ? 1 : 2);
+    i0 = ch == 0 ? d.iF : (ch == 1 ? d.iG : d.iN);
+    L = ch == 0 ? d.Lg : (ch == 1 ? d.Lp : d.Ln);
+    l = i - i0;
 }
 
 // ---- E: everything but Thomson ----
@@ -109,26 +169,24 @@ ABCMB_HD void op_E(const OdeDims &d, const StreamCoef &sc, double k, const Bg10 
     const double hp = 2.0 * kH * kH * eta +
                       3.0 * (b.v[B_FC] * dc + b.v[B_FB] * db + b.v[B_FG] * y[d.iF] + b.v[B_FNU] * y[d.iN]);
     const double ep = 1.5 * b.v[B_HC] * ik * (b.v[B_FB] * tb * ik + b.v[B_FG] * y[d.iF + 1] + b.v[B_FNU] * y[d.iN + 1]);
-    out[0] += fac * ep;
-    out[1] += fac * (-0.5 * hp);
-    out[2] += fac * (-ih * tb - 0.5 * hp);
-    out[3] += fac * (-tb + b.v[B_CS2] * k * k * ih * db);
-    for (int ch = 0; ch < 3; ch++) {
-        const int i0 = ch == 0 ? d.iF : ch == 1 ? d.iG : d.iN;
-        const int L = ch == 0 ? d.Lg : ch == 1 ? d.Lp : d.Ln;
-        for (int l = 0; l <= L; l++) {
+    for (int i = ln_id(); i < d.N; i += ln_n()) {
+        double f;
+        if (i < 4) {
+            f = i == 0 ? ep : (i == 1 ? -0.5 * hp : (i == 2 ? -ih * tb - 0.5 * hp : -tb + b.v[B_CS2] * k * k * ih * db));
+        } else {
+            int ch, l, L, i0;
+            chain_of(d, i, ch, l, L, i0);
             double A, Bc;
             sc_AB(sc, l, L, A, Bc);
-            const double prev = l > 0 ? y[i0 + l - 1] : 0.0, nxt = l < L ? y[i0 + l + 1] : 0.0;
-            double f = kH * (A * prev - Bc * nxt);
-            if (l == L) f -= (L + 1.0) * b.v[B_IHT] * y[i0 + L];
-            out[i0 + l] += fac * f;
+            const double prev = l > 0 ? y[i - 1] : 0.0, nxt = l < L ? y[i + 1] : 0.0;
+            f = kH * (A * prev - Bc * nxt);
+            if (l == L) f -= (L + 1.0) * b.v[B_IHT] * y[i];
+            if (ch != 1 && l == 0) f += -(2.0 / 3.0) * hp;
+            if (ch != 1 && l == 2) f += (4.0 / 15.0) * hp + 1.6 * ep;
         }
-        if (ch != 1) {
-            out[i0] += fac * (-(2.0 / 3.0) * hp);
-            out[i0 + 2] += fac * ((4.0 / 15.0) * hp + 1.6 * ep);
-        }
+        out[i] += fac * f;
     }
+    ln_sync();
 }
 
 ABCMB_HD void op_Et(const OdeDims &d, const StreamCoef &sc, double k, const Bg10 &b, Vec v, Vec out, double fac)
@@ -138,26 +196,37 @@ ABCMB_HD void op_Et(const OdeDims &d, const StreamCoef &sc, double k, const Bg10
                        (4.0 / 15.0) * (v[d.iF + 2] + v[d.iN + 2]);
     const double wep = v[0] + 1.6 * (v[d.iF + 2] + v[d.iN + 2]);
     const double ce = 1.5 * b.v[B_HC] * ik;
-    out[0] += fac * whp * 2.0 * kH * kH;
-    out[1] += fac * whp * 3.0 * b.v[B_FC];
-    out[2] += fac * (whp * 3.0 * b.v[B_FB] + v[3] * b.v[B_CS2] * k * k * ih);
-    out[3] += fac * (wep * ce * b.v[B_FB] * ik - ih * v[2] - v[3]);
-    out[d.iF] += fac * whp * 3.0 * b.v[B_FG];
-    out[d.iN] += fac * whp * 3.0 * b.v[B_FNU];
-    out[d.iF + 1] += fac * wep * ce * b.v[B_FG];
-    out[d.iN + 1] += fac * wep * ce * b.v[B_FNU];
-    for (int ch = 0; ch < 3; ch++) {
-        const int i0 = ch == 0 ? d.iF : ch == 1 ? d.iG : d.iN;
-        const int L = ch == 0 ? d.Lg : ch == 1 ? d.Lp : d.Ln;
-        for (int l = 0; l <= L; l++) {
+    for (int i = ln_id(); i < d.N; i += ln_n()) {
+        double g;
+        if (i < 4) {
+            g = i == 0 ? whp * 2.0 * kH * kH
+                       : (i == 1 ? whp * 3.0 * b.v[B_FC]
+                                 : (i == 2 ? whp * 3.0 * b.v[B_FB] + v[3] * b.v[B_CS2] * k * k * ih
+                                           : wep * ce * b.v[B_FB] * ik - ih * v[2] - v[3]));
+        } else {
+            // gather form of the transposed streaming: row l receives A_{l+1} v_{l+1} and -B_{l-1} v_{l-1}
+            int ch, l, L, i0;
+            chain_of(d, i, ch, l, L, i0);
+            g = 0.0;
             double A, Bc;
-            sc_AB(sc, l, L, A, Bc);
-            const double vl = v[i0 + l];
-            if (l > 0) out[i0 + l - 1] += fac * kH * A * vl;
-            if (l < L) out[i0 + l + 1] += fac * (-kH * Bc * vl);
-            if (l == L) out[i0 + L] += fac * (-(L + 1.0) * b.v[B_IHT] * vl);
+            if (l + 1 <= L) {
+                sc_AB(sc, l + 1, L, A, Bc);
+                g += kH * A * v[i + 1];
+            }
+            if (l >= 1) {
+                sc_AB(sc, l - 1, L, A, Bc);
+                g -= kH * Bc * v[i - 1];
+            }
+            if (l == L) g -= (L + 1.0) * b.v[B_IHT] * v[i];
+            if (ch != 1) {
+                const double f = ch == 0 ? b.v[B_FG] : b.v[B_FNU];
+                if (l == 0) g += whp * 3.0 * f;
+                if (l == 1) g += wep * ce * f;
+            }
         }
+        out[i] += fac * g;
     }
+    ln_sync();
 }
 
 ABCMB_HD void op_E_bgrad(const OdeDims &d, const StreamCoef &sc, double k, const Bg10 &b, Vec v, Vec y,
@@ -169,18 +238,19 @@ ABCMB_HD void op_E_bgrad(const OdeDims &d, const StreamCoef &sc, double k, const
                        (4.0 / 15.0) * (v[d.iF + 2] + v[d.iN + 2]);
     const double wep = v[0] + 1.6 * (v[d.iF + 2] + v[d.iN + 2]);
     const double ce = 1.5 * b.v[B_HC] * ik;
-    double stream = 0.0, trunc = 0.0;
-    for (int ch = 0; ch < 3; ch++) {
-        const int i0 = ch == 0 ? d.iF : ch == 1 ? d.iG : d.iN;
-        const int L = ch == 0 ? d.Lg : ch == 1 ? d.Lp : d.Ln;
-        for (int l = 0; l <= L; l++) {
-            double A, Bc;
-            sc_AB(sc, l, L, A, Bc);
-            const double prev = l > 0 ? y[i0 + l - 1] : 0.0, nxt = l < L ? y[i0 + l + 1] : 0.0;
-            stream += v[i0 + l] * (A * prev - Bc * nxt);
-        }
-        trunc += (L + 1.0) * v[i0 + L] * y[i0 + L];
+    double stream = 0.0;
+    for (int i = 4 + ln_id(); i < d.N; i += ln_n()) {
+        int ch, l, L, i0;
+        chain_of(d, i, ch, l, L, i0);
+        double A, Bc;
+        sc_AB(sc, l, L, A, Bc);
+        const double prev = l > 0 ? y[i - 1] : 0.0, nxt = l < L ? y[i + 1] : 0.0;
+        stream += v[i] * (A * prev - Bc * nxt);
     }
+    stream = ln_sum(stream);
+    const double trunc = (d.Lg + 1.0) * v[d.iF + d.Lg] * y[d.iF + d.Lg] +
+                         (d.Lp + 1.0) * v[d.iG + d.Lp] * y[d.iG + d.Lp] +
+                         (d.Ln + 1.0) * v[d.iN + d.Ln] * y[d.iN + d.Ln];
     bb.v[B_IH] += fac * (whp * 4.0 * k * k * ih * eta + k * stream - v[2] * tb + v[3] * b.v[B_CS2] * k * k * db);
     bb.v[B_IHT] += fac * (-trunc);
     bb.v[B_FC] += fac * whp * 3.0 * dc;
@@ -197,26 +267,42 @@ ABCMB_HD void op_T(const OdeDims &d, double k, const Bg10 &b, Vec y, Vec out, do
     const double nu = b.v[B_NU], rnu = b.v[B_RNU];
     const double tb = y[3], F1 = y[d.iF + 1];
     const double Pi = y[d.iF + 2] + y[d.iG] + y[d.iG + 2];
-    out[3] += fac * rnu * (0.75 * k * F1 - tb);
-    out[d.iF + 1] += fac * nu * ((4.0 / 3.0) / k * tb - F1);
-    for (int l = 2; l <= d.Lg; l++) out[d.iF + l] += fac * (-nu * y[d.iF + l]);
-    for (int l = 0; l <= d.Lp; l++) out[d.iG + l] += fac * (-nu * y[d.iG + l]);
-    out[d.iF + 2] += fac * 0.1 * nu * Pi;
-    out[d.iG] += fac * 0.5 * nu * Pi;
-    out[d.iG + 2] += fac * 0.1 * nu * Pi;
+    for (int i = ln_id(); i < d.N; i += ln_n()) {
+        double g = 0.0;
+        if (i == 3) {
+            g = rnu * (0.75 * k * F1 - tb);
+        } else if (i >= d.iF && i < d.iG) {
+            const int l = i - d.iF;
+            if (l == 1) g = nu * ((4.0 / 3.0) / k * tb - F1);
+            else if (l >= 2) g = -nu * y[i] + (l == 2 ? 0.1 * nu * Pi : 0.0);
+        } else if (i >= d.iG && i < d.iN) {
+            const int l = i - d.iG;
+            g = -nu * y[i] + (l == 0 ? 0.5 * nu * Pi : (l == 2 ? 0.1 * nu * Pi : 0.0));
+        }
+        out[i] += fac * g;
+    }
+    ln_sync();
 }
 
 ABCMB_HD void op_Tt(const OdeDims &d, double k, const Bg10 &b, Vec v, Vec out, double fac)
 {
     const double nu = b.v[B_NU], rnu = b.v[B_RNU];
     const double wpi = 0.1 * v[d.iF + 2] + 0.5 * v[d.iG] + 0.1 * v[d.iG + 2];
-    out[d.iF + 1] += fac * (rnu * 0.75 * k * v[3] - nu * v[d.iF + 1]);
-    out[3] += fac * (-rnu * v[3] + nu * (4.0 / 3.0) / k * v[d.iF + 1]);
-    for (int l = 2; l <= d.Lg; l++) out[d.iF + l] += fac * (-nu * v[d.iF + l]);
-    for (int l = 0; l <= d.Lp; l++) out[d.iG + l] += fac * (-nu * v[d.iG + l]);
-    out[d.iF + 2] += fac * nu * wpi;
-    out[d.iG] += fac * nu * wpi;
-    out[d.iG + 2] += fac * nu * wpi;
+    for (int i = ln_id(); i < d.N; i += ln_n()) {
+        double g = 0.0;
+        if (i == 3) {
+            g = -rnu * v[3] + nu * (4.0 / 3.0) / k * v[d.iF + 1];
+        } else if (i >= d.iF && i < d.iG) {
+            const int l = i - d.iF;
+            if (l == 1) g = rnu * 0.75 * k * v[3] - nu * v[i];
+            else if (l >= 2) g = -nu * v[i] + (l == 2 ? nu * wpi : 0.0);
+        } else if (i >= d.iG && i < d.iN) {
+            const int l = i - d.iG;
+            g = -nu * v[i] + ((l == 0 || l == 2) ? nu * wpi : 0.0);
+        }
+        out[i] += fac * g;
+    }
+    ln_sync();
 }
 
 ABCMB_HD void op_T_bgrad(const OdeDims &d, double k, Vec v, Vec y, double fac, Bg10 &bb)
@@ -224,9 +310,10 @@ ABCMB_HD void op_T_bgrad(const OdeDims &d, double k, Vec v, Vec y, double fac, B
     const double tb = y[3], F1 = y[d.iF + 1];
     const double Pi = y[d.iF + 2] + y[d.iG] + y[d.iG + 2];
     const double wpi = 0.1 * v[d.iF + 2] + 0.5 * v[d.iG] + 0.1 * v[d.iG + 2];
-    double dnu = v[d.iF + 1] * ((4.0 / 3.0) / k * tb - F1) + wpi * Pi;
-    for (int l = 2; l <= d.Lg; l++) dnu -= v[d.iF + l] * y[d.iF + l];
-    for (int l = 0; l <= d.Lp; l++) dnu -= v[d.iG + l] * y[d.iG + l];
+    double damp = 0.0; // sum of v y over the damped moments (photon l >= 2, all of G)
+    for (int i = d.iF + 2 + ln_id(); i < d.iN; i += ln_n()) damp += v[i] * y[i];
+    damp = ln_sum(damp);
+    const double dnu = v[d.iF + 1] * ((4.0 / 3.0) / k * tb - F1) + wpi * Pi - damp;
     bb.v[B_NU] += fac * dnu;
     bb.v[B_RNU] += fac * v[3] * (0.75 * k * F1 - tb);
 }
@@ -235,46 +322,42 @@ ABCMB_HD void op_T_bgrad(const OdeDims &d, double k, Vec v, Vec y, double fac, B
 ABCMB_HD void solve_M(const OdeDims &d, double k, const Bg10 &b, double h, Vec y)
 {
     const double hnu = h * b.v[B_NU], hR = h * b.v[B_RNU], dmp = 1.0 / (1.0 + hnu);
-    {
-        const double rb = y[3], ru = 0.75 * k * y[d.iF + 1];
-        const double idet = 1.0 / (1.0 + hR + hnu);
-        y[3] = ((1.0 + hnu) * rb + hR * ru) * idet;
-        y[d.iF + 1] = (hnu * rb + (1.0 + hR) * ru) * idet * (4.0 / 3.0) / k;
+    const double rb = y[3], ru = 0.75 * k * y[d.iF + 1];
+    const double r2 = y[d.iF + 2], g0 = y[d.iG], g2 = y[d.iG + 2];
+    ln_sync(); // every lane has read the coupled elements before any is overwritten
+    const double idet = 1.0 / (1.0 + hR + hnu);
+    const double pin = (r2 + g0 + g2) / (1.0 + 0.3 * hnu);
+    for (int i = ln_id(); i < d.N; i += ln_n()) {
+        if (i == 3) y[3] = ((1.0 + hnu) * rb + hR * ru) * idet;
+        else if (i == d.iF + 1) y[i] = (hnu * rb + (1.0 + hR) * ru) * idet * (4.0 / 3.0) / k;
+        else if (i == d.iF + 2) y[i] = (r2 + 0.1 * hnu * pin) * dmp;
+        else if (i == d.iG) y[i] = (g0 + 0.5 * hnu * pin) * dmp;
+        else if (i == d.iG + 2) y[i] = (g2 + 0.1 * hnu * pin) * dmp;
+        else if ((i >= d.iF + 3 && i < d.iG) || i == d.iG + 1 || (i >= d.iG + 3 && i < d.iN)) y[i] *= dmp;
     }
-    {
-        const double r2 = y[d.iF + 2], g0 = y[d.iG], g2 = y[d.iG + 2];
-        const double pin = (r2 + g0 + g2) / (1.0 + 0.3 * hnu);
-        y[d.iF + 2] = (r2 + 0.1 * hnu * pin) * dmp;
-        y[d.iG] = (g0 + 0.5 * hnu * pin) * dmp;
-        y[d.iG + 2] = (g2 + 0.1 * hnu * pin) * dmp;
-    }
-    for (int l = 3; l <= d.Lg; l++) y[d.iF + l] *= dmp;
-    y[d.iG + 1] *= dmp;
-    for (int l = 3; l <= d.Lp; l++) y[d.iG + l] *= dmp;
+    ln_sync();
 }
 
 // y <- (I - h T(b))^{-T} y
 ABCMB_HD void solve_Mt(const OdeDims &d, double k, const Bg10 &b, double h, Vec y)
 {
     const double hnu = h * b.v[B_NU], hR = h * b.v[B_RNU], dmp = 1.0 / (1.0 + hnu);
-    {
-        // (theta_b, F1) block: M2 = [[1 + hR, -hR 3k/4], [-hnu 4/(3k), 1 + hnu]]
-        const double a = y[3], c = y[d.iF + 1];
-        const double idet = 1.0 / (1.0 + hR + hnu);
-        y[3] = ((1.0 + hnu) * a + hnu * (4.0 / 3.0) / k * c) * idet;
-        y[d.iF + 1] = (hR * 0.75 * k * a + (1.0 + hR) * c) * idet;
+    // (theta_b, F1) block: M2 = [[1 + hR, -hR 3k/4], [-hnu 4/(3k), 1 + hnu]]
+    const double a = y[3], c = y[d.iF + 1];
+    // (F2, G0, G2): M3 = (1 + hnu) I - hnu c 1^T, c = (0.1, 0.5, 0.1); transpose solve
+    const double r2 = y[d.iF + 2], g0 = y[d.iG], g2 = y[d.iG + 2];
+    ln_sync();
+    const double idet = 1.0 / (1.0 + hR + hnu);
+    const double s = (0.1 * r2 + 0.5 * g0 + 0.1 * g2) / (1.0 + 0.3 * hnu);
+    for (int i = ln_id(); i < d.N; i += ln_n()) {
+        if (i == 3) y[3] = ((1.0 + hnu) * a + hnu * (4.0 / 3.0) / k * c) * idet;
+        else if (i == d.iF + 1) y[i] = (hR * 0.75 * k * a + (1.0 + hR) * c) * idet;
+        else if (i == d.iF + 2) y[i] = (r2 + hnu * s) * dmp;
+        else if (i == d.iG) y[i] = (g0 + hnu * s) * dmp;
+        else if (i == d.iG + 2) y[i] = (g2 + hnu * s) * dmp;
+        else if ((i >= d.iF + 3 && i < d.iG) || i == d.iG + 1 || (i >= d.iG + 3 && i < d.iN)) y[i] *= dmp;
     }
-    {
-        // (F2, G0, G2): M3 = (1 + hnu) I - hnu c 1^T, c = (0.1, 0.5, 0.1); transpose solve
-        const double r2 = y[d.iF + 2], g0 = y[d.iG], g2 = y[d.iG + 2];
-        const double s = (0.1 * r2 + 0.5 * g0 + 0.1 * g2) / (1.0 + 0.3 * hnu);
-        y[d.iF + 2] = (r2 + hnu * s) * dmp;
-        y[d.iG] = (g0 + hnu * s) * dmp;
-        y[d.iG + 2] = (g2 + hnu * s) * dmp;
-    }
-    for (int l = 3; l <= d.Lg; l++) y[d.iF + l] *= dmp;
-    y[d.iG + 1] *= dmp;
-    for (int l = 3; l <= d.Lp; l++) y[d.iG + l] *= dmp;
+    ln_sync();
 }
 
 // ---- CMB sources at a node (App. B.4 eq. source_functions; see node_sources) ----
@@ -422,20 +505,22 @@ ABCMB_HD void sources_rev(const OdeDims &d, double k, const Bg10 &b, const NodeD
 // adiabatic initial state (the formulas of initial_state, R_nu given explicitly)
 ABCMB_HD void initial_fwd(const OdeDims &d, double k, double tau_i, double Rn, Vec y)
 {
-    for (int i = 0; i < d.N; i++) y[i] = 0.0;
     const double C = 0.5, kt = k * tau_i;
     const double dg = -(2.0 / 3.0) * C * kt * kt;
     const double F1 = -(2.0 / 27.0) * C * kt * kt * kt;
     const double tg = -C * k * kt * kt * kt / 18.0;
-    y[0] = 2.0 * C - C * kt * kt * (5.0 + 4.0 * Rn) / (6.0 * (15.0 + 4.0 * Rn));
-    y[1] = 0.75 * dg;
-    y[2] = 0.75 * dg;
-    y[3] = tg;
-    y[d.iF] = dg;
-    y[d.iF + 1] = F1;
-    y[d.iN] = dg;
-    y[d.iN + 1] = F1 * (23.0 + 4.0 * Rn) / (15.0 + 4.0 * Rn);
-    y[d.iN + 2] = (4.0 / 3.0) * C * kt * kt / (15.0 + 4.0 * Rn);
+    for (int i = ln_id(); i < d.N; i += ln_n()) {
+        double v = 0.0;
+        if (i == 0) v = 2.0 * C - C * kt * kt * (5.0 + 4.0 * Rn) / (6.0 * (15.0 + 4.0 * Rn));
+        else if (i == 1 || i == 2) v = 0.75 * dg;
+        else if (i == 3) v = tg;
+        else if (i == d.iF || i == d.iN) v = dg;
+        else if (i == d.iF + 1) v = F1;
+        else if (i == d.iN + 1) v = F1 * (23.0 + 4.0 * Rn) / (15.0 + 4.0 * Rn);
+        else if (i == d.iN + 2) v = (4.0 / 3.0) * C * kt * kt / (15.0 + 4.0 * Rn);
+        y[i] = v;
+    }
+    ln_sync();
 }
 
 // d/d tau_i of the initial state, dotted with ybar

@@ -2,7 +2,7 @@
 // hand-written discrete adjoint of perturb + project + k-quadrature, then
 // the pull-back through the background record.
 //
-//   abcmb_perturb_taped     forward ODE (one thread per mode, abcmb_adjoint.cuh)
+//   abcmb_perturb_taped     forward ODE (one warp per mode, abcmb_adjoint.cuh)
 //                           recording each mode's accepted steps and
 //                           checkpoints in the caller's workspace
 //   abcmb_cl_adjoint        Cbar -> Deltabar, and the adjoints of A_s, n_s
@@ -26,6 +26,7 @@ namespace abcmb {
 namespace adj {
 
 constexpr long kCkpts = kTapeCap / kSeg + 1;
+constexpr int kGradThreads = 64; // two modes (warps) per block
 
 struct GradLayout {
     long M, N;
@@ -52,14 +53,16 @@ __host__ __device__ inline GradLayout grad_layout(int B, int Nk, const OdeDims &
     return g;
 }
 
+// each mode's vectors contiguous, so that the lanes of its warp read and
+// write consecutive elements
 __device__ inline ModeBufs mode_bufs(char *ws, const GradLayout &g, long mi)
 {
     ModeBufs m;
-    m.work = (double *)(ws + g.work) + mi;
-    m.seg = (double *)(ws + g.seg) + mi;
-    m.ckpt = (double *)(ws + g.ckpt) + mi;
+    m.work = (double *)(ws + g.work) + mi * V_COUNT * g.N;
+    m.seg = (double *)(ws + g.seg) + mi * (kSeg + 1) * g.N;
+    m.ckpt = (double *)(ws + g.ckpt) + mi * kCkpts * g.N;
     m.tape = (double *)(ws + g.tape) + (long)kTapeCap * 3 * mi;
-    m.stride = g.M;
+    m.stride = 1;
     return m;
 }
 
@@ -81,7 +84,7 @@ __device__ inline ModeCtx mode_ctx(const OdeDims &d, const StreamCoef &sc, const
     return c;
 }
 
-__global__ void __launch_bounds__(64)
+__global__ void __launch_bounds__(kGradThreads)
 taped_kernel(int B, int Nk, const double *__restrict__ bg, long len, const double *__restrict__ kv, int Lg, int Lp,
              int Ln, double rtol, double atol, int max_steps, double s_sw, double s_isw, double s_dop, double *S,
              int *status, char *ws)
@@ -94,7 +97,7 @@ taped_kernel(int B, int Nk, const double *__restrict__ bg, long len, const doubl
     __syncthreads();
     const OdeDims d = ode_dims(Lg, Lp, Ln);
     const GradLayout g = grad_layout(B, Nk, d);
-    const long mi = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long mi = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; // one warp per mode
     if (mi >= g.M) return;
     const int kidx = Nk - 1 - (int)(mi / B), b = (int)(mi % B);
     const double sw[3] = {s_sw, s_isw, s_dop};
@@ -105,18 +108,20 @@ taped_kernel(int B, int Nk, const double *__restrict__ bg, long len, const doubl
     FwdResult r = {ABCMB_OK, 0, 0, 0};
     if (c.rec[ABCMB_S_STATUS] != 0.0) {
         r.status = ABCMB_E_NONFINITE;
-        for (int n = 0; n < 3 * c.n_tau; n++) Sm[n] = 0.0;
+        for (int n = ln_id(); n < 3 * c.n_tau; n += ln_n()) Sm[n] = 0.0;
     } else {
         r = fwd_taped(c, mb, rtol, atol, max_steps, Sm);
     }
-    res[0] = r.status;
-    res[1] = r.steps;
-    res[2] = r.accepted;
-    res[3] = r.emit0;
-    status[(long)b * Nk + kidx] = r.status;
+    if (ln_id() == 0) {
+        res[0] = r.status;
+        res[1] = r.steps;
+        res[2] = r.accepted;
+        res[3] = r.emit0;
+        status[(long)b * Nk + kidx] = r.status;
+    }
 }
 
-__global__ void __launch_bounds__(64)
+__global__ void __launch_bounds__(kGradThreads)
 adjoint_kernel(int B, int Nk, const double *__restrict__ bg, long len, const double *__restrict__ kv, int Lg,
                int Lp, int Ln, double s_sw, double s_isw, double s_dop, const double *__restrict__ Sbar, char *ws,
                double *recbar)
@@ -129,7 +134,7 @@ adjoint_kernel(int B, int Nk, const double *__restrict__ bg, long len, const dou
     __syncthreads();
     const OdeDims d = ode_dims(Lg, Lp, Ln);
     const GradLayout g = grad_layout(B, Nk, d);
-    const long mi = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long mi = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; // one warp per mode
     if (mi >= g.M) return;
     const int kidx = Nk - 1 - (int)(mi / B), b = (int)(mi % B);
     const double sw[3] = {s_sw, s_isw, s_dop};
@@ -352,9 +357,9 @@ extern "C" int abcmb_perturb_taped(int B, const double *bg, const double *k, int
     if (workspace_bytes < abcmb_grad_workspace_bytes(B, Nk, o) || ((size_t)workspace & 255) != 0)
         return ABCMB_E_INVALID_ARG;
     const long len = (long)abcmb_bg_doubles(o), M = (long)B * Nk;
-    const long blocks = (M + 63) / 64;
+    const long blocks = (M * 32 + abcmb::adj::kGradThreads - 1) / abcmb::adj::kGradThreads;
     if (blocks > 2147483647L) return ABCMB_E_INVALID_ARG;
-    abcmb::adj::taped_kernel<<<(unsigned)blocks, 64, 0, (cudaStream_t)stream>>>(
+    abcmb::adj::taped_kernel<<<(unsigned)blocks, abcmb::adj::kGradThreads, 0, (cudaStream_t)stream>>>(
         B, Nk, bg, len, k, o->lmax_g, o->lmax_pol, o->lmax_nu, o->rtol, o->atol, o->max_steps, o->scale_sw,
         o->scale_isw, o->scale_dop, S, mode_status, (char *)workspace);
     return cudaGetLastError() == cudaSuccess ? ABCMB_OK : ABCMB_E_CUDA;
@@ -369,9 +374,9 @@ extern "C" int abcmb_perturb_adjoint(int B, const double *bg, const double *k, i
     if (workspace_bytes < abcmb_grad_workspace_bytes(B, Nk, o) || ((size_t)workspace & 255) != 0)
         return ABCMB_E_INVALID_ARG;
     const long len = (long)abcmb_bg_doubles(o), M = (long)B * Nk;
-    const long blocks = (M + 63) / 64;
+    const long blocks = (M * 32 + abcmb::adj::kGradThreads - 1) / abcmb::adj::kGradThreads;
     if (blocks > 2147483647L) return ABCMB_E_INVALID_ARG;
-    abcmb::adj::adjoint_kernel<<<(unsigned)blocks, 64, 0, (cudaStream_t)stream>>>(
+    abcmb::adj::adjoint_kernel<<<(unsigned)blocks, abcmb::adj::kGradThreads, 0, (cudaStream_t)stream>>>(
         B, Nk, bg, len, k, o->lmax_g, o->lmax_pol, o->lmax_nu, o->scale_sw, o->scale_isw, o->scale_dop, Sbar,
         (char *)workspace, recbar);
     return cudaGetLastError() == cudaSuccess ? ABCMB_OK : ABCMB_E_CUDA;

@@ -44,12 +44,18 @@ void setup(Run &R, const double *rec, double k, int L)
 extern "C" long h_bg_len(int n_tau) { return ABCMB_BG_NODES + 8L * n_tau; }
 extern "C" void h_build_bg(const double *p, int n_tau, double *rec) { build_background(p, rec, n_tau, 0, 1); }
 
-extern "C" int h_fwd(const double *rec, double k, int L, double rtol, double *S, int *accepted)
+// sig[0..2]: accepted steps, steps tried, and the sum of the accepted steps'
+// column counts and regimes -- equal signatures mean the same discrete map
+extern "C" int h_fwd(const double *rec, double k, int L, double rtol, double *S, int *sig)
 {
     Run R;
     setup(R, rec, k, L);
     const FwdResult fr = fwd_taped(R.c, R.mb, rtol, 1e-14, 10000000, S);
-    *accepted = fr.accepted;
+    long js = 0;
+    for (int s = 0; s < fr.accepted && s < kTapeCap; s++) js += (long)R.tape[3 * (size_t)s + 2];
+    sig[0] = fr.accepted;
+    sig[1] = fr.steps;
+    sig[2] = (int)(js % 2147483647L);
     return fr.status;
 }
 

@@ -72,20 +72,20 @@ def test_step_transpose_and_table_gradient(H, rec, x, H_, J, gbs):
 
 @pytest.mark.parametrize("k,node", [(0.02, 30), (0.02, 80), (0.003, 60)])
 def test_mode_gradient_against_finite_differences(H, rec, k, node):
-    # An adaptive forward flips an accept/reject decision (err within ~1e-7 of
-    # 1) for perturbations as small as 1e-7 of a table entry, which changes the
-    # discrete map by the integration error; the differences are therefore
-    # taken with steps of ~1e-8 relative and only where the three runs took the
-    # same accepted steps.
+    # An adaptive forward flips an accept/reject decision or a column count
+    # (err within ~1e-7 of 1) for perturbations as small as 1e-7 of a table
+    # entry, which changes the discrete map by the integration error; the
+    # differences are therefore taken with steps of ~1e-8 relative and only
+    # where the three runs took the same steps with the same column counts.
     n_tau, L, rtol = 120, 8, 1e-9
     rng = np.random.default_rng(node)
     Sb = np.zeros((n_tau, 3))
     Sb[node] = rng.normal(size=3)
 
     def phi(r):
-        S, acc = np.zeros((n_tau, 3)), ctypes.c_int()
-        assert H.h_fwd(ptr(r), k, L, rtol, ptr(S), ctypes.byref(acc)) == 0
-        return (Sb * S).sum(), acc.value
+        S, sig = np.zeros((n_tau, 3)), np.zeros(3, dtype=np.int32)
+        assert H.h_fwd(ptr(r), k, L, rtol, ptr(S), ptr(sig)) == 0
+        return (Sb * S).sum(), tuple(sig)
 
     _, acc0 = phi(rec)
     rb = np.zeros_like(rec)
@@ -94,7 +94,7 @@ def test_mode_gradient_against_finite_differences(H, rec, k, node):
     checked = 0
     for a, b in regions:
         for e in a + np.argsort(-np.abs(rb[a:b]))[:4]:
-            for hr in (1e-8, 3e-9, 1e-9):
+            for hr in (3e-8, 1e-8, 3e-9, 1e-9):
                 h = hr * abs(rec[e])
                 rp, rm = rec.copy(), rec.copy()
                 rp[e] += h
@@ -117,15 +117,15 @@ def test_node_position_gradient(H, rec, k, node):
     Sb = rng.normal(size=(n_tau, 3))
 
     def phi(r):
-        S, acc = np.zeros((n_tau, 3)), ctypes.c_int()
-        assert H.h_fwd(ptr(r), k, L, rtol, ptr(S), ctypes.byref(acc)) == 0
-        return (Sb * S).sum(), acc.value
+        S, sig = np.zeros((n_tau, 3)), np.zeros(3, dtype=np.int32)
+        assert H.h_fwd(ptr(r), k, L, rtol, ptr(S), ptr(sig)) == 0
+        return (Sb * S).sum(), tuple(sig)
 
     _, acc0 = phi(rec)
     rb = np.zeros_like(rec)
     assert H.h_grad(ptr(rec), k, L, rtol, ptr(Sb), ptr(rb)) == 0
     e = 64 + 28 * 18433 + 8 * node  # the node's ln a
-    for hr in (1e-8, 3e-9, 1e-9):
+    for hr in (3e-8, 1e-8, 3e-9, 1e-9):
         h = hr * abs(rec[e])
         rp, rm = rec.copy(), rec.copy()
         rp[e] += h
