@@ -22,9 +22,9 @@ HOOK_NO_THOMSON = 2
 HOOK_EDS_CDM = 4
 
 BG_FIELDS = ("a", "Hc", "dHc", "fc", "fb", "fg", "fnu", "tau", "xe", "dxe",
-             "nuT", "Rinv", "cs2", "kappa", "g", "dg")
+             "nuT", "Rinv", "cs2", "kappa", "g", "dg", "fncdm", "wncdm")
 SCALAR_FIELDS = ("H0", "Om_b", "Om_c", "Om_g", "Om_nu", "Om_L", "R_nu", "f_He",
-                 "nH0", "A_s", "z_reion", "lna_tc", "lna_sw", "tau0", "lna_He3", "n_s")
+                 "nH0", "A_s", "z_reion", "lna_tc", "lna_sw", "tau0", "lna_He3", "n_s", "Om_ncdm")
 
 _D = ctypes.POINTER(ctypes.c_double)
 _L = ctypes.POINTER(ctypes.c_long)
@@ -35,11 +35,11 @@ def lib():
     if _lib is None:
         path = _build.build()
         L = ctypes.CDLL(path)
-        L.orc_scalars.argtypes = [_D, ctypes.c_int, _D]
-        L.orc_background.argtypes = [_D, ctypes.c_int, _D, ctypes.c_int, _D]
-        L.orc_nodes.argtypes = [_D, ctypes.c_int, _D]
+        L.orc_scalars.argtypes = [_D, ctypes.c_int, ctypes.c_double, _D]
+        L.orc_background.argtypes = [_D, ctypes.c_int, ctypes.c_double, _D, ctypes.c_int, _D]
+        L.orc_nodes.argtypes = [_D, ctypes.c_int, ctypes.c_double, _D]
         L.orc_nstate_of.argtypes = [_D]
-        L.orc_lna_start_of.argtypes = [_D, ctypes.c_double]
+        L.orc_lna_start_of.argtypes = [_D, ctypes.c_double, ctypes.c_double]
         L.orc_lna_start_of.restype = ctypes.c_double
         L.orc_trajectory.argtypes = [_D, _D, ctypes.c_double, _D, ctypes.c_int, _D, _D,
                                      ctypes.c_double, _L]
@@ -53,6 +53,7 @@ def lib():
                               _L, ctypes.c_int]
         L.orc_radau_tableau.argtypes = [_D]
         L.orc_pk.argtypes = [_D, _D, _D, ctypes.c_int, ctypes.c_double, _D, ctypes.c_int]
+        L.orc_ncdm_density.argtypes = [_D, ctypes.c_double, ctypes.c_double, _D]
         _lib = L
     return _lib
 
@@ -66,46 +67,50 @@ def _arr(x):
 
 
 def opts(lmax=12, lmax_g=None, lmax_pol=None, lmax_nu=None, scale_sw=1.0, scale_isw=1.0,
-         scale_dop=1.0, scale_pol=1.0, step_c=0.05, step_cap=0.05, hooks=0, max_steps=0):
+         scale_dop=1.0, scale_pol=1.0, step_c=0.05, step_cap=0.05, hooks=0, max_steps=0,
+         m_ncdm=0.0, lmax_ncdm=17):
     """Options vector: hierarchy truncations, source switches (App. A.1), the
-    step schedule of the oracle's integrator and test hooks."""
+    step schedule of the oracle's integrator, test hooks, and one massive
+    neutrino of mass m_ncdm [eV] with hierarchies to lmax_ncdm (m_ncdm = 0:
+    three massless neutrinos only)."""
     lg = lmax if lmax_g is None else lmax_g
     lp = lmax if lmax_pol is None else lmax_pol
     ln = lmax if lmax_nu is None else lmax_nu
+    lm = lmax_ncdm if m_ncdm > 0.0 else 0
     return np.array([lg, lp, ln, scale_sw, scale_isw, scale_dop, scale_pol, step_c, step_cap,
-                     hooks, max_steps], dtype=np.float64)
+                     hooks, max_steps, lm, m_ncdm], dtype=np.float64)
 
 
 def nstate(o):
     return lib().orc_nstate_of(_p(_arr(o)))
 
 
-def scalars(params, hooks=0):
-    out = np.zeros(16)
-    rc = lib().orc_scalars(_p(_arr(params)), hooks, _p(out))
+def scalars(params, hooks=0, m_ncdm=0.0):
+    out = np.zeros(17)
+    rc = lib().orc_scalars(_p(_arr(params)), hooks, float(m_ncdm), _p(out))
     if rc:
         raise RuntimeError("oracle background failed")
     return dict(zip(SCALAR_FIELDS, out))
 
 
-def background(params, lna, hooks=0):
+def background(params, lna, hooks=0, m_ncdm=0.0):
     lna = _arr(np.atleast_1d(lna))
-    out = np.zeros((lna.size, 16))
-    rc = lib().orc_background(_p(_arr(params)), hooks, _p(lna), lna.size, _p(out))
+    out = np.zeros((lna.size, 18))
+    rc = lib().orc_background(_p(_arr(params)), hooks, float(m_ncdm), _p(lna), lna.size, _p(out))
     if rc:
         raise RuntimeError("oracle background failed")
     return {f: out[:, i] for i, f in enumerate(BG_FIELDS)}
 
 
-def nodes(params, n_tau):
+def nodes(params, n_tau, m_ncdm=0.0):
     out = np.zeros((3, n_tau))
-    if lib().orc_nodes(_p(_arr(params)), n_tau, _p(out)):
+    if lib().orc_nodes(_p(_arr(params)), n_tau, float(m_ncdm), _p(out)):
         raise RuntimeError("oracle nodes failed")
     return out[0], out[1], out[2]
 
 
-def lna_start(params, k):
-    return lib().orc_lna_start_of(_p(_arr(params)), float(k))
+def lna_start(params, k, m_ncdm=0.0):
+    return lib().orc_lna_start_of(_p(_arr(params)), float(k), float(m_ncdm))
 
 
 def trajectory(params, o, k, lna_out, y_init=None, lna_init=0.0):
@@ -172,6 +177,15 @@ def run(params, k, n_tau, lmax_cl, o, want=("S", "Delta", "Cl"), nthreads=0):
     if rc:
         raise RuntimeError(f"oracle run failed ({rc})")
     return {"S": S, "Delta": D, "Cl": C, "steps": steps}
+
+
+def ncdm_density(params, m_ncdm, a):
+    """One massive neutrino: (rho, p) / rho_crit today at scale factor a, its
+    relativistic-limit Omega (rho a^4 / rho_crit as a -> 0) and m / T_ncdm."""
+    out = np.zeros(5)
+    if lib().orc_ncdm_density(_p(_arr(params)), float(m_ncdm), float(a), _p(out)):
+        raise RuntimeError("oracle background failed")
+    return dict(rho=out[0], p=out[1], Om_rel=out[2], x1=out[3])
 
 
 def pk(params, k, z, o, nthreads=0):
@@ -248,14 +262,14 @@ def interp_sources(S, k, kt):
 class Cosmo:
     """Handle on one oracle cosmology (background built once)."""
 
-    def __init__(self, params, n_tau=0, hooks=0):
+    def __init__(self, params, n_tau=0, hooks=0, m_ncdm=0.0):
         L = lib()
         L.orc_create.restype = ctypes.c_void_p
-        L.orc_create.argtypes = [_D, ctypes.c_int, ctypes.c_int]
+        L.orc_create.argtypes = [_D, ctypes.c_int, ctypes.c_int, ctypes.c_double]
         L.orc_destroy.argtypes = [ctypes.c_void_p]
         L.orc_h_rhs.argtypes = [ctypes.c_void_p, _D, ctypes.c_double, ctypes.c_double, _D, _D]
         L.orc_h_matrix.argtypes = [ctypes.c_void_p, _D, ctypes.c_double, ctypes.c_double, _D]
-        self._h = L.orc_create(_p(_arr(params)), int(n_tau), int(hooks))
+        self._h = L.orc_create(_p(_arr(params)), int(n_tau), int(hooks), float(m_ncdm))
         if not self._h:
             raise RuntimeError("oracle background failed")
 

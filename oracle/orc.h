@@ -50,6 +50,9 @@ typedef struct {
     double step_cap; /* absolute cap on a step in ln a                  */
     int hooks;
     long max_steps;  /* 0 = unlimited; > 0 stops each mode early (timing samples) */
+    int lmax_ncdm;   /* massive-neutrino hierarchies' truncation (0: none)      */
+    double m_ncdm;   /* one massive neutrino of this mass [eV] (0: none); the
+                        massless species then number two (App. A.1 example)   */
 } orc_opts;
 
 /* Per-cosmology state: derived parameters, thermal-history tables, tau nodes. */
@@ -71,6 +74,10 @@ struct orc_cosmo {
     double lna_tc, lna_He3, lna_sw, lna_700;
     double tau0;
     int hooks;
+    /* one massive neutrino (App. B.3 "Massive neutrinos", App. C.6): mass,
+       temperature today T_ncdm = 0.71611 T_gamma, x = a m / T_ncdm at a = 1,
+       and rho_ncdm / rho_crit = ncdm_pref a^-4 sum_i K_i (1 + e^-q_i) eps_i / q_i^2 */
+    double m_ncdm, T_ncdm_ratio, ncdm_x1, ncdm_pref, Om_ncdm_rel, Om_ncdm;
     /* conformal-time table, uniform in ln a */
     int n_ct; double ct_lna0, ct_dlna; double *ct_tau;
     /* TLA table (x_p, T_m and their ln a derivatives) on two uniform ln a
@@ -88,6 +95,10 @@ struct orc_cosmo {
 typedef struct {
     double a, Hc, dHc;            /* conformal Hubble [1/Mpc] and d/dln a */
     double fc, fb, fg, fnu;       /* rho_i / rho_tot                      */
+    double fncdm, wncdm;          /* massive neutrinos: rho / rho_tot, p / rho */
+    double ncdm_x;                /* a m / T_ncdm                          */
+    double ncdm_n;                /* ncdm_pref a^-4 / (rho_tot / rho_crit): turns the
+                                     momentum sums into fractions of rho_tot */
     double tau;                   /* conformal time [Mpc]                 */
     double xe, dxe;               /* free-electron fraction and d/dln a   */
     double nuT;                   /* 1/(H tau_c) = a n_e sigma_T / H      */
@@ -97,7 +108,7 @@ typedef struct {
 } orc_bg;
 
 /* orc_background.c */
-int orc_cosmo_init(orc_cosmo *c, const double p[6], int n_tau, int hooks);
+int orc_cosmo_init(orc_cosmo *c, const double p[6], int n_tau, int hooks, double m_ncdm);
 void orc_cosmo_free(orc_cosmo *c);
 /* with_thermo: 0 background only, 1 + what the ODE needs, 2 + kappa, g, g' */
 void orc_bg_eval(const orc_cosmo *c, double lna, orc_bg *out, int with_thermo);

@@ -107,9 +107,37 @@ static void hermite_basis(double u, double *h00, double *h10, double *h01, doubl
 
 /* ------------------------------------------------------------------ */
 /* background                                                          */
+/* One massive neutrino (App. B.3 "Massive neutrinos"): energy density and
+   pressure in units of today's critical density by the 5-point Gauss-Laguerre
+   rule the paper gives for the background,
+     rho = (4/pi^2) T^4 a^-4 sum_i K_i (1 + e^-q_i) eps_i / q_i^2,
+     p   = (4/(3 pi^2)) T^4 a^-4 sum_i K_i (1 + e^-q_i) / eps_i,
+   eps_i = sqrt(q_i^2 + x^2), x = a m / T (the distribution is Fermi-Dirac in
+   q: the e^eps of the printed f_0 is read as e^q, which the quadrature
+   weights' q^4 e^q / (1 + e^q)^2 presuppose). */
+static const double NCDM_Q5[5] = {0.583165, 2.0, 4.0, 7.26582, 13.0};
+static const double NCDM_K5[5] = {0.0081201, 0.689407, 2.8063, 2.05156, 0.12681};
+
+static void ncdm_rho_p(const orc_cosmo *c, double a, double *rho, double *p)
+{
+    *rho = *p = 0.0;
+    if (c->ncdm_pref == 0.0) return;
+    const double x = a * c->ncdm_x1, a4 = a * a * a * a;
+    double sr = 0.0, sp = 0.0;
+    for (int i = 0; i < 5; i++) {
+        const double q = NCDM_Q5[i], eps = sqrt(q * q + x * x), w = NCDM_K5[i] * (1.0 + exp(-q));
+        sr += w * eps / (q * q);
+        sp += w / eps;
+    }
+    *rho = c->ncdm_pref * sr / a4;
+    *p = c->ncdm_pref * sp / (3.0 * a4);
+}
+
 static double E2(const orc_cosmo *c, double a)
 {
-    return c->Om_r / (a * a * a * a) + c->Om_m / (a * a * a) + c->Om_L;
+    double rn = 0.0, pn = 0.0;
+    ncdm_rho_p(c, a, &rn, &pn);
+    return (c->Om_g + c->Om_nu) / (a * a * a * a) + c->Om_m / (a * a * a) + c->Om_L + rn;
 }
 
 double orc_Hconf(const orc_cosmo *c, double lna)
@@ -428,9 +456,15 @@ void orc_bg_eval(const orc_cosmo *c, double lna, orc_bg *o, int with_thermo)
     o->Hc = a * c->H0 * sqrt(e2);
     double rg = c->Om_g / (a * a * a * a), rn = c->Om_nu / (a * a * a * a);
     double rb = c->Om_b / (a * a * a), rc = c->Om_c / (a * a * a);
+    double rm = 0.0, pm = 0.0;
+    ncdm_rho_p(c, a, &rm, &pm);
     o->fc = rc / e2; o->fb = rb / e2; o->fg = rg / e2; o->fnu = rn / e2;
-    /* d ln H_conf / d ln a = 1 + (1/2) d ln E^2 / d ln a */
-    o->dHc = o->Hc * (1.0 + 0.5 * (-4.0 * (rg + rn) - 3.0 * (rb + rc)) / e2);
+    o->fncdm = rm / e2;
+    o->wncdm = rm > 0.0 ? pm / rm : 0.0;
+    o->ncdm_x = a * c->ncdm_x1;
+    o->ncdm_n = c->ncdm_pref / (a * a * a * a * e2);
+    /* d ln H_conf / d ln a = 1 + (1/2) d ln E^2 / d ln a, d rho_ncdm / d ln a = -3 (rho + p) */
+    o->dHc = o->Hc * (1.0 + 0.5 * (-4.0 * (rg + rn) - 3.0 * (rb + rc) - 3.0 * (rm + pm)) / e2);
     o->tau = orc_tau_of_lna(c, lna);
     o->Rinv = c->Om_b > 0.0 ? (4.0 / 3.0) * c->Om_g / (c->Om_b * a) : 0.0;
     if (!with_thermo || (c->hooks & ORC_HOOK_EDS_CDM)) {
@@ -507,7 +541,7 @@ static double tau_reion_of(const orc_cosmo *c, double zre, gl_rule *gl)
     return acc;
 }
 
-int orc_cosmo_init(orc_cosmo *c, const double p[6], int n_tau, int hooks)
+int orc_cosmo_init(orc_cosmo *c, const double p[6], int n_tau, int hooks, double m_ncdm)
 {
     memset(c, 0, sizeof(*c));
     gl_rule gl = gl_make();
@@ -515,6 +549,9 @@ int orc_cosmo_init(orc_cosmo *c, const double p[6], int n_tau, int hooks)
     c->n_s = p[3]; c->ln10As = p[4]; c->tau_reio = p[5];
     c->hooks = hooks;
     c->YHe = 0.245; c->TCMB0 = 2.34865418e-4; c->Tnu_ratio = 0.71636856; c->N_nu = 3.0;
+    c->m_ncdm = m_ncdm > 0.0 ? m_ncdm : 0.0;
+    c->T_ncdm_ratio = 0.71611;
+    if (c->m_ncdm > 0.0) c->N_nu = 2.0; /* App. A.1 example: two massless + one massive */
     c->z_re_He = 3.5; c->dz_re_He = 0.5; c->dz_re = 0.5; c->beta_re = 1.5;
     c->R_tc = 1.5e-3; c->R_large = 7e-2; c->k_pivot = 0.05;
     c->A_s = exp(c->ln10As) * 1e-10;
@@ -533,10 +570,19 @@ int orc_cosmo_init(orc_cosmo *c, const double p[6], int n_tau, int hooks)
         c->Om_c = c->omega_cdm / h2;
         c->Om_g = c->rho_g0 / (rho_crit100 * h2);
         c->Om_nu = rho_nu0 / (rho_crit100 * h2);
-        c->Om_r = c->Om_g + c->Om_nu;
+        if (c->m_ncdm > 0.0) {
+            const double Tm = c->T_ncdm_ratio * T, Tm4 = Tm * Tm * Tm * Tm / (O_HBARC * O_HBARC * O_HBARC);
+            c->ncdm_x1 = c->m_ncdm / Tm;
+            c->ncdm_pref = 4.0 / (O_PI * O_PI) * Tm4 / (rho_crit100 * h2);
+            c->Om_ncdm_rel = 7.0 * O_PI * O_PI / 120.0 * Tm4 / (rho_crit100 * h2);
+            double pm;
+            ncdm_rho_p(c, 1.0, &c->Om_ncdm, &pm);
+        }
+        /* Om_r: everything relativistic early on (the base of the conformal-time integral) */
+        c->Om_r = c->Om_g + c->Om_nu + c->Om_ncdm_rel;
         c->Om_m = c->Om_b + c->Om_c;
-        c->Om_L = 1.0 - c->Om_m - c->Om_r;
-        c->R_nu = c->Om_nu / c->Om_r;
+        c->Om_L = 1.0 - c->Om_m - (c->Om_g + c->Om_nu) - c->Om_ncdm;
+        c->R_nu = (c->Om_nu + c->Om_ncdm_rel) / c->Om_r;
     }
     c->f_He = c->YHe / (O_MHE_MH * (1.0 - c->YHe));
     c->nH0 = (1.0 - c->YHe) * c->omega_b * rho_crit100 / O_MH;
@@ -659,4 +705,18 @@ double orc_lna_start(const orc_cosmo *c, double k)
     double target = k / c->R_large;
     if (orc_Hconf(c, c->lna_tc) >= target) return c->lna_tc;
     return bisect(f_Hk, c, target, LNA_MIN, c->lna_tc);
+}
+
+/* Massive-neutrino energy density and pressure at a, in units of today's
+   critical density (for the oracle's pins). */
+int orc_ncdm_density(const double *p, double m_ncdm, double a, double *out)
+{
+    orc_cosmo c;
+    if (orc_cosmo_init(&c, p, 0, 0, m_ncdm)) return -1;
+    ncdm_rho_p(&c, a, &out[0], &out[1]);
+    out[2] = c.Om_ncdm_rel;
+    out[3] = c.ncdm_x1;
+    out[4] = c.h;
+    orc_cosmo_free(&c);
+    return 0;
 }

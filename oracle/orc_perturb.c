@@ -68,7 +68,37 @@
 
 static int i_pol(const orc_opts *o) { return I_G0 + o->lmax_g + 1; }
 static int i_nu(const orc_opts *o) { return i_pol(o) + o->lmax_pol + 1; }
-int orc_nstate(const orc_opts *o) { return i_nu(o) + o->lmax_nu + 1; }
+/* massive neutrinos: bins b = 0..2, Psi_0..Psi_L of bin b at i_ncdm + b (L + 1) */
+static int i_ncdm(const orc_opts *o) { return i_nu(o) + o->lmax_nu + 1; }
+static int n_ncdm(const orc_opts *o) { return o->lmax_ncdm > 0 ? 3 * (o->lmax_ncdm + 1) : 0; }
+int orc_nstate(const orc_opts *o) { return i_ncdm(o) + n_ncdm(o); }
+
+/* Momentum bins of the perturbed massive-neutrino integrals (App. B.3,
+   3-point rule of the paper: int dq q^4 e^q/(1+e^q)^2 (q/eps)^w Psi ~
+   4 sum K_i (q_i/eps_i)^w Psi(q_i)), and d ln f_0 / d ln q = -q / (1 + e^-q). */
+static const double NCDM_Q3[3] = {0.913201, 3.37517, 7.79184};
+static const double NCDM_K3[3] = {0.0687359, 3.31435, 2.29911};
+
+/* delta rho, (rho + p) theta and (rho + p) sigma of the massive neutrinos as
+   fractions of rho_tot (eq. mnu_sum) */
+static void ncdm_sums(const orc_opts *o, const orc_bg *b, double k, const double *y,
+                      double *drho, double *rpth, double *rpsig)
+{
+    *drho = *rpth = *rpsig = 0.0;
+    if (o->lmax_ncdm <= 0) return;
+    const int L = o->lmax_ncdm, i0 = i_ncdm(o);
+    for (int j = 0; j < 3; j++) {
+        const double q = NCDM_Q3[j], eps = sqrt(q * q + b->ncdm_x * b->ncdm_x);
+        const double w = NCDM_K3[j] * (1.0 + exp(-q));
+        const double *Ps = y + i0 + j * (L + 1);
+        *drho += w * eps / (q * q) * Ps[0];
+        *rpth += w / q * k * Ps[1];
+        *rpsig += (2.0 / 3.0) * w / eps * Ps[2];
+    }
+    *drho *= b->ncdm_n;
+    *rpth *= b->ncdm_n;
+    *rpsig *= b->ncdm_n;
+}
 
 static void metric(const orc_opts *o, const orc_bg *b, double k, const double *y,
                    double *hp, double *etap)
@@ -80,6 +110,10 @@ static void metric(const orc_opts *o, const orc_bg *b, double k, const double *y
         + 3.0 * (b->fc * y[I_DC] + b->fb * y[I_DB] + b->fg * y[I_G0] + b->fnu * y[Nn]);
     *etap = 1.5 * b->Hc / (k * k)
         * (b->fb * y[I_TB] + (4.0 / 3.0) * b->fg * y[I_G0 + 1] + (4.0 / 3.0) * b->fnu * y[Nn + 1]);
+    double drho, rpth, rpsig;
+    ncdm_sums(o, b, k, y, &drho, &rpth, &rpsig);
+    *hp += 3.0 * drho;
+    *etap += 1.5 * b->Hc / (k * k) * rpth;
     if (o->hooks & ORC_HOOK_FREEZE_METRIC) { *hp = 0.0; *etap = 0.0; }
 }
 
@@ -142,6 +176,22 @@ void orc_rhs_bg(const orc_opts *o, const orc_bg *b, double k, const double *y, d
     dFn[1] = k * k / Hc * (0.25 * Fn[0] - Fn[2]);
     dFn[2] = (4.0 / 15.0) * Fn[1] / Hc - 0.3 * kH * Fn[3] + (2.0 / 15.0) * hp + 0.8 * etap;
     chain_tail(kH, Hc, b->tau, 0.0, Ln, Fn, dFn);
+
+    /* massive neutrinos (App. C.6), one hierarchy per momentum bin */
+    if (o->lmax_ncdm > 0) {
+        const int L = o->lmax_ncdm, i0 = i_ncdm(o);
+        for (int j = 0; j < 3; j++) {
+            const double q = NCDM_Q3[j], eps = sqrt(q * q + b->ncdm_x * b->ncdm_x);
+            const double v = q * k / (eps * Hc), dlnf = -q / (1.0 + exp(-q));
+            const double *Ps = y + i0 + j * (L + 1);
+            double *dPs = dy + i0 + j * (L + 1);
+            dPs[0] = -v * Ps[1] + hp / 6.0 * dlnf;
+            dPs[1] = v / 3.0 * (Ps[0] - 2.0 * Ps[2]);
+            dPs[2] = v / 5.0 * (2.0 * Ps[1] - 3.0 * Ps[3]) - (hp / 15.0 + 0.4 * etap) * dlnf;
+            for (int l = 3; l < L; l++) dPs[l] = v / (2.0 * l + 1.0) * (l * Ps[l - 1] - (l + 1.0) * Ps[l + 1]);
+            dPs[L] = v * Ps[L - 1] - (L + 1.0) / (Hc * b->tau) * Ps[L];
+        }
+    }
 }
 
 void orc_rhs(const orc_cosmo *c, const orc_opts *o, double k, double lna,
@@ -169,6 +219,20 @@ void orc_initial(const orc_cosmo *c, const orc_opts *o, double k, double lna_i, 
     y[Nn] = dg;
     y[Nn + 1] = tg * (23.0 + 4.0 * Rn) / (15.0 + 4.0 * Rn);
     y[Nn + 2] = 2.0 * C * kt * kt / (3.0 * (15.0 + 4.0 * Rn));
+    /* massive neutrinos, relativistic at the start: the massless neutrinos'
+       delta, theta, sigma carried by each momentum bin (the cited Ma &
+       Bertschinger adiabatic mode) */
+    if (o->lmax_ncdm > 0) {
+        const int L = o->lmax_ncdm, i0 = i_ncdm(o);
+        const double x = exp(lna_i) * c->ncdm_x1;
+        for (int j = 0; j < 3; j++) {
+            const double q = NCDM_Q3[j], eps = sqrt(q * q + x * x), dlnf = -q / (1.0 + exp(-q));
+            double *Ps = y + i0 + j * (L + 1);
+            Ps[0] = -0.25 * y[Nn] * dlnf;
+            Ps[1] = -eps / (3.0 * q * k) * y[Nn + 1] * dlnf;
+            Ps[2] = -0.5 * y[Nn + 2] * dlnf;
+        }
+    }
 }
 
 /* dense A(x): column j = rhs(e_j) */
@@ -316,7 +380,9 @@ static void sources_at(const orc_cosmo *c, const orc_opts *o, double k, double l
     orc_rhs_bg(o, &b, k, y, dy);
     double Hc = b.Hc, k2 = k * k;
     double alpha = Hc * (hp + 6.0 * etap) / (2.0 * k2);
-    double shear = (4.0 / 3.0) * (b.fg * y[I_G0 + 2] + b.fnu * y[Nn + 2]);
+    double drho, rpth, rpsig;
+    ncdm_sums(o, &b, k, y, &drho, &rpth, &rpsig);
+    double shear = (4.0 / 3.0) * (b.fg * y[I_G0 + 2] + b.fnu * y[Nn + 2]) + rpsig;
     double Ha_p = -2.0 * Hc * alpha + y[I_ETA] - 4.5 * Hc * Hc / k2 * shear; /* H alpha' */
     double alpha_p = Ha_p / Hc;
     double thb = y[I_TB], thb_p = dy[I_TB];

@@ -493,3 +493,91 @@ def test_source_interpolation_converges_at_third_order():
         k = np.exp(np.linspace(np.log(1e-3), np.log(0.3), n))
         errs.append(np.abs(O.interp_sources(f(k), k, kt) - f(kt)).max())
     assert errs[0] / errs[1] > 7 and errs[1] / errs[2] > 7, errs
+
+
+# ---- one massive neutrino (App. B.3 "Massive neutrinos", App. C.6) ----
+
+def test_ncdm_quadrature_weights_sum_to_the_fermi_dirac_integral():
+    # both printed rules integrate q^4 e^q / (1 + e^q)^2 = 4 int q^3 / (e^q + 1)
+    # = 7 pi^4 / 30: sum K_i = 7 pi^4 / 120
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = open(os.path.join(root, "oracle", "orc_background.c")).read() + \
+        open(os.path.join(root, "oracle", "orc_perturb.c")).read()
+    for name in ("NCDM_K5", "NCDM_K3"):
+        body = re.search(name + r"\[\d\] = \{([^}]*)\}", src).group(1)
+        K = np.array([float(v) for v in body.split(",")])
+        assert abs(K.sum() / (7 * np.pi ** 4 / 120) - 1) < 2e-7, name
+
+
+@pytest.mark.parametrize("m", [0.06, 1.0])
+def test_ncdm_density_against_the_exact_integral(small_params, m):
+    # rho = (1/pi^2) T^4 a^-4 int q^2 eps / (e^q + 1) dq: the 5-point rule
+    # stays within 1e-3 from the relativistic to the non-relativistic regime
+    from scipy import integrate
+    for a in (1e-7, 1e-4, 1e-2, 1.0):
+        d = O.ncdm_density(small_params, m, a)
+        x = a * d["x1"]
+        I = integrate.quad(lambda q: q * q * np.sqrt(q * q + x * x) / (np.exp(q) + 1), 0, 80,
+                           epsabs=0, epsrel=1e-13, limit=400)[0]
+        exact = d["Om_rel"] / a ** 4 * I / (7 * np.pi ** 4 / 120)
+        assert abs(d["rho"] / exact - 1) < 1e-3, (a, d["rho"] / exact - 1)
+        # pressure: 1/3 of rho when relativistic, <q^2> / (3 x^2) = 4.3 / x^2 of
+        # it when not (<q^2> = 12.9 for a Fermi-Dirac distribution)
+        if x < 1e-3:
+            assert abs(3 * d["p"] / d["rho"] - 1) < 1e-6
+        if x > 100:
+            assert abs(d["p"] / d["rho"] * x ** 2 / 4.3 - 1) < 0.02
+
+
+def test_ncdm_non_relativistic_density_is_m_n(small_params):
+    # at a = 1 a 1 eV neutrino (x ~ 6000) has rho = m n, n = 3 zeta(3) T^3 / (2 pi^2)
+    # (particle and antiparticle); in relativistic units rho_rel = 7 pi^2 T^4 / 120
+    from scipy.special import zeta
+    d = O.ncdm_density(small_params, 1.0, 1.0)
+    ratio = (3 * zeta(3) / (2 * np.pi ** 2)) * d["x1"] / (7 * np.pi ** 2 / 120)  # m n / rho_rel
+    assert abs(d["rho"] / (d["Om_rel"] * ratio) - 1) < 1e-3
+
+
+def test_ncdm_hierarchy_massless_limit(small_params):
+    # m -> 0: eps = q, and every momentum bin's Psi_l is the massless
+    # neutrinos' F_l times -dlnf0/dlnq / 4 (Psi_1 = -dlnf theta / (3k),
+    # Psi_2 = -dlnf sigma / 2), whatever the metric does
+    L = 10
+    o = O.opts(lmax=L, m_ncdm=1e-7, lmax_ncdm=L, step_c=0.02)
+    k = 0.05
+    lna = np.array([-9.0, -7.0, -5.0, -2.0, -0.5])
+    y, _ = O.trajectory(small_params, o, k, lna)
+    iN = 4 + 2 * (L + 1)
+    i0 = iN + L + 1
+    q = np.array([0.913201, 3.37517, 7.79184])
+    dlnf = -q / (1 + np.exp(-q))
+    for j in range(3):
+        Ps = y[:, i0 + j * (L + 1): i0 + (j + 1) * (L + 1)]
+        F = y[:, iN: iN + L + 1]
+        scale = np.abs(F).max(axis=0) * abs(dlnf[j])
+        np.testing.assert_allclose(Ps[:, 0], -0.25 * dlnf[j] * F[:, 0], atol=1e-7 * scale[0])
+        np.testing.assert_allclose(Ps[:, 1], -dlnf[j] * F[:, 1] / (3 * k), atol=1e-7 * scale[1] / k)
+        np.testing.assert_allclose(Ps[:, 2], -0.5 * dlnf[j] * F[:, 2], atol=1e-7 * scale[2])
+        np.testing.assert_allclose(Ps[:, 3:], -0.25 * dlnf[j] * F[:, 3:], atol=1e-7 * scale[3:].max())
+
+
+def test_ncdm_non_relativistic_limit_follows_cdm(small_params):
+    # a heavy neutrino on scales far above its free-streaming length keeps the
+    # adiabatic shape Psi_0(q) = -(1/3) delta_c dlnf0/dlnq, so delta rho_ncdm /
+    # rho_ncdm = delta_c -- up to the 3-point rule's error for this integrand,
+    # (1/3) sum K_i / q_i over sum K_i (1 + e^-q_i) / q_i^2 = 0.9923 instead of 1
+    L = 12
+    m = 2.0
+    o = O.opts(lmax=L, m_ncdm=m, lmax_ncdm=L, step_c=0.02)
+    k = 2e-4
+    y, _ = O.trajectory(small_params, o, k, np.array([0.0]))
+    i0 = 4 + 3 * (L + 1)
+    q = np.array([0.913201, 3.37517, 7.79184])
+    K = np.array([0.0687359, 3.31435, 2.29911])
+    x = O.ncdm_density(small_params, m, 1.0)["x1"]
+    eps = np.sqrt(q * q + x * x)
+    w = K * (1 + np.exp(-q)) * eps / q ** 2
+    dncdm = sum(w[j] * y[0, i0 + j * (L + 1)] for j in range(3)) / w.sum()
+    rule = (K / q).sum() / 3 / (K * (1 + np.exp(-q)) / q ** 2).sum()
+    assert abs(dncdm / y[0, 1] - rule) < 2e-4, (dncdm / y[0, 1], rule)
