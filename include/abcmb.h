@@ -63,6 +63,12 @@ typedef struct {
     double rtol;     /* ODE relative tolerance, (0, 1)                                     */
     double atol;     /* ODE absolute tolerance floor, >= 0                                 */
     double scale_sw, scale_isw, scale_dop, scale_pol; /* source switches (App. A.1)       */
+    double m_ncdm;   /* one massive neutrino of this mass [eV] (App. B.3, App. C.6); 0: all
+                        three neutrinos massless.  With a mass the massless species number
+                        two and the massive one has T = 0.71611 T_gamma (App. A.1 example) */
+    int lmax_ncdm;   /* its momentum-bin hierarchies' truncation: 0 when m_ncdm = 0, else
+                        3..63 (App. A.1 l_max_massive_nu, default 17)                      */
+    int reserved_;   /* zero                                                               */
 } abcmb_options;
 
 /* Fill *o with the defaults used by the library's tests: hierarchies 12,
@@ -103,7 +109,11 @@ enum {
     ABCMB_S_STATUS = 0, ABCMB_S_H0, ABCMB_S_OMB, ABCMB_S_OMC, ABCMB_S_OMG, ABCMB_S_OMNU,
     ABCMB_S_OML, ABCMB_S_RNU, ABCMB_S_FHE, ABCMB_S_NH0, ABCMB_S_AS, ABCMB_S_NS,
     ABCMB_S_ZREION, ABCMB_S_LNA_TC, ABCMB_S_LNA_SW, ABCMB_S_TAU0, ABCMB_S_LNA_HE3,
-    ABCMB_S_LNA_700, ABCMB_S_NTAU, ABCMB_S_COUNT
+    ABCMB_S_LNA_700, ABCMB_S_NTAU,
+    ABCMB_S_NCDM_PREF, /* massive neutrino: rho / rho_crit = PREF a^-4 sum_i K_i (1 + e^-q_i) eps_i / q_i^2 */
+    ABCMB_S_NCDM_X1,   /* m / T_ncdm (eps_i = sqrt(q_i^2 + (a X1)^2))                             */
+    ABCMB_S_OMNCDM_REL, /* its relativistic-limit density parameter                               */
+    ABCMB_S_COUNT
 };
 
 /*

@@ -89,9 +89,22 @@ struct ModeCtx {
     const double *rec, *tab, *ot, *nodes;
     double k, sw[3];
     int n_tau;
+    // massive neutrino: m / T_ncdm and PREF H0^2 (0 without one); see bg_at
+    double ncdm_x1 = 0.0, ncdm_pH = 0.0;
 };
 
-ABCMB_HD Bg10 bg_at(const ModeCtx &c, double lna) { return bg_eval(c.ot, hw_at(lna)); }
+// the ten table quantities at ln a, and the massive neutrino's x = a m / T and
+// nn = PREF a^-4 / E^2 = PREF H0^2 / (a^2 H_conf^2) there
+ABCMB_HD Bg10 bg_at(const ModeCtx &c, double lna)
+{
+    Bg10 b = bg_eval(c.ot, hw_at(lna));
+    if (c.ncdm_pH > 0.0) {
+        const double a = exp(lna), hc = b.v[B_HC];
+        b.nx = a * c.ncdm_x1;
+        b.nn = c.ncdm_pH / (a * a * hc * hc);
+    }
+    return b;
+}
 
 ABCMB_HD NodeD node_at(const ModeCtx &c, int n)
 {
@@ -197,11 +210,12 @@ ABCMB_HD void emit_sources(const ModeCtx &c, int n, Vec y, double *S)
     }
 }
 
-// Forward with the tape.  Error control as the four-lanes kernel (group
-// floors, slaved moments excluded while h / (H tau_c) > kSlavedHnu in the
-// implicit regime).
+// Forward with the tape (record: false runs the same integration without
+// writing the tape and checkpoints, which mb may then leave out).  Error
+// control as the four-lanes kernel (group floors, slaved moments excluded
+// while h / (H tau_c) > kSlavedHnu in the implicit regime).
 ABCMB_HD FwdResult fwd_taped(const ModeCtx &c, const ModeBufs &mb, double rtol, double atol, int max_steps,
-                             double *S)
+                             double *S, bool record = true)
 {
     const OdeDims &d = c.d;
     FwdResult r = {ABCMB_OK, 0, 0, 0};
@@ -235,7 +249,7 @@ ABCMB_HD FwdResult fwd_taped(const ModeCtx &c, const ModeBufs &mb, double rtol, 
     Vec Y = wv(mb, d, V_Y);
     {
         const Herm Hi = herm_at(x);
-        initial_fwd(d, c.k, herm_val(c.tab, Hi, C_TAU, C_DTAU), cz.R_nu, Y);
+        initial_fwd(d, c.k, herm_val(c.tab, Hi, C_TAU, C_DTAU), cz.R_nu, Y, exp(x) * c.ncdm_x1);
     }
     int node = 0;
     double h = 1e-3;
@@ -283,9 +297,9 @@ ABCMB_HD FwdResult fwd_taped(const ModeCtx &c, const ModeBufs &mb, double rtol, 
         }
         if (!(err == err) || (jacc == 0 && err > 1e300)) { r.status = ABCMB_E_NONFINITE; break; }
         if (jacc) {
-            if (r.accepted >= kTapeCap) { r.status = ABCMB_E_MAX_STEPS; break; }
-            if (r.accepted % kSeg == 0) vcopy(d, Y, ckv(mb, d, r.accepted / kSeg));
-            if (ln_id() == 0) {
+            if (record && r.accepted >= kTapeCap) { r.status = ABCMB_E_MAX_STEPS; break; }
+            if (record && r.accepted % kSeg == 0) vcopy(d, Y, ckv(mb, d, r.accepted / kSeg));
+            if (record && ln_id() == 0) {
                 double *tp = mb.tape + 3 * (long)r.accepted;
                 tp[0] = x;
                 tp[1] = H;

@@ -23,7 +23,34 @@ enum { B_IH = 0, B_IHT, B_FC, B_FB, B_FG, B_FNU, B_NU, B_RNU, B_CS2, B_HC, B_N }
 
 struct Bg10 {
     double v[B_N];
+    // massive neutrino at this point (not table columns): x = a m / T_ncdm and
+    // nn = PREF a^-4 / (rho_tot / rho_crit), which turns the momentum sums into
+    // fractions of rho_tot (both 0 without one)
+    double nx = 0.0, nn = 0.0;
 };
+
+// Momentum bins of the perturbed massive-neutrino integrals (App. B.3, the
+// paper's 3-point rule) and d ln f_0 / d ln q = -q / (1 + e^-q) at them.
+ABCMB_HD double ncdm_q(int j) { return j == 0 ? 0.913201 : (j == 1 ? 3.37517 : 7.79184); }
+ABCMB_HD double ncdm_k(int j) { return j == 0 ? 0.0687359 : (j == 1 ? 3.31435 : 2.29911); }
+
+// delta rho, (rho + p) theta / k and (rho + p) sigma of the massive neutrinos
+// as fractions of rho_tot (eq. mnu_sum); y[d.iM + j (Lm + 1) + l] = Psi_l(q_j)
+ABCMB_HD void ncdm_sums(const OdeDims &d, const Bg10 &b, Vec y, double &drho, double &rpth_k, double &rpsig)
+{
+    drho = rpth_k = rpsig = 0.0;
+    if (d.Lm <= 0) return;
+    for (int j = 0; j < 3; j++) {
+        const double q = ncdm_q(j), eps = sqrt(q * q + b.nx * b.nx), w = ncdm_k(j) * (1.0 + exp(-q));
+        const int i0 = d.iM + j * (d.Lm + 1);
+        drho += w * eps / (q * q) * y[i0];
+        rpth_k += w / q * y[i0 + 1];
+        rpsig += (2.0 / 3.0) * w / eps * y[i0 + 2];
+    }
+    drho *= b.nn;
+    rpth_k *= b.nn;
+    rpsig *= b.nn;
+}
 
 // cubic Hermite on the ODE table (20 doubles per row: value, d/dln a pairs)
 struct HW {
@@ -166,12 +193,25 @@ ABCMB_HD void op_E(const OdeDims &d, const StreamCoef &sc, double k, const Bg10 
 {
     const double ih = b.v[B_IH], kH = k * ih, ik = 1.0 / k;
     const double eta = y[0], dc = y[1], db = y[2], tb = y[3];
+    double drho, rpth_k, rpsig;
+    ncdm_sums(d, b, y, drho, rpth_k, rpsig);
     const double hp = 2.0 * kH * kH * eta +
-                      3.0 * (b.v[B_FC] * dc + b.v[B_FB] * db + b.v[B_FG] * y[d.iF] + b.v[B_FNU] * y[d.iN]);
-    const double ep = 1.5 * b.v[B_HC] * ik * (b.v[B_FB] * tb * ik + b.v[B_FG] * y[d.iF + 1] + b.v[B_FNU] * y[d.iN + 1]);
+                      3.0 * (b.v[B_FC] * dc + b.v[B_FB] * db + b.v[B_FG] * y[d.iF] + b.v[B_FNU] * y[d.iN] + drho);
+    const double ep = 1.5 * b.v[B_HC] * ik *
+                      (b.v[B_FB] * tb * ik + b.v[B_FG] * y[d.iF + 1] + b.v[B_FNU] * y[d.iN + 1] + rpth_k);
     for (int i = ln_id(); i < d.N; i += ln_n()) {
         double f;
-        if (i < 4) {
+        if (i >= d.iM) {
+            // massive neutrinos (App. C.6), bin j, moment l
+            const int j = (i - d.iM) / (d.Lm + 1), l = i - d.iM - j * (d.Lm + 1), L = d.Lm;
+            const double q = ncdm_q(j), eps = sqrt(q * q + b.nx * b.nx);
+            const double v = q * k / eps * ih, dlnf = -q / (1.0 + exp(-q));
+            if (l == 0) f = -v * y[i + 1] + hp / 6.0 * dlnf;
+            else if (l == 1) f = v / 3.0 * (y[i - 1] - 2.0 * y[i + 1]);
+            else if (l == 2) f = v / 5.0 * (2.0 * y[i - 1] - 3.0 * y[i + 1]) - (hp / 15.0 + 0.4 * ep) * dlnf;
+            else if (l < L) f = v / (2.0 * l + 1.0) * (l * y[i - 1] - (l + 1.0) * y[i + 1]);
+            else f = v * y[i - 1] - (L + 1.0) * b.v[B_IHT] * y[i];
+        } else if (i < 4) {
             f = i == 0 ? ep : (i == 1 ? -0.5 * hp : (i == 2 ? -ih * tb - 0.5 * hp : -tb + b.v[B_CS2] * k * k * ih * db));
         } else {
             int ch, l, L, i0;
@@ -198,7 +238,9 @@ ABCMB_HD void op_Et(const OdeDims &d, const StreamCoef &sc, double k, const Bg10
     const double ce = 1.5 * b.v[B_HC] * ik;
     for (int i = ln_id(); i < d.N; i += ln_n()) {
         double g;
-        if (i < 4) {
+        if (i >= d.iM) {
+            g = 0.0; // the adjoint covers the massless-neutrino path only
+        } else if (i < 4) {
             g = i == 0 ? whp * 2.0 * kH * kH
                        : (i == 1 ? whp * 3.0 * b.v[B_FC]
                                  : (i == 2 ? whp * 3.0 * b.v[B_FB] + v[3] * b.v[B_CS2] * k * k * ih
@@ -239,7 +281,7 @@ ABCMB_HD void op_E_bgrad(const OdeDims &d, const StreamCoef &sc, double k, const
     const double wep = v[0] + 1.6 * (v[d.iF + 2] + v[d.iN + 2]);
     const double ce = 1.5 * b.v[B_HC] * ik;
     double stream = 0.0;
-    for (int i = 4 + ln_id(); i < d.N; i += ln_n()) {
+    for (int i = 4 + ln_id(); i < d.iM; i += ln_n()) {
         int ch, l, L, i0;
         chain_of(d, i, ch, l, L, i0);
         double A, Bc;
@@ -374,10 +416,12 @@ ABCMB_HD void sources_fwd(const OdeDims &d, double k, const Bg10 &b, const NodeD
     const double F0 = y[d.iF], F1 = y[d.iF + 1], F2 = y[d.iF + 2], G0 = y[d.iG], G2 = y[d.iG + 2];
     const double N0 = y[d.iN], N1 = y[d.iN + 1], N2 = y[d.iN + 2];
     const double fc = b.v[B_FC], fb = b.v[B_FB], fg = b.v[B_FG], fn = b.v[B_FNU];
-    const double hp = 2.0 * kH * kH * eta + 3.0 * (fc * dc + fb * db + fg * F0 + fn * N0);
-    const double ep = 1.5 / kH * (fb * tb / k + fg * F1 + fn * N1);
+    double drho, rpth_k, rpsig;
+    ncdm_sums(d, b, y, drho, rpth_k, rpsig);
+    const double hp = 2.0 * kH * kH * eta + 3.0 * (fc * dc + fb * db + fg * F0 + fn * N0 + drho);
+    const double ep = 1.5 / kH * (fb * tb / k + fg * F1 + fn * N1 + rpth_k);
     const double alpha = Hc * (hp + 6.0 * ep) / (2.0 * k2);
-    const double shear = (2.0 / 3.0) * (fg * F2 + fn * N2);
+    const double shear = (2.0 / 3.0) * (fg * F2 + fn * N2) + rpsig;
     const double Hap = -2.0 * Hc * alpha + eta - 4.5 * Hc * Hc / k2 * shear;
     const double ap = Hap / Hc;
     const double tbp = -tb + b.v[B_CS2] * k2 * db / Hc + b.v[B_RNU] * (0.75 * k * F1 - tb);
@@ -503,14 +547,26 @@ ABCMB_HD void sources_rev(const OdeDims &d, double k, const Bg10 &b, const NodeD
 }
 
 // adiabatic initial state (the formulas of initial_state, R_nu given explicitly)
-ABCMB_HD void initial_fwd(const OdeDims &d, double k, double tau_i, double Rn, Vec y)
+// x0: the massive neutrino's a m / T_ncdm at the start; each momentum bin
+// carries the massless neutrinos' adiabatic F_0..F_2 (the species is
+// relativistic then): Psi_0 = -F_0 dlnf / 4, Psi_1 = -eps F_1 dlnf / (4 q),
+// Psi_2 = -F_2 dlnf / 4
+ABCMB_HD void initial_fwd(const OdeDims &d, double k, double tau_i, double Rn, Vec y, double x0 = 0.0)
 {
     const double C = 0.5, kt = k * tau_i;
     const double dg = -(2.0 / 3.0) * C * kt * kt;
     const double F1 = -(2.0 / 27.0) * C * kt * kt * kt;
     const double tg = -C * k * kt * kt * kt / 18.0;
+    const double N1 = F1 * (23.0 + 4.0 * Rn) / (15.0 + 4.0 * Rn), N2 = (4.0 / 3.0) * C * kt * kt / (15.0 + 4.0 * Rn);
     for (int i = ln_id(); i < d.N; i += ln_n()) {
         double v = 0.0;
+        if (i >= d.iM) {
+            const int j = (i - d.iM) / (d.Lm + 1), l = i - d.iM - j * (d.Lm + 1);
+            const double q = ncdm_q(j), eps = sqrt(q * q + x0 * x0), dlnf = -q / (1.0 + exp(-q));
+            v = l == 0 ? -0.25 * dg * dlnf : (l == 1 ? -eps / (4.0 * q) * N1 * dlnf : (l == 2 ? -0.25 * N2 * dlnf : 0.0));
+            y[i] = v;
+            continue;
+        }
         if (i == 0) v = 2.0 * C - C * kt * kt * (5.0 + 4.0 * Rn) / (6.0 * (15.0 + 4.0 * Rn));
         else if (i == 1 || i == 2) v = 0.75 * dg;
         else if (i == 3) v = tg;

@@ -52,6 +52,7 @@ constexpr double kYHe = 0.245;
 constexpr double kTcmb0 = 2.34865418e-4; // eV
 constexpr double kTnuRatio = 0.71636856;
 constexpr double kNnu = 3.0;
+constexpr double kTncdmRatio = 0.71611; // massive neutrino temperature today / T_gamma (App. A.1)
 constexpr double kZreHe = 3.5, kDzReHe = 0.5, kDzRe = 0.5, kBetaRe = 1.5;
 constexpr double kRtc = 1.5e-3, kRlarge = 7e-2, kKpivot = 0.05;
 constexpr double kLna700 = -6.55250788703459; // ln(1/701)
@@ -82,7 +83,31 @@ struct Cosmo {
     double R_nu, f_He, nH0, A_s, n_s;
     double z_reion, lna_tc, lna_sw, tau0, lna_He3;
     double rho_g0; // photon energy density today, eV/cm^3
+    // one massive neutrino (0 when absent); Om_r includes its relativistic limit
+    double ncdm_pref, ncdm_x1, Om_ncdm_rel;
 };
+
+// Massive neutrino (App. B.3 "Massive neutrinos"): energy density and pressure
+// in units of today's critical density, by the paper's 5-point rule for the
+// background, rho = PREF a^-4 sum_i K_i (1 + e^-q_i) eps_i / q_i^2 and
+// p = PREF a^-4 sum_i K_i (1 + e^-q_i) / (3 eps_i), eps_i = sqrt(q_i^2 + x^2),
+// x = a m / T_ncdm (Fermi-Dirac in the comoving momentum q).
+ABCMB_HD void ncdm_rho_p(const Cosmo &c, double a, double *rho, double *p)
+{
+    *rho = *p = 0.0;
+    if (c.ncdm_pref == 0.0) return;
+    const double q5[5] = {0.583165, 2.0, 4.0, 7.26582, 13.0};
+    const double k5[5] = {0.0081201, 0.689407, 2.8063, 2.05156, 0.12681};
+    const double x = a * c.ncdm_x1, a4 = a * a * a * a;
+    double sr = 0.0, sp = 0.0;
+    for (int i = 0; i < 5; i++) {
+        const double q = q5[i], eps = sqrt(q * q + x * x), w = k5[i] * (1.0 + exp(-q));
+        sr += w * eps / (q * q);
+        sp += w / eps;
+    }
+    *rho = c.ncdm_pref * sr / a4;
+    *p = c.ncdm_pref * sp / (3.0 * a4);
+}
 
 ABCMB_HD Cosmo load_cosmo(const double *rec)
 {
@@ -106,6 +131,10 @@ ABCMB_HD Cosmo load_cosmo(const double *rec)
     c.tau0 = rec[ABCMB_S_TAU0];
     c.lna_He3 = rec[ABCMB_S_LNA_HE3];
     c.rho_g0 = 0.0;
+    c.ncdm_pref = rec[ABCMB_S_NCDM_PREF];
+    c.ncdm_x1 = rec[ABCMB_S_NCDM_X1];
+    c.Om_ncdm_rel = rec[ABCMB_S_OMNCDM_REL];
+    c.Om_r = c.Om_g + c.Om_nu + c.Om_ncdm_rel;
     return c;
 }
 
@@ -120,22 +149,26 @@ ABCMB_HD BgClosed closed_bg(const Cosmo &c, double lna)
     b.a = exp(lna);
     b.inv_a = 1.0 / b.a;
     double ia = b.inv_a, ia3 = ia * ia * ia, ia4 = ia3 * ia;
-    double rr = c.Om_r * ia4, rm = c.Om_m * ia3;
-    double e2 = rr + rm + c.Om_L;
+    double rr = (c.Om_g + c.Om_nu) * ia4, rm = c.Om_m * ia3;
+    double rn, pn;
+    ncdm_rho_p(c, b.a, &rn, &pn);
+    double e2 = rr + rm + c.Om_L + rn;
     double ie2 = 1.0 / e2;
     b.Hc = b.a * c.H0 * sqrt(e2);
     b.fc = c.Om_c * ia3 * ie2;
     b.fb = c.Om_b * ia3 * ie2;
     b.fg = c.Om_g * ia4 * ie2;
     b.fnu = c.Om_nu * ia4 * ie2;
-    b.dlnHc = 1.0 - (2.0 * rr + 1.5 * rm) * ie2;
+    b.dlnHc = 1.0 - (2.0 * rr + 1.5 * rm + 1.5 * (rn + pn)) * ie2;
     return b;
 }
 
 ABCMB_HD double hconf(const Cosmo &c, double lna)
 {
     double a = exp(lna), ia = 1.0 / a;
-    return a * c.H0 * sqrt(c.Om_r * ia * ia * ia * ia + c.Om_m * ia * ia * ia + c.Om_L);
+    double rn, pn;
+    ncdm_rho_p(c, a, &rn, &pn);
+    return a * c.H0 * sqrt((c.Om_g + c.Om_nu) * ia * ia * ia * ia + c.Om_m * ia * ia * ia + c.Om_L + rn);
 }
 
 // exact radiation+matter conformal time
@@ -463,7 +496,7 @@ ABCMB_HD double tau_reion_par(const Cosmo &c, double zre, int lane, int nl)
 }
 
 // ---- the builder (lane = 0..nl-1 of the warp that owns this cosmology) ----
-ABCMB_HD void build_background(const double *p, double *rec, int n_tau, int lane, int nl)
+ABCMB_HD void build_background(const double *p, double *rec, int n_tau, int lane, int nl, double m_ncdm = 0.0)
 {
     double *tab = rec + ABCMB_BG_TABLE;
     double *otab = rec + ABCMB_BG_ODETAB;
@@ -480,15 +513,27 @@ ABCMB_HD void build_background(const double *p, double *rec, int n_tau, int lane
     const double T0 = kTcmb0, Tn = kTnuRatio * kTcmb0;
     const double hbc3 = kHbarC * kHbarC * kHbarC;
     c.rho_g0 = kPi * kPi / 15.0 * T0 * T0 * T0 * T0 / hbc3;
-    const double rho_nu0 = kNnu * 7.0 * kPi * kPi / 120.0 * Tn * Tn * Tn * Tn / hbc3;
+    // one massive neutrino: two massless species remain (App. A.1 example)
+    const double n_massless = m_ncdm > 0.0 ? 2.0 : kNnu;
+    const double rho_nu0 = n_massless * 7.0 * kPi * kPi / 120.0 * Tn * Tn * Tn * Tn / hbc3;
     c.Om_b = p[0] / h2;
     c.Om_c = p[1] / h2;
     c.Om_g = c.rho_g0 / (rho_crit100 * h2);
     c.Om_nu = rho_nu0 / (rho_crit100 * h2);
-    c.Om_r = c.Om_g + c.Om_nu;
+    c.ncdm_pref = c.ncdm_x1 = c.Om_ncdm_rel = 0.0;
+    double Om_ncdm = 0.0;
+    if (m_ncdm > 0.0) {
+        const double Tm = kTncdmRatio * kTcmb0, Tm4 = Tm * Tm * Tm * Tm / hbc3;
+        c.ncdm_x1 = m_ncdm / Tm;
+        c.ncdm_pref = 4.0 / (kPi * kPi) * Tm4 / (rho_crit100 * h2);
+        c.Om_ncdm_rel = 7.0 * kPi * kPi / 120.0 * Tm4 / (rho_crit100 * h2);
+        double pn;
+        ncdm_rho_p(c, 1.0, &Om_ncdm, &pn);
+    }
+    c.Om_r = c.Om_g + c.Om_nu + c.Om_ncdm_rel; // everything relativistic early on
     c.Om_m = c.Om_b + c.Om_c;
-    c.Om_L = 1.0 - c.Om_m - c.Om_r;
-    c.R_nu = c.Om_nu / c.Om_r;
+    c.Om_L = 1.0 - c.Om_m - (c.Om_g + c.Om_nu) - Om_ncdm;
+    c.R_nu = (c.Om_nu + c.Om_ncdm_rel) / c.Om_r;
     c.f_He = kYHe / (kMHeOverMH * (1.0 - kYHe));
     c.nH0 = (1.0 - kYHe) * p[0] * rho_crit100 / kMH;
     c.A_s = exp(p[4]) * 1.0e-10;
@@ -787,6 +832,9 @@ ABCMB_HD void build_background(const double *p, double *rec, int n_tau, int lane
         rec[ABCMB_S_LNA_HE3] = c.lna_He3;
         rec[ABCMB_S_LNA_700] = kLna700;
         rec[ABCMB_S_NTAU] = n_tau;
+        rec[ABCMB_S_NCDM_PREF] = c.ncdm_pref;
+        rec[ABCMB_S_NCDM_X1] = c.ncdm_x1;
+        rec[ABCMB_S_OMNCDM_REL] = c.Om_ncdm_rel;
     }
 }
 

@@ -81,6 +81,8 @@ __device__ inline ModeCtx mode_ctx(const OdeDims &d, const StreamCoef &sc, const
     c.sw[1] = sw[1];
     c.sw[2] = sw[2];
     c.n_tau = (int)c.rec[ABCMB_S_NTAU];
+    c.ncdm_x1 = c.rec[ABCMB_S_NCDM_X1];
+    c.ncdm_pH = c.rec[ABCMB_S_NCDM_PREF] * c.rec[ABCMB_S_H0] * c.rec[ABCMB_S_H0];
     return c;
 }
 
@@ -118,6 +120,48 @@ taped_kernel(int B, int Nk, const double *__restrict__ bg, long len, const doubl
         res[2] = r.accepted;
         res[3] = r.emit0;
         status[(long)b * Nk + kidx] = r.status;
+    }
+}
+
+// The forward alone, one warp per mode, working vectors from a workspace of
+// V_COUNT x N doubles per mode: the path for a massive neutrino (its three
+// momentum-bin hierarchies do not fit the four-lanes kernel's layout).
+__global__ void __launch_bounds__(kGradThreads)
+plain_kernel(int B, int Nk, const double *__restrict__ bg, long len, const double *__restrict__ kv, int Lg, int Lp,
+             int Ln, int Lm, double rtol, double atol, int max_steps, double s_sw, double s_isw, double s_dop,
+             double *S, int *status, int *steps, double *work)
+{
+    __shared__ double sa[129], sb[129];
+    for (int l = threadIdx.x; l < 129; l += blockDim.x) {
+        sa[l] = (double)l / (2.0 * l + 1.0);
+        sb[l] = (l + 1.0) / (2.0 * l + 1.0);
+    }
+    __syncthreads();
+    const OdeDims d = ode_dims(Lg, Lp, Ln, Lm);
+    const long M = (long)B * Nk;
+    const long mi = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; // one warp per mode
+    if (mi >= M) return;
+    const int kidx = Nk - 1 - (int)(mi / B), b = (int)(mi % B);
+    const double sw[3] = {s_sw, s_isw, s_dop};
+    const ModeCtx c = mode_ctx(d, StreamCoef{sa, sb}, bg, len, b, kv[kidx], sw);
+    ModeBufs mb;
+    mb.work = work + mi * V_COUNT * d.N;
+    mb.seg = mb.ckpt = mb.tape = nullptr;
+    mb.stride = 1;
+    double *Sm = S + ((long)b * Nk + kidx) * (long)c.n_tau * 3;
+    FwdResult r = {ABCMB_OK, 0, 0, 0};
+    if (c.rec[ABCMB_S_STATUS] != 0.0) {
+        r.status = ABCMB_E_NONFINITE;
+        for (int n = ln_id(); n < 3 * c.n_tau; n += ln_n()) Sm[n] = 0.0;
+    } else {
+        r = fwd_taped(c, mb, rtol, atol, max_steps, Sm, false);
+    }
+    if (ln_id() == 0) {
+        status[(long)b * Nk + kidx] = r.status;
+        if (steps) {
+            steps[2 * ((long)b * Nk + kidx)] = r.steps;
+            steps[2 * ((long)b * Nk + kidx) + 1] = 0; // substeps not counted on this path
+        }
     }
 }
 
@@ -337,6 +381,27 @@ record_vjp_kernel(int B, long len, const double *__restrict__ recbar, const doub
 } // namespace adj
 } // namespace abcmb
 
+namespace abcmb {
+size_t perturb_warp_bytes(int B, int Nk, const abcmb_options *o)
+{
+    const OdeDims d = ode_dims(o->lmax_g, o->lmax_pol, o->lmax_nu, o->lmax_ncdm);
+    return (size_t)B * Nk * adj::V_COUNT * d.N * sizeof(double);
+}
+
+// abcmb_perturb's path for a massive neutrino (arguments validated by the caller)
+int launch_perturb_warp(int B, const double *bg, const double *k, int Nk, const abcmb_options *o, double *S,
+                        int *mode_status, int *steps, double *work, cudaStream_t s)
+{
+    const long len = (long)ABCMB_BG_NODES + 8L * o->n_tau, M = (long)B * Nk;
+    const long blocks = (M * 32 + adj::kGradThreads - 1) / adj::kGradThreads;
+    if (blocks > 2147483647L) return ABCMB_E_INVALID_ARG;
+    adj::plain_kernel<<<(unsigned)blocks, adj::kGradThreads, 0, s>>>(
+        B, Nk, bg, len, k, o->lmax_g, o->lmax_pol, o->lmax_nu, o->lmax_ncdm, o->rtol, o->atol, o->max_steps,
+        o->scale_sw, o->scale_isw, o->scale_dop, S, mode_status, steps, work);
+    return cudaGetLastError() == cudaSuccess ? ABCMB_OK : ABCMB_E_CUDA;
+}
+} // namespace abcmb
+
 // ---------------------------------------------------------------- C ABI
 extern "C" size_t abcmb_bg_doubles(const abcmb_options *o);
 extern "C" int abcmb_validate_options(const abcmb_options *o);
@@ -354,6 +419,7 @@ extern "C" int abcmb_perturb_taped(int B, const double *bg, const double *k, int
 {
     if (B < 1 || Nk < 1 || !bg || !k || !S || !mode_status || !workspace || abcmb_validate_options(o) != ABCMB_OK)
         return ABCMB_E_INVALID_ARG;
+    if (o->m_ncdm > 0.0) return ABCMB_E_INVALID_ARG; // the adjoint covers massless neutrinos
     if (workspace_bytes < abcmb_grad_workspace_bytes(B, Nk, o) || ((size_t)workspace & 255) != 0)
         return ABCMB_E_INVALID_ARG;
     const long len = (long)abcmb_bg_doubles(o), M = (long)B * Nk;
@@ -371,6 +437,7 @@ extern "C" int abcmb_perturb_adjoint(int B, const double *bg, const double *k, i
 {
     if (B < 1 || Nk < 1 || !bg || !k || !Sbar || !workspace || !recbar || abcmb_validate_options(o) != ABCMB_OK)
         return ABCMB_E_INVALID_ARG;
+    if (o->m_ncdm > 0.0) return ABCMB_E_INVALID_ARG;
     if (workspace_bytes < abcmb_grad_workspace_bytes(B, Nk, o) || ((size_t)workspace & 255) != 0)
         return ABCMB_E_INVALID_ARG;
     const long len = (long)abcmb_bg_doubles(o), M = (long)B * Nk;

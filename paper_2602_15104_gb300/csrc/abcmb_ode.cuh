@@ -57,16 +57,18 @@ constexpr double kSlavedHnu = 100.0;
 struct OdeDims {
     int Lg, Lp, Ln, N;
     int iF, iG, iN; // first index of each chain
+    int Lm, iM;     // massive neutrinos: 3 momentum bins of Psi_0..Psi_Lm from iM (Lm = 0: none)
 };
 
-ABCMB_HD OdeDims ode_dims(int Lg, int Lp, int Ln)
+ABCMB_HD OdeDims ode_dims(int Lg, int Lp, int Ln, int Lm = 0)
 {
     OdeDims d;
-    d.Lg = Lg; d.Lp = Lp; d.Ln = Ln;
+    d.Lg = Lg; d.Lp = Lp; d.Ln = Ln; d.Lm = Lm;
     d.iF = 4;
     d.iG = d.iF + Lg + 1;
     d.iN = d.iG + Lp + 1;
-    d.N = d.iN + Ln + 1;
+    d.iM = d.iN + Ln + 1;
+    d.N = d.iM + (Lm > 0 ? 3 * (Lm + 1) : 0);
     return d;
 }
 

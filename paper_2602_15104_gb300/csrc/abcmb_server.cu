@@ -154,6 +154,7 @@ extern "C" int abcmb_server_create(void *arena, size_t arena_bytes, int n_slots,
     abcmb_options r = *o;
     r.lmax_cl = max_lmax_cl;
     if (abcmb_validate_options(&r) != ABCMB_OK) return ABCMB_E_INVALID_ARG;
+    if (o->m_ncdm > 0.0) return ABCMB_E_INVALID_ARG; // served requests use the on-chip path
     // requests run the on-chip perturbation path, which needs no workspace
     if (abcmb_perturb_workspace_bytes(1, 2, o) != 0) return ABCMB_E_INVALID_ARG;
     *out = nullptr;

@@ -23,11 +23,11 @@ namespace abcmb {
 
 // one warp (32 threads) per cosmology
 __global__ void __launch_bounds__(32) background_kernel(int B, const double *__restrict__ params, double *bg,
-                                                         long len, int n_tau)
+                                                         long len, int n_tau, double m_ncdm)
 {
     const int b = blockIdx.x;
     if (b >= B) return;
-    build_background(params + (long)b * ABCMB_NPARAM, bg + (long)b * len, n_tau, threadIdx.x, 32);
+    build_background(params + (long)b * ABCMB_NPARAM, bg + (long)b * len, n_tau, threadIdx.x, 32, m_ncdm);
 }
 
 constexpr int kLmaxHier = 128;
@@ -135,6 +135,9 @@ extern "C" void abcmb_default_options(abcmb_options *o)
     o->rtol = 1e-6;
     o->atol = 1e-12;
     o->scale_sw = o->scale_isw = o->scale_dop = o->scale_pol = 1.0;
+    o->m_ncdm = 0.0;
+    o->lmax_ncdm = 0;
+    o->reserved_ = 0;
 }
 
 extern "C" int abcmb_validate_options(const abcmb_options *o)
@@ -147,10 +150,17 @@ extern "C" int abcmb_validate_options(const abcmb_options *o)
     if (o->n_tau < 8 || o->n_tau > 65536) return ABCMB_E_INVALID_ARG;
     if (o->max_steps < 1) return ABCMB_E_INVALID_ARG;
     if (!(o->rtol > 0.0 && o->rtol < 1.0) || !(o->atol >= 0.0)) return ABCMB_E_INVALID_ARG;
+    if (!(o->m_ncdm >= 0.0 && o->m_ncdm <= 100.0)) return ABCMB_E_INVALID_ARG;
+    if (o->m_ncdm == 0.0 ? o->lmax_ncdm != 0 : (o->lmax_ncdm < 3 || o->lmax_ncdm > abcmb::kQLmax))
+        return ABCMB_E_INVALID_ARG;
     return ABCMB_OK;
 }
 
 namespace abcmb {
+size_t perturb_warp_bytes(int B, int Nk, const abcmb_options *o);
+int launch_perturb_warp(int B, const double *bg, const double *k, int Nk, const abcmb_options *o, double *S,
+                        int *mode_status, int *steps, double *work, cudaStream_t s);
+
 template <int P>
 static int launch_pk(int B, const double *bg, const double *k, int Nk, const abcmb_options *o, double x_out,
                      double *Pk, int *st, int *steps, cudaStream_t s)
@@ -175,6 +185,7 @@ extern "C" int abcmb_matter_pk(int B, const double *bg, const double *k, int Nk,
     if (B < 1 || Nk < 1 || !bg || !k || !Pk || !mode_status || abcmb_validate_options(o) != ABCMB_OK)
         return ABCMB_E_INVALID_ARG;
     if (!(z >= 0.0 && z <= 1000.0)) return ABCMB_E_INVALID_ARG;
+    if (o->m_ncdm > 0.0) return ABCMB_E_INVALID_ARG; // massless neutrinos only
     const int L = abcmb::max_hier(o);
     if (L > abcmb::kQLmax) return ABCMB_E_INVALID_ARG;
     const double x_out = -log1p(z);
@@ -193,6 +204,7 @@ extern "C" size_t abcmb_bg_doubles(const abcmb_options *o)
 extern "C" size_t abcmb_perturb_workspace_bytes(int B, int Nk, const abcmb_options *o)
 {
     if (B < 1 || Nk < 1 || abcmb_validate_options(o) != ABCMB_OK) return 0;
+    if (o->m_ncdm > 0.0) return abcmb::perturb_warp_bytes(B, Nk, o);
     if (abcmb::max_hier(o) <= abcmb::kQLmax) return 0; // state on chip
     const abcmb::OdeDims d = abcmb::ode_dims(o->lmax_g, o->lmax_pol, o->lmax_nu);
     return (size_t)abcmb::kNvec * d.N * (size_t)B * Nk * sizeof(double);
@@ -203,7 +215,7 @@ extern "C" int abcmb_background_tables(int B, const double *params, const abcmb_
 {
     if (B < 1 || !params || !bg || abcmb_validate_options(o) != ABCMB_OK) return ABCMB_E_INVALID_ARG;
     const long len = (long)abcmb_bg_doubles(o);
-    abcmb::background_kernel<<<B, 32, 0, (cudaStream_t)stream>>>(B, params, bg, len, o->n_tau);
+    abcmb::background_kernel<<<B, 32, 0, (cudaStream_t)stream>>>(B, params, bg, len, o->n_tau, o->m_ncdm);
     return cudaGetLastError() == cudaSuccess ? ABCMB_OK : ABCMB_E_CUDA;
 }
 
@@ -238,6 +250,7 @@ extern "C" int abcmb_perturb_noalloc(int B, const double *bg, const double *k, i
 {
     if (B < 1 || Nk < 1 || !bg || !k || !S || !mode_status || abcmb_validate_options(o) != ABCMB_OK)
         return ABCMB_E_INVALID_ARG;
+    if (o->m_ncdm > 0.0) return ABCMB_E_INVALID_ARG; // the massive-neutrino path needs a caller's workspace
     const cudaStream_t s = (cudaStream_t)stream;
     if (abcmb::max_hier(o) <= abcmb::kQLmax) return abcmb::perturb_on_chip(B, bg, k, Nk, o, S, mode_status, steps, s);
     const size_t need = abcmb_perturb_workspace_bytes(B, Nk, o);
@@ -257,6 +270,11 @@ extern "C" int abcmb_perturb(int B, const double *bg, const double *k, int Nk, c
     if (B < 1 || Nk < 1 || !bg || !k || !S || !mode_status || abcmb_validate_options(o) != ABCMB_OK)
         return ABCMB_E_INVALID_ARG;
     const cudaStream_t s = (cudaStream_t)stream;
+    if (o->m_ncdm > 0.0) {
+        if (!workspace || workspace_bytes < abcmb_perturb_workspace_bytes(B, Nk, o)) return ABCMB_E_INVALID_ARG;
+        if (((size_t)workspace & 255) != 0) return ABCMB_E_INVALID_ARG;
+        return abcmb::launch_perturb_warp(B, bg, k, Nk, o, S, mode_status, steps, (double *)workspace, s);
+    }
     if (abcmb::max_hier(o) <= abcmb::kQLmax) return abcmb::perturb_on_chip(B, bg, k, Nk, o, S, mode_status, steps, s);
     if (!workspace || workspace_bytes < abcmb_perturb_workspace_bytes(B, Nk, o)) return ABCMB_E_INVALID_ARG;
     if (((size_t)workspace & 255) != 0) return ABCMB_E_INVALID_ARG;
