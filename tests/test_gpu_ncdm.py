@@ -47,7 +47,7 @@ def test_sources_and_cl_with_a_massive_neutrino(A):
 def test_massive_neutrino_rejected_where_unsupported(A):
     o = A.options(lmax_hier=8, n_tau=64, lmax_cl=40, m_ncdm=0.06, lmax_ncdm=6)
     bg = A.abcmb_background_tables(torch.tensor(W.BATCH64.params()[:1], device="cuda"), o)
-    k = torch.tensor([1e-3, 1e-2], device="cuda")
+    k = torch.tensor([1e-3, 1e-2], dtype=torch.float64, device="cuda")
     with pytest.raises(RuntimeError):
         A.abcmb_matter_pk(bg, k, o)
     ws = torch.empty(A.grad_workspace_bytes(1, 2, A.options(lmax_hier=8, n_tau=64, lmax_cl=40)) // 8 + 1,
