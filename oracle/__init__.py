@@ -54,6 +54,7 @@ def lib():
         L.orc_radau_tableau.argtypes = [_D]
         L.orc_pk.argtypes = [_D, _D, _D, ctypes.c_int, ctypes.c_double, _D, ctypes.c_int]
         L.orc_ncdm_density.argtypes = [_D, ctypes.c_double, ctypes.c_double, _D]
+        L.orc_delta_m_nodes.argtypes = [_D, ctypes.c_int, _D, _D, ctypes.c_int, _D, ctypes.c_int]
         _lib = L
     return _lib
 
@@ -186,6 +187,17 @@ def ncdm_density(params, m_ncdm, a):
     if lib().orc_ncdm_density(_p(_arr(params)), float(m_ncdm), float(a), _p(out)):
         raise RuntimeError("oracle background failed")
     return dict(rho=out[0], p=out[1], Om_rel=out[2], x1=out[3])
+
+
+def delta_m_nodes(params, k, n_tau, o, nthreads=0):
+    """delta_m(k, tau_i) [n_k, n_tau]: the density-weighted CDM + baryon (+ massive
+    neutrino) contrast at every tau node."""
+    k = _arr(k)
+    out = np.zeros((k.size, n_tau))
+    rc = lib().orc_delta_m_nodes(_p(_arr(params)), int(n_tau), _p(_arr(o)), _p(k), k.size, _p(out), int(nthreads))
+    if rc:
+        raise RuntimeError(f"oracle delta_m failed ({rc})")
+    return out
 
 
 def pk(params, k, z, o, nthreads=0):

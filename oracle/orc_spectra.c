@@ -423,3 +423,48 @@ int orc_pk(const double *p, const double *oa, const double *k, int nk, double z,
     orc_cosmo_free(&c);
     return rc;
 }
+
+/* Density-weighted matter contrast delta_m = sum_i rho_i delta_i / sum_i rho_i
+   over CDM, baryons and (when present) the massive neutrino, at every tau
+   node, for each k: out[nk][n_tau] (App. B.4 eq. PK's bracket; inputs of the
+   lensing potential, App. B.5). */
+int orc_delta_m_nodes(const double *p, int n_tau, const double *oa, const double *k, int nk, double *out,
+                      int nthreads)
+{
+    orc_cosmo c;
+    orc_opts o;
+    opts_from(oa, &o);
+    if (orc_cosmo_init(&c, p, n_tau, o.hooks & ORC_HOOK_EDS_CDM, o.m_ncdm)) return -1;
+    set_threads(nthreads);
+    const int N = orc_nstate(&o);
+    int rc = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : rc)
+    for (int t = 0; t < nk; t++) {
+        int ik = nk - 1 - t;
+        double *Y = (double *)malloc(sizeof(double) * (size_t)n_tau * N);
+        long st = 0;
+        rc |= orc_solve_mode(&c, &o, k[ik], c.node_lna, n_tau, Y, NULL, 0.0, &st);
+        for (int i = 0; i < n_tau; i++) {
+            orc_bg b;
+            orc_bg_eval(&c, c.node_lna[i], &b, 0);
+            const double *y = Y + (size_t)i * N;
+            double num = b.fc * y[1] + b.fb * y[2], den = b.fc + b.fb;
+            if (o.lmax_ncdm > 0) {
+                /* the massive neutrino's delta rho / rho_tot from its momentum bins */
+                const double q[3] = {0.913201, 3.37517, 7.79184}, K[3] = {0.0687359, 3.31435, 2.29911};
+                const int i0 = orc_nstate(&o) - 3 * (o.lmax_ncdm + 1);
+                double drho = 0.0;
+                for (int j = 0; j < 3; j++) {
+                    const double eps = sqrt(q[j] * q[j] + b.ncdm_x * b.ncdm_x);
+                    drho += K[j] * (1.0 + exp(-q[j])) * eps / (q[j] * q[j]) * y[i0 + j * (o.lmax_ncdm + 1)];
+                }
+                num += b.ncdm_n * drho;
+                den += b.fncdm;
+            }
+            out[(size_t)ik * n_tau + i] = num / den;
+        }
+        free(Y);
+    }
+    orc_cosmo_free(&c);
+    return rc;
+}
