@@ -271,6 +271,24 @@ int abcmb_project_interp(int B, const double *bg, const double *S, const double 
 int abcmb_transfer_k_grid(int lmax_cl, double *k_host, int cap);
 
 /*
+ * CMB lensing of the spectra (App. B.5): the all-sky correlation-function
+ * method the paper cites (Challinor & Lewis 2005), integrated over all of
+ * mu in [-1, 1] on n_mu Gauss-Legendre nodes (the paper rejects the restricted
+ * "fast" range).  The lensed-minus-unlensed correlation functions are built at
+ * each node to second order in C_gl,2 and transformed back with d^l_00,
+ * d^l_22, d^l_2-2 and d^l_20.
+ *
+ *   Cl         [B][3][L-1]          device, read: unlensed TT, EE, TE, l = 2..L
+ *                                   (as abcmb_cl writes them with lmax_cl = L)
+ *   Cpsi       [B][L-1]             device, read: lensing potential C_l^psi, l = 2..L
+ *   lmax_out   2..L (lensing moves power from above lmax_out, so L should exceed it)
+ *   n_mu       L + 1 .. 20000 Gauss-Legendre nodes
+ *   Cl_lensed  [B][4][lmax_out-1]   device, written: lensed TT, EE, TE, BB
+ */
+int abcmb_lens(int B, const double *Cl, int L, const double *Cpsi, int lmax_out, int n_mu, double *Cl_lensed,
+               void *stream);
+
+/*
  * Mixed precision (the FP32 form of the two calls above; the sources stay
  * FP64): same projection and k-quadrature, with every (node, l) product and
  * the in-warp sums in FP32 and the sums over tau-node groups and over k

@@ -92,6 +92,7 @@ def lib():
         L.abcmb_project.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, O, _P, _P]
         L.abcmb_project_interp.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, _P, ctypes.c_int, O, _P, _P]
         L.abcmb_transfer_k_grid.argtypes = [ctypes.c_int, _P, ctypes.c_int]
+        L.abcmb_lens.argtypes = [ctypes.c_int, _P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, _P, _P]
         L.abcmb_cl.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, O, _P, _P]
         L.abcmb_project_mixed.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, O, _P, _P]
         L.abcmb_cl_mixed.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, O, _P, _P]
@@ -227,6 +228,18 @@ def abcmb_project_interp(bg: torch.Tensor, S: torch.Tensor, k: torch.Tensor, kt:
     _check(lib().abcmb_project_interp(B, _ptr(bg), _ptr(S), _ptr(k), Nk, _ptr(kt), Nkt, ctypes.byref(o), _ptr(D),
                                       _stream()),
            "abcmb_project_interp")
+    return D
+
+
+def abcmb_lens(Cl: torch.Tensor, Cpsi: torch.Tensor, lmax_out: int, n_mu: int | None = None, out=None):
+    """Cl [B, 3, L - 1] (TT, EE, TE for l = 2..L), Cpsi [B, L - 1] ->
+    lensed [B, 4, lmax_out - 1] (TT, EE, TE, BB)."""
+    _dev(Cl), _dev(Cpsi)
+    B, L = Cl.shape[0], Cl.shape[2] + 1
+    n_mu = n_mu or L + 100
+    D = out if out is not None else torch.empty((B, 4, lmax_out - 1), dtype=torch.float64, device=Cl.device)
+    _check(lib().abcmb_lens(B, _ptr(Cl), L, _ptr(Cpsi), int(lmax_out), int(n_mu), _ptr(D), _stream()),
+           "abcmb_lens")
     return D
 
 

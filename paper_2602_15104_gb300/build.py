@@ -15,7 +15,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libabcmb.so")
-UNITS = ["abcmb_solve.cu", "abcmb_spectra.cu", "abcmb_spectra_mixed.cu", "abcmb_server.cu", "abcmb_grad.cu"]
+UNITS = ["abcmb_solve.cu", "abcmb_spectra.cu", "abcmb_spectra_mixed.cu", "abcmb_server.cu", "abcmb_grad.cu",
+         "abcmb_lensing.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
