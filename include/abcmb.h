@@ -278,15 +278,48 @@ int abcmb_transfer_k_grid(int lmax_cl, double *k_host, int cap);
  * each node to second order in C_gl,2 and transformed back with d^l_00,
  * d^l_22, d^l_2-2 and d^l_20.
  *
- *   Cl         [B][3][L-1]          device, read: unlensed TT, EE, TE, l = 2..L
+ *   Cl         [B][3][L-1]          device, read: unlensed TT, TE, EE, l = 2..L
  *                                   (as abcmb_cl writes them with lmax_cl = L)
  *   Cpsi       [B][L-1]             device, read: lensing potential C_l^psi, l = 2..L
  *   lmax_out   2..L (lensing moves power from above lmax_out, so L should exceed it)
  *   n_mu       L + 1 .. 20000 Gauss-Legendre nodes
- *   Cl_lensed  [B][4][lmax_out-1]   device, written: lensed TT, EE, TE, BB
+ *   Cl_lensed  [B][4][lmax_out-1]   device, written: lensed TT, TE, EE, BB
  */
 int abcmb_lens(int B, const double *Cl, int L, const double *Cpsi, int lmax_out, int n_mu, double *Cl_lensed,
                void *stream);
+
+/*
+ * Matter density contrast at the tau nodes (App. B.4, eq. PK, for the
+ * lensing potential of App. B.5):
+ *   delta_m(k, tau_i) = (rho_c delta_c + rho_b delta_b) / (rho_c + rho_b)
+ * from the same perturbation equations, integrator and node landing as
+ * abcmb_perturb (which writes the CMB sources at the same nodes).
+ *
+ *   bg, k, o, mode_status   as abcmb_perturb (massless neutrinos only:
+ *                           m_ncdm > 0 is ABCMB_E_INVALID_ARG)
+ *   Dm    [B][Nk][n_tau]    device, written (NaN rows for a failed mode)
+ */
+int abcmb_delta_m_nodes(int B, const double *bg, const double *k, int Nk, const abcmb_options *o, double *Dm,
+                        int *mode_status, void *stream);
+
+/*
+ * Lensing potential spectrum in the Limber approximation (App. B.5):
+ *   C_l^psi = 8 pi^2 / (l+1/2)^3 int_0^chi* dchi/chi P_psi((l+1/2)/chi, tau0 - chi) ((chi* - chi)/chi*)^2,
+ *   P_psi(k, tau) = 9 Omega_m(tau)^2 H(tau)^4 / (8 pi^2 k) P(k, tau),
+ *   P(k, tau) = (2 pi^2 / k^3) A_s (k/0.05)^(n_s-1) delta_m(k, tau)^2,
+ * with chi* = tau0 - tau at the node of largest visibility, the trapezoid
+ * rule in chi over the nodes from there to tau0 (chi = 0), H the conformal
+ * Hubble rate, and delta_m taken between the k nodes by cubic Hermite
+ * interpolation in ln k (zero outside [k_0, k_{Nk-1}]).
+ *
+ *   bg    [B][abcmb_bg_doubles(o)]  device, read
+ *   Dm    [B][Nk][n_tau]            device, read (abcmb_delta_m_nodes)
+ *   k     [Nk]                      device, read, strictly ascending, Nk >= 4
+ *   lmax  2..6000
+ *   Cpsi  [B][lmax-1]               device, written: l = 2..lmax, the layout abcmb_lens reads
+ */
+int abcmb_cl_psi(int B, const double *bg, const double *Dm, const double *k, int Nk, const abcmb_options *o,
+                 int lmax, double *Cpsi, void *stream);
 
 /*
  * Mixed precision (the FP32 form of the two calls above; the sources stay

@@ -93,6 +93,8 @@ def lib():
         L.abcmb_project_interp.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, _P, ctypes.c_int, O, _P, _P]
         L.abcmb_transfer_k_grid.argtypes = [ctypes.c_int, _P, ctypes.c_int]
         L.abcmb_lens.argtypes = [ctypes.c_int, _P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, _P, _P]
+        L.abcmb_delta_m_nodes.argtypes = [ctypes.c_int, _P, _P, ctypes.c_int, O, _P, _P, _P]
+        L.abcmb_cl_psi.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, O, ctypes.c_int, _P, _P]
         L.abcmb_cl.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, O, _P, _P]
         L.abcmb_project_mixed.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, O, _P, _P]
         L.abcmb_cl_mixed.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, O, _P, _P]
@@ -232,8 +234,8 @@ def abcmb_project_interp(bg: torch.Tensor, S: torch.Tensor, k: torch.Tensor, kt:
 
 
 def abcmb_lens(Cl: torch.Tensor, Cpsi: torch.Tensor, lmax_out: int, n_mu: int | None = None, out=None):
-    """Cl [B, 3, L - 1] (TT, EE, TE for l = 2..L), Cpsi [B, L - 1] ->
-    lensed [B, 4, lmax_out - 1] (TT, EE, TE, BB)."""
+    """Cl [B, 3, L - 1] (TT, TE, EE for l = 2..L, as abcmb_cl writes them), Cpsi [B, L - 1] ->
+    lensed [B, 4, lmax_out - 1] (TT, TE, EE, BB)."""
     _dev(Cl), _dev(Cpsi)
     B, L = Cl.shape[0], Cl.shape[2] + 1
     n_mu = n_mu or L + 100
@@ -241,6 +243,27 @@ def abcmb_lens(Cl: torch.Tensor, Cpsi: torch.Tensor, lmax_out: int, n_mu: int | 
     _check(lib().abcmb_lens(B, _ptr(Cl), L, _ptr(Cpsi), int(lmax_out), int(n_mu), _ptr(D), _stream()),
            "abcmb_lens")
     return D
+
+
+def abcmb_delta_m_nodes(bg: torch.Tensor, k: torch.Tensor, o: Options, out=None, status=None):
+    """-> (delta_m [B, Nk, n_tau] at the tau nodes, mode_status [B, Nk])."""
+    _dev(bg), _dev(k)
+    B, Nk = bg.shape[0], k.shape[0]
+    D = out if out is not None else torch.empty((B, Nk, o.n_tau), dtype=torch.float64, device=bg.device)
+    st = status if status is not None else torch.empty((B, Nk), dtype=torch.int32, device=bg.device)
+    _check(lib().abcmb_delta_m_nodes(B, _ptr(bg), _ptr(k), Nk, ctypes.byref(o), _ptr(D), _ptr(st), _stream()),
+           "abcmb_delta_m_nodes")
+    return D, st
+
+
+def abcmb_cl_psi(bg: torch.Tensor, Dm: torch.Tensor, k: torch.Tensor, o: Options, lmax: int, out=None):
+    """Limber C_l^psi [B, lmax - 1] for l = 2..lmax from delta_m at the nodes."""
+    _dev(bg), _dev(Dm), _dev(k)
+    B, Nk = bg.shape[0], k.shape[0]
+    C = out if out is not None else torch.empty((B, lmax - 1), dtype=torch.float64, device=bg.device)
+    _check(lib().abcmb_cl_psi(B, _ptr(bg), _ptr(Dm), _ptr(k), Nk, ctypes.byref(o), int(lmax), _ptr(C),
+                              _stream()), "abcmb_cl_psi")
+    return C
 
 
 def transfer_k_grid(lmax_cl: int) -> np.ndarray:

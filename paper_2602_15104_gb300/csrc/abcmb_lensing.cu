@@ -1,4 +1,4 @@
-// abcmb_lens: lensed TT, EE, TE, BB from unlensed spectra and the lensing
+// abcmb_lens: lensed TT, TE, EE, BB from unlensed spectra and the lensing
 // potential's spectrum (App. B.5; the correlation-function method of
 // abcmb_lensing.cuh).  Grid (ceil(n_mu / kLensThreads), B): each thread owns
 // one Gauss-Legendre node, forms the four correlation-function differences
@@ -10,6 +10,9 @@
 #include "../../include/abcmb.h"
 #include "abcmb_launch.cuh"
 #include "abcmb_lensing.cuh"
+
+extern "C" size_t abcmb_bg_doubles(const abcmb_options *o);
+extern "C" int abcmb_validate_options(const abcmb_options *o);
 
 namespace abcmb {
 namespace lens {
@@ -32,7 +35,7 @@ lens_kernel(int B, const double *__restrict__ Cl, const double *__restrict__ Cps
     for (int i = threadIdx.x; i < 4 * (lout + 1); i += blockDim.x) acc[i] = 0.0;
     __syncthreads();
     const double *cl = Cl + (long)b * 3 * (L - 1);
-    const LensIn in{cl, cl + (L - 1), cl + 2 * (L - 1), Cpsi + (long)b * (L - 1), L};
+    const LensIn in{cl, cl + 2 * (L - 1), cl + (L - 1), Cpsi + (long)b * (L - 1), L}; // rows TT, TE, EE
     const int node = blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = node < n_mu;
     double mu = 0.0, w = 0.0, x[4] = {0.0, 0.0, 0.0, 0.0};
@@ -68,7 +71,7 @@ lens_kernel(int B, const double *__restrict__ Cl, const double *__restrict__ Cps
     }
 }
 
-// [dT, dP, dM, dX] -> [TT, EE, TE, BB] lensed, in place
+// [dT, dP, dM, dX] -> [TT, TE, EE, BB] lensed, in place
 __global__ void lens_finish(int B, const double *__restrict__ Cl, int L, int lout, double *out)
 {
     const int nl = lout - 1;
@@ -78,14 +81,51 @@ __global__ void lens_finish(int B, const double *__restrict__ Cl, int L, int lou
     const double *cl = Cl + (long)b * 3 * (L - 1);
     double *o = out + (long)b * 4 * nl;
     const double dT = o[q], dP = o[nl + q], dM = o[2 * nl + q], dX = o[3 * nl + q];
-    o[q] = cl[q] + dT;
-    o[nl + q] = cl[(L - 1) + q] + 0.5 * (dP + dM);
-    o[2 * nl + q] = cl[2 * (L - 1) + q] + dX;
-    o[3 * nl + q] = 0.5 * (dP - dM);
+    o[q] = cl[q] + dT;                                   // TT
+    o[nl + q] = cl[(L - 1) + q] + dX;                    // TE
+    o[2 * nl + q] = cl[2 * (L - 1) + q] + 0.5 * (dP + dM); // EE
+    o[3 * nl + q] = 0.5 * (dP - dM);                     // BB
+}
+
+// C_l^psi, grid (ceil((lmax - 1) / 128), B); dynamic smem: chi[n_tau], coef[n_tau]
+__global__ void __launch_bounds__(128)
+cl_psi_kernel(int B, const double *__restrict__ bg, long len, const double *__restrict__ Dm,
+              const double *__restrict__ kv, int Nk, int lmax, double *Cpsi)
+{
+    extern __shared__ double sm[];
+    __shared__ int s_is;
+    const int b = blockIdx.y;
+    const double *rec = bg + (long)b * len;
+    const int n_tau = (int)rec[ABCMB_S_NTAU];
+    double *chi = sm, *coef = sm + n_tau;
+    if (threadIdx.x == 0)
+        s_is = limber_prepare(rec + ABCMB_BG_NODES, n_tau, rec[ABCMB_S_TAU0], rec[ABCMB_S_OMB] + rec[ABCMB_S_OMC],
+                              rec[ABCMB_S_H0], chi, coef);
+    __syncthreads();
+    const int l = 2 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (l > lmax) return;
+    Cpsi[(long)b * (lmax - 1) + (l - 2)] =
+        limber_cl_at(l, chi, coef, s_is, n_tau, Dm + (long)b * Nk * n_tau, kv, Nk, rec[ABCMB_S_AS], rec[ABCMB_S_NS]);
 }
 
 } // namespace lens
 } // namespace abcmb
+
+extern "C" int abcmb_cl_psi(int B, const double *bg, const double *Dm, const double *k, int Nk,
+                            const abcmb_options *o, int lmax, double *Cpsi, void *stream)
+{
+    if (B < 1 || Nk < 4 || !bg || !Dm || !k || !Cpsi || lmax < 2 || lmax > 6000 ||
+        abcmb_validate_options(o) != ABCMB_OK)
+        return ABCMB_E_INVALID_ARG;
+    const size_t smem = 2 * (size_t)o->n_tau * sizeof(double);
+    const long avail = abcmb::smem_optin((const void *)abcmb::lens::cl_psi_kernel);
+    if (avail < 0) return ABCMB_E_CUDA;
+    if ((long)smem > avail) return ABCMB_E_INVALID_ARG;
+    const long len = (long)abcmb_bg_doubles(o);
+    dim3 grid((lmax - 1 + 127) / 128, B);
+    abcmb::lens::cl_psi_kernel<<<grid, 128, smem, (cudaStream_t)stream>>>(B, bg, len, Dm, k, Nk, lmax, Cpsi);
+    return cudaGetLastError() == cudaSuccess ? ABCMB_OK : ABCMB_E_CUDA;
+}
 
 extern "C" int abcmb_lens(int B, const double *Cl, int L, const double *Cpsi, int lmax_out, int n_mu,
                           double *Cl_lensed, void *stream)

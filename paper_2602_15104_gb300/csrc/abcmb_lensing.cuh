@@ -22,6 +22,8 @@
 
 #include <math.h>
 
+#include "abcmb_interp.cuh"
+
 #ifndef ABCMB_HD
 #ifdef __CUDACC__
 #define ABCMB_HD __host__ __device__ inline
@@ -200,6 +202,54 @@ ABCMB_HD void gauss_legendre(int n, int i, double *x, double *w)
     }
     *x = z;
     *w = 2.0 / ((1.0 - z * z) * pp * pp);
+}
+
+// ---- the lensing potential in the Limber approximation (App. B.5) ----
+//   C_l^psi = 8 pi^2 / (l+1/2)^3 int_0^chi* dchi / chi P_psi((l+1/2)/chi, tau0 - chi) ((chi* - chi)/chi*)^2,
+//   P_psi(k, a) = 9 Omega_m(a)^2 H^4 / (8 pi^2 k) P(k, a),
+//   P(k, a) = (2 pi^2 / k^3) A_s (k/k_pivot)^(n_s-1) delta_m(k, a)^2,
+// on the tau nodes from the visibility peak (chi*) to tau0: the trapezoid
+// weights in chi, Omega_m(a) = Omega_m0 H0^2 / (a H^2), delta_m interpolated
+// in ln k (lnk_hermite_weights) and zero outside the k nodes.
+
+// node i (8 doubles: ln a, tau, w, g, g', e^-kappa, H, H'); fills chi[i] and
+// coef[i] = w_chi / chi 9 Omega_m^2 H^4 / (8 pi^2) ((chi* - chi)/chi*)^2 for
+// i >= i_star (the visibility peak), returns i_star
+ABCMB_HD int limber_prepare(const double *nodes, int n_tau, double tau0, double Om_m, double H0, double *chi,
+                            double *coef)
+{
+    int is = 0;
+    for (int i = 1; i < n_tau; i++)
+        if (nodes[8 * i + 3] > nodes[8 * is + 3]) is = i;
+    const double chi_star = tau0 - nodes[8 * is + 1];
+    for (int i = is; i < n_tau; i++) {
+        const double tau = nodes[8 * i + 1], a = exp(nodes[8 * i]), hc = nodes[8 * i + 6];
+        const double lo = i > is ? nodes[8 * (i - 1) + 1] : tau, hi = i < n_tau - 1 ? nodes[8 * (i + 1) + 1] : tau0;
+        const double c = tau0 - tau, om = Om_m * H0 * H0 / (a * hc * hc), r = (chi_star - c) / chi_star;
+        chi[i] = c;
+        coef[i] = 0.5 * (hi - lo) / c * 9.0 * om * om * hc * hc * hc * hc / (8.0 * kPi * kPi) * r * r;
+    }
+    return is;
+}
+
+// C_l^psi from delta_m[k][n_tau] at the nodes kv[0..Nk) (Nk >= 4)
+ABCMB_HD double limber_cl_at(int l, const double *chi, const double *coef, int i_star, int n_tau, const double *dm,
+                             const double *kv, int Nk, double As, double ns)
+{
+    const double lh = l + 0.5;
+    double sum = 0.0;
+    for (int i = i_star; i < n_tau; i++) {
+        const double k = lh / chi[i];
+        if (!(k >= kv[0] && k <= kv[Nk - 1])) continue;
+        int r0;
+        double w[4];
+        lnk_hermite_weights(kv, Nk, k, &r0, w);
+        double d = 0.0;
+        for (int m = 0; m < 4; m++) d += w[m] * dm[(long)(r0 + m) * n_tau + i];
+        const double P = 2.0 * kPi * kPi / (k * k * k) * As * exp((ns - 1.0) * log(k / 0.05)) * d * d;
+        sum += coef[i] * P / k;
+    }
+    return 8.0 * kPi * kPi / (lh * lh * lh) * sum;
 }
 
 } // namespace lens

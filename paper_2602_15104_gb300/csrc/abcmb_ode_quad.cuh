@@ -404,6 +404,13 @@ __device__ __forceinline__ double q_matter_pk(const double *ot, const double *re
     return 2.0 * kPi * kPi / (k * k * k) * As * exp((ns - 1.0) * log(k / kKpivot)) * dm * dm;
 }
 
+// density-weighted CDM + baryon contrast at ln a (App. B.4 eq. PK's bracket)
+__device__ __forceinline__ double q_delta_m(const double *ot, double lna, double dc, double db)
+{
+    const QBg b = obg_all(ot, lna);
+    return (b.fc * dc + b.fb * db) / (b.fc + b.fb);
+}
+
 // Dense output.  Nodes whose e^-kappa is below kNegligibleWeight (before
 // recombination) enter every source through a factor e^-kappa or g = H nu
 // e^-kappa no larger than ~1e-12 of its peak, so steps pass them freely and
@@ -498,8 +505,12 @@ __device__ __forceinline__ void q_dense(double (&v)[kSrcComp], const double *dq,
 
 // Integrate the modes of one warp (8 per warp, mode index mi for this lane's quad).
 // PK: integrate to ln a = x_out only and write the matter power spectrum
-// there into pk_out[b][k] instead of the sources (S unused).
-template <int P, bool PK = false>
+// there into pk_out[b][k] instead of the sources (S unused).  DM: write the
+// matter contrast delta_m at every tau node into S[b][k][n_tau] instead of
+// the sources (every node by landing or Hermite dense output: the linear
+// interpolation that the sources allow where e^-kappa < kNegligibleWeight is
+// not used).
+template <int P, bool PK = false, bool DM = false>
 __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restrict__ bg, long len,
                            const double *__restrict__ kv, const QCoef &qc, double rtol, double atol, int max_steps,
                            const double sw[3], double *S, int *status, int *steps, double *smw, double *dn,
@@ -523,7 +534,7 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
     md.c43ik = (4.0 / 3.0) * md.ik;
     md.c15ik = 1.5 * md.ik;
     const double k = md.k;
-    double *Sm = PK ? nullptr : S + ((long)b * Nk + kidx) * (long)n_tau * 3;
+    double *Sm = PK ? nullptr : S + ((long)b * Nk + kidx) * (long)n_tau * (DM ? 1 : 3);
     // shared memory of this lane: element e of vector v at smw[(v E + e) 32 + lane]
     double *sl = smw + lane;
     auto Y = [&](int e) -> double & { return sl[e * 32]; };
@@ -600,7 +611,7 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
     // scalars by their owners)
     double *dq = dn + (lane >> 2) * 3 * kSrcComp;
     int n_sig = 0;
-    {
+    if (!DM) { // delta_m is wanted at every node
         int lo = 0, hi = n_tau - 1; // first node whose e^-kappa reaches the threshold
         if (nodes[8 * hi + N_EXPMK] < kNegligibleWeight) lo = hi;
         while (lo < hi) {
@@ -828,7 +839,8 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
                     const double th = fmin((nodes[8 * i + N_LNA] - x0) * iH, 1.0);
                     double v[kSrcComp];
                     q_dense<P>(v, dq, smw + qb, th, x - x0, dmode == 2);
-                    q_sources_v(ot, nodes + 8 * i, k, sw, v, Sm + 3 * i);
+                    if (DM) Sm[i] = q_delta_m(ot, nodes[8 * i + N_LNA], v[9], v[10]);
+                    else q_sources_v(ot, nodes + 8 * i, k, sw, v, Sm + 3 * i);
                 }
                 const int cnt = __popc((__ballot_sync(kFull, mine) >> qb) & 0xFu);
                 if (pend) {
@@ -855,6 +867,7 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
             if (emit) {
                 if (q == 0) {
                     if (PK) pk_out[(long)b * Nk + kidx] = q_matter_pk(ot, rec, x_out, k, sc);
+                    else if (DM) Sm[node] = q_delta_m(ot, nodes[8 * node + N_LNA], sc[1], sc[2]);
                     else q_sources<P>(ot, nodes + 8 * node, k, sw, sl, sc, Sm + 3 * node);
                 }
                 node++;
@@ -865,6 +878,8 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
     if (valid && q == 0) {
         if (PK) {
             if (node < 1) pk_out[(long)b * Nk + kidx] = nan("");
+        } else if (DM) {
+            for (int n = node; n < n_tau; n++) Sm[n] = 0.0;
         } else {
             for (int n = node; n < n_tau; n++) Sm[3 * n] = Sm[3 * n + 1] = Sm[3 * n + 2] = 0.0;
         }
@@ -948,6 +963,37 @@ pk_quad_kernel(int B, int Nk, const double *__restrict__ bg, long len, const dou
     const double sw[3] = {0.0, 0.0, 0.0};
     quad_modes<P, true>(mi, M, B, Nk, bg, len, kv, qc, rtol, atol, max_steps, sw, nullptr, status, steps, qsm,
                         qsm + (1 + kQK) * E * 32, x_out, Pk);
+}
+
+// delta_m at every tau node for every (cosmology, k) mode: Dm[B][Nk][n_tau]
+template <int P>
+__global__ void __launch_bounds__(32)
+dm_quad_kernel(int B, int Nk, const double *__restrict__ bg, long len, const double *__restrict__ kv, int Lg,
+               int Lp, int Ln, double rtol, double atol, int max_steps, double *Dm, int *status)
+{
+    extern __shared__ double qsm[];
+    __shared__ double cA[3 * 64], cB[3 * 64];
+    const int Ls[3] = {Lg, Lp, Ln};
+    for (int i = threadIdx.x; i < 3 * 64; i += blockDim.x) {
+        const int ch = i / 64, l = i % 64, L = Ls[ch];
+        cA[i] = l < L ? (double)l / (2.0 * l + 1.0) : (l == L ? 1.0 : 0.0);
+        cB[i] = l < L ? (l + 1.0) / (2.0 * l + 1.0) : 0.0;
+    }
+    __syncthreads();
+    constexpr int E = 3 * P + 1;
+    const int lane = threadIdx.x & 31;
+    const long M = (long)B * Nk;
+    const long mi = (long)blockIdx.x * 8 + (lane >> 2);
+    QCoef qc;
+    qc.A = cA;
+    qc.Bc = cB;
+    qc.L[0] = Lg;
+    qc.L[1] = Lp;
+    qc.L[2] = Ln;
+    for (int c = 0; c < 3; c++) qc.L1[c] = qc.L[c] + 1.0;
+    const double sw[3] = {1.0, 1.0, 1.0};
+    quad_modes<P, false, true>(mi, M, B, Nk, bg, len, kv, qc, rtol, atol, max_steps, sw, Dm, status, nullptr,
+                               qsm, qsm + (1 + kQK) * E * 32);
 }
 
 } // namespace abcmb

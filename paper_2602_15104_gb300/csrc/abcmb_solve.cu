@@ -195,6 +195,39 @@ extern "C" int abcmb_matter_pk(int B, const double *bg, const double *k, int Nk,
     return abcmb::launch_pk<16>(B, bg, k, Nk, o, x_out, Pk, mode_status, nullptr, s);
 }
 
+namespace abcmb {
+template <int P>
+static int launch_dm(int B, const double *bg, const double *k, int Nk, const abcmb_options *o, double *Dm, int *st,
+                     cudaStream_t s)
+{
+    const size_t smem = quad_smem_per_warp<P>();
+    auto kern = dm_quad_kernel<P>;
+    const long avail = smem_optin((const void *)kern);
+    if (avail < 0) return ABCMB_E_CUDA;
+    if ((long)smem > avail) return ABCMB_E_INVALID_ARG;
+    const long blocks = ((long)B * Nk + 7) / 8;
+    if (blocks > 2147483647L) return ABCMB_E_INVALID_ARG;
+    const long len = (long)ABCMB_BG_NODES + 8L * o->n_tau;
+    kern<<<(unsigned)blocks, 32, smem, s>>>(B, Nk, bg, len, k, o->lmax_g, o->lmax_pol, o->lmax_nu, o->rtol, o->atol,
+                                            o->max_steps, Dm, st);
+    return cudaGetLastError() == cudaSuccess ? ABCMB_OK : ABCMB_E_CUDA;
+}
+} // namespace abcmb
+
+extern "C" int abcmb_delta_m_nodes(int B, const double *bg, const double *k, int Nk, const abcmb_options *o,
+                                   double *Dm, int *mode_status, void *stream)
+{
+    if (B < 1 || Nk < 1 || !bg || !k || !Dm || !mode_status || abcmb_validate_options(o) != ABCMB_OK)
+        return ABCMB_E_INVALID_ARG;
+    if (o->m_ncdm > 0.0) return ABCMB_E_INVALID_ARG; // massless neutrinos only
+    const int L = abcmb::max_hier(o);
+    if (L > abcmb::kQLmax) return ABCMB_E_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (L <= 15) return abcmb::launch_dm<4>(B, bg, k, Nk, o, Dm, mode_status, s);
+    if (L <= 31) return abcmb::launch_dm<8>(B, bg, k, Nk, o, Dm, mode_status, s);
+    return abcmb::launch_dm<16>(B, bg, k, Nk, o, Dm, mode_status, s);
+}
+
 extern "C" size_t abcmb_bg_doubles(const abcmb_options *o)
 {
     if (abcmb_validate_options(o) != ABCMB_OK) return 0;

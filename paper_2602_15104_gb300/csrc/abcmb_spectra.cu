@@ -25,6 +25,7 @@
 
 #include "abcmb_bg.cuh"
 #include "abcmb_bessel.cuh"
+#include "abcmb_interp.cuh"
 #include "abcmb_launch.cuh"
 
 namespace abcmb {
@@ -75,42 +76,9 @@ __device__ __forceinline__ void butterfly_stage(double *v, int lane)
     }
 }
 
-// Cubic Hermite interpolation in ln k of the sources at kk from the nodes
-// kn[0..n), n >= 4, slopes from three-point derivatives (centred, one-sided at
-// the ends): S(kk) = sum_m w[m] S(kn[r0 + m]), m < 4.  Outside the nodes the
-// end intervals' cubics extend.
-__device__ void interp_weights(const double *__restrict__ kn, int n, double kk, int *r0_out, double w[4])
-{
-    const double xv = log(kk);
-    int lo = 0, hi = n - 1; // interval i: kn[i] <= kk < kn[i + 1], clamped to [0, n - 2]
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (kn[mid] <= kk) lo = mid; else hi = mid;
-    }
-    const int i = lo;
-    const int r0 = i - 1 < 0 ? 0 : (i - 1 > n - 4 ? n - 4 : i - 1);
-    for (int m = 0; m < 4; m++) w[m] = 0.0;
-    const double xi = log(kn[i]), xj = log(kn[i + 1]), h = xj - xi, t = (xv - xi) / h;
-    const double h00 = (1.0 + 2.0 * t) * (1.0 - t) * (1.0 - t), h10 = t * (1.0 - t) * (1.0 - t);
-    const double h01 = t * t * (3.0 - 2.0 * t), h11 = t * t * (t - 1.0);
-    w[i - r0] += h00;
-    w[i + 1 - r0] += h01;
-    // slope at node p: derivative of the parabola through three neighbours
-    for (int side = 0; side < 2; side++) {
-        const int p = i + side;
-        const double c = (side == 0 ? h10 : h11) * h;
-        const int a = p == 0 ? 0 : (p == n - 1 ? n - 3 : p - 1);
-        const double xa = log(kn[a]), xb = log(kn[a + 1]), xc = log(kn[a + 2]), xp = log(kn[p]);
-        w[a - r0] += c * ((xp - xb) + (xp - xc)) / ((xa - xb) * (xa - xc));
-        w[a + 1 - r0] += c * ((xp - xa) + (xp - xc)) / ((xb - xa) * (xb - xc));
-        w[a + 2 - r0] += c * ((xp - xa) + (xp - xb)) / ((xc - xa) * (xc - xb));
-    }
-    *r0_out = r0;
-}
-
 // INTERP: the transfer functions at the wavenumbers kv[0..Nk) from sources
 // given at the ODE nodes kode[0..Nko) (S[B][Nko][n_tau][3]), interpolated per
-// node in ln k (interp_weights); otherwise S is given at kv itself.
+// node in ln k (lnk_hermite_weights); otherwise S is given at kv itself.
 template <bool INTERP>
 __global__ void __launch_bounds__(128)
 project_kernel(int B, int Nk, const double *__restrict__ bg, long bg_len,
@@ -132,7 +100,7 @@ project_kernel(int B, int Nk, const double *__restrict__ bg, long bg_len,
     double wi[4] = {0.0, 0.0, 0.0, 0.0};
     long rs = 0; // element stride between consecutive source rows
     if (INTERP) {
-        interp_weights(kode, Nko, kk, &r0, wi);
+        lnk_hermite_weights(kode, Nko, kk, &r0, wi);
         Sm = S + ((long)b * Nko + r0) * (long)n_tau * 3;
         rs = (long)n_tau * 3;
     } else {

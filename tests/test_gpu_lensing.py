@@ -27,13 +27,13 @@ def test_lensed_spectra_against_oracle(A):
     from test_lensing_host import spectra
     L, lout = 400, 300
     sp = [spectra(L, 7 + b) for b in range(2)]
-    Cl = np.stack([np.stack([s[0][2:], s[1][2:], s[2][2:]]) for s in sp])
+    Cl = np.stack([np.stack([s[0][2:], s[2][2:], s[1][2:]]) for s in sp])
     Cpsi = np.stack([s[3][2:] for s in sp])
     out = A.abcmb_lens(torch.tensor(Cl, device="cuda"), torch.tensor(Cpsi, device="cuda"), lout,
                        n_mu=L + 100).cpu().numpy()
     for b, (ctt, cee, cte, cpsi) in enumerate(sp):
         TT, EE, TE, BB = LZ.lensed_cls(ctt, cee, cte, cpsi, lout, n_mu=L + 100)
-        for c, ref, scale in [(0, TT, ctt), (1, EE, cee), (2, TE, np.sqrt(ctt * cee)), (3, BB, cee)]:
+        for c, ref, scale in [(0, TT, ctt), (2, EE, cee), (1, TE, np.sqrt(ctt * cee)), (3, BB, cee)]:
             err = np.abs(out[b, c] - ref[2:]).max() / np.abs(scale).max()
             assert err < 1e-10, (b, c, err)
 

@@ -21,6 +21,8 @@ def H(tmp_path_factory):
                            os.path.join(ROOT, "tests", "host", "lensing_harness.cpp"), "-o", so])
     L = ctypes.CDLL(so)
     L.h_lens.argtypes = [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
+    L.h_cl_psi.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, P, P, ctypes.c_int,
+                           ctypes.c_double, ctypes.c_double, ctypes.c_int, P]
     return L
 
 
@@ -43,14 +45,37 @@ def test_lensed_spectra_match_oracle(H, L, lout):
     ctt, cee, cte, cpsi = spectra(L, L)
     n_mu = L + 100
     TT, EE, TE, BB = LZ.lensed_cls(ctt, cee, cte, cpsi, lout, n_mu=n_mu)
-    Cl = np.ascontiguousarray(np.stack([ctt[2:], cee[2:], cte[2:]]))
+    Cl = np.ascontiguousarray(np.stack([ctt[2:], cte[2:], cee[2:]]))
     out = np.zeros((4, lout - 1))
     H.h_lens(Cl.ctypes.data_as(P), np.ascontiguousarray(cpsi[2:]).ctypes.data_as(P), L, lout, n_mu,
              out.ctypes.data_as(P))
-    for got, ref, scale in [(out[0], TT[2:], ctt[2:lout + 1]), (out[1], EE[2:], cee[2:lout + 1]),
-                            (out[2], TE[2:], np.sqrt(ctt * cee)[2:lout + 1]), (out[3], BB[2:], cee[2:lout + 1])]:
+    for got, ref, scale in [(out[0], TT[2:], ctt[2:lout + 1]), (out[2], EE[2:], cee[2:lout + 1]),
+                            (out[1], TE[2:], np.sqrt(ctt * cee)[2:lout + 1]), (out[3], BB[2:], cee[2:lout + 1])]:
         assert np.all(np.abs(got - ref) <= 1e-10 * np.abs(scale).max() + 1e-9 * np.abs(scale)), \
             np.abs(got - ref).max()
     # lensing changed them (well beyond the tolerance): B modes from E, E smoothed
     assert out[3].max() > 1e-4 * cee.max()
-    assert np.abs(out[1] - cee[2:lout + 1]).max() > 1e-4 * cee.max()
+    assert np.abs(out[2] - cee[2:lout + 1]).max() > 1e-4 * cee.max()
+
+
+def test_limber_lensing_potential_matches_oracle(H):
+    # the library's Limber sum on the oracle's nodes, background and delta_m
+    # against the oracle's C_l^psi (App. B.5): same quadrature, so rounding only
+    import oracle as O
+    from paper_2602_15104_gb300 import workload as W
+    p = W.SMALL_TT.params()[0]
+    n_tau, lmax = 300, 150
+    k = np.exp(np.linspace(np.log(1e-4), np.log(0.3), 40))
+    o = O.opts(lmax=8)
+    ref = LZ.cl_psi(p, k, n_tau, lmax, o)
+    lna, tau, w = O.nodes(p, n_tau)
+    bg = O.background(p, lna)
+    sc = O.scalars(p)
+    nodes = np.zeros((n_tau, 8))
+    nodes[:, 0], nodes[:, 1], nodes[:, 2], nodes[:, 3], nodes[:, 6] = lna, tau, w, bg["g"], bg["Hc"]
+    dm = np.ascontiguousarray(O.delta_m_nodes(p, k, n_tau, o))
+    out = np.zeros(lmax - 1)
+    H.h_cl_psi(nodes.ctypes.data_as(P), n_tau, sc["tau0"], sc["Om_b"] + sc["Om_c"], sc["H0"], dm.ctypes.data_as(P),
+               k.ctypes.data_as(P), k.size, sc["A_s"], sc["n_s"], lmax, out.ctypes.data_as(P))
+    assert np.all(np.isfinite(out)) and out.min() > 0
+    np.testing.assert_allclose(out, ref[2:], rtol=1e-10)
