@@ -312,6 +312,86 @@ def run_gradient(args, A, torch):
     print(json.dumps(out), flush=True)
 
 
+def run_variants(args, A, torch):
+    """Timings of the variant paths on a batch of the 64-cosmology workload
+    (TT/TE/EE to l = 2500, 400 k in [1e-5, 0.5], hierarchies 30, 6000 tau
+    nodes): the transfer k grid (projection onto the 1703-node grid by
+    interpolation in ln k, then the quadrature), P(k, z = 0), the lensing
+    chain (delta_m at the nodes, Limber C_l^psi to l = 2500, lensed spectra
+    to l = 2000 from L = 2500) and the massive-neutrino perturbation solve
+    (m = 0.06 eV).  Each line: CUDA-event time per call on the current
+    stream after the warm-up calls, L2 flushed before each timed call."""
+    wl = W.BATCH64
+    B = args.batch or 8
+    params = W.draw_cosmologies(B, wl.seed)
+    k_np = W.log_k_nodes(args.n_k, wl.k_min, wl.k_max) if args.n_k else wl.k()
+    o = A.options(lmax_hier=wl.l_max_hier, lmax_cl=wl.l_max_cl, n_tau=wl.n_tau, rtol=args.rtol)
+    k = torch.tensor(k_np, device="cuda")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    p_dev = torch.tensor(params, device="cuda")
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.mean(ms), r
+
+    def line(name, units, unit, ms, extra):
+        out = {"metric": f"{name} ({unit})", "value": units / (ms * 1e-3), "unit": unit, "n_gpus": 1,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_call": ms, "higher_is_better": True,
+               "dtype": "f64", "data": "synthetic",
+               "config": {"workload": f"{wl.name} first {B} cosmologies", "n_k": len(k_np), "rtol": args.rtol,
+                          "l2": "flushed (512 MiB write) before each timed call", **extra}}
+        print(json.dumps(out), flush=True)
+
+    clocks = ClockSampler()
+    clocks.start()
+    bg = A.abcmb_background_tables(p_dev, o)
+    ms, (S, st, _) = timed(lambda: A.abcmb_perturb(bg, k, o))
+    assert int(st.abs().sum()) == 0
+    line("perturbation solve + sources, massless neutrinos", B, "cosmologies/s", ms, {})
+    kt = torch.tensor(A.transfer_k_grid(o.lmax_cl), device="cuda")
+
+    def transfer():
+        D = A.abcmb_project_interp(bg, S, k, kt, o)
+        return A.abcmb_cl(bg, D, kt, o)
+    ms, C = timed(transfer)
+    assert bool(torch.isfinite(C).all())
+    line("projection on the transfer k grid + quadrature", B, "spectra/s", ms, {"n_k_transfer": kt.numel()})
+    del S
+    ms, (P, st) = timed(lambda: A.abcmb_matter_pk(bg, k, o, 0.0))
+    assert int(st.abs().sum()) == 0
+    line("matter power spectrum P(k, z=0)", B * len(k_np), "modes/s", ms, {"z": 0.0})
+    ms, (Dm, st) = timed(lambda: A.abcmb_delta_m_nodes(bg, k, o))
+    assert int(st.abs().sum()) == 0
+    line("delta_m at the tau nodes", B, "cosmologies/s", ms, {})
+    ms, Cpsi = timed(lambda: A.abcmb_cl_psi(bg, Dm, k, o, o.lmax_cl))
+    line("Limber C_l^psi to l = 2500", B, "cosmologies/s", ms, {})
+    del Dm
+    Bl = min(B, 4)
+    ms, CL = timed(lambda: A.abcmb_lens(C[:Bl].contiguous(), Cpsi[:Bl].contiguous(), 2000, n_mu=2600))
+    assert bool(torch.isfinite(CL).all())
+    line("lensed TT/TE/EE/BB to l = 2000 from L = 2500", Bl, "spectra/s", ms, {"batch": Bl, "n_mu": 2600})
+    Bn = min(B, 2)
+    on = A.options(lmax_hier=wl.l_max_hier, lmax_cl=wl.l_max_cl, n_tau=wl.n_tau, rtol=args.rtol, m_ncdm=0.06)
+    bgn = A.abcmb_background_tables(p_dev[:Bn].contiguous(), on)
+    ms, (Sn, st, _) = timed(lambda: A.abcmb_perturb(bgn, k, on))
+    assert int(st.abs().sum()) == 0
+    line("perturbation solve + sources, one massive neutrino 0.06 eV", Bn, "cosmologies/s", ms,
+         {"batch": Bn, "lmax_ncdm": on.lmax_ncdm})
+    print(json.dumps({"clocks": clocks.stop()}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -331,6 +411,8 @@ def main():
                     help="serving benchmark: Poisson arrivals of mixed-size requests through abcmb_server")
     ap.add_argument("--grad", action="store_true",
                     help="gradient benchmark: dC_l/dtheta of a batch through the hand-written adjoint")
+    ap.add_argument("--variants", action="store_true",
+                    help="time the variant paths (transfer grid, P(k), lensing chain, massive neutrino)")
     ap.add_argument("--requests", type=int, default=4096)
     ap.add_argument("--rate", type=float, default=200.0, help="mean arrivals per second")
     ap.add_argument("--slots", type=int, default=32)
@@ -359,6 +441,10 @@ def main():
     if args.grad:
         if rank == 0:
             run_gradient(args, A, torch)
+        return
+    if args.variants:
+        if rank == 0:
+            run_variants(args, A, torch)
         return
     dist = None
     if world > 1:

@@ -176,7 +176,7 @@ def abcmb_perturb(bg: torch.Tensor, k: torch.Tensor, o: Options, S=None, status=
     if steps is None:
         steps = torch.empty((B, Nk, 2), dtype=torch.int32, device=dev)
     nbytes = perturb_workspace_bytes(B, Nk, o)
-    if workspace is None and nbytes > 0:  # hierarchies > 63 only
+    if workspace is None and nbytes > 0:  # hierarchies > 63 and massive neutrinos
         workspace = torch.empty(nbytes // 8, dtype=torch.float64, device=dev)
     wbytes = 0 if workspace is None else workspace.numel() * 8
     _check(lib().abcmb_perturb(B, _ptr(bg), _ptr(k), Nk, ctypes.byref(o), _ptr(S), _ptr(status),
