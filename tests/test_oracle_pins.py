@@ -265,6 +265,69 @@ def test_einstein_traceless_consistency(small_params):
     assert np.max(np.abs(num[sl] - Hap[sl])) < 1e-6 * np.max(np.abs(Hap))
 
 
+# ---- the CMB sources (App. B.4, eq. source_functions) against the Newtonian
+# gauge quantities they stand for: alpha = H (h' + 6 eta') / (2 k^2),
+# phi = eta - H alpha, psi = H alpha' + H alpha, theta_b^N = theta_b + k^2 alpha
+# (the synchronous-to-Newtonian transformation of the cited formalism)
+
+_P_SRC = np.array([0.0224, 0.12, 0.7, 1.0, np.log(2.1e-9 * 1e10), 0.06])
+
+
+def _sources_and_state(k, n_tau, **switches):
+    o = O.opts(lmax=12, **switches)
+    lna, tau, _ = O.nodes(_P_SRC, n_tau)
+    S = O.run(_P_SRC, np.array([k]), n_tau, 12, o, want=("S",))["S"][0]
+    y, _ = O.trajectory(_P_SRC, o, k, lna)
+    b = O.background(_P_SRC, lna)
+    hp, ep, _ = _metric(b, y, k, o)
+    alpha = b["Hc"] * (hp + 6 * ep) / (2 * k * k)
+    return tau, S, y, b, alpha
+
+
+def test_doppler_source_is_the_derivative_of_g_times_the_newtonian_velocity():
+    # the Doppler bracket H [g (theta_b'/k^2 + alpha') + g' (theta_b/k^2 + alpha)]
+    # is d/dtau [g theta_b^N / k^2]: its running integral over a fine tau grid
+    # reproduces g (theta_b/k^2 + alpha) from the state (the trapezoid error
+    # falls as the node spacing squared: 3.6e-2 at 2000 nodes, 2.3e-3 at 8000)
+    k = 7e-4
+    tau, S, y, b, alpha = _sources_and_state(k, 8000, scale_sw=0, scale_isw=0, scale_pol=0)
+    F = b["g"] * (y[:, 3] / k**2 + alpha)
+    Fc = integrate.cumulative_trapezoid(S[:, 0], tau, initial=0.0) + F[0]
+    assert np.abs(F).max() > 1.0  # recombination's g theta_b^N / k^2
+    assert np.abs(Fc - F).max() < 5e-3 * np.abs(F).max()
+
+
+def test_isw_sources_are_the_change_of_the_newtonian_potentials():
+    # ISW part: S_T1 = e^-kappa k (psi - phi) and the S_T0 part
+    # g (phi - psi) + 2 e^-kappa phi-dot, so after last scattering
+    # int (S_T0 + g S_T1 / (k e^-kappa)) / (2 e^-kappa) dtau = phi(tau) - phi(tau_a)
+    k = 7e-4
+    tau, S, y, b, alpha = _sources_and_state(k, 8000, scale_sw=0, scale_dop=0, scale_pol=0)
+    phi = y[:, 0] - b["Hc"] * alpha
+    emk = np.exp(-b["kappa"])
+    m = tau > 600.0
+    integrand = (S[:, 0] + b["g"] * S[:, 1] / (k * emk)) / (2 * emk)
+    dphi = integrate.cumulative_trapezoid(integrand[m], tau[m], initial=0.0)
+    ref = phi[m] - phi[m][0]
+    assert abs(ref[-1]) > 0.1  # the potential decays (radiation, then Lambda)
+    assert np.abs(dphi - ref).max() < 2e-5 * np.abs(phi[m]).max()
+
+
+def test_sachs_wolfe_source_tends_to_psi_over_three():
+    # SW bracket delta_g/4 + H alpha' = Theta_0^N + psi; for a superhorizon
+    # adiabatic mode this tends to psi/3 as the radiation fades (matter era),
+    # the excess shrinking with the radiation fraction ~ (1+z)/3400
+    k = 1e-5
+    tau, S, y, b, alpha = _sources_and_state(k, 800, scale_isw=0, scale_dop=0, scale_pol=0)
+    psi = np.gradient(alpha, tau) + b["Hc"] * alpha
+    z = np.exp(-np.log(b["a"])) - 1.0
+    ratio = {}
+    for zz in (200, 100, 20):
+        i = int(np.argmin(np.abs(z - zz)))
+        ratio[zz] = S[i, 0] / b["g"][i] / (psi[i] / 3.0)
+    assert 1.0 < ratio[20] < 1.02 and ratio[20] < ratio[100] < ratio[200] < 1.12, ratio
+
+
 def test_tight_coupling_and_superhorizon(small_params):
     o = O.opts(lmax=12)
     k = 0.1
