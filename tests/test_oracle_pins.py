@@ -313,6 +313,21 @@ def test_isw_sources_are_the_change_of_the_newtonian_potentials():
     assert np.abs(dphi - ref).max() < 2e-5 * np.abs(phi[m]).max()
 
 
+@pytest.mark.parametrize("k", [0.05, 0.2])
+def test_polarization_hierarchy_in_tight_coupling(small_params, k):
+    # Thomson scattering with the source Pi (delta_l0 + delta_l2 / 5) / 2 and
+    # Pi = F_2 + G_0 + G_2: deep in tight coupling G_0 = Pi/2 and G_2 = Pi/10,
+    # so Pi = 5/2 F_2, G_0 = 5/4 F_2, G_2 = 1/4 F_2 and G_1 -> 0
+    o = O.opts(lmax=12)
+    iP = 4 + 13
+    li = O.lna_start(small_params, k)
+    y, _ = O.trajectory(small_params, o, k, np.array([li + 0.5, li + 1.0]))
+    F2 = 2.0 * y[:, 6]  # sigma_g = F_2 / 2
+    np.testing.assert_allclose(y[:, iP] / F2, 1.25, atol=2e-3)
+    np.testing.assert_allclose(y[:, iP + 2] / F2, 0.25, atol=5e-4)
+    assert np.all(np.abs(y[:, iP + 1] / F2) < 1e-4)
+
+
 def test_sachs_wolfe_source_tends_to_psi_over_three():
     # SW bracket delta_g/4 + H alpha' = Theta_0^N + psi; for a superhorizon
     # adiabatic mode this tends to psi/3 as the radiation fades (matter era),
