@@ -328,6 +328,24 @@ def test_polarization_hierarchy_in_tight_coupling(small_params, k):
     assert np.all(np.abs(y[:, iP + 1] / F2) < 1e-4)
 
 
+@pytest.mark.parametrize("k", [0.01, 0.05, 0.2])
+def test_photon_shear_in_tight_coupling(small_params, k):
+    # the l = 2 Thomson term -(9/10) sigma_g / (H tau_c) with the polarization's
+    # G_0 + G_2 = 3/2 F_2 leaves the damping 3/4 F_2 / tau_c, so quasi-statically
+    # sigma_g = (16/45) tau_c (theta_g + k^2 alpha), k^2 alpha = (h-dot + 6 eta-dot)/2,
+    # up to O(1 / (H tau_c)) corrections
+    o = O.opts(lmax=12)
+    li = O.lna_start(small_params, k)
+    lna = li + np.array([0.5, 1.0, 1.5])
+    y, _ = O.trajectory(small_params, o, k, lna)
+    b = O.background(small_params, lna)
+    hp, ep, _ = _metric(b, y, k, o)
+    alpha = b["Hc"] * (hp + 6 * ep) / (2 * k * k)
+    tau_c = 1.0 / (b["Hc"] * b["nuT"])
+    ratio = y[:, 6] / (16.0 / 45.0 * tau_c * (y[:, 5] + k * k * alpha))
+    assert np.all(np.abs(ratio - 1.0) < 10.0 / b["nuT"]), ratio
+
+
 def test_sachs_wolfe_source_tends_to_psi_over_three():
     # SW bracket delta_g/4 + H alpha' = Theta_0^N + psi; for a superhorizon
     # adiabatic mode this tends to psi/3 as the radiation fades (matter era),
