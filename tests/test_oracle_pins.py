@@ -150,6 +150,19 @@ def test_golden_fiducial_conformal_times():
     assert abs(t / g["tau_rec_fid_Mpc"] - 1) < 1e-2
 
 
+def test_golden_fiducial_sound_horizon():
+    # r_s = int_0^tau_rec dtau / sqrt(3 (1 + 3 rho_b / (4 rho_g))) at the paper's
+    # fiducial tau_rec, against its fiducial r_s (App. A.1): pins the baryon
+    # loading (omega_b, T_CMB) and the radiation-era tau(a)
+    g = json.load(open(os.path.join(GOLDEN, "paper_fiducials.json")))
+    lna = np.linspace(-20.0, -6.0, 200001)
+    b = O.background(P_DEF, lna)
+    cs = 1.0 / np.sqrt(3.0 * (1.0 + 0.75 * b["fb"] / b["fg"]))
+    rs = integrate.cumulative_trapezoid(cs / b["Hc"], lna, initial=0.0) + cs[0] * b["tau"][0]
+    r = np.interp(g["tau_rec_fid_Mpc"], b["tau"], rs)
+    assert abs(r / g["rs_rec_fid_Mpc"] - 1) < 2e-3, r
+
+
 # ---------------------------------------------------------------- thermal history
 def test_ionization_history_limits(small_params):
     s = O.scalars(small_params)
