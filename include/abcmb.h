@@ -4,9 +4,18 @@
  *
  *   abcmb_background_tables   thermal history + tau nodes per cosmology
  *   abcmb_perturb             per-k stiff linear perturbation ODEs -> CMB sources
+ *                             (abcmb_perturb_noalloc: the same with fixed scratch)
  *   abcmb_project             line-of-sight projection -> transfer functions
  *   abcmb_cl                  k-quadrature -> C_ell^{TT,TE,EE}
  *   abcmb_project_mixed, abcmb_cl_mixed   the same two steps in FP32
+ * and around them
+ *   abcmb_project_interp, abcmb_transfer_k_grid   projection on the transfer k grid
+ *   abcmb_matter_pk           matter power spectrum P(k, z)
+ *   abcmb_delta_m_nodes, abcmb_cl_psi, abcmb_lens  lensing potential (Limber)
+ *                             and lensed spectra
+ *   abcmb_perturb_taped, abcmb_perturb_adjoint, abcmb_project_adjoint,
+ *   abcmb_cl_adjoint, abcmb_record_vjp            reverse-mode gradients
+ *   abcmb_server_*            a request server over one device arena
  *
  * Conventions shared by every entry point
  *   - Every pointer argument is a DEVICE pointer allocated by the caller
