@@ -117,3 +117,35 @@ def test_workload_is_seeded():
     S1 = W.synthetic_sources(3, 100, 5)
     S2 = W.synthetic_sources(3, 100, 5)
     np.testing.assert_array_equal(S1, S2)
+
+
+def test_variant_entry_points_reject_on_host(A):
+    # each of these returns before its first CUDA call (so it runs without a GPU)
+    L = A.lib()
+    o = A.options()
+    f = ctypes.c_void_p(256)
+    D = ctypes.c_double
+    # P(k): redshift outside [0, 1000], a massive neutrino, hierarchies above 63
+    assert L.abcmb_matter_pk(1, f, f, 4, ctypes.byref(o), D(-0.5), f, f, None) == A.E_INVALID_ARG
+    assert L.abcmb_matter_pk(1, f, f, 4, ctypes.byref(o), D(2000.0), f, f, None) == A.E_INVALID_ARG
+    assert L.abcmb_matter_pk(1, f, f, 4, ctypes.byref(A.options(m_ncdm=0.06)), D(0.0), f, f,
+                             None) == A.E_INVALID_ARG
+    assert L.abcmb_matter_pk(1, f, f, 4, ctypes.byref(A.options(lmax_hier=80)), D(0.0), f, f,
+                             None) == A.E_INVALID_ARG
+    # delta_m at the nodes: empty batch, missing output, massive neutrino, deep hierarchy
+    assert L.abcmb_delta_m_nodes(0, f, f, 4, ctypes.byref(o), f, f, None) == A.E_INVALID_ARG
+    assert L.abcmb_delta_m_nodes(1, f, f, 4, ctypes.byref(o), None, f, None) == A.E_INVALID_ARG
+    assert L.abcmb_delta_m_nodes(1, f, f, 4, ctypes.byref(A.options(m_ncdm=0.06)), f, f, None) == A.E_INVALID_ARG
+    assert L.abcmb_delta_m_nodes(1, f, f, 4, ctypes.byref(A.options(lmax_hier=80)), f, f, None) == A.E_INVALID_ARG
+    # Limber: fewer than 4 k nodes (no Hermite interpolation), l range
+    assert L.abcmb_cl_psi(1, f, f, f, 3, ctypes.byref(o), 100, f, None) == A.E_INVALID_ARG
+    assert L.abcmb_cl_psi(1, f, f, f, 8, ctypes.byref(o), 1, f, None) == A.E_INVALID_ARG
+    assert L.abcmb_cl_psi(1, f, f, f, 8, ctypes.byref(o), 6001, f, None) == A.E_INVALID_ARG
+    # lensing: lmax_out above L, too few Gauss-Legendre nodes
+    assert L.abcmb_lens(1, f, 100, f, 120, 200, f, None) == A.E_INVALID_ARG
+    assert L.abcmb_lens(1, f, 100, f, 80, 100, f, None) == A.E_INVALID_ARG
+    # transfer-grid projection: fewer than 4 ODE k nodes
+    assert L.abcmb_project_interp(1, f, f, f, 3, f, 10, ctypes.byref(o), f, None) == A.E_INVALID_ARG
+    # the transfer grid itself (host function): out-of-range lmax, and its size
+    assert L.abcmb_transfer_k_grid(1, None, 0) == -1
+    assert L.abcmb_transfer_k_grid(2500, None, 0) == 1703
