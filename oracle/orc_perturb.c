@@ -33,7 +33,7 @@
  *   delta_g = delta_nu = -(2/3) C (k tau)^2,  delta_b = delta_c = 3/4 delta_g,
  *   theta_g = theta_b = -C k^4 tau^3 / 18,
  *   theta_nu = theta_g (23 + 4 R_nu) / (15 + 4 R_nu),
- *   sigma_nu = 2 C (k tau)^2 / (3 (15 + 4 R_nu)),
+ *   sigma_nu = 4 C (k tau)^2 / (3 (15 + 4 R_nu)),
  *   eta = 2C - C (k tau)^2 (5 + 4 R_nu) / (6 (15 + 4 R_nu)), all others 0.
  *
  * Integrator: 3-stage Radau IIA collocation (order 5, L-stable).  The system
@@ -218,7 +218,7 @@ void orc_initial(const orc_cosmo *c, const orc_opts *o, double k, double lna_i, 
     y[I_G0 + 1] = tg;
     y[Nn] = dg;
     y[Nn + 1] = tg * (23.0 + 4.0 * Rn) / (15.0 + 4.0 * Rn);
-    y[Nn + 2] = 2.0 * C * kt * kt / (3.0 * (15.0 + 4.0 * Rn));
+    y[Nn + 2] = 4.0 * C * kt * kt / (3.0 * (15.0 + 4.0 * Rn));
     /* massive neutrinos, relativistic at the start: the massless neutrinos'
        delta, theta, sigma carried by each momentum bin (the cited Ma &
        Bertschinger adiabatic mode) */

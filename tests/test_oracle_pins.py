@@ -389,6 +389,28 @@ def test_tight_coupling_and_superhorizon(small_params):
     assert np.all(np.abs(y2[:, 0] - 1.0) < 1e-4)
 
 
+@pytest.mark.parametrize("k", [0.3, 3.0])
+def test_initial_state_solves_the_radiation_era_einstein_equations(small_params, k):
+    # the adiabatic growing mode deep in radiation domination (k tau = 0.07 at
+    # the start) has Newtonian potentials psi = 20 C / (15 + 4 R_nu) and
+    # phi = (1 + 2 R_nu / 5) psi, C = 1/2 (the cited Ma & Bertschinger mode); psi
+    # comes out of the traceless Einstein equation, so it checks the neutrino
+    # shear of the initial state against eta, h' and the other species
+    o = O.opts(lmax=12)
+    Rn = O.scalars(small_params)["R_nu"]
+    lna = np.array([O.lna_start(small_params, k)])
+    y, _ = O.trajectory(small_params, o, k, lna)
+    b = O.background(small_params, lna)
+    hp, ep, iN = _metric(b, y, k, o)
+    alpha = b["Hc"] * (hp + 6 * ep) / (2 * k * k)
+    shear = 4 / 3 * (b["fg"] * y[:, 6] + b["fnu"] * y[:, iN + 2])
+    psi = -b["Hc"] * alpha + y[:, 0] - 4.5 * b["Hc"] ** 2 / k**2 * shear
+    phi = y[:, 0] - b["Hc"] * alpha
+    psi_rd = 10.0 / (15.0 + 4.0 * Rn)
+    assert abs(psi[0] / psi_rd - 1) < 1e-3, psi[0] / psi_rd
+    assert abs(phi[0] / ((1 + 0.4 * Rn) * psi_rd) - 1) < 1e-3
+
+
 def test_matter_era_potential(small_params):
     # superhorizon mode in the matter era: Newtonian potentials phi = eta - H alpha
     # and psi = H alpha' + H alpha approach (3/5) R = 0.6 (App. B.3: R = 1)
