@@ -557,7 +557,7 @@ ABCMB_HD void initial_fwd(const OdeDims &d, double k, double tau_i, double Rn, V
     const double dg = -(2.0 / 3.0) * C * kt * kt;
     const double F1 = -(2.0 / 27.0) * C * kt * kt * kt;
     const double tg = -C * k * kt * kt * kt / 18.0;
-    const double N1 = F1 * (23.0 + 4.0 * Rn) / (15.0 + 4.0 * Rn), N2 = (4.0 / 3.0) * C * kt * kt / (15.0 + 4.0 * Rn);
+    const double N1 = F1 * (23.0 + 4.0 * Rn) / (15.0 + 4.0 * Rn), N2 = (8.0 / 3.0) * C * kt * kt / (15.0 + 4.0 * Rn);
     for (int i = ln_id(); i < d.N; i += ln_n()) {
         double v = 0.0;
         if (i >= d.iM) {
@@ -573,7 +573,7 @@ ABCMB_HD void initial_fwd(const OdeDims &d, double k, double tau_i, double Rn, V
         else if (i == d.iF || i == d.iN) v = dg;
         else if (i == d.iF + 1) v = F1;
         else if (i == d.iN + 1) v = F1 * (23.0 + 4.0 * Rn) / (15.0 + 4.0 * Rn);
-        else if (i == d.iN + 2) v = (4.0 / 3.0) * C * kt * kt / (15.0 + 4.0 * Rn);
+        else if (i == d.iN + 2) v = (8.0 / 3.0) * C * kt * kt / (15.0 + 4.0 * Rn);
         y[i] = v;
     }
     ln_sync();
@@ -591,7 +591,7 @@ ABCMB_HD double initial_dtau(const OdeDims &d, double k, double tau_i, double Rn
     s += yb[1] * 0.75 * ddg + yb[2] * 0.75 * ddg + yb[3] * dtg;
     s += yb[d.iF] * ddg + yb[d.iF + 1] * dF1 + yb[d.iN] * ddg;
     s += yb[d.iN + 1] * dF1 * (23.0 + 4.0 * Rn) / (15.0 + 4.0 * Rn);
-    s += yb[d.iN + 2] * (4.0 / 3.0) * C * 2.0 * kt * dkt / (15.0 + 4.0 * Rn);
+    s += yb[d.iN + 2] * (8.0 / 3.0) * C * 2.0 * kt * dkt / (15.0 + 4.0 * Rn);
     return s;
 }
 
@@ -603,7 +603,7 @@ ABCMB_HD double initial_dRn(const OdeDims &d, double k, double tau_i, double Rn,
     // d/dRn of (5+4Rn)/q = (4 q - 4 (5+4Rn))/q^2 = 40/q^2; of (23+4Rn)/q = -32/q^2; of 1/q = -4/q^2
     double s = yb[0] * (-C * kt * kt / 6.0 * 40.0 / (q * q));
     s += yb[d.iN + 1] * F1 * (-32.0) / (q * q);
-    s += yb[d.iN + 2] * (4.0 / 3.0) * C * kt * kt * (-4.0) / (q * q);
+    s += yb[d.iN + 2] * (8.0 / 3.0) * C * kt * kt * (-4.0) / (q * q);
     return s;
 }
 

@@ -198,7 +198,7 @@ ABCMB_HD void initial_state(const OdeDims &d, const Cosmo &c, double k, double t
     y[d.iF + 1] = F1;
     y[d.iN] = dg;
     y[d.iN + 1] = F1 * (23.0 + 4.0 * Rn) / (15.0 + 4.0 * Rn);
-    y[d.iN + 2] = (4.0 / 3.0) * C * kt * kt / (15.0 + 4.0 * Rn);
+    y[d.iN + 2] = (8.0 / 3.0) * C * kt * kt / (15.0 + 4.0 * Rn);
 }
 
 // Sources at a tau node from the state there (App. B.4, eq. source_functions).

@@ -591,7 +591,7 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
             z[0][1] = F1;
             z[2][0] = dg;
             z[2][1] = F1 * (23.0 + 4.0 * Rn) / (15.0 + 4.0 * Rn);
-            z[2][2] = (4.0 / 3.0) * C * kt * kt / (15.0 + 4.0 * Rn);
+            z[2][2] = (8.0 / 3.0) * C * kt * kt / (15.0 + 4.0 * Rn);
         }
         zs[0] = 2.0 * C - C * kt * kt * (5.0 + 4.0 * Rn) / (6.0 * (15.0 + 4.0 * Rn));
         zs[1] = 0.75 * dg;

@@ -93,14 +93,15 @@ def test_mode_gradient_against_finite_differences(H, rec, k, node):
     regions = [(64 + 8 * 18433, 64 + 28 * 18433), (64 + 28 * 18433, rec.size)]  # ODE table, node data
     checked = 0
     for a, b in regions:
-        for e in a + np.argsort(-np.abs(rb[a:b]))[:4]:
-            for hr in (3e-8, 1e-8, 3e-9, 1e-9):
+        for e in a + np.argsort(-np.abs(rb[a:b]))[:6]:
+            for hr in (3e-8, 1e-8, 3e-9, 1e-9, 3e-10):
                 h = hr * abs(rec[e])
                 rp, rm = rec.copy(), rec.copy()
                 rp[e] += h
                 rm[e] -= h
                 (fp, ap), (fm, am) = phi(rp), phi(rm)
-                if ap == am == acc0:
+                # a difference within rounding of the output checks nothing
+                if ap == am == acc0 and abs(fp - fm) > 1e-11 * max(abs(fp), abs(fm)):
                     fd = (fp - fm) / (2 * h)
                     assert abs(rb[e] - fd) <= 2e-3 * abs(fd), (e, rb[e], fd)
                     checked += 1
@@ -112,7 +113,9 @@ def test_mode_gradient_against_finite_differences(H, rec, k, node):
 def test_node_position_gradient(H, rec, k, node):
     # a node's ln a moves the sources there with the ODE flow and the
     # background's slope; later nodes are unaffected up to the integration error
-    n_tau, L, rtol = 120, 8, 1e-9
+    # (rtol 2e-9: at 1e-9 the unperturbed k = 0.02 run sits on an accept/reject
+    # boundary that every node perturbation flips, leaving no step to compare)
+    n_tau, L, rtol = 120, 8, 2e-9
     rng = np.random.default_rng(7 + node)
     Sb = rng.normal(size=(n_tau, 3))
 
