@@ -374,6 +374,35 @@ def test_sachs_wolfe_source_tends_to_psi_over_three():
     assert 1.0 < ratio[20] < 1.02 and ratio[20] < ratio[100] < ratio[200] < 1.12, ratio
 
 
+@pytest.mark.parametrize("k,lna0", [(0.01, -7.0), (0.05, -7.5), (0.2, -7.2)])
+def test_einstein_equations_close_in_tight_coupling(small_params, k, lna0):
+    # h' comes from the 00 constraint and eta' from the 0i constraint, so the
+    # trace (ij) equation h-ddot + 2 H h-dot - 2 k^2 eta = -9 H^2 dP/rho_tot holds
+    # only if every species conserves energy, and the traceless one (through
+    # d alpha / d tau) only if the photon-baryon drag and the other momentum
+    # equations conserve momentum; checked by finite differences along the
+    # solution while Thomson scattering is fast
+    o = O.opts(lmax=20, step_c=0.02)
+    lna = np.linspace(lna0, lna0 + 0.02, 41)
+    y, _ = O.trajectory(small_params, o, k, lna)
+    b = O.background(small_params, lna)
+    hp, ep, iN = _metric(b, y, k, o)
+    H = b["Hc"]
+    hdot = H * hp
+    hddot = H * np.gradient(hdot, lna, edge_order=2)
+    lhs = hddot + 2 * H * hdot - 2 * k * k * y[:, 0]
+    rhs = -3 * H**2 * (b["fg"] * y[:, 4] + b["fnu"] * y[:, iN]) - 9 * H**2 * b["fb"] * b["cs2"] * y[:, 2]
+    scale = np.max(np.abs(np.stack([hddot, 2 * H * hdot, 2 * k * k * y[:, 0], rhs])), axis=0)
+    sl = slice(3, -3)
+    assert np.max(np.abs(lhs - rhs)[sl] / scale[sl]) < 2e-6
+    alpha = H * (hp + 6 * ep) / (2 * k * k)
+    shear = 4 / 3 * (b["fg"] * y[:, 6] + b["fnu"] * y[:, iN + 2])
+    Hap = -2 * H * alpha + y[:, 0] - 4.5 * H**2 / k**2 * shear
+    num = np.gradient(alpha, lna, edge_order=2) * H
+    scale = np.max(np.abs(np.stack([2 * H * alpha, y[:, 0], Hap])), axis=0)
+    assert np.max(np.abs(num - Hap)[sl] / scale[sl]) < 2e-6
+
+
 def test_tight_coupling_and_superhorizon(small_params):
     o = O.opts(lmax=12)
     k = 0.1
