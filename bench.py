@@ -31,10 +31,12 @@ from paper_2602_15104_gb300 import workload as W  # noqa: E402
 METRIC = "C_ℓ spectra/s at ℓmax=2500 TT/TE/EE (≤1e-5 rel vs FP64 oracle); p50/p99 latency"
 FP64_PEAK = 2 * 2 * 152 * 2.07e9  # FMA units/SM x flops/FMA x SMs x max SM clock (1.26 TFLOP/s)
 FLUSH_BYTES = 512 << 20
-# DRAM bytes (read + write) per mode of the FP64 perturbation kernel, from an
-# ncu capture of 64 cosmologies x 40 k (1.452 GB read + 0.364 GB written over
-# 2560 modes); traffic grows in proportion to the modes
-PERTURB_DRAM_BYTES_PER_MODE = (1.451698e9 + 0.363785e9) / 2560
+# DRAM bytes (read + write) per mode of the FP64 perturbation kernel from an
+# ncu capture of the kernel as built (traffic grows in proportion to the
+# modes); None while no capture of the current source exists.  The capture of
+# the previous source (64 cosmologies x 40 k) read 1.452 GB and wrote
+# 0.364 GB over 2560 modes.
+PERTURB_DRAM_BYTES_PER_MODE = None
 
 
 def flops_per_substep(N: int) -> float:
@@ -536,7 +538,8 @@ def main():
     dom = max(kavg, key=kavg.get)
     if dom in flops:
         ach = flops[dom] / (kavg[dom] * 1e-3)
-        traffic = PERTURB_DRAM_BYTES_PER_MODE * B * len(k) if dom == "perturb" else None
+        traffic = (PERTURB_DRAM_BYTES_PER_MODE * B * len(k)
+                   if dom == "perturb" and PERTURB_DRAM_BYTES_PER_MODE is not None else None)
         roof = {"kernel": dom, "bound": "alu", "achieved": ach / 1e12, "peak": FP64_PEAK / 1e12,
                 "unit": "TFLOP/s", "frac": ach / FP64_PEAK, "traffic": traffic,
                 "peak_source": "FP64 pipe: 2 FMA/clk/SM x 152 SMs x 2070 MHz (nominal 1.25 TFLOP/s)"}
