@@ -1,0 +1,28 @@
+// Host build of the thread-per-mode perturbation solver (abcmb_ode.cuh, the
+// path for hierarchies above 63) for the CPU parity tests against the oracle.
+#include <vector>
+
+#include "abcmb_ode.cuh"
+
+using namespace abcmb;
+
+extern "C" long h_bg_len(int n_tau) { return ABCMB_BG_NODES + 8L * n_tau; }
+
+extern "C" void h_build_bg(const double *p, int n_tau, double *rec) { build_background(p, rec, n_tau, 0, 1); }
+
+// sources S[n_tau][3] of one mode with all three hierarchies at L; returns the status
+extern "C" int h_integrate(const double *rec, double k, int L, double rtol, double *S, int *steps)
+{
+    static double a[129], b[129]; // l = 0..128, the deepest hierarchy
+    for (int l = 0; l <= 128; l++) {
+        a[l] = (double)l / (2.0 * l + 1.0);
+        b[l] = (l + 1.0) / (2.0 * l + 1.0);
+    }
+    const OdeDims d = ode_dims(L, L, L);
+    std::vector<double> work((size_t)kNvec * d.N, 0.0);
+    const double sw[3] = {1.0, 1.0, 1.0};
+    const ModeResult r = integrate_mode(d, StreamCoef{a, b}, rec, k, rtol, 1e-12, 2000000, sw, work.data(), 1, S);
+    steps[0] = r.steps;
+    steps[1] = r.substeps;
+    return r.status;
+}
