@@ -382,7 +382,7 @@ def test_einstein_equations_close_in_tight_coupling(small_params, k, lna0):
     # d alpha / d tau) only if the photon-baryon drag and the other momentum
     # equations conserve momentum; checked by finite differences along the
     # solution while Thomson scattering is fast
-    o = O.opts(lmax=20, step_c=0.02)
+    o = O.opts(lmax=8, step_c=0.02)  # the closure does not depend on the truncation
     lna = np.linspace(lna0, lna0 + 0.02, 41)
     y, _ = O.trajectory(small_params, o, k, lna)
     b = O.background(small_params, lna)
@@ -704,9 +704,9 @@ def test_ncdm_hierarchy_massless_limit(small_params):
     # neutrinos' F_l times -dlnf0/dlnq / 4 (Psi_1 = -dlnf theta / (3k),
     # Psi_2 = -dlnf sigma / 2), whatever the metric does
     L = 10
-    o = O.opts(lmax=L, m_ncdm=1e-7, lmax_ncdm=L, step_c=0.02)
+    o = O.opts(lmax=L, m_ncdm=1e-7, lmax_ncdm=L)
     k = 0.05
-    lna = np.array([-9.0, -7.0, -5.0, -2.0, -0.5])
+    lna = np.array([-9.0, -7.0, -5.0, -2.0])
     y, _ = O.trajectory(small_params, o, k, lna)
     iN = 4 + 2 * (L + 1)
     i0 = iN + L + 1
