@@ -65,7 +65,7 @@ def test_limber_lensing_potential_matches_oracle(H):
     from paper_2602_15104_gb300 import workload as W
     p = W.SMALL_TT.params()[0]
     n_tau, lmax = 300, 150
-    k = np.exp(np.linspace(np.log(1e-4), np.log(0.3), 40))
+    k = np.exp(np.linspace(np.log(1e-4), np.log(0.15), 24))
     o = O.opts(lmax=8)
     ref = LZ.cl_psi(p, k, n_tau, lmax, o)
     lna, tau, w = O.nodes(p, n_tau)

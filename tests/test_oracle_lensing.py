@@ -126,7 +126,7 @@ def test_lensing_potential_spectrum_of_a_lcdm_cosmology():
     import oracle as O
     from paper_2602_15104_gb300 import workload as W
     p = W.SMALL_TT.params()[0]
-    k = np.exp(np.linspace(np.log(1e-4), np.log(0.5), 60))
+    k = np.exp(np.linspace(np.log(1e-4), np.log(0.3), 40))
     c = LZ.cl_psi(p, k, 400, 200, O.opts(lmax=8))
     l = np.arange(201)
     v = (l * (l + 1.0)) ** 2 * c / (2 * np.pi)
