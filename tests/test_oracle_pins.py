@@ -150,6 +150,20 @@ def test_golden_fiducial_conformal_times():
     assert abs(t / g["tau_rec_fid_Mpc"] - 1) < 1e-2
 
 
+def test_visibility_peak_at_the_paper_fiducial_recombination():
+    # the peak of g(tau) for the default cosmology against the paper's fiducial
+    # conformal time of recombination (App. A.1 tau_rec_fid): pins the timing of
+    # the recombination history set by the n=2 bottleneck of the three-level atom.
+    # The paper's HyRex and this atom differ by 0.14 % here; dropping the Peebles
+    # C factor moves the peak by -12 %, halving the Lyman-alpha escape rate by
+    # -1.4 %.  (The case-B coefficient itself barely moves it: 2x gives -0.2 %.)
+    g = json.load(open(os.path.join(GOLDEN, "paper_fiducials.json")))
+    lna = np.linspace(-7.3, -6.8, 20001)
+    b = O.background(P_DEF, lna)
+    t = b["tau"][int(np.argmax(b["g"]))]
+    assert abs(t / g["tau_rec_fid_Mpc"] - 1) < 5e-3, t
+
+
 def test_golden_fiducial_sound_horizon():
     # r_s = int_0^tau_rec dtau / sqrt(3 (1 + 3 rho_b / (4 rho_g))) at the paper's
     # fiducial tau_rec, against its fiducial r_s (App. A.1): pins the baryon
