@@ -454,6 +454,26 @@ def test_initial_state_solves_the_radiation_era_einstein_equations(small_params,
     assert abs(phi[0] / ((1 + 0.4 * Rn) * psi_rd) - 1) < 1e-3
 
 
+@pytest.mark.parametrize("k", [1.0, 3.0])
+def test_superhorizon_radiation_era_solution_is_kept(small_params, k):
+    # deep in radiation domination and outside the horizon the adiabatic mode
+    # grows as its leading-order form (powers of k tau, C = 1/2); the integrated
+    # solution must follow it as k tau grows from 0.07 to 0.15, which checks the
+    # metric terms of every l <= 2 equation (O((k tau)^2) corrections: ~0.2 %)
+    o = O.opts(lmax=12)
+    iN = 4 + 2 * 13
+    Rn = O.scalars(small_params)["R_nu"]
+    lna = O.lna_start(small_params, k) + np.array([0.25, 0.5, 0.75])
+    y, _ = O.trajectory(small_params, o, k, lna)
+    kt = k * O.background(small_params, lna)["tau"]
+    C, q = 0.5, 15.0 + 4.0 * Rn
+    ref = {0: 2 * C - C * kt**2 * (5 + 4 * Rn) / (6 * q), 1: -0.5 * C * kt**2, 4: -2 / 3 * C * kt**2,
+           5: -C * k * kt**3 / 18, iN: -2 / 3 * C * kt**2, iN + 1: -C * k * kt**3 / 18 * (23 + 4 * Rn) / q,
+           iN + 2: 4 * C * kt**2 / (3 * q)}
+    for i, r in ref.items():
+        np.testing.assert_allclose(y[:, i], r, rtol=1e-2, err_msg=str(i))
+
+
 def test_matter_era_potential(small_params):
     # superhorizon mode in the matter era: Newtonian potentials phi = eta - H alpha
     # and psi = H alpha' + H alpha approach (3/5) R = 0.6 (App. B.3: R = 1)
