@@ -37,7 +37,7 @@ def lib():
         L = ctypes.CDLL(path)
         L.orc_scalars.argtypes = [_D, ctypes.c_int, ctypes.c_double, _D]
         L.orc_background.argtypes = [_D, ctypes.c_int, ctypes.c_double, _D, ctypes.c_int, _D]
-        L.orc_nodes.argtypes = [_D, ctypes.c_int, ctypes.c_double, _D]
+        L.orc_nodes.argtypes = [_D, ctypes.c_int, ctypes.c_double, ctypes.c_int, _D]
         L.orc_nstate_of.argtypes = [_D]
         L.orc_lna_start_of.argtypes = [_D, ctypes.c_double, ctypes.c_double]
         L.orc_lna_start_of.restype = ctypes.c_double
@@ -69,17 +69,18 @@ def _arr(x):
 
 def opts(lmax=12, lmax_g=None, lmax_pol=None, lmax_nu=None, scale_sw=1.0, scale_isw=1.0,
          scale_dop=1.0, scale_pol=1.0, step_c=0.05, step_cap=0.05, hooks=0, max_steps=0,
-         m_ncdm=0.0, lmax_ncdm=17):
+         m_ncdm=0.0, lmax_ncdm=17, node_recipe=0):
     """Options vector: hierarchy truncations, source switches (App. A.1), the
     step schedule of the oracle's integrator, test hooks, and one massive
     neutrino of mass m_ncdm [eV] with hierarchies to lmax_ncdm (m_ncdm = 0:
-    three massless neutrinos only)."""
+    three massless neutrinos only), and the tau-node recipe (0 the default
+    placement, 1 the refined tail)."""
     lg = lmax if lmax_g is None else lmax_g
     lp = lmax if lmax_pol is None else lmax_pol
     ln = lmax if lmax_nu is None else lmax_nu
     lm = lmax_ncdm if m_ncdm > 0.0 else 0
     return np.array([lg, lp, ln, scale_sw, scale_isw, scale_dop, scale_pol, step_c, step_cap,
-                     hooks, max_steps, lm, m_ncdm], dtype=np.float64)
+                     hooks, max_steps, lm, m_ncdm, node_recipe], dtype=np.float64)
 
 
 def nstate(o):
@@ -103,9 +104,9 @@ def background(params, lna, hooks=0, m_ncdm=0.0):
     return {f: out[:, i] for i, f in enumerate(BG_FIELDS)}
 
 
-def nodes(params, n_tau, m_ncdm=0.0):
+def nodes(params, n_tau, m_ncdm=0.0, node_recipe=0):
     out = np.zeros((3, n_tau))
-    if lib().orc_nodes(_p(_arr(params)), n_tau, float(m_ncdm), _p(out)):
+    if lib().orc_nodes(_p(_arr(params)), n_tau, float(m_ncdm), int(node_recipe), _p(out)):
         raise RuntimeError("oracle nodes failed")
     return out[0], out[1], out[2]
 

@@ -53,6 +53,7 @@ typedef struct {
     int lmax_ncdm;   /* massive-neutrino hierarchies' truncation (0: none)      */
     double m_ncdm;   /* one massive neutrino of this mass [eV] (0: none); the
                         massless species then number two (App. A.1 example)   */
+    int node_recipe; /* tau nodes: 0 the default placement, 1 the refined tail */
 } orc_opts;
 
 /* Per-cosmology state: derived parameters, thermal-history tables, tau nodes. */
@@ -108,7 +109,7 @@ typedef struct {
 } orc_bg;
 
 /* orc_background.c */
-int orc_cosmo_init(orc_cosmo *c, const double p[6], int n_tau, int hooks, double m_ncdm);
+int orc_cosmo_init(orc_cosmo *c, const double p[6], int n_tau, int hooks, double m_ncdm, int node_recipe);
 void orc_cosmo_free(orc_cosmo *c);
 /* with_thermo: 0 background only, 1 + what the ODE needs, 2 + kappa, g, g' */
 void orc_bg_eval(const orc_cosmo *c, double lna, orc_bg *out, int with_thermo);

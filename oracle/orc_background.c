@@ -541,7 +541,7 @@ static double tau_reion_of(const orc_cosmo *c, double zre, gl_rule *gl)
     return acc;
 }
 
-int orc_cosmo_init(orc_cosmo *c, const double p[6], int n_tau, int hooks, double m_ncdm)
+int orc_cosmo_init(orc_cosmo *c, const double p[6], int n_tau, int hooks, double m_ncdm, int node_recipe)
 {
     memset(c, 0, sizeof(*c));
     gl_rule gl = gl_make();
@@ -667,7 +667,12 @@ int orc_cosmo_init(orc_cosmo *c, const double p[6], int n_tau, int hooks, double
 
     /* tau nodes */
     if (n_tau >= 4) {
-        int nA = n_tau / 4, nB = n_tau / 2, nC = n_tau - nA - nB;
+        /* recipe 0: 1/4 uniform in ln a to z = 1300, 1/2 uniform in z over
+           [1300, 900), the rest uniform in tau from z = 900 to today; recipe 1:
+           1/5, 2/5 over [1300, 900), 1/5 uniform in z over [900, 300), the rest
+           uniform in tau from z = 300 (resolves the visibility's tail) */
+        int nA = node_recipe ? n_tau / 5 : n_tau / 4, nB = node_recipe ? 2 * n_tau / 5 : n_tau / 2;
+        int nD = node_recipe ? n_tau / 5 : 0, nC = n_tau - nA - nB - nD;
         c->n_tau = n_tau;
         c->node_lna = (double *)malloc(sizeof(double) * n_tau);
         c->node_tau = (double *)malloc(sizeof(double) * n_tau);
@@ -677,10 +682,13 @@ int orc_cosmo_init(orc_cosmo *c, const double p[6], int n_tau, int hooks, double
             c->node_lna[j] = c->lna_tc + (l1300 - c->lna_tc) * j / nA;
         for (int j = 0; j < nB; j++)
             c->node_lna[nA + j] = -log(1.0 + 1300.0 - 400.0 * j / nB);
-        double t900 = orc_tau_of_lna(c, l900);
+        for (int j = 0; j < nD; j++)
+            c->node_lna[nA + nB + j] = -log(1.0 + 900.0 - 600.0 * j / nD);
+        double lC = node_recipe ? -log(301.0) : l900;
+        double tC = orc_tau_of_lna(c, lC);
         for (int j = 0; j < nC; j++) {
-            double tt = t900 + (c->tau0 - t900) * j / nC;
-            c->node_lna[nA + nB + j] = j == 0 ? l900 : bisect(f_tau, c, tt, l900, 0.0);
+            double tt = tC + (c->tau0 - tC) * j / nC;
+            c->node_lna[nA + nB + nD + j] = j == 0 ? lC : bisect(f_tau, c, tt, lC, 0.0);
         }
         for (int j = 0; j < n_tau; j++) c->node_tau[j] = orc_tau_of_lna(c, c->node_lna[j]);
         for (int j = 0; j < n_tau; j++) {
@@ -712,7 +720,7 @@ double orc_lna_start(const orc_cosmo *c, double k)
 int orc_ncdm_density(const double *p, double m_ncdm, double a, double *out)
 {
     orc_cosmo c;
-    if (orc_cosmo_init(&c, p, 0, 0, m_ncdm)) return -1;
+    if (orc_cosmo_init(&c, p, 0, 0, m_ncdm, 0)) return -1;
     ncdm_rho_p(&c, a, &out[0], &out[1]);
     out[2] = c.Om_ncdm_rel;
     out[3] = c.ncdm_x1;

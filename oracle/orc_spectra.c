@@ -122,7 +122,7 @@ static void opts_from(const double *oa, orc_opts *o)
     o->lmax_g = (int)oa[0]; o->lmax_pol = (int)oa[1]; o->lmax_nu = (int)oa[2];
     o->scale_sw = oa[3]; o->scale_isw = oa[4]; o->scale_dop = oa[5]; o->scale_pol = oa[6];
     o->step_c = oa[7]; o->step_cap = oa[8]; o->hooks = (int)oa[9]; o->max_steps = (long)oa[10];
-    o->lmax_ncdm = (int)oa[11]; o->m_ncdm = oa[12];
+    o->lmax_ncdm = (int)oa[11]; o->m_ncdm = oa[12]; o->node_recipe = (int)oa[13];
 }
 
 static void set_threads(int nthreads)
@@ -141,7 +141,7 @@ static void set_threads(int nthreads)
 int orc_scalars(const double *p, int hooks, double m_ncdm, double *out)
 {
     orc_cosmo c;
-    if (orc_cosmo_init(&c, p, 0, hooks, m_ncdm)) return -1;
+    if (orc_cosmo_init(&c, p, 0, hooks, m_ncdm, 0)) return -1;
     double v[17] = {c.H0, c.Om_b, c.Om_c, c.Om_g, c.Om_nu, c.Om_L, c.R_nu, c.f_He,
                     c.nH0, c.A_s, c.z_reion, c.lna_tc, c.lna_sw, c.tau0, c.lna_He3, c.n_s, c.Om_ncdm};
     memcpy(out, v, sizeof(v));
@@ -154,7 +154,7 @@ int orc_scalars(const double *p, int hooks, double m_ncdm, double *out)
 int orc_background(const double *p, int hooks, double m_ncdm, const double *lna, int n, double *out)
 {
     orc_cosmo c;
-    if (orc_cosmo_init(&c, p, 0, hooks, m_ncdm)) return -1;
+    if (orc_cosmo_init(&c, p, 0, hooks, m_ncdm, 0)) return -1;
     for (int i = 0; i < n; i++) {
         orc_bg b;
         orc_bg_eval(&c, lna[i], &b, 2);
@@ -167,10 +167,10 @@ int orc_background(const double *p, int hooks, double m_ncdm, const double *lna,
 }
 
 /* tau nodes: out[3][n_tau] = lna, tau, w */
-int orc_nodes(const double *p, int n_tau, double m_ncdm, double *out)
+int orc_nodes(const double *p, int n_tau, double m_ncdm, int node_recipe, double *out)
 {
     orc_cosmo c;
-    if (orc_cosmo_init(&c, p, n_tau, 0, m_ncdm)) return -1;
+    if (orc_cosmo_init(&c, p, n_tau, 0, m_ncdm, node_recipe)) return -1;
     memcpy(out, c.node_lna, sizeof(double) * n_tau);
     memcpy(out + n_tau, c.node_tau, sizeof(double) * n_tau);
     memcpy(out + 2 * n_tau, c.node_w, sizeof(double) * n_tau);
@@ -188,7 +188,7 @@ int orc_nstate_of(const double *oa)
 double orc_lna_start_of(const double *p, double k, double m_ncdm)
 {
     orc_cosmo c;
-    if (orc_cosmo_init(&c, p, 0, 0, m_ncdm)) return NAN;
+    if (orc_cosmo_init(&c, p, 0, 0, m_ncdm, 0)) return NAN;
     double v = orc_lna_start(&c, k);
     orc_cosmo_free(&c);
     return v;
@@ -201,7 +201,7 @@ int orc_trajectory(const double *p, const double *oa, double k, const double *ln
     orc_cosmo c;
     orc_opts o;
     opts_from(oa, &o);
-    if (orc_cosmo_init(&c, p, 0, o.hooks & ORC_HOOK_EDS_CDM, o.m_ncdm)) return -1;
+    if (orc_cosmo_init(&c, p, 0, o.hooks & ORC_HOOK_EDS_CDM, o.m_ncdm, 0)) return -1;
     int rc = orc_solve_mode(&c, &o, k, lna_out, n, y_out, y_init, lna_init, steps);
     orc_cosmo_free(&c);
     return rc;
@@ -213,7 +213,7 @@ int orc_rhs_at(const double *p, const double *oa, double k, double lna, const do
     orc_cosmo c;
     orc_opts o;
     opts_from(oa, &o);
-    if (orc_cosmo_init(&c, p, 0, o.hooks & ORC_HOOK_EDS_CDM, o.m_ncdm)) return -1;
+    if (orc_cosmo_init(&c, p, 0, o.hooks & ORC_HOOK_EDS_CDM, o.m_ncdm, 0)) return -1;
     orc_rhs(&c, &o, k, lna, y, dy);
     orc_cosmo_free(&c);
     return 0;
@@ -279,7 +279,7 @@ int orc_run(const double *p, int n_tau, const double *oa, const double *k, int n
     orc_cosmo c;
     orc_opts o;
     opts_from(oa, &o);
-    if (orc_cosmo_init(&c, p, n_tau, o.hooks & ORC_HOOK_EDS_CDM, o.m_ncdm)) return -1;
+    if (orc_cosmo_init(&c, p, n_tau, o.hooks & ORC_HOOK_EDS_CDM, o.m_ncdm, o.node_recipe)) return -1;
     set_threads(nthreads);
     double *S = S_out ? S_out : (double *)malloc(sizeof(double) * (size_t)nk * n_tau * 3);
     int rc = 0;
@@ -307,7 +307,7 @@ int orc_run(const double *p, int n_tau, const double *oa, const double *k, int n
 void *orc_create(const double *p, int n_tau, int hooks, double m_ncdm)
 {
     orc_cosmo *c = (orc_cosmo *)malloc(sizeof(orc_cosmo));
-    if (orc_cosmo_init(c, p, n_tau, hooks, m_ncdm)) { orc_cosmo_free(c); free(c); return NULL; }
+    if (orc_cosmo_init(c, p, n_tau, hooks, m_ncdm, 0)) { orc_cosmo_free(c); free(c); return NULL; }
     return c;
 }
 
@@ -360,7 +360,7 @@ int orc_initial_at(const double *p, const double *oa, double k, double lna, doub
     orc_cosmo c;
     orc_opts o;
     opts_from(oa, &o);
-    if (orc_cosmo_init(&c, p, 0, 0, o.m_ncdm)) return -1;
+    if (orc_cosmo_init(&c, p, 0, 0, o.m_ncdm, 0)) return -1;
     orc_initial(&c, &o, k, lna, y);
     orc_cosmo_free(&c);
     return 0;
@@ -372,7 +372,7 @@ int orc_count_steps(const double *p, int n_tau, const double *oa, const double *
     orc_cosmo c;
     orc_opts o;
     opts_from(oa, &o);
-    if (orc_cosmo_init(&c, p, n_tau, 0, o.m_ncdm)) return -1;
+    if (orc_cosmo_init(&c, p, n_tau, 0, o.m_ncdm, o.node_recipe)) return -1;
     for (int i = 0; i < nk; i++) {
         double x = orc_lna_start(&c, k[i]);
         long n = 0;
@@ -397,7 +397,7 @@ int orc_pk(const double *p, const double *oa, const double *k, int nk, double z,
     orc_cosmo c;
     orc_opts o;
     opts_from(oa, &o);
-    if (orc_cosmo_init(&c, p, 0, o.hooks & ORC_HOOK_EDS_CDM, o.m_ncdm)) return -1;
+    if (orc_cosmo_init(&c, p, 0, o.hooks & ORC_HOOK_EDS_CDM, o.m_ncdm, 0)) return -1;
     set_threads(nthreads);
     const double lna = -log1p(z);
     orc_bg b;
@@ -434,7 +434,7 @@ int orc_delta_m_nodes(const double *p, int n_tau, const double *oa, const double
     orc_cosmo c;
     orc_opts o;
     opts_from(oa, &o);
-    if (orc_cosmo_init(&c, p, n_tau, o.hooks & ORC_HOOK_EDS_CDM, o.m_ncdm)) return -1;
+    if (orc_cosmo_init(&c, p, n_tau, o.hooks & ORC_HOOK_EDS_CDM, o.m_ncdm, o.node_recipe)) return -1;
     set_threads(nthreads);
     const int N = orc_nstate(&o);
     int rc = 0;
