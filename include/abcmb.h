@@ -77,7 +77,11 @@ typedef struct {
                         two and the massive one has T = 0.71611 T_gamma (App. A.1 example) */
     int lmax_ncdm;   /* its momentum-bin hierarchies' truncation: 0 when m_ncdm = 0, else
                         3..63 (App. A.1 l_max_massive_nu, default 17)                      */
-    int reserved_;   /* zero                                                               */
+    int node_recipe; /* tau nodes: 0 = 1/4 uniform in ln a from a_tc to z = 1300, 1/2 uniform
+                        in z over [1300, 900), the rest uniform in tau to today (default);
+                        1 = 1/5, 2/5 over [1300, 900), 1/5 uniform in z over [900, 300),
+                        the rest uniform in tau from z = 300, which resolves the tail of
+                        the visibility function (low-l TT converges with ~10x fewer nodes) */
 } abcmb_options;
 
 /* Fill *o with the defaults used by the library's tests: hierarchies 12,

@@ -496,7 +496,8 @@ ABCMB_HD double tau_reion_par(const Cosmo &c, double zre, int lane, int nl)
 }
 
 // ---- the builder (lane = 0..nl-1 of the warp that owns this cosmology) ----
-ABCMB_HD void build_background(const double *p, double *rec, int n_tau, int lane, int nl, double m_ncdm = 0.0)
+ABCMB_HD void build_background(const double *p, double *rec, int n_tau, int lane, int nl, double m_ncdm = 0.0,
+                               int node_recipe = 0)
 {
     double *tab = rec + ABCMB_BG_TABLE;
     double *otab = rec + ABCMB_BG_ODETAB;
@@ -766,21 +767,27 @@ ABCMB_HD void build_background(const double *p, double *rec, int n_tau, int lane
     // tau nodes (lane-parallel)
     double node_fail = 0.0;
     if (n_tau >= 8) {
-        const int nA = n_tau / 4, nB = n_tau / 2, nC = n_tau - nA - nB;
-        const double l1300 = -log(1301.0), l900 = -log(901.0);
-        const Herm H9 = herm_at(l900);
-        const double t900 = herm_val(tab, H9, C_TAU, C_DTAU);
+        // recipe 0: 1/4 uniform in ln a to z = 1300, 1/2 uniform in z over
+        // [1300, 900), the rest uniform in tau from z = 900 to today; recipe 1
+        // (refined tail): 1/5, 2/5 over [1300, 900), 1/5 uniform in z over
+        // [900, 300), the rest uniform in tau from z = 300
+        const int nA = node_recipe ? n_tau / 5 : n_tau / 4, nB = node_recipe ? 2 * n_tau / 5 : n_tau / 2;
+        const int nD = node_recipe ? n_tau / 5 : 0, nC = n_tau - nA - nB - nD;
+        const double l1300 = -log(1301.0), lC = -log(1.0 + (node_recipe ? 300.0 : 900.0));
+        const Herm HC = herm_at(lC);
+        const double tC = herm_val(tab, HC, C_TAU, C_DTAU);
         for (int i = lane; i < n_tau; i += nl) {
             double lna;
             if (i < nA) lna = c.lna_tc + (l1300 - c.lna_tc) * i / nA;
             else if (i < nA + nB) lna = -log(1.0 + 1300.0 - 400.0 * (i - nA) / nB);
+            else if (i < nA + nB + nD) lna = -log(1.0 + 900.0 - 600.0 * (i - nA - nB) / nD);
             else {
-                const int jc = i - nA - nB;
-                const double tt = t900 + (c.tau0 - t900) * jc / nC;
+                const int jc = i - nA - nB - nD;
+                const double tt = tC + (c.tau0 - tC) * jc / nC;
                 bool ok2 = true;
-                lna = jc == 0 ? l900
+                lna = jc == 0 ? lC
                     : bisect([&](double l) { Herm H = herm_at(l); return herm_val(tab, H, C_TAU, C_DTAU); },
-                             tt, l900, 0.0, &ok2);
+                             tt, lC, 0.0, &ok2);
                 if (!ok2) node_fail = 1.0;
             }
             const Herm H = herm_at(lna);

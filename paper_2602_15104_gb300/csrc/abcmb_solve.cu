@@ -23,11 +23,12 @@ namespace abcmb {
 
 // one warp (32 threads) per cosmology
 __global__ void __launch_bounds__(32) background_kernel(int B, const double *__restrict__ params, double *bg,
-                                                         long len, int n_tau, double m_ncdm)
+                                                         long len, int n_tau, double m_ncdm, int node_recipe)
 {
     const int b = blockIdx.x;
     if (b >= B) return;
-    build_background(params + (long)b * ABCMB_NPARAM, bg + (long)b * len, n_tau, threadIdx.x, 32, m_ncdm);
+    build_background(params + (long)b * ABCMB_NPARAM, bg + (long)b * len, n_tau, threadIdx.x, 32, m_ncdm,
+                     node_recipe);
 }
 
 constexpr int kLmaxHier = 128;
@@ -137,7 +138,7 @@ extern "C" void abcmb_default_options(abcmb_options *o)
     o->scale_sw = o->scale_isw = o->scale_dop = o->scale_pol = 1.0;
     o->m_ncdm = 0.0;
     o->lmax_ncdm = 0;
-    o->reserved_ = 0;
+    o->node_recipe = 0;
 }
 
 extern "C" int abcmb_validate_options(const abcmb_options *o)
@@ -153,6 +154,7 @@ extern "C" int abcmb_validate_options(const abcmb_options *o)
     if (!(o->m_ncdm >= 0.0 && o->m_ncdm <= 100.0)) return ABCMB_E_INVALID_ARG;
     if (o->m_ncdm == 0.0 ? o->lmax_ncdm != 0 : (o->lmax_ncdm < 3 || o->lmax_ncdm > abcmb::kQLmax))
         return ABCMB_E_INVALID_ARG;
+    if (o->node_recipe != 0 && o->node_recipe != 1) return ABCMB_E_INVALID_ARG;
     return ABCMB_OK;
 }
 
@@ -248,7 +250,8 @@ extern "C" int abcmb_background_tables(int B, const double *params, const abcmb_
 {
     if (B < 1 || !params || !bg || abcmb_validate_options(o) != ABCMB_OK) return ABCMB_E_INVALID_ARG;
     const long len = (long)abcmb_bg_doubles(o);
-    abcmb::background_kernel<<<B, 32, 0, (cudaStream_t)stream>>>(B, params, bg, len, o->n_tau, o->m_ncdm);
+    abcmb::background_kernel<<<B, 32, 0, (cudaStream_t)stream>>>(B, params, bg, len, o->n_tau, o->m_ncdm,
+                                                                  o->node_recipe);
     return cudaGetLastError() == cudaSuccess ? ABCMB_OK : ABCMB_E_CUDA;
 }
 

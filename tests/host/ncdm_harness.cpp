@@ -15,6 +15,12 @@ extern "C" void h_build_bg_m(const double *p, int n_tau, double m_ncdm, double *
     build_background(p, rec, n_tau, 0, 1, m_ncdm);
 }
 
+// the same with a tau-node recipe (0 the default placement, 1 the refined tail)
+extern "C" void h_build_bg_r(const double *p, int n_tau, double m_ncdm, int recipe, double *rec)
+{
+    build_background(p, rec, n_tau, 0, 1, m_ncdm, recipe);
+}
+
 // sources S[n_tau][3] of one mode; hierarchies L (all three massless chains), Lm
 extern "C" int h_fwd_m(const double *rec, double k, int L, int Lm, double rtol, double *S)
 {

@@ -31,22 +31,23 @@ def H(tmp_path_factory):
     L = ctypes.CDLL(so)
     L.h_bg_len.restype = ctypes.c_long
     L.h_build_bg_m.argtypes = [P, I, D, P]
+    L.h_build_bg_r.argtypes = [P, I, D, I, P]
     L.h_fwd_m.argtypes = [P, D, I, I, D, P]
     return L
 
 
-def record(H, p, n_tau):
+def record(H, p, n_tau, recipe=0):
     r = np.zeros(H.h_bg_len(n_tau))
-    H.h_build_bg_m(np.ascontiguousarray(p).ctypes.data_as(P), n_tau, 0.0, r.ctypes.data_as(P))
+    H.h_build_bg_r(np.ascontiguousarray(p).ctypes.data_as(P), n_tau, 0.0, recipe, r.ctypes.data_as(P))
     return r
 
 
-@pytest.mark.parametrize("b", [0, 63])
-def test_background_record(H, b):
+@pytest.mark.parametrize("b,recipe", [(0, 0), (63, 0), (17, 1)])
+def test_background_record(H, b, recipe):
     from paper_2602_15104_gb300 import abcmb as A
     p = W.BATCH64.params()[b]
     n_tau = 2000
-    scal, tab, nodes = A.bg_view(torch.tensor(record(H, p, n_tau)), n_tau)
+    scal, tab, nodes = A.bg_view(torch.tensor(record(H, p, n_tau, recipe)), n_tau)
     assert scal["STATUS"] == 0
     s = O.scalars(p)
     for gk, ok in [("H0", "H0"), ("OMB", "Om_b"), ("OMC", "Om_c"), ("OMG", "Om_g"), ("OML", "Om_L"),
@@ -54,7 +55,7 @@ def test_background_record(H, b):
         assert abs(scal[gk] / s[ok] - 1) < 1e-12, gk
     for gk, ok in [("ZREION", "z_reion"), ("LNA_TC", "lna_tc"), ("LNA_SW", "lna_sw")]:
         assert abs(scal[gk] - s[ok]) < 1e-9 * abs(s[ok]), gk
-    lna, tau, w = O.nodes(p, n_tau)
+    lna, tau, w = O.nodes(p, n_tau, node_recipe=recipe)
     np.testing.assert_allclose(nodes[:, 0], lna, rtol=0, atol=1e-9)
     np.testing.assert_allclose(nodes[:, 1], tau, rtol=1e-10)
     np.testing.assert_allclose(nodes[:, 2], w, rtol=1e-8)
@@ -69,13 +70,13 @@ def test_background_record(H, b):
         np.testing.assert_allclose(tab[sel, c], ob[name], rtol=1e-9, err_msg=name)
 
 
-@pytest.mark.parametrize("k", [2e-4, 0.01, 0.1])
-def test_sources_of_single_modes(H, k):
+@pytest.mark.parametrize("k,recipe", [(2e-4, 0), (0.01, 0), (0.1, 0), (0.01, 1)])
+def test_sources_of_single_modes(H, k, recipe):
     p = W.BATCH64.params()[5]
     n_tau, L = 300, 8
-    r = record(H, p, n_tau)
+    r = record(H, p, n_tau, recipe)
     S = np.zeros((n_tau, 3))
     assert H.h_fwd_m(r.ctypes.data_as(P), k, L, 0, 1e-9, S.ctypes.data_as(P)) == 0
-    ref = O.run(p, np.array([k]), n_tau, 40, O.opts(lmax=L), want=("S",))["S"][0]
+    ref = O.run(p, np.array([k]), n_tau, 40, O.opts(lmax=L, node_recipe=recipe), want=("S",))["S"][0]
     err = np.abs(S - ref).max(axis=0) / np.abs(ref).max(axis=0)
     assert np.all(err < 1e-6), err
