@@ -413,6 +413,8 @@ def main():
                     help="serving benchmark: Poisson arrivals of mixed-size requests through abcmb_server")
     ap.add_argument("--grad", action="store_true",
                     help="gradient benchmark: dC_l/dtheta of a batch through the hand-written adjoint")
+    ap.add_argument("--node-recipe", type=int, default=0, choices=[0, 1],
+                    help="tau-node placement: 0 the default, 1 the refined visibility tail")
     ap.add_argument("--variants", action="store_true",
                     help="time the variant paths (transfer grid, P(k), lensing chain, massive neutrino)")
     ap.add_argument("--requests", type=int, default=4096)
@@ -456,7 +458,8 @@ def main():
     B = args.batch or wl.n_cosmo
     params = rank_params(wl, B, rank)
     k = W.log_k_nodes(args.n_k, wl.k_min, wl.k_max) if args.n_k else wl.k()
-    o = A.options(lmax_hier=wl.l_max_hier, lmax_cl=wl.l_max_cl, n_tau=wl.n_tau, rtol=args.rtol)
+    o = A.options(lmax_hier=wl.l_max_hier, lmax_cl=wl.l_max_cl, n_tau=wl.n_tau, rtol=args.rtol,
+                  node_recipe=args.node_recipe)
     N = 4 + 3 * (wl.l_max_hier + 1)
     mixed = args.precision == "mixed"
     pipe = A.Pipeline(B, k, o, mixed=mixed)
@@ -556,7 +559,7 @@ def main():
         "vs_baseline": None, "dtype": "f64+f32" if mixed else "f64", "data": "synthetic",
         "config": {"workload": wl.name, "batch": B, "n_k": len(k), "k_range": [wl.k_min, wl.k_max],
                    "lmax_cl": wl.l_max_cl, "hierarchy_lmax": wl.l_max_hier, "n_tau": wl.n_tau,
-                   "rtol": args.rtol, "precision": args.precision,
+                   "rtol": args.rtol, "precision": args.precision, "node_recipe": args.node_recipe,
                    "l2": "flushed (512 MiB write) between timed steps",
                    "parallelism": f"replicas x{world}"},
         "clocks": clk,
