@@ -150,3 +150,15 @@ def test_variant_entry_points_reject_on_host(A):
     # the transfer grid itself (host function): out-of-range lmax, and its size
     assert L.abcmb_transfer_k_grid(1, None, 0) == -1
     assert L.abcmb_transfer_k_grid(2500, None, 0) == 1703
+
+
+def test_server_request_bytes(A):
+    # host function: a request's arena footprint grows with lmax_cl and n_k, is
+    # dominated by its FP64 sources (n_k x n_tau x 3 doubles), and invalid
+    # requests need nothing
+    o = A.options(lmax_hier=30, n_tau=6000)
+    b = {(lm, nk): A.server_request_bytes(o, lm, nk) for lm in (500, 2500) for nk in (80, 400)}
+    assert b[(500, 80)] < b[(500, 400)] and b[(500, 80)] < b[(2500, 80)] < b[(2500, 400)]
+    assert b[(2500, 400)] >= 400 * 6000 * 3 * 8
+    assert A.server_request_bytes(o, 1, 80) == 0 and A.server_request_bytes(o, 500, 1) == 0
+    assert A.server_request_bytes(A.options(n_tau=4), 500, 80) == 0
