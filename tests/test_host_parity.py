@@ -80,3 +80,18 @@ def test_sources_of_single_modes(H, k, recipe):
     ref = O.run(p, np.array([k]), n_tau, 40, O.opts(lmax=L, node_recipe=recipe), want=("S",))["S"][0]
     err = np.abs(S - ref).max(axis=0) / np.abs(ref).max(axis=0)
     assert np.all(err < 1e-6), err
+
+
+@pytest.mark.parametrize("recipe", [0, 1])
+@pytest.mark.parametrize("n_tau", [8, 9, 13, 101])
+def test_nodes_of_small_and_ragged_counts(H, n_tau, recipe):
+    # the segment sizes round down; every count from the minimum of 8 gives
+    # strictly increasing nodes before tau_0 that match the oracle's
+    p = W.BATCH64.params()[3]
+    r = record(H, p, n_tau, recipe)
+    assert r[0] == 0  # status
+    nodes = r[64 + 28 * 18433: 64 + 28 * 18433 + 8 * n_tau].reshape(n_tau, 8)
+    lna, tau, w = O.nodes(p, n_tau, node_recipe=recipe)
+    assert np.all(np.diff(nodes[:, 1]) > 0) and nodes[-1, 1] < O.scalars(p)["tau0"]
+    np.testing.assert_allclose(nodes[:, 0], lna, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(nodes[:, 2], w, rtol=1e-8)
