@@ -1,6 +1,10 @@
 /*
  * ORACLE (test infrastructure only; see orc.h).
  * Dense LU factorisation with partial pivoting (textbook Doolittle form).
+ * The elimination skips exact zeros: rows whose multiplier is zero, and the
+ * pivot row's trailing zero columns (subtracting l * 0 leaves an entry as it
+ * is).  The collocation systems of the perturbation ODE are sparse, so this
+ * removes most of the work without changing any nonzero update.
  */
 #include <math.h>
 
@@ -20,11 +24,13 @@ int orc_lu_factor(double *A, int n, int *piv)
                 double t = A[k * n + j]; A[k * n + j] = A[p * n + j]; A[p * n + j] = t;
             }
         double inv = 1.0 / A[k * n + k];
+        int jend = n - 1; /* last nonzero column of the pivot row */
+        while (jend > k && A[k * n + jend] == 0.0) jend--;
         for (int i = k + 1; i < n; i++) {
             double l = A[i * n + k] * inv;
             A[i * n + k] = l;
             if (l != 0.0)
-                for (int j = k + 1; j < n; j++) A[i * n + j] -= l * A[k * n + j];
+                for (int j = k + 1; j <= jend; j++) A[i * n + j] -= l * A[k * n + j];
         }
     }
     return 0;
