@@ -202,8 +202,10 @@ size_t abcmb_perturb_workspace_bytes(int B, int Nk, const abcmb_options *o);
  *     ABCMB_E_SCRATCH_TOO_SMALL and enqueue nothing.  Every GPU that loads the
  *     library reserves the array until the process exits.
  *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture begins.
+ *     (cudaGetSymbolAddress) with that device current, and so does the first
+ *     call after the device's context was replaced (cudaDeviceReset): the
+ *     address is cached per device together with the context's unique id.
+ *     Make that first call before any stream capture begins.
  *   - Every call shares the one array, which keeps the last call's contents;
  *     the kernel overwrites every element it reads, so nothing needs
  *     clearing.  Calls whose kernels overlap on the GPU (different streams,

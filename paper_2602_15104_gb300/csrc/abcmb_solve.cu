@@ -12,6 +12,8 @@
 // on chip.
 // Both order modes k-descending, so that the most expensive modes are
 // scheduled first and a warp's modes share one k across cosmologies.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -260,24 +262,55 @@ extern "C" int abcmb_background_tables(int B, const double *params, const abcmb_
 // live in this file-scope device array instead of a caller-provided
 // workspace.  Every GPU that loads the library holds it until the process
 // exits.  Host code may not pass the symbol itself to a kernel (on the host it
-// names a stand-in, not device memory); the device address is looked up once
-// per device with cudaGetSymbolAddress and cached.
+// names a stand-in, not device memory); the device address is looked up with
+// cudaGetSymbolAddress, with the device current, once per device context.
 static __device__ __align__(256) double g_noalloc_scratch[ABCMB_NOALLOC_SCRATCH_BYTES / sizeof(double)];
 
 static std::mutex g_noalloc_mutex;
-static double *g_noalloc_ptr[256];
+struct NoallocSlot {
+    unsigned long long ctx_id; // the context the address belongs to (0: none yet)
+    double *ptr;
+};
+static NoallocSlot g_noalloc_slot[256];
+
+// Unique id of the calling thread's current context, 0 if it has none.  The
+// symbol's address belongs to the context that loaded the module, so a reset
+// device (a new primary context) needs a fresh lookup.
+static unsigned long long current_ctx_id()
+{
+    static PFN_cuCtxGetCurrent_v4000 get_cur = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    if (!get_cur || !get_id) {
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", (void **)&get_cur, 4000, cudaEnableDefault, &q1) !=
+                cudaSuccess || q1 != cudaDriverEntryPointSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", (void **)&get_id, 12000, cudaEnableDefault, &q2) !=
+                cudaSuccess || q2 != cudaDriverEntryPointSuccess) {
+            get_cur = nullptr;
+            get_id = nullptr;
+            return 0;
+        }
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_cur(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 static int noalloc_scratch(double **out)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return ABCMB_E_CUDA;
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
+    NoallocSlot &slot = g_noalloc_slot[dev];
+    const unsigned long long id = current_ctx_id();
+    if (!slot.ptr || id == 0 || id != slot.ctx_id) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return ABCMB_E_CUDA;
-        g_noalloc_ptr[dev] = (double *)p;
+        slot.ptr = (double *)p;
+        slot.ctx_id = current_ctx_id(); // the lookup makes the device's context current
     }
-    *out = g_noalloc_ptr[dev];
+    *out = slot.ptr;
     return ABCMB_OK;
 }
 
