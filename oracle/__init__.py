@@ -104,6 +104,26 @@ def background(params, lna, hooks=0, m_ncdm=0.0):
     return {f: out[:, i] for i, f in enumerate(BG_FIELDS)}
 
 
+def thermo(params, lna):
+    """Thermal history at ln a: dict of T_m [eV], dlnTm (d ln T_m / d ln a),
+    x_e and the baryon sound speed squared cs2 (App. B.1.2, App. C.3)."""
+    lna = _arr(np.atleast_1d(lna))
+    out = np.zeros((lna.size, 4))
+    L = lib()
+    L.orc_thermo.argtypes = [_D, _D, ctypes.c_int, _D]
+    if L.orc_thermo(_p(_arr(params)), _p(lna), lna.size, _p(out)):
+        raise RuntimeError("oracle background failed")
+    return dict(Tm=out[:, 0], dlnTm=out[:, 1], xe=out[:, 2], cs2=out[:, 3])
+
+
+def alpha_B(T_eV):
+    """The Peebles atom's case-B recombination coefficient [cm^3/s] at T [eV]."""
+    L = lib()
+    L.orc_alpha_B_at.argtypes = [ctypes.c_double]
+    L.orc_alpha_B_at.restype = ctypes.c_double
+    return L.orc_alpha_B_at(float(T_eV))
+
+
 def nodes(params, n_tau, m_ncdm=0.0, node_recipe=0):
     out = np.zeros((3, n_tau))
     if lib().orc_nodes(_p(_arr(params)), n_tau, float(m_ncdm), int(node_recipe), _p(out)):

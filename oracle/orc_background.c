@@ -18,9 +18,10 @@
  *    recombination fit of Pequignot, Petitjean & Boisson (1991),
  *    photo-ionisation by detailed balance at the radiation temperature,
  *    Lambda_2s1s = 8.2245809 /s, Lyman-alpha escape through
- *    K = lambda_alpha^3 / (8 pi H).  PARITY UNPINNED against an external
- *    recombination code (none is available here); pinned only by its Saha
- *    limit and its freeze-out range;
+ *    K = lambda_alpha^3 / (8 pi H).  Not compared with an external
+ *    recombination code (none is available here); pinned by its Saha limit,
+ *    its freeze-out range, the case-B coefficient against a textbook table
+ *    and the visibility peak at the paper's fiducial recombination time;
  *  - matter temperature: T_m = T_CMB (1 - H/Gamma_C) for z > 700, then
  *    dT_m/dln a = (-2 H T_m + Gamma_C (T_CMB - T_m)) / H (App. B.1.2);
  *  - reionization: tanh steps (App. B.2, eqs. h_reion, y_reio, he_reion),
@@ -223,6 +224,9 @@ static double alpha_B(double T_eV) /* cm^3/s, Pequignot et al. (1991) case-B fit
     double t = T_eV / O_KB / 1.0e4;
     return 1.0e-13 * 4.309 * pow(t, -0.6166) / (1.0 + 0.6703 * pow(t, 0.5300));
 }
+
+/* the case-B coefficient, for the oracle's own pins */
+double orc_alpha_B_at(double T_eV) { return alpha_B(T_eV); }
 
 static double H_sec(const orc_cosmo *c, double a) /* H [1/s] */
 {

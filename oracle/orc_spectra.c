@@ -167,6 +167,25 @@ int orc_background(const double *p, int hooks, double m_ncdm, const double *lna,
 }
 
 /* tau nodes: out[3][n_tau] = lna, tau, w */
+/* Thermal history at ln a[n]: out[n][4] = matter temperature T_m [eV],
+   d ln T_m / d ln a, x_e, baryon sound speed c_s^2 (App. B.1.2, App. C.3). */
+int orc_thermo(const double *p, const double *lna, int n, double *out)
+{
+    orc_cosmo c;
+    if (orc_cosmo_init(&c, p, 0, 0, 0.0, 0)) return -1;
+    for (int i = 0; i < n; i++) {
+        orc_bg b;
+        orc_bg_eval(&c, lna[i], &b, 1);
+        double dlnTm;
+        out[4 * i] = orc_Tm_of_lna(&c, lna[i], &dlnTm);
+        out[4 * i + 1] = dlnTm;
+        out[4 * i + 2] = b.xe;
+        out[4 * i + 3] = b.cs2;
+    }
+    orc_cosmo_free(&c);
+    return 0;
+}
+
 int orc_nodes(const double *p, int n_tau, double m_ncdm, int node_recipe, double *out)
 {
     orc_cosmo c;

@@ -211,6 +211,93 @@ def test_ionization_history_limits(small_params):
     assert abs((xe - (1 + f)) - (xH - 1)) < 1e-6
 
 
+# textbook constants for the thermal-history pins (CODATA 2018)
+_SIGMA_T = 6.6524587321e-25  # cm^2
+_C_CMS = 2.99792458e10       # cm/s
+_MPC_CM = 3.0856775814913673e24
+_HBARC = 1.973269804e-5      # eV cm
+_ME = 510998.95              # eV
+_MH = 938783073.6            # eV (hydrogen atom)
+_MHE_MH = 3.971480           # m(4He atom) / m(H atom)
+_KB = 8.617333262e-5         # eV / K
+_Y = 0.245
+_TCMB0 = 2.34865418e-4       # eV (App. A.2)
+
+
+def _H_per_s(s, a):
+    e2 = (s["Om_g"] + s["Om_nu"]) / a**4 + (s["Om_b"] + s["Om_c"]) / a**3 + s["Om_L"]
+    return s["H0"] * np.sqrt(e2) * _C_CMS / _MPC_CM
+
+
+def _gamma_compton(a, xe):
+    """Thomson coupling rate of the matter temperature to the photons [1/s]:
+    (8 sigma_T rho_gamma c / (3 m_e c^2)) x_e / (1 + f_He + x_e), rho_gamma =
+    (pi^2 / 15) T^4 / (hbar c)^3, f_He the helium-to-hydrogen number ratio."""
+    T = _TCMB0 / a
+    rho_g = np.pi**2 / 15.0 * T**4 / _HBARC**3  # eV / cm^3
+    f_he = _Y / (_MHE_MH * (1.0 - _Y))
+    return 8.0 * _SIGMA_T * rho_g * _C_CMS / (3.0 * _ME) * xe / (1.0 + f_he + xe)
+
+
+def test_matter_temperature_follows_its_compton_equation(small_params):
+    """App. B.1.2: dT_m/dt = -2 H T_m + Gamma_C (T_gamma - T_m).  Integrated
+    here independently (scipy Radau, from z = 2500 where T_m sits on the
+    quasi-static attractor T_gamma (1 - H/Gamma_C)) with the oracle's x_e and
+    the textbook Compton rate, it must give the oracle's T_m from the
+    recombination era (where the oracle uses the attractor) through the
+    epoch of adiabatic cooling (T_m falling as a^-2, far below T_gamma)."""
+    from scipy.interpolate import CubicSpline
+    s = O.scalars(small_params)
+    lna_g = np.linspace(-np.log(2501.0), -np.log(21.0), 20001)
+    th = O.thermo(small_params, lna_g)
+    xe = CubicSpline(lna_g, th["xe"])
+
+    def rhs(x, y):
+        a = np.exp(x)
+        return [-2.0 * y[0] + _gamma_compton(a, xe(x)) / _H_per_s(s, a) * (_TCMB0 / a - y[0])]
+
+    a0 = np.exp(lna_g[0])
+    T0 = _TCMB0 / a0 * (1.0 - _H_per_s(s, a0) / _gamma_compton(a0, th["xe"][0]))
+    z_chk = np.array([2000.0, 1500.0, 1100.0, 800.0, 650.0, 400.0, 200.0, 100.0, 50.0, 30.0])
+    x_chk = -np.log1p(z_chk)
+    sol = integrate.solve_ivp(rhs, (lna_g[0], lna_g[-1]), [T0], method="Radau", rtol=1e-11, atol=1e-20,
+                              t_eval=x_chk, dense_output=False)
+    ref = sol.y[0]
+    got = O.thermo(small_params, x_chk)["Tm"]
+    np.testing.assert_allclose(got, ref, rtol=2e-5)
+    Tg = _TCMB0 * (1.0 + z_chk)
+    assert abs(got[2] / Tg[2] - 1) < 1e-3          # still coupled at recombination
+    assert got[-1] / Tg[-1] < 0.5                  # decoupled, cooling as a^-2 by z = 30
+
+
+def test_baryon_sound_speed_definition(small_params):
+    """App. C.3: c_s^2 = (T_b / mu_b)(1 - (1/3) d ln T_b / d ln a), mu_b the mean
+    mass per particle (H and He nuclei plus free electrons).  T_b and x_e
+    from the oracle, the logarithmic derivative by central differences."""
+    z = np.array([3000.0, 1500.0, 1100.0, 900.0, 500.0, 200.0, 60.0])
+    x = -np.log1p(z)
+    d = 1e-4
+    th = O.thermo(small_params, x)
+    tp = O.thermo(small_params, x + d)["Tm"]
+    tm = O.thermo(small_params, x - d)["Tm"]
+    dln = (np.log(tp) - np.log(tm)) / (2 * d)
+    mu = _MH / ((1.0 - _Y) * (1.0 + th["xe"]) + _Y / _MHE_MH)
+    cs2 = th["Tm"] / mu * (1.0 - dln / 3.0)
+    np.testing.assert_allclose(th["cs2"], cs2, rtol=1e-6)
+    np.testing.assert_allclose(th["dlnTm"], dln, rtol=1e-5, atol=1e-7)
+    # and the library-facing background record carries the same value
+    np.testing.assert_allclose(O.background(small_params, x)["cs2"], cs2, rtol=1e-6)
+
+
+def test_case_b_recombination_coefficient_against_the_textbook_table():
+    """The Peebles atom's alpha_B against the tabulated H I case-B
+    coefficient (tests/golden/case_b_recombination.json, Osterbrock &
+    Ferland Table 2.1); the fit the oracle uses reproduces it to < 1 %."""
+    g = json.load(open(os.path.join(GOLDEN, "case_b_recombination.json")))
+    for T, ref in zip(g["T_K"], g["alpha_B"]):
+        assert abs(O.alpha_B(T * _KB) / ref - 1) < 1e-2, T
+
+
 def test_reionization_optical_depth(small_params):
     # kappa accumulated below the reionization step equals the input tau_reion
     # up to the small contribution of leftover recombination electrons
