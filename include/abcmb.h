@@ -14,7 +14,7 @@
  *   abcmb_delta_m_nodes, abcmb_cl_psi, abcmb_lens  lensing potential (Limber)
  *                             and lensed spectra
  *   abcmb_perturb_taped, abcmb_perturb_adjoint, abcmb_project_adjoint,
- *   abcmb_cl_adjoint, abcmb_record_vjp            reverse-mode gradients
+ *   abcmb_cl_adjoint, abcmb_param_stencil, abcmb_record_vjp  reverse-mode gradients
  *   abcmb_server_*            a request server over one device arena
  *
  * Conventions shared by every entry point
@@ -372,6 +372,7 @@ int abcmb_cl_mixed(int B, const double *bg, const float *Delta32, const double *
  *   abcmb_project_adjoint Deltabar -> Sbar, recbar += d/d(node tau, w), d/d tau_0
  *   abcmb_perturb_adjoint Sbar    -> recbar += d/d(ODE table, conformal-time
  *                                    table, node data, R_nu)
+ *   abcmb_param_stencil   theta -> h and the rows theta +- h e_j
  *   abcmb_record_vjp      recbar, records at theta +- h e_j -> grad
  *
  * recbar [B][abcmb_bg_doubles(o)] device, float64, zeroed by the caller
@@ -429,6 +430,21 @@ int abcmb_project_adjoint(int B, const double *bg, const double *S, const double
                           void *stream);
 
 /*
+ * The central-difference stencil of the background record's parameter
+ * Jacobian: for each cosmology b and parameter j,
+ *   h[b][j] = rel_step * max(|params[b][j]|, floor_abs),
+ *   params_plus[b][j]  = params[b] + h[b][j] e_j,
+ *   params_minus[b][j] = params[b] - h[b][j] e_j
+ * (the rows abcmb_background_tables turns into rec_plus / rec_minus below).
+ *   params                     [B][ABCMB_NPARAM]                 device, read
+ *   h                          [B][ABCMB_NPARAM]                 device, written
+ *   params_plus, params_minus  [B][ABCMB_NPARAM][ABCMB_NPARAM]   device, written
+ * rel_step > 0 and floor_abs > 0, else ABCMB_E_INVALID_ARG.
+ */
+int abcmb_param_stencil(int B, const double *params, double rel_step, double floor_abs, double *h,
+                        double *params_plus, double *params_minus, void *stream);
+
+/*
  * grad[b][j] = sum_e recbar[b][e] (rec_plus[b][j][e] - rec_minus[b][j][e]) / (2 h[b][j])
  *   recbar            [B][len]                 device, read
  *   rec_plus/minus    [B][ABCMB_NPARAM][len]   device, read: background
@@ -443,14 +459,17 @@ int abcmb_record_vjp(int B, const abcmb_options *o, const double *recbar, const 
  * Continuous-batching spectrum server.  A host runtime over the calls above
  * (no counterpart in the paper, which evaluates one cosmology per call):
  * requests of different lmax_cl and k-grid size queue on the host and are
- * admitted in arrival order as soon as a stream slot is free and the
- * caller's device arena holds the request's buffers
- * (abcmb_server_request_bytes: background record, k, sources, FP32 transfer
- * functions, C_l).  Each admitted request runs the whole path on its slot's
+ * admitted as soon as a stream slot is free and the caller's device arena
+ * holds their buffers (abcmb_server_request_bytes per request: background
+ * record, k, sources, FP32 transfer functions, C_l).  The request at the head
+ * of the queue is admitted first, together with up to seven later requests of
+ * the same lmax_cl and k grid (as many as the arena then holds): a slot runs
+ * them as one batch of cosmologies, one k per warp across them, on its
  * stream -- background tables, FP64 perturbations, FP32 projection and
  * k-quadrature (abcmb_project_mixed / abcmb_cl_mixed), C_l copied back --
- * so requests in flight overlap on the GPU.  Per-request results are
- * independent of what else is in flight (no shared state between slots).
+ * and slots in flight overlap on the GPU.  A request's result does not
+ * depend on the others beyond the ODE tolerance (the integrator's switch
+ * from implicit to explicit steps is taken per warp).
  *
  * The server object, its streams, events and pinned host staging buffers are
  * created by abcmb_server_create and released by abcmb_server_destroy; all
@@ -466,8 +485,8 @@ int abcmb_record_vjp(int B, const abcmb_options *o, const double *recbar, const 
  *                         k in [k_min, k_max]; ABCMB_E_SCRATCH_TOO_SMALL if it
  *                         could never fit the arena
  *   abcmb_server_progress admit, launch and retire without blocking; returns
- *                         the number of requests in flight, or a negated
- *                         error code
+ *                         the number of requests in flight (all slots'
+ *                         batches), or a negated error code
  *   abcmb_server_queued   requests waiting for admission
  *   abcmb_server_poll     pop one finished request: returns 1 (tag, status --
  *                         ABCMB_OK or the first failing status --, lmax_cl,

@@ -107,6 +107,7 @@ def lib():
         L.abcmb_cl_adjoint.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, O, _P, _P, _P, _P]
         L.abcmb_project_adjoint.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, O, _P, _P, _P, _P]
         L.abcmb_record_vjp.argtypes = [ctypes.c_int, O, _P, _P, _P, _P, _P, _P]
+        L.abcmb_param_stencil.argtypes = [ctypes.c_int, _P, ctypes.c_double, ctypes.c_double, _P, _P, _P, _P]
         L.abcmb_server_request_bytes.argtypes = [O, ctypes.c_int, ctypes.c_int]
         L.abcmb_server_request_bytes.restype = ctypes.c_size_t
         L.abcmb_server_create.argtypes = [_P, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_int, O,
@@ -367,6 +368,18 @@ def abcmb_project_adjoint(bg, S, k, o: Options, Deltabar, recbar, Sbar=None):
     return Sbar
 
 
+def abcmb_param_stencil(params, rel_step: float, floor_abs: float):
+    """-> h [B, 6], params_plus [B * 6, 6], params_minus [B * 6, 6] (abcmb.h)."""
+    _dev(params)
+    B = params.shape[0]
+    h = torch.empty((B, NPARAM), dtype=torch.float64, device=params.device)
+    pp = torch.empty((B * NPARAM, NPARAM), dtype=torch.float64, device=params.device)
+    pm = torch.empty_like(pp)
+    _check(lib().abcmb_param_stencil(B, _ptr(params), float(rel_step), float(floor_abs), _ptr(h), _ptr(pp),
+                                     _ptr(pm), _stream()), "abcmb_param_stencil")
+    return h, pp, pm
+
+
 def abcmb_record_vjp(o: Options, recbar, rec_plus, rec_minus, h, grad=None):
     _dev(recbar), _dev(rec_plus), _dev(rec_minus), _dev(h)
     B = recbar.shape[0]
@@ -382,6 +395,7 @@ def abcmb_record_vjp(o: Options, recbar, rec_plus, rec_minus, h, grad=None):
 # parameter Jacobian (the record is smooth in the parameters: fixed-step
 # thermal history, converged root finds), floor 1e-3 in absolute terms
 FD_REL_STEP = 1e-4
+FD_ABS_FLOOR = 1e-3
 
 
 class ClWithGradient(torch.autograd.Function):
@@ -408,19 +422,15 @@ class ClWithGradient(torch.autograd.Function):
     @staticmethod
     def backward(ctx, Cbar):
         params, k, o, bg, ws, S, D = ctx.state
-        B = params.shape[0]
         recbar = torch.zeros_like(bg)
         Cbar = Cbar.contiguous().to(torch.float64)
         Dbar = abcmb_cl_adjoint(bg, D, k, o, Cbar, recbar)
         Sbar = abcmb_project_adjoint(bg, S, k, o, Dbar, recbar)
         abcmb_perturb_adjoint(bg, k, o, Sbar, ws, recbar)
-        h = FD_REL_STEP * params.abs().clamp_min(1e-3)
-        eye = torch.eye(NPARAM, dtype=torch.float64, device=params.device)
-        pp = (params[:, None, :] + h[:, :, None] * eye).reshape(B * NPARAM, NPARAM).contiguous()
-        pm = (params[:, None, :] - h[:, :, None] * eye).reshape(B * NPARAM, NPARAM).contiguous()
+        h, pp, pm = abcmb_param_stencil(params.contiguous(), FD_REL_STEP, FD_ABS_FLOOR)
         rp = abcmb_background_tables(pp, o)
         rm = abcmb_background_tables(pm, o)
-        grad = abcmb_record_vjp(o, recbar, rp, rm, h.contiguous())
+        grad = abcmb_record_vjp(o, recbar, rp, rm, h)
         return grad, None, None
 
 

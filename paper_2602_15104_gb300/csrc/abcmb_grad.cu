@@ -485,6 +485,41 @@ extern "C" int abcmb_project_adjoint(int B, const double *bg, const double *S, c
     return cudaGetLastError() == cudaSuccess ? ABCMB_OK : ABCMB_E_CUDA;
 }
 
+namespace abcmb {
+namespace adj {
+// one thread per (cosmology, parameter j): h = rel max(|theta_j|, floor) and
+// the two shifted parameter rows theta +- h e_j
+__global__ void param_stencil_kernel(int B, const double *__restrict__ params, double rel, double floor_abs,
+                                     double *h, double *pp, double *pm)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= B * ABCMB_NPARAM) return;
+    const int b = t / ABCMB_NPARAM, j = t % ABCMB_NPARAM;
+    const double *p = params + (long)b * ABCMB_NPARAM;
+    const double hj = rel * fmax(fabs(p[j]), floor_abs);
+    h[t] = hj;
+    double *rp = pp + (long)t * ABCMB_NPARAM, *rm = pm + (long)t * ABCMB_NPARAM;
+    for (int i = 0; i < ABCMB_NPARAM; i++) {
+        rp[i] = p[i];
+        rm[i] = p[i];
+    }
+    rp[j] = p[j] + hj;
+    rm[j] = p[j] - hj;
+}
+} // namespace adj
+} // namespace abcmb
+
+extern "C" int abcmb_param_stencil(int B, const double *params, double rel_step, double floor_abs, double *h,
+                                   double *params_plus, double *params_minus, void *stream)
+{
+    if (B < 1 || !params || !h || !params_plus || !params_minus || !(rel_step > 0.0) || !(floor_abs > 0.0))
+        return ABCMB_E_INVALID_ARG;
+    const int n = B * ABCMB_NPARAM;
+    abcmb::adj::param_stencil_kernel<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(
+        B, params, rel_step, floor_abs, h, params_plus, params_minus);
+    return cudaGetLastError() == cudaSuccess ? ABCMB_OK : ABCMB_E_CUDA;
+}
+
 extern "C" int abcmb_record_vjp(int B, const abcmb_options *o, const double *recbar, const double *rec_plus,
                                 const double *rec_minus, const double *h, double *grad, void *stream)
 {

@@ -1,15 +1,20 @@
 // Continuous-batching spectrum server (host runtime over the C ABI calls).
 //
 // Requests (one cosmology, its lmax_cl and k-grid size) queue on the host;
-// progress() admits them in arrival order while a stream slot is free and
-// the caller's device arena has room for the request's buffers (first fit
-// over a sorted free list), enqueues the whole path on that slot's stream
-// (params and k H2D, background tables, FP64 perturbations, FP32 projection
-// and k-quadrature, C_l D2H into the slot's pinned buffer, completion event),
-// and retires finished slots (event query, never a blocking wait), releasing
-// their arena blocks.  Requests in flight on different streams overlap on the
-// GPU: each one's perturbation grid is small (n_k / 8 one-warp CTAs), so a
-// mix of them is what fills the SMs.
+// progress() admits them while a stream slot is free and the caller's device
+// arena has room for their buffers (first fit over a sorted free list).  The
+// request at the head of the queue is admitted first, together with up to
+// kMaxBatch - 1 later requests of the same shape (lmax_cl and k grid), which
+// share the k grid: the slot then runs them as one batch of cosmologies, so
+// that each warp of the perturbation kernel integrates one k for up to eight
+// cosmologies, whose step sequences are nearly the same (the layout of the
+// batched path), instead of eight different k of one cosmology, whose
+// warp-uniform step loop would run at the pace of the slowest.  Per slot the
+// whole path is enqueued on its stream (params and k H2D, background tables,
+// FP64 perturbations, FP32 projection and k-quadrature, C_l D2H into the
+// slot's pinned buffer, completion event); finished slots are retired by
+// event query, never a blocking wait, releasing their arena blocks.  Batches
+// in flight on different streams overlap on the GPU.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -32,14 +37,16 @@ struct Request {
     double t_submit;
 };
 
+constexpr int kMaxBatch = 8; // cosmologies per launch: one warp's modes share a k
+
 struct Slot {
     bool busy = false;
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
-    Request req;
+    std::vector<Request> reqs; // the batch: same lmax_cl and k grid
     size_t off = 0, bytes = 0;
-    double *host = nullptr;    // pinned: params, k, then C_l on return
-    int *host_status = nullptr; // pinned: mode status words
+    double *host = nullptr;     // pinned: params [B][6], k; then C_l [B][3][lmax-1] and B background statuses
+    int *host_status = nullptr; // pinned: mode status words [B][n_k]
     size_t host_doubles = 0;
     int launch_rc = ABCMB_OK;
 };
@@ -50,24 +57,30 @@ struct Result {
     std::vector<double> cl;
 };
 
-// sizes of one request's device buffers, in bytes, in allocation order
+// sizes of the device buffers of a batch of B requests of one shape, in
+// bytes, in allocation order
 struct Layout {
     size_t bg, k, params, S, status, D, Cl, total;
 };
 
-Layout layout_of(const abcmb_options *o, int n_k)
+Layout layout_of(const abcmb_options *o, int n_k, int B = 1)
 {
     Layout L;
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
-    L.bg = up(abcmb_bg_doubles(o) * sizeof(double));
+    L.bg = up((size_t)B * abcmb_bg_doubles(o) * sizeof(double));
     L.k = up((size_t)n_k * sizeof(double));
-    L.params = up(ABCMB_NPARAM * sizeof(double));
-    L.S = up((size_t)n_k * o->n_tau * 3 * sizeof(double));
-    L.status = up((size_t)n_k * sizeof(int));
-    L.D = up((size_t)n_k * (o->lmax_cl - 1) * 2 * sizeof(float));
-    L.Cl = up((size_t)3 * (o->lmax_cl - 1) * sizeof(double));
+    L.params = up((size_t)B * ABCMB_NPARAM * sizeof(double));
+    L.S = up((size_t)B * n_k * o->n_tau * 3 * sizeof(double));
+    L.status = up((size_t)B * n_k * sizeof(int));
+    L.D = up((size_t)B * n_k * (o->lmax_cl - 1) * 2 * sizeof(float));
+    L.Cl = up((size_t)B * 3 * (o->lmax_cl - 1) * sizeof(double));
     L.total = L.bg + L.k + L.params + L.S + L.status + L.D + L.Cl;
     return L;
+}
+
+bool same_shape(const Request &a, const Request &b)
+{
+    return a.lmax_cl == b.lmax_cl && a.n_k == b.n_k && a.k_min == b.k_min && a.k_max == b.k_max;
 }
 
 } // namespace
@@ -112,14 +125,16 @@ extern "C" int abcmb_server_create(void *arena, size_t arena_bytes, int n_slots,
     s->max_lmax = max_lmax_cl;
     s->max_nk = max_n_k;
     s->slots.resize(n_slots);
-    // params + k on the way in, C_l on the way out, and the background status word last
-    const size_t host_doubles = std::max((size_t)ABCMB_NPARAM + max_n_k, (size_t)3 * (max_lmax_cl - 1)) + 1;
+    // params + k on the way in, C_l on the way out, then the background status words
+    const size_t host_doubles = std::max((size_t)kMaxBatch * ABCMB_NPARAM + max_n_k,
+                                         (size_t)kMaxBatch * 3 * (max_lmax_cl - 1)) + kMaxBatch;
     for (Slot &sl : s->slots) {
         sl.host_doubles = host_doubles;
+        sl.reqs.reserve(kMaxBatch);
         if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
             cudaMallocHost((void **)&sl.host, host_doubles * sizeof(double)) != cudaSuccess ||
-            cudaMallocHost((void **)&sl.host_status, (size_t)max_n_k * sizeof(int)) != cudaSuccess) {
+            cudaMallocHost((void **)&sl.host_status, (size_t)kMaxBatch * max_n_k * sizeof(int)) != cudaSuccess) {
             abcmb_server_destroy(s);
             return ABCMB_E_CUDA;
         }
@@ -165,10 +180,11 @@ extern "C" int abcmb_server_submit(abcmb_server *s, long long tag, const double 
 
 static int launch(abcmb_server *s, Slot &sl)
 {
-    const Request &q = sl.req;
+    const Request &q = sl.reqs[0];
+    const int B = (int)sl.reqs.size();
     abcmb_options o = s->base;
     o.lmax_cl = q.lmax_cl;
-    const Layout L = layout_of(&o, q.n_k);
+    const Layout L = layout_of(&o, q.n_k, B);
     char *p = s->arena_base + sl.off;
     double *bg = (double *)p;
     double *k = (double *)(p + L.bg);
@@ -177,26 +193,29 @@ static int launch(abcmb_server *s, Slot &sl)
     int *st = (int *)(p + L.bg + L.k + L.params + L.S);
     float *D = (float *)(p + L.bg + L.k + L.params + L.S + L.status);
     double *Cl = (double *)(p + L.bg + L.k + L.params + L.S + L.status + L.D);
-    // host staging: params, then log-spaced k (the workload's grid rule)
+    // host staging: params of each cosmology, then log-spaced k (the workload's grid rule)
     double *h = sl.host;
-    memcpy(h, q.params, sizeof(q.params));
+    for (int b = 0; b < B; b++) memcpy(h + b * ABCMB_NPARAM, sl.reqs[b].params, sizeof(q.params));
+    double *hk = h + B * ABCMB_NPARAM;
     const double l0 = std::log(q.k_min), l1 = std::log(q.k_max);
-    for (int i = 0; i < q.n_k; i++) h[ABCMB_NPARAM + i] = std::exp(l0 + (l1 - l0) * i / (q.n_k - 1));
+    for (int i = 0; i < q.n_k; i++) hk[i] = std::exp(l0 + (l1 - l0) * i / (q.n_k - 1));
     cudaStream_t st_ = sl.stream;
-    if (cudaMemcpyAsync(params, h, ABCMB_NPARAM * sizeof(double), cudaMemcpyHostToDevice, st_) != cudaSuccess ||
-        cudaMemcpyAsync(k, h + ABCMB_NPARAM, q.n_k * sizeof(double), cudaMemcpyHostToDevice, st_) != cudaSuccess)
+    if (cudaMemcpyAsync(params, h, (size_t)B * ABCMB_NPARAM * sizeof(double), cudaMemcpyHostToDevice, st_) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(k, hk, q.n_k * sizeof(double), cudaMemcpyHostToDevice, st_) != cudaSuccess)
         return ABCMB_E_CUDA;
-    int rc = abcmb_background_tables(1, params, &o, bg, st_);
-    if (rc == ABCMB_OK) rc = abcmb_perturb(1, bg, k, q.n_k, &o, S, st, nullptr, nullptr, 0, st_);
-    if (rc == ABCMB_OK) rc = abcmb_project_mixed(1, bg, S, k, q.n_k, &o, D, st_);
-    if (rc == ABCMB_OK) rc = abcmb_cl_mixed(1, bg, D, k, q.n_k, &o, Cl, st_);
+    int rc = abcmb_background_tables(B, params, &o, bg, st_);
+    if (rc == ABCMB_OK) rc = abcmb_perturb(B, bg, k, q.n_k, &o, S, st, nullptr, nullptr, 0, st_);
+    if (rc == ABCMB_OK) rc = abcmb_project_mixed(B, bg, S, k, q.n_k, &o, D, st_);
+    if (rc == ABCMB_OK) rc = abcmb_cl_mixed(B, bg, D, k, q.n_k, &o, Cl, st_);
     if (rc != ABCMB_OK) return rc;
     // the host staging buffer is reused for C_l only after the H2D copies ran (stream order)
-    if (cudaMemcpyAsync(h, Cl, 3 * (size_t)(q.lmax_cl - 1) * sizeof(double), cudaMemcpyDeviceToHost, st_) !=
+    const size_t ncl = 3 * (size_t)(q.lmax_cl - 1), len = abcmb_bg_doubles(&o);
+    if (cudaMemcpyAsync(h, Cl, B * ncl * sizeof(double), cudaMemcpyDeviceToHost, st_) != cudaSuccess ||
+        cudaMemcpyAsync(sl.host_status, st, (size_t)B * q.n_k * sizeof(int), cudaMemcpyDeviceToHost, st_) !=
             cudaSuccess ||
-        cudaMemcpyAsync(sl.host_status, st, q.n_k * sizeof(int), cudaMemcpyDeviceToHost, st_) != cudaSuccess ||
-        cudaMemcpyAsync(h + sl.host_doubles - 1, bg + ABCMB_S_STATUS, sizeof(double), cudaMemcpyDeviceToHost,
-                        st_) != cudaSuccess ||
+        cudaMemcpy2DAsync(h + sl.host_doubles - kMaxBatch, sizeof(double), bg + ABCMB_S_STATUS,
+                          len * sizeof(double), sizeof(double), B, cudaMemcpyDeviceToHost, st_) != cudaSuccess ||
         cudaEventRecord(sl.done, st_) != cudaSuccess)
         return ABCMB_E_CUDA;
     return ABCMB_OK;
@@ -212,45 +231,60 @@ extern "C" int abcmb_server_progress(abcmb_server *s)
         if (!sl.busy) continue;
         const cudaError_t e = cudaEventQuery(sl.done);
         if (e == cudaErrorNotReady) continue;
-        Result r;
-        r.tag = sl.req.tag;
-        r.lmax_cl = sl.req.lmax_cl;
-        r.n_k = sl.req.n_k;
-        r.status = ABCMB_OK;
-        if (e != cudaSuccess || sl.launch_rc != ABCMB_OK) {
-            r.status = sl.launch_rc != ABCMB_OK ? sl.launch_rc : ABCMB_E_CUDA;
-        } else {
-            if (sl.host[sl.host_doubles - 1] != 0.0) r.status = ABCMB_E_BACKGROUND;
-            for (int i = 0; i < sl.req.n_k; i++)
-                if (sl.host_status[i] != ABCMB_OK) r.status = sl.host_status[i];
-            r.cl.assign(sl.host, sl.host + 3 * (size_t)(sl.req.lmax_cl - 1));
+        const int B = (int)sl.reqs.size();
+        for (int b = 0; b < B; b++) {
+            const Request &q = sl.reqs[b];
+            Result r;
+            r.tag = q.tag;
+            r.lmax_cl = q.lmax_cl;
+            r.n_k = q.n_k;
+            r.status = ABCMB_OK;
+            if (e != cudaSuccess || sl.launch_rc != ABCMB_OK) {
+                r.status = sl.launch_rc != ABCMB_OK ? sl.launch_rc : ABCMB_E_CUDA;
+            } else {
+                const size_t ncl = 3 * (size_t)(q.lmax_cl - 1);
+                if (sl.host[sl.host_doubles - kMaxBatch + b] != 0.0) r.status = ABCMB_E_BACKGROUND;
+                for (int i = 0; i < q.n_k; i++)
+                    if (sl.host_status[(size_t)b * q.n_k + i] != ABCMB_OK) r.status = sl.host_status[(size_t)b * q.n_k + i];
+                r.cl.assign(sl.host + b * ncl, sl.host + (b + 1) * ncl);
+            }
+            s->results.push_back(std::move(r));
         }
-        s->results.push_back(std::move(r));
         s->arena.release(sl.off, sl.bytes);
+        sl.reqs.clear();
         sl.busy = false;
     }
-    // admit in arrival order
+    // admit: the head of the queue first, with the later requests of its shape
     while (!s->queue.empty()) {
         Slot *free_slot = nullptr;
         for (Slot &sl : s->slots)
             if (!sl.busy) { free_slot = &sl; break; }
         if (!free_slot) break;
-        const Request &q = s->queue.front();
+        const Request head = s->queue.front();
+        size_t pick[kMaxBatch];
+        int n = 0;
+        for (size_t i = 0; i < s->queue.size() && n < kMaxBatch; i++)
+            if (same_shape(s->queue[i], head)) pick[n++] = i;
         abcmb_options o = s->base;
-        o.lmax_cl = q.lmax_cl;
-        const size_t bytes = layout_of(&o, q.n_k).total;
-        size_t off = 0;
-        if (!s->arena.alloc(bytes, &off)) break; // wait for memory: keeps arrival order
-        free_slot->req = q;
+        o.lmax_cl = head.lmax_cl;
+        size_t off = 0, bytes = 0;
+        int B = n;
+        for (; B >= 1; B--) { // the largest batch the arena holds now
+            bytes = layout_of(&o, head.n_k, B).total;
+            if (s->arena.alloc(bytes, &off)) break;
+        }
+        if (B < 1) break; // wait for memory: the head keeps its place
+        free_slot->reqs.clear();
+        for (int j = 0; j < B; j++) free_slot->reqs.push_back(s->queue[pick[j]]);
+        for (int j = B - 1; j >= 0; j--) s->queue.erase(s->queue.begin() + (long)pick[j]);
         free_slot->off = off;
         free_slot->bytes = bytes;
         free_slot->busy = true;
-        s->queue.pop_front();
         free_slot->launch_rc = launch(s, *free_slot);
         if (free_slot->launch_rc != ABCMB_OK) cudaEventRecord(free_slot->done, free_slot->stream);
     }
     int n = 0;
-    for (const Slot &sl : s->slots) n += sl.busy;
+    for (const Slot &sl : s->slots) n += sl.busy ? (int)sl.reqs.size() : 0;
     return n;
 }
 
