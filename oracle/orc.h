@@ -120,8 +120,8 @@ double orc_Tm_of_lna(const orc_cosmo *c, double lna, double *dlnTm);
 double orc_lna_start(const orc_cosmo *c, double k);
 
 /* orc_linalg.c */
-int orc_lu_factor(double *A, int n, int *piv);
-void orc_lu_solve(const double *A, int n, const int *piv, double *b);
+int orc_lu_factor(double *A, int n, int *piv, int *ext /* [2n] */);
+void orc_lu_solve(const double *A, int n, const int *piv, const int *ext, double *b);
 
 /* orc_perturb.c */
 int orc_nstate(const orc_opts *o);

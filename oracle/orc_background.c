@@ -314,13 +314,13 @@ static int tla_radau_step(const orc_cosmo *c, double x, double h, double *y, int
     }
     int m = 3 * n;
     double M[36], Z[6] = {0}, R[6];
-    int piv[6];
+    int piv[6], ext[12];
     for (int si = 0; si < 3; si++)
         for (int sj = 0; sj < 3; sj++)
             for (int i = 0; i < n; i++)
                 for (int j = 0; j < n; j++)
                     M[(si * n + i) * m + sj * n + j] = (si == sj && i == j ? 1.0 : 0.0) - h * A[si][sj] * J[i][j];
-    if (orc_lu_factor(M, m, piv)) return -1;
+    if (orc_lu_factor(M, m, piv, ext)) return -1;
     for (int it = 0; it < 60; it++) {
         double F[3][2];
         for (int s = 0; s < 3; s++) {
@@ -334,7 +334,7 @@ static int tla_radau_step(const orc_cosmo *c, double x, double h, double *y, int
                 for (int t = 0; t < 3; t++) acc += A[s][t] * F[t][i];
                 R[s * n + i] = -(Z[s * n + i] - h * acc);
             }
-        orc_lu_solve(M, m, piv, R);
+        orc_lu_solve(M, m, piv, ext, R);
         double dmax = 0.0;
         for (int i = 0; i < m; i++) {
             Z[i] += R[i];

@@ -38,8 +38,9 @@
  *
  * Integrator: 3-stage Radau IIA collocation (order 5, L-stable).  The system
  * is linear, dy/dx = A(x) y, so each step solves the 3N x 3N collocation
- * system (I - h a_ij A(x_n + c_j h)) Y = (y_n, y_n, y_n) by dense LU; A(x) is
- * built column by column from the right-hand side.  Steps follow a fixed
+ * system (I - h a_ij A(x_n + c_j h)) Y = (y_n, y_n, y_n) by LU with partial
+ * pivoting (unknowns ordered by multipole, exact zeros skipped: see
+ * orc_linalg.c); A(x) is built column by column from the right-hand side.  Steps follow a fixed
  * schedule h <= step_c / (1 + k/H) (the fastest oscillation of the hierarchy
  * has phase rate k/H per unit ln a) and land on every tau node; convergence
  * of this schedule is pinned by a step-halving test.
@@ -249,11 +250,22 @@ static void build_A(const orc_opts *o, const orc_bg *b, double k, int N, double 
 
 typedef struct {
     int N;
-    double *M, *Mc, *A, *rhs, *res, *e, *col;
-    int *piv;
+    double *M, *Mc, *A, *rhs, *rhs0, *res, *e, *col;
+    int *piv, *ext, *pos, *mlo, *mhi;
 } radau_ws;
 
-static void ws_alloc(radau_ws *w, int N)
+/* Multipole index of state element i (the four scalars count as l = 0). */
+static int multipole_of(const orc_opts *o, int i)
+{
+    if (i < I_G0) return 0;
+    const int P = i_pol(o), Nn = i_nu(o), Nc = i_ncdm(o);
+    if (i < P) return i - I_G0;
+    if (i < Nn) return i - P;
+    if (i < Nc) return i - Nn;
+    return (i - Nc) % (o->lmax_ncdm + 1);
+}
+
+static void ws_alloc(radau_ws *w, const orc_opts *o, int N)
 {
     w->N = N;
     w->M = (double *)malloc(sizeof(double) * 9 * N * N);
@@ -261,22 +273,40 @@ static void ws_alloc(radau_ws *w, int N)
     w->res = (double *)malloc(sizeof(double) * 3 * N);
     w->A = (double *)malloc(sizeof(double) * 3 * N * N);
     w->rhs = (double *)malloc(sizeof(double) * 3 * N);
+    w->rhs0 = (double *)malloc(sizeof(double) * 3 * N);
     w->e = (double *)malloc(sizeof(double) * N);
     w->col = (double *)malloc(sizeof(double) * N);
     w->piv = (int *)malloc(sizeof(int) * 3 * N);
+    w->ext = (int *)malloc(sizeof(int) * 6 * N);
+    w->pos = (int *)malloc(sizeof(int) * N);
+    w->mlo = (int *)malloc(sizeof(int) * 3 * N);
+    w->mhi = (int *)malloc(sizeof(int) * 3 * N);
+    /* unknown ordering of the collocation system: by multipole, then element,
+       then stage; the couplings of the hierarchies (l to l +- 1, the scalars
+       to l <= 2) then stay near the diagonal */
+    int p = 0, lmax = 0;
+    for (int i = 0; i < N; i++) lmax = multipole_of(o, i) > lmax ? multipole_of(o, i) : lmax;
+    for (int l = 0; l <= lmax; l++)
+        for (int i = 0; i < N; i++)
+            if (multipole_of(o, i) == l) w->pos[i] = p++;
 }
 static void ws_free(radau_ws *w)
 {
-    free(w->M); free(w->Mc); free(w->res); free(w->A); free(w->rhs); free(w->e); free(w->col);
-    free(w->piv);
+    free(w->M); free(w->Mc); free(w->res); free(w->A); free(w->rhs); free(w->rhs0); free(w->e); free(w->col);
+    free(w->piv); free(w->ext); free(w->pos); free(w->mlo); free(w->mhi);
 }
 
 void orc_radau_tableau(double *out12);
 
+/* One step of the 3-stage Radau IIA collocation method for dy/dx = A(x) y:
+   the stage values Y_s = y + h sum_t a_st A(x + c_t h) Y_t solve one linear
+   system of 3N unknowns (stage s of element i is unknown 3 pos[i] + s); the
+   step's result is the last stage (c_3 = 1). */
 static int radau_linear_step(const orc_cosmo *c, const orc_opts *o, double k,
                              double x, double h, double *y, radau_ws *w)
 {
     int N = w->N, M3 = 3 * N;
+    const int *pos = w->pos;
     double t[12];
     orc_radau_tableau(t);
     for (int s = 0; s < 3; s++) {
@@ -286,31 +316,43 @@ static int radau_linear_step(const orc_cosmo *c, const orc_opts *o, double k,
     }
     for (int si = 0; si < 3; si++)
         for (int i = 0; i < N; i++) {
-            double *row = w->M + (size_t)(si * N + i) * M3;
+            const int r = 3 * pos[i] + si;
+            double *row = w->M + (size_t)r * M3;
+            int lo = M3, hi = -1;
+            memset(row, 0, sizeof(double) * M3);
             for (int sj = 0; sj < 3; sj++) {
                 double coef = h * t[3 * si + sj];
                 const double *Aj = w->A + (size_t)sj * N * N + (size_t)i * N;
-                for (int j = 0; j < N; j++) row[sj * N + j] = -coef * Aj[j];
+                for (int j = 0; j < N; j++) {
+                    if (Aj[j] == 0.0) continue;
+                    const int cidx = 3 * pos[j] + sj;
+                    row[cidx] = -coef * Aj[j];
+                    if (cidx < lo) lo = cidx;
+                    if (cidx > hi) hi = cidx;
+                }
             }
-            row[si * N + i] += 1.0;
+            row[r] += 1.0;
+            w->mlo[r] = lo < r ? lo : r;
+            w->mhi[r] = hi > r ? hi : r;
+            w->rhs0[r] = y[i];
         }
     memcpy(w->Mc, w->M, sizeof(double) * (size_t)M3 * M3);
-    if (orc_lu_factor(w->M, M3, w->piv)) return -1;
-    for (int s = 0; s < 3; s++) memcpy(w->rhs + s * N, y, sizeof(double) * N);
-    orc_lu_solve(w->M, M3, w->piv, w->rhs);
+    if (orc_lu_factor(w->M, M3, w->piv, w->ext)) return -1;
+    memcpy(w->rhs, w->rhs0, sizeof(double) * M3);
+    orc_lu_solve(w->M, M3, w->piv, w->ext, w->rhs);
     /* iterative refinement: the state mixes O(1) and ~1e-15 components, and
        a single partial-pivoting solve is accurate only normwise */
     for (int it = 0; it < 3; it++) {
         for (int i = 0; i < M3; i++) {
-            double r = y[i % N];
+            double r = w->rhs0[i];
             const double *row = w->Mc + (size_t)i * M3;
-            for (int j = 0; j < M3; j++) r -= row[j] * w->rhs[j];
+            for (int j = w->mlo[i]; j <= w->mhi[i]; j++) r -= row[j] * w->rhs[j];
             w->res[i] = r;
         }
-        orc_lu_solve(w->M, M3, w->piv, w->res);
+        orc_lu_solve(w->M, M3, w->piv, w->ext, w->res);
         for (int i = 0; i < M3; i++) w->rhs[i] += w->res[i];
     }
-    memcpy(y, w->rhs + 2 * N, sizeof(double) * N);
+    for (int i = 0; i < N; i++) y[i] = w->rhs[3 * pos[i] + 2];
     return 0;
 }
 
@@ -342,7 +384,7 @@ int orc_solve_mode(const orc_cosmo *c, const orc_opts *o, double k,
     if (y_init) { memcpy(y, y_init, sizeof(double) * N); x = lna_init; }
     else { x = orc_lna_start(c, k); orc_initial(c, o, k, x, y); }
     radau_ws w;
-    ws_alloc(&w, N);
+    ws_alloc(&w, o, N);
     long steps = 0;
     int rc = 0;
     for (int n = 0; n < n_out && rc == 0; n++) {

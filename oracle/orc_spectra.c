@@ -366,10 +366,11 @@ int orc_h_matrix(void *h, const double *oa, double k, double lna, double *A)
 /* LU solve of a dense system (pins the factorisation against a library solve) */
 int orc_dense_solve(double *A, int n, double *b)
 {
-    int *piv = (int *)malloc(sizeof(int) * n);
-    int rc = orc_lu_factor(A, n, piv);
-    if (!rc) orc_lu_solve(A, n, piv, b);
+    int *piv = (int *)malloc(sizeof(int) * n), *ext = (int *)malloc(sizeof(int) * 2 * n);
+    int rc = orc_lu_factor(A, n, piv, ext);
+    if (!rc) orc_lu_solve(A, n, piv, ext, b);
     free(piv);
+    free(ext);
     return rc;
 }
 
