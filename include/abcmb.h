@@ -366,6 +366,7 @@ int abcmb_cl_mixed(int B, const double *bg, const float *Delta32, const double *
  * abcmb_background_tables (relative step 1e-4), contracted on the device.
  * Call order for one vector-Jacobian product:
  *
+ *   [abcmb_grad_count_steps, abcmb_grad_plan   optional: tapes sized per mode]
  *   abcmb_perturb_taped   -> S (as abcmb_perturb) and the tape in workspace
  *   abcmb_project, abcmb_cl  (forward, unchanged)
  *   abcmb_cl_adjoint      Clbar   -> Deltabar, recbar += d/d(A_s, n_s)
@@ -377,36 +378,72 @@ int abcmb_cl_mixed(int B, const double *bg, const float *Delta32, const double *
  *
  * recbar [B][abcmb_bg_doubles(o)] device, float64, zeroed by the caller
  * before the first adjoint call; the adjoint calls add into it (atomically).
- * Each mode may take up to 65536 accepted steps; more sets its status to
- * ABCMB_E_MAX_STEPS.  Errors as abcmb_perturb: ABCMB_E_INVALID_ARG for bad
+ * Without a plan each mode may take up to 65536 accepted steps (more sets
+ * its status to ABCMB_E_MAX_STEPS); with one (abcmb_grad_plan) each mode's
+ * tape is as long as a first pass found it needs.  Errors as abcmb_perturb: ABCMB_E_INVALID_ARG for bad
  * sizes, pointers or options (nothing launched), ABCMB_E_CUDA for a failed
  * launch; per-mode status in mode_status.
  */
 
 /* Bytes of device workspace abcmb_perturb_taped and abcmb_perturb_adjoint
-   need for B cosmologies x Nk modes (tape, checkpoints every 64 accepted
-   steps, replay segment, work vectors); 0 for invalid arguments. */
+   need for B cosmologies x Nk modes without a plan (each mode's tape then
+   holds 65536 accepted steps; checkpoints every 64 accepted steps, replay
+   segment, work vectors); 0 for invalid arguments. */
 size_t abcmb_grad_workspace_bytes(int B, int Nk, const abcmb_options *o);
 
 /*
- * Forward ODE of abcmb_perturb (one thread per mode), recording each mode's
+ * Sizing a gradient run to its modes (a plan).  A mode's tape length is its
+ * number of accepted steps, which grows with k and with a tighter rtol; a
+ * first pass counts them, and the tapes are then laid out back to back:
+ *
+ *   abcmb_grad_count_steps   the forward of abcmb_perturb_taped without the
+ *                            tape: writes S, mode_status and accepted [B][Nk]
+ *                            int32 (device); workspace >=
+ *                            abcmb_grad_count_workspace_bytes(B, Nk, o) bytes,
+ *                            256-byte aligned
+ *   abcmb_grad_plan          host function: from accepted (copied to the host)
+ *                            fills plan_host [2 B Nk + 2] (prefix sums of tape
+ *                            steps and checkpoint states per mode) and returns
+ *                            the workspace bytes the planned calls need (0 for
+ *                            invalid arguments)
+ *   abcmb_perturb_taped / abcmb_perturb_adjoint with plan_host: that plan (the
+ *                            same array for both calls; the calls copy it into
+ *                            the workspace, so it may be freed after each call
+ *                            returns)
+ *
+ * The taped forward repeats the counting pass's arithmetic exactly, so each
+ * mode records as many steps as were counted.
+ */
+size_t abcmb_grad_count_workspace_bytes(int B, int Nk, const abcmb_options *o);
+int abcmb_grad_count_steps(int B, const double *bg, const double *k, int Nk, const abcmb_options *o, double *S,
+                           int *mode_status, int *accepted, void *workspace, size_t workspace_bytes, void *stream);
+size_t abcmb_grad_plan(int B, int Nk, const abcmb_options *o, const int *accepted_host, long long *plan_host);
+
+/*
+ * Forward ODE of abcmb_perturb (one warp per mode), recording each mode's
  * accepted steps.
  *   bg, k, S, mode_status   as abcmb_perturb
- *   workspace  device, >= abcmb_grad_workspace_bytes(B, Nk, o) bytes,
- *              256-byte aligned, owned by the caller; written here, read by
- *              abcmb_perturb_adjoint (keep it unchanged in between)
+ *   workspace  device, 256-byte aligned, owned by the caller: >=
+ *              abcmb_grad_workspace_bytes(B, Nk, o) bytes when plan_host is
+ *              NULL, else >= the bytes abcmb_grad_plan returned for plan_host;
+ *              written here, read by abcmb_perturb_adjoint (keep it unchanged
+ *              in between)
+ *   plan_host  NULL (65536 accepted steps per mode; more sets the mode's status
+ *              to ABCMB_E_MAX_STEPS) or a plan from abcmb_grad_plan (host)
  */
 int abcmb_perturb_taped(int B, const double *bg, const double *k, int Nk, const abcmb_options *o, double *S,
-                        int *mode_status, void *workspace, size_t workspace_bytes, void *stream);
+                        int *mode_status, void *workspace, size_t workspace_bytes, const long long *plan_host,
+                        void *stream);
 
 /*
  * Reverse sweep of the ODE: replays each mode's steps from its checkpoints
  * and pulls Sbar [B][Nk][n_tau][3] (device, read) back to recbar.  Modes
- * whose forward status was not ABCMB_OK contribute nothing.
+ * whose forward status was not ABCMB_OK contribute nothing.  workspace and
+ * plan_host as given to abcmb_perturb_taped.
  */
 int abcmb_perturb_adjoint(int B, const double *bg, const double *k, int Nk, const abcmb_options *o,
-                          const double *Sbar, void *workspace, size_t workspace_bytes, double *recbar,
-                          void *stream);
+                          const double *Sbar, void *workspace, size_t workspace_bytes, const long long *plan_host,
+                          double *recbar, void *stream);
 
 /*
  * Adjoint of abcmb_cl.

@@ -101,9 +101,16 @@ def lib():
         L.abcmb_cl_mixed.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, O, _P, _P]
         L.abcmb_grad_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_int, O]
         L.abcmb_grad_workspace_bytes.restype = ctypes.c_size_t
-        L.abcmb_perturb_taped.argtypes = [ctypes.c_int, _P, _P, ctypes.c_int, O, _P, _P, _P, ctypes.c_size_t, _P]
+        L.abcmb_perturb_taped.argtypes = [ctypes.c_int, _P, _P, ctypes.c_int, O, _P, _P, _P, ctypes.c_size_t, _P,
+                                          _P]
         L.abcmb_perturb_adjoint.argtypes = [ctypes.c_int, _P, _P, ctypes.c_int, O, _P, _P, ctypes.c_size_t, _P,
-                                            _P]
+                                            _P, _P]
+        L.abcmb_grad_count_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_int, O]
+        L.abcmb_grad_count_workspace_bytes.restype = ctypes.c_size_t
+        L.abcmb_grad_count_steps.argtypes = [ctypes.c_int, _P, _P, ctypes.c_int, O, _P, _P, _P, _P, ctypes.c_size_t,
+                                             _P]
+        L.abcmb_grad_plan.argtypes = [ctypes.c_int, ctypes.c_int, O, _P, _P]
+        L.abcmb_grad_plan.restype = ctypes.c_size_t
         L.abcmb_cl_adjoint.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, O, _P, _P, _P, _P]
         L.abcmb_project_adjoint.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, O, _P, _P, _P, _P]
         L.abcmb_record_vjp.argtypes = [ctypes.c_int, O, _P, _P, _P, _P, _P, _P]
@@ -322,10 +329,52 @@ def grad_workspace_bytes(B: int, Nk: int, o: Options) -> int:
     return n
 
 
+def _plan_ptr(plan):
+    if plan is None:
+        return None
+    if not (isinstance(plan, np.ndarray) and plan.dtype == np.int64 and plan.flags.c_contiguous):
+        raise TypeError("plan: a contiguous int64 numpy array from grad_plan")
+    return plan.ctypes.data_as(ctypes.c_void_p)
+
+
+def abcmb_grad_count_steps(bg: torch.Tensor, k: torch.Tensor, o: Options, S=None, status=None):
+    """First pass of a gradient run: the taped forward without the tape.
+    -> S, mode status, accepted steps per mode [B, Nk] (device, int32)."""
+    _dev(bg), _dev(k)
+    B, Nk = bg.shape[0], k.shape[0]
+    dev = bg.device
+    if S is None:
+        S = torch.empty((B, Nk, o.n_tau, 3), dtype=torch.float64, device=dev)
+    if status is None:
+        status = torch.empty((B, Nk), dtype=torch.int32, device=dev)
+    acc = torch.empty((B, Nk), dtype=torch.int32, device=dev)
+    nb = lib().abcmb_grad_count_workspace_bytes(B, Nk, ctypes.byref(o))
+    if nb == 0:
+        raise ValueError("invalid arguments")
+    ws = torch.empty(nb // 8 + 1, dtype=torch.float64, device=dev)
+    _check(lib().abcmb_grad_count_steps(B, _ptr(bg), _ptr(k), Nk, ctypes.byref(o), _ptr(S), _ptr(status), _ptr(acc),
+                                        _ptr(ws), ws.numel() * 8, _stream()), "abcmb_grad_count_steps")
+    return S, status, acc
+
+
+def grad_plan(o: Options, accepted: torch.Tensor):
+    """Host plan of per-mode tapes from the counted accepted steps [B, Nk]
+    -> (plan int64 array, workspace bytes)."""
+    acc = np.ascontiguousarray(accepted.detach().cpu().numpy(), dtype=np.int32)
+    B, Nk = acc.shape
+    plan = np.empty(2 * B * Nk + 2, dtype=np.int64)
+    nb = lib().abcmb_grad_plan(B, Nk, ctypes.byref(o), acc.ctypes.data_as(ctypes.c_void_p),
+                               plan.ctypes.data_as(ctypes.c_void_p))
+    if nb == 0:
+        raise ValueError("invalid arguments")
+    return plan, nb
+
+
 def abcmb_perturb_taped(bg: torch.Tensor, k: torch.Tensor, o: Options, workspace: torch.Tensor, S=None,
-                        status=None):
+                        status=None, plan=None):
     """Forward ODE recording the tape for abcmb_perturb_adjoint in workspace
-    (a CUDA tensor of >= grad_workspace_bytes bytes).  -> S, mode status."""
+    (a CUDA tensor of >= grad_workspace_bytes bytes, or of the bytes
+    grad_plan returned with plan).  -> S, mode status."""
     _dev(bg), _dev(k)
     B, Nk = bg.shape[0], k.shape[0]
     dev = bg.device
@@ -334,16 +383,17 @@ def abcmb_perturb_taped(bg: torch.Tensor, k: torch.Tensor, o: Options, workspace
     if status is None:
         status = torch.empty((B, Nk), dtype=torch.int32, device=dev)
     _check(lib().abcmb_perturb_taped(B, _ptr(bg), _ptr(k), Nk, ctypes.byref(o), _ptr(S), _ptr(status),
-                                     _ptr(workspace), workspace.numel() * workspace.element_size(), _stream()),
+                                     _ptr(workspace), workspace.numel() * workspace.element_size(), _plan_ptr(plan),
+                                     _stream()),
            "abcmb_perturb_taped")
     return S, status
 
 
-def abcmb_perturb_adjoint(bg, k, o: Options, Sbar, workspace, recbar):
+def abcmb_perturb_adjoint(bg, k, o: Options, Sbar, workspace, recbar, plan=None):
     _dev(bg), _dev(k), _dev(Sbar), _dev(recbar)
     _check(lib().abcmb_perturb_adjoint(bg.shape[0], _ptr(bg), _ptr(k), k.shape[0], ctypes.byref(o), _ptr(Sbar),
                                        _ptr(workspace), workspace.numel() * workspace.element_size(),
-                                       _ptr(recbar), _stream()),
+                                       _plan_ptr(plan), _ptr(recbar), _stream()),
            "abcmb_perturb_adjoint")
     return recbar
 
@@ -400,7 +450,9 @@ FD_ABS_FLOOR = 1e-3
 
 class ClWithGradient(torch.autograd.Function):
     """C_l [B, 3, lmax_cl - 1] (FP64 path) of params [B, 6], differentiable
-    in params by the library's adjoint calls: backward runs
+    in params by the library's adjoint calls.  forward counts each mode's
+    accepted steps (abcmb_grad_count_steps), sizes the tapes to them
+    (abcmb_grad_plan) and runs the taped forward; backward runs
     abcmb_cl_adjoint, abcmb_project_adjoint and abcmb_perturb_adjoint (the
     tape of abcmb_perturb_taped), then contracts the adjoint of the
     background record with its parameter Jacobian (abcmb_record_vjp)."""
@@ -408,25 +460,27 @@ class ClWithGradient(torch.autograd.Function):
     @staticmethod
     def forward(ctx, params, k, o):
         _dev(params), _dev(k)
-        B, Nk = params.shape[0], k.shape[0]
         bg = abcmb_background_tables(params, o)
-        ws = torch.empty(grad_workspace_bytes(B, Nk, o) // 8 + 1, dtype=torch.float64, device=params.device)
-        S, status = abcmb_perturb_taped(bg, k, o, ws)
+        # first pass: count each mode's accepted steps, then size its tape
+        S, status, acc = abcmb_grad_count_steps(bg, k, o)
+        plan, nbytes = grad_plan(o, acc)
+        ws = torch.empty(nbytes // 8 + 1, dtype=torch.float64, device=params.device)
+        S, status = abcmb_perturb_taped(bg, k, o, ws, S=S, status=status, plan=plan)
         D = abcmb_project(bg, S, k, o)
         C = abcmb_cl(bg, D, k, o)
         if bool((bg[:, S_INDEX["STATUS"]] != 0).any()) or bool((status != 0).any()):
             raise RuntimeError("forward pass failed (background or mode status set)")
-        ctx.state = (params.detach(), k, o, bg, ws, S, D)
+        ctx.state = (params.detach(), k, o, bg, ws, plan, S, D)
         return C
 
     @staticmethod
     def backward(ctx, Cbar):
-        params, k, o, bg, ws, S, D = ctx.state
+        params, k, o, bg, ws, plan, S, D = ctx.state
         recbar = torch.zeros_like(bg)
         Cbar = Cbar.contiguous().to(torch.float64)
         Dbar = abcmb_cl_adjoint(bg, D, k, o, Cbar, recbar)
         Sbar = abcmb_project_adjoint(bg, S, k, o, Dbar, recbar)
-        abcmb_perturb_adjoint(bg, k, o, Sbar, ws, recbar)
+        abcmb_perturb_adjoint(bg, k, o, Sbar, ws, recbar, plan=plan)
         h, pp, pm = abcmb_param_stencil(params.contiguous(), FD_REL_STEP, FD_ABS_FLOOR)
         rp = abcmb_background_tables(pp, o)
         rm = abcmb_background_tables(pm, o)

@@ -32,7 +32,7 @@ namespace adj {
 
 constexpr int kSeg = 64;        // accepted steps per checkpoint
 constexpr int kAK = kKmax;      // extrapolation columns
-constexpr int kTapeCap = 65536; // accepted steps a mode may take in a gradient run
+constexpr int kTapeCap = 65536; // accepted steps a mode may take in a gradient run without a plan
 
 // work vectors of a mode (each N long, strided)
 enum {
@@ -52,9 +52,10 @@ enum {
 struct ModeBufs {
     double *work; // [V_COUNT][N]
     double *seg;  // [kSeg + 1][N]
-    double *ckpt; // [kTapeCap / kSeg + 1][N]
-    double *tape; // [kTapeCap][3]: x, H, J | gbs << 8 | land << 9
+    double *ckpt; // [cap / kSeg + 1][N]
+    double *tape; // [cap][3]: x, H, J | gbs << 8 | land << 9
     long stride;  // element stride of the vectors (1: each mode's vectors contiguous)
+    long cap = kTapeCap; // accepted steps the tape holds
 };
 
 ABCMB_HD Vec wv(const ModeBufs &m, const OdeDims &d, int v) { return Vec{m.work + (long)v * d.N * m.stride, m.stride}; }
@@ -297,7 +298,7 @@ ABCMB_HD FwdResult fwd_taped(const ModeCtx &c, const ModeBufs &mb, double rtol, 
         }
         if (!(err == err) || (jacc == 0 && err > 1e300)) { r.status = ABCMB_E_NONFINITE; break; }
         if (jacc) {
-            if (record && r.accepted >= kTapeCap) { r.status = ABCMB_E_MAX_STEPS; break; }
+            if (record && r.accepted >= mb.cap) { r.status = ABCMB_E_MAX_STEPS; break; }
             if (record && r.accepted % kSeg == 0) vcopy(d, Y, ckv(mb, d, r.accepted / kSeg));
             if (record && ln_id() == 0) {
                 double *tp = mb.tape + 3 * (long)r.accepted;

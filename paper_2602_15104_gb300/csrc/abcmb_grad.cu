@@ -28,16 +28,27 @@ namespace adj {
 constexpr long kCkpts = kTapeCap / kSeg + 1;
 constexpr int kGradThreads = 64; // two modes (warps) per block
 
+// Workspace of a gradient run.  Without a plan every mode's tape holds
+// kTapeCap accepted steps.  With a plan (abcmb_grad_plan: from a first pass
+// that counted each mode's accepted steps) mode m's tape holds cap_m steps
+// and its checkpoints cap_m / kSeg + 1 states: plan[m] and plan[M + 1 + m]
+// are the prefix sums of the tape steps and of the checkpoint states over
+// the modes before m (plan[M], plan[2M + 1] the totals); the plan is kept in
+// the workspace's last region.
 struct GradLayout {
     long M, N;
-    size_t work, seg, ckpt, tape, res, total; // byte offsets, total bytes
+    size_t work, seg, ckpt, tape, res, plan, total; // byte offsets, total bytes
+    long tape_steps, ckpt_states;                    // totals
 };
 
-__host__ __device__ inline GradLayout grad_layout(int B, int Nk, const OdeDims &d)
+__host__ __device__ inline GradLayout grad_layout(int B, int Nk, const OdeDims &d, long tape_steps = -1,
+                                                  long ckpt_states = -1)
 {
     GradLayout g;
     g.M = (long)B * Nk;
     g.N = d.N;
+    g.tape_steps = tape_steps >= 0 ? tape_steps : (long)kTapeCap * g.M;
+    g.ckpt_states = ckpt_states >= 0 ? ckpt_states : kCkpts * g.M;
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t o = off;
@@ -46,22 +57,30 @@ __host__ __device__ inline GradLayout grad_layout(int B, int Nk, const OdeDims &
     };
     g.work = take((size_t)V_COUNT * d.N * g.M * sizeof(double));
     g.seg = take((size_t)(kSeg + 1) * d.N * g.M * sizeof(double));
-    g.ckpt = take((size_t)kCkpts * d.N * g.M * sizeof(double));
-    g.tape = take((size_t)kTapeCap * 3 * g.M * sizeof(double));
+    g.ckpt = take((size_t)g.ckpt_states * d.N * sizeof(double));
+    g.tape = take((size_t)g.tape_steps * 3 * sizeof(double));
     g.res = take((size_t)4 * g.M * sizeof(int));
+    g.plan = take(tape_steps >= 0 ? (size_t)(2 * g.M + 2) * sizeof(long long) : 0);
     g.total = off;
     return g;
 }
 
 // each mode's vectors contiguous, so that the lanes of its warp read and
 // write consecutive elements
-__device__ inline ModeBufs mode_bufs(char *ws, const GradLayout &g, long mi)
+__device__ inline ModeBufs mode_bufs(char *ws, const GradLayout &g, long mi, const long long *plan)
 {
     ModeBufs m;
     m.work = (double *)(ws + g.work) + mi * V_COUNT * g.N;
     m.seg = (double *)(ws + g.seg) + mi * (kSeg + 1) * g.N;
-    m.ckpt = (double *)(ws + g.ckpt) + mi * kCkpts * g.N;
-    m.tape = (double *)(ws + g.tape) + (long)kTapeCap * 3 * mi;
+    if (plan) {
+        m.ckpt = (double *)(ws + g.ckpt) + plan[g.M + 1 + mi] * g.N;
+        m.tape = (double *)(ws + g.tape) + 3 * plan[mi];
+        m.cap = (long)(plan[mi + 1] - plan[mi]);
+    } else {
+        m.ckpt = (double *)(ws + g.ckpt) + mi * kCkpts * g.N;
+        m.tape = (double *)(ws + g.tape) + (long)kTapeCap * 3 * mi;
+        m.cap = kTapeCap;
+    }
     m.stride = 1;
     return m;
 }
@@ -89,7 +108,7 @@ __device__ inline ModeCtx mode_ctx(const OdeDims &d, const StreamCoef &sc, const
 __global__ void __launch_bounds__(kGradThreads)
 taped_kernel(int B, int Nk, const double *__restrict__ bg, long len, const double *__restrict__ kv, int Lg, int Lp,
              int Ln, double rtol, double atol, int max_steps, double s_sw, double s_isw, double s_dop, double *S,
-             int *status, char *ws)
+             int *status, char *ws, long tape_steps, long ckpt_states, int record, int *accepted)
 {
     __shared__ double sa[129], sb[129];
     for (int l = threadIdx.x; l < 129; l += blockDim.x) {
@@ -98,13 +117,22 @@ taped_kernel(int B, int Nk, const double *__restrict__ bg, long len, const doubl
     }
     __syncthreads();
     const OdeDims d = ode_dims(Lg, Lp, Ln);
-    const GradLayout g = grad_layout(B, Nk, d);
+    const GradLayout g = grad_layout(B, Nk, d, tape_steps, ckpt_states);
     const long mi = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; // one warp per mode
     if (mi >= g.M) return;
     const int kidx = Nk - 1 - (int)(mi / B), b = (int)(mi % B);
     const double sw[3] = {s_sw, s_isw, s_dop};
     const ModeCtx c = mode_ctx(d, StreamCoef{sa, sb}, bg, len, b, kv[kidx], sw);
-    const ModeBufs mb = mode_bufs(ws, g, mi);
+    const long long *plan = tape_steps >= 0 ? (const long long *)(ws + g.plan) : nullptr;
+    ModeBufs mb;
+    if (record) {
+        mb = mode_bufs(ws, g, mi, plan);
+    } else { // counting pass: work vectors only
+        mb.work = (double *)(ws + g.work) + mi * V_COUNT * g.N;
+        mb.seg = mb.ckpt = mb.tape = nullptr;
+        mb.stride = 1;
+        mb.cap = 0;
+    }
     double *Sm = S + ((long)b * Nk + kidx) * (long)c.n_tau * 3;
     int *res = (int *)(ws + g.res) + 4 * mi;
     FwdResult r = {ABCMB_OK, 0, 0, 0};
@@ -112,7 +140,7 @@ taped_kernel(int B, int Nk, const double *__restrict__ bg, long len, const doubl
         r.status = ABCMB_E_NONFINITE;
         for (int n = ln_id(); n < 3 * c.n_tau; n += ln_n()) Sm[n] = 0.0;
     } else {
-        r = fwd_taped(c, mb, rtol, atol, max_steps, Sm);
+        r = fwd_taped(c, mb, rtol, atol, max_steps, Sm, record != 0);
     }
     if (ln_id() == 0) {
         res[0] = r.status;
@@ -120,6 +148,7 @@ taped_kernel(int B, int Nk, const double *__restrict__ bg, long len, const doubl
         res[2] = r.accepted;
         res[3] = r.emit0;
         status[(long)b * Nk + kidx] = r.status;
+        if (accepted) accepted[(long)b * Nk + kidx] = r.accepted;
     }
 }
 
@@ -168,7 +197,7 @@ plain_kernel(int B, int Nk, const double *__restrict__ bg, long len, const doubl
 __global__ void __launch_bounds__(kGradThreads)
 adjoint_kernel(int B, int Nk, const double *__restrict__ bg, long len, const double *__restrict__ kv, int Lg,
                int Lp, int Ln, double s_sw, double s_isw, double s_dop, const double *__restrict__ Sbar, char *ws,
-               double *recbar)
+               double *recbar, long tape_steps, long ckpt_states)
 {
     __shared__ double sa[129], sb[129];
     for (int l = threadIdx.x; l < 129; l += blockDim.x) {
@@ -177,13 +206,14 @@ adjoint_kernel(int B, int Nk, const double *__restrict__ bg, long len, const dou
     }
     __syncthreads();
     const OdeDims d = ode_dims(Lg, Lp, Ln);
-    const GradLayout g = grad_layout(B, Nk, d);
+    const GradLayout g = grad_layout(B, Nk, d, tape_steps, ckpt_states);
     const long mi = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; // one warp per mode
     if (mi >= g.M) return;
     const int kidx = Nk - 1 - (int)(mi / B), b = (int)(mi % B);
     const double sw[3] = {s_sw, s_isw, s_dop};
     const ModeCtx c = mode_ctx(d, StreamCoef{sa, sb}, bg, len, b, kv[kidx], sw);
-    const ModeBufs mb = mode_bufs(ws, g, mi);
+    const long long *plan = tape_steps >= 0 ? (const long long *)(ws + g.plan) : nullptr;
+    const ModeBufs mb = mode_bufs(ws, g, mi, plan);
     const int *res = (const int *)(ws + g.res) + 4 * mi;
     const FwdResult r = {res[0], res[1], res[2], res[3]};
     const double *Sb = Sbar + ((long)b * Nk + kidx) * (long)c.n_tau * 3;
@@ -413,39 +443,114 @@ extern "C" size_t abcmb_grad_workspace_bytes(int B, int Nk, const abcmb_options 
     return abcmb::adj::grad_layout(B, Nk, d).total;
 }
 
-extern "C" int abcmb_perturb_taped(int B, const double *bg, const double *k, int Nk, const abcmb_options *o,
-                                   double *S, int *mode_status, void *workspace, size_t workspace_bytes,
-                                   void *stream)
+extern "C" size_t abcmb_grad_count_workspace_bytes(int B, int Nk, const abcmb_options *o)
 {
-    if (B < 1 || Nk < 1 || !bg || !k || !S || !mode_status || !workspace || abcmb_validate_options(o) != ABCMB_OK)
+    if (B < 1 || Nk < 1 || abcmb_validate_options(o) != ABCMB_OK) return 0;
+    const abcmb::OdeDims d = abcmb::ode_dims(o->lmax_g, o->lmax_pol, o->lmax_nu);
+    return abcmb::adj::grad_layout(B, Nk, d, 0, 0).total;
+}
+
+extern "C" size_t abcmb_grad_plan(int B, int Nk, const abcmb_options *o, const int *accepted_host,
+                                  long long *plan_host)
+{
+    if (B < 1 || Nk < 1 || !accepted_host || !plan_host || abcmb_validate_options(o) != ABCMB_OK) return 0;
+    const long M = (long)B * Nk;
+    long long tape = 0, ck = 0;
+    for (long m = 0; m < M; m++) {
+        // mode m = b * Nk + kidx in accepted_host; the kernels number modes k-descending
+        const long kidx = Nk - 1 - m / B, b = m % B;
+        const int a = accepted_host[b * Nk + kidx];
+        if (a < 0) return 0;
+        plan_host[m] = tape;
+        plan_host[M + 1 + m] = ck;
+        tape += a;
+        ck += a / abcmb::adj::kSeg + 1;
+    }
+    plan_host[M] = tape;
+    plan_host[2 * M + 1] = ck;
+    const abcmb::OdeDims d = abcmb::ode_dims(o->lmax_g, o->lmax_pol, o->lmax_nu);
+    return abcmb::adj::grad_layout(B, Nk, d, tape, ck).total;
+}
+
+namespace {
+// checks shared by the gradient ODE calls; on success fills the layout's
+// tape and checkpoint totals (-1, -1 without a plan) and, with a plan,
+// copies it into the workspace
+int grad_ws_check(int B, int Nk, const abcmb_options *o, void *workspace, size_t workspace_bytes,
+                  const long long *plan_host, long *tape, long *ck, cudaStream_t s)
+{
+    const abcmb::OdeDims d = abcmb::ode_dims(o->lmax_g, o->lmax_pol, o->lmax_nu);
+    const long M = (long)B * Nk;
+    *tape = -1;
+    *ck = -1;
+    if (plan_host) {
+        *tape = (long)plan_host[M];
+        *ck = (long)plan_host[2 * M + 1];
+        if (*tape < 0 || *ck < M) return ABCMB_E_INVALID_ARG;
+    }
+    const abcmb::adj::GradLayout g = abcmb::adj::grad_layout(B, Nk, d, *tape, *ck);
+    if (workspace_bytes < g.total || ((size_t)workspace & 255) != 0) return ABCMB_E_INVALID_ARG;
+    if (plan_host && cudaMemcpyAsync((char *)workspace + g.plan, plan_host, (size_t)(2 * M + 2) * sizeof(long long),
+                                     cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return ABCMB_E_CUDA;
+    return ABCMB_OK;
+}
+} // namespace
+
+extern "C" int abcmb_grad_count_steps(int B, const double *bg, const double *k, int Nk, const abcmb_options *o,
+                                      double *S, int *mode_status, int *accepted, void *workspace,
+                                      size_t workspace_bytes, void *stream)
+{
+    if (B < 1 || Nk < 1 || !bg || !k || !S || !mode_status || !accepted || !workspace ||
+        abcmb_validate_options(o) != ABCMB_OK)
         return ABCMB_E_INVALID_ARG;
-    if (o->m_ncdm > 0.0) return ABCMB_E_INVALID_ARG; // the adjoint covers massless neutrinos
-    if (workspace_bytes < abcmb_grad_workspace_bytes(B, Nk, o) || ((size_t)workspace & 255) != 0)
+    if (o->m_ncdm > 0.0) return ABCMB_E_INVALID_ARG;
+    if (workspace_bytes < abcmb_grad_count_workspace_bytes(B, Nk, o) || ((size_t)workspace & 255) != 0)
         return ABCMB_E_INVALID_ARG;
     const long len = (long)abcmb_bg_doubles(o), M = (long)B * Nk;
     const long blocks = (M * 32 + abcmb::adj::kGradThreads - 1) / abcmb::adj::kGradThreads;
     if (blocks > 2147483647L) return ABCMB_E_INVALID_ARG;
     abcmb::adj::taped_kernel<<<(unsigned)blocks, abcmb::adj::kGradThreads, 0, (cudaStream_t)stream>>>(
         B, Nk, bg, len, k, o->lmax_g, o->lmax_pol, o->lmax_nu, o->rtol, o->atol, o->max_steps, o->scale_sw,
-        o->scale_isw, o->scale_dop, S, mode_status, (char *)workspace);
+        o->scale_isw, o->scale_dop, S, mode_status, (char *)workspace, 0, 0, 0, accepted);
+    return cudaGetLastError() == cudaSuccess ? ABCMB_OK : ABCMB_E_CUDA;
+}
+
+extern "C" int abcmb_perturb_taped(int B, const double *bg, const double *k, int Nk, const abcmb_options *o,
+                                   double *S, int *mode_status, void *workspace, size_t workspace_bytes,
+                                   const long long *plan_host, void *stream)
+{
+    if (B < 1 || Nk < 1 || !bg || !k || !S || !mode_status || !workspace || abcmb_validate_options(o) != ABCMB_OK)
+        return ABCMB_E_INVALID_ARG;
+    if (o->m_ncdm > 0.0) return ABCMB_E_INVALID_ARG; // the adjoint covers massless neutrinos
+    long tape, ck;
+    const int rc = grad_ws_check(B, Nk, o, workspace, workspace_bytes, plan_host, &tape, &ck, (cudaStream_t)stream);
+    if (rc != ABCMB_OK) return rc;
+    const long len = (long)abcmb_bg_doubles(o), M = (long)B * Nk;
+    const long blocks = (M * 32 + abcmb::adj::kGradThreads - 1) / abcmb::adj::kGradThreads;
+    if (blocks > 2147483647L) return ABCMB_E_INVALID_ARG;
+    abcmb::adj::taped_kernel<<<(unsigned)blocks, abcmb::adj::kGradThreads, 0, (cudaStream_t)stream>>>(
+        B, Nk, bg, len, k, o->lmax_g, o->lmax_pol, o->lmax_nu, o->rtol, o->atol, o->max_steps, o->scale_sw,
+        o->scale_isw, o->scale_dop, S, mode_status, (char *)workspace, tape, ck, 1, nullptr);
     return cudaGetLastError() == cudaSuccess ? ABCMB_OK : ABCMB_E_CUDA;
 }
 
 extern "C" int abcmb_perturb_adjoint(int B, const double *bg, const double *k, int Nk, const abcmb_options *o,
-                                     const double *Sbar, void *workspace, size_t workspace_bytes, double *recbar,
-                                     void *stream)
+                                     const double *Sbar, void *workspace, size_t workspace_bytes,
+                                     const long long *plan_host, double *recbar, void *stream)
 {
     if (B < 1 || Nk < 1 || !bg || !k || !Sbar || !workspace || !recbar || abcmb_validate_options(o) != ABCMB_OK)
         return ABCMB_E_INVALID_ARG;
     if (o->m_ncdm > 0.0) return ABCMB_E_INVALID_ARG;
-    if (workspace_bytes < abcmb_grad_workspace_bytes(B, Nk, o) || ((size_t)workspace & 255) != 0)
-        return ABCMB_E_INVALID_ARG;
+    long tape, ck;
+    const int rc = grad_ws_check(B, Nk, o, workspace, workspace_bytes, plan_host, &tape, &ck, (cudaStream_t)stream);
+    if (rc != ABCMB_OK) return rc;
     const long len = (long)abcmb_bg_doubles(o), M = (long)B * Nk;
     const long blocks = (M * 32 + abcmb::adj::kGradThreads - 1) / abcmb::adj::kGradThreads;
     if (blocks > 2147483647L) return ABCMB_E_INVALID_ARG;
     abcmb::adj::adjoint_kernel<<<(unsigned)blocks, abcmb::adj::kGradThreads, 0, (cudaStream_t)stream>>>(
         B, Nk, bg, len, k, o->lmax_g, o->lmax_pol, o->lmax_nu, o->scale_sw, o->scale_isw, o->scale_dop, Sbar,
-        (char *)workspace, recbar);
+        (char *)workspace, recbar, tape, ck);
     return cudaGetLastError() == cudaSuccess ? ABCMB_OK : ABCMB_E_CUDA;
 }
 

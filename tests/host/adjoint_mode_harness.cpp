@@ -37,7 +37,7 @@ void setup(Run &R, const double *rec, double k, int L)
     R.c.k = k;
     R.c.sw[0] = R.c.sw[1] = R.c.sw[2] = 1.0;
     R.c.n_tau = (int)rec[ABCMB_S_NTAU];
-    R.mb = ModeBufs{R.work.data(), R.seg.data(), R.ckpt.data(), R.tape.data(), 1};
+    R.mb = ModeBufs{R.work.data(), R.seg.data(), R.ckpt.data(), R.tape.data(), 1, kTapeCap};
 }
 } // namespace
 

@@ -43,6 +43,6 @@ extern "C" int h_fwd_m(const double *rec, double k, int L, int Lm, double rtol, 
     c.n_tau = (int)rec[ABCMB_S_NTAU];
     c.ncdm_x1 = rec[ABCMB_S_NCDM_X1];
     c.ncdm_pH = rec[ABCMB_S_NCDM_PREF] * rec[ABCMB_S_H0] * rec[ABCMB_S_H0];
-    ModeBufs mb{work.data(), nullptr, nullptr, nullptr, 1};
+    ModeBufs mb{work.data(), nullptr, nullptr, nullptr, 1, 0};
     return fwd_taped(c, mb, rtol, 1e-15, 20000000, S, false).status;
 }

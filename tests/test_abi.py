@@ -162,3 +162,27 @@ def test_server_request_bytes(A):
     assert b[(2500, 400)] >= 400 * 6000 * 3 * 8
     assert A.server_request_bytes(o, 1, 80) == 0 and A.server_request_bytes(o, 500, 1) == 0
     assert A.server_request_bytes(A.options(n_tau=4), 500, 80) == 0
+
+
+def test_gradient_plan_host_function(A):
+    """abcmb_grad_plan (host): per-mode tape and checkpoint prefix sums in the
+    kernels' k-descending mode order, and the workspace they need, which grows
+    with the counted steps and stays below the fixed-capacity workspace for
+    modes shorter than 65536 steps."""
+    o = A.options(lmax_hier=12, n_tau=600, lmax_cl=400)
+    B, Nk = 2, 3
+    acc = np.array([[10, 200, 70000], [0, 64, 129]], dtype=np.int32)
+    acc_t = A.torch.tensor(acc)
+    plan, nb = A.grad_plan(o, acc_t)
+    M = B * Nk
+    # mode m -> (b = m % B, kidx = Nk - 1 - m // B)
+    order = [acc[m % B, Nk - 1 - m // B] for m in range(M)]
+    assert plan[M] == sum(order)
+    np.testing.assert_array_equal(plan[:M], np.concatenate([[0], np.cumsum(order)[:-1]]))
+    ck = [a // 64 + 1 for a in order]
+    assert plan[2 * M + 1] == sum(ck)
+    np.testing.assert_array_equal(plan[M + 1:2 * M + 1], np.concatenate([[0], np.cumsum(ck)[:-1]]))
+    plan2, nb2 = A.grad_plan(o, A.torch.tensor(acc * 2))
+    assert nb2 > nb
+    small, nbs = A.grad_plan(o, A.torch.tensor(np.full((B, Nk), 100, dtype=np.int32)))
+    assert nbs < A.grad_workspace_bytes(B, Nk, o)

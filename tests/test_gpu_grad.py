@@ -1,25 +1,32 @@
 """The hand-written adjoint (ClWithGradient): Cbar . dC_l/dtheta for the six
 parameters, against central differences of the same forward (relative step
-1e-4) and of the oracle, and the taped forward against the plain pipeline.
+1e-4), against the oracle's derivatives (tests/golden/grad_oracle_*.npz,
+written by tests/golden/make_grad_reference.py from the oracle alone:
+Richardson-extrapolated central differences), and the taped forward against
+the plain pipeline.
 
 The contraction weights are Cbar_l = z_l / |C_l| with z_l ~ N(0, 1), so every
 l counts alike.  The ODE runs at rtol 1e-9: adaptive step decisions that flip
 between theta +- h move C_l by ~rtol, which the differences divide by 2h ~
-1e-4 theta; at 1e-9 that stays below 1e-5 of the gradient.
+1e-4 theta; at 1e-9 that stays below 1e-5 of the gradient.  Each mode's tape
+is sized by a first pass (abcmb_grad_count_steps / abcmb_grad_plan), so the
+k range reaches 0.3 here and 0.5 at hierarchy 30 below.
 """
+import os
+
 import numpy as np
 import pytest
 
-import oracle as O
 from paper_2602_15104_gb300 import workload as W
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-# k up to 0.05 covers l <= 400 (k tau_0 ~ 700); at rtol 1e-9 the modes above
-# k ~ 0.06 would exceed the 65536 accepted steps a gradient run records
-N_K, K_MIN, K_MAX, L_HIER, N_TAU, LMAX_CL = 40, 1e-4, 0.05, 12, 600, 400
+# the oracle reference's "small" case
+N_K, K_MIN, K_MAX, L_HIER, N_TAU, LMAX_CL = 40, 1e-4, 0.3, 12, 600, 400
 REL_STEP = 1e-4
 
 
@@ -66,24 +73,41 @@ def test_adjoint_against_differences_of_the_same_forward(A, case):
         assert np.all(err <= 1e-4 * np.abs(fd).max()), (b, g[b], fd, err)
 
 
-def test_adjoint_against_differences_of_the_oracle(A, case):
-    params, Cbar, g = case["params"], case["Cbar"], case["grad"]
-    k = W.log_k_nodes(N_K, K_MIN, K_MAX)
-    oo = O.opts(lmax=L_HIER)
-    b = 0
-    fd = np.zeros(6)
-    for j in range(6):
-        h = REL_STEP * max(abs(params[b, j]), 1e-3)
-        pp, pm = params[b].copy(), params[b].copy()
-        pp[j] += h
-        pm[j] -= h
-        Cp = O.run(pp, k, N_TAU, LMAX_CL, oo, want=("Cl",))["Cl"]
-        Cm = O.run(pm, k, N_TAU, LMAX_CL, oo, want=("Cl",))["Cl"]
-        fd[j] = np.sum(Cbar[b] * (Cp - Cm)) / (2 * h)
-    err = np.abs(g[b] - fd)
-    # the two paths agree on C_l to ~1e-6 relative; their derivatives to
-    # ~1e-3 of the largest component
-    assert np.all(err <= 1e-3 * np.abs(fd).max()), (g[b], fd, err)
+def oracle_reference(case_name):
+    g = np.load(os.path.join(GOLDEN, f"grad_oracle_{case_name}.npz"))
+    np.testing.assert_array_equal(g["params"], W.BATCH16_GRAD.params()[0])
+    return g
+
+
+def test_adjoint_against_the_oracle_derivatives(A, case):
+    g = oracle_reference("small")
+    assert int(g["l_hier"]) == L_HIER and int(g["n_tau"]) == N_TAU and int(g["lmax_cl"]) == LMAX_CL
+    np.testing.assert_allclose(g["k"], case["k"].cpu().numpy(), rtol=1e-15)
+    Cbar, grad = case["Cbar"][0], case["grad"][0]
+    ref = np.array([np.sum(Cbar * g["dCl"][j]) for j in range(6)])
+    err = np.abs(grad - ref)
+    assert np.all(err <= 1e-4 * np.abs(ref).max()), (grad, ref, err)
+
+
+def test_adjoint_at_hierarchy_30_to_l_2500_and_k_0p5_against_the_oracle(A):
+    """The differentiation workload's grids (hierarchies 30, 6000 tau nodes,
+    l <= 2500) on 12 k reaching 0.5 /Mpc, one cosmology."""
+    g = oracle_reference("full")
+    o = A.options(lmax_hier=int(g["l_hier"]), n_tau=int(g["n_tau"]), lmax_cl=int(g["lmax_cl"]), rtol=1e-9,
+                  atol=1e-15)
+    k = torch.tensor(g["k"], device="cuda")
+    p = torch.tensor(g["params"][None], device="cuda", requires_grad=True)
+    C = A.cl_with_gradient(p, k, o)
+    Cn = C.detach().cpu().numpy()[0]
+    rng = np.random.default_rng(9)
+    Cbar = rng.normal(size=Cn.shape) / np.abs(Cn)
+    (C * torch.tensor(Cbar[None], device="cuda")).sum().backward()
+    grad = p.grad.cpu().numpy()[0]
+    ref = np.array([np.sum(Cbar * g["dCl"][j]) for j in range(6)])
+    err = np.abs(grad - ref)
+    assert np.all(err <= 1e-4 * np.abs(ref).max()), (grad, ref, err)
+    # and the forward itself against the oracle's C_l
+    assert np.max(np.abs(Cn[0] - g["Cl"][0]) / np.abs(g["Cl"][0])) < 1e-5
 
 
 def test_taped_forward_matches_the_pipeline(A, case):
@@ -102,6 +126,8 @@ def test_gradient_calls_reject_bad_arguments(A, case):
     small = torch.empty(16, dtype=torch.float64, device="cuda")
     with pytest.raises(RuntimeError):
         A.abcmb_perturb_taped(bg, k, o, small)
+    with pytest.raises(ValueError):  # a negative step count is no plan
+        A.grad_plan(o, torch.full((1, k.shape[0]), -1, dtype=torch.int32))
     with pytest.raises(RuntimeError):
         A.abcmb_perturb_adjoint(bg, k, o, torch.zeros((1, k.shape[0], o.n_tau, 3), dtype=torch.float64,
                                                       device="cuda"), small, torch.zeros_like(bg))
