@@ -7,7 +7,12 @@
 //    moments l in [qP, qP+P) of each of the three chains (photon
 //    temperature, polarization, neutrinos) in registers.  Streaming couples
 //    neighbours only, so a substep exchanges one boundary value per chain
-//    per direction (two shuffles).  Lane 0 also owns l <= 2 of every chain,
+//    per direction (two shuffles).  Each moment is held rescaled, u_l =
+//    F_l / s_l with s_0 = 1 and s_l = A_l s_{l-1}, A_l the coefficient of
+//    F_{l-1} in F_l' = kH (A_l F_{l-1} - B_l F_{l+1}): then u_l' = kH (u_{l-1}
+//    - beta_l u_{l+1}), beta_l = B_l A_{l+1}, and the streaming costs two FMAs
+//    per moment instead of a multiply and two FMAs.  The equations' other
+//    terms (metric, Thomson, sources, tolerances) carry the s_l factors.  Lane 0 also owns l <= 2 of every chain,
 //    hence the metric sums, both Thomson blocks and the sources; the four
 //    scalars (eta, delta_c, delta_b, theta_b) are kept identical in all four
 //    lanes.
@@ -128,15 +133,34 @@ __device__ __forceinline__ QBg qbg(const double *ot, double lna, int q, int qb)
     return b;
 }
 
-// Per-chain streaming coefficients in shared memory: F_l' = k_H (A_l F_{l-1}
-// - B_l F_{l+1}) with A_l = l/(2l+1), B_l = (l+1)/(2l+1) below the truncation,
-// A_L = 1, B_L = 0 at it (the -(L+1)/(H tau) F_L term is added separately)
-// and A = B = 0 above it, so padding moments stay zero.
+// Per-chain streaming coefficients in shared memory.  The hierarchy reads
+// F_l' = k_H (A_l F_{l-1} - B_l F_{l+1}) with A_l = l/(2l+1), B_l =
+// (l+1)/(2l+1) below the truncation, A_L = 1, B_L = 0 at it (the -(L+1)/(H tau)
+// F_L term is added separately).  In the rescaled moments u_l = F_l / s_l
+// (s_0 = 1, s_l = A_l s_{l-1} up to L, s_l = 1 above) it reads u_l' = k_H
+// (u_{l-1} - beta_l u_{l+1}) with beta_l = B_l A_{l+1} (0 from L on); the
+// coupling to u_{l-1} is masked above L, so padding moments stay zero.
 struct QCoef {
-    const volatile double *A, *Bc; // [3][64]; volatile: re-read each substep, not held in registers
+    const volatile double *S, *Bc; // s_l, beta_l [3][64]; volatile: re-read, not held in registers
     int L[3];
     double L1[3]; // L + 1
 };
+
+// s_1 = 1/3 and s_2 = 2/15 for every truncation L >= 4 (A_1 = 1/3, A_2 = 2/5)
+constexpr double kS1 = 1.0 / 3.0, kS2 = 2.0 / 15.0;
+
+// the coefficient tables of one kernel's chains, filled once per CTA
+__device__ __forceinline__ void fill_coef(double *cS, double *cB, const int Ls[3])
+{
+    for (int i = threadIdx.x; i < 3 * 64; i += blockDim.x) {
+        const int ch = i / 64, l = i % 64, L = Ls[ch];
+        auto A = [L](int m) { return m < L ? (double)m / (2.0 * m + 1.0) : 1.0; };
+        double sl = 1.0;
+        for (int m = 1; m <= l && m <= L; m++) sl *= A(m);
+        cS[i] = l <= L ? sl : 1.0;
+        cB[i] = l < L ? (l + 1.0) / (2.0 * l + 1.0) * A(l + 1) : 0.0;
+    }
+}
 
 // Aitken-Neville factors T_{j,s} = T_{j,s-1} + (T_{j,s-1} - T_{j-1,s-1}) f[j][s] for
 // the harmonic sequence n_j = j extrapolated in h (IMEX Euler: f = (j - s) / s) and
@@ -163,7 +187,7 @@ __constant__ NevTab c_nev = make_nev();
 
 // per-mode constants
 struct QMode {
-    double k, ik, k2, k34, c43ik, c15ik; // k, 1/k, k^2, 3k/4, 4/(3k), 3/(2k)
+    double k, ik, k2, k4, c4ik, c05ik, ik3; // k, 1/k, k^2, k/4, 4/k, 1/(2k), 3/k
 };
 
 // metric h', eta' from lane 0's state (result broadcast to the quad)
@@ -174,7 +198,8 @@ __device__ __forceinline__ void q_metric(const double (&z)[3][P], const double (
     const double kH = m.k * b.ih;
     const double src = fma(b.fc, zs[1], fma(b.fb, zs[2], fma(b.fg, z[0][0], b.fnu * z[2][0])));
     const double h1 = fma(2.0 * kH * kH, zs[0], 3.0 * src);
-    const double e1 = (m.c15ik * b.hc) * fma(b.fb * m.ik, zs[3], fma(b.fg, z[0][1], b.fnu * z[2][1]));
+    // (3/2)(H/k^2) (f_b theta_b + f_g theta_g + f_nu theta_nu), theta = (3k/4) F_1 = (k/4) u_1
+    const double e1 = (m.c05ik * b.hc) * fma(b.fb * m.ik3, zs[3], fma(b.fg, z[0][1], b.fnu * z[2][1]));
     hp = __shfl_sync(kFull, h1, qb);
     ep = __shfl_sync(kFull, e1, qb);
 }
@@ -222,7 +247,7 @@ __device__ __forceinline__ void q_imex(double (&z)[3][P], double (&zs)[4], const
     const double hkH = hs * m.k * bc.ih, htr = hs * bc.iht;
 #pragma unroll
     for (int ch = 0; ch < 3; ch++) {
-        const volatile double *A = qc.A + 64 * ch, *Bc = qc.Bc + 64 * ch;
+        const volatile double *Bc = qc.Bc + 64 * ch;
         const double curL = pick_L<P>(z[ch], q, qc.L[ch]);
         double prev = q == 0 ? 0.0 : lft[ch];
 #pragma unroll
@@ -230,14 +255,15 @@ __device__ __forceinline__ void q_imex(double (&z)[3][P], double (&zs)[4], const
             const int l = q * P + p;
             const double cur = z[ch][p];
             const double nxt = p < P - 1 ? z[ch][p + 1] : rgt[ch];
-            z[ch][p] = fma(hkH, fma(-Bc[l], nxt, A[l] * prev), cur);
+            z[ch][p] = fma(hkH, fma(-Bc[l], nxt, l <= qc.L[ch] ? prev : 0.0), cur);
             prev = cur;
         }
         // truncation -(L+1)/(H tau) F_L
         put_L<P>(z[ch], q, qc.L[ch], fma(-htr * qc.L1[ch], curL, pick_L<P>(z[ch], q, qc.L[ch])));
     }
     if (q == 0) {
-        const double m0 = hs * (-2.0 / 3.0) * hp, m2 = hs * fma(4.0 / 15.0, hp, 1.6 * ep);
+        // metric terms of F_0 and F_2 (the latter divided by s_2 = 2/15)
+        const double m0 = hs * (-2.0 / 3.0) * hp, m2 = hs * fma(2.0, hp, 12.0 * ep);
         z[0][0] += m0;
         z[0][2] += m2;
         z[2][0] += m0;
@@ -256,14 +282,14 @@ __device__ __forceinline__ void q_imex(double (&z)[3][P], double (&zs)[4], const
     }
     if (q == 0) {
         const double idet = r * d12, ipin = r * (d1 * d3);
-        const double rb = zs[3], ru = m.k34 * z[0][1];
+        const double rb = zs[3], ru = m.k4 * z[0][1]; // theta_gamma
         zs[3] = idet * fma(d1, rb, hRnu * ru);
-        z[0][1] = (idet * m.c43ik) * fma(hnu, rb, (1.0 + hRnu) * ru);
+        z[0][1] = (idet * m.c4ik) * fma(hnu, rb, (1.0 + hRnu) * ru);
         const double r2 = z[0][2], g0 = z[1][0], g2 = z[1][2];
-        const double hpin = hnu * ((r2 + g0 + g2) * ipin);
-        z[0][2] = fma(0.1, hpin, r2) * dmp;
+        const double hpin = hnu * (fma(kS2, r2 + g2, g0) * ipin); // h nu Pi / (1 + ...)
+        z[0][2] = fma(0.75, hpin, r2) * dmp; // (1/10) hpin / s_2
         z[1][0] = fma(0.5, hpin, g0) * dmp;
-        z[1][2] = fma(0.1, hpin, g2) * dmp;
+        z[1][2] = fma(0.75, hpin, g2) * dmp;
     }
     zs[3] = __shfl_sync(kFull, zs[3], qb);
 }
@@ -282,24 +308,24 @@ __device__ __forceinline__ void q_rhs_axpy(const double (&s)[3][P], const double
         lft[ch] = __shfl_up_sync(kFull, s[ch][P - 1], 1, 4);
         rgt[ch] = __shfl_down_sync(kFull, s[ch][0], 1, 4);
     }
-    const double F1 = __shfl_sync(kFull, s[0][1], qb);
-    const double Pi = __shfl_sync(kFull, s[0][2] + s[1][0] + s[1][2], qb);
+    const double u1 = __shfl_sync(kFull, s[0][1], qb);                     // F_1 / s_1
+    const double Pi = __shfl_sync(kFull, fma(kS2, s[0][2] + s[1][2], s[1][0]), qb); // F_2 + G_0 + G_2
     const double tb = ss[3], fhp = fac * hp;
     ds[0] = fma(fac, ep, ds[0]);
     ds[1] = fma(-0.5, fhp, ds[1]);
     ds[2] = fma(-fac * b.ih, tb, ds[2]) - 0.5 * fhp;
-    ds[3] = fma(fac, fma(b.cs2 * m.k2 * b.ih, ss[2], fma(b.rnu, fma(m.k34, F1, -tb), -tb)), ds[3]);
+    ds[3] = fma(fac, fma(b.cs2 * m.k2 * b.ih, ss[2], fma(b.rnu, fma(m.k4, u1, -tb), -tb)), ds[3]);
     const double fkH = fac * m.k * b.ih, fnu = fac * b.nu, ftr = fac * b.iht;
 #pragma unroll
     for (int ch = 0; ch < 3; ch++) {
-        const volatile double *A = qc.A + 64 * ch, *Bc = qc.Bc + 64 * ch;
+        const volatile double *Bc = qc.Bc + 64 * ch;
         double prev = q == 0 ? 0.0 : lft[ch];
 #pragma unroll
         for (int p = 0; p < P; p++) {
             const int l = q * P + p;
             const double cur = s[ch][p];
             const double nxt = p < P - 1 ? s[ch][p + 1] : rgt[ch];
-            double v = fma(fkH, fma(-Bc[l], nxt, A[l] * prev), d[ch][p]);
+            double v = fma(fkH, fma(-Bc[l], nxt, l <= qc.L[ch] ? prev : 0.0), d[ch][p]);
             if (ch == 0) v = fma((l >= 1) ? -fnu : 0.0, cur, v);
             if (ch == 1) v = fma(-fnu, cur, v);
             d[ch][p] = v;
@@ -309,12 +335,13 @@ __device__ __forceinline__ void q_rhs_axpy(const double (&s)[3][P], const double
         put_L<P>(d[ch], q, qc.L[ch], fma(-ftr * qc.L1[ch], curL, pick_L<P>(d[ch], q, qc.L[ch])));
     }
     if (q == 0) {
-        const double fPi = fnu * Pi, m2 = fma(4.0 / 15.0, fhp, 1.6 * fac * ep);
+        // the F_2 rows divided by s_2 = 2/15; the F_1 row by s_1 = 1/3
+        const double fPi = fnu * Pi, m2 = fma(2.0, fhp, 12.0 * fac * ep);
         d[0][0] = fma(-2.0 / 3.0, fhp, d[0][0]);
-        d[0][1] = fma(fnu * m.c43ik, tb, d[0][1]);
-        d[0][2] += fma(0.1, fPi, m2);
+        d[0][1] = fma(fnu * m.c4ik, tb, d[0][1]);
+        d[0][2] += fma(0.75, fPi, m2);
         d[1][0] = fma(0.5, fPi, d[1][0]);
-        d[1][2] = fma(0.1, fPi, d[1][2]);
+        d[1][2] = fma(0.75, fPi, d[1][2]);
         d[2][0] = fma(-2.0 / 3.0, fhp, d[2][0]);
         d[2][2] += m2;
     }
@@ -324,7 +351,8 @@ __device__ __forceinline__ void q_rhs_axpy(const double (&s)[3][P], const double
 // neutrino F_0..F_2 (lane 0 of a quad), then the four scalars.
 constexpr int kSrcComp = 12;
 
-// Sources at a tau node from the state components v (kSrcComp values, order above).
+// Sources at a tau node from the state components v (kSrcComp values, order
+// above; moments rescaled, u_l = F_l / s_l).
 __device__ __forceinline__ void q_sources_v(const double *ot, const double *nd, double k, const double sw[3],
                                             const double (&v)[kSrcComp], double *S)
 {
@@ -332,9 +360,9 @@ __device__ __forceinline__ void q_sources_v(const double *ot, const double *nd, 
     const double Hc = nd[N_HC], dHc = nd[N_DHC], g = nd[N_G], dg = nd[N_DG], emk = nd[N_EXPMK];
     const double kH = k / Hc, k2 = k * k;
     const double eta = v[8], dc = v[9], db = v[10], tb = v[11];
-    const double Fg0 = v[0], Fg1 = v[1], Fg2 = v[2];
-    const double G0 = v[3], G2 = v[4];
-    const double Fn0 = v[5], Fn1 = v[6], Fn2 = v[7];
+    const double Fg0 = v[0], Fg1 = kS1 * v[1], Fg2 = kS2 * v[2];
+    const double G0 = v[3], G2 = kS2 * v[4];
+    const double Fn0 = v[5], Fn1 = kS1 * v[6], Fn2 = kS2 * v[7];
     const double hp = 2.0 * kH * kH * eta + 3.0 * (b.fc * dc + b.fb * db + b.fg * Fg0 + b.fnu * Fn0);
     const double ep = 1.5 / kH * (b.fb * tb / k + b.fg * Fg1 + b.fnu * Fn1);
     const double alpha = Hc * (hp + 6.0 * ep) / (2.0 * k2);
@@ -530,9 +558,10 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
     md.k = kv[kidx];
     md.ik = 1.0 / md.k;
     md.k2 = md.k * md.k;
-    md.k34 = 0.75 * md.k;
-    md.c43ik = (4.0 / 3.0) * md.ik;
-    md.c15ik = 1.5 * md.ik;
+    md.k4 = 0.25 * md.k;
+    md.c4ik = 4.0 * md.ik;
+    md.c05ik = 0.5 * md.ik;
+    md.ik3 = 3.0 * md.ik;
     const double k = md.k;
     double *Sm = PK ? nullptr : S + ((long)b * Nk + kidx) * (long)n_tau * (DM ? 1 : 3);
     // shared memory of this lane: element e of vector v at smw[(v E + e) 32 + lane]
@@ -586,12 +615,12 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
         for (int ch = 0; ch < 3; ch++)
 #pragma unroll
             for (int p = 0; p < P; p++) z[ch][p] = 0.0;
-        if (q == 0) {
+        if (q == 0) { // rescaled: u_1 = F_1 / s_1 = 3 F_1, u_2 = F_2 / s_2 = (15/2) F_2
             z[0][0] = dg;
-            z[0][1] = F1;
+            z[0][1] = 3.0 * F1;
             z[2][0] = dg;
-            z[2][1] = F1 * (23.0 + 4.0 * Rn) / (15.0 + 4.0 * Rn);
-            z[2][2] = (8.0 / 3.0) * C * kt * kt / (15.0 + 4.0 * Rn);
+            z[2][1] = 3.0 * F1 * (23.0 + 4.0 * Rn) / (15.0 + 4.0 * Rn);
+            z[2][2] = 20.0 * C * kt * kt / (15.0 + 4.0 * Rn);
         }
         zs[0] = 2.0 * C - C * kt * kt * (5.0 + 4.0 * Rn) / (6.0 * (15.0 + 4.0 * Rn));
         zs[1] = 0.75 * dg;
@@ -663,14 +692,16 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
         // the inverse scales occupy the last tableau column's slot, which is
         // written only by the last column, after its element's scale was read
         {
+            // magnitudes and tolerances in the moments F_l = s_l u_l
             double cm2 = 0.0, cm3 = 0.0;
 #pragma unroll
             for (int p = 0; p < P; p++) {
+                const int l = q * P + p;
                 z[0][p] = Y(p);
                 z[1][p] = Y(P + p);
                 z[2][p] = Y(2 * P + p);
-                cm2 = fmax(cm2, fmax(fabs(z[0][p]), fabs(z[1][p])));
-                cm3 = fmax(cm3, fabs(z[2][p]));
+                cm2 = fmax(cm2, fmax(fabs(z[0][p]) * qc.S[l], fabs(z[1][p]) * qc.S[64 + l]));
+                cm3 = fmax(cm3, fabs(z[2][p]) * qc.S[128 + l]);
             }
             load_scalars(zs, Y(3 * P), qb);
             // floors clamped away from zero keep every scale a normal number
@@ -685,8 +716,9 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
                 for (int p = 0; p < P; p++) {
                     const int l = q * P + p;
                     const bool off = l > qc.L[ch] || (excl && (ch == 1 || (ch == 0 && l >= 2)));
-                    const double sc = fma(rtol, fmax(fabs(z[ch][p]), ch < 2 ? fl2 : fl3), atol);
-                    T(kQK - 1, ch * P + p) = off ? 0.0 : rcp_approx(sc);
+                    const double sl = qc.S[64 * ch + l];
+                    const double sc = fma(rtol, fmax(fabs(z[ch][p]) * sl, ch < 2 ? fl2 : fl3), atol);
+                    T(kQK - 1, ch * P + p) = off ? 0.0 : sl * rcp_approx(sc);
                 }
         }
         // interpolation data at the step start (z, zs hold the state here)
@@ -907,20 +939,16 @@ perturb_quad_kernel(int B, int Nk, const double *__restrict__ bg, long len, cons
                     double s_dop, double *S, int *status, int *steps)
 {
     extern __shared__ double qsm[];
-    __shared__ double cA[3 * 64], cB[3 * 64];
+    __shared__ double cS[3 * 64], cB[3 * 64];
     const int Ls[3] = {Lg, Lp, Ln};
-    for (int i = threadIdx.x; i < 3 * 64; i += blockDim.x) {
-        const int ch = i / 64, l = i % 64, L = Ls[ch];
-        cA[i] = l < L ? (double)l / (2.0 * l + 1.0) : (l == L ? 1.0 : 0.0);
-        cB[i] = l < L ? (l + 1.0) / (2.0 * l + 1.0) : 0.0;
-    }
+    fill_coef(cS, cB, Ls);
     __syncthreads();
     constexpr int E = 3 * P + 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long M = (long)B * Nk;
     const long mi = ((long)blockIdx.x * W + warp) * 8 + (lane >> 2);
     QCoef qc;
-    qc.A = cA;
+    qc.S = cS;
     qc.Bc = cB;
     qc.L[0] = Lg;
     qc.L[1] = Lp;
@@ -941,20 +969,16 @@ pk_quad_kernel(int B, int Nk, const double *__restrict__ bg, long len, const dou
                int *steps)
 {
     extern __shared__ double qsm[];
-    __shared__ double cA[3 * 64], cB[3 * 64];
+    __shared__ double cS[3 * 64], cB[3 * 64];
     const int Ls[3] = {Lg, Lp, Ln};
-    for (int i = threadIdx.x; i < 3 * 64; i += blockDim.x) {
-        const int ch = i / 64, l = i % 64, L = Ls[ch];
-        cA[i] = l < L ? (double)l / (2.0 * l + 1.0) : (l == L ? 1.0 : 0.0);
-        cB[i] = l < L ? (l + 1.0) / (2.0 * l + 1.0) : 0.0;
-    }
+    fill_coef(cS, cB, Ls);
     __syncthreads();
     constexpr int E = 3 * P + 1;
     const int lane = threadIdx.x & 31;
     const long M = (long)B * Nk;
     const long mi = (long)blockIdx.x * 8 + (lane >> 2);
     QCoef qc;
-    qc.A = cA;
+    qc.S = cS;
     qc.Bc = cB;
     qc.L[0] = Lg;
     qc.L[1] = Lp;
@@ -972,20 +996,16 @@ dm_quad_kernel(int B, int Nk, const double *__restrict__ bg, long len, const dou
                int Lp, int Ln, double rtol, double atol, int max_steps, double *Dm, int *status)
 {
     extern __shared__ double qsm[];
-    __shared__ double cA[3 * 64], cB[3 * 64];
+    __shared__ double cS[3 * 64], cB[3 * 64];
     const int Ls[3] = {Lg, Lp, Ln};
-    for (int i = threadIdx.x; i < 3 * 64; i += blockDim.x) {
-        const int ch = i / 64, l = i % 64, L = Ls[ch];
-        cA[i] = l < L ? (double)l / (2.0 * l + 1.0) : (l == L ? 1.0 : 0.0);
-        cB[i] = l < L ? (l + 1.0) / (2.0 * l + 1.0) : 0.0;
-    }
+    fill_coef(cS, cB, Ls);
     __syncthreads();
     constexpr int E = 3 * P + 1;
     const int lane = threadIdx.x & 31;
     const long M = (long)B * Nk;
     const long mi = (long)blockIdx.x * 8 + (lane >> 2);
     QCoef qc;
-    qc.A = cA;
+    qc.S = cS;
     qc.Bc = cB;
     qc.L[0] = Lg;
     qc.L[1] = Lp;
