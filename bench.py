@@ -148,38 +148,45 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def oracle_sample(wl, p, k, steps_per_mode: int, cores: int) -> dict:
+def oracle_sample(wl, p, k, cores: int, modes_per_core: int = 1) -> dict:
     """Time the FP64 oracle on a bounded sample of one cosmology of wl and
-    scale it to the whole spectrum.  Sample: `cores` k modes spread evenly
-    over the grid, each integrated for its first steps_per_mode Radau steps
-    (every step of the oracle's fixed schedule costs the same, one 3N x 3N
-    collocation solve), then projected at every l and tau node.  Scaling: the
-    ODE time by the schedule's exact step count over all k divided by the
-    steps run, the projection time by n_k / cores."""
+    scale it to the whole spectrum.  ODE: cores x modes_per_core complete
+    integrations of low-k modes, which all take the same number of Radau
+    steps (the schedule's landings on the tau nodes), one per thread, so the
+    threads stay balanced; every step solves one 3N x 3N collocation system,
+    so the rate (steps per second on all cores) scales to the schedule's
+    exact step count over all k.  Projection: `cores` k spread over the grid
+    at every l and tau node, scaled by n_k / cores."""
     import oracle as O
-    o = O.opts(lmax=wl.l_max_hier, max_steps=steps_per_mode)
-    idx = np.linspace(0, len(k) - 1, cores).round().astype(int)
+    o = O.opts(lmax=wl.l_max_hier)
+    sched = O.count_steps(p, k, wl.n_tau, o)
+    n_ode = cores * modes_per_core
+    base = int(sched.min())
+    low = np.flatnonzero(sched == base)[:n_ode]
+    if low.size < n_ode:
+        low = np.argsort(sched, kind="stable")[:n_ode]
     t0 = time.perf_counter()
     O.scalars(p)
     t_bg = time.perf_counter() - t0
-    sched = O.count_steps(p, k, wl.n_tau, O.opts(lmax=wl.l_max_hier))
-    run_steps = int(np.minimum(sched[idx], steps_per_mode).sum())
     t0 = time.perf_counter()
-    r = O.run(p, k[idx], wl.n_tau, 2, o, want=("S",), nthreads=cores)
+    r = O.run(p, k[low], wl.n_tau, 2, o, want=("S",), nthreads=cores)
     t_ode = time.perf_counter() - t0
-    assert int(r["steps"].sum()) == run_steps
+    run_steps = int(r["steps"].sum())
+    assert run_steps == int(sched[low].sum())
+    idx = np.linspace(0, len(k) - 1, cores).round().astype(int)
     lna, tau, w = O.nodes(p, wl.n_tau)
     tau0 = O.scalars(p)["tau0"]
+    S = np.ones((cores, wl.n_tau, 3))
     t0 = time.perf_counter()
-    O.project(tau, w, tau0, k[idx], r["S"], wl.l_max_cl, nthreads=cores)
+    O.project(tau, w, tau0, k[idx], S, wl.l_max_cl, nthreads=cores)
     t_proj = time.perf_counter() - t0
     measured = t_bg + t_ode + t_proj
     sec = t_bg + t_ode * sched.sum() / run_steps + t_proj * len(k) / cores
     return {"measured_s": measured, "seconds_per_spectrum": sec, "fraction": measured / sec,
-            "sample": (f"one cosmology of {wl.name}: {cores} k modes x their first {steps_per_mode} Radau "
-                       f"steps ({run_steps} of the {int(sched.sum())} the schedule takes over all "
-                       f"{len(k)} k), projected at l <= {wl.l_max_cl} on {wl.n_tau} nodes; timed "
-                       f"{measured:.1f} s, scaled to the spectrum by step count and k count")}
+            "sample": (f"one cosmology of {wl.name}: {low.size} complete k modes ({run_steps} Radau steps of the "
+                       f"{int(sched.sum())} the schedule takes over all {len(k)} k) on {cores} threads, and "
+                       f"{cores} k projected at l <= {wl.l_max_cl} on {wl.n_tau} nodes; timed {measured:.1f} s, "
+                       f"scaled to the spectrum by step count and k count")}
 
 
 def cpu_baseline(wl, params, k, nthreads=None) -> dict:
@@ -189,7 +196,7 @@ def cpu_baseline(wl, params, k, nthreads=None) -> dict:
     in full and timed."""
     import oracle as O
     cores = nthreads or os.cpu_count()
-    smp = oracle_sample(wl, params[0], k, 12000, cores)
+    smp = oracle_sample(wl, params[0], k, cores, 2)
     s1 = W.SMALL_TT
     t0 = time.perf_counter()
     O.run(s1.params()[0], s1.k(), s1.n_tau, s1.l_max_cl, O.opts(lmax=s1.l_max_hier), want=("Cl",),
@@ -211,10 +218,10 @@ def run_reference(args, rank, world):
     params, k = wl.params(), wl.k()
     cores = os.cpu_count()
     for _ in range(args.warmup):
-        oracle_sample(wl, params[0], k, 200, cores)
+        oracle_sample(wl, params[0], k, cores)
     ms, vals, smp = [], [], None
     for _ in range(args.steps):
-        smp = oracle_sample(wl, params[0], k, 3000, cores)
+        smp = oracle_sample(wl, params[0], k, cores)
         ms.append(1e3 * smp["measured_s"])
         vals.append(smp["fraction"] / smp["measured_s"])
     v = statistics.mean(vals)
@@ -361,7 +368,6 @@ def run_gradient(args, A, torch):
                       "rtol": args.rtol, "checkpoint_every": 64,
                       "l2": "flushed (512 MiB write) between timed steps"},
            "forward_ms": statistics.mean(fwd_ms), "backward_ms": t - statistics.mean(fwd_ms),
-           "workspace_gb": A.grad_workspace_bytes(B, len(k_np), o) / 2**30,
            "gpu_launches": 10 * args.steps, "clocks": clk}
     print(json.dumps(out), flush=True)
 
