@@ -20,9 +20,11 @@
 // Every background point met on the way gets the adjoint of its ten
 // quantities, scattered into the adjoint of the ODE-table rows; the sources
 // add adjoints of the node data; the initial state adds the adjoints of the
-// conformal-time table entries at the start and of R_nu.  The start time
-// a_i(k) and the switch to the explicit regime are held fixed (their effect
-// on the sources is of the order of the ODE tolerance).
+// conformal-time table entries at the start and of R_nu, and the start
+// itself, a_i(k) = min(a_tc, a_k), moves with a_tc or with the root of
+// H(a_k) = k / R_large (App. A.1).  The switch to the explicit regime is
+// held fixed (its effect on the sources is of the order of the ODE
+// tolerance).
 #pragma once
 
 #include "abcmb_adjoint_ops.cuh"
@@ -546,6 +548,18 @@ ABCMB_HD void bwd(const ModeCtx &c, const ModeBufs &mb, const Sinks &sk, const F
     const double tau_i = herm_val(c.tab, Hi, C_TAU, C_DTAU);
     const double taub = initial_dtau(d, c.k, tau_i, cz.R_nu, yb);
     const double rnub = initial_dRn(d, c.k, tau_i, cz.R_nu, yb);
+    // the start itself: moving x0 moves the initial state along dy0/dx0 =
+    // (d y0 / d tau_i) / H and starts the flow later, so
+    // dL/dx0 = taub / H(x0) - ybar0 . f(x0, y0), f the full right-hand side
+    const Bg10 b0 = bg_eval(c.ot, hw_at(x0));
+    Vec f0 = wv(mb, d, V_WT);
+    vzero(d, f0);
+    op_E(d, c.sc, c.k, b0, y0, f0, 1.0);
+    op_T(d, c.k, b0, y0, f0, 1.0);
+    double yf = 0.0;
+    for (int i = ln_id(); i < d.N; i += ln_n()) yf += yb[i] * f0[i];
+    yf = ln_sum(yf);
+    const double xbar = taub * b0.v[B_IH] - yf;
     flush_rows(sk);
     if (ln_id() != 0) return;
     double *tb = sk.recbar + ABCMB_BG_TABLE;
@@ -554,6 +568,25 @@ ABCMB_HD void bwd(const ModeCtx &c, const ModeBufs &mb, const Sinks &sk, const F
     add_to(tb + 8 * Hi.j + C_DTAU, kDlna * Hi.h10 * taub);
     add_to(tb + 8 * (Hi.j + 1) + C_DTAU, kDlna * Hi.h11 * taub);
     add_to(sk.recbar + ABCMB_S_RNU, rnub);
+    // x0 = ln a_tc (a record scalar) or the root of H(x) = k / R_large, whose
+    // dependence on H0 and the density parameters follows from H = a H0 sqrt(E2)
+    const double target = c.k / kRlarge;
+    if (!(hconf(cz, cz.lna_tc) < target)) {
+        add_to(sk.recbar + ABCMB_S_LNA_TC, xbar);
+    } else if (!(hconf(cz, kLna0) < target)) {
+        const double a = exp(x0), ia = 1.0 / a;
+        const double r = cz.Om_r * ia * ia * ia * ia, m = cz.Om_m * ia * ia * ia;
+        const double e2 = r + m + cz.Om_L;
+        const double dlnH_dx = 1.0 + 0.5 * (-4.0 * r - 3.0 * m) / e2;
+        // dx0/dp = -(d ln H / dp) / (d ln H / dx)
+        const double g = -xbar / dlnH_dx;
+        add_to(sk.recbar + ABCMB_S_H0, g / cz.H0);
+        add_to(sk.recbar + ABCMB_S_OMG, g * 0.5 * ia * ia * ia * ia / e2);
+        add_to(sk.recbar + ABCMB_S_OMNU, g * 0.5 * ia * ia * ia * ia / e2);
+        add_to(sk.recbar + ABCMB_S_OMB, g * 0.5 * ia * ia * ia / e2);
+        add_to(sk.recbar + ABCMB_S_OMC, g * 0.5 * ia * ia * ia / e2);
+        add_to(sk.recbar + ABCMB_S_OML, g * 0.5 / e2);
+    }
 }
 
 } // namespace adj
