@@ -309,9 +309,9 @@ ABCMB_HD void tla_rhs(const Cosmo &c, double lna, double xp, double Tm_in, bool 
 
 // The parts of tla_rhs that depend on ln a alone, at one stage point.
 struct TlaPt {
-    double T, nH, H, K, be, bex, xhe, g0, e1, e2;
+    double T, nH, H, K, be, bex, xhe, g0, e1, e2, iH;
 };
-constexpr int kTlaPtDoubles = 10;
+constexpr int kTlaPtDoubles = 11;
 
 ABCMB_HD TlaPt tla_point(const Cosmo &c, double lna)
 {
@@ -331,6 +331,7 @@ ABCMB_HD TlaPt tla_point(const Cosmo &c, double lna)
     const double lt0 = log(P.T / kKB * 1.0e-4);
     P.e1 = exp(-0.6166 * lt0);
     P.e2 = exp(0.5300 * lt0);
+    P.iH = 1.0 / P.H;
     return P;
 }
 
@@ -341,6 +342,10 @@ ABCMB_HD TlaPt tla_point(const Cosmo &c, double lna)
 ABCMB_HD void tla_rhs_pt(const Cosmo &c, const TlaPt &P, double xp, double Tm_in, bool two, double *dxp,
                          double *dTm)
 {
+    // The right-hand side is evaluated sequentially, one stage after another,
+    // so its chain of dependent instructions sets the builder's time: the
+    // series below run in Horner form on constant coefficients, and 1/H is
+    // tabulated, which leaves two divisions.
     const double xe = xp + P.xhe;
     const double gam = P.g0 * xe / (1.0 + c.f_He + xe);
     double Tm, al;
@@ -348,16 +353,18 @@ ABCMB_HD void tla_rhs_pt(const Cosmo &c, const TlaPt &P, double xp, double Tm_in
         const double r = P.H / gam;
         Tm = P.T * (1.0 - r);
         if (r < 0.02) {
-            double L = 0.0, rn = 1.0;
-            for (int n = 1; n <= 12; n++) {
-                rn *= r;
-                L -= rn / n;
-            }
+            // L = log(1 - r) = -sum_{n=1}^{12} r^n / n
+            double L = 1.0 / 12.0;
+#pragma unroll
+            for (int n = 11; n >= 1; n--) L = fma(r, L, 1.0 / n);
+            L *= -r;
+            // f = exp(q) = sum_{n=0}^{8} q^n / n!, q1 = -0.6166 L, q2 = 0.53 L
             const double q1 = -0.6166 * L, q2 = 0.5300 * L;
             double f1 = 1.0, f2 = 1.0;
+#pragma unroll
             for (int n = 8; n >= 1; n--) {
-                f1 = 1.0 + q1 * f1 / n;
-                f2 = 1.0 + q2 * f2 / n;
+                f1 = fma(q1 * (1.0 / n), f1, 1.0);
+                f2 = fma(q2 * (1.0 / n), f2, 1.0);
             }
             al = 4.309e-13 * P.e1 * f1 / (1.0 + 0.6703 * P.e2 * f2);
         } else {
@@ -369,8 +376,8 @@ ABCMB_HD void tla_rhs_pt(const Cosmo &c, const TlaPt &P, double xp, double Tm_in
     }
     const double n1s = P.nH * (1.0 - xp);
     const double C = (1.0 + P.K * kL2s1s * n1s) / (1.0 + P.K * (kL2s1s + P.be) * n1s);
-    *dxp = -C * (al * P.nH * xe * xp - P.bex * (1.0 - xp)) / P.H;
-    *dTm = two ? (-2.0 * Tm + gam / P.H * (P.T - Tm)) : 0.0;
+    *dxp = -C * (al * P.nH * xe * xp - P.bex * (1.0 - xp)) * P.iH;
+    *dTm = two ? (-2.0 * Tm + gam * P.iH * (P.T - Tm)) : 0.0;
 }
 
 ABCMB_HD double nuT_closed(const Cosmo &c, double lna, double xe)
@@ -551,15 +558,36 @@ ABCMB_HD void build_background(const double *p, double *rec, int n_tau, int lane
 
     // reionization redshift from tau_reion (lane-parallel quadrature, every
     // lane takes the same bisection path)
+    // tau_reion(z) is smooth and increasing: regula falsi with the Illinois
+    // modification (the retained end's value halved when the same end is
+    // kept twice) converges superlinearly inside the bracket [0, 60], in about
+    // a tenth of the evaluations bisection needs to reach rounding
     {
         double lo = 0.0, hi = 60.0;
-        if (tau_reion_par(c, hi, lane, nl) < p[5] || tau_reion_par(c, lo, lane, nl) > p[5])
-            status = ABCMB_E_BACKGROUND;
-        for (int it = 0; it < 80; it++) {
-            const double mid = 0.5 * (lo + hi);
-            if (tau_reion_par(c, mid, lane, nl) < p[5]) lo = mid; else hi = mid;
+        double flo = tau_reion_par(c, lo, lane, nl) - p[5], fhi = tau_reion_par(c, hi, lane, nl) - p[5];
+        if (!(fhi >= 0.0) || !(flo <= 0.0)) status = ABCMB_E_BACKGROUND;
+        double z = 0.5 * (lo + hi);
+        int side = 0;
+        for (int it = 0; it < 100 && status == ABCMB_OK; it++) {
+            z = (fhi - flo) > 0.0 ? (lo * fhi - hi * flo) / (fhi - flo) : 0.5 * (lo + hi);
+            if (!(z > lo && z < hi)) z = 0.5 * (lo + hi);
+            if (hi - lo <= 1e-13 * (1.0 + hi)) break;
+            const double f = tau_reion_par(c, z, lane, nl) - p[5];
+            if (f == 0.0) break;
+            if (f < 0.0) {
+                lo = z;
+                flo = f;
+                if (side < 0) fhi *= 0.5;
+                side = -1;
+            } else {
+                hi = z;
+                fhi = f;
+                if (side > 0) flo *= 0.5;
+                side = 1;
+            }
+            if (fabs(f) <= 1e-15 * p[5]) break;
         }
-        c.z_reion = 0.5 * (lo + hi);
+        c.z_reion = z;
     }
 
     // Peebles TLA (x_p, then also T_m below z = 700), RK4, stored at the table
@@ -578,7 +606,7 @@ ABCMB_HD void build_background(const double *p, double *rec, int n_tau, int lane
             const TlaPt P = tla_point(c, kLna0 + (jc + 0.5 * i) * kDlna);
             double *d = pts + kTlaPtDoubles * i;
             d[0] = P.T; d[1] = P.nH; d[2] = P.H; d[3] = P.K; d[4] = P.be;
-            d[5] = P.bex; d[6] = P.xhe; d[7] = P.g0; d[8] = P.e1; d[9] = P.e2;
+            d[5] = P.bex; d[6] = P.xhe; d[7] = P.g0; d[8] = P.e1; d[9] = P.e2; d[10] = P.iH;
         }
         lane_sync();
         if (lane == 0) {
@@ -586,7 +614,7 @@ ABCMB_HD void build_background(const double *p, double *rec, int n_tau, int lane
                 const double *d = pts + kTlaPtDoubles * i;
                 TlaPt P;
                 P.T = d[0]; P.nH = d[1]; P.H = d[2]; P.K = d[3]; P.be = d[4];
-                P.bex = d[5]; P.xhe = d[6]; P.g0 = d[7]; P.e1 = d[8]; P.e2 = d[9];
+                P.bex = d[5]; P.xhe = d[6]; P.g0 = d[7]; P.e1 = d[8]; P.e2 = d[9]; P.iH = d[10];
                 return P;
             };
             double dum;
