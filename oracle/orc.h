@@ -28,11 +28,18 @@
  *                     c_ell_def, eq. PK_pivot), trapezoid in ln k
  *
  * Parity-unpinned parts are listed in the file headers that implement them.
+ *
+ * The arithmetic is written once over the scalar type real_t (orc_real.h):
+ * double in liborc.so, double complex in liborc_cs.so, which gives the
+ * forward sensitivities of every output to one parameter by the complex
+ * step (see orc_real.h).
  */
 #ifndef ORC_H
 #define ORC_H
 
 #include <stddef.h>
+
+#include "orc_real.h"
 
 #define ORC_MAX_L 64
 
@@ -61,84 +68,84 @@ typedef struct orc_cosmo orc_cosmo;
 
 struct orc_cosmo {
     /* inputs */
-    double omega_b, omega_cdm, h, n_s, ln10As, tau_reio;
+    real_t omega_b, omega_cdm, h, n_s, ln10As, tau_reio;
     /* fixed parameters (App. A.2 defaults) */
-    double YHe, TCMB0, Tnu_ratio, N_nu;
-    double z_re_He, dz_re_He, dz_re, beta_re;
-    double R_tc, R_large, k_pivot;
+    real_t YHe, TCMB0, Tnu_ratio, N_nu;
+    real_t z_re_He, dz_re_He, dz_re, beta_re;
+    real_t R_tc, R_large, k_pivot;
     /* derived */
-    double H0;                         /* [1/Mpc]                           */
-    double Om_b, Om_c, Om_g, Om_nu, Om_r, Om_m, Om_L;
-    double R_nu, f_He, nH0, A_s;
-    double rho_g0;                     /* photon energy density today [eV/cm^3] */
-    double z_reion;
-    double lna_tc, lna_He3, lna_sw, lna_700;
-    double tau0;
+    real_t H0;                         /* [1/Mpc]                           */
+    real_t Om_b, Om_c, Om_g, Om_nu, Om_r, Om_m, Om_L;
+    real_t R_nu, f_He, nH0, A_s;
+    real_t rho_g0;                     /* photon energy density today [eV/cm^3] */
+    real_t z_reion;
+    real_t lna_tc, lna_He3, lna_sw, lna_700;
+    real_t tau0;
     int hooks;
     /* one massive neutrino (App. B.3 "Massive neutrinos", App. C.6): mass,
        temperature today T_ncdm = 0.71611 T_gamma, x = a m / T_ncdm at a = 1,
        and rho_ncdm / rho_crit = ncdm_pref a^-4 sum_i K_i (1 + e^-q_i) eps_i / q_i^2 */
-    double m_ncdm, T_ncdm_ratio, ncdm_x1, ncdm_pref, Om_ncdm_rel, Om_ncdm;
+    real_t m_ncdm, T_ncdm_ratio, ncdm_x1, ncdm_pref, Om_ncdm_rel, Om_ncdm;
     /* conformal-time table, uniform in ln a */
-    int n_ct; double ct_lna0, ct_dlna; double *ct_tau;
+    int n_ct; real_t ct_lna0, ct_dlna; real_t *ct_tau;
     /* TLA table (x_p, T_m and their ln a derivatives) on two uniform ln a
        segments: [lna_sw, lna_700] (n_th1 intervals) and [lna_700, 0]
        (n_th2 intervals); node i at th_lna[i] */
-    int n_th1, n_th2; double *th_lna;
-    double *th_xp, *th_dxp, *th_Tm, *th_dTm;
+    int n_th1, n_th2; real_t *th_lna;
+    real_t *th_xp, *th_dxp, *th_Tm, *th_dTm;
     /* optical depth table kappa(ln a), uniform grid from ct_lna0 to 0 */
-    int n_kp; double kp_lna0, kp_dlna; double *kp_kappa;
+    int n_kp; real_t kp_lna0, kp_dlna; real_t *kp_kappa;
     /* tau nodes */
-    int n_tau; double *node_lna, *node_tau, *node_w;
+    int n_tau; real_t *node_lna, *node_tau, *node_w;
 };
 
 /* background point evaluation */
 typedef struct {
-    double a, Hc, dHc;            /* conformal Hubble [1/Mpc] and d/dln a */
-    double fc, fb, fg, fnu;       /* rho_i / rho_tot                      */
-    double fncdm, wncdm;          /* massive neutrinos: rho / rho_tot, p / rho */
-    double ncdm_x;                /* a m / T_ncdm                          */
-    double ncdm_n;                /* ncdm_pref a^-4 / (rho_tot / rho_crit): turns the
+    real_t a, Hc, dHc;            /* conformal Hubble [1/Mpc] and d/dln a */
+    real_t fc, fb, fg, fnu;       /* rho_i / rho_tot                      */
+    real_t fncdm, wncdm;          /* massive neutrinos: rho / rho_tot, p / rho */
+    real_t ncdm_x;                /* a m / T_ncdm                          */
+    real_t ncdm_n;                /* ncdm_pref a^-4 / (rho_tot / rho_crit): turns the
                                      momentum sums into fractions of rho_tot */
-    double tau;                   /* conformal time [Mpc]                 */
-    double xe, dxe;               /* free-electron fraction and d/dln a   */
-    double nuT;                   /* 1/(H tau_c) = a n_e sigma_T / H      */
-    double Rinv;                  /* 4 rho_g / (3 rho_b)                  */
-    double cs2;                   /* baryon sound speed squared           */
-    double kappa, expmk, g, dg;   /* optical depth, e^-kappa, visibility  */
+    real_t tau;                   /* conformal time [Mpc]                 */
+    real_t xe, dxe;               /* free-electron fraction and d/dln a   */
+    real_t nuT;                   /* 1/(H tau_c) = a n_e sigma_T / H      */
+    real_t Rinv;                  /* 4 rho_g / (3 rho_b)                  */
+    real_t cs2;                   /* baryon sound speed squared           */
+    real_t kappa, expmk, g, dg;   /* optical depth, e^-kappa, visibility  */
 } orc_bg;
 
 /* orc_background.c */
-int orc_cosmo_init(orc_cosmo *c, const double p[6], int n_tau, int hooks, double m_ncdm, int node_recipe);
+int orc_cosmo_init(orc_cosmo *c, const real_t p[6], int n_tau, int hooks, double m_ncdm, int node_recipe);
 void orc_cosmo_free(orc_cosmo *c);
 /* with_thermo: 0 background only, 1 + what the ODE needs, 2 + kappa, g, g' */
-void orc_bg_eval(const orc_cosmo *c, double lna, orc_bg *out, int with_thermo);
-double orc_Hconf(const orc_cosmo *c, double lna);
-double orc_tau_of_lna(const orc_cosmo *c, double lna);
-double orc_xe_of_lna(const orc_cosmo *c, double lna, double *dxe);
-double orc_Tm_of_lna(const orc_cosmo *c, double lna, double *dlnTm);
-double orc_lna_start(const orc_cosmo *c, double k);
+void orc_bg_eval(const orc_cosmo *c, real_t lna, orc_bg *out, int with_thermo);
+real_t orc_Hconf(const orc_cosmo *c, real_t lna);
+real_t orc_tau_of_lna(const orc_cosmo *c, real_t lna);
+real_t orc_xe_of_lna(const orc_cosmo *c, real_t lna, real_t *dxe);
+real_t orc_Tm_of_lna(const orc_cosmo *c, real_t lna, real_t *dlnTm);
+real_t orc_lna_start(const orc_cosmo *c, real_t k);
 
 /* orc_linalg.c */
-int orc_lu_factor(double *A, int n, int *piv, int *ext /* [2n] */);
-void orc_lu_solve(const double *A, int n, const int *piv, const int *ext, double *b);
+int orc_lu_factor(real_t *A, int n, int *piv, int *ext /* [2n] */);
+void orc_lu_solve(const real_t *A, int n, const int *piv, const int *ext, real_t *b);
 
 /* orc_perturb.c */
 int orc_nstate(const orc_opts *o);
-int orc_schedule_count(const orc_cosmo *c, const orc_opts *o, double k, double x0, double x1);
-void orc_rhs_bg(const orc_opts *o, const orc_bg *b, double k, const double *y,
-                double *dy);
-void orc_rhs(const orc_cosmo *c, const orc_opts *o, double k, double lna,
-             const double *y, double *dy);
-void orc_initial(const orc_cosmo *c, const orc_opts *o, double k, double lna_i,
-                 double *y);
-int orc_solve_mode(const orc_cosmo *c, const orc_opts *o, double k,
-                   const double *lna_out, int n_out, double *y_out,
-                   const double *y_init, double lna_init, long *n_steps);
-int orc_sources_mode(const orc_cosmo *c, const orc_opts *o, double k,
-                     double *S /* [n_tau][3] */, long *n_steps);
+int orc_schedule_count(const orc_cosmo *c, const orc_opts *o, real_t k, real_t x0, real_t x1);
+void orc_rhs_bg(const orc_opts *o, const orc_bg *b, real_t k, const real_t *y,
+                real_t *dy);
+void orc_rhs(const orc_cosmo *c, const orc_opts *o, real_t k, real_t lna,
+             const real_t *y, real_t *dy);
+void orc_initial(const orc_cosmo *c, const orc_opts *o, real_t k, real_t lna_i,
+                 real_t *y);
+int orc_solve_mode(const orc_cosmo *c, const orc_opts *o, real_t k,
+                   const real_t *lna_out, int n_out, real_t *y_out,
+                   const real_t *y_init, real_t lna_init, long *n_steps);
+int orc_sources_mode(const orc_cosmo *c, const orc_opts *o, real_t k,
+                     real_t *S /* [n_tau][3] */, long *n_steps);
 
 /* orc_spectra.c */
-void orc_bessel_all(int lmax, double x, double *j /* [lmax+1] */);
+void orc_bessel_all(int lmax, real_t x, real_t *j /* [lmax+1] */);
 
 #endif

@@ -16,7 +16,7 @@
 
 #include "orc.h"
 
-int orc_lu_factor(double *A, int n, int *piv, int *ext)
+int orc_lu_factor(real_t *A, int n, int *piv, int *ext)
 {
     int *rend = ext, *lbeg = ext + n;
     for (int i = 0; i < n; i++) {
@@ -27,25 +27,25 @@ int orc_lu_factor(double *A, int n, int *piv, int *ext)
     }
     for (int k = 0; k < n; k++) {
         int p = k;
-        double best = fabs(A[k * n + k]);
+        real_t best = ABS(A[k * n + k]);
         for (int i = k + 1; i < n; i++)
-            if (fabs(A[i * n + k]) > best) { best = fabs(A[i * n + k]); p = i; }
+            if (RE(ABS(A[i * n + k])) > RE(best)) { best = ABS(A[i * n + k]); p = i; }
         piv[k] = p;
         if (best == 0.0) return -1;
         if (p != k) {
             const int j0 = lbeg[k] < lbeg[p] ? lbeg[k] : lbeg[p];
             const int j1 = rend[k] > rend[p] ? rend[k] : rend[p];
             for (int j = j0; j <= j1; j++) {
-                double t = A[k * n + j]; A[k * n + j] = A[p * n + j]; A[p * n + j] = t;
+                real_t t = A[k * n + j]; A[k * n + j] = A[p * n + j]; A[p * n + j] = t;
             }
             int t = rend[k]; rend[k] = rend[p]; rend[p] = t;
             t = lbeg[k]; lbeg[k] = lbeg[p]; lbeg[p] = t;
         }
-        const double inv = 1.0 / A[k * n + k];
+        const real_t inv = 1.0 / A[k * n + k];
         const int jend = rend[k];
         for (int i = k + 1; i < n; i++) {
             if (A[i * n + k] == 0.0) continue;
-            const double l = A[i * n + k] * inv;
+            const real_t l = A[i * n + k] * inv;
             A[i * n + k] = l;
             if (k < lbeg[i]) lbeg[i] = k;
             for (int j = k + 1; j <= jend; j++) A[i * n + j] -= l * A[k * n + j];
@@ -55,20 +55,20 @@ int orc_lu_factor(double *A, int n, int *piv, int *ext)
     return 0;
 }
 
-void orc_lu_solve(const double *A, int n, const int *piv, const int *ext, double *b)
+void orc_lu_solve(const real_t *A, int n, const int *piv, const int *ext, real_t *b)
 {
     const int *rend = ext, *lbeg = ext + n;
     for (int k = 0; k < n; k++) {
         int p = piv[k];
-        if (p != k) { double t = b[k]; b[k] = b[p]; b[p] = t; }
+        if (p != k) { real_t t = b[k]; b[k] = b[p]; b[p] = t; }
     }
     for (int i = 0; i < n; i++) {
-        double s = b[i];
+        real_t s = b[i];
         for (int j = lbeg[i]; j < i; j++) s -= A[i * n + j] * b[j];
         b[i] = s;
     }
     for (int i = n - 1; i >= 0; i--) {
-        double s = b[i];
+        real_t s = b[i];
         for (int j = i + 1; j <= rend[i]; j++) s -= A[i * n + j] * b[j];
         b[i] = s / A[i * n + i];
     }

@@ -32,80 +32,80 @@
 
 #define S_PI 3.14159265358979323846
 
-static double j1_of(double x)
+static real_t j1_of(real_t x)
 {
-    if (x < 0.5) { /* Taylor series; term ratio -x^2 / ((2n+2)(2n+5)) */
-        double x2 = x * x;
+    if (RE(x) < 0.5) { /* Taylor series; term ratio -x^2 / ((2n+2)(2n+5)) */
+        real_t x2 = x * x;
         return x / 3.0 * (1.0 - x2 / 10.0 * (1.0 - x2 / 28.0 * (1.0 - x2 / 54.0 * (1.0 - x2 / 88.0 * (1.0 - x2 / 130.0 * (1.0 - x2 / 180.0))))));
     }
     return sin(x) / (x * x) - cos(x) / x;
 }
 
-static double j0_of(double x)
+static real_t j0_of(real_t x)
 {
-    if (x < 1e-4) return 1.0 - x * x / 6.0;
+    if (RE(x) < 1e-4) return 1.0 - x * x / 6.0;
     return sin(x) / x;
 }
 
-void orc_bessel_all(int lmax, double x, double *j)
+void orc_bessel_all(int lmax, real_t x, real_t *j)
 {
-    memset(j, 0, sizeof(double) * (lmax + 1));
+    memset(j, 0, sizeof(real_t) * (lmax + 1));
     if (x == 0.0) { j[0] = 1.0; return; }
-    double j0 = j0_of(x), j1 = j1_of(x);
-    if (x > lmax) {
+    real_t j0 = j0_of(x), j1 = j1_of(x);
+    if (RE(x) > lmax) {
         j[0] = j0;
         if (lmax >= 1) j[1] = j1;
         for (int l = 1; l < lmax; l++) j[l + 1] = (2.0 * l + 1.0) / x * j[l] - j[l - 1];
         return;
     }
-    int ls = (int)ceil(x + 20.0 + 15.0 * cbrt(x));
+    int ls = (int)ceil(RE(x) + 20.0 + 15.0 * cbrt(RE(x)));
     int lcap = lmax + 30 + (int)sqrt(40.0 * lmax);
     if (ls > lcap) ls = lcap;
-    double jp = 0.0, jc = 1e-250;
+    real_t jp = 0.0, jc = 1e-250;
     for (int l = ls; l >= 1; l--) {
         /* jc = j_l (unnormalised), jp = j_{l+1} */
         if (l <= lmax) j[l] = jc;
-        double jm = (2.0 * l + 1.0) / x * jc - jp;
+        real_t jm = (2.0 * l + 1.0) / x * jc - jp;
         jp = jc;
         jc = jm;
-        if (fabs(jc) > 1e200) {
+        if (RE(ABS(jc)) > 1e200) {
             jc *= 1e-200; jp *= 1e-200;
             int top = ls < lmax ? ls : lmax;
             for (int m = l; m <= top; m++) j[m] *= 1e-200;
         }
     }
     j[0] = jc;
-    double scale = (fabs(j0) >= fabs(j1)) ? j0 / j[0] : j1 / j[1];
+    real_t scale = (RE(ABS(j0)) >= RE(ABS(j1))) ? j0 / j[0] : j1 / j[1];
     for (int l = 0; l <= lmax; l++) j[l] *= scale;
 }
 
 /* ------------------------------------------------------------------ */
-static void neumaier_add(double *sum, double *comp, double v)
+static void neumaier_add(real_t *sum, real_t *comp, real_t v)
 {
-    double t = *sum + v;
-    if (fabs(*sum) >= fabs(v)) *comp += (*sum - t) + v;
+    real_t t = *sum + v;
+    if (RE(ABS(*sum)) >= RE(ABS(v))) *comp += (*sum - t) + v;
     else *comp += (v - t) + *sum;
     *sum = t;
 }
 
 /* Project one k mode: S [n_tau][3] -> Delta [lmax-1][2] (l = 2..lmax). */
-static void project_mode(int n_tau, const double *tau, const double *w, double tau0,
-                         double k, const double *S, int lmax, double scale_pol,
-                         double *Delta, double *jbuf, double *acc)
+static void project_mode(int n_tau, const real_t *tau, const real_t *w, real_t tau0,
+                         real_t k, const real_t *S, int lmax, real_t scale_pol,
+                         real_t *Delta, real_t *jbuf, real_t *acc)
 {
     int nl = lmax - 1;
-    memset(acc, 0, sizeof(double) * 4 * nl);
+    memset(acc, 0, sizeof(real_t) * 4 * nl);
     for (int i = 0; i < n_tau; i++) {
-        double x = k * (tau0 - tau[i]);
+        real_t x = k * (tau0 - tau[i]);
         orc_bessel_all(lmax, x, jbuf);
-        double s0 = S[3 * i], s1 = S[3 * i + 1], sp = S[3 * i + 2];
+        real_t s0 = S[3 * i], s1 = S[3 * i + 1], sp = S[3 * i + 2];
         for (int l = 2; l <= lmax; l++) {
-            double jl = jbuf[l];
-            double jp = jbuf[l - 1] - (l + 1.0) * jl / x;
-            double jpp = -2.0 / x * jp - (1.0 - l * (l + 1.0) / (x * x)) * jl;
-            double dT = w[i] * (s0 * jl + s1 * jp + scale_pol * sp * 0.5 * (3.0 * jpp + jl));
-            double cE = sqrt(3.0 * (l + 2.0) * (l + 1.0) * l * (l - 1.0) / 8.0);
-            double dE = w[i] * sqrt(6.0) * sp * cE * jl / (x * x);
+            real_t jl = jbuf[l];
+            real_t jp = jbuf[l - 1] - (l + 1.0) * jl / x;
+            real_t jpp = -2.0 / x * jp - (1.0 - l * (l + 1.0) / (x * x)) * jl;
+            real_t dT = w[i] * (s0 * jl + s1 * jp + scale_pol * sp * 0.5 * (3.0 * jpp + jl));
+            real_t cE = sqrt(3.0 * (l + 2.0) * (l + 1.0) * l * (l - 1.0) / 8.0);
+            real_t dE = w[i] * sqrt(6.0) * sp * cE * jl / (x * x);
             int q = l - 2;
             neumaier_add(&acc[4 * q], &acc[4 * q + 1], dT);
             neumaier_add(&acc[4 * q + 2], &acc[4 * q + 3], dE);
@@ -138,11 +138,11 @@ static void set_threads(int nthreads)
 
 /* Scalars: [H0, Om_b, Om_c, Om_g, Om_nu, Om_L, R_nu, f_He, nH0, A_s, z_reion,
              lna_tc, lna_sw, tau0, lna_He3, n_s, Om_ncdm] */
-int orc_scalars(const double *p, int hooks, double m_ncdm, double *out)
+int orc_scalars(const real_t *p, int hooks, double m_ncdm, real_t *out)
 {
     orc_cosmo c;
     if (orc_cosmo_init(&c, p, 0, hooks, m_ncdm, 0)) return -1;
-    double v[17] = {c.H0, c.Om_b, c.Om_c, c.Om_g, c.Om_nu, c.Om_L, c.R_nu, c.f_He,
+    real_t v[17] = {c.H0, c.Om_b, c.Om_c, c.Om_g, c.Om_nu, c.Om_L, c.R_nu, c.f_He,
                     c.nH0, c.A_s, c.z_reion, c.lna_tc, c.lna_sw, c.tau0, c.lna_He3, c.n_s, c.Om_ncdm};
     memcpy(out, v, sizeof(v));
     orc_cosmo_free(&c);
@@ -151,14 +151,14 @@ int orc_scalars(const double *p, int hooks, double m_ncdm, double *out)
 
 /* Background at points: out[n][18] = [a, Hc, dHc, fc, fb, fg, fnu, tau, xe,
    dxe, nuT, Rinv, cs2, kappa, g, dg, fncdm, wncdm] */
-int orc_background(const double *p, int hooks, double m_ncdm, const double *lna, int n, double *out)
+int orc_background(const real_t *p, int hooks, double m_ncdm, const real_t *lna, int n, real_t *out)
 {
     orc_cosmo c;
     if (orc_cosmo_init(&c, p, 0, hooks, m_ncdm, 0)) return -1;
     for (int i = 0; i < n; i++) {
         orc_bg b;
         orc_bg_eval(&c, lna[i], &b, 2);
-        double v[18] = {b.a, b.Hc, b.dHc, b.fc, b.fb, b.fg, b.fnu, b.tau, b.xe, b.dxe,
+        real_t v[18] = {b.a, b.Hc, b.dHc, b.fc, b.fb, b.fg, b.fnu, b.tau, b.xe, b.dxe,
                         b.nuT, b.Rinv, b.cs2, b.kappa, b.g, b.dg, b.fncdm, b.wncdm};
         memcpy(out + 18 * i, v, sizeof(v));
     }
@@ -169,14 +169,14 @@ int orc_background(const double *p, int hooks, double m_ncdm, const double *lna,
 /* tau nodes: out[3][n_tau] = lna, tau, w */
 /* Thermal history at ln a[n]: out[n][4] = matter temperature T_m [eV],
    d ln T_m / d ln a, x_e, baryon sound speed c_s^2 (App. B.1.2, App. C.3). */
-int orc_thermo(const double *p, const double *lna, int n, double *out)
+int orc_thermo(const real_t *p, const real_t *lna, int n, real_t *out)
 {
     orc_cosmo c;
     if (orc_cosmo_init(&c, p, 0, 0, 0.0, 0)) return -1;
     for (int i = 0; i < n; i++) {
         orc_bg b;
         orc_bg_eval(&c, lna[i], &b, 1);
-        double dlnTm;
+        real_t dlnTm;
         out[4 * i] = orc_Tm_of_lna(&c, lna[i], &dlnTm);
         out[4 * i + 1] = dlnTm;
         out[4 * i + 2] = b.xe;
@@ -186,13 +186,13 @@ int orc_thermo(const double *p, const double *lna, int n, double *out)
     return 0;
 }
 
-int orc_nodes(const double *p, int n_tau, double m_ncdm, int node_recipe, double *out)
+int orc_nodes(const real_t *p, int n_tau, double m_ncdm, int node_recipe, real_t *out)
 {
     orc_cosmo c;
     if (orc_cosmo_init(&c, p, n_tau, 0, m_ncdm, node_recipe)) return -1;
-    memcpy(out, c.node_lna, sizeof(double) * n_tau);
-    memcpy(out + n_tau, c.node_tau, sizeof(double) * n_tau);
-    memcpy(out + 2 * n_tau, c.node_w, sizeof(double) * n_tau);
+    memcpy(out, c.node_lna, sizeof(real_t) * n_tau);
+    memcpy(out + n_tau, c.node_tau, sizeof(real_t) * n_tau);
+    memcpy(out + 2 * n_tau, c.node_w, sizeof(real_t) * n_tau);
     orc_cosmo_free(&c);
     return 0;
 }
@@ -204,18 +204,18 @@ int orc_nstate_of(const double *oa)
     return orc_nstate(&o);
 }
 
-double orc_lna_start_of(const double *p, double k, double m_ncdm)
+real_t orc_lna_start_of(const real_t *p, real_t k, double m_ncdm)
 {
     orc_cosmo c;
     if (orc_cosmo_init(&c, p, 0, 0, m_ncdm, 0)) return NAN;
-    double v = orc_lna_start(&c, k);
+    real_t v = orc_lna_start(&c, k);
     orc_cosmo_free(&c);
     return v;
 }
 
 /* Trajectory of one mode at ascending ln a points (y_init may be NULL). */
-int orc_trajectory(const double *p, const double *oa, double k, const double *lna_out,
-                   int n, double *y_out, const double *y_init, double lna_init, long *steps)
+int orc_trajectory(const real_t *p, const double *oa, real_t k, const real_t *lna_out,
+                   int n, real_t *y_out, const real_t *y_init, real_t lna_init, long *steps)
 {
     orc_cosmo c;
     orc_opts o;
@@ -227,7 +227,7 @@ int orc_trajectory(const double *p, const double *oa, double k, const double *ln
 }
 
 /* Right-hand side at one point (for consistency pins). */
-int orc_rhs_at(const double *p, const double *oa, double k, double lna, const double *y, double *dy)
+int orc_rhs_at(const real_t *p, const double *oa, real_t k, real_t lna, const real_t *y, real_t *dy)
 {
     orc_cosmo c;
     orc_opts o;
@@ -238,19 +238,19 @@ int orc_rhs_at(const double *p, const double *oa, double k, double lna, const do
     return 0;
 }
 
-void orc_bessel(int lmax, double x, double *out) { orc_bessel_all(lmax, x, out); }
+void orc_bessel(int lmax, real_t x, real_t *out) { orc_bessel_all(lmax, x, out); }
 
 /* Project given sources (synthetic ones in the pins) on given nodes. */
-int orc_project(int n_tau, const double *tau, const double *w, double tau0,
-                const double *k, int nk, const double *S, int lmax, double scale_pol,
-                double *Delta, int nthreads)
+int orc_project(int n_tau, const real_t *tau, const real_t *w, real_t tau0,
+                const real_t *k, int nk, const real_t *S, int lmax, real_t scale_pol,
+                real_t *Delta, int nthreads)
 {
     set_threads(nthreads);
     int nl = lmax - 1;
 #pragma omp parallel
     {
-        double *jbuf = (double *)malloc(sizeof(double) * (lmax + 1));
-        double *acc = (double *)malloc(sizeof(double) * 4 * nl);
+        real_t *jbuf = (real_t *)malloc(sizeof(real_t) * (lmax + 1));
+        real_t *acc = (real_t *)malloc(sizeof(real_t) * 4 * nl);
 #pragma omp for schedule(dynamic, 1)
         for (int ik = 0; ik < nk; ik++)
             project_mode(n_tau, tau, w, tau0, k[ik], S + (size_t)ik * n_tau * 3, lmax,
@@ -262,22 +262,22 @@ int orc_project(int n_tau, const double *tau, const double *w, double tau0,
 }
 
 /* C_ell from Delta[nk][lmax-1][2]: Cl[3][lmax-1] = TT, TE, EE */
-int orc_cl(const double *k, int nk, const double *Delta, int lmax, double A_s, double n_s,
-           double k_pivot, double *Cl)
+int orc_cl(const real_t *k, int nk, const real_t *Delta, int lmax, real_t A_s, real_t n_s,
+           real_t k_pivot, real_t *Cl)
 {
     int nl = lmax - 1;
-    double *wk = (double *)malloc(sizeof(double) * nk);
+    real_t *wk = (real_t *)malloc(sizeof(real_t) * nk);
     for (int i = 0; i < nk; i++) {
-        double lo = i > 0 ? log(k[i - 1]) : log(k[i]);
-        double hi = i < nk - 1 ? log(k[i + 1]) : log(k[i]);
+        real_t lo = i > 0 ? log(k[i - 1]) : log(k[i]);
+        real_t hi = i < nk - 1 ? log(k[i + 1]) : log(k[i]);
         wk[i] = 0.5 * (hi - lo);
     }
     for (int q = 0; q < nl; q++) {
-        double s[3] = {0, 0, 0}, cmp[3] = {0, 0, 0};
+        real_t s[3] = {0, 0, 0}, cmp[3] = {0, 0, 0};
         for (int i = 0; i < nk; i++) {
-            double P = A_s * pow(k[i] / k_pivot, n_s - 1.0);
-            double dT = Delta[((size_t)i * nl + q) * 2], dE = Delta[((size_t)i * nl + q) * 2 + 1];
-            double f = 4.0 * S_PI * wk[i] * P;
+            real_t P = A_s * pow(k[i] / k_pivot, n_s - 1.0);
+            real_t dT = Delta[((size_t)i * nl + q) * 2], dE = Delta[((size_t)i * nl + q) * 2 + 1];
+            real_t f = 4.0 * S_PI * wk[i] * P;
             neumaier_add(&s[0], &cmp[0], f * dT * dT);
             neumaier_add(&s[1], &cmp[1], f * dT * dE);
             neumaier_add(&s[2], &cmp[2], f * dE * dE);
@@ -291,8 +291,8 @@ int orc_cl(const double *k, int nk, const double *Delta, int lmax, double A_s, d
 /* Whole path for one cosmology. Any output pointer may be NULL.
    S_out [nk][n_tau][3], Delta_out [nk][lmax-1][2], Cl_out [3][lmax-1],
    steps_out [nk]. */
-int orc_run(const double *p, int n_tau, const double *oa, const double *k, int nk,
-            int lmax_cl, double *S_out, double *Delta_out, double *Cl_out,
+int orc_run(const real_t *p, int n_tau, const double *oa, const real_t *k, int nk,
+            int lmax_cl, real_t *S_out, real_t *Delta_out, real_t *Cl_out,
             long *steps_out, int nthreads)
 {
     orc_cosmo c;
@@ -300,7 +300,7 @@ int orc_run(const double *p, int n_tau, const double *oa, const double *k, int n
     opts_from(oa, &o);
     if (orc_cosmo_init(&c, p, n_tau, o.hooks & ORC_HOOK_EDS_CDM, o.m_ncdm, o.node_recipe)) return -1;
     set_threads(nthreads);
-    double *S = S_out ? S_out : (double *)malloc(sizeof(double) * (size_t)nk * n_tau * 3);
+    real_t *S = S_out ? S_out : (real_t *)malloc(sizeof(real_t) * (size_t)nk * n_tau * 3);
     int rc = 0;
     /* highest k first: the most expensive modes start earliest */
 #pragma omp parallel for schedule(dynamic, 1) reduction(| : rc)
@@ -312,7 +312,7 @@ int orc_run(const double *p, int n_tau, const double *oa, const double *k, int n
     }
     if (rc == 0 && (Delta_out || Cl_out)) {
         int nl = lmax_cl - 1;
-        double *D = Delta_out ? Delta_out : (double *)malloc(sizeof(double) * (size_t)nk * nl * 2);
+        real_t *D = Delta_out ? Delta_out : (real_t *)malloc(sizeof(real_t) * (size_t)nk * nl * 2);
         orc_project(n_tau, c.node_tau, c.node_w, c.tau0, k, nk, S, lmax_cl, o.scale_pol, D, nthreads);
         if (Cl_out) orc_cl(k, nk, D, lmax_cl, c.A_s, c.n_s, c.k_pivot, Cl_out);
         if (!Delta_out) free(D);
@@ -323,7 +323,7 @@ int orc_run(const double *p, int n_tau, const double *oa, const double *k, int n
 }
 
 /* Handle-based access for tests that call the right-hand side many times. */
-void *orc_create(const double *p, int n_tau, int hooks, double m_ncdm)
+void *orc_create(const real_t *p, int n_tau, int hooks, double m_ncdm)
 {
     orc_cosmo *c = (orc_cosmo *)malloc(sizeof(orc_cosmo));
     if (orc_cosmo_init(c, p, n_tau, hooks, m_ncdm, 0)) { orc_cosmo_free(c); free(c); return NULL; }
@@ -335,7 +335,7 @@ void orc_destroy(void *h)
     if (h) { orc_cosmo_free((orc_cosmo *)h); free(h); }
 }
 
-int orc_h_rhs(void *h, const double *oa, double k, double lna, const double *y, double *dy)
+int orc_h_rhs(void *h, const double *oa, real_t k, real_t lna, const real_t *y, real_t *dy)
 {
     orc_opts o;
     opts_from(oa, &o);
@@ -344,14 +344,14 @@ int orc_h_rhs(void *h, const double *oa, double k, double lna, const double *y, 
 }
 
 /* dense A(ln a) [N][N] */
-int orc_h_matrix(void *h, const double *oa, double k, double lna, double *A)
+int orc_h_matrix(void *h, const double *oa, real_t k, real_t lna, real_t *A)
 {
     orc_opts o;
     opts_from(oa, &o);
     int N = orc_nstate(&o);
     orc_bg b;
     orc_bg_eval((orc_cosmo *)h, lna, &b, 1);
-    double *e = (double *)calloc(N, sizeof(double)), *col = (double *)malloc(sizeof(double) * N);
+    real_t *e = (real_t *)calloc(N, sizeof(real_t)), *col = (real_t *)malloc(sizeof(real_t) * N);
     for (int j = 0; j < N; j++) {
         e[j] = 1.0;
         orc_rhs_bg(&o, &b, k, e, col);
@@ -364,7 +364,7 @@ int orc_h_matrix(void *h, const double *oa, double k, double lna, double *A)
 }
 
 /* LU solve of a dense system (pins the factorisation against a library solve) */
-int orc_dense_solve(double *A, int n, double *b)
+int orc_dense_solve(real_t *A, int n, real_t *b)
 {
     int *piv = (int *)malloc(sizeof(int) * n), *ext = (int *)malloc(sizeof(int) * 2 * n);
     int rc = orc_lu_factor(A, n, piv, ext);
@@ -375,7 +375,7 @@ int orc_dense_solve(double *A, int n, double *b)
 }
 
 /* Adiabatic initial state of the oracle at a given ln a. */
-int orc_initial_at(const double *p, const double *oa, double k, double lna, double *y)
+int orc_initial_at(const real_t *p, const double *oa, real_t k, real_t lna, real_t *y)
 {
     orc_cosmo c;
     orc_opts o;
@@ -387,17 +387,17 @@ int orc_initial_at(const double *p, const double *oa, double k, double lna, doub
 }
 
 /* Steps the oracle's schedule takes for each k mode over the tau nodes. */
-int orc_count_steps(const double *p, int n_tau, const double *oa, const double *k, int nk, long *out)
+int orc_count_steps(const real_t *p, int n_tau, const double *oa, const real_t *k, int nk, long *out)
 {
     orc_cosmo c;
     orc_opts o;
     opts_from(oa, &o);
     if (orc_cosmo_init(&c, p, n_tau, 0, o.m_ncdm, o.node_recipe)) return -1;
     for (int i = 0; i < nk; i++) {
-        double x = orc_lna_start(&c, k[i]);
+        real_t x = orc_lna_start(&c, k[i]);
         long n = 0;
         for (int j = 0; j < n_tau; j++) {
-            if (c.node_lna[j] > x) { n += orc_schedule_count(&c, &o, k[i], x, c.node_lna[j]); x = c.node_lna[j]; }
+            if (RE(c.node_lna[j]) > RE(x)) { n += orc_schedule_count(&c, &o, k[i], x, c.node_lna[j]); x = c.node_lna[j]; }
         }
         out[i] = n;
     }
@@ -412,14 +412,14 @@ int orc_count_steps(const double *p, int n_tau, const double *oa, const double *
    baryons here; photons and massless neutrinos are relativistic), with
    delta_c, delta_b (state entries 1 and 2) from the mode integrated from its
    adiabatic start to ln a = -ln(1 + z) on the oracle's step schedule. */
-int orc_pk(const double *p, const double *oa, const double *k, int nk, double z, double *Pk, int nthreads)
+int orc_pk(const real_t *p, const double *oa, const real_t *k, int nk, double z, real_t *Pk, int nthreads)
 {
     orc_cosmo c;
     orc_opts o;
     opts_from(oa, &o);
     if (orc_cosmo_init(&c, p, 0, o.hooks & ORC_HOOK_EDS_CDM, o.m_ncdm, 0)) return -1;
     set_threads(nthreads);
-    const double lna = -log1p(z);
+    const real_t lna = -log1p(z);
     orc_bg b;
     orc_bg_eval(&c, lna, &b, 0);
     const int N = orc_nstate(&o);
@@ -427,15 +427,15 @@ int orc_pk(const double *p, const double *oa, const double *k, int nk, double z,
 #pragma omp parallel for schedule(dynamic, 1) reduction(| : rc)
     for (int t = 0; t < nk; t++) {
         int ik = nk - 1 - t;
-        double *y = (double *)malloc(sizeof(double) * N);
+        real_t *y = (real_t *)malloc(sizeof(real_t) * N);
         long st = 0;
-        if (orc_lna_start(&c, k[ik]) >= lna) {
+        if (RE(orc_lna_start(&c, k[ik])) >= RE(lna)) {
             rc |= 2; /* the mode starts after the requested time */
             Pk[ik] = NAN;
         } else {
             rc |= orc_solve_mode(&c, &o, k[ik], &lna, 1, y, NULL, 0.0, &st);
-            const double dm = (b.fc * y[1] + b.fb * y[2]) / (b.fc + b.fb);
-            const double kk = k[ik];
+            const real_t dm = (b.fc * y[1] + b.fb * y[2]) / (b.fc + b.fb);
+            const real_t kk = k[ik];
             Pk[ik] = 2.0 * S_PI * S_PI / (kk * kk * kk) * c.A_s * pow(kk / c.k_pivot, c.n_s - 1.0) * dm * dm;
         }
         free(y);
@@ -448,7 +448,7 @@ int orc_pk(const double *p, const double *oa, const double *k, int nk, double z,
    over CDM, baryons and (when present) the massive neutrino, at every tau
    node, for each k: out[nk][n_tau] (App. B.4 eq. PK's bracket; inputs of the
    lensing potential, App. B.5). */
-int orc_delta_m_nodes(const double *p, int n_tau, const double *oa, const double *k, int nk, double *out,
+int orc_delta_m_nodes(const real_t *p, int n_tau, const double *oa, const real_t *k, int nk, real_t *out,
                       int nthreads)
 {
     orc_cosmo c;
@@ -461,21 +461,21 @@ int orc_delta_m_nodes(const double *p, int n_tau, const double *oa, const double
 #pragma omp parallel for schedule(dynamic, 1) reduction(| : rc)
     for (int t = 0; t < nk; t++) {
         int ik = nk - 1 - t;
-        double *Y = (double *)malloc(sizeof(double) * (size_t)n_tau * N);
+        real_t *Y = (real_t *)malloc(sizeof(real_t) * (size_t)n_tau * N);
         long st = 0;
         rc |= orc_solve_mode(&c, &o, k[ik], c.node_lna, n_tau, Y, NULL, 0.0, &st);
         for (int i = 0; i < n_tau; i++) {
             orc_bg b;
             orc_bg_eval(&c, c.node_lna[i], &b, 0);
-            const double *y = Y + (size_t)i * N;
-            double num = b.fc * y[1] + b.fb * y[2], den = b.fc + b.fb;
+            const real_t *y = Y + (size_t)i * N;
+            real_t num = b.fc * y[1] + b.fb * y[2], den = b.fc + b.fb;
             if (o.lmax_ncdm > 0) {
                 /* the massive neutrino's delta rho / rho_tot from its momentum bins */
-                const double q[3] = {0.913201, 3.37517, 7.79184}, K[3] = {0.0687359, 3.31435, 2.29911};
+                const real_t q[3] = {0.913201, 3.37517, 7.79184}, K[3] = {0.0687359, 3.31435, 2.29911};
                 const int i0 = orc_nstate(&o) - 3 * (o.lmax_ncdm + 1);
-                double drho = 0.0;
+                real_t drho = 0.0;
                 for (int j = 0; j < 3; j++) {
-                    const double eps = sqrt(q[j] * q[j] + b.ncdm_x * b.ncdm_x);
+                    const real_t eps = sqrt(q[j] * q[j] + b.ncdm_x * b.ncdm_x);
                     drho += K[j] * (1.0 + exp(-q[j])) * eps / (q[j] * q[j]) * y[i0 + j * (o.lmax_ncdm + 1)];
                 }
                 num += b.ncdm_n * drho;
