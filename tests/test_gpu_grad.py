@@ -1,9 +1,11 @@
 """The hand-written adjoint (ClWithGradient): Cbar . dC_l/dtheta for the six
 parameters, against central differences of the same forward (relative step
-1e-4), against the oracle's derivatives (tests/golden/grad_oracle_*.npz,
-written by tests/golden/make_grad_reference.py from the oracle alone:
-Richardson-extrapolated central differences), and the taped forward against
-the plain pipeline.
+1e-4), against the oracle's forward sensitivities (tests/golden/
+grad_forward_*.npz: the whole oracle run in complex arithmetic, one run per
+parameter, exact to rounding) and its Richardson-extrapolated central
+differences (tests/golden/grad_oracle_*.npz), both written by
+tests/golden/make_grad_reference.py from the oracle alone, and the taped
+forward against the plain pipeline.
 
 The contraction weights are Cbar_l = z_l / |C_l| with z_l ~ N(0, 1), so every
 l counts alike.  The ODE runs at rtol 1e-9: adaptive step decisions that flip
@@ -79,14 +81,15 @@ def test_adjoint_against_differences_of_the_same_forward(A, case):
         assert np.all(err <= 1e-4 * np.abs(fd).max()), (b, g[b], fd, err)
 
 
-def oracle_reference(case_name):
-    g = np.load(os.path.join(GOLDEN, f"grad_oracle_{case_name}.npz"))
+def oracle_reference(case_name, forward=False):
+    g = np.load(os.path.join(GOLDEN, f"grad_{'forward' if forward else 'oracle'}_{case_name}.npz"))
     np.testing.assert_array_equal(g["params"], W.BATCH16_GRAD.params()[0])
     return g
 
 
-def test_adjoint_against_the_oracle_derivatives(A, case):
-    g = oracle_reference("small")
+@pytest.mark.parametrize("forward", [True, False])
+def test_adjoint_against_the_oracle_derivatives(A, case, forward):
+    g = oracle_reference("small", forward)
     assert int(g["l_hier"]) == L_HIER and int(g["n_tau"]) == N_TAU and int(g["lmax_cl"]) == LMAX_CL
     np.testing.assert_allclose(g["k"], case["k"].cpu().numpy(), rtol=1e-15)
     Cbar, grad = case["Cbar"][0], case["grad"][0]
@@ -97,8 +100,12 @@ def test_adjoint_against_the_oracle_derivatives(A, case):
 
 def test_adjoint_at_hierarchy_30_to_l_2500_and_k_0p5_against_the_oracle(A):
     """The differentiation workload's grids (hierarchies 30, 6000 tau nodes,
-    l <= 2500) on 12 k reaching 0.5 /Mpc, one cosmology."""
-    g = oracle_reference("full")
+    l <= 2500) on 12 k reaching 0.5 /Mpc, one cosmology, against the oracle's
+    forward sensitivities.  (Its Richardson differences are not used here:
+    the oracle's fixed step schedule changes its step count between nodes as
+    theta moves, and those jumps put the differences 1.13e-4 of the largest
+    component off the forward sensitivity in the omega_cdm contraction.)"""
+    g = oracle_reference("full", forward=True)
     o = A.options(lmax_hier=int(g["l_hier"]), n_tau=int(g["n_tau"]), lmax_cl=int(g["lmax_cl"]), rtol=1e-9,
                   atol=1e-15)
     k = torch.tensor(g["k"], device="cuda")
@@ -111,12 +118,7 @@ def test_adjoint_at_hierarchy_30_to_l_2500_and_k_0p5_against_the_oracle(A):
     grad = p.grad.cpu().numpy()[0]
     ref = np.array([np.sum(Cbar * g["dCl"][j]) for j in range(6)])
     err = np.abs(grad - ref)
-    # measured on a GB300: five components within 6e-6 of the largest, the
-    # omega_cdm one at 1.13e-4, from l >= 1000 (EE 5e-5, TT and TE 2e-5 of
-    # those multipoles' own sums), where differences of the same forward agree
-    # with the oracle to 5e-6; the bar keeps that known deviation in view
-    assert np.all(err <= 2e-4 * np.abs(ref).max()), (grad, ref, err)
-    assert np.sum(err > 1e-5 * np.abs(ref).max()) <= 1, (grad, ref, err)
+    assert np.all(err <= 1e-4 * np.abs(ref).max()), (grad, ref, err)
     # and the forward itself against the oracle's C_l
     assert np.max(np.abs(Cn[0] - g["Cl"][0]) / np.abs(g["Cl"][0])) < 1e-5
 
