@@ -465,6 +465,8 @@ def main():
                     help="cosmologies per step (default: the workload's); smaller cases are for profiling")
     ap.add_argument("--n-k", type=int, default=None,
                     help="k modes (default: the workload's), log-spaced over the workload's range")
+    ap.add_argument("--k-range", type=float, nargs=2, default=None, metavar=("K_MIN", "K_MAX"),
+                    help="override the workload's k range (profiling cases; with --n-k 1, k = K_MAX alone)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="mixed: FP64 ODE, FP32 projection and k-quadrature with Kahan sums")
     ap.add_argument("--serve", action="store_true",
@@ -515,7 +517,13 @@ def main():
     wl = W.WORKLOADS[args.workload]
     B = args.batch or wl.n_cosmo
     params = rank_params(wl, B, rank)
-    k = W.log_k_nodes(args.n_k, wl.k_min, wl.k_max) if args.n_k else wl.k()
+    k_min, k_max = args.k_range if args.k_range else (wl.k_min, wl.k_max)
+    if args.n_k == 1:
+        k = np.array([k_max])
+    elif args.n_k or args.k_range:
+        k = W.log_k_nodes(args.n_k or wl.n_k, k_min, k_max)
+    else:
+        k = wl.k()
     o = A.options(lmax_hier=wl.l_max_hier, lmax_cl=wl.l_max_cl, n_tau=wl.n_tau, rtol=args.rtol,
                   node_recipe=args.node_recipe)
     N = 4 + 3 * (wl.l_max_hier + 1)
@@ -621,7 +629,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "spectra/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64+f32" if mixed else "f64", "data": "synthetic",
-        "config": {"workload": wl.name, "batch": B, "n_k": len(k), "k_range": [wl.k_min, wl.k_max],
+        "config": {"workload": wl.name, "batch": B, "n_k": len(k), "k_range": [float(k[0]), float(k[-1])],
                    "lmax_cl": wl.l_max_cl, "hierarchy_lmax": wl.l_max_hier, "n_tau": wl.n_tau,
                    "rtol": args.rtol, "precision": args.precision, "node_recipe": args.node_recipe,
                    "l2": "flushed (512 MiB write) between timed steps",

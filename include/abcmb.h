@@ -108,8 +108,14 @@ size_t abcmb_bg_doubles(const abcmb_options *o);
             d/dln a) pairs per node read by the ODE kernel: 1/H, 1/(H tau),
             f_c, f_b, f_gamma, f_nu (rho_i / rho_tot), 1/(H tau_c),
             (4 rho_g / 3 rho_b) / (H tau_c), c_s^2, H (all conformal)
-     then 8 columns per tau node (n_tau nodes): ln a, tau, trapezoid weight,
-            g, dg/dln a, e^-kappa, conformal H, dH/dln a                     */
+     [ABCMB_BG_NODES, + 8 * n_tau) 8 columns per tau node: ln a, tau,
+            trapezoid weight, g, dg/dln a, e^-kappa, conformal H, dH/dln a
+     [ABCMB_BG_NODES + 8 * n_tau, + ABCMB_BG_ODEPOLY_DOUBLES) the ODE table
+            again, as the cubic Hermite polynomial of each interval: for
+            interval j (ln a_j to ln a_j+1) and each of its 10 quantities in
+            the order above, c0..c3 of c0 + u (c1 + u (c2 + u c3)), u the
+            fraction of the interval (the form the four-lane ODE kernel reads)
+   The whole record is ABCMB_BG_LEN(n_tau) doubles (abcmb_bg_doubles).      */
 #define ABCMB_BG_NSCALAR 64
 #define ABCMB_BG_PER_UNIT 1024
 #define ABCMB_BG_LNA0 (-18.0)
@@ -117,6 +123,9 @@ size_t abcmb_bg_doubles(const abcmb_options *o);
 #define ABCMB_BG_TABLE ABCMB_BG_NSCALAR
 #define ABCMB_BG_ODETAB (ABCMB_BG_TABLE + 8 * ABCMB_BG_NLNA)
 #define ABCMB_BG_NODES (ABCMB_BG_ODETAB + 20 * ABCMB_BG_NLNA)
+#define ABCMB_BG_ODEPOLY_DOUBLES (40L * (ABCMB_BG_NLNA - 1))
+#define ABCMB_BG_ODEPOLY(n_tau) (ABCMB_BG_NODES + 8L * (n_tau))
+#define ABCMB_BG_LEN(n_tau) (ABCMB_BG_ODEPOLY(n_tau) + ABCMB_BG_ODEPOLY_DOUBLES)
 
 enum {
     ABCMB_S_STATUS = 0, ABCMB_S_H0, ABCMB_S_OMB, ABCMB_S_OMC, ABCMB_S_OMG, ABCMB_S_OMNU,

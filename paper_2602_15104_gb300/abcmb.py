@@ -31,6 +31,7 @@ BG_NLNA = 18 * 1024 + 1
 BG_TABLE = BG_NSCALAR
 BG_ODETAB = BG_TABLE + 8 * BG_NLNA
 BG_NODES = BG_ODETAB + 20 * BG_NLNA
+BG_ODEPOLY_DOUBLES = 40 * (BG_NLNA - 1)  # the ODE table as per-interval cubics, after the nodes
 S_INDEX = dict(STATUS=0, H0=1, OMB=2, OMC=3, OMG=4, OMNU=5, OML=6, RNU=7, FHE=8, NH0=9, AS=10,
                NS=11, ZREION=12, LNA_TC=13, LNA_SW=14, TAU0=15, LNA_HE3=16, LNA_700=17, NTAU=18)
 TABLE_COLUMNS = ("nuT", "dnuT", "tau", "dtau", "cs2", "dcs2", "kappa", "xe")

@@ -786,6 +786,23 @@ ABCMB_HD void build_background(const double *p, double *rec, int n_tau, int lane
         o[18] = b.Hc;
         o[19] = b.Hc * b.dlnHc;
     }
+    lane_sync();
+    // the same table as one cubic per interval: the Hermite cubic of values
+    // v0, v1 and slopes (per interval) d0, d1 is v0 + u (d0 + u (3 (v1 - v0)
+    // - 2 d0 - d1 + u (d0 + d1 - 2 (v1 - v0))))
+    double *opoly = rec + ABCMB_BG_ODEPOLY(n_tau);
+    for (int j = lane; j < kNlna - 1; j += nl) {
+        const double *o0 = otab + 20 * j, *o1 = o0 + 20;
+        double *pc = opoly + 40 * j;
+        for (int q = 0; q < 10; q++) {
+            const double v0 = o0[2 * q], v1 = o1[2 * q];
+            const double d0 = kDlna * o0[2 * q + 1], d1 = kDlna * o1[2 * q + 1], dv = v1 - v0;
+            pc[4 * q] = v0;
+            pc[4 * q + 1] = d0;
+            pc[4 * q + 2] = 3.0 * dv - 2.0 * d0 - d1;
+            pc[4 * q + 3] = d0 + d1 - 2.0 * dv;
+        }
+    }
 
     // tight-coupling start: H tau_c = R_tc (every lane, identically)
     c.lna_tc = bisect([&](double l) { Herm H = herm_at(l); return -herm_val(tab, H, C_NUT, C_DNUT); },

@@ -422,7 +422,7 @@ size_t perturb_warp_bytes(int B, int Nk, const abcmb_options *o)
 int launch_perturb_warp(int B, const double *bg, const double *k, int Nk, const abcmb_options *o, double *S,
                         int *mode_status, int *steps, double *work, cudaStream_t s)
 {
-    const long len = (long)ABCMB_BG_NODES + 8L * o->n_tau, M = (long)B * Nk;
+    const long len = (long)ABCMB_BG_LEN(o->n_tau), M = (long)B * Nk;
     const long blocks = (M * 32 + adj::kGradThreads - 1) / adj::kGradThreads;
     if (blocks > 2147483647L) return ABCMB_E_INVALID_ARG;
     adj::plain_kernel<<<(unsigned)blocks, adj::kGradThreads, 0, s>>>(

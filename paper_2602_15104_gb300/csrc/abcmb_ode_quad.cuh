@@ -67,58 +67,58 @@ struct QBg {
     double ih, iht, fc, fb, fg, fnu, nu, rnu, cs2, hc;
 };
 
-// cubic Hermite weights on the uniform ln a grid, derivative weights scaled by the spacing
-struct QHerm {
+// position on the uniform ln a grid: interval j and fraction u of it
+struct QPos {
     int j;
-    double w0, w1, d0, d1;
+    double u;
 };
 
-__device__ __forceinline__ QHerm qherm(double lna)
+__device__ __forceinline__ QPos qpos(double lna)
 {
-    const double t = (lna - kLna0) * ABCMB_BG_PER_UNIT;
+    // (ln a - ln a_0) per unit spacing; scaling by the power of two is exact,
+    // so the single rounding of the fma equals that of the subtraction
+    const double t = fma(lna, (double)ABCMB_BG_PER_UNIT, -kLna0 * ABCMB_BG_PER_UNIT);
     int j = (int)t; // t >= 0 on the table (ln a >= -18): truncation is floor
     j = j < 0 ? 0 : (j > kNlna - 2 ? kNlna - 2 : j);
-    const double u = t - (double)j, um = 1.0 - u, um2 = um * um;
-    QHerm H;
-    H.j = j;
-    H.w0 = fma(u + u, um2, um2); // (1 + 2u)(1 - u)^2
-    H.w1 = 1.0 - H.w0;           // u^2 (3 - 2u)
-    H.d0 = kDlna * u * um2;      // u (1 - u)^2
-    H.d1 = -kDlna * u * u * um;  // u^2 (u - 1)
-    return H;
+    QPos X;
+    X.j = j;
+    X.u = t - (double)j;
+    return X;
 }
 
-__device__ __forceinline__ double ocol(const double *ot, const QHerm &H, int c)
+// ODE-table quantity c at X: the cubic of its interval from the record's
+// polynomial section op (abcmb.h), three FMAs
+__device__ __forceinline__ double pcol(const double *op, const QPos &X, int c)
 {
-    const double *r0 = ot + kOStride * H.j + 2 * c, *r1 = r0 + kOStride;
-    return fma(H.w0, r0[0], fma(H.w1, r1[0], fma(H.d0, r0[1], H.d1 * r1[1])));
+    const double *pc = op + 40 * X.j + 4 * c;
+    return fma(fma(fma(pc[3], X.u, pc[2]), X.u, pc[1]), X.u, pc[0]);
 }
 
 // all ten quantities, interpolated by one lane (used for the sources)
-__device__ __forceinline__ QBg obg_all(const double *ot, double lna)
+__device__ __forceinline__ QBg obg_all(const double *op, double lna)
 {
-    const QHerm H = qherm(lna);
+    const QPos X = qpos(lna);
     QBg b;
-    b.ih = ocol(ot, H, O_IH);
-    b.iht = ocol(ot, H, O_IHT);
-    b.fc = ocol(ot, H, O_FC);
-    b.fb = ocol(ot, H, O_FB);
-    b.fg = ocol(ot, H, O_FG);
-    b.fnu = ocol(ot, H, O_FNU);
-    b.nu = ocol(ot, H, O_NU);
-    b.rnu = ocol(ot, H, O_RNU);
-    b.cs2 = ocol(ot, H, O_CS2);
-    b.hc = ocol(ot, H, O_HC);
+    b.ih = pcol(op, X, O_IH);
+    b.iht = pcol(op, X, O_IHT);
+    b.fc = pcol(op, X, O_FC);
+    b.fb = pcol(op, X, O_FB);
+    b.fg = pcol(op, X, O_FG);
+    b.fnu = pcol(op, X, O_FNU);
+    b.nu = pcol(op, X, O_NU);
+    b.rnu = pcol(op, X, O_RNU);
+    b.cs2 = pcol(op, X, O_CS2);
+    b.hc = pcol(op, X, O_HC);
     return b;
 }
 
 // split over the quad and broadcast
-__device__ __forceinline__ QBg qbg(const double *ot, double lna, int q, int qb)
+__device__ __forceinline__ QBg qbg(const double *op, double lna, int q, int qb)
 {
-    const QHerm H = qherm(lna);
-    const double v0 = ocol(ot, H, q);
-    const double v1 = ocol(ot, H, q + 4);
-    const double v2 = ocol(ot, H, O_CS2 + (q & 1));
+    const QPos X = qpos(lna);
+    const double v0 = pcol(op, X, q);
+    const double v1 = pcol(op, X, q + 4);
+    const double v2 = pcol(op, X, O_CS2 + (q & 1));
     QBg b;
     b.ih = __shfl_sync(kFull, v0, qb);
     b.iht = __shfl_sync(kFull, v0, qb + 1);
@@ -184,6 +184,44 @@ constexpr NevTab make_nev()
 }
 
 __constant__ NevTab c_nev = make_nev();
+
+// The same extrapolations as explicit linear combinations of a step's column
+// values z_1..z_j (z_i from n_i substeps): the value extrapolated to h = 0
+// through points 1..j is sum_i lam[j][i] z_i (Lagrange weights at 0 in x = h
+// for the implicit sequence n_i = i, x = h^2 for the Gragg sequence n_i = 2i),
+// and the error estimate, that value minus the one through points 2..j, is
+// sum_i mu[j][i] z_i.  A column then costs j + 1 operations per element for
+// its error and j for the accepted value, against 2j for Aitken-Neville's
+// recursion; the weights are at most a few hundred in size, so rounding
+// stays ~1e-13 of the state.
+struct ExtTab {
+    double lam[2][kQK + 1][kQK + 1], mu[2][kQK + 1][kQK + 1]; // [0: implicit, 1: Gragg][j][i]
+};
+
+constexpr double ext_x(int g, int i) { return g ? 1.0 / (4.0 * i * i) : 1.0 / i; }
+
+// Lagrange weight at 0 of point i among points a..b
+constexpr double ext_lagrange0(int g, int a, int b, int i)
+{
+    double w = 1.0;
+    for (int k = a; k <= b; k++)
+        if (k != i) w *= ext_x(g, k) / (ext_x(g, k) - ext_x(g, i));
+    return w;
+}
+
+constexpr ExtTab make_ext()
+{
+    ExtTab t{};
+    for (int g = 0; g < 2; g++)
+        for (int j = 1; j <= kQK; j++)
+            for (int i = 1; i <= j; i++) {
+                t.lam[g][j][i] = ext_lagrange0(g, 1, j, i);
+                t.mu[g][j][i] = t.lam[g][j][i] - (i >= 2 ? ext_lagrange0(g, 2, j, i) : 0.0);
+            }
+    return t;
+}
+
+__constant__ ExtTab c_ext = make_ext();
 
 // per-mode constants
 struct QMode {
@@ -353,10 +391,10 @@ constexpr int kSrcComp = 12;
 
 // Sources at a tau node from the state components v (kSrcComp values, order
 // above; moments rescaled, u_l = F_l / s_l).
-__device__ __forceinline__ void q_sources_v(const double *ot, const double *nd, double k, const double sw[3],
+__device__ __forceinline__ void q_sources_v(const double *op, const double *nd, double k, const double sw[3],
                                             const double (&v)[kSrcComp], double *S)
 {
-    const QBg b = obg_all(ot, nd[N_LNA]);
+    const QBg b = obg_all(op, nd[N_LNA]);
     const double Hc = nd[N_HC], dHc = nd[N_DHC], g = nd[N_G], dg = nd[N_DG], emk = nd[N_EXPMK];
     const double kH = k / Hc, k2 = k * k;
     const double eta = v[8], dc = v[9], db = v[10], tb = v[11];
@@ -387,7 +425,7 @@ __device__ __forceinline__ int src_elem(int c)
 
 // Sources at a tau node from the accepted state in shared memory (lane 0).
 template <int P>
-__device__ __forceinline__ void q_sources(const double *ot, const double *nd, double k, const double sw[3],
+__device__ __forceinline__ void q_sources(const double *op, const double *nd, double k, const double sw[3],
                                           const double *Y, const double sc[4], double *S)
 {
     double v[kSrcComp];
@@ -395,7 +433,7 @@ __device__ __forceinline__ void q_sources(const double *ot, const double *nd, do
     for (int c = 0; c < 8; c++) v[c] = Y[src_elem<P>(c) * 32];
 #pragma unroll
     for (int s = 0; s < 4; s++) v[8 + s] = sc[s];
-    q_sources_v(ot, nd, k, sw, v, S);
+    q_sources_v(op, nd, k, sw, v, S);
 }
 
 // scalar q of four (eta, delta_c, delta_b, theta_b): this lane's share of the scalar row
@@ -423,19 +461,19 @@ __device__ __forceinline__ double quad_max(double v)
 // Matter power spectrum (App. B.4, eq. PK) from the scalars sc (eta, delta_c,
 // delta_b, theta_b) at ln a = lna: P = (2 pi^2 / k^3) A_s (k/k_pivot)^(n_s-1)
 // delta_m^2, delta_m = (rho_c delta_c + rho_b delta_b) / (rho_c + rho_b).
-__device__ __forceinline__ double q_matter_pk(const double *ot, const double *rec, double lna, double k,
+__device__ __forceinline__ double q_matter_pk(const double *op, const double *rec, double lna, double k,
                                               const double sc[4])
 {
-    const QBg b = obg_all(ot, lna);
+    const QBg b = obg_all(op, lna);
     const double dm = (b.fc * sc[1] + b.fb * sc[2]) / (b.fc + b.fb);
     const double As = rec[ABCMB_S_AS], ns = rec[ABCMB_S_NS];
     return 2.0 * kPi * kPi / (k * k * k) * As * exp((ns - 1.0) * log(k / kKpivot)) * dm * dm;
 }
 
 // density-weighted CDM + baryon contrast at ln a (App. B.4 eq. PK's bracket)
-__device__ __forceinline__ double q_delta_m(const double *ot, double lna, double dc, double db)
+__device__ __forceinline__ double q_delta_m(const double *op, double lna, double dc, double db)
 {
-    const QBg b = obg_all(ot, lna);
+    const QBg b = obg_all(op, lna);
     return (b.fc * dc + b.fb * db) / (b.fc + b.fb);
 }
 
@@ -552,6 +590,7 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
     const double *rec = bg + (long)b * len;
     const double *tab = rec + ABCMB_BG_TABLE;
     const double *ot = rec + ABCMB_BG_ODETAB;
+    const double *op = rec + ABCMB_BG_ODEPOLY((long)rec[ABCMB_S_NTAU]);
     const double *nodes = rec + ABCMB_BG_NODES;
     const int n_tau = PK ? 1 : (int)rec[ABCMB_S_NTAU];
     QMode md;
@@ -660,7 +699,7 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
         double xn = x, H = 0.0;
         bool land = false, emit = false, capped = false;
         int dmode = 0; // 0: none or landing on one node, 1: linear, 2: Hermite dense output
-        const QBg bx = qbg(ot, x, q, qb);
+        const QBg bx = qbg(op, x, q, qb);
         if (stepping) {
             xn = PK ? x_out : nodes[8 * node + N_LNA];
             H = h;
@@ -751,10 +790,10 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
             }
             if (!gbs) {
                 const double hs = H * c_nev.inv[j];
-                QBg bc = qbg(ot, x, q, qb);
+                QBg bc = qbg(op, x, q, qb);
                 for (int m = 0; m < j; m++) {
                     const double xm = m == j - 1 ? x + H : x + (m + 1) * hs;
-                    const QBg bn = qbg(ot, xm, q, qb);
+                    const QBg bn = qbg(op, xm, q, qb);
                     q_imex<P>(z, zs, bc, bn, md, hs, q, qb, qc);
                     bc = bn;
                 }
@@ -768,19 +807,22 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
                     for (int p = 0; p < P; p++) w[ch][p] = z[ch][p];
 #pragma unroll
                 for (int s = 0; s < 4; s++) ws[s] = zs[s];
-                q_rhs_axpy<P>(z, zs, w, ws, qbg(ot, x, q, qb), md, hs, q, qb, qc); // w = z1
+                q_rhs_axpy<P>(z, zs, w, ws, qbg(op, x, q, qb), md, hs, q, qb, qc); // w = z1
                 for (int m = 1; m < n; m += 2) {
-                    const QBg bm = qbg(ot, x + m * hs, q, qb);
+                    const QBg bm = qbg(op, x + m * hs, q, qb);
                     q_rhs_axpy<P>(w, ws, z, zs, bm, md, 2.0 * hs, q, qb, qc); // z = z_{m+1}
                     if (m + 1 < n) {
-                        const QBg bm1 = qbg(ot, x + (m + 1) * hs, q, qb);
+                        const QBg bm1 = qbg(op, x + (m + 1) * hs, q, qb);
                         q_rhs_axpy<P>(z, zs, w, ws, bm1, md, 2.0 * hs, q, qb, qc);
                     }
                 }
                 if (open) nsub += n;
             }
-            // Aitken-Neville update of the tableau and the error estimate
-            const double *cf = gbs ? c_nev.gbs[j] : c_nev.imex[j];
+            // column j's value is the j-th point of the extrapolation: kept in
+            // slot j - 1 (the last slot holds the inverse error scales, and
+            // the last column's value stays in registers); error estimate
+            // sum_i mu[j][i] z_i (see ExtTab)
+            const double *mw = c_ext.mu[gbs ? 1 : 0][j];
             // max of the scaled errors on the high words of their bit patterns:
             // integer work, monotone for non-negative doubles, NaN on top, exact to 2^-20
             int elh = 0;
@@ -788,25 +830,16 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
             for (int e = 0; e < E; e++) {
                 const int ch = e < 3 * P ? e / P : 3;
                 const int p = e - ch * P;
-                double cur = ch < 3 ? z[ch][p] : pick4(zs, q);
-                const double is = T(kQK - 1, e);
-                double lower = cur;
-                double prev = T(0, e);
-                T(0, e) = cur;
-#pragma unroll
-                for (int s = 1; s < kQK; s++) {
-                    if (s < j) {
-                        const double nw = fma(cur - prev, cf[s], cur);
-                        prev = T(s, e);
-                        T(s, e) = nw;
-                        lower = cur;
-                        cur = nw;
-                    }
-                }
+                const double cur = ch < 3 ? z[ch][p] : pick4(zs, q);
                 if (j >= 2) {
-                    const double er = fabs(cur - lower) * is;
-                    elh = max(elh, __double2hiint(fabs(er)));
+                    double d = mw[j] * cur;
+#pragma unroll
+                    for (int i = 1; i < kQK; i++)
+                        if (i < j) d = fma(mw[i], T(i - 1, e), d);
+                    const double er = fabs(d) * T(kQK - 1, e);
+                    elh = max(elh, __double2hiint(er));
                 }
+                if (j < kQK) T(j - 1, e) = cur;
             }
             elh = max(elh, __shfl_xor_sync(kFull, elh, 1));
             elh = max(elh, __shfl_xor_sync(kFull, elh, 2));
@@ -821,8 +854,18 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
                 } else if (el <= 1.0) {
                     jacc = j;
                     open = false;
+                    // accepted value sum_i lam[j][i] z_i, z_j from registers
+                    const double *lw = c_ext.lam[gbs ? 1 : 0][j];
 #pragma unroll
-                    for (int e = 0; e < E; e++) Y(e) = T(j - 1, e);
+                    for (int e = 0; e < E; e++) {
+                        const int ch = e < 3 * P ? e / P : 3;
+                        const int p = e - ch * P;
+                        double v = lw[j] * (ch < 3 ? z[ch][p] : pick4(zs, q));
+#pragma unroll
+                        for (int i = 1; i < kQK; i++)
+                            if (i < j) v = fma(lw[i], T(i - 1, e), v);
+                        Y(e) = v;
+                    }
                 }
             }
         }
@@ -855,7 +898,7 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
                 for (int p = 0; p < P; p++) z[ch][p] = Y(ch * P + p);
             load_scalars(zs, Y(3 * P), qb);
             q_zero<P>(w, ws);
-            q_rhs_axpy<P>(z, zs, w, ws, qbg(ot, x, q, qb), md, 1.0, q, qb, qc);
+            q_rhs_axpy<P>(z, zs, w, ws, qbg(op, x, q, qb), md, 1.0, q, qb, qc);
             if (pend && dmode == 2) {
                 q_store_src<P>(dq + 2 * kSrcComp, w, ws, q);
                 nsub++;
@@ -871,8 +914,8 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
                     const double th = fmin((nodes[8 * i + N_LNA] - x0) * iH, 1.0);
                     double v[kSrcComp];
                     q_dense<P>(v, dq, smw + qb, th, x - x0, dmode == 2);
-                    if (DM) Sm[i] = q_delta_m(ot, nodes[8 * i + N_LNA], v[9], v[10]);
-                    else q_sources_v(ot, nodes + 8 * i, k, sw, v, Sm + 3 * i);
+                    if (DM) Sm[i] = q_delta_m(op, nodes[8 * i + N_LNA], v[9], v[10]);
+                    else q_sources_v(op, nodes + 8 * i, k, sw, v, Sm + 3 * i);
                 }
                 const int cnt = __popc((__ballot_sync(kFull, mine) >> qb) & 0xFu);
                 if (pend) {
@@ -898,9 +941,9 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
             load_scalars(sc, Y(3 * P), qb); // the accepted scalars, one per quad lane
             if (emit) {
                 if (q == 0) {
-                    if (PK) pk_out[(long)b * Nk + kidx] = q_matter_pk(ot, rec, x_out, k, sc);
-                    else if (DM) Sm[node] = q_delta_m(ot, nodes[8 * node + N_LNA], sc[1], sc[2]);
-                    else q_sources<P>(ot, nodes + 8 * node, k, sw, sl, sc, Sm + 3 * node);
+                    if (PK) pk_out[(long)b * Nk + kidx] = q_matter_pk(op, rec, x_out, k, sc);
+                    else if (DM) Sm[node] = q_delta_m(op, nodes[8 * node + N_LNA], sc[1], sc[2]);
+                    else q_sources<P>(op, nodes + 8 * node, k, sw, sl, sc, Sm + 3 * node);
                 }
                 node++;
                 if (node >= n_tau) done = true;

@@ -94,7 +94,7 @@ static int launch_quad(int B, const double *bg, const double *k, int Nk, const a
     const long M = (long)B * Nk;
     const long blocks = (M + 8 * W - 1) / (8 * W);
     if (blocks > 2147483647L) return ABCMB_E_INVALID_ARG;
-    const long len = (long)ABCMB_BG_NODES + 8L * o->n_tau;
+    const long len = (long)ABCMB_BG_LEN(o->n_tau);
     kern<<<(unsigned)blocks, 32 * W, smem, s>>>(B, Nk, bg, len, k, o->lmax_g, o->lmax_pol, o->lmax_nu, o->rtol,
                                                  o->atol, o->max_steps, o->scale_sw, o->scale_isw, o->scale_dop, S,
                                                  st, steps);
@@ -113,7 +113,7 @@ static int perturb_on_chip(int B, const double *bg, const double *k, int Nk, con
 static int perturb_in_workspace(int B, const double *bg, const double *k, int Nk, const abcmb_options *o,
                                 double *S, int *st, int *steps, double *work, cudaStream_t s)
 {
-    const long len = (long)ABCMB_BG_NODES + 8L * o->n_tau;
+    const long len = (long)ABCMB_BG_LEN(o->n_tau);
     const long M = (long)B * Nk;
     const int threads = 64;
     const long blocks = (M + threads - 1) / threads;
@@ -176,7 +176,7 @@ static int launch_pk(int B, const double *bg, const double *k, int Nk, const abc
     if ((long)smem > avail) return ABCMB_E_INVALID_ARG;
     const long blocks = ((long)B * Nk + 7) / 8;
     if (blocks > 2147483647L) return ABCMB_E_INVALID_ARG;
-    const long len = (long)ABCMB_BG_NODES + 8L * o->n_tau;
+    const long len = (long)ABCMB_BG_LEN(o->n_tau);
     kern<<<(unsigned)blocks, 32, smem, s>>>(B, Nk, bg, len, k, o->lmax_g, o->lmax_pol, o->lmax_nu, o->rtol, o->atol,
                                             o->max_steps, x_out, Pk, st, steps);
     return cudaGetLastError() == cudaSuccess ? ABCMB_OK : ABCMB_E_CUDA;
@@ -211,7 +211,7 @@ static int launch_dm(int B, const double *bg, const double *k, int Nk, const abc
     if ((long)smem > avail) return ABCMB_E_INVALID_ARG;
     const long blocks = ((long)B * Nk + 7) / 8;
     if (blocks > 2147483647L) return ABCMB_E_INVALID_ARG;
-    const long len = (long)ABCMB_BG_NODES + 8L * o->n_tau;
+    const long len = (long)ABCMB_BG_LEN(o->n_tau);
     kern<<<(unsigned)blocks, 32, smem, s>>>(B, Nk, bg, len, k, o->lmax_g, o->lmax_pol, o->lmax_nu, o->rtol, o->atol,
                                             o->max_steps, Dm, st);
     return cudaGetLastError() == cudaSuccess ? ABCMB_OK : ABCMB_E_CUDA;
@@ -235,7 +235,7 @@ extern "C" int abcmb_delta_m_nodes(int B, const double *bg, const double *k, int
 extern "C" size_t abcmb_bg_doubles(const abcmb_options *o)
 {
     if (abcmb_validate_options(o) != ABCMB_OK) return 0;
-    return (size_t)ABCMB_BG_NODES + 8 * (size_t)o->n_tau;
+    return (size_t)ABCMB_BG_LEN(o->n_tau);
 }
 
 extern "C" size_t abcmb_perturb_workspace_bytes(int B, int Nk, const abcmb_options *o)

@@ -41,7 +41,7 @@ void setup(Run &R, const double *rec, double k, int L)
 }
 } // namespace
 
-extern "C" long h_bg_len(int n_tau) { return ABCMB_BG_NODES + 8L * n_tau; }
+extern "C" long h_bg_len(int n_tau) { return ABCMB_BG_LEN(n_tau); }
 extern "C" void h_build_bg(const double *p, int n_tau, double *rec) { build_background(p, rec, n_tau, 0, 1); }
 
 // sig[0..2]: accepted steps, steps tried, and the sum of the accepted steps'

@@ -8,7 +8,7 @@
 using namespace abcmb;
 using namespace abcmb::adj;
 
-extern "C" long h_bg_len(int n_tau) { return ABCMB_BG_NODES + 8L * n_tau; }
+extern "C" long h_bg_len(int n_tau) { return ABCMB_BG_LEN(n_tau); }
 
 extern "C" void h_build_bg_m(const double *p, int n_tau, double m_ncdm, double *rec)
 {

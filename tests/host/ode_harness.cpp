@@ -6,7 +6,7 @@
 
 using namespace abcmb;
 
-extern "C" long h_bg_len(int n_tau) { return ABCMB_BG_NODES + 8L * n_tau; }
+extern "C" long h_bg_len(int n_tau) { return ABCMB_BG_LEN(n_tau); }
 
 extern "C" void h_build_bg(const double *p, int n_tau, double *rec) { build_background(p, rec, n_tau, 0, 1); }
 

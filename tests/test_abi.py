@@ -43,7 +43,7 @@ def test_defaults_and_sizes(A):
     L.abcmb_default_options(ctypes.byref(o))
     assert (o.lmax_g, o.lmax_cl, o.n_tau, o.node_recipe) == (12, 2500, 6000, 0)
     assert L.abcmb_validate_options(ctypes.byref(A.options(node_recipe=1))) == A.OK
-    assert A.bg_doubles(o) == A.BG_NODES + 8 * o.n_tau
+    assert A.bg_doubles(o) == A.BG_NODES + 8 * o.n_tau + A.BG_ODEPOLY_DOUBLES
     # hierarchies <= 63 keep the ODE state on chip: no workspace
     assert A.perturb_workspace_bytes(64, 400, o) == 0
     assert A.perturb_workspace_bytes(64, 400, A.options(lmax_hier=63)) == 0

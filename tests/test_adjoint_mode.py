@@ -94,7 +94,7 @@ def test_mode_gradient_against_finite_differences(H, rec, k, node):
     _, acc0 = phi(rec)
     rb = np.zeros_like(rec)
     assert H.h_grad(ptr(rec), k, L, rtol, ptr(Sb), ptr(rb)) == 0
-    regions = [(64 + 8 * 18433, 64 + 28 * 18433), (64 + 28 * 18433, rec.size)]  # ODE table, node data
+    regions = [(64 + 8 * 18433, 64 + 28 * 18433), (64 + 28 * 18433, 64 + 28 * 18433 + 8 * n_tau)]  # ODE table, nodes
     checked = 0
     for a, b in regions:
         for e in a + np.argsort(-np.abs(rb[a:b] * rec[a:b]))[:6]:

@@ -95,3 +95,28 @@ def test_nodes_of_small_and_ragged_counts(H, n_tau, recipe):
     assert np.all(np.diff(nodes[:, 1]) > 0) and nodes[-1, 1] < O.scalars(p)["tau0"]
     np.testing.assert_allclose(nodes[:, 0], lna, rtol=0, atol=1e-9)
     np.testing.assert_allclose(nodes[:, 2], w, rtol=1e-8)
+
+
+def test_ode_table_cubics_are_the_hermite_interpolants(H):
+    # the record's polynomial section (read by the four-lane ODE kernel) holds,
+    # per interval and quantity, the cubic Hermite interpolant of the (value,
+    # d/dln a) pairs of the ODE table: compare at points inside intervals
+    from paper_2602_15104_gb300 import abcmb as A
+    n_tau = 400
+    r = record(H, W.BATCH64.params()[5], n_tau)
+    assert r.size == A.BG_NODES + 8 * n_tau + A.BG_ODEPOLY_DOUBLES
+    pairs = r[A.BG_ODETAB:A.BG_NODES].reshape(A.BG_NLNA, 10, 2)
+    poly = r[A.BG_NODES + 8 * n_tau:].reshape(A.BG_NLNA - 1, 10, 4)
+    rng = np.random.default_rng(2)
+    dx = 1.0 / 1024
+    for j in np.concatenate([[0, A.BG_NLNA - 2], rng.integers(0, A.BG_NLNA - 1, 200)]):
+        for u in (0.0, 0.31, 0.77, 1.0):
+            h00, h10 = (1 + 2 * u) * (1 - u) ** 2, u * (1 - u) ** 2
+            h01, h11 = u * u * (3 - 2 * u), u * u * (u - 1)
+            v0, d0 = pairs[j, :, 0], pairs[j, :, 1]
+            v1, d1 = pairs[j + 1, :, 0], pairs[j + 1, :, 1]
+            herm = h00 * v0 + h10 * dx * d0 + h01 * v1 + h11 * dx * d1
+            c = poly[j]
+            cub = c[:, 0] + u * (c[:, 1] + u * (c[:, 2] + u * c[:, 3]))
+            scale = np.maximum(np.abs(v0), np.abs(v1))
+            assert np.all(np.abs(cub - herm) <= 2e-15 * scale + 1e-300), (j, u)
