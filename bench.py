@@ -473,6 +473,8 @@ def main():
                     help="serving benchmark: Poisson arrivals of mixed-size requests through abcmb_server")
     ap.add_argument("--grad", action="store_true",
                     help="gradient benchmark: dC_l/dtheta of a batch through the hand-written adjoint")
+    ap.add_argument("--n-wide", type=int, default=0,
+                    help="modes of the n highest k on eight lanes (abcmb_options.n_wide)")
     ap.add_argument("--node-recipe", type=int, default=0, choices=[0, 1],
                     help="tau-node placement: 0 the default, 1 the refined visibility tail")
     ap.add_argument("--variants", action="store_true",
@@ -525,7 +527,7 @@ def main():
     else:
         k = wl.k()
     o = A.options(lmax_hier=wl.l_max_hier, lmax_cl=wl.l_max_cl, n_tau=wl.n_tau, rtol=args.rtol,
-                  node_recipe=args.node_recipe)
+                  node_recipe=args.node_recipe, n_wide=args.n_wide)
     N = 4 + 3 * (wl.l_max_hier + 1)
     mixed = args.precision == "mixed"
     pipe = A.Pipeline(B, k, o, mixed=mixed)
@@ -632,6 +634,7 @@ def main():
         "config": {"workload": wl.name, "batch": B, "n_k": len(k), "k_range": [float(k[0]), float(k[-1])],
                    "lmax_cl": wl.l_max_cl, "hierarchy_lmax": wl.l_max_hier, "n_tau": wl.n_tau,
                    "rtol": args.rtol, "precision": args.precision, "node_recipe": args.node_recipe,
+                   "n_wide": args.n_wide,
                    "l2": "flushed (512 MiB write) between timed steps",
                    "parallelism": f"replicas x{world}"},
         "clocks": clk,

@@ -82,6 +82,13 @@ typedef struct {
                         1 = 1/5, 2/5 over [1300, 900), 1/5 uniform in z over [900, 300),
                         the rest uniform in tau from z = 300, which resolves the tail of
                         the visibility function (low-l TT converges with ~10x fewer nodes) */
+    int n_wide;      /* abcmb_perturb with hierarchies 16..63: the modes of the n_wide largest k
+                        (k ascending in the array) run on eight lanes each instead of four: the
+                        same arithmetic per mode, a shorter chain of work per step for the most
+                        expensive modes (a mode's result depends on its warp-mates only through
+                        the warp-wide switch to the explicit regime, within the ODE tolerance);
+                        0: none (the default: on the 64-cosmology, 400 k workload 12, 25 and
+                        50 wide k gave no gain); must be >= 0                              */
 } abcmb_options;
 
 /* Fill *o with the defaults used by the library's tests: hierarchies 12,

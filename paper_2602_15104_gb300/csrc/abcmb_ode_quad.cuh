@@ -112,24 +112,42 @@ __device__ __forceinline__ QBg obg_all(const double *op, double lna)
     return b;
 }
 
-// split over the quad and broadcast
+// split over the lanes of a mode and broadcast: with four lanes, lane q
+// interpolates columns q, q + 4 and 8 + (q & 1); with eight, columns q and
+// 8 + (q & 1)
+template <int LQ = 4>
 __device__ __forceinline__ QBg qbg(const double *op, double lna, int q, int qb)
 {
     const QPos X = qpos(lna);
-    const double v0 = pcol(op, X, q);
-    const double v1 = pcol(op, X, q + 4);
-    const double v2 = pcol(op, X, O_CS2 + (q & 1));
     QBg b;
-    b.ih = __shfl_sync(kFull, v0, qb);
-    b.iht = __shfl_sync(kFull, v0, qb + 1);
-    b.fc = __shfl_sync(kFull, v0, qb + 2);
-    b.fb = __shfl_sync(kFull, v0, qb + 3);
-    b.fg = __shfl_sync(kFull, v1, qb);
-    b.fnu = __shfl_sync(kFull, v1, qb + 1);
-    b.nu = __shfl_sync(kFull, v1, qb + 2);
-    b.rnu = __shfl_sync(kFull, v1, qb + 3);
-    b.cs2 = __shfl_sync(kFull, v2, qb);
-    b.hc = __shfl_sync(kFull, v2, qb + 1);
+    if (LQ == 8) {
+        const double v0 = pcol(op, X, q);
+        const double v1 = pcol(op, X, O_CS2 + (q & 1));
+        b.ih = __shfl_sync(kFull, v0, qb);
+        b.iht = __shfl_sync(kFull, v0, qb + 1);
+        b.fc = __shfl_sync(kFull, v0, qb + 2);
+        b.fb = __shfl_sync(kFull, v0, qb + 3);
+        b.fg = __shfl_sync(kFull, v0, qb + 4);
+        b.fnu = __shfl_sync(kFull, v0, qb + 5);
+        b.nu = __shfl_sync(kFull, v0, qb + 6);
+        b.rnu = __shfl_sync(kFull, v0, qb + 7);
+        b.cs2 = __shfl_sync(kFull, v1, qb);
+        b.hc = __shfl_sync(kFull, v1, qb + 1);
+    } else {
+        const double v0 = pcol(op, X, q);
+        const double v1 = pcol(op, X, q + 4);
+        const double v2 = pcol(op, X, O_CS2 + (q & 1));
+        b.ih = __shfl_sync(kFull, v0, qb);
+        b.iht = __shfl_sync(kFull, v0, qb + 1);
+        b.fc = __shfl_sync(kFull, v0, qb + 2);
+        b.fb = __shfl_sync(kFull, v0, qb + 3);
+        b.fg = __shfl_sync(kFull, v1, qb);
+        b.fnu = __shfl_sync(kFull, v1, qb + 1);
+        b.nu = __shfl_sync(kFull, v1, qb + 2);
+        b.rnu = __shfl_sync(kFull, v1, qb + 3);
+        b.cs2 = __shfl_sync(kFull, v2, qb);
+        b.hc = __shfl_sync(kFull, v2, qb + 1);
+    }
     return b;
 }
 
@@ -260,7 +278,7 @@ __device__ __forceinline__ void put_L(double (&v)[P], int q, int L, double x)
 }
 
 // one linearly implicit Euler substep (see imex_substep), in place
-template <int P>
+template <int P, int LQ = 4>
 __device__ __forceinline__ void q_imex(double (&z)[3][P], double (&zs)[4], const QBg &bc, const QBg &bn,
                                        const QMode &m, double hs, int q, int qb, const QCoef &qc)
 {
@@ -269,8 +287,8 @@ __device__ __forceinline__ void q_imex(double (&z)[3][P], double (&zs)[4], const
     double lft[3], rgt[3];
 #pragma unroll
     for (int ch = 0; ch < 3; ch++) {
-        lft[ch] = __shfl_up_sync(kFull, z[ch][P - 1], 1, 4);
-        rgt[ch] = __shfl_down_sync(kFull, z[ch][0], 1, 4);
+        lft[ch] = __shfl_up_sync(kFull, z[ch][P - 1], 1, LQ);
+        rgt[ch] = __shfl_down_sync(kFull, z[ch][0], 1, LQ);
     }
     // scalars, explicit
     {
@@ -333,7 +351,7 @@ __device__ __forceinline__ void q_imex(double (&z)[3][P], double (&zs)[4], const
 }
 
 // dst += fac f(src), everything explicit (see rhs_axpy)
-template <int P>
+template <int P, int LQ = 4>
 __device__ __forceinline__ void q_rhs_axpy(const double (&s)[3][P], const double (&ss)[4], double (&d)[3][P],
                                            double (&ds)[4], const QBg &b, const QMode &m, double fac, int q,
                                            int qb, const QCoef &qc)
@@ -343,8 +361,8 @@ __device__ __forceinline__ void q_rhs_axpy(const double (&s)[3][P], const double
     double lft[3], rgt[3];
 #pragma unroll
     for (int ch = 0; ch < 3; ch++) {
-        lft[ch] = __shfl_up_sync(kFull, s[ch][P - 1], 1, 4);
-        rgt[ch] = __shfl_down_sync(kFull, s[ch][0], 1, 4);
+        lft[ch] = __shfl_up_sync(kFull, s[ch][P - 1], 1, LQ);
+        rgt[ch] = __shfl_down_sync(kFull, s[ch][0], 1, LQ);
     }
     const double u1 = __shfl_sync(kFull, s[0][1], qb);                     // F_1 / s_1
     const double Pi = __shfl_sync(kFull, fma(kS2, s[0][2] + s[1][2], s[1][0]), qb); // F_2 + G_0 + G_2
@@ -449,12 +467,15 @@ __device__ __forceinline__ void load_scalars(double (&v)[4], double mine, int qb
     for (int s = 0; s < 4; s++) v[s] = __shfl_sync(kFull, mine, qb + s);
 }
 
+// maximum over the LQ lanes of a mode
+template <int LQ = 4>
 __device__ __forceinline__ double quad_max(double v)
 {
-    const double a = __shfl_xor_sync(kFull, v, 1);
-    if (!(a <= v)) v = a; // NaN propagates
-    const double c = __shfl_xor_sync(kFull, v, 2);
-    if (!(c <= v)) v = c;
+#pragma unroll
+    for (int o = 1; o < LQ; o <<= 1) {
+        const double a = __shfl_xor_sync(kFull, v, o);
+        if (!(a <= v)) v = a; // NaN propagates
+    }
     return v;
 }
 
@@ -528,20 +549,27 @@ __device__ __forceinline__ void q_store_src(double *dst, const double (&v)[3][P]
     }
 }
 
+template <int LQ = 4>
 __device__ __forceinline__ void q_copy_src(double *dst, const double *src, int q)
 {
-#pragma unroll
-    for (int c = 0; c < 3; c++) dst[q + 4 * c] = src[q + 4 * c];
+    for (int c = q; c < kSrcComp; c += LQ) dst[c] = src[c];
 }
 
-// the source components of the accepted state (shared memory, quad base
-// column Yq = smw + qb) into dst: lane q copies components q, q + 4, q + 8
-template <int P>
+// the source components of the accepted state (shared memory, mode base
+// column Yq = smw + qb) into dst: with four lanes, lane q copies components q,
+// q + 4 and the scalar 8 + q; with eight, lane q copies component q and lanes
+// 0..3 the scalars
+template <int P, int LQ = 4>
 __device__ __forceinline__ void q_store_y1(double *dst, const double *Yq, int q)
 {
-    dst[q] = Yq[src_elem<P>(q) * 32];
-    dst[q + 4] = Yq[src_elem<P>(q + 4) * 32];
-    dst[8 + q] = Yq[3 * P * 32 + q];
+    if (LQ == 8) {
+        dst[q] = Yq[src_elem<P>(q) * 32];
+        if (q < 4) dst[8 + q] = Yq[3 * P * 32 + q];
+    } else {
+        dst[q] = Yq[src_elem<P>(q) * 32];
+        dst[q + 4] = Yq[src_elem<P>(q + 4) * 32];
+        dst[8 + q] = Yq[3 * P * 32 + q];
+    }
 }
 
 // interpolated source components at fraction th of the step of length H
@@ -569,21 +597,24 @@ __device__ __forceinline__ void q_dense(double (&v)[kSrcComp], const double *dq,
     }
 }
 
-// Integrate the modes of one warp (8 per warp, mode index mi for this lane's quad).
+// Integrate the modes of one warp: LQ = 4 lanes per mode (8 modes per warp)
+// or LQ = 8 (4 modes per warp, P half as large: a shorter chain of work per
+// substep for the most expensive modes); mi is the mode of this lane's group.
 // PK: integrate to ln a = x_out only and write the matter power spectrum
 // there into pk_out[b][k] instead of the sources (S unused).  DM: write the
 // matter contrast delta_m at every tau node into S[b][k][n_tau] instead of
 // the sources (every node by landing or Hermite dense output: the linear
 // interpolation that the sources allow where e^-kappa < kNegligibleWeight is
 // not used).
-template <int P, bool PK = false, bool DM = false>
+template <int P, bool PK = false, bool DM = false, int LQ = 4>
 __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restrict__ bg, long len,
                            const double *__restrict__ kv, const QCoef &qc, double rtol, double atol, int max_steps,
                            const double sw[3], double *S, int *status, int *steps, double *smw, double *dn,
                            double x_out = 0.0, double *pk_out = nullptr)
 {
     constexpr int E = 3 * P + 1; // chain moments, then one scalar per quad lane
-    const int lane = threadIdx.x & 31, q = lane & 3, qb = lane & ~3;
+    static_assert(LQ == 4 || (LQ == 8 && P >= 4), "four lanes, or eight with lane 0 holding l <= 2");
+    const int lane = threadIdx.x & 31, q = lane & (LQ - 1), qb = lane & ~(LQ - 1);
     const bool valid = mi < M;
     const int kidx = valid ? Nk - 1 - (int)(mi / B) : 0;
     const int b = valid ? (int)(mi % B) : 0;
@@ -677,7 +708,7 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
     // interpolation cap allows.  This quad's interpolation data in dn:
     // y0[kSrcComp] f0[kSrcComp] f1[kSrcComp] (lane 0 the chain moments, the
     // scalars by their owners)
-    double *dq = dn + (lane >> 2) * 3 * kSrcComp;
+    double *dq = dn + (lane / LQ) * 3 * kSrcComp;
     int n_sig = 0;
     if (!DM) { // delta_m is wanted at every node
         int lo = 0, hi = n_tau - 1; // first node whose e^-kappa reaches the threshold
@@ -699,7 +730,7 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
         double xn = x, H = 0.0;
         bool land = false, emit = false, capped = false;
         int dmode = 0; // 0: none or landing on one node, 1: linear, 2: Hermite dense output
-        const QBg bx = qbg(op, x, q, qb);
+        const QBg bx = qbg<LQ>(op, x, q, qb);
         if (stepping) {
             xn = PK ? x_out : nodes[8 * node + N_LNA];
             H = h;
@@ -746,9 +777,10 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
             // floors clamped away from zero keep every scale a normal number
             const double fl0 = fmax(ABCMB_CHAIN_FLOOR * fmax(fabs(zs[0]), fmax(fabs(zs[1]), fabs(zs[2]))), 1e-290);
             const double fl1 = fmax(ABCMB_CHAIN_FLOOR * fabs(zs[3]), 1e-290);
-            const double fl2 = fmax(ABCMB_CHAIN_FLOOR * quad_max(cm2), 1e-290);
-            const double fl3 = fmax(ABCMB_CHAIN_FLOOR * quad_max(cm3), 1e-290);
-            T(kQK - 1, 3 * P) = rcp_approx(fma(rtol, fmax(fabs(pick4(zs, q)), q < 3 ? fl0 : fl1), atol));
+            const double fl2 = fmax(ABCMB_CHAIN_FLOOR * quad_max<LQ>(cm2), 1e-290);
+            const double fl3 = fmax(ABCMB_CHAIN_FLOOR * quad_max<LQ>(cm3), 1e-290);
+            // (with eight lanes, lanes 4..7 hold no scalar)
+            T(kQK - 1, 3 * P) = q < 4 ? rcp_approx(fma(rtol, fmax(fabs(pick4(zs, q)), q < 3 ? fl0 : fl1), atol)) : 0.0;
 #pragma unroll
             for (int ch = 0; ch < 3; ch++)
 #pragma unroll
@@ -765,7 +797,7 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
             const bool need_f = stepping && dmode == 2 && !have_f0;
             if (__any_sync(kFull, need_f)) {
                 q_zero<P>(w, ws);
-                q_rhs_axpy<P>(z, zs, w, ws, bx, md, 1.0, q, qb, qc);
+                q_rhs_axpy<P, LQ>(z, zs, w, ws, bx, md, 1.0, q, qb, qc);
                 if (need_f) {
                     q_store_src<P>(dq + kSrcComp, w, ws, q);
                     nsub++;
@@ -790,11 +822,11 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
             }
             if (!gbs) {
                 const double hs = H * c_nev.inv[j];
-                QBg bc = qbg(op, x, q, qb);
+                QBg bc = qbg<LQ>(op, x, q, qb);
                 for (int m = 0; m < j; m++) {
                     const double xm = m == j - 1 ? x + H : x + (m + 1) * hs;
-                    const QBg bn = qbg(op, xm, q, qb);
-                    q_imex<P>(z, zs, bc, bn, md, hs, q, qb, qc);
+                    const QBg bn = qbg<LQ>(op, xm, q, qb);
+                    q_imex<P, LQ>(z, zs, bc, bn, md, hs, q, qb, qc);
                     bc = bn;
                 }
                 if (open) nsub += j;
@@ -807,13 +839,13 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
                     for (int p = 0; p < P; p++) w[ch][p] = z[ch][p];
 #pragma unroll
                 for (int s = 0; s < 4; s++) ws[s] = zs[s];
-                q_rhs_axpy<P>(z, zs, w, ws, qbg(op, x, q, qb), md, hs, q, qb, qc); // w = z1
+                q_rhs_axpy<P, LQ>(z, zs, w, ws, qbg<LQ>(op, x, q, qb), md, hs, q, qb, qc); // w = z1
                 for (int m = 1; m < n; m += 2) {
-                    const QBg bm = qbg(op, x + m * hs, q, qb);
-                    q_rhs_axpy<P>(w, ws, z, zs, bm, md, 2.0 * hs, q, qb, qc); // z = z_{m+1}
+                    const QBg bm = qbg<LQ>(op, x + m * hs, q, qb);
+                    q_rhs_axpy<P, LQ>(w, ws, z, zs, bm, md, 2.0 * hs, q, qb, qc); // z = z_{m+1}
                     if (m + 1 < n) {
-                        const QBg bm1 = qbg(op, x + (m + 1) * hs, q, qb);
-                        q_rhs_axpy<P>(z, zs, w, ws, bm1, md, 2.0 * hs, q, qb, qc);
+                        const QBg bm1 = qbg<LQ>(op, x + (m + 1) * hs, q, qb);
+                        q_rhs_axpy<P, LQ>(z, zs, w, ws, bm1, md, 2.0 * hs, q, qb, qc);
                     }
                 }
                 if (open) nsub += n;
@@ -841,8 +873,8 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
                 }
                 if (j < kQK) T(j - 1, e) = cur;
             }
-            elh = max(elh, __shfl_xor_sync(kFull, elh, 1));
-            elh = max(elh, __shfl_xor_sync(kFull, elh, 2));
+#pragma unroll
+            for (int o = 1; o < LQ; o <<= 1) elh = max(elh, __shfl_xor_sync(kFull, elh, o));
             const double el = __hiloint2double(elh, 0);
             if (open && j >= 2) {
                 err = el;
@@ -898,7 +930,7 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
                 for (int p = 0; p < P; p++) z[ch][p] = Y(ch * P + p);
             load_scalars(zs, Y(3 * P), qb);
             q_zero<P>(w, ws);
-            q_rhs_axpy<P>(z, zs, w, ws, qbg(op, x, q, qb), md, 1.0, q, qb, qc);
+            q_rhs_axpy<P, LQ>(z, zs, w, ws, qbg<LQ>(op, x, q, qb), md, 1.0, q, qb, qc);
             if (pend && dmode == 2) {
                 q_store_src<P>(dq + 2 * kSrcComp, w, ws, q);
                 nsub++;
@@ -917,11 +949,11 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
                     if (DM) Sm[i] = q_delta_m(op, nodes[8 * i + N_LNA], v[9], v[10]);
                     else q_sources_v(op, nodes + 8 * i, k, sw, v, Sm + 3 * i);
                 }
-                const int cnt = __popc((__ballot_sync(kFull, mine) >> qb) & 0xFu);
+                const int cnt = __popc((__ballot_sync(kFull, mine) >> qb) & ((1u << LQ) - 1u));
                 if (pend) {
                     node += cnt;
                     if (node >= n_tau) done = true;
-                    if (cnt < 4 || done) pend = false;
+                    if (cnt < LQ || done) pend = false;
                 }
             }
             __syncwarp();
@@ -929,8 +961,8 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
         if (stepping && jacc > 0) {
             // the step end is the next step's start
             if (dmode >= 1) {
-                if (dmode == 2) q_copy_src(dq + kSrcComp, dq + 2 * kSrcComp, q);
-                q_store_y1<P>(dq, smw + qb, q);
+                if (dmode == 2) q_copy_src<LQ>(dq + kSrcComp, dq + 2 * kSrcComp, q);
+                q_store_y1<P, LQ>(dq, smw + qb, q);
             }
             have_y0 = dmode >= 1;
             have_f0 = dmode == 2;
@@ -975,21 +1007,24 @@ constexpr size_t quad_smem_per_warp()
     return ((size_t)(1 + kQK) * (3 * P + 1) * 32 + 8 * 3 * kSrcComp) * sizeof(double);
 }
 
+// Modes (k-descending, then cosmology) [0, M8) run eight lanes each in the
+// first nb8 one-warp CTAs (the highest k: their per-substep chain of work is
+// what bounds the launch); the rest run four lanes each.  W = 1 whenever
+// nb8 > 0.  Both layouts evaluate the same expressions for a mode; its warp-
+// mates differ, which moves the warp-wide switch to the explicit regime.
 template <int P, int W>
 __global__ void __launch_bounds__(32 * W)
 perturb_quad_kernel(int B, int Nk, const double *__restrict__ bg, long len, const double *__restrict__ kv, int Lg,
                     int Lp, int Ln, double rtol, double atol, int max_steps, double s_sw, double s_isw,
-                    double s_dop, double *S, int *status, int *steps)
+                    double s_dop, double *S, int *status, int *steps, int nb8, long M8)
 {
     extern __shared__ double qsm[];
     __shared__ double cS[3 * 64], cB[3 * 64];
     const int Ls[3] = {Lg, Lp, Ln};
     fill_coef(cS, cB, Ls);
     __syncthreads();
-    constexpr int E = 3 * P + 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long M = (long)B * Nk;
-    const long mi = ((long)blockIdx.x * W + warp) * 8 + (lane >> 2);
     QCoef qc;
     qc.S = cS;
     qc.Bc = cB;
@@ -998,6 +1033,17 @@ perturb_quad_kernel(int B, int Nk, const double *__restrict__ bg, long len, cons
     qc.L[2] = Ln;
     for (int c = 0; c < 3; c++) qc.L1[c] = qc.L[c] + 1.0;
     const double sw[3] = {s_sw, s_isw, s_dop};
+    if constexpr (P >= 8) {
+        if ((int)blockIdx.x < nb8) {
+            constexpr int P8 = P / 2, E8 = 3 * P8 + 1;
+            const long mi = (long)blockIdx.x * 4 + (lane >> 3);
+            quad_modes<P8, false, false, 8>(mi, M8, B, Nk, bg, len, kv, qc, rtol, atol, max_steps, sw, S, status,
+                                            steps, qsm, qsm + (1 + kQK) * E8 * 32);
+            return;
+        }
+    }
+    constexpr int E = 3 * P + 1;
+    const long mi = M8 + ((long)(blockIdx.x - nb8) * W + warp) * 8 + (lane >> 2);
     double *smw = qsm + (long)warp * ((1 + kQK) * E * 32 + 8 * 3 * kSrcComp);
     quad_modes<P>(mi, M, B, Nk, bg, len, kv, qc, rtol, atol, max_steps, sw, S, status, steps, smw,
                   smw + (1 + kQK) * E * 32);

@@ -3,8 +3,8 @@
 //
 // background_kernel: one warp per cosmology runs abcmb::build_background.
 // perturb_quad_kernel (abcmb_ode_quad.cuh): four lanes per (cosmology, k)
-// mode, state in registers and shared memory; the path for hierarchies up to
-// kQLmax = 63.
+// mode (eight for the modes of the highest k, abcmb_options.n_wide), state in
+// registers and shared memory; the path for hierarchies up to kQLmax = 63.
 // perturb_kernel: one thread per mode runs abcmb::integrate_mode with the
 // per-mode working vectors in a global workspace, laid out
 // [vector][component][mode] so that the lanes of a warp touch consecutive
@@ -85,19 +85,24 @@ template <int P>
 static int launch_quad(int B, const double *bg, const double *k, int Nk, const abcmb_options *o, double *S,
                        int *st, int *steps, cudaStream_t s)
 {
-    constexpr int W = 1; // one warp (8 modes) per CTA: fine-grained scheduling of uneven modes
+    constexpr int W = 1; // one warp per CTA: fine-grained scheduling of uneven modes
     const size_t smem = W * quad_smem_per_warp<P>();
     auto kern = perturb_quad_kernel<P, W>;
     const long avail = smem_optin((const void *)kern);
     if (avail < 0) return ABCMB_E_CUDA;
     if ((long)smem > avail) return ABCMB_E_INVALID_ARG;
     const long M = (long)B * Nk;
-    const long blocks = (M + 8 * W - 1) / (8 * W);
+    // the highest k on eight lanes per mode (four modes per warp); P = 4 keeps
+    // four lanes (lane 0 must hold l <= 2)
+    long kw = P >= 8 ? o->n_wide : 0;
+    if (kw > Nk) kw = Nk;
+    const long M8 = (long)B * kw;
+    const long nb8 = (M8 + 3) / 4, blocks = nb8 + (M - M8 + 8 * W - 1) / (8 * W);
     if (blocks > 2147483647L) return ABCMB_E_INVALID_ARG;
     const long len = (long)ABCMB_BG_LEN(o->n_tau);
     kern<<<(unsigned)blocks, 32 * W, smem, s>>>(B, Nk, bg, len, k, o->lmax_g, o->lmax_pol, o->lmax_nu, o->rtol,
                                                  o->atol, o->max_steps, o->scale_sw, o->scale_isw, o->scale_dop, S,
-                                                 st, steps);
+                                                 st, steps, (int)nb8, M8);
     return cudaGetLastError() == cudaSuccess ? ABCMB_OK : ABCMB_E_CUDA;
 }
 
@@ -141,6 +146,7 @@ extern "C" void abcmb_default_options(abcmb_options *o)
     o->m_ncdm = 0.0;
     o->lmax_ncdm = 0;
     o->node_recipe = 0;
+    o->n_wide = 0;
 }
 
 extern "C" int abcmb_validate_options(const abcmb_options *o)
@@ -157,6 +163,7 @@ extern "C" int abcmb_validate_options(const abcmb_options *o)
     if (o->m_ncdm == 0.0 ? o->lmax_ncdm != 0 : (o->lmax_ncdm < 3 || o->lmax_ncdm > abcmb::kQLmax))
         return ABCMB_E_INVALID_ARG;
     if (o->node_recipe != 0 && o->node_recipe != 1) return ABCMB_E_INVALID_ARG;
+    if (o->n_wide < 0) return ABCMB_E_INVALID_ARG;
     return ABCMB_OK;
 }
 

@@ -270,3 +270,29 @@ def test_repeatable(A):
     r2 = run_gpu(A, p, k, o)
     np.testing.assert_array_equal(r1["S"], r2["S"])
     np.testing.assert_allclose(r1["Cl"], r2["Cl"], rtol=1e-13)
+
+
+@pytest.mark.parametrize("lmax_hier", [30, 40])
+def test_eight_lane_layout_agrees_with_the_four_lane_one(A, lmax_hier):
+    # abcmb_options.n_wide moves the modes of the highest k from four lanes per
+    # mode to eight, with the same arithmetic per mode; a mode's result still
+    # depends on its warp-mates through the warp-wide switch to the explicit
+    # regime, so the layouts agree to the ODE tolerance, not bit for bit
+    # (ragged: 5 cosmologies, so warps of the eight-lane layout mix k values)
+    p = W.BATCH64.params()[:5]
+    k = torch.tensor(W.log_k_nodes(23, 1e-4, 0.5), device="cuda")
+    bg = A.abcmb_background_tables(torch.tensor(p, device="cuda"),
+                                   A.options(lmax_hier=lmax_hier, n_tau=800, lmax_cl=300))
+    out = []
+    for n_wide in (0, 7, 23, 40):  # (steps returned for the record, not compared)
+        o = A.options(lmax_hier=lmax_hier, n_tau=800, lmax_cl=300, n_wide=n_wide, rtol=1e-9)
+        S, st, steps = A.abcmb_perturb(bg, k, o)
+        out.append((S.cpu().numpy(), st.cpu().numpy(), steps.cpu().numpy()))
+    S0 = out[0][0]
+    peak = np.abs(S0).max(axis=2, keepdims=True)
+    assert np.all(out[0][1] == 0)
+    for S, st, steps in out[1:]:
+        np.testing.assert_array_equal(st, out[0][1])
+        assert np.all(np.abs(S - S0) <= 1e-7 * peak), np.abs((S - S0) / peak).max()
+        # (step counts differ: a warp of mixed k keeps its modes in the
+        # implicit regime until the last of them may leave it)
