@@ -180,32 +180,23 @@ __device__ __forceinline__ void fill_coef(double *cS, double *cB, const int Ls[3
     }
 }
 
-// Aitken-Neville factors T_{j,s} = T_{j,s-1} + (T_{j,s-1} - T_{j-1,s-1}) f[j][s] for
-// the harmonic sequence n_j = j extrapolated in h (IMEX Euler: f = (j - s) / s) and
-// the sequence n_j = 2j extrapolated in h^2 (Gragg: f = 1 / ((j / (j - s))^2 - 1)),
-// and 1/n, tabulated so that no column divides.
-struct NevTab {
-    double imex[kQK + 1][kQK], gbs[kQK + 1][kQK], inv[2 * kQK + 1];
+// 1/n for the substep lengths, tabulated so that no column divides
+struct InvTab {
+    double inv[2 * kQK + 1];
 };
 
-constexpr NevTab make_nev()
+constexpr InvTab make_inv()
 {
-    NevTab t{};
-    for (int j = 1; j <= kQK; j++)
-        for (int s = 1; s < j; s++) {
-            t.imex[j][s] = (double)(j - s) / (double)s;
-            const double js = (double)(j - s);
-            t.gbs[j][s] = js * js / ((double)j * j - js * js);
-        }
+    InvTab t{};
     for (int n = 1; n <= 2 * kQK; n++) t.inv[n] = 1.0 / n;
     return t;
 }
 
-__constant__ NevTab c_nev = make_nev();
+__constant__ InvTab c_inv = make_inv();
 
-// The same extrapolations as explicit linear combinations of a step's column
-// values z_1..z_j (z_i from n_i substeps): the value extrapolated to h = 0
-// through points 1..j is sum_i lam[j][i] z_i (Lagrange weights at 0 in x = h
+// Extrapolation of a step's column values z_1..z_j (z_i from n_i substeps) as
+// explicit linear combinations, in place of the Aitken-Neville recursion: the
+// value extrapolated to h = 0 through points 1..j is sum_i lam[j][i] z_i (Lagrange weights at 0 in x = h
 // for the implicit sequence n_i = i, x = h^2 for the Gragg sequence n_i = 2i),
 // and the error estimate, that value minus the one through points 2..j, is
 // sum_i mu[j][i] z_i.  A column then costs j + 1 operations per element for
@@ -821,7 +812,7 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
                 load_scalars(zs, Y(3 * P), qb);
             }
             if (!gbs) {
-                const double hs = H * c_nev.inv[j];
+                const double hs = H * c_inv.inv[j];
                 QBg bc = qbg<LQ>(op, x, q, qb);
                 for (int m = 0; m < j; m++) {
                     const double xm = m == j - 1 ? x + H : x + (m + 1) * hs;
@@ -832,7 +823,7 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
                 if (open) nsub += j;
             } else {
                 const int n = 2 * j;
-                const double hs = H * c_nev.inv[n];
+                const double hs = H * c_inv.inv[n];
 #pragma unroll
                 for (int ch = 0; ch < 3; ch++)
 #pragma unroll
