@@ -32,11 +32,11 @@ METRIC = "C_ℓ spectra/s at ℓmax=2500 TT/TE/EE (≤1e-5 rel vs FP64 oracle); 
 FP64_PEAK = 2 * 2 * 152 * 2.07e9  # FMA units/SM x flops/FMA x SMs x max SM clock (1.26 TFLOP/s)
 FLUSH_BYTES = 512 << 20
 # DRAM bytes (read + write) per mode of the FP64 perturbation kernel, from an
-# ncu capture of the kernel as built (64 cosmologies x 40 k: 3.971023 GB read,
-# 0.373314 GB written over 2560 modes); traffic grows in proportion to the
+# ncu capture of the kernel as built (64 cosmologies x 40 k: 4.096524 GB read,
+# 0.374885 GB written over 2560 modes); traffic grows in proportion to the
 # modes, since every mode reads its cosmology's tables and writes its own
 # sources.  Set to None whenever the kernel changes until it is re-captured.
-PERTURB_DRAM_BYTES_PER_MODE = (3.971023e9 + 0.373314e9) / 2560
+PERTURB_DRAM_BYTES_PER_MODE = (4.096524e9 + 0.374885e9) / 2560
 
 
 def flops_per_step(N: int, stages: int = 6) -> float:
