@@ -1,7 +1,9 @@
 // Perturbation ODEs with four lanes per (cosmology, k) mode -- the path
 // abcmb_perturb runs.  Same equations and integrator as abcmb_ode.cuh (which
 // documents them: IMEX-Euler / Gragg extrapolation, steps landing on every tau
-// node), laid out for the GB300 FP64 pipe, whose issue rate bounds this kernel:
+// node), laid out for the GB300 FP64 pipe, whose issue rate bounds this kernel
+// (each SM sub-partition's FP64 unit takes one warp instruction per 64
+// cycles, so a warp's time is its count of FP64 instructions):
 //
 //  * A warp holds 8 modes; lane q = 0..3 of a mode's quad owns the Legendre
 //    moments l in [qP, qP+P) of each of the three chains (photon
@@ -12,18 +14,23 @@
 //    F_{l-1} in F_l' = kH (A_l F_{l-1} - B_l F_{l+1}): then u_l' = kH (u_{l-1}
 //    - beta_l u_{l+1}), beta_l = B_l A_{l+1}, and the streaming costs two FMAs
 //    per moment instead of a multiply and two FMAs.  The equations' other
-//    terms (metric, Thomson, sources, tolerances) carry the s_l factors.  Lane 0 also owns l <= 2 of every chain,
-//    hence the metric sums, both Thomson blocks and the sources; the four
+//    terms (metric, Thomson, sources, tolerances) carry the s_l factors.
+//    Lane 0 also owns l <= 2 of every chain, hence the metric sums, both
+//    Thomson blocks and the sources; the four
 //    scalars (eta, delta_c, delta_b, theta_b) are kept identical in all four
 //    lanes.
 //  * The background point (10 interpolated quantities) is split over the
-//    quad: lane q interpolates ODE-table columns q, q+4 and 8 + (q & 1), then
-//    the values are broadcast inside the quad.
-//  * The accepted state and the extrapolation tableau live in shared memory
+//    quad: lane q evaluates ODE-table columns q, q+4 and 8 + (q & 1), each
+//    from the record's cubic of its ln a interval (three FMAs), then the
+//    values are broadcast inside the quad.
+//  * The accepted state and the step's column values live in shared memory
 //    ([vector][element][lane], conflict-free; the scalars take one row, lane
-//    q of a quad holding scalar q), the inverse error scales in
-//    the last tableau column's slot until that column is formed; the
-//    working vectors of a column live in registers.
+//    q of a quad holding scalar q), the inverse error scales in the last
+//    column's slot (the last column's values stay in registers); the working
+//    vectors of a column live in registers.  The extrapolation is a weighted
+//    sum of the column values (ExtTab).
+//  * With eight lanes per mode (LQ = 8, abcmb_options.n_wide) a lane owns P
+//    moments with P half as large; everything else is the same.
 //  * The error norm is max_i |T_j,j-1 - T_j,j-2|_i / (atol + rtol max(|y_i|,
 //    1e-4 m_g(i))) with y the state at the step start and m_g the largest
 //    magnitude of i's group (eta/delta_c/delta_b, theta_b, photons, neutrinos);
