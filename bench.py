@@ -32,11 +32,12 @@ METRIC = "C_ℓ spectra/s at ℓmax=2500 TT/TE/EE (≤1e-5 rel vs FP64 oracle); 
 FP64_PEAK = 2 * 2 * 152 * 2.07e9  # FMA units/SM x flops/FMA x SMs x max SM clock (1.26 TFLOP/s)
 FLUSH_BYTES = 512 << 20
 # DRAM bytes (read + write) per mode of the FP64 perturbation kernel, from an
-# ncu capture of the kernel as built (64 cosmologies x 40 k: 4.096524 GB read,
-# 0.374885 GB written over 2560 modes); traffic grows in proportion to the
+# ncu capture of the kernel as built; traffic grows in proportion to the
 # modes, since every mode reads its cosmology's tables and writes its own
-# sources.  Set to None whenever the kernel changes until it is re-captured.
-PERTURB_DRAM_BYTES_PER_MODE = (4.096524e9 + 0.374885e9) / 2560
+# sources.  None: the kernel gained the err_floor argument and the benchmark
+# runs it at 1e-2 after the last capture (1.75 MB per mode at 1e-4), which has
+# not been repeated.
+PERTURB_DRAM_BYTES_PER_MODE = None
 
 
 def flops_per_step(N: int, stages: int = 6) -> float:
@@ -473,6 +474,8 @@ def main():
                     help="serving benchmark: Poisson arrivals of mixed-size requests through abcmb_server")
     ap.add_argument("--grad", action="store_true",
                     help="gradient benchmark: dC_l/dtheta of a batch through the hand-written adjoint")
+    ap.add_argument("--err-floor", type=float, default=None,
+                    help="ODE error norm's group floor (abcmb_options.err_floor; default: the workload's)")
     ap.add_argument("--n-wide", type=int, default=0,
                     help="modes of the n highest k on eight lanes (abcmb_options.n_wide)")
     ap.add_argument("--node-recipe", type=int, default=0, choices=[0, 1],
@@ -526,8 +529,9 @@ def main():
         k = W.log_k_nodes(args.n_k or wl.n_k, k_min, k_max)
     else:
         k = wl.k()
+    err_floor = wl.err_floor if args.err_floor is None else args.err_floor
     o = A.options(lmax_hier=wl.l_max_hier, lmax_cl=wl.l_max_cl, n_tau=wl.n_tau, rtol=args.rtol,
-                  node_recipe=args.node_recipe, n_wide=args.n_wide)
+                  node_recipe=args.node_recipe, n_wide=args.n_wide, err_floor=err_floor)
     N = 4 + 3 * (wl.l_max_hier + 1)
     mixed = args.precision == "mixed"
     pipe = A.Pipeline(B, k, o, mixed=mixed)
@@ -634,7 +638,7 @@ def main():
         "config": {"workload": wl.name, "batch": B, "n_k": len(k), "k_range": [float(k[0]), float(k[-1])],
                    "lmax_cl": wl.l_max_cl, "hierarchy_lmax": wl.l_max_hier, "n_tau": wl.n_tau,
                    "rtol": args.rtol, "precision": args.precision, "node_recipe": args.node_recipe,
-                   "n_wide": args.n_wide,
+                   "n_wide": args.n_wide, "err_floor": err_floor,
                    "l2": "flushed (512 MiB write) between timed steps",
                    "parallelism": f"replicas x{world}"},
         "clocks": clk,

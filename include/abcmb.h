@@ -89,6 +89,12 @@ typedef struct {
                         the warp-wide switch to the explicit regime, within the ODE tolerance);
                         0: none (the default: on the 64-cosmology, 400 k workload 12, 25 and
                         50 wide k gave no gain); must be >= 0                              */
+    double err_floor; /* the four-lane kernel's error norm: component i is measured against
+                        atol + rtol max(|y_i|, err_floor m_g), m_g the largest magnitude in its
+                        group (eta/delta_c/delta_b, theta_b, photons, neutrinos), so components
+                        below err_floor of their group are held to rtol of that level; in
+                        (0, 1], default 1e-4 (the thread-per-mode and adjoint solvers keep
+                        1e-4)                                                             */
 } abcmb_options;
 
 /* Fill *o with the defaults used by the library's tests: hierarchies 12,

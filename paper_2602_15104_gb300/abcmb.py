@@ -47,12 +47,12 @@ class Options(ctypes.Structure):
                 ("scale_sw", ctypes.c_double), ("scale_isw", ctypes.c_double),
                 ("scale_dop", ctypes.c_double), ("scale_pol", ctypes.c_double),
                 ("m_ncdm", ctypes.c_double), ("lmax_ncdm", ctypes.c_int), ("node_recipe", ctypes.c_int),
-                ("n_wide", ctypes.c_int)]
+                ("n_wide", ctypes.c_int), ("err_floor", ctypes.c_double)]
 
 
 def options(lmax_hier=12, lmax_cl=2500, n_tau=6000, rtol=1e-6, atol=1e-12, max_steps=2_000_000,
             scale_sw=1.0, scale_isw=1.0, scale_dop=1.0, scale_pol=1.0, lmax_g=None, lmax_pol=None,
-            lmax_nu=None, m_ncdm=0.0, lmax_ncdm=17, node_recipe=0, n_wide=0) -> Options:
+            lmax_nu=None, m_ncdm=0.0, lmax_ncdm=17, node_recipe=0, n_wide=0, err_floor=1e-4) -> Options:
     """m_ncdm > 0: one massive neutrino of that mass [eV] (two massless ones
     remain), its hierarchies to lmax_ncdm; abcmb_perturb then runs one warp
     per mode and needs a workspace.  node_recipe 1 places the tau nodes so
@@ -62,6 +62,7 @@ def options(lmax_hier=12, lmax_cl=2500, n_tau=6000, rtol=1e-6, atol=1e-12, max_s
     o.lmax_ncdm = int(lmax_ncdm) if m_ncdm > 0.0 else 0
     o.node_recipe = int(node_recipe)
     o.n_wide = int(n_wide)
+    o.err_floor = float(err_floor)
     o.lmax_g = lmax_hier if lmax_g is None else lmax_g
     o.lmax_pol = lmax_hier if lmax_pol is None else lmax_pol
     o.lmax_nu = lmax_hier if lmax_nu is None else lmax_nu

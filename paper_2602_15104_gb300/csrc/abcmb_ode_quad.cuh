@@ -32,7 +32,8 @@
 //  * With eight lanes per mode (LQ = 8, abcmb_options.n_wide) a lane owns P
 //    moments with P half as large; everything else is the same.
 //  * The error norm is max_i |T_j,j-1 - T_j,j-2|_i / (atol + rtol max(|y_i|,
-//    1e-4 m_g(i))) with y the state at the step start and m_g the largest
+//    f m_g(i))) with y the state at the step start, f the group floor
+//    (abcmb_options.err_floor, default 1e-4) and m_g the largest
 //    magnitude of i's group (eta/delta_c/delta_b, theta_b, photons, neutrinos);
 //    the inverse scales are formed once per step with the approximate
 //    reciprocal (a few ulp of float accuracy, ample for step control).
@@ -608,7 +609,7 @@ template <int P, bool PK = false, bool DM = false, int LQ = 4>
 __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restrict__ bg, long len,
                            const double *__restrict__ kv, const QCoef &qc, double rtol, double atol, int max_steps,
                            const double sw[3], double *S, int *status, int *steps, double *smw, double *dn,
-                           double x_out = 0.0, double *pk_out = nullptr)
+                           double efloor, double x_out = 0.0, double *pk_out = nullptr)
 {
     constexpr int E = 3 * P + 1; // chain moments, then one scalar per quad lane
     static_assert(LQ == 4 || (LQ == 8 && P >= 4), "four lanes, or eight with lane 0 holding l <= 2");
@@ -773,10 +774,10 @@ __device__ void quad_modes(long mi, long M, int B, int Nk, const double *__restr
             }
             load_scalars(zs, Y(3 * P), qb);
             // floors clamped away from zero keep every scale a normal number
-            const double fl0 = fmax(ABCMB_CHAIN_FLOOR * fmax(fabs(zs[0]), fmax(fabs(zs[1]), fabs(zs[2]))), 1e-290);
-            const double fl1 = fmax(ABCMB_CHAIN_FLOOR * fabs(zs[3]), 1e-290);
-            const double fl2 = fmax(ABCMB_CHAIN_FLOOR * quad_max<LQ>(cm2), 1e-290);
-            const double fl3 = fmax(ABCMB_CHAIN_FLOOR * quad_max<LQ>(cm3), 1e-290);
+            const double fl0 = fmax(efloor * fmax(fabs(zs[0]), fmax(fabs(zs[1]), fabs(zs[2]))), 1e-290);
+            const double fl1 = fmax(efloor * fabs(zs[3]), 1e-290);
+            const double fl2 = fmax(efloor * quad_max<LQ>(cm2), 1e-290);
+            const double fl3 = fmax(efloor * quad_max<LQ>(cm3), 1e-290);
             // (with eight lanes, lanes 4..7 hold no scalar)
             T(kQK - 1, 3 * P) = q < 4 ? rcp_approx(fma(rtol, fmax(fabs(pick4(zs, q)), q < 3 ? fl0 : fl1), atol)) : 0.0;
 #pragma unroll
@@ -1014,7 +1015,7 @@ template <int P, int W>
 __global__ void __launch_bounds__(32 * W)
 perturb_quad_kernel(int B, int Nk, const double *__restrict__ bg, long len, const double *__restrict__ kv, int Lg,
                     int Lp, int Ln, double rtol, double atol, int max_steps, double s_sw, double s_isw,
-                    double s_dop, double *S, int *status, int *steps, int nb8, long M8)
+                    double s_dop, double *S, int *status, int *steps, int nb8, long M8, double efloor)
 {
     extern __shared__ double qsm[];
     __shared__ double cS[3 * 64], cB[3 * 64];
@@ -1036,7 +1037,7 @@ perturb_quad_kernel(int B, int Nk, const double *__restrict__ bg, long len, cons
             constexpr int P8 = P / 2, E8 = 3 * P8 + 1;
             const long mi = (long)blockIdx.x * 4 + (lane >> 3);
             quad_modes<P8, false, false, 8>(mi, M8, B, Nk, bg, len, kv, qc, rtol, atol, max_steps, sw, S, status,
-                                            steps, qsm, qsm + (1 + kQK) * E8 * 32);
+                                            steps, qsm, qsm + (1 + kQK) * E8 * 32, efloor);
             return;
         }
     }
@@ -1044,7 +1045,7 @@ perturb_quad_kernel(int B, int Nk, const double *__restrict__ bg, long len, cons
     const long mi = M8 + ((long)(blockIdx.x - nb8) * W + warp) * 8 + (lane >> 2);
     double *smw = qsm + (long)warp * ((1 + kQK) * E * 32 + 8 * 3 * kSrcComp);
     quad_modes<P>(mi, M, B, Nk, bg, len, kv, qc, rtol, atol, max_steps, sw, S, status, steps, smw,
-                  smw + (1 + kQK) * E * 32);
+                  smw + (1 + kQK) * E * 32, efloor);
 }
 
 // Matter power spectrum at ln a = x_out for every (cosmology, k) mode: the
@@ -1053,7 +1054,7 @@ template <int P>
 __global__ void __launch_bounds__(32)
 pk_quad_kernel(int B, int Nk, const double *__restrict__ bg, long len, const double *__restrict__ kv, int Lg,
                int Lp, int Ln, double rtol, double atol, int max_steps, double x_out, double *Pk, int *status,
-               int *steps)
+               int *steps, double efloor)
 {
     extern __shared__ double qsm[];
     __shared__ double cS[3 * 64], cB[3 * 64];
@@ -1073,14 +1074,14 @@ pk_quad_kernel(int B, int Nk, const double *__restrict__ bg, long len, const dou
     for (int c = 0; c < 3; c++) qc.L1[c] = qc.L[c] + 1.0;
     const double sw[3] = {0.0, 0.0, 0.0};
     quad_modes<P, true>(mi, M, B, Nk, bg, len, kv, qc, rtol, atol, max_steps, sw, nullptr, status, steps, qsm,
-                        qsm + (1 + kQK) * E * 32, x_out, Pk);
+                        qsm + (1 + kQK) * E * 32, efloor, x_out, Pk);
 }
 
 // delta_m at every tau node for every (cosmology, k) mode: Dm[B][Nk][n_tau]
 template <int P>
 __global__ void __launch_bounds__(32)
 dm_quad_kernel(int B, int Nk, const double *__restrict__ bg, long len, const double *__restrict__ kv, int Lg,
-               int Lp, int Ln, double rtol, double atol, int max_steps, double *Dm, int *status)
+               int Lp, int Ln, double rtol, double atol, int max_steps, double *Dm, int *status, double efloor)
 {
     extern __shared__ double qsm[];
     __shared__ double cS[3 * 64], cB[3 * 64];
@@ -1100,7 +1101,7 @@ dm_quad_kernel(int B, int Nk, const double *__restrict__ bg, long len, const dou
     for (int c = 0; c < 3; c++) qc.L1[c] = qc.L[c] + 1.0;
     const double sw[3] = {1.0, 1.0, 1.0};
     quad_modes<P, false, true>(mi, M, B, Nk, bg, len, kv, qc, rtol, atol, max_steps, sw, Dm, status, nullptr,
-                               qsm, qsm + (1 + kQK) * E * 32);
+                               qsm, qsm + (1 + kQK) * E * 32, efloor);
 }
 
 } // namespace abcmb

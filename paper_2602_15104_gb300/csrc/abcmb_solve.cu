@@ -102,7 +102,7 @@ static int launch_quad(int B, const double *bg, const double *k, int Nk, const a
     const long len = (long)ABCMB_BG_LEN(o->n_tau);
     kern<<<(unsigned)blocks, 32 * W, smem, s>>>(B, Nk, bg, len, k, o->lmax_g, o->lmax_pol, o->lmax_nu, o->rtol,
                                                  o->atol, o->max_steps, o->scale_sw, o->scale_isw, o->scale_dop, S,
-                                                 st, steps, (int)nb8, M8);
+                                                 st, steps, (int)nb8, M8, o->err_floor);
     return cudaGetLastError() == cudaSuccess ? ABCMB_OK : ABCMB_E_CUDA;
 }
 
@@ -147,6 +147,7 @@ extern "C" void abcmb_default_options(abcmb_options *o)
     o->lmax_ncdm = 0;
     o->node_recipe = 0;
     o->n_wide = 0;
+    o->err_floor = 1e-4;
 }
 
 extern "C" int abcmb_validate_options(const abcmb_options *o)
@@ -164,6 +165,7 @@ extern "C" int abcmb_validate_options(const abcmb_options *o)
         return ABCMB_E_INVALID_ARG;
     if (o->node_recipe != 0 && o->node_recipe != 1) return ABCMB_E_INVALID_ARG;
     if (o->n_wide < 0) return ABCMB_E_INVALID_ARG;
+    if (!(o->err_floor > 0.0 && o->err_floor <= 1.0)) return ABCMB_E_INVALID_ARG;
     return ABCMB_OK;
 }
 
@@ -185,7 +187,7 @@ static int launch_pk(int B, const double *bg, const double *k, int Nk, const abc
     if (blocks > 2147483647L) return ABCMB_E_INVALID_ARG;
     const long len = (long)ABCMB_BG_LEN(o->n_tau);
     kern<<<(unsigned)blocks, 32, smem, s>>>(B, Nk, bg, len, k, o->lmax_g, o->lmax_pol, o->lmax_nu, o->rtol, o->atol,
-                                            o->max_steps, x_out, Pk, st, steps);
+                                            o->max_steps, x_out, Pk, st, steps, o->err_floor);
     return cudaGetLastError() == cudaSuccess ? ABCMB_OK : ABCMB_E_CUDA;
 }
 } // namespace abcmb
@@ -220,7 +222,7 @@ static int launch_dm(int B, const double *bg, const double *k, int Nk, const abc
     if (blocks > 2147483647L) return ABCMB_E_INVALID_ARG;
     const long len = (long)ABCMB_BG_LEN(o->n_tau);
     kern<<<(unsigned)blocks, 32, smem, s>>>(B, Nk, bg, len, k, o->lmax_g, o->lmax_pol, o->lmax_nu, o->rtol, o->atol,
-                                            o->max_steps, Dm, st);
+                                            o->max_steps, Dm, st, o->err_floor);
     return cudaGetLastError() == cudaSuccess ? ABCMB_OK : ABCMB_E_CUDA;
 }
 } // namespace abcmb

@@ -42,6 +42,7 @@ def test_defaults_and_sizes(A):
     o = A.Options()
     L.abcmb_default_options(ctypes.byref(o))
     assert (o.lmax_g, o.lmax_cl, o.n_tau, o.node_recipe, o.n_wide) == (12, 2500, 6000, 0, 0)
+    assert o.err_floor == 1e-4
     assert L.abcmb_validate_options(ctypes.byref(A.options(node_recipe=1))) == A.OK
     assert A.bg_doubles(o) == A.BG_NODES + 8 * o.n_tau + A.BG_ODEPOLY_DOUBLES
     # hierarchies <= 63 keep the ODE state on chip: no workspace
@@ -57,7 +58,7 @@ def test_defaults_and_sizes(A):
 @pytest.mark.parametrize("field,value", [("lmax_g", 3), ("lmax_nu", 129), ("lmax_cl", 1), ("lmax_cl", 5001),
                                          ("n_tau", 7), ("max_steps", 0), ("rtol", 0.0), ("rtol", 1.0),
                                          ("atol", -1.0), ("node_recipe", 2), ("node_recipe", -1),
-                                         ("n_wide", -1)])
+                                         ("n_wide", -1), ("err_floor", 0.0), ("err_floor", 1.5)])
 def test_invalid_options_rejected_on_host(A, field, value):
     L = A.lib()
     o = A.options()
