@@ -27,7 +27,11 @@
  *   C_ell             4 pi int dk/k P(k) Delta_X Delta_Y (App. B.4, eq.
  *                     c_ell_def, eq. PK_pivot), trapezoid in ln k
  *
- * Parity-unpinned parts are listed in the file headers that implement them.
+ * Every part is pinned by tests/test_oracle_pins.py (closed forms, textbook
+ * tables, the paper's printed values, defining equations), each pin checked
+ * against a planted mistake.  What no test here can fix is the physical
+ * accuracy against an external Boltzmann or recombination code (none is
+ * available); orc_background.c says where that touches the thermal history.
  *
  * The arithmetic is written once over the scalar type real_t (orc_real.h):
  * double in liborc.so, double complex in liborc_cs.so, which gives the

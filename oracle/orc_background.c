@@ -35,7 +35,9 @@
  *    k / H(a_k) = R_large (eq. k_start_large);
  *  - tau nodes: 1/4 uniform in ln a on [ln a_tc, ln a(z=1300)), 1/2 uniform in
  *    z on [1300, 900), 1/4 uniform in tau on [tau(z=900), tau_0); trapezoid
- *    weights in tau (App. B.6: trapezoid rules, no time cut).
+ *    weights in tau (App. B.6: trapezoid rules, no time cut).  Option
+ *    node_recipe = 1: 1/5 in ln a, 2/5 over [1300, 900), 1/5 uniform in z
+ *    over [900, 300), the rest uniform in tau from z = 300.
  */
 #include <math.h>
 #include <stdlib.h>

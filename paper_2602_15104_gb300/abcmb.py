@@ -147,10 +147,32 @@ def _check(rc, what):
         raise RuntimeError(f"{what}: {ERRORS.get(rc, rc)}")
 
 
+def _on_gpu(t):
+    return isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()
+
+
 def _dev(t, dtype=torch.float64):
-    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+    if not (_on_gpu(t) and t.dtype == dtype):
         raise TypeError(f"expected a contiguous CUDA {dtype} tensor")
     return t
+
+
+def _fits(t, n, what, dtype=torch.float64):
+    """t as a buffer the library reads or writes n elements of through its
+    pointer (the extent include/abcmb.h gives): a contiguous CUDA tensor of
+    dtype with at least n elements, else the call is refused before it is
+    made."""
+    _dev(t, dtype)
+    if t.numel() < n:
+        raise ValueError(f"{what}: {t.numel()} elements, the call needs {n}")
+    return t
+
+
+def _bytes(t, what):
+    """A workspace of any dtype -> its size in bytes."""
+    if not _on_gpu(t):
+        raise TypeError(f"{what}: expected a contiguous CUDA tensor")
+    return t.numel() * t.element_size()
 
 
 def bg_doubles(o: Options) -> int:
@@ -167,9 +189,11 @@ def perturb_workspace_bytes(B: int, Nk: int, o: Options) -> int:
 def abcmb_background_tables(params: torch.Tensor, o: Options, out: torch.Tensor | None = None):
     """params [B, 6] (omega_b, omega_cdm, h, n_s, ln(1e10 A_s), tau_reion) -> bg [B, bg_doubles]."""
     _dev(params)
-    B = params.shape[0]
-    bg = out if out is not None else torch.empty((B, bg_doubles(o)), dtype=torch.float64,
-                                                 device=params.device)
+    if params.dim() != 2 or params.shape[1] != NPARAM:
+        raise ValueError(f"params: expected [B, {NPARAM}], got {list(params.shape)}")
+    B, n = params.shape[0], bg_doubles(o)
+    bg = out if out is not None else torch.empty((B, n), dtype=torch.float64, device=params.device)
+    _fits(bg, B * n, "bg")
     _check(lib().abcmb_background_tables(B, _ptr(params), ctypes.byref(o), _ptr(bg), _stream()),
            "abcmb_background_tables")
     return bg
@@ -181,6 +205,7 @@ def abcmb_perturb(bg: torch.Tensor, k: torch.Tensor, o: Options, S=None, status=
     (steps taken, IMEX substeps)."""
     _dev(bg), _dev(k)
     B, Nk = bg.shape[0], k.shape[0]
+    _fits(bg, B * bg_doubles(o), "bg")
     dev = bg.device
     if S is None:
         S = torch.empty((B, Nk, o.n_tau, 3), dtype=torch.float64, device=dev)
@@ -188,10 +213,13 @@ def abcmb_perturb(bg: torch.Tensor, k: torch.Tensor, o: Options, S=None, status=
         status = torch.empty((B, Nk), dtype=torch.int32, device=dev)
     if steps is None:
         steps = torch.empty((B, Nk, 2), dtype=torch.int32, device=dev)
+    _fits(S, B * Nk * o.n_tau * 3, "S")
+    _fits(status, B * Nk, "mode_status", torch.int32)
+    _fits(steps, B * Nk * 2, "steps", torch.int32)
     nbytes = perturb_workspace_bytes(B, Nk, o)
     if workspace is None and nbytes > 0:  # hierarchies > 63 and massive neutrinos
         workspace = torch.empty(nbytes // 8, dtype=torch.float64, device=dev)
-    wbytes = 0 if workspace is None else workspace.numel() * 8
+    wbytes = 0 if workspace is None else _bytes(workspace, "workspace")
     _check(lib().abcmb_perturb(B, _ptr(bg), _ptr(k), Nk, ctypes.byref(o), _ptr(S), _ptr(status),
                                _ptr(steps), _ptr(workspace), wbytes, _stream()),
            "abcmb_perturb")
@@ -201,9 +229,13 @@ def abcmb_perturb(bg: torch.Tensor, k: torch.Tensor, o: Options, S=None, status=
 def abcmb_perturb_noalloc(bg: torch.Tensor, k: torch.Tensor, o: Options, S, status, steps=None):
     """abcmb_perturb without a workspace, for callers that cannot allocate
     device memory: hierarchies > 63 keep their working vectors in the
-    library's static scratch.  Outputs must be preallocated by the caller;
-    returns the C status code."""
-    _dev(bg), _dev(k), _dev(S)
+    library's static scratch.  Outputs must be preallocated by the caller
+    ([B, Nk, n_tau, 3], [B, Nk] and [B, Nk, 2] as abcmb_perturb; their
+    sizes are not checked here, since a problem beyond the scratch is
+    refused before they are touched); returns the C status code."""
+    _dev(bg), _dev(k), _dev(S), _dev(status, torch.int32)
+    if steps is not None:
+        _dev(steps, torch.int32)
     B, Nk = bg.shape[0], k.shape[0]
     return lib().abcmb_perturb_noalloc(B, _ptr(bg), _ptr(k), Nk, ctypes.byref(o), _ptr(S), _ptr(status),
                                        _ptr(steps), _stream())
@@ -213,9 +245,12 @@ def abcmb_matter_pk(bg: torch.Tensor, k: torch.Tensor, o: Options, z: float = 0.
     """-> P(k, z) [B, Nk] in Mpc^3, mode status [B, Nk] int32."""
     _dev(bg), _dev(k)
     B, Nk = bg.shape[0], k.shape[0]
+    _fits(bg, B * bg_doubles(o), "bg")
     Pk = out if out is not None else torch.empty((B, Nk), dtype=torch.float64, device=bg.device)
     if status is None:
         status = torch.empty((B, Nk), dtype=torch.int32, device=bg.device)
+    _fits(Pk, B * Nk, "Pk")
+    _fits(status, B * Nk, "mode_status", torch.int32)
     _check(lib().abcmb_matter_pk(B, _ptr(bg), _ptr(k), Nk, ctypes.byref(o), float(z), _ptr(Pk), _ptr(status),
                                  _stream()),
            "abcmb_matter_pk")
@@ -226,8 +261,11 @@ def abcmb_project(bg: torch.Tensor, S: torch.Tensor, k: torch.Tensor, o: Options
     """-> Delta [B, Nk, lmax_cl - 1, 2] (T, E) for l = 2..lmax_cl."""
     _dev(bg), _dev(S), _dev(k)
     B, Nk = bg.shape[0], k.shape[0]
+    _fits(bg, B * bg_doubles(o), "bg")
+    _fits(S, B * Nk * o.n_tau * 3, "S")
     D = out if out is not None else torch.empty((B, Nk, o.lmax_cl - 1, 2), dtype=torch.float64,
                                                 device=bg.device)
+    _fits(D, B * Nk * (o.lmax_cl - 1) * 2, "Delta")
     _check(lib().abcmb_project(B, _ptr(bg), _ptr(S), _ptr(k), Nk, ctypes.byref(o), _ptr(D), _stream()),
            "abcmb_project")
     return D
@@ -238,8 +276,11 @@ def abcmb_project_interp(bg: torch.Tensor, S: torch.Tensor, k: torch.Tensor, kt:
     """Sources S at the ODE nodes k -> Delta [B, len(kt), lmax_cl - 1, 2] at kt."""
     _dev(bg), _dev(S), _dev(k), _dev(kt)
     B, Nk, Nkt = bg.shape[0], k.shape[0], kt.shape[0]
+    _fits(bg, B * bg_doubles(o), "bg")
+    _fits(S, B * Nk * o.n_tau * 3, "S")
     D = out if out is not None else torch.empty((B, Nkt, o.lmax_cl - 1, 2), dtype=torch.float64,
                                                 device=bg.device)
+    _fits(D, B * Nkt * (o.lmax_cl - 1) * 2, "Delta")
     _check(lib().abcmb_project_interp(B, _ptr(bg), _ptr(S), _ptr(k), Nk, _ptr(kt), Nkt, ctypes.byref(o), _ptr(D),
                                       _stream()),
            "abcmb_project_interp")
@@ -250,9 +291,14 @@ def abcmb_lens(Cl: torch.Tensor, Cpsi: torch.Tensor, lmax_out: int, n_mu: int | 
     """Cl [B, 3, L - 1] (TT, TE, EE for l = 2..L, as abcmb_cl writes them), Cpsi [B, L - 1] ->
     lensed [B, 4, lmax_out - 1] (TT, TE, EE, BB)."""
     _dev(Cl), _dev(Cpsi)
+    if Cl.dim() != 3 or Cl.shape[1] != 3:
+        raise ValueError(f"Cl: expected [B, 3, L - 1], got {list(Cl.shape)}")
     B, L = Cl.shape[0], Cl.shape[2] + 1
+    _fits(Cpsi, B * (L - 1), "Cpsi")
     n_mu = n_mu or L + 100
-    D = out if out is not None else torch.empty((B, 4, lmax_out - 1), dtype=torch.float64, device=Cl.device)
+    D = out if out is not None else torch.empty((B, 4, max(lmax_out - 1, 0)), dtype=torch.float64,
+                                                device=Cl.device)
+    _fits(D, B * 4 * max(lmax_out - 1, 0), "Cl_lensed")
     _check(lib().abcmb_lens(B, _ptr(Cl), L, _ptr(Cpsi), int(lmax_out), int(n_mu), _ptr(D), _stream()),
            "abcmb_lens")
     return D
@@ -262,8 +308,11 @@ def abcmb_delta_m_nodes(bg: torch.Tensor, k: torch.Tensor, o: Options, out=None,
     """-> (delta_m [B, Nk, n_tau] at the tau nodes, mode_status [B, Nk])."""
     _dev(bg), _dev(k)
     B, Nk = bg.shape[0], k.shape[0]
+    _fits(bg, B * bg_doubles(o), "bg")
     D = out if out is not None else torch.empty((B, Nk, o.n_tau), dtype=torch.float64, device=bg.device)
     st = status if status is not None else torch.empty((B, Nk), dtype=torch.int32, device=bg.device)
+    _fits(D, B * Nk * o.n_tau, "Dm")
+    _fits(st, B * Nk, "mode_status", torch.int32)
     _check(lib().abcmb_delta_m_nodes(B, _ptr(bg), _ptr(k), Nk, ctypes.byref(o), _ptr(D), _ptr(st), _stream()),
            "abcmb_delta_m_nodes")
     return D, st
@@ -273,7 +322,10 @@ def abcmb_cl_psi(bg: torch.Tensor, Dm: torch.Tensor, k: torch.Tensor, o: Options
     """Limber C_l^psi [B, lmax - 1] for l = 2..lmax from delta_m at the nodes."""
     _dev(bg), _dev(Dm), _dev(k)
     B, Nk = bg.shape[0], k.shape[0]
-    C = out if out is not None else torch.empty((B, lmax - 1), dtype=torch.float64, device=bg.device)
+    _fits(bg, B * bg_doubles(o), "bg")
+    _fits(Dm, B * Nk * o.n_tau, "Dm")
+    C = out if out is not None else torch.empty((B, max(lmax - 1, 0)), dtype=torch.float64, device=bg.device)
+    _fits(C, B * max(lmax - 1, 0), "Cpsi")
     _check(lib().abcmb_cl_psi(B, _ptr(bg), _ptr(Dm), _ptr(k), Nk, ctypes.byref(o), int(lmax), _ptr(C),
                               _stream()), "abcmb_cl_psi")
     return C
@@ -293,8 +345,11 @@ def abcmb_cl(bg: torch.Tensor, Delta: torch.Tensor, k: torch.Tensor, o: Options,
     """-> C_l [B, 3, lmax_cl - 1] (TT, TE, EE) for l = 2..lmax_cl."""
     _dev(bg), _dev(Delta), _dev(k)
     B, Nk = bg.shape[0], k.shape[0]
+    _fits(bg, B * bg_doubles(o), "bg")
+    _fits(Delta, B * Nk * (o.lmax_cl - 1) * 2, "Delta")
     C = out if out is not None else torch.empty((B, 3, o.lmax_cl - 1), dtype=torch.float64,
                                                 device=bg.device)
+    _fits(C, B * 3 * (o.lmax_cl - 1), "Cl")
     _check(lib().abcmb_cl(B, _ptr(bg), _ptr(Delta), _ptr(k), Nk, ctypes.byref(o), _ptr(C), _stream()),
            "abcmb_cl")
     return C
@@ -304,10 +359,11 @@ def abcmb_project_mixed(bg: torch.Tensor, S: torch.Tensor, k: torch.Tensor, o: O
     """FP32 projection -> Delta32 [B, Nk, lmax_cl - 1, 2] float32 (T, E)."""
     _dev(bg), _dev(S), _dev(k)
     B, Nk = bg.shape[0], k.shape[0]
+    _fits(bg, B * bg_doubles(o), "bg")
+    _fits(S, B * Nk * o.n_tau * 3, "S")
     D = out if out is not None else torch.empty((B, Nk, o.lmax_cl - 1, 2), dtype=torch.float32,
                                                 device=bg.device)
-    if D.dtype != torch.float32:
-        raise TypeError("Delta32 must be float32")
+    _fits(D, B * Nk * (o.lmax_cl - 1) * 2, "Delta32", torch.float32)
     _check(lib().abcmb_project_mixed(B, _ptr(bg), _ptr(S), _ptr(k), Nk, ctypes.byref(o), _ptr(D), _stream()),
            "abcmb_project_mixed")
     return D
@@ -316,11 +372,12 @@ def abcmb_project_mixed(bg: torch.Tensor, S: torch.Tensor, k: torch.Tensor, o: O
 def abcmb_cl_mixed(bg: torch.Tensor, Delta32: torch.Tensor, k: torch.Tensor, o: Options, out=None):
     """FP32 k-quadrature with Kahan sums -> C_l [B, 3, lmax_cl - 1] float64."""
     _dev(bg), _dev(Delta32, torch.float32), _dev(k)
-    if Delta32.dtype != torch.float32:
-        raise TypeError("Delta32 must be float32")
     B, Nk = bg.shape[0], k.shape[0]
+    _fits(bg, B * bg_doubles(o), "bg")
+    _fits(Delta32, B * Nk * (o.lmax_cl - 1) * 2, "Delta32", torch.float32)
     C = out if out is not None else torch.empty((B, 3, o.lmax_cl - 1), dtype=torch.float64,
                                                 device=bg.device)
+    _fits(C, B * 3 * (o.lmax_cl - 1), "Cl")
     _check(lib().abcmb_cl_mixed(B, _ptr(bg), _ptr(Delta32), _ptr(k), Nk, ctypes.byref(o), _ptr(C), _stream()),
            "abcmb_cl_mixed")
     return C
@@ -333,11 +390,13 @@ def grad_workspace_bytes(B: int, Nk: int, o: Options) -> int:
     return n
 
 
-def _plan_ptr(plan):
+def _plan_ptr(plan, B, Nk):
     if plan is None:
         return None
     if not (isinstance(plan, np.ndarray) and plan.dtype == np.int64 and plan.flags.c_contiguous):
         raise TypeError("plan: a contiguous int64 numpy array from grad_plan")
+    if plan.size < 2 * B * Nk + 2:
+        raise ValueError(f"plan: {plan.size} entries, a plan of {B} x {Nk} modes has {2 * B * Nk + 2}")
     return plan.ctypes.data_as(ctypes.c_void_p)
 
 
@@ -346,11 +405,14 @@ def abcmb_grad_count_steps(bg: torch.Tensor, k: torch.Tensor, o: Options, S=None
     -> S, mode status, accepted steps per mode [B, Nk] (device, int32)."""
     _dev(bg), _dev(k)
     B, Nk = bg.shape[0], k.shape[0]
+    _fits(bg, B * bg_doubles(o), "bg")
     dev = bg.device
     if S is None:
         S = torch.empty((B, Nk, o.n_tau, 3), dtype=torch.float64, device=dev)
     if status is None:
         status = torch.empty((B, Nk), dtype=torch.int32, device=dev)
+    _fits(S, B * Nk * o.n_tau * 3, "S")
+    _fits(status, B * Nk, "mode_status", torch.int32)
     acc = torch.empty((B, Nk), dtype=torch.int32, device=dev)
     nb = lib().abcmb_grad_count_workspace_bytes(B, Nk, ctypes.byref(o))
     if nb == 0:
@@ -381,42 +443,57 @@ def abcmb_perturb_taped(bg: torch.Tensor, k: torch.Tensor, o: Options, workspace
     grad_plan returned with plan).  -> S, mode status."""
     _dev(bg), _dev(k)
     B, Nk = bg.shape[0], k.shape[0]
+    _fits(bg, B * bg_doubles(o), "bg")
     dev = bg.device
     if S is None:
         S = torch.empty((B, Nk, o.n_tau, 3), dtype=torch.float64, device=dev)
     if status is None:
         status = torch.empty((B, Nk), dtype=torch.int32, device=dev)
+    _fits(S, B * Nk * o.n_tau * 3, "S")
+    _fits(status, B * Nk, "mode_status", torch.int32)
     _check(lib().abcmb_perturb_taped(B, _ptr(bg), _ptr(k), Nk, ctypes.byref(o), _ptr(S), _ptr(status),
-                                     _ptr(workspace), workspace.numel() * workspace.element_size(), _plan_ptr(plan),
+                                     _ptr(workspace), _bytes(workspace, "workspace"), _plan_ptr(plan, B, Nk),
                                      _stream()),
            "abcmb_perturb_taped")
     return S, status
 
 
 def abcmb_perturb_adjoint(bg, k, o: Options, Sbar, workspace, recbar, plan=None):
-    _dev(bg), _dev(k), _dev(Sbar), _dev(recbar)
-    _check(lib().abcmb_perturb_adjoint(bg.shape[0], _ptr(bg), _ptr(k), k.shape[0], ctypes.byref(o), _ptr(Sbar),
-                                       _ptr(workspace), workspace.numel() * workspace.element_size(),
-                                       _plan_ptr(plan), _ptr(recbar), _stream()),
+    _dev(bg), _dev(k)
+    B, Nk, n = bg.shape[0], k.shape[0], bg_doubles(o)
+    _fits(bg, B * n, "bg"), _fits(Sbar, B * Nk * o.n_tau * 3, "Sbar"), _fits(recbar, B * n, "recbar")
+    _check(lib().abcmb_perturb_adjoint(B, _ptr(bg), _ptr(k), Nk, ctypes.byref(o), _ptr(Sbar),
+                                       _ptr(workspace), _bytes(workspace, "workspace"),
+                                       _plan_ptr(plan, B, Nk), _ptr(recbar), _stream()),
            "abcmb_perturb_adjoint")
     return recbar
 
 
 def abcmb_cl_adjoint(bg, Delta, k, o: Options, Clbar, recbar, Deltabar=None):
-    _dev(bg), _dev(Delta), _dev(k), _dev(Clbar), _dev(recbar)
+    _dev(bg), _dev(k)
+    B, Nk, n = bg.shape[0], k.shape[0], bg_doubles(o)
+    nD = B * Nk * (o.lmax_cl - 1) * 2
+    _fits(bg, B * n, "bg"), _fits(Delta, nD, "Delta"), _fits(recbar, B * n, "recbar")
+    _fits(Clbar, B * 3 * (o.lmax_cl - 1), "Clbar")
     if Deltabar is None:
         Deltabar = torch.empty_like(Delta)
-    _check(lib().abcmb_cl_adjoint(bg.shape[0], _ptr(bg), _ptr(Delta), _ptr(k), k.shape[0], ctypes.byref(o),
+    _fits(Deltabar, nD, "Deltabar")
+    _check(lib().abcmb_cl_adjoint(B, _ptr(bg), _ptr(Delta), _ptr(k), Nk, ctypes.byref(o),
                                   _ptr(Clbar), _ptr(Deltabar), _ptr(recbar), _stream()),
            "abcmb_cl_adjoint")
     return Deltabar
 
 
 def abcmb_project_adjoint(bg, S, k, o: Options, Deltabar, recbar, Sbar=None):
-    _dev(bg), _dev(S), _dev(k), _dev(Deltabar), _dev(recbar)
+    _dev(bg), _dev(k)
+    B, Nk, n = bg.shape[0], k.shape[0], bg_doubles(o)
+    nS = B * Nk * o.n_tau * 3
+    _fits(bg, B * n, "bg"), _fits(S, nS, "S"), _fits(recbar, B * n, "recbar")
+    _fits(Deltabar, B * Nk * (o.lmax_cl - 1) * 2, "Deltabar")
     if Sbar is None:
         Sbar = torch.empty_like(S)
-    _check(lib().abcmb_project_adjoint(bg.shape[0], _ptr(bg), _ptr(S), _ptr(k), k.shape[0], ctypes.byref(o),
+    _fits(Sbar, nS, "Sbar")
+    _check(lib().abcmb_project_adjoint(B, _ptr(bg), _ptr(S), _ptr(k), Nk, ctypes.byref(o),
                                        _ptr(Deltabar), _ptr(Sbar), _ptr(recbar), _stream()),
            "abcmb_project_adjoint")
     return Sbar
@@ -425,6 +502,8 @@ def abcmb_project_adjoint(bg, S, k, o: Options, Deltabar, recbar, Sbar=None):
 def abcmb_param_stencil(params, rel_step: float, floor_abs: float):
     """-> h [B, 6], params_plus [B * 6, 6], params_minus [B * 6, 6] (abcmb.h)."""
     _dev(params)
+    if params.dim() != 2 or params.shape[1] != NPARAM:
+        raise ValueError(f"params: expected [B, {NPARAM}], got {list(params.shape)}")
     B = params.shape[0]
     h = torch.empty((B, NPARAM), dtype=torch.float64, device=params.device)
     pp = torch.empty((B * NPARAM, NPARAM), dtype=torch.float64, device=params.device)
@@ -435,10 +514,13 @@ def abcmb_param_stencil(params, rel_step: float, floor_abs: float):
 
 
 def abcmb_record_vjp(o: Options, recbar, rec_plus, rec_minus, h, grad=None):
-    _dev(recbar), _dev(rec_plus), _dev(rec_minus), _dev(h)
-    B = recbar.shape[0]
+    _dev(recbar)
+    B, n = recbar.shape[0], bg_doubles(o)
+    _fits(recbar, B * n, "recbar"), _fits(h, B * NPARAM, "h")
+    _fits(rec_plus, B * NPARAM * n, "rec_plus"), _fits(rec_minus, B * NPARAM * n, "rec_minus")
     if grad is None:
         grad = torch.empty((B, NPARAM), dtype=torch.float64, device=recbar.device)
+    _fits(grad, B * NPARAM, "grad")
     _check(lib().abcmb_record_vjp(B, ctypes.byref(o), _ptr(recbar), _ptr(rec_plus), _ptr(rec_minus), _ptr(h),
                                   _ptr(grad), _stream()),
            "abcmb_record_vjp")
