@@ -19,10 +19,13 @@
  *
  * Conventions shared by every entry point
  *   - Every pointer argument is a DEVICE pointer allocated by the caller
- *     (the library allocates nothing and keeps no state between calls), unless
- *     its name ends in _host.  Every array is C-contiguous float64 (int32 for
- *     status/step arrays, float32 where a name ends in 32) in the layout
- *     stated at each argument.
+ *     (the library allocates nothing; apart from a server's handle and the
+ *     static scratch of abcmb_perturb_noalloc it keeps no state between
+ *     calls), unless its name ends in _host.  Every array is C-contiguous
+ *     float64 (int32 for status/step arrays, float32 where a name ends in 32)
+ *     in the layout stated at each argument, and must hold at least the
+ *     elements that layout gives: a plain pointer carries no extent, so the
+ *     library cannot check it (the Python binding does, before each call).
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Calls only enqueue work on it; results are valid once the
  *     stream has been synchronised.
