@@ -674,7 +674,9 @@ class Pipeline:
         return self.C
 
     def run_host(self, params_host: np.ndarray, cl_host: torch.Tensor | None = None):
-        """End to end from host parameters (pinned copy in, C_l copy out)."""
+        """End to end from host parameters (pinned copy in, C_l copy out into a
+        pinned host tensor).  Asynchronous like every call here: synchronise
+        the current stream before reading the returned tensor."""
         src = torch.from_numpy(np.ascontiguousarray(params_host, dtype=np.float64))
         if not src.is_pinned():
             src = src.pin_memory()
