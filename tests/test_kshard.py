@@ -60,7 +60,7 @@ def _rank_main(rank, world, port, out):
 def test_partial_cl_sum_equals_single_pass(world):
     import oracle as O
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:  # no fork of a threaded process
         out = m.dict()
         mp.start_processes(_rank_main, args=(world, port, out), nprocs=world, start_method="spawn")
         res = dict(out)

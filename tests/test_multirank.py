@@ -39,7 +39,7 @@ def _rank_main(rank, world, port, out):
 
 def test_two_cpu_ranks_weak_scaling_and_max_timing():
     world, port = 2, _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:  # no fork of a threaded process
         out = m.dict()
         mp.start_processes(_rank_main, args=(world, port, out), nprocs=world, start_method="spawn")
         res = dict(out)
