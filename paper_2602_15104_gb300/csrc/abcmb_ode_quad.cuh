@@ -54,7 +54,11 @@ constexpr int kQLmax = 63;  // highest hierarchy truncation (4 lanes x 16 moment
 __device__ __forceinline__ double rcp_approx(double x)
 {
     double r;
+#ifdef __CUDA_ARCH__
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+#else
+    r = 1.0 / x; // host builds of this header (the CPU tests)
+#endif
     return r;
 }
 

@@ -1,0 +1,116 @@
+// Host build of the four-lane perturbation kernel (abcmb_ode_quad.cuh, the
+// path abcmb_perturb runs for hierarchies up to 63) for the CPU parity tests:
+// each one-warp CTA of perturb_quad_kernel runs as 32 host threads under
+// warp_emu.h, CTAs one after another.  The per-CTA setup below is the
+// kernel's (streaming coefficients, mode numbering, shared-memory split); the
+// integration is the header's own quad_modes.
+#include "warp_emu.h"
+
+#include <thread>
+#include <vector>
+
+#include "abcmb_ode_quad.cuh"
+
+thread_local EmuDim3 threadIdx, blockIdx, blockDim;
+namespace emu {
+thread_local Warp *warp = nullptr;
+thread_local int lane = 0;
+thread_local int parity = 0;
+} // namespace emu
+
+using namespace abcmb;
+
+extern "C" long h_bg_len(int n_tau) { return ABCMB_BG_LEN(n_tau); }
+
+extern "C" void h_build_bg(const double *p, int n_tau, double *rec) { build_background(p, rec, n_tau, 0, 1); }
+
+namespace {
+
+struct Args {
+    int B, Nk;
+    const double *bg;
+    long len;
+    const double *k;
+    int L;
+    double rtol, atol;
+    int max_steps;
+    double efloor;
+    double *S;
+    int *status, *steps;
+    long nb8, M8;
+};
+
+// one CTA of perturb_quad_kernel<P, 1>, lane `lane` of its warp
+template <int P>
+void cta_lane(const Args &a, const QCoef &qc, double *qsm, long block, int lane)
+{
+    const double sw[3] = {1.0, 1.0, 1.0};
+    const long M = (long)a.B * a.Nk;
+    if constexpr (P >= 8) {
+        if (block < a.nb8) {
+            constexpr int P8 = P / 2;
+            constexpr int E8 = 3 * P8 + 1;
+            const long mi = block * 4 + (lane >> 3);
+            quad_modes<P8, false, false, 8>(mi, a.M8, a.B, a.Nk, a.bg, a.len, a.k, qc, a.rtol, a.atol, a.max_steps,
+                                            sw, a.S, a.status, a.steps, qsm, qsm + (1 + kQK) * E8 * 32, a.efloor);
+            return;
+        }
+    }
+    constexpr int E = 3 * P + 1;
+    const long mi = a.M8 + (block - a.nb8) * 8 + (lane >> 2);
+    quad_modes<P>(mi, M, a.B, a.Nk, a.bg, a.len, a.k, qc, a.rtol, a.atol, a.max_steps, sw, a.S, a.status, a.steps,
+                  qsm, qsm + (1 + kQK) * E * 32, a.efloor);
+}
+
+template <int P>
+void run(const Args &a)
+{
+    std::vector<double> qsm(quad_smem_per_warp<P>() / sizeof(double));
+    double cS[3 * 64], cB[3 * 64];
+    const int Ls[3] = {a.L, a.L, a.L};
+    blockDim.x = 1; // one thread fills the coefficient tables
+    threadIdx.x = 0;
+    fill_coef(cS, cB, Ls);
+    QCoef qc;
+    qc.S = cS;
+    qc.Bc = cB;
+    for (int c = 0; c < 3; c++) {
+        qc.L[c] = a.L;
+        qc.L1[c] = a.L + 1.0;
+    }
+    const long M = (long)a.B * a.Nk;
+    const long blocks = a.nb8 + (M - a.M8 + 7) / 8;
+    for (long blk = 0; blk < blocks; blk++) {
+        emu::Warp w;
+        std::vector<std::thread> lanes;
+        for (int l = 0; l < 32; l++)
+            lanes.emplace_back([&, l] {
+                emu::warp = &w;
+                emu::lane = l;
+                emu::parity = 0;
+                threadIdx.x = l;
+                blockIdx.x = (unsigned)blk;
+                blockDim.x = 32;
+                cta_lane<P>(a, qc, qsm.data(), blk, l);
+            });
+        for (auto &t : lanes) t.join();
+    }
+}
+
+} // namespace
+
+// S[B][Nk][n_tau][3], status[B][Nk], steps[B][Nk][2] of the B x Nk modes, all
+// three hierarchies truncated at L (<= 63), the n_wide highest k on eight lanes
+extern "C" void h_quad(int B, const double *bg, const double *k, int Nk, int L, double rtol, double atol,
+                       int max_steps, double efloor, int n_wide, double *S, int *status, int *steps)
+{
+    Args a{B, Nk, bg, (long)ABCMB_BG_LEN((long)bg[ABCMB_S_NTAU]), k, L, rtol, atol, max_steps, efloor, S, status,
+           steps, 0, 0};
+    const int P = L <= 15 ? 4 : (L <= 31 ? 8 : 16);
+    const long kw = P >= 8 ? (n_wide > Nk ? Nk : n_wide) : 0;
+    a.M8 = (long)B * kw;
+    a.nb8 = (a.M8 + 3) / 4;
+    if (P == 4) run<4>(a);
+    else if (P == 8) run<8>(a);
+    else run<16>(a);
+}
