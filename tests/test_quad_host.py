@@ -2,10 +2,12 @@
 path abcmb_perturb, and so the benchmark, runs for hierarchies up to 63),
 built for the host with each one-warp CTA's 32 lanes run as threads
 (tests/host/warp_emu.h), against the oracle's CMB sources (App. B.4 eq.
-source_functions): the initial state, the IMEX / Gragg extrapolation spread
-over four (or eight) lanes per mode, the background read from the record's
-cubic section, dense output at the tau nodes, the error norm's group floor,
-the step budget.  The same kernel runs on a GB300 in tests/test_gpu_*.py.
+source_functions), matter power spectrum (App. B.4 eq. PK) and matter
+contrast at the tau nodes: the initial state, the IMEX / Gragg extrapolation
+spread over four (or eight) lanes per mode, the background read from the
+record's cubic section, dense output at the tau nodes, the error norm's group
+floor, the step budget.  The same kernels run on a GB300 in
+tests/test_gpu_*.py.
 """
 import ctypes
 import os
@@ -36,6 +38,10 @@ def H(tmp_path_factory):
     L.h_build_bg.argtypes = [P, ctypes.c_int, P]
     L.h_quad.argtypes = [ctypes.c_int, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                          ctypes.c_int, ctypes.c_double, ctypes.c_int, P, P, P]
+    L.h_quad_pk.argtypes = [ctypes.c_int, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                            ctypes.c_int, ctypes.c_double, ctypes.c_double, P, P, P]
+    L.h_quad_dm.argtypes = [ctypes.c_int, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                            ctypes.c_int, ctypes.c_double, P, P]
     return L
 
 
@@ -118,3 +124,39 @@ def test_step_budget_ends_the_mode_with_its_status(H):
     # the nodes reached keep their sources (about half of them here), the rest are zero
     live = np.nonzero(np.abs(S[0, 0]).sum(axis=1))[0]
     assert 0 < live.size < N_TAU and np.all(S[0, 0, live.max() + 1:] == 0.0)
+
+
+def test_matter_power_spectrum_against_oracle(H):
+    # the P(k) form (pk_quad_kernel): integrate to a = 1/(1+z) without the
+    # sources; P is quadratic in delta_m, 1e-5 relative at rtol 1e-6
+    # (measured 2.8e-7; the GPU test also runs z = 2)
+    z = 0.0
+    params = np.vstack([W.SMALL_TT.params(), W.BATCH64.params()[[17]]])
+    k = np.array([1e-5, 1e-4, 1e-3, 6e-3, 0.02, 0.05])
+    bg = records(H, params, 400)
+    Pk = np.zeros((2, k.size))
+    st = np.full((2, k.size), -1, dtype=np.int32)
+    H.h_quad_pk(2, bg.ctypes.data_as(P), k.ctypes.data_as(P), k.size, 12, 1e-6, 1e-12, 2_000_000, 1e-4, z,
+                Pk.ctypes.data_as(P), st.ctypes.data_as(P), None)
+    assert np.all(st == 0)
+    for b in range(2):
+        ref = O.pk(params[b], k, z, O.opts(lmax=12))
+        assert np.all(np.abs(Pk[b] / ref - 1.0) < 1e-5), (b, Pk[b] / ref - 1.0)
+
+
+def test_matter_contrast_at_the_nodes_against_oracle(H):
+    # the delta_m form (dm_quad_kernel): every node landed or Hermite-interpolated;
+    # errors measured against the running maximum of |delta_m| (it grows)
+    params = np.vstack([W.SMALL_TT.params(), W.BATCH64.params()[[17]]])
+    k = np.array([1e-4, 1e-3, 0.01, 0.05])
+    n_tau = 400
+    bg = records(H, params, n_tau)
+    Dm = np.zeros((2, k.size, n_tau))
+    st = np.full((2, k.size), -1, dtype=np.int32)
+    H.h_quad_dm(2, bg.ctypes.data_as(P), k.ctypes.data_as(P), k.size, 12, 1e-6, 1e-12, 2_000_000, 1e-4,
+                Dm.ctypes.data_as(P), st.ctypes.data_as(P))
+    assert np.all(st == 0)
+    for b in range(2):
+        ref = O.delta_m_nodes(params[b], k, n_tau, O.opts(lmax=12))
+        err = np.abs(Dm[b] - ref) / np.maximum.accumulate(np.abs(ref), axis=1)
+        assert err.max() < 2e-5, (b, err.max())
