@@ -307,7 +307,7 @@ project_adjoint_kernel(int B, int Nk, const double *__restrict__ bg, long len, c
         const double x = kk * (tau0 - nd[N_TAU]);
         const double u = 1.0 / x;
         const double s0 = Sm[3 * i], s1 = Sm[3 * i + 1], sp = Sm[3 * i + 2];
-        // the forward kernel's cutoff and starting values (abcmb_spectra.cu)
+        // the forward kernel's cutoff and starting values (abcmb_spectra.cuh)
         const bool series = x < 1.0;
         // the series path stops at l = 30 in the forward kernel
         const int lc = series ? min(bessel_cut((float)x, lmax), 30) : bessel_cut((float)x, lmax);

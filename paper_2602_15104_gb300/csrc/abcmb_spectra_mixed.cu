@@ -11,7 +11,7 @@
 //    rounding is amplified by the growing solution past the turning point,
 //    and a float 1/x alone shifts the phase by x 2^-24 (1e-4 at x ~ 2000).
 //  * The collapsed temperature kernel (A0 + l A1 + l^2 A2) j_l + B j_{l-1}
-//    and the E kernel E j_l (see abcmb_spectra.cu) in FP32 on the float j_l;
+//    and the E kernel E j_l (see abcmb_spectra.cuh) in FP32 on the float j_l;
 //    per-lane partial sums over 4 nodes, a 32-lane butterfly reduce-scatter
 //    over 128 nodes, then a Kahan-compensated FP32 accumulator per
 //    (l, T/E) in shared memory across the node groups.  One warp per
@@ -34,7 +34,7 @@ constexpr int kLB = 16;     // l per block
 constexpr int kSerL = 32;   // series table rows (l)
 constexpr float kSeriesX = 1.0f;
 
-// Debye cutoff of abcmb_spectra.cu (exponent 16, plus 2 ln(1/x) below x = 1)
+// Debye cutoff of abcmb_spectra.cuh (exponent 16, plus 2 ln(1/x) below x = 1)
 __device__ __forceinline__ int bessel_cut_f(float x, int lmax)
 {
     if (x > (float)lmax + 200.0f) return lmax;

@@ -7,17 +7,7 @@
 // split); the integration is the header's own quad_modes.
 #include "warp_emu.h"
 
-#include <thread>
-#include <vector>
-
 #include "abcmb_ode_quad.cuh"
-
-thread_local EmuDim3 threadIdx, blockIdx, blockDim;
-namespace emu {
-thread_local Warp *warp = nullptr;
-thread_local int lane = 0;
-thread_local int parity = 0;
-} // namespace emu
 
 using namespace abcmb;
 
@@ -102,22 +92,12 @@ void run(const Args &a, int form = 0, double x_out = 0.0, double *out = nullptr)
     }
     const long M = (long)a.B * a.Nk;
     const long blocks = a.nb8 + (M - a.M8 + 7) / 8;
-    for (long blk = 0; blk < blocks; blk++) {
-        emu::Warp w;
-        std::vector<std::thread> lanes;
-        for (int l = 0; l < 32; l++)
-            lanes.emplace_back([&, l] {
-                emu::warp = &w;
-                emu::lane = l;
-                emu::parity = 0;
-                threadIdx.x = l;
-                blockIdx.x = (unsigned)blk;
-                blockDim.x = 32;
-                if (form == 0) cta_lane<P>(a, qc, qsm.data(), blk, l);
-                else cta_lane_form<P>(a, qc, qsm.data(), blk, l, form, x_out, out);
-            });
-        for (auto &t : lanes) t.join();
-    }
+    for (long blk = 0; blk < blocks; blk++)
+        emu::run_cta((unsigned)blk, 0, 32, [&] {
+            const int l = (int)threadIdx.x;
+            if (form == 0) cta_lane<P>(a, qc, qsm.data(), blk, l);
+            else cta_lane_form<P>(a, qc, qsm.data(), blk, l, form, x_out, out);
+        });
 }
 
 Args args_of(int B, const double *bg, const double *k, int Nk, int L, double rtol, double atol, int max_steps,
