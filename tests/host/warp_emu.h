@@ -31,6 +31,9 @@
 struct alignas(16) double2 {
     double x, y;
 };
+struct alignas(8) float2 {
+    float x, y;
+};
 
 struct EmuDim3 {
     unsigned x = 0, y = 0, z = 0;
@@ -188,6 +191,10 @@ inline double __hiloint2double(int hi, int lo)
     return emu::from_bits<double>(((uint64_t)(uint32_t)hi << 32) | (uint32_t)lo);
 }
 inline float __powf(float x, float y) { return powf(x, y); }
+// single-precision operations rounded once each (this build contracts nothing)
+inline float __fadd_rn(float a, float b) { return a + b; }
+inline float __fsub_rn(float a, float b) { return a - b; }
+inline float __fmul_rn(float a, float b) { return a * b; }
 inline int max(int a, int b) { return a > b ? a : b; }
 inline int min(int a, int b) { return a < b ? a : b; }
 
