@@ -446,10 +446,11 @@ ABCMB_HD double bisect(F f, double target, double lo, double hi, bool *ok)
 
 
 // ---- lane helpers: on the device the builder runs on one warp per cosmology,
-// on a host (debugging) on one thread ----
+// on a host on one thread, or on an emulated warp where the host build
+// defines ABCMB_HOST_WARPS (the CPU tests) ----
 ABCMB_HD double lane_sum(double v)
 {
-#ifdef __CUDA_ARCH__
+#if defined(__CUDA_ARCH__) || defined(ABCMB_HOST_WARPS)
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
 #endif
     return v;
@@ -459,7 +460,7 @@ ABCMB_HD double lane_sum(double v)
 ABCMB_HD double lane_scan_excl(double v, int lane, int dir)
 {
     double acc = 0.0;
-#ifdef __CUDA_ARCH__
+#if defined(__CUDA_ARCH__) || defined(ABCMB_HOST_WARPS)
     for (int s = 0; s < 32; s++) {
         const int src = dir > 0 ? s : 31 - s;
         const double t = __shfl_sync(0xffffffffu, v, src);
@@ -473,7 +474,7 @@ ABCMB_HD double lane_scan_excl(double v, int lane, int dir)
 
 ABCMB_HD void lane_sync()
 {
-#ifdef __CUDA_ARCH__
+#if defined(__CUDA_ARCH__) || defined(ABCMB_HOST_WARPS)
     __syncwarp();
 #endif
 }
