@@ -99,7 +99,7 @@ ABCMB_HD Bg10 bg_eval_dlna(const double *ot, double lna)
 
 ABCMB_HD void add_to(double *p, double v)
 {
-#ifdef __CUDA_ARCH__
+#if defined(__CUDA_ARCH__) || defined(ABCMB_HOST_WARPS)
     atomicAdd(p, v);
 #else
     *p += v;
@@ -121,13 +121,15 @@ ABCMB_HD void bg_scatter(double *otbar, const HW &h, const Bg10 &bb)
 }
 
 // The lanes that share one mode: on the device the 32 lanes of a warp, lane
-// i taking the state elements i, i + 32, ...; on the host a single lane.
+// i taking the state elements i, i + 32, ...; on the host a single lane, or
+// an emulated warp where the host build defines ABCMB_HOST_WARPS (the CPU
+// tests).
 // Every operator below is called by all lanes of the mode alike, reads its
 // inputs, writes only its own lane's elements of the output, and ends with a
 // lane barrier, so the next operator may read any element.
 ABCMB_HD int ln_id()
 {
-#ifdef __CUDA_ARCH__
+#if defined(__CUDA_ARCH__) || defined(ABCMB_HOST_WARPS)
     return threadIdx.x & 31;
 #else
     return 0;
@@ -136,7 +138,7 @@ ABCMB_HD int ln_id()
 
 ABCMB_HD int ln_n()
 {
-#ifdef __CUDA_ARCH__
+#if defined(__CUDA_ARCH__) || defined(ABCMB_HOST_WARPS)
     return 32;
 #else
     return 1;
@@ -145,14 +147,14 @@ ABCMB_HD int ln_n()
 
 ABCMB_HD void ln_sync()
 {
-#ifdef __CUDA_ARCH__
+#if defined(__CUDA_ARCH__) || defined(ABCMB_HOST_WARPS)
     __syncwarp();
 #endif
 }
 
 ABCMB_HD double ln_sum(double v)
 {
-#ifdef __CUDA_ARCH__
+#if defined(__CUDA_ARCH__) || defined(ABCMB_HOST_WARPS)
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
 #endif
     return v;
@@ -161,7 +163,7 @@ ABCMB_HD double ln_sum(double v)
 // maximum over the lanes; a NaN anywhere gives NaN
 ABCMB_HD double ln_max(double v)
 {
-#ifdef __CUDA_ARCH__
+#if defined(__CUDA_ARCH__) || defined(ABCMB_HOST_WARPS)
     for (int o = 16; o > 0; o >>= 1) {
         const double u = __shfl_xor_sync(0xffffffffu, v, o);
         if (!(u <= v)) v = u;
@@ -301,6 +303,7 @@ ABCMB_HD void op_E_bgrad(const OdeDims &d, const StreamCoef &sc, double k, const
     bb.v[B_FNU] += fac * (whp * 3.0 * y[d.iN] + wep * ce * y[d.iN + 1]);
     bb.v[B_CS2] += fac * v[3] * k * k * ih * db;
     bb.v[B_HC] += fac * wep * 1.5 * ik * (b.v[B_FB] * tb * ik + b.v[B_FG] * y[d.iF + 1] + b.v[B_FNU] * y[d.iN + 1]);
+    ln_sync(); // every lane has read v and y before the caller overwrites them
 }
 
 // ---- T: Thomson scattering ----
@@ -358,6 +361,7 @@ ABCMB_HD void op_T_bgrad(const OdeDims &d, double k, Vec v, Vec y, double fac, B
     const double dnu = v[d.iF + 1] * ((4.0 / 3.0) / k * tb - F1) + wpi * Pi - damp;
     bb.v[B_NU] += fac * dnu;
     bb.v[B_RNU] += fac * v[3] * (0.75 * k * F1 - tb);
+    ln_sync(); // every lane has read v and y before the caller overwrites them
 }
 
 // y <- (I - h T(b))^{-1} y  (the IMEX implicit part; same algebra as imex_substep)
