@@ -27,6 +27,12 @@
 #define ABCMB_HD inline
 #endif
 
+// storage shared by the threads of a CTA; a host build of the kernels (the
+// CPU tests, which run a CTA's threads as host threads) makes it static
+#ifndef ABCMB_CTA_SHARED
+#define ABCMB_CTA_SHARED __shared__
+#endif
+
 namespace abcmb {
 
 // ---- physical constants ----

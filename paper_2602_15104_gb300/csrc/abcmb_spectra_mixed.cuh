@@ -25,12 +25,6 @@
 
 #include "abcmb_bg.cuh"
 
-// storage shared by the threads of a CTA; a host build of these kernels (the
-// CPU tests, which run a CTA's threads as host threads) makes it static
-#ifndef ABCMB_CTA_SHARED
-#define ABCMB_CTA_SHARED __shared__
-#endif
-
 namespace abcmb {
 
 namespace mixed {

@@ -1,0 +1,75 @@
+// Host build of the projection and k-quadrature kernels and of their
+// adjoints (abcmb_spectra.cuh, abcmb_grad.cuh) for the CPU tests: every CTA
+// runs as host threads under warp_emu.h, CTAs one after another, with the
+// grids and arguments of abcmb_project, abcmb_cl, abcmb_project_adjoint and
+// abcmb_cl_adjoint.
+#define ABCMB_HOST_WARPS
+#include "warp_emu.h"
+
+#include "abcmb_grad.cuh"
+#include "abcmb_spectra.cuh"
+
+// the kernels' dynamic shared memory (one CTA at a time)
+namespace abcmb {
+double acc[2 * 5000];
+double wk[1 << 16];
+namespace adj {
+double wk[1 << 17];
+double db[2 * 5000];
+} // namespace adj
+} // namespace abcmb
+
+using namespace abcmb;
+
+namespace {
+long rec_len(const double *bg) { return ABCMB_BG_LEN((long)bg[ABCMB_S_NTAU]); }
+} // namespace
+
+extern "C" long h_bg_len(int n_tau) { return ABCMB_BG_LEN(n_tau); }
+
+extern "C" void h_build_bg(const double *p, int n_tau, double *rec)
+{
+    emu::run_cta(0, 0, 32, [&] { build_background(p, rec, n_tau, (int)threadIdx.x, 32); });
+}
+
+// Delta[B][Nk][lmax-1][2], as abcmb_project
+extern "C" void h_project(int B, const double *bg, const double *S, const double *k, int Nk, int lmax,
+                          double scale_pol, double *Delta)
+{
+    const long len = rec_len(bg);
+    for (long blk = 0; blk < (long)B * Nk; blk++)
+        emu::run_cta((unsigned)blk, 0, 128,
+                     [&] { project_kernel<false>(B, Nk, bg, len, S, k, lmax, scale_pol, Delta, nullptr, 0); });
+}
+
+// Cl[B][3][lmax-1], as abcmb_cl
+extern "C" void h_cl(int B, const double *bg, const double *Delta, const double *k, int Nk, int lmax, double *Cl)
+{
+    const long len = rec_len(bg);
+    for (int b = 0; b < B; b++)
+        for (int gx = 0; gx < (lmax - 1 + 255) / 256; gx++)
+            emu::run_cta((unsigned)gx, (unsigned)b, 256, [&] { cl_kernel(B, Nk, bg, len, Delta, k, lmax, Cl); });
+}
+
+// Sbar [B][Nk][n_tau][3] and recbar += the node and tau_0 adjoints, as abcmb_project_adjoint
+extern "C" void h_project_adjoint(int B, const double *bg, const double *S, const double *k, int Nk, int lmax,
+                                  double scale_pol, const double *Deltabar, double *Sbar, double *recbar)
+{
+    const long len = rec_len(bg);
+    for (long blk = 0; blk < (long)B * Nk; blk++)
+        emu::run_cta((unsigned)blk, 0, 128, [&] {
+            adj::project_adjoint_kernel(B, Nk, bg, len, S, k, lmax, scale_pol, Deltabar, Sbar, recbar);
+        });
+}
+
+// Deltabar [B][Nk][lmax-1][2] and recbar += the A_s, n_s adjoints, as abcmb_cl_adjoint
+extern "C" void h_cl_adjoint(int B, const double *bg, const double *Delta, const double *k, int Nk, int lmax,
+                             const double *Clbar, double *Deltabar, double *recbar)
+{
+    const long len = rec_len(bg);
+    for (int b = 0; b < B; b++)
+        for (int gx = 0; gx < (lmax - 1 + 255) / 256; gx++)
+            emu::run_cta((unsigned)gx, (unsigned)b, 256, [&] {
+                adj::cl_adjoint_kernel(B, Nk, bg, len, Delta, k, lmax, Clbar, Deltabar, recbar);
+            });
+}

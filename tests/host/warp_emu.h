@@ -21,6 +21,7 @@
 #include <sched.h>
 
 #define __device__
+#define __host__
 #define __forceinline__ inline
 #define __global__
 #define __constant__

@@ -1,0 +1,137 @@
+"""CPU checks of the projection and k-quadrature adjoint kernels
+(abcmb_grad.cuh: project_adjoint_kernel and cl_adjoint_kernel, behind
+abcmb_project_adjoint and abcmb_cl_adjoint), built for the host with every
+CTA's threads run as host threads (tests/host/warp_emu.h), beside the forward
+kernels built the same way (abcmb_spectra.cuh):
+
+  * Sbar is the exact transpose of the projection, which is linear in S:
+    <Dbar, P S> = <P^T Dbar, S>;
+  * the node-weight adjoints satisfy Euler's identity for a map linear in
+    the weights, sum_i w_i wbar_i = <Dbar, P S>;
+  * the node-position and tau_0 adjoints equal Richardson differences of the
+    oracle's exact-Bessel projection (App. B.4 transfer functions), and sum
+    to zero (only tau_0 - tau_i enters);
+  * Deltabar is the derivative of <Cbar, C> (App. B.4 eq. c_ell_def, quadratic
+    in Delta: central differences are exact), and the A_s and n_s adjoints
+    match differences of the forward quadrature.
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2602_15104_gb300 import workload as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+P = ctypes.c_void_p
+D = ctypes.c_double
+I = ctypes.c_int
+NODES = 64 + 28 * (18 * 1024 + 1)  # ABCMB_BG_NODES
+S_AS, S_NS, S_TAU0 = 10, 11, 15  # ABCMB_S_AS, ABCMB_S_NS, ABCMB_S_TAU0
+N_TAU, LMAX = 600, 400
+K = np.array([3e-4, 0.004, 0.05, 0.15])
+
+
+@pytest.fixture(scope="module")
+def H(tmp_path_factory):
+    so = str(tmp_path_factory.mktemp("gradk") / "libgradk.so")
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-pthread", "-fPIC", "-shared",
+                           "-I" + os.path.join(ROOT, "include"),
+                           "-I" + os.path.join(ROOT, "paper_2602_15104_gb300", "csrc"),
+                           os.path.join(ROOT, "tests", "host", "grad_harness.cpp"), "-o", so])
+    L = ctypes.CDLL(so)
+    L.h_bg_len.restype = ctypes.c_long
+    L.h_build_bg.argtypes = [P, I, P]
+    L.h_project.argtypes = [I, P, P, P, I, I, D, P]
+    L.h_cl.argtypes = [I, P, P, P, I, I, P]
+    L.h_project_adjoint.argtypes = [I, P, P, P, I, I, D, P, P, P]
+    L.h_cl_adjoint.argtypes = [I, P, P, P, I, I, P, P, P]
+    return L
+
+
+def ptr(a):
+    return a.ctypes.data_as(P)
+
+
+@pytest.fixture(scope="module")
+def case(H):
+    p = W.BATCH64.params()[7]
+    bg = np.zeros((1, H.h_bg_len(N_TAU)))
+    H.h_build_bg(ptr(p), N_TAU, ptr(bg))
+    S = W.synthetic_sources(K.size, N_TAU, 5)[None]
+    Db = np.random.default_rng(1).normal(size=(1, K.size, LMAX - 1, 2))
+    Sb, rb = np.zeros_like(S), np.zeros_like(bg)
+    H.h_project_adjoint(1, ptr(bg), ptr(S), ptr(K), K.size, LMAX, 1.0, ptr(Db), ptr(Sb), ptr(rb))
+    return dict(p=p, bg=bg, S=S, Db=Db, Sb=Sb, rb=rb)
+
+
+def project(H, bg, S):
+    Dl = np.zeros((1, K.size, LMAX - 1, 2))
+    H.h_project(1, ptr(bg), ptr(S), ptr(K), K.size, LMAX, 1.0, ptr(Dl))
+    return Dl
+
+
+def richardson(f, h):
+    d1 = (f(h) - f(-h)) / (2 * h)
+    d2 = (f(2 * h) - f(-2 * h)) / (4 * h)
+    return (4 * d1 - d2) / 3
+
+
+def test_projection_adjoint_is_the_transpose(H, case):
+    bg, S, Db, Sb, rb = case["bg"], case["S"], case["Db"], case["Sb"], case["rb"]
+    L0 = np.sum(Db * project(H, bg, S))
+    assert abs(np.sum(Sb * S) / L0 - 1) < 1e-13
+    w = bg[0, NODES + 2:NODES + 8 * N_TAU:8]
+    wb = rb[0, NODES + 2:NODES + 8 * N_TAU:8]
+    assert abs(np.sum(w * wb) / L0 - 1) < 1e-13
+    taub = rb[0, NODES + 1:NODES + 8 * N_TAU:8]
+    assert abs(taub.sum() + rb[0, S_TAU0]) < 1e-12 * abs(rb[0, S_TAU0])
+
+
+def test_node_position_adjoints_against_oracle_differences(case):
+    # measured 4e-11 (tau_0) and <= 3e-9 of the largest node adjoint
+    p, S, Db, rb = case["p"], case["S"], case["Db"], case["rb"]
+    lna, tau, w = O.nodes(p, N_TAU)
+    t0 = O.scalars(p)["tau0"]
+
+    def L(tau_, t0_):
+        return np.sum(Db[0] * O.project(tau_, w, t0_, K, S[0], LMAX))
+
+    g0 = richardson(lambda e: L(tau, t0 + e), 1e-2)
+    assert abs(rb[0, S_TAU0] / g0 - 1) < 1e-8
+    taub = rb[0, NODES + 1:NODES + 8 * N_TAU:8]
+    for i in (150, 300, 420, 590):
+        def f(e, i=i):
+            tt = tau.copy()
+            tt[i] += e
+            return L(tt, t0)
+        assert abs(taub[i] - richardson(f, 1e-2)) < 1e-7 * np.abs(taub).max(), i
+
+
+def test_quadrature_adjoint(H, case):
+    bg = case["bg"]
+    Dl = project(H, bg, case["S"])
+    rng = np.random.default_rng(2)
+    Cb = rng.normal(size=(1, 3, LMAX - 1))
+
+    def L(bg_, D_):
+        C = np.zeros((1, 3, LMAX - 1))
+        H.h_cl(1, ptr(bg_), ptr(D_), ptr(K), K.size, LMAX, ptr(C))
+        return np.sum(Cb * C)
+
+    Dbar, rb = np.zeros_like(Dl), np.zeros_like(bg)
+    H.h_cl_adjoint(1, ptr(bg), ptr(Dl), ptr(K), K.size, LMAX, ptr(Cb), ptr(Dbar), ptr(rb))
+    V = rng.normal(size=Dl.shape)
+    fd = (L(bg, Dl + 1e-3 * V) - L(bg, Dl - 1e-3 * V)) / 2e-3  # exact for a quadratic
+    assert abs(np.sum(Dbar * V) / fd - 1) < 1e-10  # measured 6e-13
+    for idx in (S_AS, S_NS):
+        h = 1e-5 * abs(bg[0, idx])
+
+        def f(e, idx=idx):
+            b2 = bg.copy()
+            b2[0, idx] += e
+            return L(b2, Dl)
+        assert abs(rb[0, idx] / richardson(f, h) - 1) < 1e-8, idx
