@@ -1,6 +1,6 @@
 // Discrete adjoint of the perturbation step, one warp per (cosmology, k) mode
 // (host+device; on the host one lane does everything; the GPU kernels in
-// abcmb_grad.cu call these per mode, the 32 lanes sharing the state vectors'
+// abcmb_grad.cuh call these per mode, the 32 lanes sharing the state vectors'
 // elements, see ln_id in abcmb_adjoint_ops.cuh).
 //
 // Forward (fwd_taped): the extrapolated IMEX / Gragg integrator of
