@@ -73,3 +73,43 @@ extern "C" void h_cl_adjoint(int B, const double *bg, const double *Delta, const
                 adj::cl_adjoint_kernel(B, Nk, bg, len, Delta, k, lmax, Clbar, Deltabar, recbar);
             });
 }
+
+// The gradient's ODE pass over B x Nk modes (taped_kernel, two one-warp modes
+// per CTA), into the workspace ws laid out by grad_layout: with plan == NULL
+// the counting pass of abcmb_grad_count_steps (accepted[b][k] written, no
+// tape), else the recording pass of abcmb_perturb_taped with that plan (as
+// abcmb_grad_plan writes it), which is first copied into ws as the C ABI does.
+extern "C" void h_taped(int B, const double *bg, const double *k, int Nk, int L, double rtol, double atol,
+                        int max_steps, double *S, int *status, char *ws, const long long *plan, int *accepted)
+{
+    const long len = rec_len(bg), M = (long)B * Nk;
+    long tape = 0, ck = 0;
+    int record = 0;
+    if (plan) {
+        tape = (long)plan[M];
+        ck = (long)plan[2 * M + 1];
+        const adj::GradLayout g = adj::grad_layout(B, Nk, ode_dims(L, L, L), tape, ck);
+        std::memcpy(ws + g.plan, plan, (size_t)(2 * M + 2) * sizeof(long long));
+        record = 1;
+    }
+    const long blocks = (M * 32 + adj::kGradThreads - 1) / adj::kGradThreads;
+    for (long blk = 0; blk < blocks; blk++)
+        emu::run_cta((unsigned)blk, 0, adj::kGradThreads, [&] {
+            adj::taped_kernel(B, Nk, bg, len, k, L, L, L, rtol, atol, max_steps, 1.0, 1.0, 1.0, S, status, ws, tape,
+                              ck, record, plan ? nullptr : accepted);
+        });
+}
+
+// The reverse sweep over every mode (adjoint_kernel), after h_taped with the
+// same plan: recbar[b] += the adjoint of cosmology b's record
+extern "C" void h_adjoint(int B, const double *bg, const double *k, int Nk, int L, const double *Sbar, char *ws,
+                          const long long *plan, double *recbar)
+{
+    const long len = rec_len(bg), M = (long)B * Nk;
+    const long blocks = (M * 32 + adj::kGradThreads - 1) / adj::kGradThreads;
+    for (long blk = 0; blk < blocks; blk++)
+        emu::run_cta((unsigned)blk, 0, adj::kGradThreads, [&] {
+            adj::adjoint_kernel(B, Nk, bg, len, k, L, L, L, 1.0, 1.0, 1.0, Sbar, ws, recbar, (long)plan[M],
+                                (long)plan[2 * M + 1]);
+        });
+}

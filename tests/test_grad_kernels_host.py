@@ -13,10 +13,16 @@ kernels built the same way (abcmb_spectra.cuh):
     to zero (only tau_0 - tau_i enters);
   * Deltabar is the derivative of <Cbar, C> (App. B.4 eq. c_ell_def, quadratic
     in Delta: central differences are exact), and the A_s and n_s adjoints
-    match differences of the forward quadrature.
+    match differences of the forward quadrature;
+  * the ODE passes over a batch of modes (taped_kernel, adjoint_kernel) in
+    a workspace laid out from the library's own step-count plan
+    (abcmb_grad_plan) reproduce the per-mode one-lane build: the counted
+    steps, the sources bit for bit, and each cosmology's record adjoint as
+    the sum of its modes'.
 """
 import ctypes
 import os
+import shutil
 import subprocess
 
 import numpy as np
@@ -135,3 +141,63 @@ def test_quadrature_adjoint(H, case):
             b2[0, idx] += e
             return L(b2, Dl)
         assert abs(rb[0, idx] / richardson(f, h) - 1) < 1e-8, idx
+
+
+@pytest.fixture(scope="module")
+def one_lane(tmp_path_factory):
+    so = str(tmp_path_factory.mktemp("adjone") / "libadjone.so")
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-I" + os.path.join(ROOT, "include"),
+                           "-I" + os.path.join(ROOT, "paper_2602_15104_gb300", "csrc"),
+                           os.path.join(ROOT, "tests", "host", "adjoint_mode_harness.cpp"), "-o", so])
+    L = ctypes.CDLL(so)
+    L.h_bg_len.restype = ctypes.c_long
+    L.h_fwd.argtypes = [P, D, I, D, P, P]
+    L.h_grad.argtypes = [P, D, I, D, P, P]
+    return L
+
+
+@pytest.mark.skipif(shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"),
+                    reason="the library's host functions need nvcc to build")
+def test_planned_batch_of_modes_matches_the_per_mode_adjoint(H, one_lane):
+    from paper_2602_15104_gb300 import abcmb as A
+    from paper_2602_15104_gb300 import build
+    build.build()
+    lib = A.lib()  # host functions only: the workspace sizes and the tape plan
+    H.h_taped.argtypes = [I, P, P, I, I, D, D, I, P, P, P, P, P]
+    H.h_adjoint.argtypes = [I, P, P, I, I, P, P, P, P]
+    B, L, n_tau, rtol = 2, 8, 120, 1e-5
+    k = np.array([0.02, 0.05])
+    params = W.BATCH64.params()[[0, 9]]
+    o = A.options(lmax_hier=L, n_tau=n_tau, lmax_cl=40, rtol=rtol, atol=1e-14)
+    n = one_lane.h_bg_len(n_tau)
+    bg = np.zeros((B, n))
+    for b in range(B):
+        one_lane.h_build_bg(ptr(np.ascontiguousarray(params[b])), n_tau, ptr(bg[b]))
+    S = np.zeros((B, k.size, n_tau, 3))
+    st = np.full((B, k.size), -1, np.int32)
+    acc = np.zeros((B, k.size), np.int32)
+    ws = np.zeros(lib.abcmb_grad_count_workspace_bytes(B, k.size, ctypes.byref(o)) // 8 + 1)
+    H.h_taped(B, ptr(bg), ptr(k), k.size, L, rtol, 1e-14, 10_000_000, ptr(S), ptr(st), ptr(ws), None, ptr(acc))
+    assert np.all(st == 0)
+    plan = np.zeros(2 * B * k.size + 2, np.int64)
+    nbytes = lib.abcmb_grad_plan(B, k.size, ctypes.byref(o), ptr(acc), ptr(plan))
+    assert nbytes > 0
+    ws = np.zeros(nbytes // 8 + 1)
+    S2 = np.zeros_like(S)
+    H.h_taped(B, ptr(bg), ptr(k), k.size, L, rtol, 1e-14, 10_000_000, ptr(S2), ptr(st), ptr(ws), ptr(plan), None)
+    assert np.all(st == 0)
+    np.testing.assert_array_equal(S2, S)
+    Sb = np.random.default_rng(4).normal(size=S.shape) / np.abs(S).max()
+    rb = np.zeros_like(bg)
+    H.h_adjoint(B, ptr(bg), ptr(k), k.size, L, ptr(Sb), ptr(ws), ptr(plan), ptr(rb))
+    for b in range(B):
+        ref = np.zeros(n)
+        for i in range(k.size):
+            S1, sig, g = np.zeros((n_tau, 3)), np.zeros(3, np.int32), np.zeros(n)
+            assert one_lane.h_fwd(ptr(bg[b]), k[i], L, rtol, ptr(S1), ptr(sig)) == 0
+            assert sig[0] == acc[b, i]
+            np.testing.assert_array_equal(S[b, i], S1)
+            assert one_lane.h_grad(ptr(bg[b]), k[i], L, rtol, ptr(np.ascontiguousarray(Sb[b, i])), ptr(g)) == 0
+            ref += g
+        # measured 3e-17 of the largest entry
+        assert np.abs(rb[b] - ref).max() <= 1e-12 * np.abs(ref).max(), b
