@@ -113,3 +113,28 @@ extern "C" void h_adjoint(int B, const double *bg, const double *k, int Nk, int 
                                 (long)plan[2 * M + 1]);
         });
 }
+
+// abcmb_perturb's path for a massive neutrino: the forward alone over B x Nk
+// modes (plain_kernel, two one-warp modes per CTA, V_COUNT x N doubles of
+// work per mode)
+extern "C" void h_plain(int B, const double *bg, const double *k, int Nk, int L, int Lm, double rtol, double atol,
+                        int max_steps, double *S, int *status, int *steps, double *work)
+{
+    const long len = rec_len(bg), M = (long)B * Nk;
+    const long blocks = (M * 32 + adj::kGradThreads - 1) / adj::kGradThreads;
+    for (long blk = 0; blk < blocks; blk++)
+        emu::run_cta((unsigned)blk, 0, adj::kGradThreads, [&] {
+            adj::plain_kernel(B, Nk, bg, len, k, L, L, L, Lm, rtol, atol, max_steps, 1.0, 1.0, 1.0, S, status, steps,
+                              work);
+        });
+}
+
+// grad [B][6] from the record adjoint and the records at params -+ h e_j, as abcmb_record_vjp
+extern "C" void h_record_vjp(int B, long len, const double *recbar, const double *rp, const double *rm,
+                             const double *h, double *grad)
+{
+    for (int b = 0; b < B; b++)
+        for (int j = 0; j < ABCMB_NPARAM; j++)
+            emu::run_cta((unsigned)b, (unsigned)j, 256,
+                         [&] { adj::record_vjp_kernel(B, len, recbar, rp, rm, h, grad); });
+}

@@ -55,6 +55,7 @@ def H(tmp_path_factory):
     L.h_cl.argtypes = [I, P, P, P, I, I, P]
     L.h_project_adjoint.argtypes = [I, P, P, P, I, I, D, P, P, P]
     L.h_cl_adjoint.argtypes = [I, P, P, P, I, I, P, P, P]
+    L.h_record_vjp.argtypes = [I, ctypes.c_long, P, P, P, P, P]
     return L
 
 
@@ -201,3 +202,59 @@ def test_planned_batch_of_modes_matches_the_per_mode_adjoint(H, one_lane):
             ref += g
         # measured 3e-17 of the largest entry
         assert np.abs(rb[b] - ref).max() <= 1e-12 * np.abs(ref).max(), b
+
+
+@pytest.fixture(scope="module")
+def ncdm_lane(tmp_path_factory):
+    so = str(tmp_path_factory.mktemp("ncdmone") / "libncdmone.so")
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-I" + os.path.join(ROOT, "include"),
+                           "-I" + os.path.join(ROOT, "paper_2602_15104_gb300", "csrc"),
+                           os.path.join(ROOT, "tests", "host", "ncdm_harness.cpp"), "-o", so])
+    L = ctypes.CDLL(so)
+    L.h_bg_len.restype = ctypes.c_long
+    L.h_build_bg_m.argtypes = [P, I, D, P]
+    L.h_fwd_m.argtypes = [P, D, I, I, D, P]
+    return L
+
+
+@pytest.mark.skipif(shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"),
+                    reason="the library's host functions need nvcc to build")
+def test_massive_neutrino_warps_equal_the_one_lane_forward(H, ncdm_lane):
+    # plain_kernel, the massive-neutrino path of abcmb_perturb: its momentum-
+    # bin sums split over the lanes; the one-lane build is held against the
+    # oracle in tests/test_ncdm_host.py
+    H.h_plain.argtypes = [I, P, P, I, I, I, D, D, I, P, P, P, P]
+    p = np.ascontiguousarray(W.BATCH64.params()[7])
+    m, n_tau, L, Lm, rtol = 0.1, 300, 8, 6, 1e-7
+    k = np.array([0.01, 0.08])
+    rec = np.zeros((1, ncdm_lane.h_bg_len(n_tau)))
+    ncdm_lane.h_build_bg_m(ptr(p), n_tau, m, ptr(rec))
+    from paper_2602_15104_gb300 import abcmb as A
+    from paper_2602_15104_gb300 import build
+    build.build()
+    o = A.options(lmax_hier=L, n_tau=n_tau, lmax_cl=40, m_ncdm=m, lmax_ncdm=Lm)
+    work = np.zeros(A.perturb_workspace_bytes(1, k.size, o) // 8)  # the library's own size for this path
+    assert work.size > 0
+    S = np.zeros((1, k.size, n_tau, 3))
+    st = np.full((1, k.size), -1, np.int32)
+    steps = np.zeros((1, k.size, 2), np.int32)
+    H.h_plain(1, ptr(rec), ptr(k), k.size, L, Lm, rtol, 1e-15, 20_000_000, ptr(S), ptr(st), ptr(steps), ptr(work))
+    assert np.all(st == 0)
+    for i in range(k.size):
+        S1 = np.zeros((n_tau, 3))
+        assert ncdm_lane.h_fwd_m(ptr(rec[0]), k[i], L, Lm, rtol, ptr(S1)) == 0
+        assert np.abs(S[0, i] - S1).max() <= 1e-12 * np.abs(S1).max(), i
+
+
+def test_record_vector_jacobian_product(H):
+    # grad[b][j] = sum_e recbar[b][e] (rp[b][j][e] - rm[b][j][e]) / (2 h[b][j])
+    rng = np.random.default_rng(6)
+    B, n = 2, 5000
+    rb = rng.normal(size=(B, n))
+    rb[:, ::7] = 0.0  # entries the kernel skips
+    rp, rm = rng.normal(size=(B, 6, n)), rng.normal(size=(B, 6, n))
+    h = rng.uniform(1e-4, 1e-2, size=(B, 6))
+    grad = np.zeros((B, 6))
+    H.h_record_vjp(B, n, ptr(rb), ptr(rp), ptr(rm), ptr(h), ptr(grad))
+    ref = np.einsum("be,bje->bj", rb, rp - rm) / (2 * h)
+    np.testing.assert_allclose(grad, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
