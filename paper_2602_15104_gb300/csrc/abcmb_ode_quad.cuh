@@ -1022,7 +1022,7 @@ perturb_quad_kernel(int B, int Nk, const double *__restrict__ bg, long len, cons
                     double s_dop, double *S, int *status, int *steps, int nb8, long M8, double efloor)
 {
     extern __shared__ double qsm[];
-    __shared__ double cS[3 * 64], cB[3 * 64];
+    ABCMB_CTA_SHARED double cS[3 * 64], cB[3 * 64];
     const int Ls[3] = {Lg, Lp, Ln};
     fill_coef(cS, cB, Ls);
     __syncthreads();
@@ -1061,7 +1061,7 @@ pk_quad_kernel(int B, int Nk, const double *__restrict__ bg, long len, const dou
                int *steps, double efloor)
 {
     extern __shared__ double qsm[];
-    __shared__ double cS[3 * 64], cB[3 * 64];
+    ABCMB_CTA_SHARED double cS[3 * 64], cB[3 * 64];
     const int Ls[3] = {Lg, Lp, Ln};
     fill_coef(cS, cB, Ls);
     __syncthreads();
@@ -1088,7 +1088,7 @@ dm_quad_kernel(int B, int Nk, const double *__restrict__ bg, long len, const dou
                int Lp, int Ln, double rtol, double atol, int max_steps, double *Dm, int *status, double efloor)
 {
     extern __shared__ double qsm[];
-    __shared__ double cS[3 * 64], cB[3 * 64];
+    ABCMB_CTA_SHARED double cS[3 * 64], cB[3 * 64];
     const int Ls[3] = {Lg, Lp, Ln};
     fill_coef(cS, cB, Ls);
     __syncthreads();
