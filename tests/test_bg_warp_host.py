@@ -52,6 +52,9 @@ def test_warp_record_equals_the_one_lane_record(libs, b, recipe, m_ncdm):
     lane.h_build_bg_r(p.ctypes.data_as(P), n_tau, m_ncdm, recipe, r1.ctypes.data_as(P))
     warp.h_build_bg_warp(p.ctypes.data_as(P), n_tau, m_ncdm, recipe, r32.ctypes.data_as(P))
     assert r1[0] == 0 and r32[0] == 0  # status
+    again = np.full_like(r1, np.nan)  # a second build repeats the first bit for bit
+    warp.h_build_bg_warp(p.ctypes.data_as(P), n_tau, m_ncdm, recipe, again.ctypes.data_as(P))
+    np.testing.assert_array_equal(again, r32)
     np.testing.assert_allclose(r32[:TABLE], r1[:TABLE], rtol=1e-14, atol=0)
     poly = NODES + 8 * n_tau
     for name, a, e, ncol in [("table", TABLE, ODETAB, 8), ("ode table", ODETAB, NODES, 20), ("nodes", NODES, poly, 8)]:
