@@ -3,8 +3,9 @@
 project_kernel, cl_kernel), with their grids and arguments, built for the host
 with every CTA's threads run as host threads (tests/host/warp_emu.h), against
 the oracle's C_l (App. B.4 eq. c_ell_def) on the single-cosmology TT workload's
-grids (l <= 500, hierarchies 12, 2000 tau nodes) at every fourth of its 100 k.
-The GPU runs the same kernels on the full workload in tests/test_gpu_parity.py.
+grids (l <= 500, hierarchies 12, 2000 tau nodes) at every fourth of its 100 k
+up to 0.1 /Mpc (k chi* ~ 1400 there, past every l kept).  The GPU runs the same
+kernels on the full workload in tests/test_gpu_parity.py.
 """
 import ctypes
 import os
@@ -31,7 +32,8 @@ def test_hot_path_kernels_on_the_host_against_the_oracle(tmp_path):
     H.h_bg_len.restype = ctypes.c_long
     H.h_pipeline.argtypes = [I, P, P, I, I, I, I, D, D, P, P, P, P, P]
     wl = W.SMALL_TT
-    params, k = np.ascontiguousarray(wl.params()), np.ascontiguousarray(wl.k()[::4])
+    k = wl.k()[::4]
+    params, k = np.ascontiguousarray(wl.params()), np.ascontiguousarray(k[k <= 0.1])
     n_tau, lmax, L = wl.n_tau, wl.l_max_cl, wl.l_max_hier
     bg = np.zeros((1, H.h_bg_len(n_tau)))
     S = np.zeros((1, k.size, n_tau, 3))
@@ -47,5 +49,5 @@ def test_hot_path_kernels_on_the_host_against_the_oracle(tmp_path):
     tt = np.abs(C[0, 0] - ref[0]) / np.abs(ref[0])
     ee = np.abs(C[0, 2] - ref[2]) / np.abs(ref[2])
     te = np.abs(C[0, 1] - ref[1]) / np.sqrt(np.abs(ref[0] * ref[2]))
-    # the FP64 bar, 1e-5 (measured 8.2e-7 TT, 4.8e-7 TE, 2.0e-7 EE)
+    # the FP64 bar, 1e-5 (measured 8.7e-7 TT, 6.3e-7 TE, 2.0e-7 EE)
     assert tt.max() < 1e-5 and te.max() < 1e-5 and ee.max() < 1e-5, (tt.max(), te.max(), ee.max())
