@@ -1,0 +1,163 @@
+"""Calls into an AddressSanitizer / UndefinedBehaviorSanitizer build of one
+host harness (run by tests/test_sanitized_kernels_host.py in a subprocess with
+the sanitizer runtimes preloaded): the emulated kernels on small, ragged
+shapes, every buffer its own allocation, so that a read or write past any
+buffer the kernels index, or undefined behaviour in their arithmetic, ends
+the process with the sanitizer's report.
+
+usage: python sanitize_calls.py <harness> <path to the instrumented .so>
+       [<path to the instrumented background harness, for adjwarp>]
+"""
+import ctypes
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+sys.path.insert(0, os.path.join(ROOT, "tests"))
+from paper_2602_15104_gb300 import workload as W  # noqa: E402
+
+P, D, I = ctypes.c_void_p, ctypes.c_double, ctypes.c_int
+
+
+def ptr(a):
+    return a.ctypes.data_as(P)
+
+
+def own(a):
+    """a copy in a buffer of exactly its size"""
+    return np.array(a, copy=True, order="C")
+
+
+def records(H, params, n_tau, build):
+    H.h_bg_len.restype = ctypes.c_long
+    out = []
+    for p in np.atleast_2d(params):
+        r = np.zeros(H.h_bg_len(n_tau))
+        build(own(p), r)
+        out.append(r)
+    return own(np.stack(out))
+
+
+def quad(H):
+    H.h_build_bg.argtypes = [P, I, P]
+    H.h_quad.argtypes = [I, P, P, I, I, D, D, I, D, I, P, P, P]
+    H.h_quad_pk.argtypes = [I, P, P, I, I, D, D, I, D, D, P, P, P]
+    H.h_quad_dm.argtypes = [I, P, P, I, I, D, D, I, D, P, P]
+    n_tau = 157
+    bg = records(H, W.BATCH64.params()[:3], n_tau, lambda p, r: H.h_build_bg(ptr(p), n_tau, ptr(r)))
+    k = own([0.002, 0.03])
+    for L, n_wide in [(12, 0), (30, 0), (30, 1), (50, 2)]:
+        S, st, steps = np.zeros((3, 2, n_tau, 3)), np.zeros((3, 2), np.int32), np.zeros((3, 2, 2), np.int32)
+        H.h_quad(3, ptr(bg), ptr(k), 2, L, 1e-5, 1e-12, 2_000_000, 1e-4, n_wide, ptr(S), ptr(st), ptr(steps))
+        assert np.all(st == 0), (L, n_wide, st)
+    Pk, st = np.zeros((3, 2)), np.zeros((3, 2), np.int32)
+    H.h_quad_pk(3, ptr(bg), ptr(k), 2, 12, 1e-5, 1e-12, 2_000_000, 1e-4, 0.5, ptr(Pk), ptr(st), None)
+    Dm = np.zeros((3, 2, n_tau))
+    H.h_quad_dm(3, ptr(bg), ptr(k), 2, 12, 1e-5, 1e-12, 2_000_000, 1e-4, ptr(Dm), ptr(st))
+    S, st, steps = np.zeros((1, 1, n_tau, 3)), np.zeros((1, 1), np.int32), np.zeros((1, 1, 2), np.int32)
+    H.h_quad(1, ptr(own(bg[:1])), ptr(own([0.05])), 1, 12, 1e-6, 1e-12, 40, 1e-4, 0, ptr(S), ptr(st), ptr(steps))
+    assert st[0, 0] == 3  # the step budget
+
+
+def spectra(H):
+    H.h_build_bg.argtypes = [P, I, P]
+    H.h_project.argtypes = [I, P, P, P, I, I, D, P]
+    H.h_project_interp.argtypes = [I, P, P, P, I, P, I, I, D, P]
+    H.h_cl.argtypes = [I, P, P, P, I, I, P]
+    n_tau, lmax = 333, 257
+    bg = records(H, W.BATCH64.params()[:2], n_tau, lambda p, r: H.h_build_bg(ptr(p), n_tau, ptr(r)))
+    k = own([1e-5, 3e-4, 0.01, 0.2, 0.5])
+    S = own(np.stack([W.synthetic_sources(k.size, n_tau, b) for b in range(2)]))
+    Dl = np.zeros((2, k.size, lmax - 1, 2))
+    H.h_project(2, ptr(bg), ptr(S), ptr(k), k.size, lmax, 1.0, ptr(Dl))
+    kt = own([2e-5, 1e-3, 0.3])
+    Dt = np.zeros((2, kt.size, lmax - 1, 2))
+    H.h_project_interp(2, ptr(bg), ptr(S), ptr(k), k.size, ptr(kt), kt.size, lmax, 1.0, ptr(Dt))
+    C = np.zeros((2, 3, lmax - 1))
+    H.h_cl(2, ptr(bg), ptr(Dl), ptr(k), k.size, lmax, ptr(C))
+    assert np.isfinite(C).all()
+
+
+def mixed(H):
+    H.h_build_bg.argtypes = [P, I, P]
+    H.h_project_mixed.argtypes = [I, P, P, P, I, I, D, P]
+    H.h_cl_mixed.argtypes = [I, P, P, P, I, I, P]
+    n_tau, lmax = 333, 257
+    bg = records(H, W.BATCH64.params()[:2], n_tau, lambda p, r: H.h_build_bg(ptr(p), n_tau, ptr(r)))
+    k = own([1e-5, 0.01, 0.5])
+    S = own(np.stack([W.synthetic_sources(k.size, n_tau, b) for b in range(2)]))
+    Dl = np.zeros((2, k.size, lmax - 1, 2), np.float32)
+    H.h_project_mixed(2, ptr(bg), ptr(S), ptr(k), k.size, lmax, 1.0, ptr(Dl))
+    C = np.zeros((2, 3, lmax - 1))
+    H.h_cl_mixed(2, ptr(bg), ptr(Dl), ptr(k), k.size, lmax, ptr(C))
+    assert np.isfinite(C).all()
+
+
+def grad(H):
+    H.h_build_bg.argtypes = [P, I, P]
+    H.h_project_adjoint.argtypes = [I, P, P, P, I, I, D, P, P, P]
+    H.h_cl_adjoint.argtypes = [I, P, P, P, I, I, P, P, P]
+    H.h_record_vjp.argtypes = [I, ctypes.c_long, P, P, P, P, P]
+    n_tau, lmax = 333, 257
+    bg = records(H, W.BATCH64.params()[3:4], n_tau, lambda p, r: H.h_build_bg(ptr(p), n_tau, ptr(r)))
+    k = own([1e-5, 0.01, 0.5])
+    S = own(W.synthetic_sources(k.size, n_tau, 2)[None])
+    rng = np.random.default_rng(0)
+    Db, Sb, rb = rng.normal(size=(1, k.size, lmax - 1, 2)), np.zeros_like(S), np.zeros_like(bg)
+    H.h_project_adjoint(1, ptr(bg), ptr(S), ptr(k), k.size, lmax, 1.0, ptr(Db), ptr(Sb), ptr(rb))
+    Cb, Dbar = rng.normal(size=(1, 3, lmax - 1)), np.zeros_like(Db)
+    H.h_cl_adjoint(1, ptr(bg), ptr(Db), ptr(k), k.size, lmax, ptr(Cb), ptr(Dbar), ptr(rb))
+    n = 777
+    g = np.zeros((2, 6))
+    H.h_record_vjp(2, n, ptr(rng.normal(size=(2, n))), ptr(rng.normal(size=(2, 6, n))),
+                   ptr(rng.normal(size=(2, 6, n))), ptr(rng.uniform(1e-3, 1e-2, size=(2, 6))), ptr(g))
+    assert np.isfinite(rb).all() and np.isfinite(g).all()
+
+
+def lens(H):
+    from test_lensing_host import spectra as synthetic_spectra
+    H.h_lens.argtypes = [I, P, I, P, I, I, P]
+    L, lout = 150, 100
+    sp = [synthetic_spectra(L, 7 + b) for b in range(2)]
+    Cl = own(np.stack([np.stack([s[0][2:], s[2][2:], s[1][2:]]) for s in sp]))
+    Cpsi = own(np.stack([s[3][2:] for s in sp]))
+    out = np.zeros((2, 4, lout - 1))
+    H.h_lens(2, ptr(Cl), L, ptr(Cpsi), lout, L + 37, ptr(out))
+    assert np.isfinite(out).all()
+
+
+def bgwarp(H):
+    H.h_bg_len.restype = ctypes.c_long
+    H.h_build_bg_warp.argtypes = [P, I, D, I, P]
+    for b, m, recipe, n_tau in [(0, 0.0, 0, 101), (17, 0.06, 1, 64)]:
+        r = np.zeros(H.h_bg_len(n_tau))
+        H.h_build_bg_warp(ptr(own(W.BATCH64.params()[b])), n_tau, m, recipe, ptr(r))
+        assert r[0] == 0
+
+
+def adjwarp(H):
+    H.h_bg_len.restype = ctypes.c_long
+    H.h_fwd_warp.argtypes = [P, D, I, D, P, P]
+    H.h_grad_warp.argtypes = [P, D, I, D, P, P]
+    # the adjoint harness has no background builder: the record comes from
+    # the instrumented background harness, argv[3]
+    lib = ctypes.CDLL(sys.argv[3])
+    lib.h_bg_len.restype = ctypes.c_long
+    lib.h_build_bg_warp.argtypes = [P, I, D, I, P]
+    n_tau = 60
+    r = np.zeros(lib.h_bg_len(n_tau))
+    lib.h_build_bg_warp(ptr(own(W.BATCH64.params()[0])), n_tau, 0.0, 0, ptr(r))
+    S, sig = np.zeros((n_tau, 3)), np.zeros(3, np.int32)
+    assert H.h_fwd_warp(ptr(r), 0.05, 8, 1e-4, ptr(S), ptr(sig)) == 0
+    Sb, rb = own(np.random.default_rng(1).normal(size=(n_tau, 3))), np.zeros_like(r)
+    assert H.h_grad_warp(ptr(r), 0.05, 8, 1e-4, ptr(Sb), ptr(rb)) == 0
+    assert np.isfinite(rb).all()
+
+
+if __name__ == "__main__":
+    which, so = sys.argv[1], sys.argv[2]
+    globals()[which](ctypes.CDLL(so))
+    print("ok")
