@@ -157,6 +157,41 @@ def adjwarp(H):
     assert np.isfinite(rb).all()
 
 
+def ode(H):
+    # the thread-per-mode solver (hierarchies 64..128), one lane
+    H.h_bg_len.restype = ctypes.c_long
+    H.h_build_bg.argtypes = [P, I, P]
+    H.h_integrate.argtypes = [P, D, I, D, P, P]
+    n_tau = 77
+    r = np.zeros(H.h_bg_len(n_tau))
+    H.h_build_bg(ptr(own(W.BATCH64.params()[2])), n_tau, ptr(r))
+    for k, L in [(3e-4, 64), (0.02, 90)]:
+        S, steps = np.zeros((n_tau, 3)), np.zeros(2, np.int32)
+        assert H.h_integrate(ptr(r), k, L, 1e-5, ptr(S), ptr(steps)) == 0
+
+
+def arena(H):
+    # the serving arena's first-fit allocator under a seeded random workload
+    H.h_arena_init.argtypes = [ctypes.c_size_t]
+    H.h_arena_alloc.argtypes = [ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
+    H.h_arena_release.argtypes = [ctypes.c_size_t, ctypes.c_size_t]
+    H.h_arena_largest.restype = H.h_arena_size.restype = ctypes.c_size_t
+    rng = np.random.default_rng(3)
+    H.h_arena_init(1 << 20)
+    live = []
+    for _ in range(4000):
+        if live and rng.uniform() < 0.45:
+            off, n = live.pop(rng.integers(len(live)))
+            H.h_arena_release(off, n)
+        else:
+            n, got = int(rng.integers(1, 40000)), ctypes.c_size_t()
+            if H.h_arena_alloc(n, ctypes.byref(got)):
+                live.append((got.value, n))
+    for off, n in live:
+        H.h_arena_release(off, n)
+    assert H.h_arena_largest() == H.h_arena_size()
+
+
 if __name__ == "__main__":
     which, so = sys.argv[1], sys.argv[2]
     globals()[which](ctypes.CDLL(so))

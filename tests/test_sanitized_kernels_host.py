@@ -5,8 +5,10 @@ preloaded, on small and ragged shapes (node counts and l ranges that fill no
 tile evenly, one- and eight-lane layouts, hierarchies up to 50, a step
 budget that runs out).  A read or write past any buffer the kernels index
 (the caller's arrays and the emulated shared memory), or undefined behaviour
-in their integer and floating-point arithmetic, fails the run.  On the
-device the same accesses are unchecked; compute-sanitizer is not used here.
+in their integer and floating-point arithmetic, fails the run.  Also the
+thread-per-mode solver for deep hierarchies and the serving arena's
+allocator.  On the device the same accesses are unchecked; compute-sanitizer
+is not used here.
 """
 import os
 import subprocess
@@ -31,7 +33,7 @@ pytestmark = pytest.mark.skipif(ASAN is None or UBSAN is None, reason="no saniti
 
 HARNESSES = {"quad": "quad_harness.cpp", "spectra": "spectra_harness.cpp", "mixed": "spectra_mixed_harness.cpp",
              "grad": "grad_harness.cpp", "lens": "lens_kernels_harness.cpp", "bgwarp": "bg_warp_harness.cpp",
-             "adjwarp": "adjoint_warp_harness.cpp"}
+             "adjwarp": "adjoint_warp_harness.cpp", "ode": "ode_harness.cpp", "arena": "arena_harness.cpp"}
 
 
 @pytest.fixture(scope="module")
