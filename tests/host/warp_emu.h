@@ -18,6 +18,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <thread>
+#include <vector>
+
 #include <sched.h>
 
 #define __device__
@@ -43,7 +46,7 @@ extern thread_local EmuDim3 threadIdx, blockIdx, blockDim;
 
 namespace emu {
 
-// sense-counting barrier: spin briefly, then yield (a CTA's threads share
+// generation-counting barrier: spin briefly, then yield (a CTA's threads share
 // few cores); a wait longer than kDeadlineS means lanes disagree about the
 // collectives, and the process ends with a message rather than hanging
 struct Barrier {
@@ -192,15 +195,13 @@ inline double __hiloint2double(int hi, int lo)
     return emu::from_bits<double>(((uint64_t)(uint32_t)hi << 32) | (uint32_t)lo);
 }
 inline float __powf(float x, float y) { return powf(x, y); }
-// single-precision operations rounded once each (this build contracts nothing)
+// single-precision operations rounded once each (the harnesses build with
+// floating-point contraction off)
 inline float __fadd_rn(float a, float b) { return a + b; }
 inline float __fsub_rn(float a, float b) { return a - b; }
 inline float __fmul_rn(float a, float b) { return a * b; }
 inline int max(int a, int b) { return a > b ? a : b; }
 inline int min(int a, int b) { return a < b ? a : b; }
-
-#include <thread>
-#include <vector>
 
 thread_local EmuDim3 threadIdx, blockIdx, blockDim;
 namespace emu {
