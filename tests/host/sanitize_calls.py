@@ -60,6 +60,11 @@ def quad(H):
     S, st, steps = np.zeros((1, 1, n_tau, 3)), np.zeros((1, 1), np.int32), np.zeros((1, 1, 2), np.int32)
     H.h_quad(1, ptr(own(bg[:1])), ptr(own([0.05])), 1, 12, 1e-6, 1e-12, 40, 1e-4, 0, ptr(S), ptr(st), ptr(steps))
     assert st[0, 0] == 3  # the step budget
+    # the smallest shapes: one cosmology, one k, the minimum of 8 tau nodes, hierarchy 4
+    bg8 = records(H, W.BATCH64.params()[5:6], 8, lambda p, r: H.h_build_bg(ptr(p), 8, ptr(r)))
+    S = np.zeros((1, 1, 8, 3))
+    H.h_quad(1, ptr(bg8), ptr(own([1e-3])), 1, 4, 1e-5, 1e-12, 2_000_000, 1e-4, 0, ptr(S), ptr(st), ptr(steps))
+    assert st[0, 0] == 0
 
 
 def spectra(H):
@@ -79,6 +84,15 @@ def spectra(H):
     C = np.zeros((2, 3, lmax - 1))
     H.h_cl(2, ptr(bg), ptr(Dl), ptr(k), k.size, lmax, ptr(C))
     assert np.isfinite(C).all()
+    # the smallest shapes: 8 nodes, l = 2 alone and l <= 3, two k, one below the series limit
+    bg8 = records(H, W.BATCH64.params()[5:6], 8, lambda p, r: H.h_build_bg(ptr(p), 8, ptr(r)))
+    k2 = own([1e-6, 0.4])
+    S8 = own(W.synthetic_sources(2, 8, 9)[None])
+    for lm in (2, 3):
+        D8, C8 = np.zeros((1, 2, lm - 1, 2)), np.zeros((1, 3, lm - 1))
+        H.h_project(1, ptr(bg8), ptr(S8), ptr(k2), 2, lm, 1.0, ptr(D8))
+        H.h_cl(1, ptr(bg8), ptr(D8), ptr(k2), 2, lm, ptr(C8))
+        assert np.isfinite(C8).all()
 
 
 def mixed(H):
@@ -94,6 +108,14 @@ def mixed(H):
     C = np.zeros((2, 3, lmax - 1))
     H.h_cl_mixed(2, ptr(bg), ptr(Dl), ptr(k), k.size, lmax, ptr(C))
     assert np.isfinite(C).all()
+    bg8 = records(H, W.BATCH64.params()[5:6], 8, lambda p, r: H.h_build_bg(ptr(p), 8, ptr(r)))
+    k2 = own([1e-6, 0.4])
+    S8 = own(W.synthetic_sources(2, 8, 9)[None])
+    for lm in (2, 3):
+        D8, C8 = np.zeros((1, 2, lm - 1, 2), np.float32), np.zeros((1, 3, lm - 1))
+        H.h_project_mixed(1, ptr(bg8), ptr(S8), ptr(k2), 2, lm, 1.0, ptr(D8))
+        H.h_cl_mixed(1, ptr(bg8), ptr(D8), ptr(k2), 2, lm, ptr(C8))
+        assert np.isfinite(C8).all()
 
 
 def grad(H):
