@@ -601,7 +601,10 @@ class Server:
         self._buf = np.empty(3 * (max_lmax_cl - 1), dtype=np.float64)
 
     def submit(self, tag: int, params, lmax_cl: int, n_k: int, k_min: float, k_max: float) -> int:
+        """Queue one cosmology (params: its 6 parameters, host) -> the C status code."""
         p = np.ascontiguousarray(params, dtype=np.float64)
+        if p.size != NPARAM:
+            raise ValueError(f"params: {NPARAM} values, got {p.size}")  # the library copies exactly 6
         return lib().abcmb_server_submit(self._h, tag, p.ctypes.data_as(ctypes.c_void_p), lmax_cl, n_k,
                                          k_min, k_max)
 

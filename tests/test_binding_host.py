@@ -238,3 +238,16 @@ def test_params_must_be_rows_of_six(AR):
         A.abcmb_param_stencil(f64(12), 1e-4, 1e-3)
     assert rec.calls == []
     assert np.array_equal(A.abcmb_background_tables(f64(3, 6), o).shape, (3, A.bg_doubles(o)))
+
+
+def test_server_submit_takes_six_parameters(AR):
+    A, rec = AR
+    srv = A.Server.__new__(A.Server)  # no device arena needed to check the arguments
+    srv._h = None
+    for bad in (np.zeros(5), np.zeros((2, 6)), 3.0):
+        with pytest.raises(ValueError):
+            srv.submit(1, bad, 100, 8, 1e-4, 0.1)
+    assert rec.calls == []
+    assert srv.submit(1, np.zeros(6), 100, 8, 1e-4, 0.1) == A.OK
+    (name, args), = rec.calls
+    assert name == "abcmb_server_submit" and args[3:] == (100, 8, 1e-4, 0.1)
