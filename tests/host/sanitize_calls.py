@@ -214,6 +214,32 @@ def arena(H):
     assert H.h_arena_largest() == H.h_arena_size()
 
 
+def server(H):
+    # the serving runtime over its stand-in CUDA runtime: mixed shapes queued,
+    # batched, admitted to a small arena and retired until all are served
+    from test_server_host import Run
+    H.h_arena.restype = P
+    H.h_arena.argtypes = [ctypes.c_size_t]
+    H.h_free.argtypes = [P]
+    H.h_reset.argtypes = [P, ctypes.c_size_t, I]
+    H.h_launch.argtypes = [I, P, P]
+    H.abcmb_server_request_bytes.restype = ctypes.c_size_t
+    H.abcmb_server_create.argtypes = [P, ctypes.c_size_t, I, I, I, P, ctypes.POINTER(P)]
+    H.abcmb_server_destroy.argtypes = [P]
+    H.abcmb_server_submit.argtypes = [P, ctypes.c_longlong, P, I, I, D, D]
+    H.abcmb_server_progress.argtypes = [P]
+    H.abcmb_server_poll.argtypes = [P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(I), ctypes.POINTER(I), P,
+                                    ctypes.c_size_t]
+    rng = np.random.default_rng(2)
+    r = Run(H, 120 << 20, slots=3)
+    for tag in range(30):
+        lm, nk = [(100, 16), (100, 32), (300, 8)][rng.integers(3)]
+        assert r.submit(tag, own([float(tag), 0.12, 0.7, 0.96, 3.0, 0.06]), lm, nk) == 0
+    assert len(r.drain(30)) == 30
+    assert H.h_violations() == 0
+    r.close()
+
+
 if __name__ == "__main__":
     which, so = sys.argv[1], sys.argv[2]
     globals()[which](ctypes.CDLL(so))

@@ -6,8 +6,8 @@ tile evenly, one- and eight-lane layouts, hierarchies up to 50, a step
 budget that runs out).  A read or write past any buffer the kernels index
 (the caller's arrays and the emulated shared memory), or undefined behaviour
 in their integer and floating-point arithmetic, fails the run.  Also the
-thread-per-mode solver for deep hierarchies and the serving arena's
-allocator.  On the device the same accesses are unchecked; compute-sanitizer
+thread-per-mode solver for deep hierarchies, the serving arena's allocator
+and the serving runtime itself (over its stand-in CUDA runtime).  On the device the same accesses are unchecked; compute-sanitizer
 is not used here.
 """
 import os
@@ -33,7 +33,8 @@ pytestmark = pytest.mark.skipif(ASAN is None or UBSAN is None, reason="no saniti
 
 HARNESSES = {"quad": "quad_harness.cpp", "spectra": "spectra_harness.cpp", "mixed": "spectra_mixed_harness.cpp",
              "grad": "grad_harness.cpp", "lens": "lens_kernels_harness.cpp", "bgwarp": "bg_warp_harness.cpp",
-             "adjwarp": "adjoint_warp_harness.cpp", "ode": "ode_harness.cpp", "arena": "arena_harness.cpp"}
+             "adjwarp": "adjoint_warp_harness.cpp", "ode": "ode_harness.cpp", "arena": "arena_harness.cpp",
+             "server": "server_harness.cpp"}
 
 
 @pytest.fixture(scope="module")
@@ -43,11 +44,16 @@ def builds(tmp_path_factory):
     for name, src in HARNESSES.items():  # compiled side by side
         so = str(d / f"{name}.so")
         flags = ["-ffp-contract=off"] if name == "mixed" else []
+        sources = [os.path.join(HOST, src)]
+        if name == "server":  # the runtime itself, over the stand-in CUDA runtime
+            flags.append("-I" + os.path.join(HOST, "fake_cuda"))
+            sources = ["-x", "c++", os.path.join(ROOT, "paper_2602_15104_gb300", "csrc", "abcmb_server.cu"),
+                       "-x", "none", *sources]
         jobs.append(subprocess.Popen(["g++", "-O1", "-g", "-std=c++17", "-pthread", "-fPIC", "-shared", *flags,
                                       "-fsanitize=address,undefined", "-fno-omit-frame-pointer",
                                       "-I" + os.path.join(ROOT, "include"),
                                       "-I" + os.path.join(ROOT, "paper_2602_15104_gb300", "csrc"),
-                                      os.path.join(HOST, src), "-o", so]))
+                                      *sources, "-o", so]))
         out[name] = so
     assert all(j.wait() == 0 for j in jobs)
     return out
