@@ -14,7 +14,7 @@ extern "C" long h_bg_len(int n_tau) { return ABCMB_BG_LEN(n_tau); }
 
 extern "C" void h_build_bg(const double *p, int n_tau, double *rec) { build_background(p, rec, n_tau, 0, 1); }
 
-// the kernels' dynamic shared memory (one CTA at a time): the largest warp's
+// the kernels' dynamic shared memory (one CTA at a time), sized for P = 16
 namespace abcmb {
 double qsm[quad_smem_per_warp<16>() / sizeof(double)];
 } // namespace abcmb
