@@ -190,6 +190,11 @@ def ode(H):
     for k, L in [(3e-4, 64), (0.02, 90)]:
         S, steps = np.zeros((n_tau, 3)), np.zeros(2, np.int32)
         assert H.h_integrate(ptr(r), k, L, 1e-5, ptr(S), ptr(steps)) == 0
+    H.h_integrate_batch.argtypes = [P, P, I, I, D, P, P]
+    k = own([3e-4, 1e-3, 5e-3])  # three modes interleaved in one workspace, at once
+    S, st = np.zeros((3, n_tau, 3)), np.zeros(3, np.int32)
+    H.h_integrate_batch(ptr(r), ptr(k), 3, 66, 1e-5, ptr(S), ptr(st))
+    assert np.all(st == 0)
 
 
 def arena(H):
