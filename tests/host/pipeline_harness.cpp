@@ -7,12 +7,17 @@
 
 #include "abcmb_ode_quad.cuh"
 #include "abcmb_spectra.cuh"
+#include "abcmb_spectra_mixed.cuh"
 
 // the kernels' dynamic shared memory (one CTA at a time)
 namespace abcmb {
 double qsm[quad_smem_per_warp<16>() / sizeof(double)];
 double acc[2 * 5000];
 double wk[1 << 16];
+namespace mixed {
+float acc[4 * 5000];
+float wkf[1 << 16];
+} // namespace mixed
 } // namespace abcmb
 
 using namespace abcmb;
@@ -50,4 +55,19 @@ extern "C" void h_pipeline(int B, const double *params, const double *k, int Nk,
     for (int b = 0; b < B; b++)
         for (int gx = 0; gx < (lmax - 1 + 255) / 256; gx++)
             emu::run_cta((unsigned)gx, (unsigned)b, 256, [&] { cl_kernel(B, Nk, bg, len, Delta, k, lmax, Cl); });
+}
+
+// the mixed-precision end of the path on the same records and sources, as
+// Pipeline(mixed=True) runs it: Delta32 [B][Nk][lmax-1][2], then C_l
+extern "C" void h_mixed_tail(int B, const double *bg, const double *S, const double *k, int Nk, int n_tau, int lmax,
+                             float *Delta32, double *Cl)
+{
+    const long len = ABCMB_BG_LEN(n_tau);
+    for (long blk = 0; blk < (long)B * Nk; blk++)
+        emu::run_cta((unsigned)blk, 0, 32,
+                      [&] { mixed::project_mixed_kernel(B, Nk, bg, len, S, k, lmax, 1.0, Delta32); });
+    for (int b = 0; b < B; b++)
+        for (int gx = 0; gx < (lmax - 1 + 255) / 256; gx++)
+            emu::run_cta((unsigned)gx, (unsigned)b, 256,
+                         [&] { mixed::cl_mixed_kernel(B, Nk, bg, len, Delta32, k, lmax, Cl); });
 }

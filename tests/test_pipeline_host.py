@@ -1,6 +1,7 @@
 """The whole hot path on the CPU: the calls Pipeline.run makes on the GPU
 (the background builder on one warp per cosmology, perturb_quad_kernel,
-project_kernel, cl_kernel), with their grids and arguments, built for the host
+project_kernel, cl_kernel, and for the mixed form project_mixed_kernel and
+cl_mixed_kernel), with their grids and arguments, built for the host
 with every CTA's threads run as host threads (tests/host/warp_emu.h), against
 the oracle's C_l (App. B.4 eq. c_ell_def) on the single-cosmology TT workload's
 grids (l <= 500, hierarchies 12, 2000 tau nodes) at every fourth of its 100 k
@@ -51,3 +52,11 @@ def test_hot_path_kernels_on_the_host_against_the_oracle(tmp_path):
     te = np.abs(C[0, 1] - ref[1]) / np.sqrt(np.abs(ref[0] * ref[2]))
     # the FP64 bar, 1e-5 (measured 8.7e-7 TT, 6.3e-7 TE, 2.0e-7 EE)
     assert tt.max() < 1e-5 and te.max() < 1e-5 and ee.max() < 1e-5, (tt.max(), te.max(), ee.max())
+    # the mixed-precision end (FP32 projection and quadrature) on the same sources: the 1e-4 bar
+    H.h_mixed_tail.argtypes = [I, P, P, P, I, I, I, P, P]
+    D32, C32 = np.zeros((1, k.size, lmax - 1, 2), np.float32), np.zeros((1, 3, lmax - 1))
+    H.h_mixed_tail(1, ptr(bg), ptr(S), ptr(k), k.size, n_tau, lmax, ptr(D32), ptr(C32))
+    tt = np.abs(C32[0, 0] - ref[0]) / np.abs(ref[0])
+    ee = np.abs(C32[0, 2] - ref[2]) / np.abs(ref[2])
+    te = np.abs(C32[0, 1] - ref[1]) / np.sqrt(np.abs(ref[0] * ref[2]))
+    assert tt.max() < 1e-4 and te.max() < 1e-4 and ee.max() < 1e-4, (tt.max(), te.max(), ee.max())
