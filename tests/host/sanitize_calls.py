@@ -20,6 +20,8 @@ sys.path.insert(0, os.path.join(ROOT, "tests"))
 from paper_2602_15104_gb300 import workload as W  # noqa: E402
 
 P, D, I = ctypes.c_void_p, ctypes.c_double, ctypes.c_int
+# a lighter set of the same paths, for ThreadSanitizer (tens of times slower)
+LIGHT = os.environ.get("SANITIZE_LIGHT") == "1"
 
 
 def ptr(a):
@@ -46,17 +48,18 @@ def quad(H):
     H.h_quad.argtypes = [I, P, P, I, I, D, D, I, D, I, P, P, P]
     H.h_quad_pk.argtypes = [I, P, P, I, I, D, D, I, D, D, P, P, P]
     H.h_quad_dm.argtypes = [I, P, P, I, I, D, D, I, D, P, P]
-    n_tau = 157
+    n_tau, rtol = (40, 1e-4) if LIGHT else (157, 1e-5)
     bg = records(H, W.BATCH64.params()[:3], n_tau, lambda p, r: H.h_build_bg(ptr(p), n_tau, ptr(r)))
     k = own([0.002, 0.03])
-    for L, n_wide in [(12, 0), (30, 0), (30, 1), (50, 2)]:
+    cases = [(12, 0), (30, 1)] if LIGHT else [(12, 0), (30, 0), (30, 1), (50, 2)]
+    for L, n_wide in cases:
         S, st, steps = np.zeros((3, 2, n_tau, 3)), np.zeros((3, 2), np.int32), np.zeros((3, 2, 2), np.int32)
-        H.h_quad(3, ptr(bg), ptr(k), 2, L, 1e-5, 1e-12, 2_000_000, 1e-4, n_wide, ptr(S), ptr(st), ptr(steps))
+        H.h_quad(3, ptr(bg), ptr(k), 2, L, rtol, 1e-12, 2_000_000, 1e-4, n_wide, ptr(S), ptr(st), ptr(steps))
         assert np.all(st == 0), (L, n_wide, st)
     Pk, st = np.zeros((3, 2)), np.zeros((3, 2), np.int32)
-    H.h_quad_pk(3, ptr(bg), ptr(k), 2, 12, 1e-5, 1e-12, 2_000_000, 1e-4, 0.5, ptr(Pk), ptr(st), None)
+    H.h_quad_pk(3, ptr(bg), ptr(k), 2, 12, rtol, 1e-12, 2_000_000, 1e-4, 0.5, ptr(Pk), ptr(st), None)
     Dm = np.zeros((3, 2, n_tau))
-    H.h_quad_dm(3, ptr(bg), ptr(k), 2, 12, 1e-5, 1e-12, 2_000_000, 1e-4, ptr(Dm), ptr(st))
+    H.h_quad_dm(3, ptr(bg), ptr(k), 2, 12, rtol, 1e-12, 2_000_000, 1e-4, ptr(Dm), ptr(st))
     S, st, steps = np.zeros((1, 1, n_tau, 3)), np.zeros((1, 1), np.int32), np.zeros((1, 1, 2), np.int32)
     H.h_quad(1, ptr(own(bg[:1])), ptr(own([0.05])), 1, 12, 1e-6, 1e-12, 40, 1e-4, 0, ptr(S), ptr(st), ptr(steps))
     assert st[0, 0] == 3  # the step budget
@@ -169,13 +172,13 @@ def adjwarp(H):
     lib = ctypes.CDLL(sys.argv[3])
     lib.h_bg_len.restype = ctypes.c_long
     lib.h_build_bg_warp.argtypes = [P, I, D, I, P]
-    n_tau = 60
+    n_tau, rtol = (30, 1e-3) if LIGHT else (60, 1e-4)
     r = np.zeros(lib.h_bg_len(n_tau))
     lib.h_build_bg_warp(ptr(own(W.BATCH64.params()[0])), n_tau, 0.0, 0, ptr(r))
     S, sig = np.zeros((n_tau, 3)), np.zeros(3, np.int32)
-    assert H.h_fwd_warp(ptr(r), 0.05, 8, 1e-4, ptr(S), ptr(sig)) == 0
+    assert H.h_fwd_warp(ptr(r), 0.05, 8, rtol, ptr(S), ptr(sig)) == 0
     Sb, rb = own(np.random.default_rng(1).normal(size=(n_tau, 3))), np.zeros_like(r)
-    assert H.h_grad_warp(ptr(r), 0.05, 8, 1e-4, ptr(Sb), ptr(rb)) == 0
+    assert H.h_grad_warp(ptr(r), 0.05, 8, rtol, ptr(Sb), ptr(rb)) == 0
     assert np.isfinite(rb).all()
 
 

@@ -47,8 +47,14 @@ extern thread_local EmuDim3 threadIdx, blockIdx, blockDim;
 namespace emu {
 
 // generation-counting barrier: spin briefly, then yield (a CTA's threads share
-// few cores); a wait longer than kDeadlineS means lanes disagree about the
+// few cores; under ThreadSanitizer, where every spin is instrumented, yield at
+// once); a wait longer than kDeadlineS means lanes disagree about the
 // collectives, and the process ends with a message rather than hanging
+#if defined(__SANITIZE_THREAD__)
+constexpr long kSpins = 0;
+#else
+constexpr long kSpins = 64;
+#endif
 struct Barrier {
     explicit Barrier(int n_) : n(n_) {}
     std::atomic<int> count{0}, gen{0};
@@ -65,7 +71,7 @@ struct Barrier {
         long spins = 0;
         auto t0 = std::chrono::steady_clock::now();
         while (gen.load(std::memory_order_acquire) == g) {
-            if (++spins > 64) sched_yield();
+            if (++spins > kSpins) sched_yield();
             if ((spins & 0xfffff) == 0 &&
                 std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > kDeadlineS) {
                 std::fprintf(stderr, "warp emulation: lanes never met at a collective\n");
