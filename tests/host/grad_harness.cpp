@@ -138,3 +138,9 @@ extern "C" void h_record_vjp(int B, long len, const double *recbar, const double
             emu::run_cta((unsigned)b, (unsigned)j, 256,
                          [&] { adj::record_vjp_kernel(B, len, recbar, rp, rm, h, grad); });
 }
+
+// bytes of the gradient workspace grad_layout lays out (tape = ck = 0: the counting pass)
+extern "C" size_t h_grad_layout_bytes(int B, int Nk, int L, long tape, long ck)
+{
+    return adj::grad_layout(B, Nk, ode_dims(L, L, L), tape, ck).total;
+}

@@ -140,6 +140,24 @@ def grad(H):
     H.h_record_vjp(2, n, ptr(rng.normal(size=(2, n))), ptr(rng.normal(size=(2, 6, n))),
                    ptr(rng.normal(size=(2, 6, n))), ptr(rng.uniform(1e-3, 1e-2, size=(2, 6))), ptr(g))
     assert np.isfinite(rb).all() and np.isfinite(g).all()
+    # the ODE passes of the gradient, two one-warp modes per CTA: the counting
+    # pass of taped_kernel, and plain_kernel (the massive-neutrino forward,
+    # here on a massless record)
+    H.h_taped.argtypes = [I, P, P, I, I, D, D, I, P, P, P, P, P]
+    H.h_plain.argtypes = [I, P, P, I, I, I, D, D, I, P, P, P, P]
+    H.h_grad_layout_bytes.restype = ctypes.c_size_t
+    H.h_grad_layout_bytes.argtypes = [I, I, I, ctypes.c_long, ctypes.c_long]
+    n_tau = 40
+    bg2 = records(H, W.BATCH64.params()[:2], n_tau, lambda p, r: H.h_build_bg(ptr(p), n_tau, ptr(r)))
+    k2 = own([0.01, 0.05])
+    S, st, acc = np.zeros((2, 2, n_tau, 3)), np.zeros((2, 2), np.int32), np.zeros((2, 2), np.int32)
+    ws = np.zeros(H.h_grad_layout_bytes(2, 2, 8, 0, 0) // 8 + 1)
+    H.h_taped(2, ptr(bg2), ptr(k2), 2, 8, 1e-4, 1e-14, 10_000_000, ptr(S), ptr(st), ptr(ws), None, ptr(acc))
+    assert np.all(st == 0) and np.all(acc > 0)
+    work = np.zeros(2 * 2 * 64 * (4 + 3 * 9))  # at least V_COUNT (32) vectors of N per mode
+    steps = np.zeros((2, 2, 2), np.int32)
+    H.h_plain(2, ptr(bg2), ptr(k2), 2, 8, 0, 1e-4, 1e-14, 10_000_000, ptr(S), ptr(st), ptr(steps), ptr(work))
+    assert np.all(st == 0)
 
 
 def lens(H):
