@@ -47,22 +47,8 @@ extern "C" size_t abcmb_grad_plan(int B, int Nk, const abcmb_options *o, const i
                                   long long *plan_host)
 {
     if (B < 1 || Nk < 1 || !accepted_host || !plan_host || abcmb_validate_options(o) != ABCMB_OK) return 0;
-    const long M = (long)B * Nk;
-    long long tape = 0, ck = 0;
-    for (long m = 0; m < M; m++) {
-        // mode m = b * Nk + kidx in accepted_host; the kernels number modes k-descending
-        const long kidx = Nk - 1 - m / B, b = m % B;
-        const int a = accepted_host[b * Nk + kidx];
-        if (a < 0) return 0;
-        plan_host[m] = tape;
-        plan_host[M + 1 + m] = ck;
-        tape += a;
-        ck += a / abcmb::adj::kSeg + 1;
-    }
-    plan_host[M] = tape;
-    plan_host[2 * M + 1] = ck;
-    const abcmb::OdeDims d = abcmb::ode_dims(o->lmax_g, o->lmax_pol, o->lmax_nu);
-    return abcmb::adj::grad_layout(B, Nk, d, tape, ck).total;
+    return abcmb::adj::make_plan(B, Nk, abcmb::ode_dims(o->lmax_g, o->lmax_pol, o->lmax_nu), accepted_host,
+                                 plan_host);
 }
 
 namespace {

@@ -64,6 +64,28 @@ __host__ __device__ inline GradLayout grad_layout(int B, int Nk, const OdeDims &
     return g;
 }
 
+// The tape plan (host) from each mode's accepted steps accepted[b][k]: the
+// prefix sums grad_layout's comment describes, in the kernels' mode order
+// (k-descending, then cosmology) -> the workspace bytes, 0 if a count is
+// negative.
+inline size_t make_plan(int B, int Nk, const OdeDims &d, const int *accepted, long long *plan)
+{
+    const long M = (long)B * Nk;
+    long long tape = 0, ck = 0;
+    for (long m = 0; m < M; m++) {
+        const long kidx = Nk - 1 - m / B, b = m % B;
+        const int a = accepted[b * Nk + kidx];
+        if (a < 0) return 0;
+        plan[m] = tape;
+        plan[M + 1 + m] = ck;
+        tape += a;
+        ck += a / kSeg + 1;
+    }
+    plan[M] = tape;
+    plan[2 * M + 1] = ck;
+    return grad_layout(B, Nk, d, tape, ck).total;
+}
+
 // each mode's vectors contiguous, so that the lanes of its warp read and
 // write consecutive elements
 __device__ inline ModeBufs mode_bufs(char *ws, const GradLayout &g, long mi, const long long *plan)

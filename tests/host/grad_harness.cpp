@@ -144,3 +144,9 @@ extern "C" size_t h_grad_layout_bytes(int B, int Nk, int L, long tape, long ck)
 {
     return adj::grad_layout(B, Nk, ode_dims(L, L, L), tape, ck).total;
 }
+
+// the tape plan from the counted steps, as abcmb_grad_plan makes it -> workspace bytes
+extern "C" size_t h_make_plan(int B, int Nk, int L, const int *accepted, long long *plan)
+{
+    return adj::make_plan(B, Nk, ode_dims(L, L, L), accepted, plan);
+}

@@ -154,6 +154,16 @@ def grad(H):
     ws = np.zeros(H.h_grad_layout_bytes(2, 2, 8, 0, 0) // 8 + 1)
     H.h_taped(2, ptr(bg2), ptr(k2), 2, 8, 1e-4, 1e-14, 10_000_000, ptr(S), ptr(st), ptr(ws), None, ptr(acc))
     assert np.all(st == 0) and np.all(acc > 0)
+    # then the recording pass and the reverse sweep in the planned workspace
+    H.h_make_plan.restype = ctypes.c_size_t
+    H.h_make_plan.argtypes = [I, I, I, P, P]
+    H.h_adjoint.argtypes = [I, P, P, I, I, P, P, P, P]
+    plan = np.zeros(2 * 4 + 2, np.int64)
+    ws = np.zeros(H.h_make_plan(2, 2, 8, ptr(acc), ptr(plan)) // 8 + 1)
+    H.h_taped(2, ptr(bg2), ptr(k2), 2, 8, 1e-4, 1e-14, 10_000_000, ptr(S), ptr(st), ptr(ws), ptr(plan), None)
+    Sb2, rb2 = own(rng.normal(size=S.shape)), np.zeros_like(bg2)
+    H.h_adjoint(2, ptr(bg2), ptr(k2), 2, 8, ptr(Sb2), ptr(ws), ptr(plan), ptr(rb2))
+    assert np.all(st == 0) and np.isfinite(rb2).all()
     work = np.zeros(2 * 2 * 64 * (4 + 3 * 9))  # at least V_COUNT (32) vectors of N per mode
     steps = np.zeros((2, 2, 2), np.int32)
     H.h_plain(2, ptr(bg2), ptr(k2), 2, 8, 0, 1e-4, 1e-14, 10_000_000, ptr(S), ptr(st), ptr(steps), ptr(work))
