@@ -85,6 +85,7 @@ def lib():
         L = ctypes.CDLL(LIB_PATH)
         O = ctypes.POINTER(Options)
         L.abcmb_default_options.argtypes = [O]
+        L.abcmb_validate_options.argtypes = [O]
         L.abcmb_bg_doubles.argtypes = [O]
         L.abcmb_bg_doubles.restype = ctypes.c_size_t
         L.abcmb_perturb_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_int, O]
