@@ -19,9 +19,10 @@
  *
  * Conventions shared by every entry point
  *   - Every pointer argument is a DEVICE pointer allocated by the caller
- *     (the library allocates nothing; apart from a server's handle and the
- *     static scratch of abcmb_perturb_noalloc it keeps no state between
- *     calls), unless its name ends in _host.  Every array is C-contiguous
+ *     (the library allocates no device memory; a server allocates its
+ *     handle, streams, events and pinned host staging when it is created;
+ *     apart from a server and the static scratch of abcmb_perturb_noalloc
+ *     it keeps no state between calls), unless its name ends in _host.  Every array is C-contiguous
  *     float64 (int32 for status/step arrays, float32 where a name ends in 32)
  *     in the layout stated at each argument, and must hold at least the
  *     elements that layout gives: a plain pointer carries no extent, so the
