@@ -251,3 +251,49 @@ def test_server_submit_takes_six_parameters(AR):
     assert srv.submit(1, np.zeros(6), 100, 8, 1e-4, 0.1) == A.OK
     (name, args), = rec.calls
     assert name == "abcmb_server_submit" and args[3:] == (100, 8, 1e-4, 0.1)
+
+
+def _args_by_name(name, args):
+    from test_binding_signatures import prototypes
+    params = prototypes()[name][1]
+    assert len(params) == len(args), name
+    return {pname: (a.value if isinstance(a, ctypes.c_void_p) else a) for (_, _, pname), a in zip(params, args)}
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_pipeline_threads_its_buffers_through_the_four_calls(AR, mixed):
+    A, rec = AR
+    o = A.options(lmax_hier=12, lmax_cl=40, n_tau=64)
+    pipe = A.Pipeline(B, np.geomspace(1e-4, 0.1, NK), o, device="cpu", mixed=mixed)
+    params = f64(B, 6)
+    assert pipe.run(params) is pipe.C
+    tail = ["abcmb_project_mixed", "abcmb_cl_mixed"] if mixed else ["abcmb_project", "abcmb_cl"]
+    assert [c[0] for c in rec.calls] == ["abcmb_background_tables", "abcmb_perturb", *tail]
+    bgt, per, proj, cl = (_args_by_name(n, a) for n, a in rec.calls)
+    bg, k = pipe.bg.data_ptr(), pipe.k.data_ptr()
+    assert bgt["B"] == B and bgt["params"] == params.data_ptr() and bgt["bg"] == bg
+    assert per["bg"] == bg and per["k"] == k and per["Nk"] == NK
+    assert (per["S"], per["mode_status"], per["steps"]) == (pipe.S.data_ptr(), pipe.status.data_ptr(),
+                                                            pipe.steps.data_ptr())
+    D = "Delta32" if mixed else "Delta"
+    assert proj["bg"] == bg and proj["S"] == pipe.S.data_ptr() and proj["k"] == k and proj["Nk"] == NK
+    assert cl["bg"] == bg and cl["k"] == k and cl[D] == proj[D] == pipe.D.data_ptr()
+    assert cl["Cl"] == pipe.C.data_ptr()
+    assert pipe.D.dtype == (torch.float32 if mixed else torch.float64)
+    rec.calls.clear()
+    pipe.run()  # no params given: the pipeline's own parameter buffer
+    assert _args_by_name(*rec.calls[0])["params"] == pipe.params.data_ptr()
+
+
+def test_pipeline_status_words_raise(AR):
+    A, _ = AR
+    pipe = A.Pipeline(B, np.geomspace(1e-4, 0.1, NK), A.options(lmax_hier=12, lmax_cl=40, n_tau=64), device="cpu")
+    pipe.bg.zero_()
+    pipe.status.zero_()
+    pipe.check_status()
+    pipe.status[1, 3] = A.E_MAX_STEPS
+    with pytest.raises(RuntimeError, match=r"1 modes failed, first \[1, 3\]: step budget"):
+        pipe.check_status()
+    pipe.bg[1, A.S_INDEX["STATUS"]] = A.E_BACKGROUND
+    with pytest.raises(RuntimeError, match=r"background failed for cosmologies \[1\]"):
+        pipe.check_status()
