@@ -4,8 +4,10 @@ Every buffer a call hands the library is held against the extent that
 include/abcmb.h gives it ([B][Nk][n_tau][3] sources, [B][abcmb_bg_doubles]
 records, ...) before the C entry point is called, so a short tensor is
 refused on the host instead of being read or written past its end; a
-workspace goes over with its size in bytes whatever its dtype; and each
-buffer reaches the entry point.  The compute entry points are replaced by a
+workspace goes over with its size in bytes whatever its dtype; each
+buffer reaches the entry point; and Pipeline hands one set of buffers from
+call to call (the background record to every step, the sources to the
+projection, the transfer functions to the quadrature).  The compute entry points are replaced by a
 recorder and the device test by one that accepts host tensors; the size
 queries (abcmb_bg_doubles, the workspace sizes, the gradient plan) are the
 real library's host functions.
