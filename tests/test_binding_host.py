@@ -7,7 +7,9 @@ refused on the host instead of being read or written past its end; a
 workspace goes over with its size in bytes whatever its dtype; each
 buffer reaches the entry point; and Pipeline hands one set of buffers from
 call to call (the background record to every step, the sources to the
-projection, the transfer functions to the quadrature).  The compute entry points are replaced by a
+projection, the transfer functions to the quadrature), and ClWithGradient
+its forward and reverse calls (each adjoint to the next, the tape and its
+plan from the taped forward to the reverse sweep).  The compute entry points are replaced by a
 recorder and the device test by one that accepts host tensors; the size
 queries (abcmb_bg_doubles, the workspace sizes, the gradient plan) are the
 real library's host functions.
@@ -299,3 +301,66 @@ def test_pipeline_status_words_raise(AR):
     pipe.bg[1, A.S_INDEX["STATUS"]] = A.E_BACKGROUND
     with pytest.raises(RuntimeError, match=r"background failed for cosmologies \[1\]"):
         pipe.check_status()
+
+
+class Filler(Recorder):
+    """A Recorder whose stubs also write what ClWithGradient reads back on
+    the host: clear status words (the background record's and the modes'),
+    and a count of accepted steps for the tape plan."""
+
+    def __getattr__(self, name):
+        call = super().__getattr__(name)
+        if name in SIZE_QUERIES:
+            return call
+
+        def fill(*args):
+            a = _args_by_name(name, args)
+            if name == "abcmb_background_tables":
+                ctypes.memset(a["bg"], 0, a["B"] * self.n_bg * 8)
+            if "mode_status" in a:
+                ctypes.memset(a["mode_status"], 0, a["B"] * a["Nk"] * 4)
+            if "accepted" in a:
+                acc = np.ctypeslib.as_array((ctypes.c_int32 * (a["B"] * a["Nk"])).from_address(a["accepted"]))
+                acc[:] = np.arange(acc.size) + 40  # ragged tapes
+            return call(*args)
+        return fill
+
+
+def test_gradient_function_chains_its_calls(real_lib, monkeypatch):
+    from paper_2602_15104_gb300 import abcmb as A
+    rec = Filler(real_lib)
+    monkeypatch.setattr(A, "lib", lambda: rec)
+    monkeypatch.setattr(A, "_stream", lambda: None)
+    monkeypatch.setattr(A, "_on_gpu", lambda t: isinstance(t, torch.Tensor) and t.is_contiguous())
+    o = A.options(lmax_hier=12, lmax_cl=40, n_tau=64)
+    rec.n_bg = A.bg_doubles(o)
+    params, k = f64(B, 6).requires_grad_(), torch.tensor(np.geomspace(1e-4, 0.1, NK))
+    C = A.cl_with_gradient(params, k, o)
+    fwd = ["abcmb_background_tables", "abcmb_grad_count_steps", "abcmb_perturb_taped", "abcmb_project", "abcmb_cl"]
+    assert [c[0] for c in rec.calls] == fwd
+    bg0, cnt, taped, proj, cl = (_args_by_name(n, a) for n, a in rec.calls)
+    assert bg0["params"] == params.data_ptr()
+    assert cnt["bg"] == taped["bg"] == proj["bg"] == cl["bg"] == bg0["bg"]
+    assert taped["S"] == proj["S"] and proj["Delta"] == cl["Delta"] and cl["Cl"] == C.data_ptr()
+    # the tapes are sized from the counted steps: the plan's total is the workspace
+    acc = np.arange(B * NK, dtype=np.int32) + 40
+    plan = np.empty(2 * B * NK + 2, np.int64)
+    nb = real_lib.abcmb_grad_plan(B, NK, ctypes.byref(o), acc.ctypes.data_as(ctypes.c_void_p),
+                                  plan.ctypes.data_as(ctypes.c_void_p))
+    assert nb > 0 and taped["workspace_bytes"] >= nb
+    rec.calls.clear()
+    Cbar = torch.randn(C.shape, dtype=torch.float64)
+    (g,) = torch.autograd.grad(C, params, Cbar)
+    back = ["abcmb_cl_adjoint", "abcmb_project_adjoint", "abcmb_perturb_adjoint", "abcmb_param_stencil",
+            "abcmb_background_tables", "abcmb_background_tables", "abcmb_record_vjp"]
+    assert [c[0] for c in rec.calls] == back
+    cla, pra, pea, st, bp, bm, vjp = (_args_by_name(n, a) for n, a in rec.calls)
+    assert cla["Clbar"] == Cbar.data_ptr() and cla["Delta"] == cl["Delta"] and cla["bg"] == bg0["bg"]
+    assert pra["Deltabar"] == cla["Deltabar"] and pra["S"] == taped["S"]
+    assert pea["Sbar"] == pra["Sbar"] and pea["workspace"] == taped["workspace"]
+    assert pea["plan_host"] == taped["plan_host"] and pea["workspace_bytes"] == taped["workspace_bytes"]
+    assert cla["recbar"] == pra["recbar"] == pea["recbar"] == vjp["recbar"]
+    assert st["params"] == params.data_ptr()
+    assert bp["params"] == st["params_plus"] and bm["params"] == st["params_minus"]
+    assert (vjp["rec_plus"], vjp["rec_minus"], vjp["h"]) == (bp["bg"], bm["bg"], st["h"])
+    assert vjp["grad"] == g.data_ptr() and g.shape == (B, 6)
